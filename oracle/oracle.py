@@ -1,0 +1,318 @@
+"""FP64 CPU oracle of one MPCD collision interval -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s cpu_baseline /
+reference leg may import this module.  The product package never imports it,
+and it imports nothing from the product package: the oracle and the CUDA path
+share no code.  The arithmetic lives in ``rmpcd_oracle.c`` (compiled here with
+gcc, ``-ffp-contract=off``); this file only marshals numpy arrays.
+
+Order of one collision interval (the paper lists the ingredients in §1.4 but
+not their order; this is the reading used throughout):
+
+    interval motion (MD sub-steps near colloids, free flight elsewhere)
+    -> random grid shift -> stable sort into cells -> collision (SRD / MPC-AT /
+    virtual wall particles) -> bulk B->A reaction -> step counter + 1
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rmpcd_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+F_B = 1      # species B
+F_TAG = 2    # A particle inside a catalytic colloid's range
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, FP64, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+               "-fno-fast-math", "-Wall", "-Wextra", "-Wno-unused-parameter",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("L", C.c_int32 * 3), ("walls", C.c_int32), ("rho_wall", C.c_int32),
+        ("n_md", C.c_int32), ("n_slabs", C.c_int32), ("bulk_mode", C.c_int32),
+        ("kT", C.c_double), ("alpha", C.c_double), ("tau", C.c_double),
+        ("g", C.c_double * 3), ("bulk_rate", C.c_double), ("cat_prob", C.c_double),
+        ("skin", C.c_double),
+        ("slab_x0", C.c_double * 4), ("slab_x1", C.c_double * 4), ("slab_kT", C.c_double * 4),
+        ("cc_eps", C.c_double), ("cc_sigma", C.c_double), ("cc_rc", C.c_double),
+        ("seed", C.c_uint64),
+    ]
+
+
+def make_params(cfg: dict) -> Params:
+    """Fill the oracle's parameter struct from a plain configuration dict."""
+    p = Params()
+    p.L[:] = [int(a) for a in cfg["L"]]
+    p.walls = int(cfg.get("walls", 0))
+    p.rho_wall = int(cfg.get("rho_wall", 0))
+    p.n_md = int(cfg.get("n_md", 1))
+    slabs = cfg.get("slabs", [])
+    p.n_slabs = len(slabs)
+    for k, (x0, x1, kt) in enumerate(slabs):
+        p.slab_x0[k], p.slab_x1[k], p.slab_kT[k] = x0, x1, kt
+    p.bulk_mode = 1 if cfg.get("bulk_rate", 0.0) > 0.0 else 0
+    p.kT = float(cfg["kT"])
+    p.alpha = float(cfg["alpha"])
+    p.tau = float(cfg["tau"])
+    p.g[:] = [float(a) for a in cfg.get("g", (0.0, 0.0, 0.0))]
+    p.bulk_rate = float(cfg.get("bulk_rate", 0.0))
+    p.cat_prob = float(cfg.get("cat_prob", 1.0))
+    p.skin = float(cfg.get("skin", 0.5))
+    cc = cfg.get("cc_lj")
+    if cc:
+        p.cc_eps, p.cc_sigma, p.cc_rc = cc
+    p.seed = int(cfg["seed"]) & 0xFFFFFFFFFFFFFFFF
+    return p
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            d, i64, u32, u8, i32 = C.c_double, C.c_int64, C.c_uint32, C.c_uint8, C.c_int32
+            P = C.POINTER
+            L.orc_philox4x32_10.argtypes = [P(u32), P(u32), P(u32)]
+            L.orc_grid_shift.argtypes = [C.c_uint64, u32, P(d)]
+            L.orc_rotation_axis.argtypes = [C.c_uint64, u32, u32, P(d)]
+            L.orc_n_cells.argtypes = [P(Params)]
+            L.orc_n_cells.restype = i64
+            L.orc_cell_keys.argtypes = [P(Params), i64, P(d), P(d), P(i32)]
+            L.orc_counting_sort.argtypes = [i64, P(i32), i64, P(i64), P(i64), P(i64)]
+            L.orc_gather.argtypes = [i64, P(i64), C.c_void_p, C.c_void_p, i64]
+            L.orc_collide.argtypes = [P(Params), u32, i64, P(i64), P(i64), P(d)]
+            L.orc_bulk_react.argtypes = [P(Params), u32, i64, P(i64), P(i64), P(u8)]
+            L.orc_flight.argtypes = [P(Params), i64, P(d), P(d), P(u8)]
+            L.orc_wca_force.argtypes = [P(d), d, d, d, P(d), P(d)]
+            L.orc_wca_force.restype = C.c_int
+            L.orc_wca_rc2.argtypes = [d]
+            L.orc_wca_rc2.restype = d
+            L.orc_interval.argtypes = [P(Params), u32, i64, P(d), P(d), P(u8), P(u32),
+                                       C.c_int, P(d), P(d), P(d), P(d), P(d), P(d), P(i32),
+                                       C.c_int, P(i32), P(i32), P(d), C.c_int, P(u8)]
+            L.orc_interval.restype = C.c_int
+            L.orc_forces.argtypes = [P(Params), i64, P(d), P(u8), C.c_int, P(d), P(d), P(d), P(d),
+                                     P(d), P(d)]
+            L.orc_potential_energy.argtypes = [P(Params), i64, P(d), P(u8), C.c_int, P(d), P(d), P(d), P(d),
+                                               C.c_int, P(i32), P(i32)]
+            L.orc_potential_energy.restype = d
+            L.orc_temperature.argtypes = [i64, P(i64), P(i64), P(d), P(i64)]
+            L.orc_temperature.restype = d
+            _lib = L
+    return _lib
+
+
+# --------------------------------------------------------------------------
+# thin functional wrappers
+# --------------------------------------------------------------------------
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.asarray(ctr, dtype=np.uint32).copy()
+    k = np.asarray(key, dtype=np.uint32).copy()
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_ptr(c, C.c_uint32), _ptr(k, C.c_uint32), _ptr(out, C.c_uint32))
+    return out
+
+
+def grid_shift(seed: int, step: int) -> np.ndarray:
+    s = np.zeros(3)
+    lib().orc_grid_shift(C.c_uint64(seed), step, _ptr(s, C.c_double))
+    return s
+
+
+def rotation_axis(seed: int, step: int, cell: int) -> np.ndarray:
+    n = np.zeros(3)
+    lib().orc_rotation_axis(C.c_uint64(seed), step, cell, _ptr(n, C.c_double))
+    return n
+
+
+def wca_force(d, sigma, eps, rc2=None):
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    f = np.zeros(3)
+    e = np.zeros(1)
+    if rc2 is None:
+        rc2 = lib().orc_wca_rc2(sigma)
+    hit = lib().orc_wca_force(_ptr(d, C.c_double), sigma, eps, rc2, _ptr(f, C.c_double), _ptr(e, C.c_double))
+    return bool(hit), f, float(e[0])
+
+
+def n_cells(cfg) -> int:
+    p = make_params(cfg)
+    return int(lib().orc_n_cells(C.byref(p)))
+
+
+def cell_keys(cfg, x, s) -> np.ndarray:
+    p = make_params(cfg)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    key = np.zeros(len(x), dtype=np.int32)
+    lib().orc_cell_keys(C.byref(p), len(x), _ptr(x, C.c_double), _ptr(s, C.c_double), _ptr(key, C.c_int32))
+    return key
+
+
+def counting_sort(key, ncells):
+    key = np.ascontiguousarray(key, dtype=np.int32)
+    perm = np.zeros(len(key), dtype=np.int64)
+    count = np.zeros(ncells, dtype=np.int64)
+    start = np.zeros(ncells, dtype=np.int64)
+    lib().orc_counting_sort(len(key), _ptr(key, C.c_int32), ncells, _ptr(perm, C.c_int64),
+                            _ptr(count, C.c_int64), _ptr(start, C.c_int64))
+    return perm, count, start
+
+
+def forces(cfg, x, flags, colloids):
+    """Per-particle WCA force and total (fixed-point summed) colloid force."""
+    p = make_params(cfg)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    flags = np.ascontiguousarray(flags, dtype=np.uint8)
+    nc = len(colloids["mass"])
+    X = np.ascontiguousarray(colloids["x"], dtype=np.float64)
+    f = np.zeros_like(x)
+    F = np.zeros((nc, 3))
+    lib().orc_forces(C.byref(p), len(x), _ptr(x, C.c_double), _ptr(flags, C.c_uint8), nc,
+                     _ptr(X, C.c_double), _ptr(np.ascontiguousarray(colloids["sigma"], np.float64), C.c_double),
+                     _ptr(np.ascontiguousarray(colloids["eps_A"], np.float64), C.c_double),
+                     _ptr(np.ascontiguousarray(colloids["eps_B"], np.float64), C.c_double),
+                     _ptr(f, C.c_double), _ptr(F, C.c_double))
+    return f, F
+
+
+class SkinError(RuntimeError):
+    """A colloid moved further than the skin during one interval."""
+
+
+class OracleSystem:
+    """One replica: solvent state (x, v, flags, id) in storage order, colloids and bonds.
+
+    ``flags``: bit 0 = species B, bit 1 = catalytic tag.  ``id`` is carried so
+    that permutations can be compared; it never enters the arithmetic except as
+    the counter of the catalytic draw.
+    """
+
+    def __init__(self, cfg: dict, x, v, flags=None, ids=None, colloids=None, bonds=None, step: int = 0):
+        self.cfg = dict(cfg)
+        self.p = make_params(cfg)
+        n = len(x)
+        self.x = np.ascontiguousarray(x, dtype=np.float64).reshape(n, 3).copy()
+        self.v = np.ascontiguousarray(v, dtype=np.float64).reshape(n, 3).copy()
+        self.flags = (np.zeros(n, np.uint8) if flags is None else np.asarray(flags, np.uint8).copy())
+        self.id = (np.arange(n, dtype=np.uint32) if ids is None else np.asarray(ids, np.uint32).copy())
+        colloids = colloids or {"x": np.zeros((0, 3)), "v": np.zeros((0, 3)), "mass": [], "sigma": [],
+                                "eps_A": [], "eps_B": [], "catalytic": []}
+        self.X = np.ascontiguousarray(colloids["x"], dtype=np.float64).reshape(-1, 3).copy()
+        self.V = np.ascontiguousarray(colloids["v"], dtype=np.float64).reshape(-1, 3).copy()
+        self.M = np.ascontiguousarray(colloids["mass"], dtype=np.float64)
+        self.sig = np.ascontiguousarray(colloids["sigma"], dtype=np.float64)
+        self.epsA = np.ascontiguousarray(colloids["eps_A"], dtype=np.float64)
+        self.epsB = np.ascontiguousarray(colloids["eps_B"], dtype=np.float64)
+        self.cat = np.ascontiguousarray(colloids["catalytic"], dtype=np.int32)
+        bonds = bonds or []
+        self.ba = np.ascontiguousarray([b[0] for b in bonds], dtype=np.int32)
+        self.bb = np.ascontiguousarray([b[1] for b in bonds], dtype=np.int32)
+        self.bd = np.ascontiguousarray([b[2] for b in bonds], dtype=np.float64)
+        self.step_index = int(step)
+        self.ncells = int(lib().orc_n_cells(C.byref(self.p)))
+        self.key = None
+        self.count = None
+        self.start = None
+        self.perm = None
+        self.near = np.zeros(n, np.uint8)
+
+    @property
+    def n(self):
+        return len(self.x)
+
+    # -- the steps of one interval ------------------------------------------
+    def interval(self, all_substep: bool = False) -> None:
+        """Interval motion: MD sub-steps near colloids, free flight elsewhere."""
+        L = lib()
+        d, u8, u32, i32 = C.c_double, C.c_uint8, C.c_uint32, C.c_int32
+        nc = len(self.M)
+        rc = L.orc_interval(C.byref(self.p), self.step_index, self.n, _ptr(self.x, d), _ptr(self.v, d),
+                            _ptr(self.flags, u8), _ptr(self.id, u32), nc, _ptr(self.X, d), _ptr(self.V, d),
+                            _ptr(self.M, d), _ptr(self.sig, d), _ptr(self.epsA, d), _ptr(self.epsB, d),
+                            _ptr(self.cat, i32), len(self.ba), _ptr(self.ba, i32), _ptr(self.bb, i32),
+                            _ptr(self.bd, d), 1 if all_substep else 0, _ptr(self.near, u8))
+        if rc != 0:
+            raise SkinError("colloid displacement exceeded the skin")
+
+    def shift_and_sort(self) -> None:
+        """Random grid shift, cell keys and stable counting sort; reorders the state."""
+        L = lib()
+        s = grid_shift(self.p.seed, self.step_index)
+        key = np.zeros(self.n, dtype=np.int32)
+        L.orc_cell_keys(C.byref(self.p), self.n, _ptr(self.x, C.c_double), _ptr(s, C.c_double),
+                        _ptr(key, C.c_int32))
+        perm, count, start = counting_sort(key, self.ncells)
+        self.x = self.x[perm]
+        self.v = self.v[perm]
+        self.flags = self.flags[perm]
+        self.id = self.id[perm]
+        self.near = self.near[perm]
+        self.key = key[perm]
+        self.perm, self.count, self.start = perm, count, start
+        self.shift = s
+
+    def collide(self) -> None:
+        lib().orc_collide(C.byref(self.p), self.step_index, self.ncells, _ptr(self.count, C.c_int64),
+                          _ptr(self.start, C.c_int64), _ptr(self.v, C.c_double))
+
+    def react(self) -> None:
+        lib().orc_bulk_react(C.byref(self.p), self.step_index, self.ncells, _ptr(self.count, C.c_int64),
+                             _ptr(self.start, C.c_int64), _ptr(self.flags, C.c_uint8))
+
+    def step(self, k: int = 1, all_substep: bool = False) -> None:
+        """k full collision intervals."""
+        for _ in range(k):
+            self.interval(all_substep)
+            self.shift_and_sort()
+            self.collide()
+            self.react()
+            self.step_index += 1
+
+    # -- observables ---------------------------------------------------------
+    def temperature(self) -> float:
+        """Cell-frame temperature of §1.4 on the current sort (cells with N >= 2)."""
+        used = C.c_int64(0)
+        return float(lib().orc_temperature(self.ncells, _ptr(self.count, C.c_int64),
+                                           _ptr(self.start, C.c_int64), _ptr(self.v, C.c_double),
+                                           C.byref(used)))
+
+    def potential_energy(self) -> float:
+        d, i32 = C.c_double, C.c_int32
+        return float(lib().orc_potential_energy(
+            C.byref(self.p), self.n, _ptr(self.x, d), _ptr(self.flags, C.c_uint8), len(self.M),
+            _ptr(self.X, d), _ptr(self.sig, d), _ptr(self.epsA, d), _ptr(self.epsB, d),
+            len(self.ba), _ptr(self.ba, i32), _ptr(self.bb, i32)))
+
+    def kinetic_energy(self) -> float:
+        return 0.5 * float((self.v ** 2).sum()) + 0.5 * float((self.M[:, None] * self.V ** 2).sum())
+
+    def momentum(self) -> np.ndarray:
+        return self.v.sum(0) + (self.M[:, None] * self.V).sum(0)
+
+    def colloids(self) -> dict:
+        return {"x": self.X.copy(), "v": self.V.copy()}

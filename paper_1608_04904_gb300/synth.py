@@ -1,0 +1,151 @@
+"""Seeded synthetic systems shaped like the paper's simulation setups.
+
+This module only builds inputs: parameter dicts and initial solvent/colloid
+states drawn with numpy's PCG64.  It holds none of the method's arithmetic and
+is shared by the tests, ``bench.py`` and the oracle checks.
+
+Positions are drawn as integer multiples of 2^-24 so that ``cell + offset``
+with an FP32 offset represents them exactly; for the mixed-precision path the
+velocities are rounded to FP32 values, so both sides of a parity test start
+from the same numbers.
+
+Workloads (stand-ins for the paper's ``experiments/``, §1.5 and Appendix A):
+
+* ``sphere16``   -- 16^3 periodic box, rho = 10, one WCA sphere (sigma 2, M 200),
+  alpha 130 deg, tau 0.5, 50 MD sub-steps, FP64.
+* ``dimer32``    -- reactive sphere-dimer nanomotor (``single_dimer_pbc``), 32^3,
+  rho = 10, catalytic C and inert N (sigma 2, M 100, bond 4.5), kT = 1/3,
+  alpha 90 deg, tau 0.5, 50 sub-steps, A->B on leaving C, bulk B->A k = 0.01.
+* ``poiseuille128`` -- 128^3 channel with stick walls at z = 0, 128, body
+  acceleration 0.001 along x, alpha 130 deg, tau 1 (``poiseuille_flow``).
+* ``thermal256`` -- 256 x 64 x 64, 64 WCA spheres (sigma 2.5, M 150), MPC-AT
+  slabs at kT 1.2 / 0.8, colloid-colloid LJ (``single_sphere_thermo_trap``).
+* ``batch``      -- independent replicas with cubic sides drawn from
+  {16, 20, 24, 32, 40, 48}.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+WCA_RC_FACTOR = 2.0 ** (1.0 / 6.0)
+
+
+def base_config(**kw) -> dict:
+    cfg = {
+        "L": (16, 16, 16), "rho": 10, "kT": 1.0, "alpha": math.radians(130.0), "tau": 0.5,
+        "n_md": 50, "walls": 0, "rho_wall": 0, "g": (0.0, 0.0, 0.0), "bulk_rate": 0.0,
+        "cat_prob": 1.0, "skin": 0.5, "slabs": [], "cc_lj": None, "seed": 1,
+        "precision": "fp64", "bucket_cap": 64,
+    }
+    cfg.update(kw)
+    return cfg
+
+
+def sphere16(precision="fp64", seed=1):
+    cfg = base_config(L=(16, 16, 16), alpha=math.radians(130.0), tau=0.5, n_md=50, kT=1.0,
+                      seed=seed, precision=precision)
+    col = [dict(x=(8.0, 8.0, 8.0), v=(0.0, 0.0, 0.0), mass=200.0, sigma=2.0, eps_A=1.0, eps_B=1.0,
+                catalytic=0)]
+    return cfg, col, []
+
+
+def dimer32(precision="mixed", seed=2, L=32):
+    cfg = base_config(L=(L, L, L), alpha=math.radians(90.0), tau=0.5, n_md=50, kT=1.0 / 3.0,
+                      bulk_rate=0.01, cat_prob=1.0, seed=seed, precision=precision)
+    c = L / 2.0
+    col = [dict(x=(c - 2.25, c, c), v=(0.0, 0.0, 0.0), mass=100.0, sigma=2.0, eps_A=1.0, eps_B=1.0,
+                catalytic=1),
+           dict(x=(c + 2.25, c, c), v=(0.0, 0.0, 0.0), mass=100.0, sigma=2.0, eps_A=1.0, eps_B=0.1,
+                catalytic=0)]
+    return cfg, col, [(0, 1, 4.5)]
+
+
+def poiseuille(precision="mixed", seed=3, L=(128, 128, 128), g=0.001):
+    cfg = base_config(L=tuple(L), alpha=math.radians(130.0), tau=1.0, n_md=1, kT=1.0, walls=1,
+                      rho_wall=10, g=(g, 0.0, 0.0), seed=seed, precision=precision)
+    return cfg, [], []
+
+
+def thermal(precision="mixed", seed=5, L=(256, 64, 64), n_spheres=64):
+    cfg = base_config(L=tuple(L), alpha=math.radians(130.0), tau=0.5, n_md=50, kT=1.0,
+                      slabs=[(0.0, 8.0, 1.2), (L[0] / 2.0, L[0] / 2.0 + 8.0, 0.8)],
+                      cc_lj=(1.0, 5.5, 2.5 * 5.5), seed=seed, precision=precision)
+    rng = np.random.Generator(np.random.PCG64(seed + 1000))
+    pos = []
+    dmin = WCA_RC_FACTOR * 5.5
+    while len(pos) < n_spheres:
+        p = rng.uniform(0, 1, 3) * np.asarray(L, float)
+        ok = True
+        for q in pos:
+            d = p - q
+            d -= np.asarray(L) * np.round(d / np.asarray(L))
+            if np.dot(d, d) < dmin * dmin:
+                ok = False
+                break
+        if ok:
+            pos.append(p)
+    col = [dict(x=tuple(p), v=(0.0, 0.0, 0.0), mass=150.0, sigma=2.5, eps_A=1.0, eps_B=1.0, catalytic=0)
+           for p in pos]
+    return cfg, col, []
+
+
+def colloid_arrays(col) -> dict:
+    n = len(col)
+    return {
+        "x": np.asarray([c["x"] for c in col], dtype=np.float64).reshape(n, 3),
+        "v": np.asarray([c["v"] for c in col], dtype=np.float64).reshape(n, 3),
+        "mass": np.asarray([c["mass"] for c in col], dtype=np.float64),
+        "sigma": np.asarray([c["sigma"] for c in col], dtype=np.float64),
+        "eps_A": np.asarray([c["eps_A"] for c in col], dtype=np.float64),
+        "eps_B": np.asarray([c["eps_B"] for c in col], dtype=np.float64),
+        "catalytic": np.asarray([c["catalytic"] for c in col], dtype=np.int32),
+    }
+
+
+def solvent(cfg, col=(), n=None, seed=None, frac_b=0.0, tag_frac=0.0, exclude=True, exclude_factor=None):
+    """Uniform positions (multiples of 2^-24) outside every colloid's cut-off
+    (or outside ``exclude_factor * sigma`` when given),
+    Maxwell-Boltzmann velocities at kT with the mean removed, species A (or a
+    fraction ``frac_b`` of B)."""
+    L = np.asarray(cfg["L"], dtype=np.int64)
+    if n is None:
+        n = int(cfg["rho"] * L.prod())
+    rng = np.random.Generator(np.random.PCG64(cfg["seed"] if seed is None else seed))
+    scale = np.int64(1) << np.int64(24)
+    x = np.empty((n, 3), dtype=np.float64)
+    todo = np.arange(n)
+    cx = np.asarray([c["x"] for c in col], dtype=np.float64).reshape(-1, 3)
+    fac = WCA_RC_FACTOR if exclude_factor is None else exclude_factor
+    rcs = np.asarray([fac * c["sigma"] for c in col], dtype=np.float64)
+    for _ in range(1000):
+        k = len(todo)
+        if k == 0:
+            break
+        ints = rng.integers(0, L * scale, size=(k, 3), dtype=np.int64)
+        x[todo] = ints.astype(np.float64) * 2.0 ** -24
+        if not exclude or len(col) == 0:
+            todo = todo[:0]
+            break
+        bad = np.zeros(k, dtype=bool)
+        for j in range(len(col)):
+            d = x[todo] - np.mod(cx[j], L)
+            d -= L * np.round(d / L)
+            bad |= (d * d).sum(1) < rcs[j] ** 2
+        todo = todo[bad]
+    v = rng.standard_normal((n, 3)) * math.sqrt(cfg["kT"])
+    v -= v.mean(axis=0)
+    if cfg.get("precision", "fp64") == "mixed":
+        v = v.astype(np.float32).astype(np.float64)
+    flags = np.zeros(n, dtype=np.uint8)
+    if frac_b > 0:
+        flags |= (rng.uniform(size=n) < frac_b).astype(np.uint8)
+    if tag_frac > 0:
+        flags |= ((rng.uniform(size=n) < tag_frac) & ((flags & 1) == 0)).astype(np.uint8) * 2
+    return x, v, flags
+
+
+def batch_sides(n_replicas, seed=4):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [int(s) for s in rng.choice([16, 20, 24, 32, 40, 48], size=n_replicas)]
