@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark of the fused MPCD collision interval on GB300.
+
+Metric: MPCD solvent particle-steps/s (one particle-step = one solvent particle
+advanced through one full collision interval: near-colloid MD sub-steps or free
+flight, grid shift, sort, collision, reactions), mixed FP32 path, with the FP64
+path on the same workload for comparison, and the HBM roofline fraction of the
+dominant kernel.
+
+Default workload: the reactive sphere-dimer nanomotor in a 32^3 box at density
+10 (327,680 solvent), 50 MD sub-steps of dt = 0.01 per collision, alpha = 90 deg,
+kT = 1/3, A -> B at the catalytic sphere and bulk B -> A at k = 0.01.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload dimer32|sphere16|poiseuille128] [--precision mixed|fp64]
+
+With torchrun (N > 1) every rank runs an independent replica of the workload
+(replicas only: the method has no data exchange between independent systems).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MPCD solvent particle-steps/s, mixed-FP32 vs FP64 on 1 GB300; HBM roofline %"
+UNIT = "particle-steps/s"
+# algorithmic bytes per particle-step of the cell pass: record read + write
+# (28 B mixed / 52 B fp64 of state each way) + bucket entry write + read
+ALG_BYTES = {"mixed": 64, "fp64": 112}
+L2_FLUSH_BYTES = 256 << 20
+KERNEL_NAMES = {"cellpass": "k_cellpass", "md": "k_md", "prime": "k_particles", "obs": "k_obs_reduce"}
+KERNEL_SOURCES = ["rmpcd_common.cuh", "rmpcd_kernels.cuh", "k_cellpass.cu", "k_md.cu", "k_particles.cu"]
+
+
+def workload(name, precision, seed_offset=0):
+    from paper_1608_04904_gb300 import synth
+    if name == "dimer32":
+        cfg, col, bonds = synth.dimer32(precision=precision, seed=2 + seed_offset)
+        desc = ("reactive sphere dimer (C+N, sigma 2, M 100, bond 4.5), 32^3 periodic box, rho 10, "
+                "327680 solvent, 50 MD sub-steps dt 0.01, alpha 90 deg, tau 0.5, kT 1/3, p_cat 1, bulk k 0.01")
+    elif name == "sphere16":
+        cfg, col, bonds = synth.sphere16(precision=precision, seed=1 + seed_offset)
+        desc = "one WCA sphere (sigma 2, M 200), 16^3 periodic box, rho 10, 40960 solvent, 50 MD sub-steps"
+    elif name == "poiseuille128":
+        cfg, col, bonds = synth.poiseuille(precision=precision, seed=3 + seed_offset)
+        desc = ("Poiseuille channel 128^3 with stick walls in z, rho 10, 20971520 solvent, g 0.001 x, "
+                "alpha 130 deg, tau 1")
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return cfg, col, bonds, desc
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for s in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1608_04904_gb300", "csrc", s), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel, workload_name, precision):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or None
+    when absent or taken on a different kernel build."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_hash") != kernel_hash():
+        return None
+    e = d.get("kernels", {}).get(f"{kernel}/{workload_name}/{precision}")
+    return None if e is None else e.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"rmpcd_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(name, precision, budget_s=15.0):
+    """The oracle, as it stands, on the host cores: full collision intervals of
+    the same workload until the time budget is spent (after one warm-up)."""
+    from oracle import oracle
+    from paper_1608_04904_gb300 import synth
+    oracle.build()
+    cfg, col, bonds, _ = workload(name, precision)
+    x, v, fl = synth.solvent(cfg, col, seed=cfg["seed"] + 100)
+    o = oracle.OracleSystem(cfg, x, v, fl, colloids=synth.colloid_arrays(col) if col else None, bonds=bonds)
+    o.step(1)
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        o.step(1)
+        k += 1
+        el = time.perf_counter() - t0
+        if (el >= budget_s and k >= 2) or k >= 10000:
+            break
+    return {"value": len(x) * k / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{k} full collision intervals of the workload ({len(x)} solvent) after 1 warm-up, "
+                      f"{el:.1f} s, single-threaded FP64 C oracle", "seconds": el}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    from paper_1608_04904_gb300 import synth
+    cfg, col, bonds, desc = workload(args.workload, args.precision)
+    from oracle import oracle
+    oracle.build()
+    x, v, fl = synth.solvent(cfg, col, seed=cfg["seed"] + 100)
+    o = oracle.OracleSystem(cfg, x, v, fl, colloids=synth.colloid_arrays(col) if col else None, bonds=bonds)
+    for _ in range(args.warmup):
+        o.step(1)
+    budget = 150.0
+    times = []
+    t_all = time.perf_counter()
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        o.step(1)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_all > budget:
+            break
+    done = len(times)
+    tot = sum(times)
+    value = len(x) * done / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": done,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot / done, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {desc}", "n_solvent": len(x), "precision": "fp64 oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{done} of {args.steps} requested full intervals (time budget {budget:.0f} s) "
+                                   f"after {args.warmup} warm-up"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def timed_run(api, torch, cfg, col, bonds, x, v, fl, precision, steps, warmup, flush, dev_index, sample_clocks,
+              barrier):
+    stream = torch.cuda.current_stream()
+    s = api.System.single(cfg, len(x), col, bonds, precision=precision, stream=stream)
+    s.set_state(0, x, v, fl)
+    for _ in range(warmup):
+        s.step(1)
+    torch.cuda.synchronize()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    s.enable_timers(True)
+    s.read_timers(reset=True)
+    launches0 = s.launch_count()
+    clk = ClockSampler(dev_index) if sample_clocks else None
+    if clk:
+        clk.start()
+        time.sleep(0.25)
+    barrier()
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.zero_()
+        ev0[k].record(stream)
+        s.step(1)
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop() if clk else None
+    launches = s.launch_count() - launches0
+    ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+    timers = s.read_timers(reset=True)
+    s.enable_timers(False)
+    obs = s.observables(0)
+    s.close()
+    return ms, timers, launches, clocks, obs
+
+
+def e2e_run(api, torch, cfg, col, bonds, x, v, fl, precision, steps):
+    """Same metric through the public API with pinned host buffers: every step
+    copies the state in, runs one interval and reads the state back."""
+    n = len(x)
+    pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
+    xh, vh, fh = pin((n, 3), torch.float64), pin((n, 3), torch.float64), pin((n,), torch.uint8)
+    xh[:], vh[:], fh[:] = x, v, fl
+    out = {"x": pin((n, 3), torch.float64), "v": pin((n, 3), torch.float64), "flags": pin((n,), torch.uint8)}
+    s = api.System.single(cfg, n, col, bonds, precision=precision, stream=torch.cuda.current_stream())
+    s.set_state(0, xh, vh, fh)
+    s.step(1)
+    s.get_state(0, out=out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s.set_state(0, xh, vh, fh)
+        s.step(1)
+        s.get_state(0, out=out)
+        # the state read back is the next step's input
+        xh, out["x"] = out["x"], xh
+        vh, out["v"] = out["v"], vh
+        fh, out["flags"] = out["flags"], fh
+    el = time.perf_counter() - t0
+    s.close()
+    per = n * (24 + 24 + 1)
+    return {"value": n * steps / el, "unit": UNIT, "h2d_bytes_per_step": per, "d2h_bytes_per_step": per,
+            "steps": steps, "api": "rmpcd_set_state(host) + rmpcd_step(1) + rmpcd_get_state(host), pinned"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dimer32", choices=["dimer32", "sphere16", "poiseuille128"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    ws, rank, local = dist_setup()
+
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        barrier = lambda: dist.barrier()
+    else:
+        barrier = lambda: None
+
+    from paper_1608_04904_gb300 import api, build, synth
+    build.build()
+    api.load()
+
+    cfg, col, bonds, desc = workload(args.workload, args.precision, seed_offset=rank)
+    x, v, fl = synth.solvent(cfg, col, seed=cfg["seed"] + 100)
+    n = len(x)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    ms, timers, launches, clocks, obs = timed_run(api, torch, cfg, col, bonds, x, v, fl, args.precision,
+                                                  args.steps, args.warmup, flush, local, rank == 0, barrier)
+    ms_max = ms
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = ws * n * args.steps / (ms_max / 1e3)
+
+    # roofline of the dominant kernel (CUDA events around each launch on the library's stream)
+    phases = {k: v_ for k, v_ in timers.items() if v_["launches"] > 0}
+    dominant = max(phases, key=lambda k: phases[k]["ms"])
+    peak, peak_src = measured_peaks()
+    kernels = {}
+    for k, t in phases.items():
+        avg_ms = t["ms"] / t["launches"]
+        entry = {"launches": t["launches"], "avg_us": 1e3 * avg_ms, "share": t["ms"] / sum(p["ms"] for p in phases.values())}
+        if k == "cellpass":
+            alg = n * ALG_BYTES[args.precision]
+            entry.update({"alg_bytes_per_launch": alg, "achieved_gbs": alg / (avg_ms / 1e3) / 1e9})
+        kernels[KERNEL_NAMES[k]] = entry
+    cp = phases["cellpass"]
+    cp_avg_s = cp["ms"] / cp["launches"] / 1e3
+    alg = n * ALG_BYTES[args.precision]
+    achieved = alg / cp_avg_s / 1e9
+    roofline = {"kernel": "k_cellpass", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": ncu_traffic("k_cellpass", args.workload, args.precision),
+                "peak_source": f"{peak_src} hbm_gbs", "dominant_kernel": KERNEL_NAMES[dominant],
+                "alg_bytes_per_particle": ALG_BYTES[args.precision]}
+    if dominant == "md":
+        md = phases["md"]
+        roofline["note"] = ("k_md (near-colloid velocity-Verlet, %d dependent sub-steps in one CTA) takes %.0f%% of "
+                            "the step and is latency-bound; the HBM roofline is that of the cell pass"
+                            % (cfg["n_md"], 100 * md["ms"] / sum(p["ms"] for p in phases.values())))
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {desc}", "n_solvent": n, "precision": args.precision,
+                   "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
+                   "timing": "CUDA events around each rmpcd_step(1) on the library's stream"},
+        "roofline": roofline, "kernels": kernels, "gpu_launches": launches, "clocks": clocks,
+        "observables": {"temperature": obs["temperature"], "n_B": obs["n_B"], "kT": cfg["kT"]},
+    }
+    if rank == 0 and not args.no_fp64 and args.precision == "mixed":
+        k64 = max(20, args.steps // 4)
+        ms64, t64, _, _, _ = timed_run(api, torch, cfg, col, bonds, x, v, fl, "fp64", k64, args.warmup, flush, local,
+                                       False, lambda: None)
+        v64 = n * k64 / (ms64 / 1e3)
+        line["fp64"] = {"value": v64, "ms_per_step": ms64 / k64, "steps": k64,
+                        "cellpass_avg_us": 1e3 * t64["cellpass"]["ms"] / t64["cellpass"]["launches"]}
+        line["speedup_mixed_over_fp64"] = (n * args.steps / (ms / 1e3)) / v64
+    if rank == 0 and not args.no_e2e:
+        line["e2e"] = e2e_run(api, torch, cfg, col, bonds, x, v, fl, args.precision, min(args.steps, 200))
+    if rank == 0 and not args.no_cpu and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(args.workload, args.precision)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

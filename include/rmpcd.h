@@ -1,0 +1,205 @@
+/*
+ * rmpcd.h -- C ABI of the GB300 (sm_103a) MPCD solvent collision-interval update.
+ *
+ * Method: Multiparticle Collision Dynamics solvent coupled to colloids by MD,
+ * as described by de Buyl, Huang & Deprez, "RMPCDMD" (arXiv:1608.04904):
+ * §1.1 (solvent + colloids in a cuboid, velocity-Verlet, no solvent-solvent
+ * potential, bulk RMPCD reactions), §1.4 (SRD collision rule, Anderson
+ * thermostat, random grid shift, body force, bounce-back walls with virtual
+ * particles, WCA colloid-solvent potential, Verlet/cell lists sharing the MPCD
+ * sort, exact RATTLE for the dimer, counter-based RNG, temperature estimator),
+ * §1.5 (catalytic A -> B at the dimer's C sphere) and Appendix A (parameters).
+ *
+ * Conventions for every entry point:
+ *   - Every call returns an rmpcd_status; no call prints or aborts.
+ *   - Work is queued on the CUDA stream given to rmpcd_create and is
+ *     asynchronous, except where a call says it synchronises.  Errors raised
+ *     by kernels (bucket overflow, skin violation, a look-back that timed out)
+ *     are latched on the device and returned by the next synchronising call
+ *     (rmpcd_sync, rmpcd_get_state, rmpcd_observables).
+ *   - Host buffers passed in are copied before the call returns (or, for
+ *     on_device = 0 outputs, filled before it returns); the library never keeps
+ *     a caller's pointer.  All device memory of a system is owned by the
+ *     library and released by rmpcd_destroy.
+ *   - rmpcd_last_error() gives a one-line description of the last failure.
+ *
+ * Units: cell side a = 1, solvent mass m = 1.  Solvent flags: bit 0 = species
+ * B (else A), bit 1 = catalytic tag (an A particle currently inside a
+ * catalytic colloid's interaction range).
+ */
+#ifndef RMPCD_H
+#define RMPCD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rmpcd_system rmpcd_system;
+
+typedef enum {
+    RMPCD_OK = 0,
+    RMPCD_EINVAL = 1,     /* invalid argument or parameter combination          */
+    RMPCD_ECUDA = 2,      /* a CUDA runtime call failed                          */
+    RMPCD_ENOMEM = 3,     /* device allocation failed                            */
+    RMPCD_EOVERFLOW = 4,  /* a cell held more particles than bucket_cap          */
+    RMPCD_ESKIN = 5,      /* a colloid moved further than skin in one interval   */
+    RMPCD_ETIMEOUT = 6,   /* a bounded device wait ran out (state is invalid)    */
+    RMPCD_ESTATE = 7      /* call not valid in the current state                 */
+} rmpcd_status;
+
+typedef enum { RMPCD_FP64 = 0, RMPCD_MIXED = 1 } rmpcd_precision;
+
+/* Parameters of one replica (one independent system).  §1.4, Appendix A. */
+typedef struct {
+    int32_t L[3];          /* box sides in cells, each in [2, 1023]                      */
+    int32_t walls;         /* 1: stick walls at z = 0 and z = L[2] (bounce-back + virtual particles) */
+    int32_t rho_wall;      /* particles per cell that virtual particles fill wall cells up to */
+    int32_t n_md;          /* velocity-Verlet sub-steps per collision interval (dt = tau / n_md) */
+    int32_t n_slabs;       /* number of Anderson-thermostat (MPC-AT) slabs, 0..4          */
+    int32_t n_solvent;     /* solvent particles of this replica                          */
+    int32_t n_colloids;    /* colloids of this replica                                   */
+    int32_t n_bonds;       /* rigid bonds (RATTLE) between this replica's colloids       */
+    double kT;             /* solvent temperature                                        */
+    double alpha;          /* SRD rotation angle in radians                              */
+    double tau;            /* collision interval                                         */
+    double g[3];           /* body acceleration on the solvent (g[2] must be 0 with walls) */
+    double bulk_rate;      /* bulk B -> A rate k; 0 disables the bulk reaction            */
+    double cat_prob;       /* probability of A -> B when a tagged A leaves catalytic range */
+    double skin;           /* bound on colloid displacement per interval                 */
+    double slab_x0[4], slab_x1[4], slab_kT[4];  /* MPC-AT slabs: cells with x0 <= cx < x1 */
+    double cc_eps, cc_sigma, cc_rc;             /* colloid-colloid LJ; cc_rc = 0 disables  */
+    uint64_t seed;         /* key of the counter-based RNG                               */
+} rmpcd_params;
+
+/* One colloid (§1.1: mass, position, velocity; §1.4: WCA sigma and per-species
+ * epsilon).  x is kept unwrapped. */
+typedef struct {
+    double x[3], v[3];
+    double mass, sigma, eps_A, eps_B;
+    int32_t catalytic;     /* 1: converts A -> B (§1.5)                                */
+    int32_t pad;
+} rmpcd_colloid;
+
+/* A rigid bond |x_a - x_b| = d held by exact RATTLE (§1.4, dimer motor).
+ * a and b index the replica's own colloids. */
+typedef struct {
+    int32_t a, b;
+    double d;
+} rmpcd_bond;
+
+/* Observables of one replica after the last collision (§1.4 temperature
+ * estimator; totals accumulated in FP64). */
+typedef struct {
+    double temperature;    /* 1/(3 N_c) sum_cells 1/(N-1) sum (v - v_cell)^2, cells with N >= 2 */
+    double momentum[3];    /* total solvent momentum                                    */
+    double kinetic;        /* total solvent kinetic energy                              */
+    int64_t n_cells_used;  /* N_c                                                       */
+    int64_t n_B;           /* solvent particles of species B                            */
+    int64_t n_solvent;
+    uint32_t step;         /* collision index the values belong to                      */
+    uint32_t pad;
+} rmpcd_obs;
+
+/* Create a system of n_replicas independent replicas on the current CUDA
+ * device.  params[n_replicas]; colloids and bonds are the replicas' lists
+ * concatenated in replica order (params[r].n_colloids / n_bonds entries each;
+ * may be NULL when all counts are 0).  precision: rmpcd_precision.
+ * bucket_cap: most particles one cell may hold (1..768; 64 is safe at
+ * density 10).  stream: a cudaStream_t, or NULL for the legacy default
+ * stream.  Solvent state is all zero until rmpcd_set_state.
+ * Errors: EINVAL (bad sizes or parameters), ENOMEM, ECUDA. */
+rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_replicas,
+                          const rmpcd_params *params, const rmpcd_colloid *colloids,
+                          const rmpcd_bond *bonds, int32_t bucket_cap, void *stream);
+
+/* Release every device buffer of the system.  NULL is accepted. */
+void rmpcd_destroy(rmpcd_system *sys);
+
+/* Load the solvent of one replica: x[n][3] and v[n][3] FP64 (row-major,
+ * x in [0, L) on periodic axes and [0, L[2]] with walls), flags[n] (may be
+ * NULL = all A), n = params.n_solvent.  on_device = 1: the three pointers are
+ * device pointers; 0: host pointers.  Particle ids are set to 0..n-1.  Any
+ * pending fused-step state is discarded.  Errors: EINVAL, ECUDA. */
+rmpcd_status rmpcd_set_state(rmpcd_system *sys, int32_t replica, const double *x, const double *v,
+                             const uint8_t *flags, int64_t n, int32_t on_device);
+
+/* Read the solvent of one replica in storage order (which, after any sort
+ * or step, is the sorted-cell order of the last collision).  Any output
+ * pointer may be NULL.  id[n]: particle ids; cell[n]: key of each particle's
+ * cell on the grid of the last sort (-1 before any sort).  Synchronises and
+ * returns latched device errors.  Errors: EINVAL, ECUDA, EOVERFLOW, ESKIN, ETIMEOUT. */
+rmpcd_status rmpcd_get_state(rmpcd_system *sys, int32_t replica, double *x, double *v, uint8_t *flags,
+                             uint32_t *id, int32_t *cell, int64_t n, int32_t on_device);
+
+/* Colloids of one replica (host arrays of params.n_colloids entries). */
+rmpcd_status rmpcd_set_colloids(rmpcd_system *sys, int32_t replica, const rmpcd_colloid *c, int32_t n);
+rmpcd_status rmpcd_get_colloids(rmpcd_system *sys, int32_t replica, rmpcd_colloid *c, int32_t n);
+
+/* Collision counter that keys every random draw of the next interval. */
+rmpcd_status rmpcd_set_step(rmpcd_system *sys, uint32_t step);
+rmpcd_status rmpcd_get_step(const rmpcd_system *sys, uint32_t *step);
+
+/* --- granular steps of one interval (§1.1, §1.4), all replicas ----------- */
+
+/* Interval motion: solvent that may come within a colloid's cut-off during
+ * the interval (distance < r_c + |v| tau + |g| tau^2 / 2 + skin) is integrated
+ * with the colloids by n_md velocity-Verlet sub-steps under WCA forces, with
+ * exact RATTLE on bonds and catalytic A -> B on leaving a catalytic colloid;
+ * all other solvent flies freely over tau (body force, bounce-back walls).
+ * Does not advance the step counter. */
+rmpcd_status rmpcd_stream(rmpcd_system *sys);
+
+/* Random grid shift of the current step, cell keys and stable counting sort:
+ * storage becomes sorted by cell, ties kept in previous storage order. */
+rmpcd_status rmpcd_shift_and_sort(rmpcd_system *sys);
+
+/* Collision on the grid of the current step: SRD rotation by alpha about a
+ * random axis per cell; MPC-AT inside slabs; virtual particles in wall cells.
+ * Requires the state sorted on that grid (rmpcd_shift_and_sort). */
+rmpcd_status rmpcd_collide(rmpcd_system *sys);
+
+/* Bulk B -> A reaction per cell (one B with probability 1 - exp(-k N_B tau)).
+ * Requires the state sorted on the current grid. */
+rmpcd_status rmpcd_react(rmpcd_system *sys);
+
+/* n_intervals full collision intervals (motion, shift, sort, collision,
+ * bulk reaction), fused into two kernels per interval; the step counter
+ * advances by n_intervals.  Equivalent to the granular sequence
+ * stream, shift_and_sort, collide, react, step + 1. */
+rmpcd_status rmpcd_step(rmpcd_system *sys, int32_t n_intervals);
+
+/* Observables of one replica for the last collision.  Synchronises. */
+rmpcd_status rmpcd_observables(rmpcd_system *sys, int32_t replica, rmpcd_obs *out);
+
+/* Wait for all queued work and return latched device errors. */
+rmpcd_status rmpcd_sync(rmpcd_system *sys);
+
+/* Per-phase GPU timers (the paper's per-phase timers, §1.2 `timers`).  When
+ * enabled, rmpcd_step records a CUDA event pair on the system's stream
+ * around each kernel it launches; rmpcd_read_timers synchronises and returns,
+ * per phase, the launches and their summed duration since the last reset.
+ * Phases: 0 = first binning of a fused run, 1 = near-colloid MD,
+ * 2 = cell pass (sort + collide + react + next flight/bin), 3 = observables. */
+typedef struct {
+    int64_t launches[4];
+    double ms[4];
+} rmpcd_timers;
+
+rmpcd_status rmpcd_enable_timers(rmpcd_system *sys, int32_t on);
+rmpcd_status rmpcd_read_timers(rmpcd_system *sys, rmpcd_timers *out, int32_t reset);
+
+/* Count of this library's kernel launches since creation (for accounting). */
+rmpcd_status rmpcd_launch_count(const rmpcd_system *sys, int64_t *count);
+
+/* One-line description of the last failure of this system (or of the last
+ * failed rmpcd_create when sys is NULL).  Never NULL. */
+const char *rmpcd_last_error(const rmpcd_system *sys);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RMPCD_H */

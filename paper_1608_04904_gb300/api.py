@@ -1,0 +1,326 @@
+"""Thin ctypes binding of the C ABI in ``include/rmpcd.h`` (argument marshalling only).
+
+Every step of the collision interval runs in the CUDA kernels of
+``_build/librmpcd.so``; if that library is missing this module raises -- there
+is no CPU path.  PyTorch is used only for device buffers and the current CUDA
+stream when it is available.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+RMPCD_FP64 = 0
+RMPCD_MIXED = 1
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ECUDA", 3: "ENOMEM", 4: "EOVERFLOW", 5: "ESKIN", 6: "ETIMEOUT", 7: "ESTATE"}
+
+
+class RmpcdError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"rmpcd {STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.code = STATUS.get(status, str(status))
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("L", C.c_int32 * 3), ("walls", C.c_int32), ("rho_wall", C.c_int32), ("n_md", C.c_int32),
+        ("n_slabs", C.c_int32), ("n_solvent", C.c_int32), ("n_colloids", C.c_int32), ("n_bonds", C.c_int32),
+        ("kT", C.c_double), ("alpha", C.c_double), ("tau", C.c_double), ("g", C.c_double * 3),
+        ("bulk_rate", C.c_double), ("cat_prob", C.c_double), ("skin", C.c_double),
+        ("slab_x0", C.c_double * 4), ("slab_x1", C.c_double * 4), ("slab_kT", C.c_double * 4),
+        ("cc_eps", C.c_double), ("cc_sigma", C.c_double), ("cc_rc", C.c_double), ("seed", C.c_uint64),
+    ]
+
+
+class Colloid(C.Structure):
+    _fields_ = [("x", C.c_double * 3), ("v", C.c_double * 3), ("mass", C.c_double), ("sigma", C.c_double),
+                ("eps_A", C.c_double), ("eps_B", C.c_double), ("catalytic", C.c_int32), ("pad", C.c_int32)]
+
+
+class Bond(C.Structure):
+    _fields_ = [("a", C.c_int32), ("b", C.c_int32), ("d", C.c_double)]
+
+
+class Obs(C.Structure):
+    _fields_ = [("temperature", C.c_double), ("momentum", C.c_double * 3), ("kinetic", C.c_double),
+                ("n_cells_used", C.c_int64), ("n_B", C.c_int64), ("n_solvent", C.c_int64),
+                ("step", C.c_uint32), ("pad", C.c_uint32)]
+
+
+class Timers(C.Structure):
+    _fields_ = [("launches", C.c_int64 * 4), ("ms", C.c_double * 4)]
+
+
+PHASES = ("prime", "md", "cellpass", "obs")
+
+EXPORTS = [
+    "rmpcd_create", "rmpcd_destroy", "rmpcd_set_state", "rmpcd_get_state", "rmpcd_set_colloids",
+    "rmpcd_get_colloids", "rmpcd_set_step", "rmpcd_get_step", "rmpcd_stream", "rmpcd_shift_and_sort",
+    "rmpcd_collide", "rmpcd_react", "rmpcd_step", "rmpcd_observables", "rmpcd_sync", "rmpcd_launch_count",
+    "rmpcd_last_error", "rmpcd_enable_timers", "rmpcd_read_timers",
+]
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load librmpcd.so (built by ``build.build()``); raise if it is missing."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first (paper_1608_04904_gb300.build.build())")
+    L = C.CDLL(path)
+    P = C.POINTER
+    vp, i32, i64, u32, d = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_double
+    L.rmpcd_create.argtypes = [P(vp), i32, i32, P(Params), P(Colloid), P(Bond), i32, vp]
+    L.rmpcd_destroy.argtypes = [vp]
+    L.rmpcd_destroy.restype = None
+    L.rmpcd_set_state.argtypes = [vp, i32, vp, vp, vp, i64, i32]
+    L.rmpcd_get_state.argtypes = [vp, i32, vp, vp, vp, vp, vp, i64, i32]
+    L.rmpcd_set_colloids.argtypes = [vp, i32, P(Colloid), i32]
+    L.rmpcd_get_colloids.argtypes = [vp, i32, P(Colloid), i32]
+    L.rmpcd_set_step.argtypes = [vp, u32]
+    L.rmpcd_get_step.argtypes = [vp, P(u32)]
+    for name in ("rmpcd_stream", "rmpcd_shift_and_sort", "rmpcd_collide", "rmpcd_react", "rmpcd_sync"):
+        getattr(L, name).argtypes = [vp]
+    L.rmpcd_step.argtypes = [vp, i32]
+    L.rmpcd_observables.argtypes = [vp, i32, P(Obs)]
+    L.rmpcd_launch_count.argtypes = [vp, P(i64)]
+    L.rmpcd_enable_timers.argtypes = [vp, i32]
+    L.rmpcd_read_timers.argtypes = [vp, P(Timers), i32]
+    L.rmpcd_last_error.argtypes = [vp]
+    L.rmpcd_last_error.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("rmpcd_destroy", "rmpcd_last_error"):
+            getattr(L, name).restype = C.c_int
+    _LIB = L
+    return L
+
+
+def make_params(cfg: dict, n_solvent: int, n_colloids: int = 0, n_bonds: int = 0) -> Params:
+    p = Params()
+    p.L[:] = [int(a) for a in cfg["L"]]
+    p.walls = int(cfg.get("walls", 0))
+    p.rho_wall = int(cfg.get("rho_wall", 0))
+    p.n_md = int(cfg.get("n_md", 1))
+    slabs = cfg.get("slabs", []) or []
+    p.n_slabs = len(slabs)
+    for k, (x0, x1, kt) in enumerate(slabs):
+        p.slab_x0[k], p.slab_x1[k], p.slab_kT[k] = x0, x1, kt
+    p.n_solvent = int(n_solvent)
+    p.n_colloids = int(n_colloids)
+    p.n_bonds = int(n_bonds)
+    p.kT = float(cfg["kT"])
+    p.alpha = float(cfg["alpha"])
+    p.tau = float(cfg["tau"])
+    p.g[:] = [float(a) for a in cfg.get("g", (0.0, 0.0, 0.0))]
+    p.bulk_rate = float(cfg.get("bulk_rate", 0.0))
+    p.cat_prob = float(cfg.get("cat_prob", 1.0))
+    p.skin = float(cfg.get("skin", 0.5))
+    cc = cfg.get("cc_lj")
+    if cc:
+        p.cc_eps, p.cc_sigma, p.cc_rc = cc
+    p.seed = int(cfg["seed"]) & 0xFFFFFFFFFFFFFFFF
+    return p
+
+
+def _colloid(c) -> Colloid:
+    o = Colloid()
+    o.x[:] = [float(a) for a in c["x"]]
+    o.v[:] = [float(a) for a in c.get("v", (0.0, 0.0, 0.0))]
+    o.mass, o.sigma = float(c["mass"]), float(c["sigma"])
+    o.eps_A, o.eps_B = float(c["eps_A"]), float(c["eps_B"])
+    o.catalytic = int(c.get("catalytic", 0))
+    return o
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _default_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return 0
+
+
+class System:
+    """A set of independent replicas on the current CUDA device.
+
+    ``replicas``: list of dicts with keys ``cfg`` (parameter dict), ``n``
+    (solvent count), ``colloids`` (list of dicts) and ``bonds`` (list of
+    ``(a, b, d)``).
+    """
+
+    def __init__(self, replicas, precision: str = "mixed", bucket_cap: int = 64, stream=None):
+        self._lib = load()
+        self.precision = precision
+        self.replicas = list(replicas)
+        n = len(self.replicas)
+        params = (Params * n)()
+        cols, bonds = [], []
+        self.n = []
+        self.n_col = []
+        for r, rep in enumerate(self.replicas):
+            cl = list(rep.get("colloids", []) or [])
+            bl = list(rep.get("bonds", []) or [])
+            params[r] = make_params(rep["cfg"], rep["n"], len(cl), len(bl))
+            cols += [_colloid(c) for c in cl]
+            for a, b, dd in bl:
+                bo = Bond()
+                bo.a, bo.b, bo.d = int(a), int(b), float(dd)
+                bonds.append(bo)
+            self.n.append(int(rep["n"]))
+            self.n_col.append(len(cl))
+        carr = (Colloid * max(1, len(cols)))(*cols)
+        barr = (Bond * max(1, len(bonds)))(*bonds)
+        if stream is None:
+            stream = _default_stream()
+        elif hasattr(stream, "cuda_stream"):
+            stream = int(stream.cuda_stream)
+        self.stream = int(stream)
+        handle = C.c_void_p()
+        prec = RMPCD_MIXED if precision == "mixed" else RMPCD_FP64
+        st = self._lib.rmpcd_create(C.byref(handle), prec, n, params, carr if cols else None,
+                                    barr if bonds else None, int(bucket_cap), C.c_void_p(self.stream))
+        if st != 0:
+            raise RmpcdError(st, self._lib.rmpcd_last_error(None).decode())
+        self._h = handle
+
+    @classmethod
+    def single(cls, cfg, n, colloids=(), bonds=(), precision=None, bucket_cap=None, stream=None):
+        precision = precision or cfg.get("precision", "mixed")
+        bucket_cap = bucket_cap or cfg.get("bucket_cap", 64)
+        return cls([dict(cfg=cfg, n=n, colloids=list(colloids), bonds=list(bonds))], precision, bucket_cap, stream)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.rmpcd_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, st):
+        if st != 0:
+            raise RmpcdError(st, self._lib.rmpcd_last_error(self._h).decode())
+
+    # -- state ---------------------------------------------------------------
+    def set_state(self, replica, x, v, flags=None):
+        n = self.n[replica]
+        if _is_torch(x) and x.is_cuda:
+            import torch
+            x = x.contiguous().to(torch.float64)
+            v = v.contiguous().to(torch.float64)
+            f = None if flags is None else flags.contiguous().to(torch.uint8)
+            self._keep = (x, v, f)
+            self._check(self._lib.rmpcd_set_state(self._h, replica, C.c_void_p(x.data_ptr()),
+                                                  C.c_void_p(v.data_ptr()),
+                                                  None if f is None else C.c_void_p(f.data_ptr()), n, 1))
+            return
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(n, 3)
+        v = np.ascontiguousarray(v, dtype=np.float64).reshape(n, 3)
+        f = None if flags is None else np.ascontiguousarray(flags, dtype=np.uint8).reshape(n)
+        self._check(self._lib.rmpcd_set_state(self._h, replica, x.ctypes.data_as(C.c_void_p),
+                                              v.ctypes.data_as(C.c_void_p),
+                                              None if f is None else f.ctypes.data_as(C.c_void_p), n, 0))
+
+    def get_state(self, replica=0, out=None):
+        """Return dict x, v, flags, id, cell (numpy arrays); with ``out`` (a dict
+        of preallocated arrays, host numpy or CUDA torch tensors) fill those."""
+        n = self.n[replica]
+        if out is not None and any(_is_torch(a) and a.is_cuda for a in out.values()):
+            ptr = lambda k: C.c_void_p(out[k].data_ptr()) if k in out else None
+            self._check(self._lib.rmpcd_get_state(self._h, replica, ptr("x"), ptr("v"), ptr("flags"), ptr("id"),
+                                                  ptr("cell"), n, 1))
+            return out
+        if out is None:
+            out = {"x": np.empty((n, 3)), "v": np.empty((n, 3)), "flags": np.empty(n, np.uint8),
+                   "id": np.empty(n, np.uint32), "cell": np.empty(n, np.int32)}
+        ptr = lambda k: out[k].ctypes.data_as(C.c_void_p) if k in out else None
+        self._check(self._lib.rmpcd_get_state(self._h, replica, ptr("x"), ptr("v"), ptr("flags"), ptr("id"),
+                                              ptr("cell"), n, 0))
+        return out
+
+    def set_colloids(self, replica, colloids):
+        arr = (Colloid * max(1, len(colloids)))(*[_colloid(c) for c in colloids])
+        self._check(self._lib.rmpcd_set_colloids(self._h, replica, arr, len(colloids)))
+
+    def get_colloids(self, replica=0):
+        k = self.n_col[replica]
+        arr = (Colloid * max(1, k))()
+        self._check(self._lib.rmpcd_get_colloids(self._h, replica, arr, k))
+        return {"x": np.array([list(arr[j].x) for j in range(k)]).reshape(k, 3),
+                "v": np.array([list(arr[j].v) for j in range(k)]).reshape(k, 3)}
+
+    def set_step(self, step):
+        self._check(self._lib.rmpcd_set_step(self._h, int(step)))
+
+    def get_step(self):
+        s = C.c_uint32()
+        self._check(self._lib.rmpcd_get_step(self._h, C.byref(s)))
+        return int(s.value)
+
+    # -- the steps -----------------------------------------------------------
+    def stream_interval(self):
+        self._check(self._lib.rmpcd_stream(self._h))
+
+    def shift_and_sort(self):
+        self._check(self._lib.rmpcd_shift_and_sort(self._h))
+
+    def collide(self):
+        self._check(self._lib.rmpcd_collide(self._h))
+
+    def react(self):
+        self._check(self._lib.rmpcd_react(self._h))
+
+    def step(self, n=1):
+        self._check(self._lib.rmpcd_step(self._h, int(n)))
+
+    def sync(self):
+        self._check(self._lib.rmpcd_sync(self._h))
+
+    def observables(self, replica=0) -> dict:
+        o = Obs()
+        self._check(self._lib.rmpcd_observables(self._h, replica, C.byref(o)))
+        return {"temperature": o.temperature, "momentum": np.array(list(o.momentum)), "kinetic": o.kinetic,
+                "n_cells_used": int(o.n_cells_used), "n_B": int(o.n_B), "n_solvent": int(o.n_solvent),
+                "step": int(o.step)}
+
+    def enable_timers(self, on=True):
+        self._check(self._lib.rmpcd_enable_timers(self._h, 1 if on else 0))
+
+    def read_timers(self, reset=True) -> dict:
+        t = Timers()
+        self._check(self._lib.rmpcd_read_timers(self._h, C.byref(t), 1 if reset else 0))
+        return {name: {"launches": int(t.launches[k]), "ms": float(t.ms[k])} for k, name in enumerate(PHASES)}
+
+    def launch_count(self) -> int:
+        c = C.c_int64()
+        self._check(self._lib.rmpcd_launch_count(self._h, C.byref(c)))
+        return int(c.value)

@@ -1,0 +1,815 @@
+// capi.cu -- host side of the C ABI declared in include/rmpcd.h.
+//
+// Owns the device buffers of a system, validates parameters, precomputes the
+// per-replica constants, and sequences the kernels of one collision interval
+// (§1.1, §1.4 of the RMPCDMD paper, arXiv:1608.04904):
+//   granular: stream -> shift_and_sort -> collide -> react
+//   fused   : [prime] { md ; cellpass(collide, react, next flight + bin) }*
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/rmpcd.h"
+#include "rmpcd_kernels.cuh"
+
+using namespace rmpcd;
+
+struct rmpcd_system {
+    bool mixed = false;
+    int n_rep = 0;
+    int cap = 64;
+    cudaStream_t stream = nullptr;
+    std::vector<rmpcd_params> params;
+    std::vector<ReplicaDev> rep;
+    std::vector<rmpcd_colloid> colloids;
+    int n_total = 0, n_tiles = 0, n_col = 0, n_bond = 0, max_part = 0;
+    int any_colloids = 0;
+    Dev d{};
+    // device allocations
+    std::vector<void *> allocs;
+    double *stage_x = nullptr, *stage_v = nullptr;
+    uint8_t *stage_f = nullptr;
+    uint32_t *stage_id = nullptr;
+    int32_t *stage_cell = nullptr;
+    // pipeline state
+    uint32_t step = 0;
+    int cur = 0;        // record buffer holding the state
+    int bcur = 0;       // count/bucket buffer of the next collision (fused)
+    bool primed = false;
+    bool has_sort = false;
+    uint32_t sort_step = 0;
+    bool obs_valid = false;
+    uint32_t epoch = 0;
+    long long launches = 0;
+    std::string err;
+    // per-phase timers
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Pending { int phase; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    long long t_launches[4] = {0, 0, 0, 0};
+    double t_ms[4] = {0, 0, 0, 0};
+};
+
+static cudaEvent_t pool_event(rmpcd_system *sys)
+{
+    if (!sys->ev_pool.empty()) {
+        cudaEvent_t e = sys->ev_pool.back();
+        sys->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Record the start event of a timed phase (no-op when timers are off).
+static void tstart(rmpcd_system *sys, cudaEvent_t *a)
+{
+    *a = nullptr;
+    if (!sys->timing) return;
+    *a = pool_event(sys);
+    cudaEventRecord(*a, sys->stream);
+}
+
+static void tstop(rmpcd_system *sys, int phase, cudaEvent_t a)
+{
+    if (!sys->timing || !a) return;
+    cudaEvent_t b = pool_event(sys);
+    cudaEventRecord(b, sys->stream);
+    sys->pending.push_back({phase, a, b});
+}
+
+static std::string g_create_error;
+
+// Mixed-path colloid representation: unwrapped integer cell, FP32 offset in
+// [0,1), wrapped integer cell, FP32 velocity.
+static void split_colloid(const rmpcd_colloid &c, const rmpcd_params &p, int Xi[3], float Xf[3], int Ci[3], float Vf[3])
+{
+    for (int k = 0; k < 3; ++k) {
+        double fl = floor(c.x[k]);
+        Xi[k] = (int)fl;
+        Xf[k] = (float)(c.x[k] - fl);
+        if (Xf[k] >= 1.0f) { Xf[k] = 0.0f; Xi[k] += 1; }
+        int m = Xi[k] % p.L[k];
+        Ci[k] = m < 0 ? m + p.L[k] : m;
+        Vf[k] = (float)c.v[k];
+    }
+}
+
+static rmpcd_status fail(rmpcd_system *s, rmpcd_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (s) s->err = buf; else g_create_error = buf;
+    return st;
+}
+
+static rmpcd_status cuda_check(rmpcd_system *s, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return RMPCD_OK;
+    return fail(s, e == cudaErrorMemoryAllocation ? RMPCD_ENOMEM : RMPCD_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define CK(expr)                                                       \
+    do {                                                               \
+        rmpcd_status _st = cuda_check(sys, (expr), #expr);             \
+        if (_st != RMPCD_OK) return _st;                               \
+    } while (0)
+
+static rmpcd_status after_launch(rmpcd_system *sys, int n)
+{
+    sys->launches += n;
+    return cuda_check(sys, cudaGetLastError(), "kernel launch");
+}
+
+template <typename T>
+static rmpcd_status dalloc(rmpcd_system *sys, T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) return cuda_check(sys, e, "cudaMalloc");
+    sys->allocs.push_back(q);
+    *p = static_cast<T *>(q);
+    return RMPCD_OK;
+}
+
+static void fill_rep(ReplicaDev &rp, const rmpcd_params &p)
+{
+    std::memset(&rp, 0, sizeof rp);
+    for (int k = 0; k < 3; ++k) rp.L[k] = p.L[k];
+    rp.walls = p.walls ? 1 : 0;
+    rp.nz = p.L[2] + rp.walls;
+    rp.rho_wall = p.rho_wall;
+    rp.n_md = p.n_md;
+    rp.n_slabs = p.n_slabs;
+    rp.n_part = p.n_solvent;
+    rp.n_cells = p.L[0] * p.L[1] * rp.nz;
+    rp.n_tiles = (rp.n_cells + CPT - 1) / CPT;
+    rp.n_col = p.n_colloids;
+    rp.n_bond = p.n_bonds;
+    rp.bulk_on = p.bulk_rate > 0.0 ? 1 : 0;
+    rp.has_g = (p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0) ? 1 : 0;
+    rp.kT = p.kT;
+    rp.tau = p.tau;
+    rp.dt = p.tau / (double)p.n_md;
+    rp.hdt = 0.5 * rp.dt;
+    rp.ca = cos(p.alpha);
+    rp.sa = sin(p.alpha);
+    rp.omc = 1.0 - rp.ca;
+    for (int k = 0; k < 3; ++k) rp.g[k] = p.g[k];
+    rp.gnorm = sqrt(p.g[0] * p.g[0] + p.g[1] * p.g[1] + p.g[2] * p.g[2]);
+    rp.cat_thr = p.cat_prob * 4294967296.0;
+    rp.skin = p.skin;
+    for (int k = 0; k < 4; ++k) {
+        rp.slab_x0[k] = p.slab_x0[k];
+        rp.slab_x1[k] = p.slab_x1[k];
+        rp.slab_sd[k] = sqrt(p.slab_kT[k] > 0.0 ? p.slab_kT[k] : 0.0);
+        rp.slab_sd_f[k] = (float)rp.slab_sd[k];
+    }
+    rp.cc_eps = p.cc_eps;
+    rp.cc_sigma = p.cc_sigma;
+    rp.cc_rc = p.cc_rc;
+    rp.tau_f = (float)rp.tau;
+    rp.dt_f = (float)rp.dt;
+    rp.hdt_f = (float)rp.hdt;
+    rp.ca_f = (float)rp.ca;
+    rp.sa_f = (float)rp.sa;
+    rp.omc_f = (float)rp.omc;
+    for (int k = 0; k < 3; ++k) rp.g_f[k] = (float)p.g[k];
+    rp.gnorm_f = (float)rp.gnorm;
+    rp.skin_f = (float)rp.skin;
+    rp.seed = (unsigned long long)p.seed;
+}
+
+static rmpcd_status validate(const rmpcd_params &p, int r, const rmpcd_colloid *cols, const rmpcd_bond *bonds)
+{
+    for (int k = 0; k < 3; ++k)
+        if (p.L[k] < 2 || p.L[k] > 1023) return fail(nullptr, RMPCD_EINVAL, "replica %d: L[%d]=%d not in [2,1023]", r, k, p.L[k]);
+    if (p.n_md < 1) return fail(nullptr, RMPCD_EINVAL, "replica %d: n_md must be >= 1", r);
+    if (!(p.tau > 0.0) || !std::isfinite(p.tau)) return fail(nullptr, RMPCD_EINVAL, "replica %d: tau must be > 0", r);
+    if (!(p.kT >= 0.0)) return fail(nullptr, RMPCD_EINVAL, "replica %d: kT must be >= 0", r);
+    if (!std::isfinite(p.alpha)) return fail(nullptr, RMPCD_EINVAL, "replica %d: alpha not finite", r);
+    if (p.n_solvent < 0 || p.n_solvent > (int)ID_MASK) return fail(nullptr, RMPCD_EINVAL, "replica %d: n_solvent out of range", r);
+    if (p.n_colloids < 0 || p.n_colloids > MAXC)
+        return fail(nullptr, RMPCD_EINVAL, "replica %d: n_colloids %d not in [0,%d]", r, p.n_colloids, MAXC);
+    if (p.n_bonds < 0 || p.n_bonds > MAXB) return fail(nullptr, RMPCD_EINVAL, "replica %d: n_bonds not in [0,%d]", r, MAXB);
+    if (p.n_slabs < 0 || p.n_slabs > 4) return fail(nullptr, RMPCD_EINVAL, "replica %d: n_slabs not in [0,4]", r);
+    if (p.walls && p.g[2] != 0.0) return fail(nullptr, RMPCD_EINVAL, "replica %d: walls need g[2] = 0", r);
+    if (p.walls && p.n_colloids > 0) return fail(nullptr, RMPCD_EINVAL, "replica %d: colloids with walls are not supported", r);
+    if (p.walls && p.rho_wall < 0) return fail(nullptr, RMPCD_EINVAL, "replica %d: rho_wall < 0", r);
+    if (!(p.cat_prob >= 0.0 && p.cat_prob <= 1.0)) return fail(nullptr, RMPCD_EINVAL, "replica %d: cat_prob not in [0,1]", r);
+    if (!(p.skin >= 0.0)) return fail(nullptr, RMPCD_EINVAL, "replica %d: skin < 0", r);
+    if (!(p.bulk_rate >= 0.0)) return fail(nullptr, RMPCD_EINVAL, "replica %d: bulk_rate < 0", r);
+    for (int j = 0; j < p.n_colloids; ++j) {
+        const rmpcd_colloid &c = cols[j];
+        if (!(c.mass > 0.0) || !(c.sigma > 0.0)) return fail(nullptr, RMPCD_EINVAL, "replica %d colloid %d: mass and sigma must be > 0", r, j);
+        if (2.0 * c.sigma * 1.1224620483093730 + 2.0 * p.skin >= (double)std::min(p.L[0], std::min(p.L[1], p.L[2])))
+            return fail(nullptr, RMPCD_EINVAL, "replica %d colloid %d: box too small for the cut-off", r, j);
+    }
+    for (int k = 0; k < p.n_bonds; ++k) {
+        const rmpcd_bond &b = bonds[k];
+        if (b.a < 0 || b.b < 0 || b.a >= p.n_colloids || b.b >= p.n_colloids || b.a == b.b || !(b.d > 0.0))
+            return fail(nullptr, RMPCD_EINVAL, "replica %d bond %d invalid", r, k);
+    }
+    return RMPCD_OK;
+}
+
+extern "C" {
+
+const char *rmpcd_last_error(const rmpcd_system *sys)
+{
+    if (!sys) return g_create_error.c_str();
+    return sys->err.c_str();
+}
+
+void rmpcd_destroy(rmpcd_system *sys)
+{
+    if (!sys) return;
+    cudaStreamSynchronize(sys->stream);
+    for (void *p : sys->allocs) cudaFree(p);
+    for (auto &q : sys->pending) { sys->ev_pool.push_back(q.a); sys->ev_pool.push_back(q.b); }
+    for (cudaEvent_t e : sys->ev_pool) cudaEventDestroy(e);
+    delete sys;
+}
+
+rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_replicas, const rmpcd_params *params,
+                          const rmpcd_colloid *colloids, const rmpcd_bond *bonds, int32_t bucket_cap, void *stream)
+{
+    if (!out) return fail(nullptr, RMPCD_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (precision != RMPCD_FP64 && precision != RMPCD_MIXED) return fail(nullptr, RMPCD_EINVAL, "unknown precision %d", precision);
+    if (n_replicas < 1 || !params) return fail(nullptr, RMPCD_EINVAL, "need n_replicas >= 1 and params");
+    const int max_cap = std::min(TP_M, TP_D);
+    if (bucket_cap < 1 || bucket_cap > max_cap) return fail(nullptr, RMPCD_EINVAL, "bucket_cap %d not in [1,%d]", bucket_cap, max_cap);
+    long long n_total = 0, n_tiles = 0, n_col = 0, n_bond = 0;
+    for (int r = 0; r < n_replicas; ++r) {
+        if ((params[r].n_colloids > 0 && !colloids) || (params[r].n_bonds > 0 && !bonds))
+            return fail(nullptr, RMPCD_EINVAL, "replica %d: colloid or bond array missing", r);
+        rmpcd_status st = validate(params[r], r, colloids ? colloids + n_col : nullptr, bonds ? bonds + n_bond : nullptr);
+        if (st != RMPCD_OK) return st;
+        n_total += params[r].n_solvent;
+        const long long nz = params[r].L[2] + (params[r].walls ? 1 : 0);
+        n_tiles += ((long long)params[r].L[0] * params[r].L[1] * nz + CPT - 1) / CPT;
+        n_col += params[r].n_colloids;
+        n_bond += params[r].n_bonds;
+    }
+    if (n_total > 0x7FFFFFF0ll) return fail(nullptr, RMPCD_EINVAL, "too many solvent particles");
+    if (n_tiles * CPT * (long long)bucket_cap > 0x7FFFFFFFll) return fail(nullptr, RMPCD_EINVAL, "cells x bucket_cap too large");
+
+    rmpcd_system *sys = new rmpcd_system();
+    sys->mixed = precision == RMPCD_MIXED;
+    sys->n_rep = n_replicas;
+    sys->cap = bucket_cap;
+    sys->stream = static_cast<cudaStream_t>(stream);
+    sys->params.assign(params, params + n_replicas);
+    sys->n_total = (int)n_total;
+    sys->n_tiles = (int)n_tiles;
+    sys->n_col = (int)n_col;
+    sys->n_bond = (int)n_bond;
+    if (n_col > 0) sys->colloids.assign(colloids, colloids + n_col);
+
+    // per-replica constants and layout
+    sys->rep.resize(n_replicas);
+    std::vector<int> tile_rep((size_t)n_tiles);
+    int part_off = 0, tile_off = 0, col_off = 0, bond_off = 0;
+    for (int r = 0; r < n_replicas; ++r) {
+        ReplicaDev &rp = sys->rep[r];
+        fill_rep(rp, params[r]);
+        rp.part_off = part_off;
+        rp.tile_off = tile_off;
+        rp.cell_off = tile_off * CPT;
+        rp.col_off = col_off;
+        rp.bond_off = bond_off;
+        rp.thr_off = r * (bucket_cap + 1);
+        for (int t = 0; t < rp.n_tiles; ++t) tile_rep[tile_off + t] = r;
+        part_off += rp.n_part;
+        tile_off += rp.n_tiles;
+        col_off += rp.n_col;
+        bond_off += rp.n_bond;
+        sys->max_part = std::max(sys->max_part, rp.n_part);
+        if (rp.n_col > 0) sys->any_colloids = 1;
+    }
+    // bulk reaction thresholds: accept iff draw < (1 - exp(-k N_B tau)) 2^32
+    std::vector<double> thr((size_t)n_replicas * (bucket_cap + 1));
+    for (int r = 0; r < n_replicas; ++r)
+        for (int nb = 0; nb <= bucket_cap; ++nb)
+            thr[(size_t)r * (bucket_cap + 1) + nb] =
+                (1.0 - exp(-params[r].bulk_rate * (double)nb * params[r].tau)) * 4294967296.0;
+    // colloid constants
+    std::vector<double> cM(n_col), cS(n_col), cEA(n_col), cEB(n_col), cR2(n_col), cR(n_col), cX(3 * n_col), cV(3 * n_col);
+    std::vector<float> fS(n_col), fEA(n_col), fEB(n_col), fR2(n_col), fR(n_col);
+    std::vector<int> cCat(n_col), cXi(3 * n_col), cCi(3 * n_col);
+    std::vector<float> cXf(3 * n_col), cVf(3 * n_col), cRb(n_col), cIM(n_col);
+    std::vector<int> col_rep(n_col);
+    for (int r = 0, j = 0; r < n_replicas; ++r)
+        for (int k = 0; k < params[r].n_colloids; ++k) col_rep[j++] = r;
+    for (long long j = 0; j < n_col; ++j) {
+        const rmpcd_colloid &c = colloids[j];
+        const rmpcd_params &pr = params[col_rep[j]];
+        split_colloid(c, pr, &cXi[3 * j], &cXf[3 * j], &cCi[3 * j], &cVf[3 * j]);
+        const double gn = sqrt(pr.g[0] * pr.g[0] + pr.g[1] * pr.g[1] + pr.g[2] * pr.g[2]);
+        cRb[j] = (float)(sqrt(c.sigma * c.sigma * cbrt(2.0)) + 0.5 * gn * pr.tau * pr.tau + pr.skin);
+        cIM[j] = (float)(1.0 / c.mass);
+        cM[j] = c.mass; cS[j] = c.sigma; cEA[j] = c.eps_A; cEB[j] = c.eps_B;
+        cR2[j] = c.sigma * c.sigma * cbrt(2.0);
+        cR[j] = sqrt(cR2[j]);
+        fS[j] = (float)c.sigma; fEA[j] = (float)c.eps_A; fEB[j] = (float)c.eps_B;
+        fR2[j] = (float)cR2[j]; fR[j] = (float)cR[j];
+        cCat[j] = c.catalytic ? 1 : 0;
+        for (int k = 0; k < 3; ++k) { cX[3 * j + k] = c.x[k]; cV[3 * j + k] = c.v[k]; }
+    }
+    std::vector<BondDev> bd(n_bond);
+    for (long long k = 0; k < n_bond; ++k) bd[k] = BondDev{bonds[k].a, bonds[k].b, bonds[k].d};
+
+    rmpcd_status st = RMPCD_OK;
+    Dev &d = sys->d;
+    const size_t recsz = sys->mixed ? sizeof(RecM) : sizeof(RecD);
+    const long long ncells = (long long)n_tiles * CPT;
+    ReplicaDev *drep = nullptr;
+    int *dtile = nullptr;
+    double *dthr = nullptr;
+    double *dM, *dS, *dEA, *dEB, *dR2, *dR;
+    float *dfS, *dfEA, *dfEB, *dfR2, *dfR;
+    int *dCat;
+    float *dRb, *dIM;
+    BondDev *dB;
+    unsigned char *r0, *r1, *work;
+#define AL(p, n) if (st == RMPCD_OK) st = dalloc(sys, p, (size_t)(n))
+    AL(&drep, n_replicas);
+    AL(&dtile, n_tiles);
+    AL(&r0, recsz * n_total);
+    AL(&r1, recsz * n_total);
+    AL(&d.count[0], ncells);
+    AL(&d.count[1], ncells);
+    AL(&d.bucket[0], ncells * bucket_cap);
+    AL(&d.bucket[1], ncells * bucket_cap);
+    AL(&d.near_list, n_total);
+    AL(&d.near_count, n_replicas);
+    AL(&d.tile_state, n_tiles);
+    AL(&d.ticket, 2);
+    AL(&d.err, ERR_COUNT);
+    AL(&d.obs_part, (size_t)n_tiles * 8);
+    AL(&d.obs_out, (size_t)n_replicas * 8);
+    AL(&dthr, thr.size());
+    AL(&d.colX, 3 * n_col);
+    AL(&d.colV, 3 * n_col);
+    AL(&dM, n_col); AL(&dS, n_col); AL(&dEA, n_col); AL(&dEB, n_col); AL(&dR2, n_col); AL(&dR, n_col);
+    AL(&dfS, n_col); AL(&dfEA, n_col); AL(&dfEB, n_col); AL(&dfR2, n_col); AL(&dfR, n_col);
+    AL(&dCat, n_col);
+    AL(&d.colXi, 3 * n_col);
+    AL(&d.colCi, 3 * n_col);
+    AL(&d.colXf, 3 * n_col);
+    AL(&d.colVf, 3 * n_col);
+    AL(&dRb, n_col);
+    AL(&dIM, n_col);
+    AL(&dB, n_bond);
+    AL(&work, (sys->mixed ? 64 : 80) * (size_t)(sys->any_colloids ? n_total : 1));
+    AL(&sys->stage_x, 3 * (size_t)sys->max_part);
+    AL(&sys->stage_v, 3 * (size_t)sys->max_part);
+    AL(&sys->stage_f, (size_t)sys->max_part);
+    AL(&sys->stage_id, (size_t)sys->max_part);
+    AL(&sys->stage_cell, (size_t)sys->max_part);
+#undef AL
+    if (st != RMPCD_OK) {
+        g_create_error = sys->err;
+        rmpcd_destroy(sys);
+        return st;
+    }
+    cudaStream_t s = sys->stream;
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        if (st == RMPCD_OK && bytes) st = cuda_check(sys, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s), "upload");
+    };
+    auto zero = [&](void *dst, size_t bytes) {
+        if (st == RMPCD_OK && bytes) st = cuda_check(sys, cudaMemsetAsync(dst, 0, bytes, s), "memset");
+    };
+    up(drep, sys->rep.data(), sizeof(ReplicaDev) * n_replicas);
+    up(dtile, tile_rep.data(), sizeof(int) * n_tiles);
+    up(dthr, thr.data(), sizeof(double) * thr.size());
+    up(d.colX, cX.data(), sizeof(double) * cX.size());
+    up(d.colV, cV.data(), sizeof(double) * cV.size());
+    up(dM, cM.data(), sizeof(double) * n_col); up(dS, cS.data(), sizeof(double) * n_col);
+    up(dEA, cEA.data(), sizeof(double) * n_col); up(dEB, cEB.data(), sizeof(double) * n_col);
+    up(dR2, cR2.data(), sizeof(double) * n_col); up(dR, cR.data(), sizeof(double) * n_col);
+    up(dfS, fS.data(), sizeof(float) * n_col); up(dfEA, fEA.data(), sizeof(float) * n_col);
+    up(dfEB, fEB.data(), sizeof(float) * n_col); up(dfR2, fR2.data(), sizeof(float) * n_col);
+    up(dfR, fR.data(), sizeof(float) * n_col);
+    up(dCat, cCat.data(), sizeof(int) * n_col);
+    up(d.colXi, cXi.data(), sizeof(int) * 3 * n_col);
+    up(d.colCi, cCi.data(), sizeof(int) * 3 * n_col);
+    up(d.colXf, cXf.data(), sizeof(float) * 3 * n_col);
+    up(d.colVf, cVf.data(), sizeof(float) * 3 * n_col);
+    up(dRb, cRb.data(), sizeof(float) * n_col);
+    up(dIM, cIM.data(), sizeof(float) * n_col);
+    up(dB, bd.data(), sizeof(BondDev) * n_bond);
+    zero(r0, recsz * n_total);
+    zero(r1, recsz * n_total);
+    zero(d.count[0], sizeof(int) * ncells);
+    zero(d.count[1], sizeof(int) * ncells);
+    zero(d.near_count, sizeof(int) * n_replicas);
+    zero(d.tile_state, sizeof(unsigned long long) * n_tiles);
+    zero(d.ticket, sizeof(unsigned int) * 2);
+    zero(d.err, sizeof(unsigned int) * ERR_COUNT);
+    zero(d.obs_out, sizeof(double) * 8 * n_replicas);
+    if (st == RMPCD_OK) st = cuda_check(sys, cudaStreamSynchronize(s), "create sync");
+    if (st != RMPCD_OK) {
+        g_create_error = sys->err;
+        rmpcd_destroy(sys);
+        return st;
+    }
+    d.rep = drep;
+    d.tile_rep = dtile;
+    d.rec[0] = r0;
+    d.rec[1] = r1;
+    d.bulk_thr = dthr;
+    d.colM = dM; d.colSig = dS; d.colEpsA = dEA; d.colEpsB = dEB; d.colRc2 = dR2; d.colRc = dR;
+    d.colSig_f = dfS; d.colEpsA_f = dfEA; d.colEpsB_f = dfEB; d.colRc2_f = dfR2; d.colRc_f = dfR;
+    d.colCat = dCat;
+    d.colRb_f = dRb;
+    d.colInvM_f = dIM;
+    d.bonds = dB;
+    d.md_work = work;
+    d.cap = bucket_cap;
+    d.n_rep = n_replicas;
+    d.n_tiles = (int)n_tiles;
+    d.n_total = (int)n_total;
+    *out = sys;
+    return RMPCD_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------------------
+// pipeline helpers
+// ----------------------------------------------------------------------------
+// Launch counter of the cell pass: its parity selects the ticket counter,
+// consecutive launches alternate; the kernel derives its look-back tag from it.
+static uint32_t next_epoch(rmpcd_system *sys)
+{
+    sys->epoch += 1u;
+    return sys->epoch;
+}
+
+// Drop a primed fused pipeline (pending bins and near lists).
+static rmpcd_status unprime(rmpcd_system *sys)
+{
+    if (!sys->primed) return RMPCD_OK;
+    const size_t ncells = (size_t)sys->n_tiles * CPT;
+    CK(cudaMemsetAsync(sys->d.count[0], 0, sizeof(int) * ncells, sys->stream));
+    CK(cudaMemsetAsync(sys->d.count[1], 0, sizeof(int) * ncells, sys->stream));
+    CK(cudaMemsetAsync(sys->d.near_count, 0, sizeof(int) * sys->n_rep, sys->stream));
+    sys->primed = false;
+    return RMPCD_OK;
+}
+
+// Bin the stored state on the grid of collision `grid_step` into count/bucket
+// buffer `b` and run one cell pass with `opts` over it.
+static rmpcd_status rebin_pass(rmpcd_system *sys, uint32_t grid_step, int opts, int b)
+{
+    launch_particles(sys->mixed, sys->d, PM_BIN, grid_step, sys->cur, b, sys->stream);
+    rmpcd_status st = after_launch(sys, 1);
+    if (st != RMPCD_OK) return st;
+    CellPassArgs a{opts, grid_step, b, b ^ 1, sys->cur, sys->cur ^ 1, next_epoch(sys)};
+    launch_cellpass(sys->mixed, sys->d, a, sys->stream);
+    st = after_launch(sys, 1);
+    if (st != RMPCD_OK) return st;
+    if (opts & CP_WRITE) sys->cur ^= 1;
+    return RMPCD_OK;
+}
+
+static rmpcd_status check_errors(rmpcd_system *sys)
+{
+    unsigned int e[ERR_COUNT];
+    CK(cudaMemcpyAsync(e, sys->d.err, sizeof e, cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaStreamSynchronize(sys->stream));
+    bool any = false;
+    for (int k = 0; k < ERR_COUNT; ++k) any |= e[k] != 0;
+    if (!any) return RMPCD_OK;
+    CK(cudaMemsetAsync(sys->d.err, 0, sizeof e, sys->stream));
+    CK(cudaStreamSynchronize(sys->stream));
+    if (e[ERR_TIMEOUT]) return fail(sys, RMPCD_ETIMEOUT, "a cell-pass look-back wait timed out; the state is invalid");
+    if (e[ERR_BOUNDS]) return fail(sys, RMPCD_ESTATE, "inconsistent bins (slot out of range); the state is invalid");
+    if (e[ERR_OVERFLOW])
+        return fail(sys, RMPCD_EOVERFLOW, "a cell held %u particles, above bucket_cap %d; raise bucket_cap", e[ERR_OVERFLOW],
+                    sys->cap);
+    if (e[ERR_SKIN]) return fail(sys, RMPCD_ESKIN, "a colloid moved further than skin in one interval (%u times)", e[ERR_SKIN]);
+    return fail(sys, RMPCD_ESTATE, "device error");
+}
+
+extern "C" {
+
+rmpcd_status rmpcd_set_state(rmpcd_system *sys, int32_t replica, const double *x, const double *v,
+                             const uint8_t *flags, int64_t n, int32_t on_device)
+{
+    if (!sys) return RMPCD_EINVAL;
+    if (replica < 0 || replica >= sys->n_rep) return fail(sys, RMPCD_EINVAL, "replica %d out of range", replica);
+    const ReplicaDev &rp = sys->rep[replica];
+    if (n != rp.n_part) return fail(sys, RMPCD_EINVAL, "n = %lld but replica %d has %d particles", (long long)n, replica, rp.n_part);
+    if (n > 0 && (!x || !v)) return fail(sys, RMPCD_EINVAL, "x and v are required");
+    rmpcd_status st = unprime(sys);
+    if (st != RMPCD_OK) return st;
+    const double *dx = x, *dv = v;
+    const uint8_t *df = flags;
+    if (!on_device && n > 0) {
+        CK(cudaMemcpyAsync(sys->stage_x, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, sys->stream));
+        CK(cudaMemcpyAsync(sys->stage_v, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, sys->stream));
+        if (flags) CK(cudaMemcpyAsync(sys->stage_f, flags, n, cudaMemcpyHostToDevice, sys->stream));
+        dx = sys->stage_x;
+        dv = sys->stage_v;
+        df = flags ? sys->stage_f : nullptr;
+    }
+    // the other replicas' records live in the current buffer too
+    launch_set_state(sys->mixed, sys->d, replica, (int)n, dx, dv, df, sys->cur, sys->stream);
+    st = after_launch(sys, n > 0 ? 1 : 0);
+    if (st != RMPCD_OK) return st;
+    if (!on_device) CK(cudaStreamSynchronize(sys->stream));   // host buffers may go away
+    sys->has_sort = false;
+    sys->obs_valid = false;
+    return RMPCD_OK;
+}
+
+rmpcd_status rmpcd_get_state(rmpcd_system *sys, int32_t replica, double *x, double *v, uint8_t *flags,
+                             uint32_t *id, int32_t *cell, int64_t n, int32_t on_device)
+{
+    if (!sys) return RMPCD_EINVAL;
+    if (replica < 0 || replica >= sys->n_rep) return fail(sys, RMPCD_EINVAL, "replica %d out of range", replica);
+    const ReplicaDev &rp = sys->rep[replica];
+    if (n != rp.n_part) return fail(sys, RMPCD_EINVAL, "n = %lld but replica %d has %d particles", (long long)n, replica, rp.n_part);
+    if (n > 0) {
+        double *ox = x, *ov = v;
+        uint8_t *of = flags;
+        uint32_t *oi = id;
+        int32_t *oc = cell;
+        if (!on_device) {
+            ox = x ? sys->stage_x : nullptr;
+            ov = v ? sys->stage_v : nullptr;
+            of = flags ? sys->stage_f : nullptr;
+            oi = id ? sys->stage_id : nullptr;
+            oc = cell ? sys->stage_cell : nullptr;
+        }
+        launch_get_state(sys->mixed, sys->d, replica, (int)n, sys->cur, ox, ov, of, oi, oc, sys->has_sort ? 1 : 0,
+                         sys->sort_step, sys->stream);
+        rmpcd_status st = after_launch(sys, 1);
+        if (st != RMPCD_OK) return st;
+        if (!on_device) {
+            if (x) CK(cudaMemcpyAsync(x, sys->stage_x, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, sys->stream));
+            if (v) CK(cudaMemcpyAsync(v, sys->stage_v, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, sys->stream));
+            if (flags) CK(cudaMemcpyAsync(flags, sys->stage_f, n, cudaMemcpyDeviceToHost, sys->stream));
+            if (id) CK(cudaMemcpyAsync(id, sys->stage_id, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, sys->stream));
+            if (cell) CK(cudaMemcpyAsync(cell, sys->stage_cell, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, sys->stream));
+        }
+    }
+    return check_errors(sys);
+}
+
+rmpcd_status rmpcd_set_colloids(rmpcd_system *sys, int32_t replica, const rmpcd_colloid *c, int32_t n)
+{
+    if (!sys) return RMPCD_EINVAL;
+    if (replica < 0 || replica >= sys->n_rep) return fail(sys, RMPCD_EINVAL, "replica %d out of range", replica);
+    const ReplicaDev &rp = sys->rep[replica];
+    if (n != rp.n_col || (n > 0 && !c)) return fail(sys, RMPCD_EINVAL, "replica %d has %d colloids", replica, rp.n_col);
+    rmpcd_status st = unprime(sys);
+    if (st != RMPCD_OK) return st;
+    std::vector<double> X(3 * n), V(3 * n);
+    std::vector<int> Xi(3 * n), Ci(3 * n);
+    std::vector<float> Xf(3 * n), Vf(3 * n);
+    for (int j = 0; j < n; ++j) {
+        for (int k = 0; k < 3; ++k) { X[3 * j + k] = c[j].x[k]; V[3 * j + k] = c[j].v[k]; }
+        split_colloid(c[j], sys->params[replica], &Xi[3 * j], &Xf[3 * j], &Ci[3 * j], &Vf[3 * j]);
+    }
+    if (n > 0) {
+        const size_t o = 3 * (size_t)rp.col_off;
+        cudaStream_t s = sys->stream;
+        CK(cudaMemcpyAsync(sys->d.colX + o, X.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(sys->d.colV + o, V.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(sys->d.colXi + o, Xi.data(), sizeof(int) * 3 * n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(sys->d.colCi + o, Ci.data(), sizeof(int) * 3 * n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(sys->d.colXf + o, Xf.data(), sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(sys->d.colVf + o, Vf.data(), sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return RMPCD_OK;
+}
+
+rmpcd_status rmpcd_get_colloids(rmpcd_system *sys, int32_t replica, rmpcd_colloid *c, int32_t n)
+{
+    if (!sys) return RMPCD_EINVAL;
+    if (replica < 0 || replica >= sys->n_rep) return fail(sys, RMPCD_EINVAL, "replica %d out of range", replica);
+    const ReplicaDev &rp = sys->rep[replica];
+    if (n != rp.n_col || (n > 0 && !c)) return fail(sys, RMPCD_EINVAL, "replica %d has %d colloids", replica, rp.n_col);
+    std::vector<double> X(3 * n + 1), V(3 * n + 1);
+    std::vector<int> Xi(3 * n + 1);
+    std::vector<float> Xf(3 * n + 1), Vf(3 * n + 1);
+    if (n > 0) {
+        const size_t o = 3 * (size_t)rp.col_off;
+        cudaStream_t s = sys->stream;
+        if (sys->mixed) {
+            CK(cudaMemcpyAsync(Xi.data(), sys->d.colXi + o, sizeof(int) * 3 * n, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(Xf.data(), sys->d.colXf + o, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(Vf.data(), sys->d.colVf + o, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, s));
+        } else {
+            CK(cudaMemcpyAsync(X.data(), sys->d.colX + o, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(V.data(), sys->d.colV + o, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+        }
+    }
+    rmpcd_status st = check_errors(sys);
+    for (int j = 0; j < n; ++j) {
+        c[j] = sys->colloids[rp.col_off + j];
+        for (int k = 0; k < 3; ++k) {
+            if (sys->mixed) {
+                c[j].x[k] = (double)Xi[3 * j + k] + (double)Xf[3 * j + k];
+                c[j].v[k] = (double)Vf[3 * j + k];
+            } else {
+                c[j].x[k] = X[3 * j + k];
+                c[j].v[k] = V[3 * j + k];
+            }
+        }
+    }
+    return st;
+}
+
+rmpcd_status rmpcd_set_step(rmpcd_system *sys, uint32_t step)
+{
+    if (!sys) return RMPCD_EINVAL;
+    rmpcd_status st = unprime(sys);
+    if (st != RMPCD_OK) return st;
+    sys->step = step;
+    return RMPCD_OK;
+}
+
+rmpcd_status rmpcd_get_step(const rmpcd_system *sys, uint32_t *step)
+{
+    if (!sys || !step) return RMPCD_EINVAL;
+    *step = sys->step;
+    return RMPCD_OK;
+}
+
+rmpcd_status rmpcd_stream(rmpcd_system *sys)
+{
+    if (!sys) return RMPCD_EINVAL;
+    rmpcd_status st = unprime(sys);
+    if (st != RMPCD_OK) return st;
+    launch_particles(sys->mixed, sys->d, PM_STREAM, sys->step, sys->cur, 0, sys->stream);
+    if ((st = after_launch(sys, sys->n_total > 0 ? 1 : 0)) != RMPCD_OK) return st;
+    if (sys->any_colloids) {
+        launch_md(sys->mixed, sys->d, sys->step, sys->cur, 0, 0, sys->stream);
+        if ((st = after_launch(sys, 1)) != RMPCD_OK) return st;
+    }
+    sys->has_sort = false;
+    sys->obs_valid = false;
+    return RMPCD_OK;
+}
+
+rmpcd_status rmpcd_shift_and_sort(rmpcd_system *sys)
+{
+    if (!sys) return RMPCD_EINVAL;
+    rmpcd_status st = unprime(sys);
+    if (st != RMPCD_OK) return st;
+    if ((st = rebin_pass(sys, sys->step, CP_WRITE, 0)) != RMPCD_OK) return st;
+    sys->has_sort = true;
+    sys->sort_step = sys->step;
+    sys->obs_valid = false;
+    return RMPCD_OK;
+}
+
+static rmpcd_status sorted_op(rmpcd_system *sys, int opts, const char *name)
+{
+    if (!sys) return RMPCD_EINVAL;
+    if (!sys->has_sort || sys->sort_step != sys->step)
+        return fail(sys, RMPCD_ESTATE, "%s needs the state sorted on the grid of the current step (call rmpcd_shift_and_sort)", name);
+    rmpcd_status st = unprime(sys);
+    if (st != RMPCD_OK) return st;
+    if ((st = rebin_pass(sys, sys->step, CP_WRITE | opts, 0)) != RMPCD_OK) return st;
+    sys->obs_valid = false;
+    return RMPCD_OK;
+}
+
+rmpcd_status rmpcd_collide(rmpcd_system *sys) { return sorted_op(sys, CP_COLLIDE, "rmpcd_collide"); }
+rmpcd_status rmpcd_react(rmpcd_system *sys) { return sorted_op(sys, CP_REACT, "rmpcd_react"); }
+
+rmpcd_status rmpcd_step(rmpcd_system *sys, int32_t n_intervals)
+{
+    if (!sys) return RMPCD_EINVAL;
+    if (n_intervals < 0) return fail(sys, RMPCD_EINVAL, "n_intervals < 0");
+    if (n_intervals == 0) return RMPCD_OK;
+    rmpcd_status st;
+    cudaEvent_t ev;
+    if (!sys->primed) {
+        // bins for the collision of `step`: far particles at their flown
+        // position, near particles through the MD kernel
+        tstart(sys, &ev);
+        launch_particles(sys->mixed, sys->d, PM_PRIME, sys->step, sys->cur, sys->bcur, sys->stream);
+        tstop(sys, 0, ev);
+        if ((st = after_launch(sys, sys->n_total > 0 ? 1 : 0)) != RMPCD_OK) return st;
+        sys->primed = true;
+    }
+    for (int i = 0; i < n_intervals; ++i) {
+        if (sys->any_colloids) {
+            tstart(sys, &ev);
+            launch_md(sys->mixed, sys->d, sys->step, sys->cur, sys->bcur, 1, sys->stream);
+            tstop(sys, 1, ev);
+            if ((st = after_launch(sys, 1)) != RMPCD_OK) return st;
+        }
+        const bool last = i == n_intervals - 1;
+        CellPassArgs a{CP_FLIGHT | CP_COLLIDE | CP_REACT | CP_NEXT | CP_WRITE | (last ? CP_OBS : 0), sys->step, sys->bcur,
+                       sys->bcur ^ 1, sys->cur, sys->cur ^ 1, next_epoch(sys)};
+        tstart(sys, &ev);
+        launch_cellpass(sys->mixed, sys->d, a, sys->stream);
+        tstop(sys, 2, ev);
+        if ((st = after_launch(sys, 1)) != RMPCD_OK) return st;
+        sys->cur ^= 1;
+        sys->bcur ^= 1;
+        sys->sort_step = sys->step;
+        sys->step += 1u;
+    }
+    tstart(sys, &ev);
+    launch_obs_reduce(sys->d, sys->stream);
+    tstop(sys, 3, ev);
+    if ((st = after_launch(sys, 1)) != RMPCD_OK) return st;
+    sys->has_sort = true;
+    sys->obs_valid = true;
+    return RMPCD_OK;
+}
+
+rmpcd_status rmpcd_observables(rmpcd_system *sys, int32_t replica, rmpcd_obs *out)
+{
+    if (!sys || !out) return RMPCD_EINVAL;
+    if (replica < 0 || replica >= sys->n_rep) return fail(sys, RMPCD_EINVAL, "replica %d out of range", replica);
+    rmpcd_status st;
+    if (!sys->obs_valid) {
+        if (!sys->has_sort) return fail(sys, RMPCD_ESTATE, "no collision grid yet: sort or step first");
+        // rebin on the grid of the last sort into the free count buffer
+        const int b = sys->primed ? (sys->bcur ^ 1) : sys->bcur;
+        if ((st = rebin_pass(sys, sys->sort_step, CP_OBS, b)) != RMPCD_OK) return st;
+        launch_obs_reduce(sys->d, sys->stream);
+        if ((st = after_launch(sys, 1)) != RMPCD_OK) return st;
+        sys->obs_valid = true;
+    }
+    double o[8];
+    CK(cudaMemcpyAsync(o, sys->d.obs_out + 8 * replica, sizeof o, cudaMemcpyDeviceToHost, sys->stream));
+    st = check_errors(sys);
+    std::memset(out, 0, sizeof *out);
+    out->n_cells_used = (int64_t)o[1];
+    out->temperature = o[1] > 0 ? o[0] / (3.0 * o[1]) : 0.0;
+    out->momentum[0] = o[2];
+    out->momentum[1] = o[3];
+    out->momentum[2] = o[4];
+    out->kinetic = o[5];
+    out->n_B = (int64_t)o[6];
+    out->n_solvent = (int64_t)o[7];
+    out->step = sys->sort_step;
+    return st;
+}
+
+rmpcd_status rmpcd_sync(rmpcd_system *sys)
+{
+    if (!sys) return RMPCD_EINVAL;
+    return check_errors(sys);
+}
+
+rmpcd_status rmpcd_enable_timers(rmpcd_system *sys, int32_t on)
+{
+    if (!sys) return RMPCD_EINVAL;
+    sys->timing = on != 0;
+    return RMPCD_OK;
+}
+
+rmpcd_status rmpcd_read_timers(rmpcd_system *sys, rmpcd_timers *out, int32_t reset)
+{
+    if (!sys || !out) return RMPCD_EINVAL;
+    CK(cudaStreamSynchronize(sys->stream));
+    for (auto &q : sys->pending) {
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, q.a, q.b));
+        sys->t_ms[q.phase] += ms;
+        sys->t_launches[q.phase] += 1;
+        sys->ev_pool.push_back(q.a);
+        sys->ev_pool.push_back(q.b);
+    }
+    sys->pending.clear();
+    for (int k = 0; k < 4; ++k) {
+        out->launches[k] = sys->t_launches[k];
+        out->ms[k] = sys->t_ms[k];
+        if (reset) { sys->t_launches[k] = 0; sys->t_ms[k] = 0.0; }
+    }
+    return RMPCD_OK;
+}
+
+rmpcd_status rmpcd_launch_count(const rmpcd_system *sys, int64_t *count)
+{
+    if (!sys || !count) return RMPCD_EINVAL;
+    *count = sys->launches;
+    return RMPCD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,744 @@
+// k_md.cu -- near-colloid molecular dynamics of one collision interval
+// (§1.1 velocity Verlet; §1.4 WCA colloid-solvent potential, Verlet-list
+// radius, exact RATTLE for the dimer; §1.5 catalytic A -> B on leaving the
+// catalytic sphere) for the solvent particles in the near list.
+//
+// One thread-block cluster of MD_CS CTAs per replica runs all n_md
+// sub-steps.  The near solvent is spread over the cluster's threads; the few
+// colloids are integrated redundantly (identically) by thread 0 of every CTA
+// in FP64.  Colloid forces are summed as 64-bit fixed point (2^-40
+// resolution): per thread over its particles, per warp by shuffles, per CTA
+// in shared memory, and across the cluster through distributed shared memory
+// in rank order, so the sum is exact and does not depend on the order of the
+// near list.  Per sub-step the cluster synchronises once and each CTA twice.
+//
+// The mixed path does no FP64 arithmetic per particle: every colloid position
+// is split once per sub-step into an integer cell and an FP32 offset, so the
+// particle-colloid separation is an integer difference plus FP32 offsets.
+#include <cooperative_groups.h>
+#include <type_traits>
+
+#include "rmpcd_kernels.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace rmpcd {
+
+constexpr int MDT = 512;        // threads per MD CTA
+constexpr int MD_CS = 8;        // CTAs per replica (cluster size)
+constexpr int NCR = 4;          // colloids whose force partials live in registers
+constexpr int MD_WARPS = MDT / 32;
+
+struct __align__(16) WorkM {
+    int c[3];
+    uint32_t fid;
+    float o[3];
+    int slot;
+    float v[3];
+    float p0;
+    float f[3];
+    float p1;
+};
+struct __align__(16) WorkD {
+    double x[3];
+    double v[3];
+    double f[3];
+    uint32_t fid;
+    int slot;
+};
+
+// FP64 colloid state (fp64 path): unwrapped positions, wrapped copies.
+struct ColD {
+    double X[MAXC][3], V[MAXC][3], Xw[MAXC][3], F[MAXC][3], X0[MAXC][3], Xold[MAXC][3];
+};
+// Mixed colloid state: unwrapped integer cell + FP32 offset in [0,1), FP32
+// velocity and force; Ci is the wrapped integer cell.
+struct ColM {
+    int Xi[MAXC][3], Xoi[MAXC][3], X0i[MAXC][3], Ci[MAXC][3];
+    float Xf[MAXC][3], Xof[MAXC][3], X0f[MAXC][3], V[MAXC][3], F[MAXC][3];
+    float invM[MAXC];
+};
+
+template <bool MIXED>
+struct MDShared {
+    typename std::conditional<MIXED, ColM, ColD>::type C;
+    double M[MAXC], sig[MAXC], epsA[MAXC], epsB[MAXC], rc2[MAXC];
+    float sigf[MAXC], epsAf[MAXC], epsBf[MAXC], rc2f[MAXC];
+    int cat[MAXC];
+    BondDev bond[MAXB];
+    unsigned long long Fq[MAXC * 3];                 // this CTA's partial (atomic path)
+    unsigned long long wpart[MD_WARPS][NCR * 3];     // per-warp partials (register path)
+    unsigned long long part[2][MD_CS][MAXC * 3];     // partials of every CTA of the cluster
+    long long Fsum[MAXC * 3];                        // cluster total (thread 0)
+    int nc, nbond, nn;
+};
+
+// --- per-particle forces ----------------------------------------------------
+// Force on one solvent particle from all colloids (WCA, §1.4).  The reaction
+// on colloid j is -f_j, added in fixed point to acc (register path, j < NCR)
+// or to the CTA's shared sums (atomic path).
+template <bool REG>
+__device__ __forceinline__ void force_d(const ReplicaDev &rp, MDShared<false> &S, const double x[3], uint32_t fid,
+                                        double f[3], long long acc[NCR][3])
+{
+    f[0] = f[1] = f[2] = 0.0;
+    for (int j = 0; j < S.nc; ++j) {
+        double d[3] = {x[0] - S.C.Xw[j][0], x[1] - S.C.Xw[j][1], x[2] - S.C.Xw[j][2]};
+        min_image(rp, d);
+        const double eps = (fid & F_B) ? S.epsB[j] : S.epsA[j];
+        const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (r2 < S.rc2[j]) {
+            const double ir2 = 1.0 / r2;
+            const double s2 = S.sig[j] * S.sig[j] * ir2;
+            const double s6 = s2 * s2 * s2;
+            const double fr = 24.0 * eps * s6 * (2.0 * s6 - 1.0) * ir2;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const double fk = fr * d[k];
+                f[k] = f[k] + fk;
+                const long long q = __double2ll_rn(fk * 0x1p40);
+                if (REG) {
+#pragma unroll
+                    for (int jj = 0; jj < NCR; ++jj)
+                        if (jj == j) acc[jj][k] -= q;
+                } else {
+                    atomicAdd(&S.Fq[3 * j + k], (unsigned long long)(-q));
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) f[k] = f[k] + rp.g[k];
+}
+
+// Mixed: separation from the wrapped colloid cell and offset, FP32 only.
+__device__ __forceinline__ void sep_m(const ReplicaDev &rp, const MDShared<true> &S, int j, const int c[3],
+                                      const float o[3], float d[3])
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] = (float)(c[k] - S.C.Ci[j][k]) + (o[k] - S.C.Xf[j][k]);
+    min_image(rp, d);
+}
+
+template <bool REG>
+__device__ __forceinline__ void force_m(const ReplicaDev &rp, MDShared<true> &S, const int c[3], const float o[3],
+                                        uint32_t fid, float f[3], long long acc[NCR][3])
+{
+    f[0] = f[1] = f[2] = 0.0f;
+    for (int j = 0; j < S.nc; ++j) {
+        float d[3];
+        sep_m(rp, S, j, c, o, d);
+        const float eps = (fid & F_B) ? S.epsBf[j] : S.epsAf[j];
+        const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (r2 < S.rc2f[j]) {
+            const float ir2 = 1.0f / r2;
+            const float s2 = S.sigf[j] * S.sigf[j] * ir2;
+            const float s6 = s2 * s2 * s2;
+            const float fr = 24.0f * eps * s6 * (2.0f * s6 - 1.0f) * ir2;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float fk = fr * d[k];
+                f[k] = f[k] + fk;
+                const long long q = __float2ll_rn(fk * 0x1p40f);   // exact scaling, one rounding
+                if (REG) {
+#pragma unroll
+                    for (int jj = 0; jj < NCR; ++jj)
+                        if (jj == j) acc[jj][k] -= q;
+                } else {
+                    atomicAdd(&S.Fq[3 * j + k], (unsigned long long)(-q));
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) f[k] = f[k] + rp.g_f[k];
+}
+
+__device__ __forceinline__ bool inside_cat_d(const ReplicaDev &rp, const MDShared<false> &S, const double x[3])
+{
+    for (int j = 0; j < S.nc; ++j) {
+        if (!S.cat[j]) continue;
+        double d[3] = {x[0] - S.C.Xw[j][0], x[1] - S.C.Xw[j][1], x[2] - S.C.Xw[j][2]};
+        min_image(rp, d);
+        if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < S.rc2[j]) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool inside_cat_m(const ReplicaDev &rp, const MDShared<true> &S, const int c[3],
+                                             const float o[3])
+{
+    for (int j = 0; j < S.nc; ++j) {
+        if (!S.cat[j]) continue;
+        float d[3];
+        sep_m(rp, S, j, c, o, d);
+        if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < S.rc2f[j]) return true;
+    }
+    return false;
+}
+
+// A tagged A particle that has left every catalytic range becomes B with
+// probability cat_prob (§1.5); an A particle inside a range is tagged.
+__device__ __forceinline__ uint32_t catalysis(const ReplicaDev &rp, uint32_t fid, bool inside, uint32_t step, int s)
+{
+    if (fid & F_B) return fid;
+    if (inside) return fid | F_TAG;
+    if (!(fid & F_TAG)) return fid;
+    bool go = true;
+    if (rp.cat_thr < 4294967296.0) {
+        U4 w = philox(fid & ID_MASK, step, P_CAT, (uint32_t)s, rp.seed);
+        go = (double)w.x < rp.cat_thr;
+    }
+    fid &= ~F_TAG;
+    if (go) fid |= F_B;
+    return fid;
+}
+
+__device__ __forceinline__ bool bonded(const BondDev *bond, int nbond, int a, int b)
+{
+    for (int k = 0; k < nbond; ++k)
+        if ((bond[k].a == a && bond[k].b == b) || (bond[k].a == b && bond[k].b == a)) return true;
+    return false;
+}
+
+// ===========================================================================
+// FP64 colloid integrator (fp64 path; same operation order as the FP64 oracle)
+// ===========================================================================
+// Colloid-colloid truncated LJ (energy shifted at cc_rc), bonded pairs excluded.
+__device__ void colloid_colloid(const ReplicaDev &rp, MDShared<false> &S, long long *Fq)
+{
+    if (!(rp.cc_rc > 0.0)) return;
+    for (int a = 0; a < S.nc; ++a)
+        for (int b = a + 1; b < S.nc; ++b) {
+            if (bonded(S.bond, S.nbond, a, b)) continue;
+            double d[3] = {S.C.Xw[a][0] - S.C.Xw[b][0], S.C.Xw[a][1] - S.C.Xw[b][1], S.C.Xw[a][2] - S.C.Xw[b][2]};
+            min_image(rp, d);
+            const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (!(r2 < rp.cc_rc * rp.cc_rc)) continue;
+            const double ir2 = 1.0 / r2;
+            const double s2 = rp.cc_sigma * rp.cc_sigma * ir2;
+            const double s6 = s2 * s2 * s2;
+            const double fr = 24.0 * rp.cc_eps * s6 * (2.0 * s6 - 1.0) * ir2;
+            for (int k = 0; k < 3; ++k) {
+                const long long q = __double2ll_rn(fr * d[k] * 0x1p40);
+                Fq[3 * a + k] += q;
+                Fq[3 * b + k] -= q;
+            }
+        }
+}
+
+// Exact RATTLE for single bonds (Andersen 1983): the position stage moves
+// both bodies along the old bond vector onto |X_a - X_b| = d (root of smaller
+// magnitude of the quadratic) and corrects their velocities accordingly.
+__device__ void rattle_pos(MDShared<false> &S, double dt)
+{
+    ColD &C = S.C;
+    for (int k = 0; k < S.nbond; ++k) {
+        const int a = S.bond[k].a, b = S.bond[k].b;
+        const double dd = S.bond[k].d;
+        double ro[3], rn[3];
+        for (int t = 0; t < 3; ++t) {
+            ro[t] = C.Xold[a][t] - C.Xold[b][t];
+            rn[t] = C.X[a][t] - C.X[b][t];
+        }
+        const double inv = 1.0 / S.M[a] + 1.0 / S.M[b];
+        const double oo = ro[0] * ro[0] + ro[1] * ro[1] + ro[2] * ro[2];
+        const double on = rn[0] * ro[0] + rn[1] * ro[1] + rn[2] * ro[2];
+        const double nn = rn[0] * rn[0] + rn[1] * rn[1] + rn[2] * rn[2];
+        const double qa = inv * inv * oo;
+        const double qb = 2.0 * inv * on;
+        const double qc = nn - dd * dd;
+        double disc = qb * qb - 4.0 * qa * qc;
+        if (disc < 0.0) disc = 0.0;
+        const double q = -0.5 * (qb + copysign(sqrt(disc), qb));
+        const double gmul = qc / q;
+        for (int t = 0; t < 3; ++t) {
+            const double ca = gmul * ro[t] / S.M[a];
+            const double cb = gmul * ro[t] / S.M[b];
+            C.X[a][t] = C.X[a][t] + ca;
+            C.X[b][t] = C.X[b][t] - cb;
+            C.V[a][t] = C.V[a][t] + ca / dt;
+            C.V[b][t] = C.V[b][t] - cb / dt;
+        }
+    }
+}
+
+// Velocity stage: remove the relative velocity along each bond.
+__device__ void rattle_vel(MDShared<false> &S)
+{
+    ColD &C = S.C;
+    for (int k = 0; k < S.nbond; ++k) {
+        const int a = S.bond[k].a, b = S.bond[k].b;
+        double r[3], dv[3];
+        for (int t = 0; t < 3; ++t) {
+            r[t] = C.X[a][t] - C.X[b][t];
+            dv[t] = C.V[a][t] - C.V[b][t];
+        }
+        const double inv = 1.0 / S.M[a] + 1.0 / S.M[b];
+        const double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        const double rv = dv[0] * r[0] + dv[1] * r[1] + dv[2] * r[2];
+        const double kk = rv / (rr * inv);
+        for (int t = 0; t < 3; ++t) {
+            C.V[a][t] = C.V[a][t] - kk * r[t] / S.M[a];
+            C.V[b][t] = C.V[b][t] + kk * r[t] / S.M[b];
+        }
+    }
+}
+
+__device__ void col_load(const Dev &d, const ReplicaDev &rp, MDShared<false> &S, int j)
+{
+    const int g = rp.col_off + j;
+    for (int k = 0; k < 3; ++k) {
+        S.C.X[j][k] = d.colX[3 * g + k];
+        S.C.V[j][k] = d.colV[3 * g + k];
+        S.C.X0[j][k] = S.C.X[j][k];
+    }
+}
+
+__device__ void col_frames(const ReplicaDev &rp, MDShared<false> &S)
+{
+    for (int j = 0; j < S.nc; ++j) wrapped_colloid(rp, S.C.X[j], S.C.Xw[j]);
+}
+
+__device__ void col_gather(const ReplicaDev &rp, MDShared<false> &S, int par)
+{
+    long long *Fq = S.Fsum;
+    for (int i = 0; i < 3 * S.nc; ++i) {
+        long long acc = 0;
+        for (int q = 0; q < MD_CS; ++q) acc += (long long)S.part[par][q][i];
+        Fq[i] = acc;
+    }
+    colloid_colloid(rp, S, Fq);
+    for (int j = 0; j < S.nc; ++j)
+        for (int k = 0; k < 3; ++k) S.C.F[j][k] = (double)Fq[3 * j + k] * 0x1p-40;
+}
+
+__device__ void col_kick_drift(const ReplicaDev &rp, MDShared<false> &S)
+{
+    const double dt = rp.dt, hdt = rp.hdt;
+    for (int j = 0; j < S.nc; ++j)
+        for (int t = 0; t < 3; ++t) {
+            S.C.V[j][t] = fma(hdt, S.C.F[j][t] / S.M[j], S.C.V[j][t]);
+            S.C.Xold[j][t] = S.C.X[j][t];
+            S.C.X[j][t] = fma(dt, S.C.V[j][t], S.C.X[j][t]);
+        }
+    rattle_pos(S, dt);
+}
+
+__device__ void col_kick(const ReplicaDev &rp, MDShared<false> &S)
+{
+    for (int j = 0; j < S.nc; ++j)
+        for (int t = 0; t < 3; ++t) S.C.V[j][t] = fma(rp.hdt, S.C.F[j][t] / S.M[j], S.C.V[j][t]);
+    rattle_vel(S);
+}
+
+__device__ void col_store(const Dev &d, const ReplicaDev &rp, MDShared<false> &S)
+{
+    bool bad = false;
+    for (int j = 0; j < S.nc; ++j) {
+        const int g = rp.col_off + j;
+        double dd = 0.0;
+        for (int t = 0; t < 3; ++t) {
+            const double e = S.C.X[j][t] - S.C.X0[j][t];
+            dd = dd + e * e;
+            d.colX[3 * g + t] = S.C.X[j][t];
+            d.colV[3 * g + t] = S.C.V[j][t];
+        }
+        if (!(dd <= rp.skin * rp.skin)) bad = true;
+    }
+    if (bad) atomicAdd(&d.err[ERR_SKIN], 1u);
+}
+
+// ===========================================================================
+// Mixed colloid integrator: integer cell + FP32 offset, FP32 arithmetic
+// ===========================================================================
+__device__ __forceinline__ void col_renorm(int Xi[3], float Xf[3])
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float fl = floorf(Xf[k]);
+        Xi[k] += (int)fl;
+        Xf[k] = Xf[k] - fl;
+        if (Xf[k] >= 1.0f) { Xf[k] = 0.0f; Xi[k] += 1; }
+    }
+}
+
+__device__ __forceinline__ void col_sep(const int ai[3], const float af[3], const int bi[3], const float bf[3],
+                                        float r[3])
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r[k] = (float)(ai[k] - bi[k]) + (af[k] - bf[k]);
+}
+
+__device__ void colloid_colloid(const ReplicaDev &rp, MDShared<true> &S, long long *Fq)
+{
+    if (!(rp.cc_rc > 0.0)) return;
+    const float rc = (float)rp.cc_rc, sg = (float)rp.cc_sigma, ep = (float)rp.cc_eps;
+    for (int a = 0; a < S.nc; ++a)
+        for (int b = a + 1; b < S.nc; ++b) {
+            if (bonded(S.bond, S.nbond, a, b)) continue;
+            float d[3];
+            col_sep(S.C.Ci[a], S.C.Xf[a], S.C.Ci[b], S.C.Xf[b], d);
+            min_image(rp, d);
+            const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (!(r2 < rc * rc)) continue;
+            const float ir2 = 1.0f / r2;
+            const float s2 = sg * sg * ir2;
+            const float s6 = s2 * s2 * s2;
+            const float fr = 24.0f * ep * s6 * (2.0f * s6 - 1.0f) * ir2;
+            for (int k = 0; k < 3; ++k) {
+                const long long q = __float2ll_rn(fr * d[k] * 0x1p40f);
+                Fq[3 * a + k] += q;
+                Fq[3 * b + k] -= q;
+            }
+        }
+}
+
+__device__ void rattle_pos(MDShared<true> &S, float dt)
+{
+    ColM &C = S.C;
+    for (int k = 0; k < S.nbond; ++k) {
+        const int a = S.bond[k].a, b = S.bond[k].b;
+        const float dd = (float)S.bond[k].d;
+        float ro[3], rn[3];
+        col_sep(C.Xoi[a], C.Xof[a], C.Xoi[b], C.Xof[b], ro);
+        col_sep(C.Xi[a], C.Xf[a], C.Xi[b], C.Xf[b], rn);
+        const float inv = C.invM[a] + C.invM[b];
+        const float oo = ro[0] * ro[0] + ro[1] * ro[1] + ro[2] * ro[2];
+        const float on = rn[0] * ro[0] + rn[1] * ro[1] + rn[2] * ro[2];
+        const float nn = rn[0] * rn[0] + rn[1] * rn[1] + rn[2] * rn[2];
+        const float qa = inv * inv * oo;
+        const float qb = 2.0f * inv * on;
+        const float qc = nn - dd * dd;
+        float disc = qb * qb - 4.0f * qa * qc;
+        if (disc < 0.0f) disc = 0.0f;
+        const float q = -0.5f * (qb + copysignf(sqrtf(disc), qb));
+        const float gmul = qc / q;
+        const float idt = 1.0f / dt;
+        for (int t = 0; t < 3; ++t) {
+            const float ca = gmul * ro[t] * C.invM[a];
+            const float cb = gmul * ro[t] * C.invM[b];
+            C.Xf[a][t] += ca;
+            C.Xf[b][t] -= cb;
+            C.V[a][t] += ca * idt;
+            C.V[b][t] -= cb * idt;
+        }
+        col_renorm(C.Xi[a], C.Xf[a]);
+        col_renorm(C.Xi[b], C.Xf[b]);
+    }
+}
+
+__device__ void rattle_vel(MDShared<true> &S)
+{
+    ColM &C = S.C;
+    for (int k = 0; k < S.nbond; ++k) {
+        const int a = S.bond[k].a, b = S.bond[k].b;
+        float r[3], dv[3];
+        col_sep(C.Xi[a], C.Xf[a], C.Xi[b], C.Xf[b], r);
+        for (int t = 0; t < 3; ++t) dv[t] = C.V[a][t] - C.V[b][t];
+        const float inv = C.invM[a] + C.invM[b];
+        const float rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        const float rv = dv[0] * r[0] + dv[1] * r[1] + dv[2] * r[2];
+        const float kk = rv / (rr * inv);
+        for (int t = 0; t < 3; ++t) {
+            C.V[a][t] -= kk * r[t] * C.invM[a];
+            C.V[b][t] += kk * r[t] * C.invM[b];
+        }
+    }
+}
+
+__device__ void col_load(const Dev &d, const ReplicaDev &rp, MDShared<true> &S, int j)
+{
+    const int g = rp.col_off + j;
+    for (int k = 0; k < 3; ++k) {
+        S.C.Xi[j][k] = d.colXi[3 * g + k];
+        S.C.Xf[j][k] = d.colXf[3 * g + k];
+        S.C.V[j][k] = d.colVf[3 * g + k];
+        S.C.X0i[j][k] = S.C.Xi[j][k];
+        S.C.X0f[j][k] = S.C.Xf[j][k];
+    }
+    S.C.invM[j] = d.colInvM_f[g];
+}
+
+__device__ void col_frames(const ReplicaDev &rp, MDShared<true> &S)
+{
+    for (int j = 0; j < S.nc; ++j)
+        for (int k = 0; k < 3; ++k) S.C.Ci[j][k] = imod(S.C.Xi[j][k], rp.L[k]);
+}
+
+__device__ void col_gather(const ReplicaDev &rp, MDShared<true> &S, int par)
+{
+    long long *Fq = S.Fsum;
+    for (int i = 0; i < 3 * S.nc; ++i) {
+        long long acc = 0;
+        for (int q = 0; q < MD_CS; ++q) acc += (long long)S.part[par][q][i];
+        Fq[i] = acc;
+    }
+    colloid_colloid(rp, S, Fq);
+    for (int j = 0; j < S.nc; ++j)
+        for (int k = 0; k < 3; ++k) S.C.F[j][k] = __ll2float_rn(Fq[3 * j + k]) * 0x1p-40f;
+}
+
+__device__ void col_kick_drift(const ReplicaDev &rp, MDShared<true> &S)
+{
+    const float dt = rp.dt_f, hdt = rp.hdt_f;
+    for (int j = 0; j < S.nc; ++j) {
+        for (int t = 0; t < 3; ++t) {
+            S.C.V[j][t] = fmaf(hdt, S.C.F[j][t] * S.C.invM[j], S.C.V[j][t]);
+            S.C.Xoi[j][t] = S.C.Xi[j][t];
+            S.C.Xof[j][t] = S.C.Xf[j][t];
+            S.C.Xf[j][t] = fmaf(dt, S.C.V[j][t], S.C.Xf[j][t]);
+        }
+        col_renorm(S.C.Xi[j], S.C.Xf[j]);
+    }
+    rattle_pos(S, dt);
+}
+
+__device__ void col_kick(const ReplicaDev &rp, MDShared<true> &S)
+{
+    for (int j = 0; j < S.nc; ++j)
+        for (int t = 0; t < 3; ++t) S.C.V[j][t] = fmaf(rp.hdt_f, S.C.F[j][t] * S.C.invM[j], S.C.V[j][t]);
+    rattle_vel(S);
+}
+
+__device__ void col_store(const Dev &d, const ReplicaDev &rp, MDShared<true> &S)
+{
+    bool bad = false;
+    const float skin = rp.skin_f;
+    for (int j = 0; j < S.nc; ++j) {
+        const int g = rp.col_off + j;
+        float e[3];
+        col_sep(S.C.Xi[j], S.C.Xf[j], S.C.X0i[j], S.C.X0f[j], e);
+        const float dd = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+        for (int t = 0; t < 3; ++t) {
+            d.colXi[3 * g + t] = S.C.Xi[j][t];
+            d.colXf[3 * g + t] = S.C.Xf[j][t];
+            d.colVf[3 * g + t] = S.C.V[j][t];
+            d.colCi[3 * g + t] = S.C.Ci[j][t];
+        }
+        if (!(dd <= skin * skin)) bad = true;
+    }
+    if (bad) atomicAdd(&d.err[ERR_SKIN], 1u);
+}
+
+// ===========================================================================
+// Cluster-wide reduction of the colloid forces
+// ===========================================================================
+// Reduce this CTA's fixed-point partials and publish them to every CTA of
+// the cluster (slot = this CTA's rank, buffer = sub-step parity).
+template <bool MIXED, bool REG>
+__device__ __forceinline__ void publish_partials(cg::cluster_group &cl, MDShared<MIXED> &S, long long acc[NCR][3],
+                                                 int par)
+{
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int rank = (int)cl.block_rank();
+    if (REG) {
+#pragma unroll
+        for (int j = 0; j < NCR; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                long long x = acc[j][k];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+                if (lane == 0) S.wpart[wid][3 * j + k] = (unsigned long long)x;
+            }
+        __syncthreads();
+        if (tid < 3 * S.nc) {
+            long long x = 0;
+            for (int w = 0; w < MD_WARPS; ++w) x += (long long)S.wpart[w][tid];
+            for (int q = 0; q < MD_CS; ++q) *cl.map_shared_rank(&S.part[par][rank][tid], q) = (unsigned long long)x;
+        }
+    } else {
+        __syncthreads();
+        for (int i = tid; i < 3 * S.nc; i += MDT) {
+            const unsigned long long x = S.Fq[i];
+            for (int q = 0; q < MD_CS; ++q) *cl.map_shared_rank(&S.part[par][rank][i], q) = x;
+        }
+    }
+}
+
+template <bool MIXED, bool REG>
+__device__ void md_body(const Dev &d, MDShared<MIXED> &S, const ReplicaDev &rp, cg::cluster_group &cl,
+                        uint32_t step, int rbuf, int bbuf, int do_bin, int r)
+{
+    using W = typename std::conditional<MIXED, WorkM, WorkD>::type;
+    const int tid = threadIdx.x;
+    const int rank = (int)cl.block_rank();
+    const int nn = S.nn;
+    const int *list = d.near_list + rp.part_off;
+    W *work = reinterpret_cast<W *>(d.md_work) + rp.part_off;
+    const int first = rank * MDT + tid;
+    const int stride = MD_CS * MDT;
+    long long acc[NCR][3];
+    auto zero_acc = [&]() {
+#pragma unroll
+        for (int j = 0; j < NCR; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) acc[j][k] = 0;
+        if (!REG)
+            for (int i = tid; i < 3 * S.nc; i += MDT) S.Fq[i] = 0ull;
+    };
+
+    // forces at the start of the interval
+    zero_acc();
+    if (!REG) __syncthreads();
+    for (int k = first; k < nn; k += stride) {
+        W w;
+        const int slot = list[k];
+        w.slot = slot;
+        if constexpr (MIXED) {
+            RecM rec = load_rec(reinterpret_cast<const RecM *>(d.rec[rbuf]) + slot);
+            for (int t = 0; t < 3; ++t) { w.c[t] = cw_get(rec.cw, t); w.o[t] = rec.o[t]; w.v[t] = rec.v[t]; }
+            w.fid = rec.fid;
+            force_m<REG>(rp, S, w.c, w.o, w.fid, w.f, acc);
+        } else {
+            RecD rec = load_rec(reinterpret_cast<const RecD *>(d.rec[rbuf]) + slot);
+            for (int t = 0; t < 3; ++t) { w.x[t] = rec.x[t]; w.v[t] = rec.v[t]; }
+            w.fid = rec.fid;
+            force_d<REG>(rp, S, w.x, w.fid, w.f, acc);
+        }
+        work[k] = w;
+    }
+    publish_partials<MIXED, REG>(cl, S, acc, 0);
+    cl.sync();
+    if (tid == 0) col_gather(rp, S, 0);
+
+    const double dt = rp.dt, hdt = rp.hdt;
+    for (int s = 0; s < rp.n_md; ++s) {
+        const int par = (s + 1) & 1;
+        if (tid == 0) {
+            // colloids: first half kick, drift, RATTLE position stage
+            col_kick_drift(rp, S);
+            col_frames(rp, S);
+        }
+        zero_acc();
+        __syncthreads();
+        // solvent: second half kick of the previous sub-step, first half kick
+        // and drift of this one, new forces, catalytic conversion
+        for (int k = first; k < nn; k += stride) {
+            W w = work[k];
+            if constexpr (MIXED) {
+                const float hdtf = rp.hdt_f, dtf = rp.dt_f;
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    if (s > 0) w.v[t] = fmaf(hdtf, w.f[t], w.v[t]);
+                    w.v[t] = fmaf(hdtf, w.f[t], w.v[t]);
+                    w.o[t] = fmaf(dtf, w.v[t], w.o[t]);
+                }
+                force_m<REG>(rp, S, w.c, w.o, w.fid, w.f, acc);
+                w.fid = catalysis(rp, w.fid, inside_cat_m(rp, S, w.c, w.o), step, s);
+            } else {
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    if (s > 0) w.v[t] = fma(hdt, w.f[t], w.v[t]);
+                    w.v[t] = fma(hdt, w.f[t], w.v[t]);
+                    w.x[t] = fma(dt, w.v[t], w.x[t]);
+                }
+                force_d<REG>(rp, S, w.x, w.fid, w.f, acc);
+                w.fid = catalysis(rp, w.fid, inside_cat_d(rp, S, w.x), step, s);
+            }
+            work[k] = w;
+        }
+        publish_partials<MIXED, REG>(cl, S, acc, par);
+        cl.sync();
+        if (tid == 0) {
+            // colloids: new forces, second half kick, RATTLE velocity stage
+            col_gather(rp, S, par);
+            col_kick(rp, S);
+        }
+    }
+
+    // last half kick, wrap, write back (and bin for the collision of `step`)
+    double sh[3];
+    grid_shift(rp.seed, step, sh);
+    for (int k = first; k < nn; k += stride) {
+        W w = work[k];
+        if constexpr (MIXED) {
+            for (int t = 0; t < 3; ++t) w.v[t] = fmaf(rp.hdt_f, w.f[t], w.v[t]);
+            renorm_m(rp, w.c, w.o);
+            RecM rec;
+            rec.cw = cw_make(w.c[0], w.c[1], w.c[2]);
+            for (int t = 0; t < 3; ++t) { rec.o[t] = w.o[t]; rec.v[t] = w.v[t]; }
+            rec.fid = do_bin ? (w.fid | F_PROP) : (w.fid & ~F_PROP);
+            store_rec(reinterpret_cast<RecM *>(d.rec[rbuf]) + w.slot, rec);
+            if (do_bin) {
+                float sf[3] = {(float)sh[0], (float)sh[1], (float)sh[2]};
+                bin_particle(d, bbuf, rp.cell_off + cell_key_m(rp, w.c, w.o, sf), w.slot);
+            }
+        } else {
+            for (int t = 0; t < 3; ++t) w.v[t] = fma(hdt, w.f[t], w.v[t]);
+            wrap_periodic_d(rp, w.x);
+            RecD rec;
+            for (int t = 0; t < 3; ++t) { rec.x[t] = w.x[t]; rec.v[t] = w.v[t]; }
+            rec.fid = do_bin ? (w.fid | F_PROP) : (w.fid & ~F_PROP);
+            rec.u0 = 0u;
+            rec.u1 = 0.0;
+            store_rec(reinterpret_cast<RecD *>(d.rec[rbuf]) + w.slot, rec);
+            if (do_bin) bin_particle(d, bbuf, rp.cell_off + cell_key_d(rp, w.x, sh), w.slot);
+        }
+    }
+    if (tid == 0 && rank == 0) {
+        col_frames(rp, S);
+        col_store(d, rp, S);
+        // every CTA read near_count before the first cluster barrier
+        d.near_count[r] = 0;
+    }
+    cl.sync();   // no CTA leaves while a peer may still write to its shared memory
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(MDT, 1) k_md(Dev d, uint32_t step, int rbuf, int bbuf, int do_bin)
+{
+    __shared__ MDShared<MIXED> S;
+    __shared__ ReplicaDev s_rp;
+    cg::cluster_group cl = cg::this_cluster();
+    const int r = blockIdx.x / MD_CS;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_rp = d.rep[r];
+    __syncthreads();
+    const ReplicaDev &rp = s_rp;
+    if (rp.n_col == 0) return;   // uniform over the cluster
+    if (tid == 0) {
+        S.nc = rp.n_col;
+        S.nbond = rp.n_bond;
+        S.nn = min(d.near_count[r], rp.n_part);
+    }
+    if (tid < rp.n_col) {
+        const int j = tid, g = rp.col_off + tid;
+        col_load(d, rp, S, j);
+        S.M[j] = d.colM[g];
+        S.sig[j] = d.colSig[g]; S.epsA[j] = d.colEpsA[g]; S.epsB[j] = d.colEpsB[g]; S.rc2[j] = d.colRc2[g];
+        S.sigf[j] = d.colSig_f[g]; S.epsAf[j] = d.colEpsA_f[g]; S.epsBf[j] = d.colEpsB_f[g];
+        S.rc2f[j] = d.colRc2_f[g];
+        S.cat[j] = d.colCat[g];
+    }
+    if (tid < rp.n_bond) S.bond[tid] = d.bonds[rp.bond_off + tid];
+    __syncthreads();
+    if (tid == 0) col_frames(rp, S);
+    __syncthreads();
+    // all CTAs of the cluster must have read near_count before rank 0 resets it
+    cl.sync();
+    if (rp.n_col <= NCR) md_body<MIXED, true>(d, S, rp, cl, step, rbuf, bbuf, do_bin, r);
+    else md_body<MIXED, false>(d, S, rp, cl, step, rbuf, bbuf, do_bin, r);
+}
+
+void launch_md(bool mixed, const Dev &d, uint32_t step, int rbuf, int bbuf, int do_bin, cudaStream_t s)
+{
+    if (d.n_rep <= 0) return;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(d.n_rep * MD_CS), 1, 1);
+    cfg.blockDim = dim3(MDT, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = MD_CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (mixed) cudaLaunchKernelEx(&cfg, k_md<true>, d, step, rbuf, bbuf, do_bin);
+    else cudaLaunchKernelEx(&cfg, k_md<false>, d, step, rbuf, bbuf, do_bin);
+}
+
+}  // namespace rmpcd

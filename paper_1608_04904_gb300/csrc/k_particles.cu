@@ -1,0 +1,230 @@
+// k_particles.cu -- particle-parallel kernels: state conversion, the granular
+// interval flight and binning (§1.1 streaming, §1.4 grid shift and sort), and
+// the final reduction of the observables (§1.4 temperature estimator).
+#include "rmpcd_kernels.cuh"
+
+namespace rmpcd {
+
+// Replica of a global storage slot (replicas are contiguous and in order).
+__device__ __forceinline__ int replica_of(const Dev &d, int slot)
+{
+    int lo = 0, hi = d.n_rep - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (d.rep[mid].part_off <= slot) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// State conversion: canonical FP64 arrays <-> records.
+// ---------------------------------------------------------------------------
+__global__ void k_set_state_m(Dev d, int r, int n, const double *x, const double *v, const uint8_t *fl, int rbuf)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const ReplicaDev rp = d.rep[r];
+    RecM rec;
+    int c[3];
+    for (int k = 0; k < 3; ++k) {
+        double xk = x[3 * i + k];
+        int ck = (int)floor(xk);
+        if (ck < 0) ck = 0;
+        if (ck > rp.L[k] - 1) ck = rp.L[k] - 1;
+        c[k] = ck;
+        rec.o[k] = (float)(xk - (double)ck);
+        rec.v[k] = (float)v[3 * i + k];
+    }
+    rec.cw = cw_make(c[0], c[1], c[2]);
+    uint8_t f = fl ? fl[i] : 0;
+    rec.fid = (uint32_t)i | ((f & 1) ? F_B : 0u) | ((f & 2) ? F_TAG : 0u);
+    store_rec(reinterpret_cast<RecM *>(d.rec[rbuf]) + rp.part_off + i, rec);
+}
+
+__global__ void k_set_state_d(Dev d, int r, int n, const double *x, const double *v, const uint8_t *fl, int rbuf)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int off = d.rep[r].part_off;
+    RecD rec;
+    for (int k = 0; k < 3; ++k) { rec.x[k] = x[3 * i + k]; rec.v[k] = v[3 * i + k]; }
+    uint8_t f = fl ? fl[i] : 0;
+    rec.fid = (uint32_t)i | ((f & 1) ? F_B : 0u) | ((f & 2) ? F_TAG : 0u);
+    rec.u0 = 0u;
+    rec.u1 = 0.0;
+    store_rec(reinterpret_cast<RecD *>(d.rec[rbuf]) + off + i, rec);
+}
+
+__global__ void k_get_state_m(Dev d, int r, int n, int rbuf, double *x, double *v, uint8_t *fl, uint32_t *id,
+                              int32_t *cell, int has_sort, uint32_t sort_step)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const ReplicaDev rp = d.rep[r];
+    RecM rec = load_rec(reinterpret_cast<const RecM *>(d.rec[rbuf]) + rp.part_off + i);
+    int c[3] = {cw_get(rec.cw, 0), cw_get(rec.cw, 1), cw_get(rec.cw, 2)};
+    for (int k = 0; k < 3; ++k) {
+        if (x) x[3 * i + k] = (double)c[k] + (double)rec.o[k];
+        if (v) v[3 * i + k] = (double)rec.v[k];
+    }
+    if (fl) fl[i] = (uint8_t)(((rec.fid & F_B) ? 1 : 0) | ((rec.fid & F_TAG) ? 2 : 0));
+    if (id) id[i] = rec.fid & ID_MASK;
+    if (cell) {
+        if (has_sort) {
+            double s[3];
+            grid_shift(rp.seed, sort_step, s);
+            float sf[3] = {(float)s[0], (float)s[1], (float)s[2]};
+            cell[i] = cell_key_m(rp, c, rec.o, sf);
+        } else {
+            cell[i] = -1;
+        }
+    }
+}
+
+__global__ void k_get_state_d(Dev d, int r, int n, int rbuf, double *x, double *v, uint8_t *fl, uint32_t *id,
+                              int32_t *cell, int has_sort, uint32_t sort_step)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const ReplicaDev rp = d.rep[r];
+    RecD rec = load_rec(reinterpret_cast<const RecD *>(d.rec[rbuf]) + rp.part_off + i);
+    for (int k = 0; k < 3; ++k) {
+        if (x) x[3 * i + k] = rec.x[k];
+        if (v) v[3 * i + k] = rec.v[k];
+    }
+    if (fl) fl[i] = (uint8_t)(((rec.fid & F_B) ? 1 : 0) | ((rec.fid & F_TAG) ? 2 : 0));
+    if (id) id[i] = rec.fid & ID_MASK;
+    if (cell) {
+        if (has_sort) {
+            double s[3];
+            grid_shift(rp.seed, sort_step, s);
+            cell[i] = cell_key_d(rp, rec.x, s);
+        } else {
+            cell[i] = -1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Particle pass over every slot.
+//   PM_STREAM: near-colloid particles join the near list, the others fly over
+//              tau and are stored (granular interval motion).
+//   PM_BIN:    bin the stored positions on the grid of collision `step`.
+//   PM_PRIME:  like PM_STREAM, but far particles are binned at their flown
+//              position and stored unmoved (first interval of a fused run).
+// ---------------------------------------------------------------------------
+template <bool MIXED>
+__global__ void k_particles(Dev d, int mode, uint32_t step, int rbuf, int bbuf)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.n_total) return;
+    const int r = replica_of(d, i);
+    const ReplicaDev &rp = d.rep[r];
+    double s[3];
+    if (mode != PM_STREAM) grid_shift(rp.seed, step, s);
+    if (MIXED) {
+        RecM *recs = reinterpret_cast<RecM *>(d.rec[rbuf]);
+        RecM rec = load_rec(recs + i);
+        int c[3] = {cw_get(rec.cw, 0), cw_get(rec.cw, 1), cw_get(rec.cw, 2)};
+        if (mode == PM_BIN) {
+            float sf[3] = {(float)s[0], (float)s[1], (float)s[2]};
+            bin_particle(d, bbuf, rp.cell_off + cell_key_m(rp, c, rec.o, sf), i);
+            return;
+        }
+        if (rp.n_col > 0 && near_test_m(rp, rp.n_col, d.colCi + 3 * rp.col_off, d.colXf + 3 * rp.col_off,
+                                        d.colRb_f + rp.col_off, c, rec.o, rec.v)) {
+            int k = atomicAdd(&d.near_count[r], 1);
+            if (k < rp.n_part) d.near_list[rp.part_off + k] = i;
+            else atomicOr(&d.err[ERR_BOUNDS], 1u);
+            return;
+        }
+        float o[3] = {rec.o[0], rec.o[1], rec.o[2]};
+        float v[3] = {rec.v[0], rec.v[1], rec.v[2]};
+        flight_m(rp, c, o, v);
+        if (mode == PM_STREAM) {
+            rec.cw = cw_make(c[0], c[1], c[2]);
+            for (int k = 0; k < 3; ++k) { rec.o[k] = o[k]; rec.v[k] = v[k]; }
+            store_rec(recs + i, rec);
+        } else {
+            float sf[3] = {(float)s[0], (float)s[1], (float)s[2]};
+            bin_particle(d, bbuf, rp.cell_off + cell_key_m(rp, c, o, sf), i);
+        }
+    } else {
+        RecD *recs = reinterpret_cast<RecD *>(d.rec[rbuf]);
+        RecD rec = load_rec(recs + i);
+        if (mode == PM_BIN) {
+            bin_particle(d, bbuf, rp.cell_off + cell_key_d(rp, rec.x, s), i);
+            return;
+        }
+        if (rp.n_col > 0 && near_test_d(d, rp, rec.x, rec.v)) {
+            int k = atomicAdd(&d.near_count[r], 1);
+            if (k < rp.n_part) d.near_list[rp.part_off + k] = i;
+            else atomicOr(&d.err[ERR_BOUNDS], 1u);
+            return;
+        }
+        double x[3] = {rec.x[0], rec.x[1], rec.x[2]};
+        double v[3] = {rec.v[0], rec.v[1], rec.v[2]};
+        flight_d(rp, x, v);
+        if (mode == PM_STREAM) {
+            for (int k = 0; k < 3; ++k) { rec.x[k] = x[k]; rec.v[k] = v[k]; }
+            store_rec(recs + i, rec);
+        } else {
+            bin_particle(d, bbuf, rp.cell_off + cell_key_d(rp, x, s), i);
+        }
+    }
+}
+
+// Per replica: sum the per-tile partial observables in tile order.
+__global__ void k_obs_reduce(Dev d)
+{
+    const int r = blockIdx.x;
+    const ReplicaDev &rp = d.rep[r];
+    __shared__ double part[256][8];
+    const int tid = threadIdx.x;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // thread t sums tiles t, t + 256, ... in order; then a fixed tree
+    for (int t = tid; t < rp.n_tiles; t += 256)
+        for (int k = 0; k < 8; ++k) acc[k] += d.obs_part[(long long)(rp.tile_off + t) * 8 + k];
+    for (int k = 0; k < 8; ++k) part[tid][k] = acc[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (tid < w)
+            for (int k = 0; k < 8; ++k) part[tid][k] += part[tid + w][k];
+        __syncthreads();
+    }
+    if (tid < 8) d.obs_out[r * 8 + tid] = part[0][tid];
+}
+
+void launch_set_state(bool mixed, const Dev &d, int replica, int n, const double *x, const double *v,
+                      const uint8_t *flags, int rbuf, cudaStream_t s)
+{
+    if (n <= 0) return;
+    int nb = (n + 255) / 256;
+    if (mixed) k_set_state_m<<<nb, 256, 0, s>>>(d, replica, n, x, v, flags, rbuf);
+    else k_set_state_d<<<nb, 256, 0, s>>>(d, replica, n, x, v, flags, rbuf);
+}
+
+void launch_get_state(bool mixed, const Dev &d, int replica, int n, int rbuf, double *x, double *v, uint8_t *flags,
+                      uint32_t *id, int32_t *cell, int has_sort, uint32_t sort_step, cudaStream_t s)
+{
+    if (n <= 0) return;
+    int nb = (n + 255) / 256;
+    if (mixed) k_get_state_m<<<nb, 256, 0, s>>>(d, replica, n, rbuf, x, v, flags, id, cell, has_sort, sort_step);
+    else k_get_state_d<<<nb, 256, 0, s>>>(d, replica, n, rbuf, x, v, flags, id, cell, has_sort, sort_step);
+}
+
+void launch_particles(bool mixed, const Dev &d, int mode, uint32_t step, int rbuf, int bbuf, cudaStream_t s)
+{
+    if (d.n_total <= 0) return;
+    int nb = (d.n_total + 255) / 256;
+    if (mixed) k_particles<true><<<nb, 256, 0, s>>>(d, mode, step, rbuf, bbuf);
+    else k_particles<false><<<nb, 256, 0, s>>>(d, mode, step, rbuf, bbuf);
+}
+
+void launch_obs_reduce(const Dev &d, cudaStream_t s)
+{
+    if (d.n_rep <= 0) return;
+    k_obs_reduce<<<d.n_rep, 256, 0, s>>>(d);
+}
+
+}  // namespace rmpcd

@@ -1,0 +1,475 @@
+// rmpcd_common.cuh -- device data layout and per-particle arithmetic shared by
+// the sm_103a kernels of the MPCD collision-interval update.
+//
+// Method: de Buyl, Huang & Deprez, RMPCDMD (arXiv:1608.04904), §1.1 and §1.4.
+// Units: cell side 1, solvent mass 1.
+//
+// Two storage precisions:
+//   mixed: 32-byte record {packed integer cell (10/10/10 bits), FP32 offset in
+//          the cell [0,1)^3, FP32 velocity, id+flags}; arithmetic in FP32.
+//   fp64 : 64-byte record {FP64 position, id+flags, FP64 velocity}.
+// The id+flags word holds the particle id in bits 0..28 and the flags
+// B (species), TAG (inside a catalytic range) and PROP (already moved through
+// the current interval by the MD kernel) in bits 29..31.
+//
+// FP64 arithmetic is written with explicit fma() where a fused multiply-add is
+// meant and is compiled with --fmad=false, so every other product and sum is
+// rounded where written.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rmpcd {
+
+constexpr int CPT = 64;            // cells per tile of the cell pass
+constexpr int CP_THREADS = 256;    // threads per cell-pass CTA
+constexpr int TP_M = 1024;         // particles a mixed cell-pass CTA stages at once
+constexpr int TP_D = 768;          // particles an fp64 cell-pass CTA stages at once
+constexpr int MD_THREADS = 1024;   // threads of the near-field MD CTA (one per replica)
+constexpr int MAXC = 64;           // colloids per replica handled by the MD CTA
+constexpr int MAXB = 16;           // bonds per replica
+
+constexpr uint32_t F_B = 1u << 29;
+constexpr uint32_t F_TAG = 1u << 30;
+constexpr uint32_t F_PROP = 1u << 31;
+constexpr uint32_t ID_MASK = (1u << 29) - 1u;
+
+enum Purpose : uint32_t { P_SHIFT = 1, P_ROT = 2, P_REACT = 3, P_THERMO = 4, P_VIRT = 5, P_CAT = 6 };
+
+enum ErrSlot { ERR_OVERFLOW = 0, ERR_SKIN = 1, ERR_TIMEOUT = 2, ERR_BOUNDS = 3, ERR_COUNT = 8 };
+
+// Per-replica constants, computed on the host once.
+struct ReplicaDev {
+    int L[3];
+    int nz;                 // z layers of the shifted grid: L[2] + walls
+    int walls, rho_wall, n_md, n_slabs;
+    int n_part, part_off;   // solvent slots [part_off, part_off + n_part)
+    int n_cells, cell_off;  // cells [cell_off, cell_off + n_cells), cell_off = CPT * tile_off
+    int tile_off, n_tiles;
+    int n_col, col_off, n_bond, bond_off;
+    int bulk_on, has_g;
+    int thr_off, pad;
+    double kT, tau, dt, hdt, ca, sa, omc;
+    double g[3];
+    double gnorm, cat_thr, skin;
+    double slab_x0[4], slab_x1[4], slab_sd[4];
+    double cc_eps, cc_sigma, cc_rc;
+    float tau_f, dt_f, hdt_f, ca_f, sa_f, omc_f;
+    float g_f[3];
+    float gnorm_f, skin_f;
+    float slab_sd_f[4];
+    unsigned long long seed;
+};
+
+struct BondDev { int a, b; double d; };
+
+// All device pointers of a system (passed by value to every kernel).
+struct Dev {
+    const ReplicaDev *rep;
+    const int *tile_rep;         // tile -> replica
+    void *rec[2];                // solvent records, double buffered
+    int *count[2];               // particles per cell, double buffered
+    int *bucket[2];              // [cell * cap + rank] -> storage slot
+    int *near_list;              // per replica region [part_off, part_off + n_part)
+    int *near_count;             // [n_rep]
+    unsigned long long *tile_state;  // decoupled look-back, one word per tile
+    unsigned int *ticket;        // [2]
+    unsigned int *err;           // [ERR_COUNT]
+    double *obs_part;            // [n_tiles][8]
+    double *obs_out;             // [n_rep][8]
+    const double *bulk_thr;      // per replica [cap + 1]: accept iff draw < thr[N_B]
+    double *colX, *colV;         // fp64 path: [n_col_total * 3], unwrapped
+    int *colXi, *colCi;          // mixed path: unwrapped / wrapped integer cell [3n]
+    float *colXf, *colVf;        // mixed path: FP32 offset in the cell, velocity [3n]
+    const double *colM, *colSig, *colEpsA, *colEpsB, *colRc2, *colRc;
+    const float *colSig_f, *colEpsA_f, *colEpsB_f, *colRc2_f, *colRc_f;
+    const float *colRb_f;        // r_c + |g| tau^2 / 2 + skin (near-list radius without |v| tau)
+    const float *colInvM_f;      // 1 / mass
+    const int *colCat;
+    const BondDev *bonds;
+    void *md_work;               // near-particle working state
+    int cap;
+    int n_rep;
+    int n_tiles;
+    int n_total;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): 10 rounds of the
+// multiply-xor bijection with a Weyl key schedule.
+// ---------------------------------------------------------------------------
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                     unsigned long long seed)
+{
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
+// 24-bit uniform in [0,1), exact in FP32 and FP64.
+__device__ __forceinline__ double u24d(uint32_t b) { return (double)(b >> 8) * 0x1p-24; }
+__device__ __forceinline__ float u24f(uint32_t b) { return (float)(b >> 8) * 0x1p-24f; }
+
+// Random grid shift of one collision (§1.4): s uniform in [0,1)^3.
+__device__ __forceinline__ void grid_shift(unsigned long long seed, uint32_t step, double s[3])
+{
+    U4 w = philox(0u, step, P_SHIFT, 0u, seed);
+    s[0] = u24d(w.x); s[1] = u24d(w.y); s[2] = u24d(w.z);
+}
+
+// Uniform point on the unit sphere (Marsaglia 1972) for the rotation axis of
+// one cell; the acceptance test is exact integer arithmetic.
+template <typename R>
+__device__ __forceinline__ void rotation_axis(unsigned long long seed, uint32_t step, uint32_t cell, R n[3])
+{
+    for (uint32_t attempt = 0; attempt < 16u; ++attempt) {
+        U4 w = philox(cell, step, P_ROT, attempt, seed);
+        uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int pair = 0; pair < 2; ++pair) {
+            long long A = 2 * (long long)(ws[2 * pair] >> 8) + 1 - (1 << 24);
+            long long B = 2 * (long long)(ws[2 * pair + 1] >> 8) + 1 - (1 << 24);
+            long long S = A * A + B * B;
+            if (S < (1ll << 48)) {
+                // 1 - s and 1 - 2s are formed as exact integers before the one
+                // rounding to R: no cancellation near the poles in FP32, and in
+                // FP64 the same values as (1 - s), (1 - 2 s) computed directly.
+                R a = (R)A * (R)0x1p-24;
+                R b = (R)B * (R)0x1p-24;
+                R q = sqrt((R)((1ll << 48) - S) * (R)0x1p-48);
+                n[0] = R(2) * a * q;
+                n[1] = R(2) * b * q;
+                n[2] = (R)((1ll << 48) - 2 * S) * (R)0x1p-48;
+                return;
+            }
+        }
+    }
+    n[0] = R(0); n[1] = R(0); n[2] = R(1);
+}
+
+// Box-Muller pair from two words, u1 in (0,1], u2 in [0,1).
+__device__ __forceinline__ void box_muller(uint32_t b0, uint32_t b1, double &g0, double &g1)
+{
+    double u1 = (double)((b0 >> 8) + 1u) * 0x1p-24;
+    double u2 = (double)(b1 >> 8) * 0x1p-24;
+    double r = sqrt(-2.0 * log(u1));
+    double ph = 6.283185307179586 * u2;
+    double sn, cs;
+    sincos(ph, &sn, &cs);
+    g0 = r * cs;
+    g1 = r * sn;
+}
+__device__ __forceinline__ void box_muller(uint32_t b0, uint32_t b1, float &g0, float &g1)
+{
+    float u1 = (float)((b0 >> 8) + 1u) * 0x1p-24f;
+    float u2 = (float)(b1 >> 8) * 0x1p-24f;
+    float r = sqrtf(-2.0f * logf(u1));
+    float sn, cs;
+    sincospif(2.0f * u2, &sn, &cs);
+    g0 = r * cs;
+    g1 = r * sn;
+}
+
+// ---------------------------------------------------------------------------
+// Records.
+// ---------------------------------------------------------------------------
+struct __align__(16) RecM {
+    uint32_t cw;        // cx | cy << 10 | cz << 20
+    float o[3];         // offset in the cell
+    float v[3];
+    uint32_t fid;       // id | flags
+};
+struct __align__(16) RecD {
+    double x[3];
+    uint32_t fid;
+    uint32_t u0;
+    double v[3];
+    double u1;
+};
+static_assert(sizeof(RecM) == 32, "mixed record is one 32-byte sector");
+static_assert(sizeof(RecD) == 64, "fp64 record is two 32-byte sectors");
+
+__device__ __forceinline__ RecM load_rec(const RecM *p)
+{
+    const uint4 *q = reinterpret_cast<const uint4 *>(p);
+    uint4 a = __ldg(q), b = __ldg(q + 1);
+    RecM r;
+    r.cw = a.x; r.o[0] = __uint_as_float(a.y); r.o[1] = __uint_as_float(a.z); r.o[2] = __uint_as_float(a.w);
+    r.v[0] = __uint_as_float(b.x); r.v[1] = __uint_as_float(b.y); r.v[2] = __uint_as_float(b.z); r.fid = b.w;
+    return r;
+}
+__device__ __forceinline__ void store_rec(RecM *p, const RecM &r)
+{
+    uint4 *q = reinterpret_cast<uint4 *>(p);
+    q[0] = make_uint4(r.cw, __float_as_uint(r.o[0]), __float_as_uint(r.o[1]), __float_as_uint(r.o[2]));
+    q[1] = make_uint4(__float_as_uint(r.v[0]), __float_as_uint(r.v[1]), __float_as_uint(r.v[2]), r.fid);
+}
+__device__ __forceinline__ RecD load_rec(const RecD *p)
+{
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    double2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3);
+    RecD r;
+    r.x[0] = a.x; r.x[1] = a.y; r.x[2] = b.x;
+    unsigned long long w = (unsigned long long)__double_as_longlong(b.y);
+    r.fid = (uint32_t)w; r.u0 = (uint32_t)(w >> 32);
+    r.v[0] = c.x; r.v[1] = c.y; r.v[2] = d.x; r.u1 = d.y;
+    return r;
+}
+__device__ __forceinline__ void store_rec(RecD *p, const RecD &r)
+{
+    double2 *q = reinterpret_cast<double2 *>(p);
+    unsigned long long w = (unsigned long long)r.fid | ((unsigned long long)r.u0 << 32);
+    q[0] = make_double2(r.x[0], r.x[1]);
+    q[1] = make_double2(r.x[2], __longlong_as_double((long long)w));
+    q[2] = make_double2(r.v[0], r.v[1]);
+    q[3] = make_double2(r.v[2], 0.0);
+}
+
+__device__ __forceinline__ int cw_get(uint32_t cw, int d) { return (int)((cw >> (10 * d)) & 1023u); }
+__device__ __forceinline__ uint32_t cw_make(int cx, int cy, int cz)
+{
+    return (uint32_t)cx | ((uint32_t)cy << 10) | ((uint32_t)cz << 20);
+}
+__device__ __forceinline__ int imod(int a, int L) { int m = a % L; return m < 0 ? m + L : m; }
+
+// ---------------------------------------------------------------------------
+// Free flight over time t (§1.1 streaming; §1.4 constant acceleration).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void fly_d(const ReplicaDev &rp, double x[3], double v[3], double t)
+{
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        x[d] = fma(v[d], t, x[d]);
+        if (rp.has_g) {
+            x[d] = x[d] + 0.5 * rp.g[d] * t * t;
+            v[d] = v[d] + rp.g[d] * t;
+        }
+    }
+}
+
+__device__ __forceinline__ void wrap_periodic_d(const ReplicaDev &rp, double x[3])
+{
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d == 2 && rp.walls) continue;
+        double L = (double)rp.L[d];
+        if (x[d] >= L) x[d] = x[d] - L;
+        else if (x[d] < 0.0) { x[d] = x[d] + L; if (x[d] >= L) x[d] = 0.0; }
+    }
+}
+
+// Flight over tau with stick walls at z = 0, L[2] (bounce-back: the whole
+// velocity reverses at the wall) or periodic boundaries.
+__device__ __forceinline__ void flight_d(const ReplicaDev &rp, double x[3], double v[3])
+{
+    if (!rp.walls) { fly_d(rp, x, v, rp.tau); wrap_periodic_d(rp, x); return; }
+    double Lz = (double)rp.L[2];
+    double zend = fma(v[2], rp.tau, x[2]);
+    double th = -1.0, wall = 0.0;
+    if (zend < 0.0) { th = -x[2] / v[2]; wall = 0.0; }
+    else if (zend > Lz) { th = (Lz - x[2]) / v[2]; wall = Lz; }
+    if (th < 0.0) {
+        fly_d(rp, x, v, rp.tau);
+    } else {
+        fly_d(rp, x, v, th);
+        x[2] = wall;
+        v[0] = -v[0]; v[1] = -v[1]; v[2] = -v[2];
+        fly_d(rp, x, v, rp.tau - th);
+        if (x[2] < 0.0) x[2] = 0.0;
+        if (x[2] > Lz) x[2] = Lz;
+    }
+    wrap_periodic_d(rp, x);
+}
+
+// Mixed precision: position = integer cell + FP32 offset.  Renormalise the
+// offset to [0,1) and carry into the cell index (periodic axes wrap).
+__device__ __forceinline__ void renorm_m(const ReplicaDev &rp, int c[3], float o[3])
+{
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        float fl = floorf(o[d]);
+        c[d] += (int)fl;
+        o[d] = o[d] - fl;
+        if (o[d] >= 1.0f) { o[d] = 0.0f; c[d] += 1; }
+        if (d == 2 && rp.walls) {
+            if (c[2] < 0) { c[2] = 0; o[2] = 0.0f; }
+            if (c[2] > rp.L[2] - 1) { c[2] = rp.L[2] - 1; o[2] = 1.0f; }
+        } else {
+            c[d] = imod(c[d], rp.L[d]);
+        }
+    }
+}
+
+__device__ __forceinline__ void fly_m(const ReplicaDev &rp, float o[3], float v[3], float t)
+{
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        o[d] = fmaf(v[d], t, o[d]);
+        if (rp.has_g) {
+            o[d] = o[d] + 0.5f * rp.g_f[d] * t * t;
+            v[d] = v[d] + rp.g_f[d] * t;
+        }
+    }
+}
+
+__device__ __forceinline__ void flight_m(const ReplicaDev &rp, int c[3], float o[3], float v[3])
+{
+    const float tau = rp.tau_f;
+    if (rp.walls) {
+        // distance to the wall the particle moves towards, from the nearby cell
+        float th = -1.0f;
+        int hit = 0;
+        if (v[2] < 0.0f) {
+            float dist = (float)c[2] + o[2];
+            if (v[2] * tau < -dist) { th = dist / -v[2]; hit = 1; }
+        } else if (v[2] > 0.0f) {
+            float dist = (float)(rp.L[2] - 1 - c[2]) + (1.0f - o[2]);
+            if (v[2] * tau > dist) { th = dist / v[2]; hit = 2; }
+        }
+        if (hit) {
+            fly_m(rp, o, v, th);
+            if (hit == 1) { c[2] = 0; o[2] = 0.0f; } else { c[2] = rp.L[2] - 1; o[2] = 1.0f; }
+            v[0] = -v[0]; v[1] = -v[1]; v[2] = -v[2];
+            fly_m(rp, o, v, tau - th);
+            renorm_m(rp, c, o);
+            return;
+        }
+    }
+    fly_m(rp, o, v, tau);
+    renorm_m(rp, c, o);
+}
+
+// ---------------------------------------------------------------------------
+// Cell key on the grid shifted by s (x fastest); walls add one z layer.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int cell_key_d(const ReplicaDev &rp, const double x[3], const double s[3])
+{
+    int c[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        long long k = (long long)floor(x[d] - s[d]);
+        if (d == 2 && rp.walls) {
+            k += 1;
+            if (k < 0) k = 0;
+            if (k > rp.nz - 1) k = rp.nz - 1;
+        } else {
+            k %= rp.L[d];
+            if (k < 0) k += rp.L[d];
+        }
+        c[d] = (int)k;
+    }
+    return c[0] + rp.L[0] * (c[1] + rp.L[1] * c[2]);
+}
+
+__device__ __forceinline__ int cell_key_m(const ReplicaDev &rp, const int cc[3], const float o[3], const float s[3])
+{
+    int c[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        int k = cc[d] + (int)floorf(o[d] - s[d]);   // exact: the sign of o - s is exact
+        if (d == 2 && rp.walls) {
+            k += 1;
+            if (k < 0) k = 0;
+            if (k > rp.nz - 1) k = rp.nz - 1;
+        } else {
+            k = imod(k, rp.L[d]);
+        }
+        c[d] = k;
+    }
+    return c[0] + rp.L[0] * (c[1] + rp.L[1] * c[2]);
+}
+
+// Minimum image along periodic axes, |d| < 1.5 L assumed.
+template <typename R>
+__device__ __forceinline__ void min_image(const ReplicaDev &rp, R d[3])
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (k == 2 && rp.walls) continue;
+        R L = (R)rp.L[k];
+        if (d[k] > R(0.5) * L) d[k] = d[k] - L;
+        else if (d[k] < -R(0.5) * L) d[k] = d[k] + L;
+    }
+}
+
+__device__ __forceinline__ void wrapped_colloid(const ReplicaDev &rp, const double *X, double out[3])
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double L = (double)rp.L[k];
+        out[k] = X[k] - L * floor(X[k] / L);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Bins: one particle into the cell's bucket.  Cells above cap raise
+// ERR_OVERFLOW (the entry is dropped; the step is then invalid).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void bin_particle(const Dev &d, int buf, int gcell, int slot)
+{
+    int r = atomicAdd(&d.count[buf][gcell], 1);
+    if (r < d.cap) d.bucket[buf][(long long)gcell * d.cap + r] = slot;
+    else atomicMax(&d.err[ERR_OVERFLOW], (unsigned int)(r + 1));
+}
+
+// Near-colloid test of §1.4's Verlet-list radius: may this particle come
+// within a colloid's cut-off during the interval?
+__device__ __forceinline__ bool near_test_d(const Dev &d, const ReplicaDev &rp, const double x[3], const double v[3])
+{
+    double speed = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    for (int j = 0; j < rp.n_col; ++j) {
+        const double *X = d.colX + 3 * (rp.col_off + j);
+        double Xw[3];
+        wrapped_colloid(rp, X, Xw);
+        double dd[3] = {x[0] - Xw[0], x[1] - Xw[1], x[2] - Xw[2]};
+        min_image(rp, dd);
+        double r2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
+        double R = d.colRc[rp.col_off + j] + speed * rp.tau + 0.5 * rp.gnorm * rp.tau * rp.tau + rp.skin;
+        if (r2 < R * R) return true;
+    }
+    return false;
+}
+
+// Mixed path: colloids as wrapped integer cell Ci + FP32 offset Cf (stride 3),
+// so the test needs no FP64 arithmetic.
+__device__ __forceinline__ bool near_test_m(const ReplicaDev &rp, int nc, const int *Ci, const float *Cf,
+                                            const float *Rb, const int c[3], const float o[3], const float v[3])
+{
+    const float st = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * rp.tau_f;
+    for (int j = 0; j < nc; ++j) {
+        float dd[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dd[k] = (float)(c[k] - Ci[3 * j + k]) + (o[k] - Cf[3 * j + k]);
+        min_image(rp, dd);
+        const float r2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
+        const float R = Rb[j] + st;
+        if (r2 < R * R) return true;
+    }
+    return false;
+}
+
+// Acquire / release accesses for the look-back scan.
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+}  // namespace rmpcd

@@ -1,0 +1,39 @@
+// rmpcd_kernels.cuh -- host-side launchers of the sm_103a kernels (internal).
+#pragma once
+
+#include "rmpcd_common.cuh"
+
+namespace rmpcd {
+
+// Options of one cell pass (bit mask).
+enum CellPassOpt {
+    CP_FLIGHT = 1,    // records not marked PROP fly over tau when gathered
+    CP_COLLIDE = 2,   // SRD / MPC-AT / virtual-particle collision
+    CP_REACT = 4,     // bulk B -> A reaction
+    CP_NEXT = 8,      // classify and bin every written record for the next collision
+    CP_OBS = 16,      // per-tile observable partial sums
+    CP_WRITE = 32     // write the gathered (sorted) records to the output buffer
+};
+
+struct CellPassArgs {
+    int opts;
+    uint32_t step;     // collision index: grid shift, rotation axes, reactions
+    int cur;           // count / bucket buffer consumed
+    int nxt;           // count / bucket buffer filled by CP_NEXT
+    int rin, rout;     // record buffers
+    uint32_t epoch;    // launch counter: parity picks the ticket, (epoch % 65535) + 1 tags the look-back
+};
+
+enum ParticleMode { PM_STREAM = 0, PM_BIN = 1, PM_PRIME = 2 };
+
+void launch_cellpass(bool mixed, const Dev &d, const CellPassArgs &a, cudaStream_t s);
+void launch_particles(bool mixed, const Dev &d, int mode, uint32_t step, int rbuf, int bbuf, cudaStream_t s);
+void launch_md(bool mixed, const Dev &d, uint32_t step, int rbuf, int bbuf, int do_bin, cudaStream_t s);
+void launch_set_state(bool mixed, const Dev &d, int replica, int n, const double *x, const double *v,
+                      const uint8_t *flags, int rbuf, cudaStream_t s);
+void launch_get_state(bool mixed, const Dev &d, int replica, int n, int rbuf, double *x, double *v, uint8_t *flags,
+                      uint32_t *id, int32_t *cell, int has_sort, uint32_t sort_step, cudaStream_t s);
+void launch_obs_reduce(const Dev &d, cudaStream_t s);
+size_t cellpass_smem(bool mixed);
+
+}  // namespace rmpcd

@@ -135,7 +135,8 @@ def solvent(cfg, col=(), n=None, seed=None, frac_b=0.0, tag_frac=0.0, exclude=Tr
             bad |= (d * d).sum(1) < rcs[j] ** 2
         todo = todo[bad]
     v = rng.standard_normal((n, 3)) * math.sqrt(cfg["kT"])
-    v -= v.mean(axis=0)
+    if n > 0:
+        v -= v.mean(axis=0)
     if cfg.get("precision", "fp64") == "mixed":
         v = v.astype(np.float32).astype(np.float64)
     flags = np.zeros(n, dtype=np.uint8)

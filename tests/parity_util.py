@@ -1,0 +1,37 @@
+"""Helpers of the GPU-vs-oracle parity tests.
+
+Tolerances (per velocity component, relative to max(|v_oracle|, sqrt(kT))):
+  fp64 path 1e-12, mixed path 1e-5.  Positions: absolute 1e-12 * L (fp64) and
+  1e-5 (mixed, cell side 1), compared modulo the box on periodic axes.
+"""
+import numpy as np
+
+TOL = {"fp64": 1e-12, "mixed": 1e-5}
+
+
+def vel_bad(v_gpu, v_orc, kT, precision):
+    scale = np.maximum(np.abs(v_orc), np.sqrt(kT) if kT > 0 else 1.0)
+    return (np.abs(v_gpu - v_orc) > TOL[precision] * scale).any(axis=1)
+
+
+def pos_bad(x_gpu, x_orc, L, walls, precision):
+    L = np.asarray(L, float)
+    d = x_gpu - x_orc
+    per = np.ones(3, bool)
+    if walls:
+        per[2] = False
+    d[:, per] -= L[per] * np.round(d[:, per] / L[per])
+    tol = TOL[precision] * (L.max() if precision == "fp64" else 1.0)
+    return (np.abs(d) > tol).any(axis=1)
+
+
+def by_id(state_ids, *arrays):
+    order = np.argsort(state_ids)
+    return [a[order] for a in arrays]
+
+
+def near_boundary(x, s, eps):
+    """Particles whose position lies within eps of a plane of the shifted grid."""
+    f = x - s
+    frac = f - np.floor(f)
+    return ((frac < eps) | (frac > 1.0 - eps)).any(axis=1)

@@ -1,0 +1,134 @@
+"""CPU checks of the C ABI: the library loads, exports what include/rmpcd.h
+declares, and rejects invalid parameters before touching the GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1608_04904_gb300 import api, build
+    build.build()
+    return api
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "rmpcd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rmpcd_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(api):
+    lib = api.load()
+    names = _declared()
+    assert len(names) >= 19
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(api.EXPORTS) == names
+
+
+def test_struct_layouts_match_header(api, tmp_path):
+    """Every field offset and struct size of the ctypes mirror equals what a C
+    compiler makes of include/rmpcd.h."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    structs = {"rmpcd_params": api.Params, "rmpcd_colloid": api.Colloid, "rmpcd_bond": api.Bond,
+               "rmpcd_obs": api.Obs, "rmpcd_timers": api.Timers}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rmpcd.h"', "int main(void){"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0;}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line.strip():
+            a, b, c = line.split()
+            got[(a, b)] = int(c)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def _create(api, params, colloids=None, bonds=None, cap=64, precision=1, n=1):
+    lib = api.load()
+    h = C.c_void_p()
+    st = lib.rmpcd_create(C.byref(h), precision, n, params, colloids, bonds, cap, None)
+    return st, lib.rmpcd_last_error(None).decode()
+
+
+def _params(api, **kw):
+    from paper_1608_04904_gb300 import synth
+    cfg = synth.base_config(**kw)
+    return api.make_params(cfg, 100)
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("L", (1, 16, 16), "L[0]"),
+    ("L", (16, 16, 2000), "L[2]"),
+    ("n_md", 0, "n_md"),
+    ("tau", 0.0, "tau"),
+    ("cat_prob", 1.5, "cat_prob"),
+    ("skin", -1.0, "skin"),
+])
+def test_invalid_parameters_are_rejected(api, field, value, msg):
+    p = _params(api, **{field: value})
+    st, err = _create(api, p)
+    assert st == 1 and msg in err
+
+
+def test_invalid_bucket_cap_and_precision(api):
+    p = _params(api)
+    st, err = _create(api, p, cap=0)
+    assert st == 1 and "bucket_cap" in err
+    st, err = _create(api, p, cap=100000)
+    assert st == 1 and "bucket_cap" in err
+    st, err = _create(api, p, precision=7)
+    assert st == 1 and "precision" in err
+
+
+def test_walls_need_no_z_force_and_no_colloids(api):
+    p = _params(api, walls=1, rho_wall=10, g=(0.0, 0.0, 0.01))
+    st, err = _create(api, p)
+    assert st == 1 and "g[2]" in err
+    p = _params(api, walls=1, rho_wall=10)
+    p.n_colloids = 1
+    col = (api.Colloid * 1)()
+    col[0].mass, col[0].sigma = 1.0, 1.0
+    st, err = _create(api, p, colloids=col)
+    assert st == 1 and "walls" in err
+
+
+def test_bad_bond_is_rejected(api):
+    p = _params(api)
+    p.n_colloids = 2
+    p.n_bonds = 1
+    col = (api.Colloid * 2)()
+    for c in col:
+        c.mass, c.sigma = 1.0, 1.0
+    b = (api.Bond * 1)()
+    b[0].a, b[0].b, b[0].d = 0, 0, 1.0
+    st, err = _create(api, p, colloids=col, bonds=b)
+    assert st == 1 and "bond" in err
+
+
+def test_null_arguments(api):
+    lib = api.load()
+    assert lib.rmpcd_step(None, 1) == 1
+    assert lib.rmpcd_sync(None) == 1
+    lib.rmpcd_destroy(None)
+    h = C.c_void_p()
+    assert lib.rmpcd_create(C.byref(h), 1, 0, None, None, None, 64, None) == 1

@@ -1,0 +1,374 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.  Integer results (cell keys, sort permutation, species
+flags) must be bit-identical; velocities and positions within the
+tolerances of parity_util (fp64 1e-12, mixed 1e-5)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1608_04904_gb300 import api, build, synth
+from parity_util import by_id, near_boundary, pos_bad, vel_bad
+
+pytestmark = pytest.mark.gpu
+
+PRECS = ["fp64", "mixed"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    build.build()
+    api.load()
+
+
+def gpu(cfg, x, v, fl, col=(), bonds=(), precision="fp64", cap=64, step=0):
+    s = api.System.single(cfg, len(x), col, bonds, precision=precision, bucket_cap=cap)
+    s.set_state(0, x, v, fl)
+    s.set_step(step)
+    return s
+
+
+def oracle(cfg, x, v, fl, col=(), bonds=(), step=0):
+    return orc.OracleSystem(cfg, x, v, fl, colloids=synth.colloid_arrays(col) if col else None,
+                            bonds=list(bonds), step=step)
+
+
+SORT_CASES = {
+    "ragged": dict(L=(5, 7, 6), n=2113),
+    "rho10": dict(L=(16, 16, 16), n=40960),
+    "walls": dict(L=(8, 8, 6), n=3000, walls=1, rho_wall=10),
+    "long": dict(L=(40, 8, 9), n=29000),
+}
+
+
+def _case(name, precision, seed=3, **extra):
+    c = dict(SORT_CASES[name])
+    n = c.pop("n")
+    cfg = synth.base_config(precision=precision, seed=seed, **c, **extra)
+    x, v, fl = synth.solvent(cfg, n=n, seed=seed + 100, frac_b=0.3)
+    return cfg, x, v, fl
+
+
+@pytest.mark.parametrize("precision", PRECS)
+@pytest.mark.parametrize("name", list(SORT_CASES))
+def test_shift_and_sort_bit_exact(precision, name):
+    cfg, x, v, fl = _case(name, precision)
+    g = gpu(cfg, x, v, fl, precision=precision, step=7)
+    g.shift_and_sort()
+    st = g.get_state()
+    o = oracle(cfg, x, v, fl, step=7)
+    o.shift_and_sort()
+    assert np.array_equal(st["id"], o.id)
+    assert np.array_equal(st["cell"], o.key)
+    assert np.array_equal(st["flags"], o.flags)
+    assert np.array_equal(st["x"], o.x)
+    assert np.array_equal(st["v"], o.v)
+
+
+@pytest.mark.parametrize("precision", PRECS)
+@pytest.mark.parametrize("name,extra", [
+    ("ragged", {}), ("rho10", {}), ("long", {"alpha": math.radians(90.0)}),
+    ("walls", {}), ("rho10", {"slabs": [(0.0, 4.0, 1.5), (8.0, 10.0, 0.5)]}),
+])
+def test_collide_parity(precision, name, extra):
+    cfg, x, v, fl = _case(name, precision, **extra)
+    g = gpu(cfg, x, v, fl, precision=precision, step=11)
+    g.shift_and_sort()
+    g.collide()
+    st = g.get_state()
+    o = oracle(cfg, x, v, fl, step=11)
+    o.shift_and_sort()
+    o.collide()
+    assert np.array_equal(st["id"], o.id)
+    bad = vel_bad(st["v"], o.v, cfg["kT"], precision)
+    assert not bad.any(), (int(bad.sum()), np.abs(st["v"] - o.v).max())
+
+
+def test_fp64_srd_is_bit_exact():
+    cfg, x, v, fl = _case("rho10", "fp64")
+    g = gpu(cfg, x, v, fl, precision="fp64", step=2)
+    g.shift_and_sort()
+    g.collide()
+    o = oracle(cfg, x, v, fl, step=2)
+    o.shift_and_sort()
+    o.collide()
+    assert np.array_equal(g.get_state()["v"], o.v)
+
+
+@pytest.mark.parametrize("precision", PRECS)
+@pytest.mark.parametrize("rate", [0.05, 1e6])
+def test_bulk_reaction_flags_bit_exact(precision, rate):
+    cfg, x, v, fl = _case("rho10", precision, bulk_rate=rate)
+    x, v, fl = synth.solvent(cfg, n=len(x), seed=5, frac_b=0.5, tag_frac=0.2)
+    g = gpu(cfg, x, v, fl, precision=precision, step=4)
+    g.shift_and_sort()
+    g.react()
+    st = g.get_state()
+    o = oracle(cfg, x, v, fl, step=4)
+    o.shift_and_sort()
+    o.react()
+    assert np.array_equal(st["id"], o.id)
+    assert np.array_equal(st["flags"], o.flags)
+    assert (st["flags"] & 1).sum() < (fl & 1).sum()
+
+
+@pytest.mark.parametrize("precision", PRECS)
+@pytest.mark.parametrize("kind", ["periodic_g", "walls_g"])
+def test_free_flight_parity(precision, kind):
+    if kind == "periodic_g":
+        cfg = synth.base_config(L=(9, 10, 11), g=(0.01, -0.003, 0.002), tau=0.7, precision=precision)
+    else:
+        cfg = synth.base_config(L=(8, 8, 10), walls=1, rho_wall=10, g=(0.02, 0.0, 0.0), tau=1.0,
+                                precision=precision)
+    x, v, fl = synth.solvent(cfg, n=9000, seed=8)
+    g = gpu(cfg, x, v, fl, precision=precision)
+    g.stream_interval()
+    st = g.get_state()
+    o = oracle(cfg, x, v, fl)
+    o.interval()
+    assert np.array_equal(st["id"], np.arange(len(x)))
+    assert not pos_bad(st["x"], o.x, cfg["L"], cfg["walls"], precision).any()
+    assert not vel_bad(st["v"], o.v, cfg["kT"], precision).any()
+    if kind == "walls_g":
+        assert st["x"][:, 2].min() >= 0.0 and st["x"][:, 2].max() <= cfg["L"][2]
+        assert (np.sign(st["v"][:, 2]) != np.sign(v[:, 2])).sum() > 100
+
+
+def _dimer(precision, L=12, seed=2, **kw):
+    cfg, col, bonds = synth.dimer32(precision=precision, L=L)
+    cfg.update(kw)
+    x, v, fl = synth.solvent(cfg, col, seed=seed, frac_b=0.2, tag_frac=0.0)
+    return cfg, col, bonds, x, v, fl
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_md_interval_parity(precision):
+    cfg, col, bonds, x, v, fl = _dimer(precision)
+    col[0]["v"] = (0.02, -0.01, 0.0)
+    col[1]["v"] = (0.02, -0.01, 0.0)
+    g = gpu(cfg, x, v, fl, col, bonds, precision=precision, step=3)
+    g.stream_interval()
+    st = g.get_state()
+    o = oracle(cfg, x, v, fl, col, bonds, step=3)
+    o.interval()
+    near = o.near.astype(bool)
+    assert near.sum() > 500
+    pb = pos_bad(st["x"], o.x, cfg["L"], 0, precision)
+    vb = vel_bad(st["v"], o.v, cfg["kT"], precision)
+    if precision == "fp64":
+        assert not pb.any() and not vb.any()
+        assert np.array_equal(st["flags"], o.flags)
+    else:
+        # FP32 forces: a particle that grazes a cut-off may take the other branch
+        assert pb.sum() <= 2 and vb.sum() <= 2, (pb.sum(), vb.sum())
+        assert (st["flags"] != o.flags).sum() <= 2
+    gc = g.get_colloids(0)
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    assert np.allclose(gc["x"], o.X, rtol=0, atol=tol * cfg["L"][0])
+    assert np.allclose(gc["v"], o.V, rtol=0, atol=max(tol, 1e-9) * 10)
+    r = gc["x"][0] - gc["x"][1]
+    # exact RATTLE: to rounding of the path's precision
+    assert abs(np.linalg.norm(r) - 4.5) < (1e-11 if precision == "fp64" else 1e-5)
+
+
+def _compare_step(cfg, st, o, precision):
+    """Compare a GPU state with the oracle's after full intervals."""
+    gid, gx, gv, gf, gc = by_id(st["id"], st["id"], st["x"], st["v"], st["flags"], st["cell"])
+    oid, ox, ov, of, oc = by_id(o.id, o.id, o.x, o.v, o.flags, o.key)
+    assert np.array_equal(gid, oid)
+    if precision == "fp64":
+        assert np.array_equal(st["id"], o.id)
+        assert np.array_equal(gc, oc)
+        assert np.array_equal(gf, of)
+        assert not pos_bad(gx, ox, cfg["L"], cfg.get("walls", 0), "fp64").any()
+        assert not vel_bad(gv, ov, cfg["kT"], "fp64").any()
+        return
+    # mixed: keys may differ for particles that FP32 flight puts on the other
+    # side of a cell plane; those cells are excluded from the velocity check
+    mism = gc != oc
+    s = o.shift
+    border = near_boundary(ox, s, 1e-4)
+    assert np.all(border[mism]), "key mismatch away from a cell boundary"
+    assert mism.sum() <= max(3, 1e-4 * len(gc))
+    badcells = np.isin(oc, oc[mism]) | np.isin(oc, gc[mism])
+    assert not pos_bad(gx, ox, cfg["L"], cfg.get("walls", 0), "mixed").any()
+    vb = vel_bad(gv, ov, cfg["kT"], "mixed") & ~badcells
+    assert vb.sum() <= 2, int(vb.sum())
+    assert (gf != of).sum() <= 2 + mism.sum()
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_fused_step_parity_dimer(precision):
+    cfg, col, bonds, x, v, fl = _dimer(precision, bulk_rate=0.05)
+    g = gpu(cfg, x, v, fl, col, bonds, precision=precision, step=5)
+    g.step(1)
+    o = oracle(cfg, x, v, fl, col, bonds, step=5)
+    o.step(1)
+    _compare_step(cfg, g.get_state(), o, precision)
+    assert g.get_step() == 6
+
+
+def test_fused_three_steps_fp64():
+    cfg, col, bonds, x, v, fl = _dimer("fp64", L=14, bulk_rate=0.05)
+    g = gpu(cfg, x, v, fl, col, bonds, precision="fp64")
+    g.step(3)
+    o = oracle(cfg, x, v, fl, col, bonds)
+    o.step(3)
+    _compare_step(cfg, g.get_state(), o, "fp64")
+    gc = g.get_colloids(0)
+    assert np.allclose(gc["x"], o.X, rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_fused_equals_granular(precision):
+    cfg, col, bonds, x, v, fl = _dimer(precision, bulk_rate=0.05)
+    a = gpu(cfg, x, v, fl, col, bonds, precision=precision, step=9)
+    a.step(2)
+    sa = a.get_state()
+    b = gpu(cfg, x, v, fl, col, bonds, precision=precision, step=9)
+    for k in range(2):
+        b.stream_interval()
+        b.shift_and_sort()
+        b.collide()
+        b.react()
+        b.set_step(10 + k)
+    sb = b.get_state()
+    for key in ("id", "x", "v", "flags", "cell"):
+        assert np.array_equal(sa[key], sb[key]), key
+    assert np.array_equal(a.get_colloids(0)["x"], b.get_colloids(0)["x"])
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_runs_are_deterministic(precision):
+    cfg, col, bonds, x, v, fl = _dimer(precision, bulk_rate=0.05)
+    outs = []
+    for _ in range(2):
+        g = gpu(cfg, x, v, fl, col, bonds, precision=precision)
+        g.step(3)
+        outs.append(g.get_state())
+    for key in outs[0]:
+        assert np.array_equal(outs[0][key], outs[1][key]), key
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_observables_match_oracle(precision):
+    cfg, col, bonds, x, v, fl = _dimer(precision, bulk_rate=0.05)
+    g = gpu(cfg, x, v, fl, col, bonds, precision=precision)
+    g.step(2)
+    ob = g.observables(0)
+    o = oracle(cfg, x, v, fl, col, bonds)
+    o.step(2)
+    tol = 1e-10 if precision == "fp64" else 2e-5
+    assert abs(ob["temperature"] - o.temperature()) < tol * o.temperature()
+    assert ob["n_B"] == int((o.flags & 1).sum()) or precision == "mixed"
+    assert ob["n_solvent"] == len(x)
+    assert np.allclose(ob["momentum"], o.v.sum(0), rtol=0, atol=1e-6 if precision == "fp64" else 1e-2)
+    # granular path computes the same numbers on the same grid
+    st = g.get_state()
+    h = gpu(cfg, st["x"], st["v"], st["flags"], col, bonds, precision=precision, step=1)
+    h.shift_and_sort()
+    assert abs(h.observables(0)["temperature"] - ob["temperature"]) < 1e-6 * ob["temperature"]
+
+
+def test_empty_and_single_particle_systems():
+    for n in (0, 1):
+        cfg = synth.base_config(L=(4, 5, 6), precision="mixed")
+        x, v, fl = synth.solvent(cfg, n=n, seed=1)
+        g = gpu(cfg, x, v, fl, precision="mixed")
+        g.step(3)
+        st = g.get_state()
+        assert len(st["id"]) == n
+        o = oracle(cfg, x, v, fl)
+        o.step(3)
+        if n:
+            assert not pos_bad(st["x"], o.x, cfg["L"], 0, "mixed").any()
+            assert np.array_equal(st["v"], o.v.astype(np.float32).astype(np.float64)) or \
+                not vel_bad(st["v"], o.v, 1.0, "mixed").any()
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_one_crowded_cell(precision):
+    cfg = synth.base_config(L=(4, 4, 4), precision=precision, bulk_rate=0.3)
+    rng = np.random.Generator(np.random.PCG64(4))
+    n = 700
+    x = 1.25 + np.floor(rng.uniform(0, 0.5, (n, 3)) * 2**24) * 2.0**-24
+    v = rng.standard_normal((n, 3)).astype(np.float32).astype(np.float64)
+    fl = (rng.uniform(size=n) < 0.5).astype(np.uint8)
+    g = gpu(cfg, x, v, fl, precision=precision, cap=768)
+    g.shift_and_sort()
+    g.collide()
+    g.react()
+    st = g.get_state()
+    o = oracle(cfg, x, v, fl)
+    o.shift_and_sort()
+    o.collide()
+    o.react()
+    assert o.count.max() > 300
+    assert np.array_equal(st["id"], o.id)
+    assert np.array_equal(st["flags"], o.flags)
+    assert not vel_bad(st["v"], o.v, 1.0, precision).any()
+
+
+def test_bucket_overflow_is_reported():
+    cfg = synth.base_config(L=(4, 4, 4), precision="mixed")
+    n = 200
+    x = np.full((n, 3), 1.5) + np.linspace(0, 0.01, n)[:, None]
+    v = np.zeros((n, 3))
+    g = gpu(cfg, x, v, None, precision="mixed", cap=64)
+    g.shift_and_sort()
+    with pytest.raises(api.RmpcdError) as e:
+        g.get_state()
+    assert e.value.code == "EOVERFLOW"
+
+
+def test_skin_violation_is_reported():
+    cfg, col, bonds, x, v, fl = _dimer("fp64")
+    col[0]["v"] = (3.0, 0.0, 0.0)
+    col[1]["v"] = (3.0, 0.0, 0.0)
+    g = gpu(cfg, x, v, fl, col, bonds, precision="fp64")
+    g.stream_interval()
+    with pytest.raises(api.RmpcdError) as e:
+        g.sync()
+    assert e.value.code == "ESKIN"
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_replicas_in_one_batch_match_single_runs(precision):
+    reps = []
+    for k, L in enumerate((6, 9, 12)):
+        cfg, col, bonds = synth.dimer32(precision=precision, L=L, seed=20 + k) if L == 12 else \
+            (synth.base_config(L=(L, L + 1, L), precision=precision, seed=20 + k, bulk_rate=0.1), [], [])
+        x, v, fl = synth.solvent(cfg, col, seed=30 + k, frac_b=0.3)
+        reps.append((cfg, col, bonds, x, v, fl))
+    b = api.System([dict(cfg=c, n=len(x), colloids=col, bonds=bd) for c, col, bd, x, v, fl in reps],
+                   precision=precision)
+    for r, (c, col, bd, x, v, fl) in enumerate(reps):
+        b.set_state(r, x, v, fl)
+    b.step(2)
+    for r, (c, col, bd, x, v, fl) in enumerate(reps):
+        s = gpu(c, x, v, fl, col, bd, precision=precision)
+        s.step(2)
+        sa, sb = b.get_state(r), s.get_state(0)
+        for key in sa:
+            assert np.array_equal(sa[key], sb[key]), (r, key)
+        o = oracle(c, x, v, fl, col, bd)
+        o.step(2)
+        if precision == "fp64":
+            _compare_step(c, sa, o, "fp64")
+
+
+def test_device_pointer_state_roundtrip():
+    import torch
+    cfg, x, v, fl = _case("ragged", "fp64")
+    g = api.System.single(cfg, len(x), precision="fp64")
+    g.set_state(0, torch.from_numpy(x).cuda(), torch.from_numpy(v).cuda(), torch.from_numpy(fl).cuda())
+    out = {"x": torch.empty((len(x), 3), dtype=torch.float64, device="cuda"),
+           "v": torch.empty((len(x), 3), dtype=torch.float64, device="cuda"),
+           "flags": torch.empty(len(x), dtype=torch.uint8, device="cuda")}
+    g.get_state(0, out=out)
+    assert np.array_equal(out["x"].cpu().numpy(), x)
+    assert np.array_equal(out["v"].cpu().numpy(), v)
+    assert np.array_equal(out["flags"].cpu().numpy(), fl)
