@@ -49,6 +49,10 @@ def workload(name, precision, seed_offset=0):
         cfg, col, bonds = synth.dimer32(precision=precision, seed=2 + seed_offset)
         desc = ("reactive sphere dimer (C+N, sigma 2, M 100, bond 4.5), 32^3 periodic box, rho 10, "
                 "327680 solvent, 50 MD sub-steps dt 0.01, alpha 90 deg, tau 0.5, kT 1/3, p_cat 1, bulk k 0.01")
+    elif name == "dimer64":
+        cfg, col, bonds = synth.dimer32(precision=precision, seed=2 + seed_offset, L=64)
+        desc = ("reactive sphere dimer as dimer32 in a 64^3 periodic box, rho 10, 2621440 solvent "
+                "(larger than L2; profiling case)")
     elif name == "sphere16":
         cfg, col, bonds = synth.sphere16(precision=precision, seed=1 + seed_offset)
         desc = "one WCA sphere (sigma 2, M 200), 16^3 periodic box, rho 10, 40960 solvent, 50 MD sub-steps"
@@ -202,11 +206,13 @@ def run_reference(args, ws, rank):
 
 
 def timed_run(api, torch, cfg, col, bonds, x, v, fl, precision, steps, warmup, flush, dev_index, sample_clocks,
-              barrier):
+              barrier, md_cluster=0, md_kernel=0):
     stream = torch.cuda.current_stream()
     s = api.System.single(cfg, len(x), col, bonds, precision=precision, stream=stream)
+    s.set_tuning(md_cluster, md_kernel)
     s.set_state(0, x, v, fl)
-    for _ in range(warmup):
+    # warm-up, including the 12 tuning intervals of the MD cluster size
+    for _ in range(max(warmup, 13 if (col and md_cluster == 0) else 0)):   # 3 trials x <= 4 sizes
         s.step(1)
     torch.cuda.synchronize()
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -233,6 +239,7 @@ def timed_run(api, torch, cfg, col, bonds, x, v, fl, precision, steps, warmup, f
     timers = s.read_timers(reset=True)
     s.enable_timers(False)
     obs = s.observables(0)
+    obs["md_cluster"], obs["md_kernel"] = s.get_tuning()
     s.close()
     return ms, timers, launches, clocks, obs
 
@@ -272,8 +279,10 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="dimer32", choices=["dimer32", "sphere16", "poiseuille128"])
+    ap.add_argument("--workload", default="dimer32", choices=["dimer32", "dimer64", "sphere16", "poiseuille128"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--md-cluster", type=int, default=0, help="MD CTAs per replica (0 = autotune)")
+    ap.add_argument("--md-kernel", type=int, default=0, help="MD kernel: 0 auto, 1 general, 2 few-colloid")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--no-e2e", action="store_true")
@@ -305,7 +314,8 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     ms, timers, launches, clocks, obs = timed_run(api, torch, cfg, col, bonds, x, v, fl, args.precision,
-                                                  args.steps, args.warmup, flush, local, rank == 0, barrier)
+                                                  args.steps, args.warmup, flush, local, rank == 0, barrier,
+                                                  args.md_cluster, args.md_kernel)
     ms_max = ms
     if ws > 1:
         import torch.distributed as dist
@@ -347,14 +357,15 @@ def main():
         "config": {"workload": f"{args.workload}: {desc}", "n_solvent": n, "precision": args.precision,
                    "parallelism": "replicas" if ws > 1 else "single",
                    "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
-                   "timing": "CUDA events around each rmpcd_step(1) on the library's stream"},
+                   "timing": "CUDA events around each rmpcd_step(1) on the library's stream",
+                   "md_cluster": obs["md_cluster"], "md_kernel": obs["md_kernel"]},
         "roofline": roofline, "kernels": kernels, "gpu_launches": launches, "clocks": clocks,
         "observables": {"temperature": obs["temperature"], "n_B": obs["n_B"], "kT": cfg["kT"]},
     }
     if rank == 0 and not args.no_fp64 and args.precision == "mixed":
         k64 = max(20, args.steps // 4)
         ms64, t64, _, _, _ = timed_run(api, torch, cfg, col, bonds, x, v, fl, "fp64", k64, args.warmup, flush, local,
-                                       False, lambda: None)
+                                       False, lambda: None, args.md_cluster, args.md_kernel)
         v64 = n * k64 / (ms64 / 1e3)
         line["fp64"] = {"value": v64, "ms_per_step": ms64 / k64, "steps": k64,
                         "cellpass_avg_us": 1e3 * t64["cellpass"]["ms"] / t64["cellpass"]["launches"]}

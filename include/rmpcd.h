@@ -171,7 +171,8 @@ rmpcd_status rmpcd_react(rmpcd_system *sys);
  * stream, shift_and_sort, collide, react, step + 1. */
 rmpcd_status rmpcd_step(rmpcd_system *sys, int32_t n_intervals);
 
-/* Observables of one replica for the last collision.  Synchronises. */
+/* Observables of one replica on the grid of the last collision (computed by
+ * one extra cell pass over the stored state when requested).  Synchronises. */
 rmpcd_status rmpcd_observables(rmpcd_system *sys, int32_t replica, rmpcd_obs *out);
 
 /* Wait for all queued work and return latched device errors. */
@@ -182,7 +183,7 @@ rmpcd_status rmpcd_sync(rmpcd_system *sys);
  * around each kernel it launches; rmpcd_read_timers synchronises and returns,
  * per phase, the launches and their summed duration since the last reset.
  * Phases: 0 = first binning of a fused run, 1 = near-colloid MD,
- * 2 = cell pass (sort + collide + react + next flight/bin), 3 = observables. */
+ * 2 = cell pass (sort + collide + react + next flight/bin), 3 = unused. */
 typedef struct {
     int64_t launches[4];
     double ms[4];
@@ -190,6 +191,21 @@ typedef struct {
 
 rmpcd_status rmpcd_enable_timers(rmpcd_system *sys, int32_t on);
 rmpcd_status rmpcd_read_timers(rmpcd_system *sys, rmpcd_timers *out, int32_t reset);
+
+/* Launch tuning of the near-colloid MD kernel; the results are bit-identical
+ * for every choice because the colloid forces are exact fixed-point sums.
+ * md_cluster: CTAs per replica (one thread-block cluster): 1, 2, 4, 8, or 16
+ *   for the few-colloid kernel where the device schedules 16-CTA clusters;
+ *   0 (the default) times each candidate size three times on the first
+ *   intervals of rmpcd_step (one synchronisation) and keeps the fastest.
+ * md_kernel: 1 = general kernel; 2 = few-colloid kernel (every replica with at
+ *   most 2 colloids and no colloid-colloid potential: each warp integrates
+ *   the colloids itself, one barrier per sub-step); 0 (default) = 2 when
+ *   allowed, else 1.
+ * rmpcd_get_tuning reports the cluster size in use (0 while tuning) and the
+ * kernel.  Errors: EINVAL. */
+rmpcd_status rmpcd_set_tuning(rmpcd_system *sys, int32_t md_cluster, int32_t md_kernel);
+rmpcd_status rmpcd_get_tuning(const rmpcd_system *sys, int32_t *md_cluster, int32_t *md_kernel);
 
 /* Count of this library's kernel launches since creation (for accounting). */
 rmpcd_status rmpcd_launch_count(const rmpcd_system *sys, int64_t *count);

@@ -63,7 +63,7 @@ EXPORTS = [
     "rmpcd_create", "rmpcd_destroy", "rmpcd_set_state", "rmpcd_get_state", "rmpcd_set_colloids",
     "rmpcd_get_colloids", "rmpcd_set_step", "rmpcd_get_step", "rmpcd_stream", "rmpcd_shift_and_sort",
     "rmpcd_collide", "rmpcd_react", "rmpcd_step", "rmpcd_observables", "rmpcd_sync", "rmpcd_launch_count",
-    "rmpcd_last_error", "rmpcd_enable_timers", "rmpcd_read_timers",
+    "rmpcd_last_error", "rmpcd_enable_timers", "rmpcd_read_timers", "rmpcd_set_tuning", "rmpcd_get_tuning",
 ]
 
 _LIB = None
@@ -100,6 +100,8 @@ def load():
     L.rmpcd_launch_count.argtypes = [vp, P(i64)]
     L.rmpcd_enable_timers.argtypes = [vp, i32]
     L.rmpcd_read_timers.argtypes = [vp, P(Timers), i32]
+    L.rmpcd_set_tuning.argtypes = [vp, i32, i32]
+    L.rmpcd_get_tuning.argtypes = [vp, P(i32), P(i32)]
     L.rmpcd_last_error.argtypes = [vp]
     L.rmpcd_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -319,6 +321,15 @@ class System:
         t = Timers()
         self._check(self._lib.rmpcd_read_timers(self._h, C.byref(t), 1 if reset else 0))
         return {name: {"launches": int(t.launches[k]), "ms": float(t.ms[k])} for k, name in enumerate(PHASES)}
+
+    def set_tuning(self, md_cluster=0, md_kernel=0):
+        self._check(self._lib.rmpcd_set_tuning(self._h, int(md_cluster), int(md_kernel)))
+
+    def get_tuning(self):
+        """(md_cluster, md_kernel) in use; md_cluster is 0 while tuning."""
+        c, k = C.c_int32(), C.c_int32()
+        self._check(self._lib.rmpcd_get_tuning(self._h, C.byref(c), C.byref(k)))
+        return int(c.value), int(k.value)
 
     def launch_count(self) -> int:
         c = C.c_int64()

@@ -53,6 +53,17 @@ struct rmpcd_system {
     std::vector<Pending> pending;
     long long t_launches[4] = {0, 0, 0, 0};
     double t_ms[4] = {0, 0, 0, 0};
+    // MD kernel: 1 = general, 2 = few-colloid (when every replica allows it)
+    int md_kernel = 1;
+    bool fast_ok = false;
+    int md_kernel_req = 0;
+    // MD cluster size: fixed (1, 2, 4, 8) or tuned on the first intervals
+    int md_fixed = 0;
+    bool md_tuned = false;
+    int md_best = 4;
+    int md_fast_max = 8;              // largest cluster the device runs for the few-colloid kernel
+    std::vector<int> md_cand;         // cluster sizes the tuner tries
+    std::vector<Pending> md_trials;   // phase field holds the cluster size
 };
 
 static cudaEvent_t pool_event(rmpcd_system *sys)
@@ -85,6 +96,23 @@ static void tstop(rmpcd_system *sys, int phase, cudaEvent_t a)
 }
 
 static std::string g_create_error;
+
+// MD kernel choice (0 = the few-colloid kernel when allowed) and the cluster
+// sizes the tuner tries for it.
+static void set_md_kernel(rmpcd_system *sys, int req)
+{
+    sys->md_kernel_req = req;
+    sys->md_kernel = req ? req : (sys->fast_ok ? 2 : 1);
+    sys->md_cand.clear();
+    if (sys->md_kernel == 2) {
+        sys->md_cand = {2, 4, 8};
+        if (sys->md_fast_max >= 16) sys->md_cand.push_back(16);
+        sys->md_best = 8;
+    } else {
+        sys->md_cand = {1, 2, 4, 8};
+        sys->md_best = 4;
+    }
+}
 
 // Mixed-path colloid representation: unwrapped integer cell, FP32 offset in
 // [0,1), wrapped integer cell, FP32 velocity.
@@ -239,6 +267,7 @@ void rmpcd_destroy(rmpcd_system *sys)
     cudaStreamSynchronize(sys->stream);
     for (void *p : sys->allocs) cudaFree(p);
     for (auto &q : sys->pending) { sys->ev_pool.push_back(q.a); sys->ev_pool.push_back(q.b); }
+    for (auto &q : sys->md_trials) { sys->ev_pool.push_back(q.a); sys->ev_pool.push_back(q.b); }
     for (cudaEvent_t e : sys->ev_pool) cudaEventDestroy(e);
     delete sys;
 }
@@ -300,6 +329,9 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
         sys->max_part = std::max(sys->max_part, rp.n_part);
         if (rp.n_col > 0) sys->any_colloids = 1;
     }
+    sys->fast_ok = true;
+    for (int r = 0; r < n_replicas; ++r)
+        if (params[r].n_colloids > MD_FAST_NC || params[r].cc_rc > 0.0) sys->fast_ok = false;
     // bulk reaction thresholds: accept iff draw < (1 - exp(-k N_B tau)) 2^32
     std::vector<double> thr((size_t)n_replicas * (bucket_cap + 1));
     for (int r = 0; r < n_replicas; ++r)
@@ -443,6 +475,8 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
     d.n_rep = n_replicas;
     d.n_tiles = (int)n_tiles;
     d.n_total = (int)n_total;
+    if (sys->fast_ok && sys->any_colloids) sys->md_fast_max = md_fast_max_cluster(sys->mixed);
+    set_md_kernel(sys, 0);
     *out = sys;
     return RMPCD_OK;
 }
@@ -662,7 +696,9 @@ rmpcd_status rmpcd_stream(rmpcd_system *sys)
     launch_particles(sys->mixed, sys->d, PM_STREAM, sys->step, sys->cur, 0, sys->stream);
     if ((st = after_launch(sys, sys->n_total > 0 ? 1 : 0)) != RMPCD_OK) return st;
     if (sys->any_colloids) {
-        launch_md(sys->mixed, sys->d, sys->step, sys->cur, 0, 0, sys->stream);
+        const int cs = sys->md_fixed ? sys->md_fixed : sys->md_best;
+        if (sys->md_kernel == 2) launch_md_fast(sys->mixed, sys->d, sys->step, sys->cur, 0, 0, cs, sys->stream);
+        else launch_md(sys->mixed, sys->d, sys->step, sys->cur, 0, 0, cs, sys->stream);
         if ((st = after_launch(sys, 1)) != RMPCD_OK) return st;
     }
     sys->has_sort = false;
@@ -697,6 +733,46 @@ static rmpcd_status sorted_op(rmpcd_system *sys, int opts, const char *name)
 rmpcd_status rmpcd_collide(rmpcd_system *sys) { return sorted_op(sys, CP_COLLIDE, "rmpcd_collide"); }
 rmpcd_status rmpcd_react(rmpcd_system *sys) { return sorted_op(sys, CP_REACT, "rmpcd_react"); }
 
+// Cluster size of the next MD launch; while tuning, each size in turn with a
+// CUDA event pair around the launch.
+static int md_cluster_for_launch(rmpcd_system *sys, cudaEvent_t *a)
+{
+    *a = nullptr;
+    if (sys->md_fixed) return sys->md_fixed;
+    if (sys->md_tuned) return sys->md_best;
+    const int cs = sys->md_cand[sys->md_trials.size() % sys->md_cand.size()];
+    *a = pool_event(sys);
+    cudaEventRecord(*a, sys->stream);
+    return cs;
+}
+
+static void md_trial_done(rmpcd_system *sys, int cs, cudaEvent_t a)
+{
+    if (!a) return;
+    cudaEvent_t b = pool_event(sys);
+    cudaEventRecord(b, sys->stream);
+    sys->md_trials.push_back({cs, a, b});
+    if (sys->md_trials.size() < 3 * sys->md_cand.size()) return;
+    // three launches of each size: keep the size with the smallest median
+    cudaEventSynchronize(b);
+    double best_t = 1e30;
+    for (int c : sys->md_cand) {
+        std::vector<float> t;
+        for (auto &q : sys->md_trials)
+            if (q.phase == c) {
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, q.a, q.b);
+                t.push_back(ms);
+            }
+        std::sort(t.begin(), t.end());
+        const double med = t.empty() ? 1e30 : t[t.size() / 2];
+        if (med < best_t) { best_t = med; sys->md_best = c; }
+    }
+    for (auto &q : sys->md_trials) { sys->ev_pool.push_back(q.a); sys->ev_pool.push_back(q.b); }
+    sys->md_trials.clear();
+    sys->md_tuned = true;
+}
+
 rmpcd_status rmpcd_step(rmpcd_system *sys, int32_t n_intervals)
 {
     if (!sys) return RMPCD_EINVAL;
@@ -715,14 +791,17 @@ rmpcd_status rmpcd_step(rmpcd_system *sys, int32_t n_intervals)
     }
     for (int i = 0; i < n_intervals; ++i) {
         if (sys->any_colloids) {
+            cudaEvent_t tev;
+            const int cs = md_cluster_for_launch(sys, &tev);
             tstart(sys, &ev);
-            launch_md(sys->mixed, sys->d, sys->step, sys->cur, sys->bcur, 1, sys->stream);
+            if (sys->md_kernel == 2) launch_md_fast(sys->mixed, sys->d, sys->step, sys->cur, sys->bcur, 1, cs, sys->stream);
+            else launch_md(sys->mixed, sys->d, sys->step, sys->cur, sys->bcur, 1, cs, sys->stream);
             tstop(sys, 1, ev);
+            md_trial_done(sys, cs, tev);
             if ((st = after_launch(sys, 1)) != RMPCD_OK) return st;
         }
-        const bool last = i == n_intervals - 1;
-        CellPassArgs a{CP_FLIGHT | CP_COLLIDE | CP_REACT | CP_NEXT | CP_WRITE | (last ? CP_OBS : 0), sys->step, sys->bcur,
-                       sys->bcur ^ 1, sys->cur, sys->cur ^ 1, next_epoch(sys)};
+        CellPassArgs a{CP_FLIGHT | CP_COLLIDE | CP_REACT | CP_NEXT | CP_WRITE, sys->step, sys->bcur, sys->bcur ^ 1,
+                       sys->cur, sys->cur ^ 1, next_epoch(sys)};
         tstart(sys, &ev);
         launch_cellpass(sys->mixed, sys->d, a, sys->stream);
         tstop(sys, 2, ev);
@@ -732,12 +811,8 @@ rmpcd_status rmpcd_step(rmpcd_system *sys, int32_t n_intervals)
         sys->sort_step = sys->step;
         sys->step += 1u;
     }
-    tstart(sys, &ev);
-    launch_obs_reduce(sys->d, sys->stream);
-    tstop(sys, 3, ev);
-    if ((st = after_launch(sys, 1)) != RMPCD_OK) return st;
     sys->has_sort = true;
-    sys->obs_valid = true;
+    sys->obs_valid = false;   // observables are computed on request
     return RMPCD_OK;
 }
 
@@ -802,6 +877,36 @@ rmpcd_status rmpcd_read_timers(rmpcd_system *sys, rmpcd_timers *out, int32_t res
         out->ms[k] = sys->t_ms[k];
         if (reset) { sys->t_launches[k] = 0; sys->t_ms[k] = 0.0; }
     }
+    return RMPCD_OK;
+}
+
+rmpcd_status rmpcd_set_tuning(rmpcd_system *sys, int32_t md_cluster, int32_t md_kernel)
+{
+    if (!sys) return RMPCD_EINVAL;
+    if (md_kernel < 0 || md_kernel > 2) return fail(sys, RMPCD_EINVAL, "md_kernel must be 0, 1 or 2");
+    if (md_kernel == 2 && !sys->fast_ok)
+        return fail(sys, RMPCD_EINVAL, "the few-colloid MD kernel needs <= %d colloids and no colloid-colloid potential",
+                    MD_FAST_NC);
+    const int kern = md_kernel ? md_kernel : (sys->fast_ok ? 2 : 1);
+    const int maxc = kern == 2 ? sys->md_fast_max : 8;
+    if (md_cluster != 0 && md_cluster != 1 && md_cluster != 2 && md_cluster != 4 && md_cluster != 8 &&
+        !(md_cluster == 16 && maxc >= 16))
+        return fail(sys, RMPCD_EINVAL, "md_cluster must be 0 (tune), 1, 2, 4, 8%s", maxc >= 16 ? " or 16" : "");
+    set_md_kernel(sys, md_kernel);
+    sys->md_fixed = md_cluster;
+    if (md_cluster == 0) {
+        sys->md_tuned = false;
+        for (auto &q : sys->md_trials) { sys->ev_pool.push_back(q.a); sys->ev_pool.push_back(q.b); }
+        sys->md_trials.clear();
+    }
+    return RMPCD_OK;
+}
+
+rmpcd_status rmpcd_get_tuning(const rmpcd_system *sys, int32_t *md_cluster, int32_t *md_kernel)
+{
+    if (!sys || !md_cluster) return RMPCD_EINVAL;
+    *md_cluster = sys->md_fixed ? sys->md_fixed : (sys->md_tuned ? sys->md_best : 0);
+    if (md_kernel) *md_kernel = sys->md_kernel;
     return RMPCD_OK;
 }
 

@@ -39,13 +39,13 @@ __device__ __forceinline__ void rec_flight(const ReplicaDev &rp, RecM &r)
 }
 __device__ __forceinline__ void rec_flight(const ReplicaDev &rp, RecD &r) { flight_d(rp, r.x, r.v); }
 
-__device__ __forceinline__ int rec_key(const ReplicaDev &rp, const RecM &r, const double s[3])
+// s: the shift in FP64; sf: the same shift in FP32 (exact: 24-bit uniforms)
+__device__ __forceinline__ int rec_key(const ReplicaDev &rp, const RecM &r, const double *, const float *sf)
 {
     int c[3] = {cw_get(r.cw, 0), cw_get(r.cw, 1), cw_get(r.cw, 2)};
-    float sf[3] = {(float)s[0], (float)s[1], (float)s[2]};   // exact: 24-bit uniforms
     return cell_key_m(rp, c, r.o, sf);
 }
-__device__ __forceinline__ int rec_key(const ReplicaDev &rp, const RecD &r, const double s[3])
+__device__ __forceinline__ int rec_key(const ReplicaDev &rp, const RecD &r, const double *s, const float *)
 {
     return cell_key_d(rp, r.x, s);
 }
@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(CP_THREADS) k_cellpass(Dev d, CellPassArgs a)
     __shared__ int s_tile, s_r, s_ce, s_base;
     __shared__ int s_cnt[CPT], s_ls[CPT + 1], s_wt[2];
     __shared__ double s_sh[3], s_shn[3];
+    __shared__ float s_shnf[3];
     __shared__ R s_vcm[CPT][3], s_ax[CPT][3];
     __shared__ int s_mode[CPT], s_react[CPT];
     __shared__ double s_red[CP_THREADS / 32][8];
@@ -153,6 +154,7 @@ __global__ void __launch_bounds__(CP_THREADS) k_cellpass(Dev d, CellPassArgs a)
         s_sh[0] = s[0]; s_sh[1] = s[1]; s_sh[2] = s[2];
         grid_shift(rp.seed, a.step + 1u, s);
         s_shn[0] = s[0]; s_shn[1] = s[1]; s_shn[2] = s[2];
+        s_shnf[0] = (float)s[0]; s_shnf[1] = (float)s[1]; s_shnf[2] = (float)s[2];
     }
     __syncthreads();
     if (tid >= 32 && tid < CPT) s_ls[tid + 1] += s_wt[0];
@@ -369,7 +371,7 @@ __global__ void __launch_bounds__(CP_THREADS) k_cellpass(Dev d, CellPassArgs a)
                 } else {
                     Rec fl = rec;
                     rec_flight(rp, fl);
-                    const int key = rec_key(rp, fl, s_shn);
+                    const int key = rec_key(rp, fl, s_shn, s_shnf);
                     bin_particle(d, a.nxt, rp.cell_off + key, gslot);
                 }
             }

@@ -24,10 +24,14 @@ namespace cg = cooperative_groups;
 
 namespace rmpcd {
 
-constexpr int MDT = 512;        // threads per MD CTA
-constexpr int MD_CS = 8;        // CTAs per replica (cluster size)
 constexpr int NCR = 4;          // colloids whose force partials live in registers
-constexpr int MD_WARPS = MDT / 32;
+constexpr int MD_MAXW = 32;     // most warps of one MD CTA
+
+// Threads per CTA of an MD cluster of CS CTAs: a lone CTA takes 1024.
+template <int CS> struct MDGeom {
+    static constexpr int NT = CS == 1 ? 1024 : 512;
+    static constexpr int NW = NT / 32;
+};
 
 struct __align__(16) WorkM {
     int c[3];
@@ -67,9 +71,9 @@ struct MDShared {
     int cat[MAXC];
     BondDev bond[MAXB];
     unsigned long long Fq[MAXC * 3];                 // this CTA's partial (atomic path)
-    unsigned long long wpart[MD_WARPS][NCR * 3];     // per-warp partials (register path)
-    unsigned long long part[2][MD_CS][MAXC * 3];     // partials of every CTA of the cluster
-    long long Fsum[MAXC * 3];                        // cluster total (thread 0)
+    unsigned long long wpart[MD_MAXW][NCR * 3];      // per-warp partials (register path)
+    unsigned long long part[2][8][MAXC * 3];         // partials of every CTA of the cluster
+    long long Fsum[MAXC * 3];                        // cluster total
     int nc, nbond, nn;
 };
 
@@ -300,14 +304,13 @@ __device__ void col_frames(const ReplicaDev &rp, MDShared<false> &S)
     for (int j = 0; j < S.nc; ++j) wrapped_colloid(rp, S.C.X[j], S.C.Xw[j]);
 }
 
+template <int CS>
 __device__ void col_gather(const ReplicaDev &rp, MDShared<false> &S, int par)
 {
     long long *Fq = S.Fsum;
-    for (int i = 0; i < 3 * S.nc; ++i) {
-        long long acc = 0;
-        for (int q = 0; q < MD_CS; ++q) acc += (long long)S.part[par][q][i];
-        Fq[i] = acc;
-    }
+    for (int i = 0; i < 3 * S.nc; ++i) Fq[i] = (long long)S.part[par][0][i];
+    for (int q = 1; q < CS; ++q)
+        for (int i = 0; i < 3 * S.nc; ++i) Fq[i] += (long long)S.part[par][q][i];
     colloid_colloid(rp, S, Fq);
     for (int j = 0; j < S.nc; ++j)
         for (int k = 0; k < 3; ++k) S.C.F[j][k] = (double)Fq[3 * j + k] * 0x1p-40;
@@ -350,24 +353,89 @@ __device__ void col_store(const Dev &d, const ReplicaDev &rp, MDShared<false> &S
 }
 
 // ===========================================================================
-// Mixed colloid integrator: integer cell + FP32 offset, FP32 arithmetic
+// Mixed colloid integrator: integer cell + FP32 offset, FP32 arithmetic, run
+// by warp 0 with one lane per colloid component (lane l: colloid l / 3, axis
+// l % 3) and three lanes per bond for RATTLE.
 // ===========================================================================
-__device__ __forceinline__ void col_renorm(int Xi[3], float Xf[3])
+__device__ __forceinline__ void col_carry(const ReplicaDev &rp, ColM &C, int j, int t)
 {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float fl = floorf(Xf[k]);
-        Xi[k] += (int)fl;
-        Xf[k] = Xf[k] - fl;
-        if (Xf[k] >= 1.0f) { Xf[k] = 0.0f; Xi[k] += 1; }
+    const float fl = floorf(C.Xf[j][t]);
+    int c = (int)fl;
+    float f = C.Xf[j][t] - fl;
+    if (f >= 1.0f) { f = 0.0f; c += 1; }
+    C.Xf[j][t] = f;
+    C.Xi[j][t] += c;
+    int ci = C.Ci[j][t] + c;
+    const int L = rp.L[t];
+    if (ci >= L || ci < 0) ci = imod(ci, L);
+    C.Ci[j][t] = ci;
+}
+
+// Sum over lanes 0..2 of warp 0, in lane order (all lanes get the result).
+__device__ __forceinline__ float sum3(float a)
+{
+    return (__shfl_sync(0xffffffffu, a, 0) + __shfl_sync(0xffffffffu, a, 1)) + __shfl_sync(0xffffffffu, a, 2);
+}
+
+__device__ __forceinline__ float col_sep1(const ColM &C, int a, int b, int t)
+{
+    return (float)(C.Xi[a][t] - C.Xi[b][t]) + (C.Xf[a][t] - C.Xf[b][t]);
+}
+
+// RATTLE position stage for every bond (warp 0; lanes 0..2 = axes).
+__device__ void rattle_pos_w(const ReplicaDev &rp, MDShared<true> &S, int lane)
+{
+    ColM &C = S.C;
+    const float idt = 1.0f / rp.dt_f;
+    for (int k = 0; k < S.nbond; ++k) {
+        const int a = S.bond[k].a, b = S.bond[k].b;
+        const float dd = (float)S.bond[k].d;
+        const int t = lane < 3 ? lane : 0;
+        const float ro = (float)(C.Xoi[a][t] - C.Xoi[b][t]) + (C.Xof[a][t] - C.Xof[b][t]);
+        const float rn = col_sep1(C, a, b, t);
+        const float inv = C.invM[a] + C.invM[b];
+        const float oo = sum3(ro * ro), on = sum3(rn * ro), nn = sum3(rn * rn);
+        const float qa = inv * inv * oo;
+        const float qb = 2.0f * inv * on;
+        const float qc = nn - dd * dd;
+        float disc = qb * qb - 4.0f * qa * qc;
+        if (disc < 0.0f) disc = 0.0f;
+        const float q = -0.5f * (qb + copysignf(sqrtf(disc), qb));
+        const float gmul = qc / q;
+        __syncwarp();
+        if (lane < 3) {
+            const float ca = gmul * ro * C.invM[a];
+            const float cb = gmul * ro * C.invM[b];
+            C.Xf[a][t] += ca;
+            C.Xf[b][t] -= cb;
+            C.V[a][t] += ca * idt;
+            C.V[b][t] -= cb * idt;
+            col_carry(rp, C, a, t);
+            col_carry(rp, C, b, t);
+        }
+        __syncwarp();
     }
 }
 
-__device__ __forceinline__ void col_sep(const int ai[3], const float af[3], const int bi[3], const float bf[3],
-                                        float r[3])
+// RATTLE velocity stage (warp 0).
+__device__ void rattle_vel_w(MDShared<true> &S, int lane)
 {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) r[k] = (float)(ai[k] - bi[k]) + (af[k] - bf[k]);
+    ColM &C = S.C;
+    for (int k = 0; k < S.nbond; ++k) {
+        const int a = S.bond[k].a, b = S.bond[k].b;
+        const int t = lane < 3 ? lane : 0;
+        const float r = col_sep1(C, a, b, t);
+        const float dv = C.V[a][t] - C.V[b][t];
+        const float inv = C.invM[a] + C.invM[b];
+        const float rr = sum3(r * r), rv = sum3(dv * r);
+        const float kk = rv / (rr * inv);
+        __syncwarp();
+        if (lane < 3) {
+            C.V[a][t] -= kk * r * C.invM[a];
+            C.V[b][t] += kk * r * C.invM[b];
+        }
+        __syncwarp();
+    }
 }
 
 __device__ void colloid_colloid(const ReplicaDev &rp, MDShared<true> &S, long long *Fq)
@@ -378,7 +446,7 @@ __device__ void colloid_colloid(const ReplicaDev &rp, MDShared<true> &S, long lo
         for (int b = a + 1; b < S.nc; ++b) {
             if (bonded(S.bond, S.nbond, a, b)) continue;
             float d[3];
-            col_sep(S.C.Ci[a], S.C.Xf[a], S.C.Ci[b], S.C.Xf[b], d);
+            for (int t = 0; t < 3; ++t) d[t] = (float)(S.C.Ci[a][t] - S.C.Ci[b][t]) + (S.C.Xf[a][t] - S.C.Xf[b][t]);
             min_image(rp, d);
             const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
             if (!(r2 < rc * rc)) continue;
@@ -394,65 +462,13 @@ __device__ void colloid_colloid(const ReplicaDev &rp, MDShared<true> &S, long lo
         }
 }
 
-__device__ void rattle_pos(MDShared<true> &S, float dt)
-{
-    ColM &C = S.C;
-    for (int k = 0; k < S.nbond; ++k) {
-        const int a = S.bond[k].a, b = S.bond[k].b;
-        const float dd = (float)S.bond[k].d;
-        float ro[3], rn[3];
-        col_sep(C.Xoi[a], C.Xof[a], C.Xoi[b], C.Xof[b], ro);
-        col_sep(C.Xi[a], C.Xf[a], C.Xi[b], C.Xf[b], rn);
-        const float inv = C.invM[a] + C.invM[b];
-        const float oo = ro[0] * ro[0] + ro[1] * ro[1] + ro[2] * ro[2];
-        const float on = rn[0] * ro[0] + rn[1] * ro[1] + rn[2] * ro[2];
-        const float nn = rn[0] * rn[0] + rn[1] * rn[1] + rn[2] * rn[2];
-        const float qa = inv * inv * oo;
-        const float qb = 2.0f * inv * on;
-        const float qc = nn - dd * dd;
-        float disc = qb * qb - 4.0f * qa * qc;
-        if (disc < 0.0f) disc = 0.0f;
-        const float q = -0.5f * (qb + copysignf(sqrtf(disc), qb));
-        const float gmul = qc / q;
-        const float idt = 1.0f / dt;
-        for (int t = 0; t < 3; ++t) {
-            const float ca = gmul * ro[t] * C.invM[a];
-            const float cb = gmul * ro[t] * C.invM[b];
-            C.Xf[a][t] += ca;
-            C.Xf[b][t] -= cb;
-            C.V[a][t] += ca * idt;
-            C.V[b][t] -= cb * idt;
-        }
-        col_renorm(C.Xi[a], C.Xf[a]);
-        col_renorm(C.Xi[b], C.Xf[b]);
-    }
-}
-
-__device__ void rattle_vel(MDShared<true> &S)
-{
-    ColM &C = S.C;
-    for (int k = 0; k < S.nbond; ++k) {
-        const int a = S.bond[k].a, b = S.bond[k].b;
-        float r[3], dv[3];
-        col_sep(C.Xi[a], C.Xf[a], C.Xi[b], C.Xf[b], r);
-        for (int t = 0; t < 3; ++t) dv[t] = C.V[a][t] - C.V[b][t];
-        const float inv = C.invM[a] + C.invM[b];
-        const float rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-        const float rv = dv[0] * r[0] + dv[1] * r[1] + dv[2] * r[2];
-        const float kk = rv / (rr * inv);
-        for (int t = 0; t < 3; ++t) {
-            C.V[a][t] -= kk * r[t] * C.invM[a];
-            C.V[b][t] += kk * r[t] * C.invM[b];
-        }
-    }
-}
-
 __device__ void col_load(const Dev &d, const ReplicaDev &rp, MDShared<true> &S, int j)
 {
     const int g = rp.col_off + j;
     for (int k = 0; k < 3; ++k) {
         S.C.Xi[j][k] = d.colXi[3 * g + k];
         S.C.Xf[j][k] = d.colXf[3 * g + k];
+        S.C.Ci[j][k] = d.colCi[3 * g + k];
         S.C.V[j][k] = d.colVf[3 * g + k];
         S.C.X0i[j][k] = S.C.Xi[j][k];
         S.C.X0f[j][k] = S.C.Xf[j][k];
@@ -460,45 +476,55 @@ __device__ void col_load(const Dev &d, const ReplicaDev &rp, MDShared<true> &S, 
     S.C.invM[j] = d.colInvM_f[g];
 }
 
-__device__ void col_frames(const ReplicaDev &rp, MDShared<true> &S)
+// Warp 0: sum the force partials (per warp of a lone CTA when FROM_WARPS,
+// else per CTA of the cluster), add colloid-colloid forces, convert to FP32.
+template <int CS, bool FROM_WARPS>
+__device__ void col_gather_w(const ReplicaDev &rp, MDShared<true> &S, int par, int lane)
 {
-    for (int j = 0; j < S.nc; ++j)
-        for (int k = 0; k < 3; ++k) S.C.Ci[j][k] = imod(S.C.Xi[j][k], rp.L[k]);
-}
-
-__device__ void col_gather(const ReplicaDev &rp, MDShared<true> &S, int par)
-{
-    long long *Fq = S.Fsum;
-    for (int i = 0; i < 3 * S.nc; ++i) {
-        long long acc = 0;
-        for (int q = 0; q < MD_CS; ++q) acc += (long long)S.part[par][q][i];
-        Fq[i] = acc;
-    }
-    colloid_colloid(rp, S, Fq);
-    for (int j = 0; j < S.nc; ++j)
-        for (int k = 0; k < 3; ++k) S.C.F[j][k] = __ll2float_rn(Fq[3 * j + k]) * 0x1p-40f;
-}
-
-__device__ void col_kick_drift(const ReplicaDev &rp, MDShared<true> &S)
-{
-    const float dt = rp.dt_f, hdt = rp.hdt_f;
-    for (int j = 0; j < S.nc; ++j) {
-        for (int t = 0; t < 3; ++t) {
-            S.C.V[j][t] = fmaf(hdt, S.C.F[j][t] * S.C.invM[j], S.C.V[j][t]);
-            S.C.Xoi[j][t] = S.C.Xi[j][t];
-            S.C.Xof[j][t] = S.C.Xf[j][t];
-            S.C.Xf[j][t] = fmaf(dt, S.C.V[j][t], S.C.Xf[j][t]);
+    constexpr int NW = MDGeom<CS>::NW;
+    for (int l = lane; l < 3 * S.nc; l += 32) {
+        long long x = 0;
+        if (FROM_WARPS) {
+            for (int w = 0; w < NW; ++w) x += (long long)S.wpart[w][l];
+        } else {
+            for (int q = 0; q < CS; ++q) x += (long long)S.part[par][q][l];
         }
-        col_renorm(S.C.Xi[j], S.C.Xf[j]);
+        S.Fsum[l] = x;
     }
-    rattle_pos(S, dt);
+    __syncwarp();
+    if (rp.cc_rc > 0.0) {
+        if (lane == 0) colloid_colloid(rp, S, S.Fsum);
+        __syncwarp();
+    }
+    for (int l = lane; l < 3 * S.nc; l += 32) S.C.F[l / 3][l % 3] = __ll2float_rn(S.Fsum[l]) * 0x1p-40f;
+    __syncwarp();
 }
 
-__device__ void col_kick(const ReplicaDev &rp, MDShared<true> &S)
+// Warp 0: first half kick, drift, carry, RATTLE position stage.
+__device__ void col_kick_drift_w(const ReplicaDev &rp, MDShared<true> &S, int lane)
 {
-    for (int j = 0; j < S.nc; ++j)
-        for (int t = 0; t < 3; ++t) S.C.V[j][t] = fmaf(rp.hdt_f, S.C.F[j][t] * S.C.invM[j], S.C.V[j][t]);
-    rattle_vel(S);
+    for (int l = lane; l < 3 * S.nc; l += 32) {
+        const int j = l / 3, t = l % 3;
+        ColM &C = S.C;
+        C.V[j][t] = fmaf(rp.hdt_f, C.F[j][t] * C.invM[j], C.V[j][t]);
+        C.Xoi[j][t] = C.Xi[j][t];
+        C.Xof[j][t] = C.Xf[j][t];
+        C.Xf[j][t] = fmaf(rp.dt_f, C.V[j][t], C.Xf[j][t]);
+        col_carry(rp, C, j, t);
+    }
+    __syncwarp();
+    rattle_pos_w(rp, S, lane);
+}
+
+// Warp 0: second half kick, RATTLE velocity stage.
+__device__ void col_kick_w(const ReplicaDev &rp, MDShared<true> &S, int lane)
+{
+    for (int l = lane; l < 3 * S.nc; l += 32) {
+        const int j = l / 3, t = l % 3;
+        S.C.V[j][t] = fmaf(rp.hdt_f, S.C.F[j][t] * S.C.invM[j], S.C.V[j][t]);
+    }
+    __syncwarp();
+    rattle_vel_w(S, lane);
 }
 
 __device__ void col_store(const Dev &d, const ReplicaDev &rp, MDShared<true> &S)
@@ -508,7 +534,7 @@ __device__ void col_store(const Dev &d, const ReplicaDev &rp, MDShared<true> &S)
     for (int j = 0; j < S.nc; ++j) {
         const int g = rp.col_off + j;
         float e[3];
-        col_sep(S.C.Xi[j], S.C.Xf[j], S.C.X0i[j], S.C.X0f[j], e);
+        for (int t = 0; t < 3; ++t) e[t] = (float)(S.C.Xi[j][t] - S.C.X0i[j][t]) + (S.C.Xf[j][t] - S.C.X0f[j][t]);
         const float dd = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
         for (int t = 0; t < 3; ++t) {
             d.colXi[3 * g + t] = S.C.Xi[j][t];
@@ -522,19 +548,18 @@ __device__ void col_store(const Dev &d, const ReplicaDev &rp, MDShared<true> &S)
 }
 
 // ===========================================================================
-// Cluster-wide reduction of the colloid forces
+// Reduction of the colloid forces over the CTA and the cluster
 // ===========================================================================
-// Reduce this CTA's fixed-point partials and publish them to every CTA of
-// the cluster (slot = this CTA's rank, buffer = sub-step parity).
+// Each warp reduces its lanes' fixed-point partials (exact integer sums).
 template <bool MIXED, bool REG>
-__device__ __forceinline__ void publish_partials(cg::cluster_group &cl, MDShared<MIXED> &S, long long acc[NCR][3],
-                                                 int par)
+__device__ __forceinline__ void warp_partials(MDShared<MIXED> &S, long long acc[NCR][3])
 {
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int rank = (int)cl.block_rank();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (REG) {
+        const int nc = S.nc;
 #pragma unroll
-        for (int j = 0; j < NCR; ++j)
+        for (int j = 0; j < NCR; ++j) {
+            if (j >= nc) break;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 long long x = acc[j][k];
@@ -542,46 +567,79 @@ __device__ __forceinline__ void publish_partials(cg::cluster_group &cl, MDShared
                 for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
                 if (lane == 0) S.wpart[wid][3 * j + k] = (unsigned long long)x;
             }
-        __syncthreads();
-        if (tid < 3 * S.nc) {
-            long long x = 0;
-            for (int w = 0; w < MD_WARPS; ++w) x += (long long)S.wpart[w][tid];
-            for (int q = 0; q < MD_CS; ++q) *cl.map_shared_rank(&S.part[par][rank][tid], q) = (unsigned long long)x;
-        }
-    } else {
-        __syncthreads();
-        for (int i = tid; i < 3 * S.nc; i += MDT) {
-            const unsigned long long x = S.Fq[i];
-            for (int q = 0; q < MD_CS; ++q) *cl.map_shared_rank(&S.part[par][rank][i], q) = x;
         }
     }
 }
 
-template <bool MIXED, bool REG>
+// After the CTA barrier: this CTA's total goes to slot `rank` of every CTA of
+// the cluster (buffer = sub-step parity).
+template <bool MIXED, bool REG, int CS>
+__device__ __forceinline__ void publish_cluster(cg::cluster_group &cl, MDShared<MIXED> &S, int par)
+{
+    constexpr int NT = MDGeom<CS>::NT, NW = MDGeom<CS>::NW;
+    const int tid = threadIdx.x;
+    const int rank = (int)cl.block_rank();
+    for (int i = tid; i < 3 * S.nc; i += NT) {
+        long long x = 0;
+        if (REG) {
+            for (int w = 0; w < NW; ++w) x += (long long)S.wpart[w][i];
+        } else {
+            x = (long long)S.Fq[i];
+        }
+        for (int q = 0; q < CS; ++q) *cl.map_shared_rank(&S.part[par][rank][i], q) = (unsigned long long)x;
+    }
+}
+
+template <bool MIXED, bool REG, int CS>
 __device__ void md_body(const Dev &d, MDShared<MIXED> &S, const ReplicaDev &rp, cg::cluster_group &cl,
                         uint32_t step, int rbuf, int bbuf, int do_bin, int r)
 {
     using W = typename std::conditional<MIXED, WorkM, WorkD>::type;
-    const int tid = threadIdx.x;
-    const int rank = (int)cl.block_rank();
+    constexpr int NT = MDGeom<CS>::NT;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int rank = CS == 1 ? 0 : (int)cl.block_rank();
     const int nn = S.nn;
     const int *list = d.near_list + rp.part_off;
     W *work = reinterpret_cast<W *>(d.md_work) + rp.part_off;
-    const int first = rank * MDT + tid;
-    const int stride = MD_CS * MDT;
+    const int first = rank * NT + tid;
+    const int stride = CS * NT;
     long long acc[NCR][3];
     auto zero_acc = [&]() {
 #pragma unroll
         for (int j = 0; j < NCR; ++j)
 #pragma unroll
             for (int k = 0; k < 3; ++k) acc[j][k] = 0;
+    };
+    // fixed-point sums of this CTA (and the cluster), then warp 0 / thread 0
+    // turns them into colloid forces
+    auto reduce_forces = [&](int par) {
+        warp_partials<MIXED, REG>(S, acc);
+        __syncthreads();
+        if (CS == 1 && REG) {
+            // a lone CTA sums the per-warp partials directly
+            if (!MIXED && tid < 3 * S.nc) {
+                long long x = 0;
+                for (int w = 0; w < MDGeom<CS>::NW; ++w) x += (long long)S.wpart[w][tid];
+                S.part[par][0][tid] = (unsigned long long)x;
+            }
+            if (!MIXED) __syncthreads();
+        } else if (CS == 1) {
+            if (tid < 3 * S.nc) S.part[par][0][tid] = S.Fq[tid];
+            __syncthreads();
+        } else {
+            publish_cluster<MIXED, REG, CS>(cl, S, par);
+            cl.sync();
+        }
+    };
+    auto zero_fq = [&]() {
         if (!REG)
-            for (int i = tid; i < 3 * S.nc; i += MDT) S.Fq[i] = 0ull;
+            for (int i = tid; i < 3 * S.nc; i += NT) S.Fq[i] = 0ull;
     };
 
     // forces at the start of the interval
     zero_acc();
-    if (!REG) __syncthreads();
+    zero_fq();
+    __syncthreads();
     for (int k = first; k < nn; k += stride) {
         W w;
         const int slot = list[k];
@@ -599,19 +657,27 @@ __device__ void md_body(const Dev &d, MDShared<MIXED> &S, const ReplicaDev &rp, 
         }
         work[k] = w;
     }
-    publish_partials<MIXED, REG>(cl, S, acc, 0);
-    cl.sync();
-    if (tid == 0) col_gather(rp, S, 0);
+    reduce_forces(0);
+    if constexpr (MIXED) {
+        if (wid == 0) col_gather_w<CS, (CS == 1 && REG)>(rp, S, 0, lane);
+    } else {
+        if (tid == 0) col_gather<CS>(rp, S, 0);
+    }
 
     const double dt = rp.dt, hdt = rp.hdt;
     for (int s = 0; s < rp.n_md; ++s) {
         const int par = (s + 1) & 1;
-        if (tid == 0) {
-            // colloids: first half kick, drift, RATTLE position stage
-            col_kick_drift(rp, S);
-            col_frames(rp, S);
+        // colloids: first half kick, drift, RATTLE position stage
+        if constexpr (MIXED) {
+            if (wid == 0) col_kick_drift_w(rp, S, lane);
+        } else {
+            if (tid == 0) {
+                col_kick_drift(rp, S);
+                col_frames(rp, S);
+            }
         }
         zero_acc();
+        zero_fq();
         __syncthreads();
         // solvent: second half kick of the previous sub-step, first half kick
         // and drift of this one, new forces, catalytic conversion
@@ -639,12 +705,18 @@ __device__ void md_body(const Dev &d, MDShared<MIXED> &S, const ReplicaDev &rp, 
             }
             work[k] = w;
         }
-        publish_partials<MIXED, REG>(cl, S, acc, par);
-        cl.sync();
-        if (tid == 0) {
-            // colloids: new forces, second half kick, RATTLE velocity stage
-            col_gather(rp, S, par);
-            col_kick(rp, S);
+        reduce_forces(par);
+        // colloids: new forces, second half kick, RATTLE velocity stage
+        if constexpr (MIXED) {
+            if (wid == 0) {
+                col_gather_w<CS, (CS == 1 && REG)>(rp, S, par, lane);
+                col_kick_w(rp, S, lane);
+            }
+        } else {
+            if (tid == 0) {
+                col_gather<CS>(rp, S, par);
+                col_kick(rp, S);
+            }
         }
     }
 
@@ -677,22 +749,23 @@ __device__ void md_body(const Dev &d, MDShared<MIXED> &S, const ReplicaDev &rp, 
             if (do_bin) bin_particle(d, bbuf, rp.cell_off + cell_key_d(rp, w.x, sh), w.slot);
         }
     }
+    __syncwarp();
     if (tid == 0 && rank == 0) {
-        col_frames(rp, S);
+        if constexpr (!MIXED) col_frames(rp, S);
         col_store(d, rp, S);
-        // every CTA read near_count before the first cluster barrier
+        // every CTA read near_count before the first barrier of the cluster
         d.near_count[r] = 0;
     }
-    cl.sync();   // no CTA leaves while a peer may still write to its shared memory
+    if (CS > 1) cl.sync();   // no CTA leaves while a peer may still write to its shared memory
 }
 
-template <bool MIXED>
-__global__ void __launch_bounds__(MDT, 1) k_md(Dev d, uint32_t step, int rbuf, int bbuf, int do_bin)
+template <bool MIXED, int CS>
+__global__ void __launch_bounds__(MDGeom<CS>::NT, 1) k_md(Dev d, uint32_t step, int rbuf, int bbuf, int do_bin)
 {
     __shared__ MDShared<MIXED> S;
     __shared__ ReplicaDev s_rp;
     cg::cluster_group cl = cg::this_cluster();
-    const int r = blockIdx.x / MD_CS;
+    const int r = blockIdx.x / CS;
     const int tid = threadIdx.x;
     if (tid == 0) s_rp = d.rep[r];
     __syncthreads();
@@ -714,31 +787,45 @@ __global__ void __launch_bounds__(MDT, 1) k_md(Dev d, uint32_t step, int rbuf, i
     }
     if (tid < rp.n_bond) S.bond[tid] = d.bonds[rp.bond_off + tid];
     __syncthreads();
-    if (tid == 0) col_frames(rp, S);
-    __syncthreads();
+    if constexpr (!MIXED) {
+        if (tid == 0) col_frames(rp, S);
+        __syncthreads();
+    }
     // all CTAs of the cluster must have read near_count before rank 0 resets it
-    cl.sync();
-    if (rp.n_col <= NCR) md_body<MIXED, true>(d, S, rp, cl, step, rbuf, bbuf, do_bin, r);
-    else md_body<MIXED, false>(d, S, rp, cl, step, rbuf, bbuf, do_bin, r);
+    if (CS > 1) cl.sync();
+    if (rp.n_col <= NCR) md_body<MIXED, true, CS>(d, S, rp, cl, step, rbuf, bbuf, do_bin, r);
+    else md_body<MIXED, false, CS>(d, S, rp, cl, step, rbuf, bbuf, do_bin, r);
 }
 
-void launch_md(bool mixed, const Dev &d, uint32_t step, int rbuf, int bbuf, int do_bin, cudaStream_t s)
+template <bool MIXED, int CS>
+static void launch_md_cs(const Dev &d, uint32_t step, int rbuf, int bbuf, int do_bin, cudaStream_t s)
 {
-    if (d.n_rep <= 0) return;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(d.n_rep * MD_CS), 1, 1);
-    cfg.blockDim = dim3(MDT, 1, 1);
+    cfg.gridDim = dim3((unsigned)(d.n_rep * CS), 1, 1);
+    cfg.blockDim = dim3(MDGeom<CS>::NT, 1, 1);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = MD_CS;
+    attr[0].val.clusterDim.x = CS;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (mixed) cudaLaunchKernelEx(&cfg, k_md<true>, d, step, rbuf, bbuf, do_bin);
-    else cudaLaunchKernelEx(&cfg, k_md<false>, d, step, rbuf, bbuf, do_bin);
+    cudaLaunchKernelEx(&cfg, k_md<MIXED, CS>, d, step, rbuf, bbuf, do_bin);
+}
+
+const int MD_CLUSTER_SIZES[4] = {1, 2, 4, 8};
+
+void launch_md(bool mixed, const Dev &d, uint32_t step, int rbuf, int bbuf, int do_bin, int cs, cudaStream_t s)
+{
+    if (d.n_rep <= 0) return;
+    switch (cs) {
+    case 1: mixed ? launch_md_cs<true, 1>(d, step, rbuf, bbuf, do_bin, s) : launch_md_cs<false, 1>(d, step, rbuf, bbuf, do_bin, s); break;
+    case 2: mixed ? launch_md_cs<true, 2>(d, step, rbuf, bbuf, do_bin, s) : launch_md_cs<false, 2>(d, step, rbuf, bbuf, do_bin, s); break;
+    case 4: mixed ? launch_md_cs<true, 4>(d, step, rbuf, bbuf, do_bin, s) : launch_md_cs<false, 4>(d, step, rbuf, bbuf, do_bin, s); break;
+    default: mixed ? launch_md_cs<true, 8>(d, step, rbuf, bbuf, do_bin, s) : launch_md_cs<false, 8>(d, step, rbuf, bbuf, do_bin, s); break;
+    }
 }
 
 }  // namespace rmpcd

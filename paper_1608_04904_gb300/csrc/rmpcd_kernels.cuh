@@ -28,7 +28,15 @@ enum ParticleMode { PM_STREAM = 0, PM_BIN = 1, PM_PRIME = 2 };
 
 void launch_cellpass(bool mixed, const Dev &d, const CellPassArgs &a, cudaStream_t s);
 void launch_particles(bool mixed, const Dev &d, int mode, uint32_t step, int rbuf, int bbuf, cudaStream_t s);
-void launch_md(bool mixed, const Dev &d, uint32_t step, int rbuf, int bbuf, int do_bin, cudaStream_t s);
+// cs: CTAs per replica cluster, one of MD_CLUSTER_SIZES (results do not depend on it)
+extern const int MD_CLUSTER_SIZES[4];
+void launch_md(bool mixed, const Dev &d, uint32_t step, int rbuf, int bbuf, int do_bin, int cs, cudaStream_t s);
+// Few-colloid variant (every replica: at most MD_FAST_NC colloids, no
+// colloid-colloid potential); bit-identical results to launch_md.
+constexpr int MD_FAST_NC = 2;
+// cs: 1, 2, 4, 8 or 16 (16 when md_fast_max_cluster allows it)
+void launch_md_fast(bool mixed, const Dev &d, uint32_t step, int rbuf, int bbuf, int do_bin, int cs, cudaStream_t s);
+int md_fast_max_cluster(bool mixed);
 void launch_set_state(bool mixed, const Dev &d, int replica, int n, const double *x, const double *v,
                       const uint8_t *flags, int rbuf, cudaStream_t s);
 void launch_get_state(bool mixed, const Dev &d, int replica, int n, int rbuf, double *x, double *v, uint8_t *flags,

@@ -372,3 +372,31 @@ def test_device_pointer_state_roundtrip():
     assert np.array_equal(out["x"].cpu().numpy(), x)
     assert np.array_equal(out["v"].cpu().numpy(), v)
     assert np.array_equal(out["flags"].cpu().numpy(), fl)
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_md_launch_choices_do_not_change_results(precision):
+    """The colloid forces are exact fixed-point sums, so every MD kernel and
+    cluster size (and the autotuned choice) gives bit-identical states."""
+    cfg, col, bonds, x, v, fl = _dimer(precision, bulk_rate=0.05)
+    ref = None
+    for kern in (1, 2):
+        for cs in (1, 2, 4, 8, 16, 0):
+            g = gpu(cfg, x, v, fl, col, bonds, precision=precision)
+            try:
+                g.set_tuning(cs, kern)
+            except api.RmpcdError:
+                assert cs == 16   # 16-CTA clusters: few-colloid kernel on capable devices only
+                continue
+            g.step(14 if cs == 0 else 3)
+            if cs == 0:
+                assert g.get_tuning()[0] in (1, 2, 4, 8, 16) and g.get_tuning()[1] == kern
+                continue
+            st = g.get_state()
+            cx = g.get_colloids(0)["x"]
+            if ref is None:
+                ref = (st, cx)
+            else:
+                for key in st:
+                    assert np.array_equal(st[key], ref[0][key]), (kern, cs, key)
+                assert np.array_equal(cx, ref[1])
