@@ -202,6 +202,9 @@ static void fill_rep(ReplicaDev &rp, const rmpcd_params &p)
     for (int k = 0; k < 4; ++k) {
         rp.slab_x0[k] = p.slab_x0[k];
         rp.slab_x1[k] = p.slab_x1[k];
+        // integer cx: x0 <= cx  <=>  ceil(x0) <= cx,   cx < x1  <=>  cx < ceil(x1)
+        rp.slab_lo[k] = (int)std::max(-1e9, std::min(1e9, ceil(p.slab_x0[k])));
+        rp.slab_hi[k] = (int)std::max(-1e9, std::min(1e9, ceil(p.slab_x1[k])));
         rp.slab_sd[k] = sqrt(p.slab_kT[k] > 0.0 ? p.slab_kT[k] : 0.0);
         rp.slab_sd_f[k] = (float)rp.slab_sd[k];
     }
@@ -279,7 +282,7 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
     *out = nullptr;
     if (precision != RMPCD_FP64 && precision != RMPCD_MIXED) return fail(nullptr, RMPCD_EINVAL, "unknown precision %d", precision);
     if (n_replicas < 1 || !params) return fail(nullptr, RMPCD_EINVAL, "need n_replicas >= 1 and params");
-    const int max_cap = std::min(TP_M, TP_D);
+    const int max_cap = CP_MAX_CAP;
     if (bucket_cap < 1 || bucket_cap > max_cap) return fail(nullptr, RMPCD_EINVAL, "bucket_cap %d not in [1,%d]", bucket_cap, max_cap);
     long long n_total = 0, n_tiles = 0, n_col = 0, n_bond = 0;
     for (int r = 0; r < n_replicas; ++r) {
@@ -332,12 +335,13 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
     sys->fast_ok = true;
     for (int r = 0; r < n_replicas; ++r)
         if (params[r].n_colloids > MD_FAST_NC || params[r].cc_rc > 0.0) sys->fast_ok = false;
-    // bulk reaction thresholds: accept iff draw < (1 - exp(-k N_B tau)) 2^32
-    std::vector<double> thr((size_t)n_replicas * (bucket_cap + 1));
+    // bulk reaction thresholds: accept iff draw < (1 - exp(-k N_B tau)) 2^32;
+    // for an integer draw that is draw < ceil((1 - exp(-k N_B tau)) 2^32)
+    std::vector<unsigned long long> thr((size_t)n_replicas * (bucket_cap + 1));
     for (int r = 0; r < n_replicas; ++r)
         for (int nb = 0; nb <= bucket_cap; ++nb)
-            thr[(size_t)r * (bucket_cap + 1) + nb] =
-                (1.0 - exp(-params[r].bulk_rate * (double)nb * params[r].tau)) * 4294967296.0;
+            thr[(size_t)r * (bucket_cap + 1) + nb] = (unsigned long long)ceil(
+                (1.0 - exp(-params[r].bulk_rate * (double)nb * params[r].tau)) * 4294967296.0);
     // colloid constants
     std::vector<double> cM(n_col), cS(n_col), cEA(n_col), cEB(n_col), cR2(n_col), cR(n_col), cX(3 * n_col), cV(3 * n_col);
     std::vector<float> fS(n_col), fEA(n_col), fEB(n_col), fR2(n_col), fR(n_col);
@@ -370,7 +374,7 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
     const long long ncells = (long long)n_tiles * CPT;
     ReplicaDev *drep = nullptr;
     int *dtile = nullptr;
-    double *dthr = nullptr;
+    unsigned long long *dthr = nullptr;
     double *dM, *dS, *dEA, *dEB, *dR2, *dR;
     float *dfS, *dfEA, *dfEB, *dfR2, *dfR;
     int *dCat;
@@ -427,7 +431,7 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
     };
     up(drep, sys->rep.data(), sizeof(ReplicaDev) * n_replicas);
     up(dtile, tile_rep.data(), sizeof(int) * n_tiles);
-    up(dthr, thr.data(), sizeof(double) * thr.size());
+    up(dthr, thr.data(), sizeof(unsigned long long) * thr.size());
     up(d.colX, cX.data(), sizeof(double) * cX.size());
     up(d.colV, cV.data(), sizeof(double) * cV.size());
     up(dM, cM.data(), sizeof(double) * n_col); up(dS, cS.data(), sizeof(double) * n_col);

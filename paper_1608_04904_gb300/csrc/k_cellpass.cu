@@ -11,6 +11,11 @@
 // particle counts, found by a single-pass decoupled look-back (Merrill &
 // Garland 2016) over tiles taken in ticket order.
 //
+// After the tile base is known each warp handles CPT / CP_WARPS cells on its
+// own (warp-synchronous, no CTA barrier), so the warps' memory traffic
+// overlaps freely.  A tile with a cell too crowded for one warp's staging
+// area runs the same stages with the whole CTA as one group instead.
+//
 // Per particle this reads its bucket entry (4 B) and its record (32 B mixed /
 // 64 B fp64) and writes its record and its next bucket entry: one pass over
 // the solvent per collision.
@@ -22,12 +27,14 @@ template <bool MIXED> struct Traits;
 template <> struct Traits<true> {
     using Rec = RecM;
     using R = float;
-    static constexpr int TP = TP_M;
+    static constexpr int WPC = CP_WPC_M;
+    static constexpr int TP = CP_WARPS * WPC;
 };
 template <> struct Traits<false> {
     using Rec = RecD;
     using R = double;
-    static constexpr int TP = TP_D;
+    static constexpr int WPC = CP_WPC_D;
+    static constexpr int TP = CP_WARPS * WPC;
 };
 
 // --- per-record helpers ----------------------------------------------------
@@ -57,7 +64,7 @@ struct NearFrames {
     float Rb[MAXC];
 };
 
-__device__ __forceinline__ bool rec_near(const Dev &d, const ReplicaDev &rp, const NearFrames &nf, const RecM &r)
+__device__ __forceinline__ bool rec_near(const Dev &, const ReplicaDev &rp, const NearFrames &nf, const RecM &r)
 {
     int c[3] = {cw_get(r.cw, 0), cw_get(r.cw, 1), cw_get(r.cw, 2)};
     return near_test_m(rp, rp.n_col, nf.Ci, nf.Cf, nf.Rb, c, r.o, r.v);
@@ -79,94 +86,489 @@ __device__ __forceinline__ double r_omc(const ReplicaDev &rp, double) { return r
 constexpr unsigned long long LB_VALUE_MASK = (1ull << 46) - 1ull;
 constexpr int LB_SPIN_LIMIT = 1 << 22;
 
+// Per-tile state shared by the groups of one CTA.
 template <bool MIXED>
-__global__ void __launch_bounds__(CP_THREADS) k_cellpass(Dev d, CellPassArgs a)
-{
-    using T = Traits<MIXED>;
-    using Rec = typename T::Rec;
-    using R = typename T::R;
-    constexpr int TP = T::TP;
+struct TileShared {
+    using R = typename Traits<MIXED>::R;
+    ReplicaDev rp;
+    NearFrames nf;
+    int tile, r, base, maxcnt;
+    int cnt[CPT], ls[CPT + 1], wt[CPT / 32];
+    double sh[3], shn[3];     // fp64 path
+    float shf[3], shnf[3];
+    R vcm[CPT][3], ax[CPT][3];
+    int mode[CPT], react[CPT];
+    int mnear[CPT];   // 0: no particle of the cell can come near a colloid
+    double red[CP_WARPS][8];
+};
 
+template <int G>
+__device__ __forceinline__ void group_sync()
+{
+    if (G == 32) __syncwarp();
+    else __syncthreads();
+}
+
+// Stage D, one thread per cell, particles summed in sorted order (the same
+// order as the FP64 oracle).
+template <bool MIXED, int G>
+__device__ __forceinline__ void cells_D_serial(const Dev &d, const CellPassArgs &a, TileShared<MIXED> &T, int gt,
+                                               int cb, int ce, int pofs, typename Traits<MIXED>::Rec *srec)
+{
+    using R = typename Traits<MIXED>::R;
+    const ReplicaDev &rp = T.rp;
+    const int lc0 = T.tile * CPT - rp.cell_off;
+    const int opts = a.opts;
+    for (int c = cb + gt; c < ce; c += G) {
+        const int n = T.cnt[c];
+        const int lo = T.ls[c] - pofs;
+        const int lc = lc0 + c;
+        T.mode[c] = 0;
+        T.react[c] = -1;
+        T.mnear[c] = 1;
+        if ((opts & CP_COLLIDE) && n >= 2) {
+            R sum[3] = {R(0), R(0), R(0)};
+            for (int i = 0; i < n; ++i)
+                for (int k = 0; k < 3; ++k) sum[k] = sum[k] + srec[lo + i].v[k];
+            const int cx = lc % rp.L[0];
+            const int cz = lc / (rp.L[0] * rp.L[1]);
+            R vcm[3];
+            const bool wall_cell = rp.walls && (cz == 0 || cz == rp.nz - 1);
+            if (wall_cell && n < rp.rho_wall) {
+                // virtual particles fill the wall cell up to rho_wall (§1.4)
+                const int nv = rp.rho_wall - n;
+                U4 w = philox((uint32_t)lc, a.step, P_VIRT, 0u, rp.seed);
+                R g0, g1, g2, g3;
+                box_muller(w.x, w.y, g0, g1);
+                box_muller(w.z, w.w, g2, g3);
+                const R sd = sqrt((R)nv * (R)rp.kT);
+                const R gg[3] = {g0, g1, g2};
+                for (int k = 0; k < 3; ++k) vcm[k] = (sum[k] + sd * gg[k]) / (R)(n + nv);
+            } else {
+                for (int k = 0; k < 3; ++k) vcm[k] = sum[k] / (R)n;
+            }
+            int slab = -1;
+            for (int k = 0; k < rp.n_slabs; ++k)
+                if (cx >= rp.slab_lo[k] && cx < rp.slab_hi[k]) { slab = k; break; }
+            if (slab >= 0) {
+                // Anderson thermostat (MPC-AT): fresh relative velocities
+                const R sd = slab_sd(rp, slab, R(0));
+                R xs[3] = {R(0), R(0), R(0)};
+                for (int i = 0; i < n; ++i) {
+                    U4 w = philox((uint32_t)lc, a.step, P_THERMO, (uint32_t)i, rp.seed);
+                    R g0, g1, g2, g3;
+                    box_muller(w.x, w.y, g0, g1);
+                    box_muller(w.z, w.w, g2, g3);
+                    const R gg[3] = {g0, g1, g2};
+                    for (int k = 0; k < 3; ++k) {
+                        const R xi = sd * gg[k];
+                        srec[lo + i].v[k] = xi;
+                        xs[k] = xs[k] + xi;
+                    }
+                }
+                for (int k = 0; k < 3; ++k) xs[k] = xs[k] / (R)n;
+                for (int i = 0; i < n; ++i)
+                    for (int k = 0; k < 3; ++k) srec[lo + i].v[k] = vcm[k] + (srec[lo + i].v[k] - xs[k]);
+                T.mode[c] = 2;
+            } else {
+                R ax[3];
+                rotation_axis<R>(rp.seed, a.step, (uint32_t)lc, ax);
+                for (int k = 0; k < 3; ++k) { T.vcm[c][k] = vcm[k]; T.ax[c][k] = ax[k]; }
+                T.mode[c] = 1;
+            }
+        }
+        if ((opts & CP_REACT) && rp.bulk_on && n > 0) {
+            int nbB = 0;
+            for (int i = 0; i < n; ++i) nbB += (srec[lo + i].fid & F_B) ? 1 : 0;
+            if (nbB > 0) {
+                U4 w = philox((uint32_t)lc, a.step, P_REACT, 0u, rp.seed);
+                if ((unsigned long long)w.x < d.bulk_thr[rp.thr_off + nbB]) {
+                    const int pick = (int)(((unsigned long long)w.y * (unsigned long long)nbB) >> 32);
+                    for (int i = 0, seen = 0; i < n; ++i) {
+                        if (srec[lo + i].fid & F_B) {
+                            if (seen == pick) { T.react[c] = lo + i; break; }
+                            ++seen;
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Stage D of the mixed path for a warp: four lanes per cell.  Sums, the
+// bound on post-collision speeds and the species count are split over the
+// lanes and combined by shuffles; lane 0 of the cell draws the rotation axis
+// (or runs MPC-AT), lane 1 the bulk reaction, lane 3 tests whether any
+// particle of the cell can come near a colloid during the next interval.
+__device__ __forceinline__ void cells_D_warp8(const Dev &d, const CellPassArgs &a, TileShared<true> &T, int lane,
+                                              int cb, int ce, int pofs, RecM *srec)
+{
+    const ReplicaDev &rp = T.rp;
+    const int lc0 = T.tile * CPT - rp.cell_off;
+    const int opts = a.opts;
+    const int q = lane & 3;
+    const int c = cb + (lane >> 2);
+    const bool cv = c < ce;
+    const int n = cv ? T.cnt[c] : 0;
+    const int lo = cv ? T.ls[c] - pofs : 0;
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+    int nB = 0;
+    for (int i = q; i < n; i += 4) {
+        const RecM &r = srec[lo + i];
+        s0 += r.v[0]; s1 += r.v[1]; s2 += r.v[2];
+        nB += (r.fid & F_B) ? 1 : 0;
+    }
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        nB += __shfl_xor_sync(0xffffffffu, nB, o);
+    }
+    const int lc = lc0 + c;
+    int cx = 0, cy = 0, cz = 0;
+    if (cv) {
+        cx = lc % rp.L[0];
+        const int t = lc / rp.L[0];
+        cy = t % rp.L[1];
+        cz = t / rp.L[1];
+    }
+    const bool collide = cv && (opts & CP_COLLIDE) && n >= 2;
+    float vcm[3] = {0.0f, 0.0f, 0.0f};
+    if (n > 0) {
+        const bool wall_cell = rp.walls && (cz == 0 || cz == rp.nz - 1);
+        if (collide && wall_cell && n < rp.rho_wall) {
+            // virtual particles fill the wall cell up to rho_wall (§1.4)
+            const int nv = rp.rho_wall - n;
+            U4 w = philox((uint32_t)lc, a.step, P_VIRT, 0u, rp.seed);
+            float g0, g1, g2, g3;
+            box_muller(w.x, w.y, g0, g1);
+            box_muller(w.z, w.w, g2, g3);
+            const float sd = sqrtf((float)nv * (float)rp.kT);
+            vcm[0] = (s0 + sd * g0) / (float)(n + nv);
+            vcm[1] = (s1 + sd * g1) / (float)(n + nv);
+            vcm[2] = (s2 + sd * g2) / (float)(n + nv);
+        } else {
+            vcm[0] = s0 / (float)n; vcm[1] = s1 / (float)n; vcm[2] = s2 / (float)n;
+        }
+    }
+    int slab = -1;
+    if (collide)
+        for (int k = 0; k < rp.n_slabs; ++k)
+            if (cx >= rp.slab_lo[k] && cx < rp.slab_hi[k]) { slab = k; break; }
+    // bound on the post-collision speeds of the cell: |v'| <= |v_cm| + max |v - v_cm|
+    float u2 = 0.0f;
+    const bool want_near = cv && (opts & CP_NEXT) && rp.n_col > 0;
+    if (want_near)
+        for (int i = q; i < n; i += 4) {
+            const RecM &r = srec[lo + i];
+            const float a0 = r.v[0] - vcm[0], a1 = r.v[1] - vcm[1], a2 = r.v[2] - vcm[2];
+            u2 = fmaxf(u2, a0 * a0 + a1 * a1 + a2 * a2);
+        }
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) u2 = fmaxf(u2, __shfl_xor_sync(0xffffffffu, u2, o));
+    if (!cv) return;
+    if (q == 0) {
+        T.mode[c] = 0;
+        if (collide && slab >= 0) {
+            // Anderson thermostat (MPC-AT): fresh relative velocities
+            const float sd = rp.slab_sd_f[slab];
+            float xs[3] = {0.0f, 0.0f, 0.0f};
+            for (int i = 0; i < n; ++i) {
+                U4 w = philox((uint32_t)lc, a.step, P_THERMO, (uint32_t)i, rp.seed);
+                float g0, g1, g2, g3;
+                box_muller(w.x, w.y, g0, g1);
+                box_muller(w.z, w.w, g2, g3);
+                const float gg[3] = {g0, g1, g2};
+                for (int k = 0; k < 3; ++k) {
+                    const float xi = sd * gg[k];
+                    srec[lo + i].v[k] = xi;
+                    xs[k] = xs[k] + xi;
+                }
+            }
+            for (int k = 0; k < 3; ++k) xs[k] = xs[k] / (float)n;
+            for (int i = 0; i < n; ++i)
+                for (int k = 0; k < 3; ++k) srec[lo + i].v[k] = vcm[k] + (srec[lo + i].v[k] - xs[k]);
+            T.mode[c] = 2;
+        } else if (collide) {
+            float ax[3];
+            rotation_axis<float>(rp.seed, a.step, (uint32_t)lc, ax);
+            for (int k = 0; k < 3; ++k) { T.vcm[c][k] = vcm[k]; T.ax[c][k] = ax[k]; }
+            T.mode[c] = 1;
+        }
+    } else if (q == 1) {
+        T.react[c] = -1;
+        if ((opts & CP_REACT) && rp.bulk_on && nB > 0) {
+            U4 w = philox((uint32_t)lc, a.step, P_REACT, 0u, rp.seed);
+            if ((unsigned long long)w.x < d.bulk_thr[rp.thr_off + nB]) {
+                const int pick = (int)(((unsigned long long)w.y * (unsigned long long)nB) >> 32);
+                for (int i = 0, seen = 0; i < n; ++i) {
+                    if (srec[lo + i].fid & F_B) {
+                        if (seen == pick) { T.react[c] = lo + i; break; }
+                        ++seen;
+                    }
+                }
+            }
+        }
+    } else if (q == 3) {
+        int mn = 1;
+        if (want_near && slab < 0) {
+            // the cell's particles lie within sqrt(3)/2 of its centre on this
+            // step's grid; compare with every colloid's near radius bound
+            const float vb = sqrtf(vcm[0] * vcm[0] + vcm[1] * vcm[1] + vcm[2] * vcm[2]) + sqrtf(u2);
+            const int kc[3] = {cx, cy, rp.walls ? cz - 1 : cz};
+            mn = 0;
+            for (int j = 0; j < rp.n_col && !mn; ++j) {
+                float dd[3];
+                for (int k = 0; k < 3; ++k)
+                    dd[k] = (float)(kc[k] - T.nf.Ci[3 * j + k]) + ((0.5f + T.shf[k]) - T.nf.Cf[3 * j + k]);
+                min_image(rp, dd);
+                const float dist = sqrtf(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+                if (dist - 0.8661f < T.nf.Rb[j] + vb * rp.tau_f + 1e-3f) mn = 1;
+            }
+        } else if (!want_near) {
+            mn = 0;
+        }
+        T.mnear[c] = mn;
+    }
+}
+
+// Stage D of the mixed path for a warp, eight cells at a time.
+__device__ __forceinline__ void cells_D_warp(const Dev &d, const CellPassArgs &a, TileShared<true> &T, int lane,
+                                             int cb, int ce, int pofs, RecM *srec)
+{
+    for (int c8 = cb; c8 < ce; c8 += 8) cells_D_warp8(d, a, T, lane, c8, ce, pofs, srec);
+}
+
+// The stages of the cell pass for the cells [cb, ce) of the tile, run by a
+// group of G threads (one warp, or the whole CTA), gt = thread index in the
+// group.  srec/ent/srt/cellof are the group's staging arrays (>= the batch).
+template <bool MIXED, int G>
+__device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXED> &T, int gt, int cb, int ce,
+                            typename Traits<MIXED>::Rec *srec, int *ent, int *srt, unsigned char *cellof,
+                            double acc[8])
+{
+    using Rec = typename Traits<MIXED>::Rec;
+    using R = typename Traits<MIXED>::R;
+    const ReplicaDev &rp = T.rp;
+    const int gc0 = T.tile * CPT;
+    const int lc0 = gc0 - rp.cell_off;
+    const int pofs = T.ls[cb];
+    const int nb = T.ls[ce] - pofs;
+    const int part_lo = rp.part_off, part_hi = rp.part_off + rp.n_part;
+    const int opts = a.opts;
+    const Rec *rin = reinterpret_cast<const Rec *>(d.rec[a.rin]);
+    Rec *rout = reinterpret_cast<Rec *>(d.rec[a.rout]);
+
+    // A: the cell of every staged particle, then its bucket entry
+    for (int c = cb + gt; c < ce; c += G) {
+        const int lo = T.ls[c] - pofs, n = T.cnt[c];
+        for (int i = 0; i < n; ++i) cellof[lo + i] = (unsigned char)(c - cb);
+    }
+    group_sync<G>();
+    for (int j = gt; j < nb; j += G) {
+        const int c = cb + cellof[j];
+        ent[j] = d.bucket[a.cur][(long long)(gc0 + c) * d.cap + (j + pofs - T.ls[c])];
+    }
+    group_sync<G>();
+    // B: stable order inside each cell = increasing previous slot
+    for (int j = gt; j < nb; j += G) {
+        const int c = cb + cellof[j];
+        const int lo = T.ls[c] - pofs, n = T.cnt[c];
+        const int e = ent[j];
+        int rank = 0;
+        for (int k = 0; k < n; ++k) rank += (ent[lo + k] < e) ? 1 : 0;
+        srt[lo + rank] = e;
+    }
+    group_sync<G>();
+    // C: gather (and fly the records the MD kernel did not move)
+#pragma unroll 4
+    for (int p = gt; p < nb; p += G) {
+        const int slot = srt[p];
+        Rec rec;
+        if (slot >= part_lo && slot < part_hi) {
+            rec = load_rec(rin + slot);
+        } else {
+            atomicOr(&d.err[ERR_BOUNDS], 1u);
+            rec = Rec{};
+        }
+        if ((opts & CP_FLIGHT) && !(rec.fid & F_PROP)) rec_flight(rp, rec);
+        rec.fid &= ~F_PROP;
+        srec[p] = rec;
+    }
+    group_sync<G>();
+    // D: per-cell work
+    if constexpr (MIXED && G == 32) cells_D_warp(d, a, T, gt, cb, ce, pofs, srec);
+    else cells_D_serial<MIXED, G>(d, a, T, gt, cb, ce, pofs, srec);
+    group_sync<G>();
+    // E: apply, write, classify / bin for the next collision
+#pragma unroll 2
+    for (int p = gt; p < nb; p += G) {
+        const int c = cb + cellof[p];
+        Rec rec = srec[p];
+        if (T.mode[c] == 1) {
+            const R ca = r_ca(rp, R(0)), sa = r_sa(rp, R(0)), omc = r_omc(rp, R(0));
+            const R *vc = T.vcm[c];
+            const R *nh = T.ax[c];
+            const R u0 = rec.v[0] - vc[0], u1 = rec.v[1] - vc[1], u2 = rec.v[2] - vc[2];
+            // Rodrigues: R u = u cos a + (n x u) sin a + n (n.u)(1 - cos a)
+            const R dot = nh[0] * u0 + nh[1] * u1 + nh[2] * u2;
+            const R x0 = nh[1] * u2 - nh[2] * u1;
+            const R x1 = nh[2] * u0 - nh[0] * u2;
+            const R x2 = nh[0] * u1 - nh[1] * u0;
+            const R od = omc * dot;
+            rec.v[0] = vc[0] + (ca * u0 + sa * x0 + od * nh[0]);
+            rec.v[1] = vc[1] + (ca * u1 + sa * x1 + od * nh[1]);
+            rec.v[2] = vc[2] + (ca * u2 + sa * x2 + od * nh[2]);
+        }
+        if (T.react[c] == p) rec.fid &= ~(F_B | F_TAG);
+        const int gslot = T.base + pofs + p;
+        const bool inb = gslot >= part_lo && gslot < part_hi;
+        if (!inb) atomicOr(&d.err[ERR_BOUNDS], 1u);
+        if ((opts & CP_WRITE) && inb) store_rec(rout + gslot, rec);
+        if (opts & CP_OBS) srec[p] = rec;
+        if ((opts & CP_NEXT) && inb) {
+            if (rp.n_col > 0 && T.mnear[c] && rec_near(d, rp, T.nf, rec)) {
+                const int k = atomicAdd(&d.near_count[T.r], 1);
+                if (k < rp.n_part) d.near_list[rp.part_off + k] = gslot;
+                else atomicOr(&d.err[ERR_BOUNDS], 1u);
+            } else {
+                Rec fl = rec;
+                rec_flight(rp, fl);
+                const int key = rec_key(rp, fl, T.shn, T.shnf);
+                bin_particle(d, a.nxt, rp.cell_off + key, gslot);
+            }
+        }
+    }
+    group_sync<G>();
+    // F: observables of the post-collision state (§1.4 temperature)
+    if (opts & CP_OBS) {
+        for (int c = cb + gt; c < ce; c += G) {
+            const int n = T.cnt[c];
+            const int lo = T.ls[c] - pofs;
+            // within a cell in the path's precision, across cells in FP64
+            R sum[3] = {R(0), R(0), R(0)};
+            R ke2 = R(0);
+            int nbB = 0;
+            for (int i = 0; i < n; ++i) {
+                for (int k = 0; k < 3; ++k) {
+                    const R vk = srec[lo + i].v[k];
+                    sum[k] = sum[k] + vk;
+                    ke2 = ke2 + vk * vk;
+                }
+                nbB += (srec[lo + i].fid & F_B) ? 1 : 0;
+            }
+            if (n >= 2) {
+                R vcm[3] = {sum[0] / (R)n, sum[1] / (R)n, sum[2] / (R)n};
+                R ke = R(0);
+                for (int i = 0; i < n; ++i)
+                    for (int k = 0; k < 3; ++k) {
+                        const R u = srec[lo + i].v[k] - vcm[k];
+                        ke = ke + u * u;
+                    }
+                acc[0] += (double)(ke / (R)(n - 1));
+                acc[1] += 1.0;
+            }
+            acc[2] += (double)sum[0]; acc[3] += (double)sum[1]; acc[4] += (double)sum[2];
+            acc[5] += 0.5 * (double)ke2;
+            acc[6] += (double)nbB;
+            acc[7] += (double)n;
+        }
+        group_sync<G>();
+    }
+}
+
+// A run of cells from cb on whose particles fit `cap` staging slots (at
+// least one cell; a single cell never exceeds bucket_cap <= cap).
+__device__ __forceinline__ int batch_end(const int *ls, int cb, int cend, int cap)
+{
+    int ce = cb + 1;
+    while (ce < cend && ls[ce + 1] - ls[cb] <= cap) ++ce;
+    return ce;
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, CellPassArgs a)
+{
+    using Rec = typename Traits<MIXED>::Rec;
+    constexpr int WPC = Traits<MIXED>::WPC;
+    constexpr int TP = Traits<MIXED>::TP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Rec *srec = reinterpret_cast<Rec *>(smem_raw);
     int *ent = reinterpret_cast<int *>(srec + TP);
     int *srt = ent + TP;
     unsigned char *cellof = reinterpret_cast<unsigned char *>(srt + TP);
+    __shared__ TileShared<MIXED> T;
 
-    __shared__ ReplicaDev s_rp;
-    __shared__ int s_tile, s_r, s_ce, s_base;
-    __shared__ int s_cnt[CPT], s_ls[CPT + 1], s_wt[2];
-    __shared__ double s_sh[3], s_shn[3];
-    __shared__ float s_shnf[3];
-    __shared__ R s_vcm[CPT][3], s_ax[CPT][3];
-    __shared__ int s_mode[CPT], s_react[CPT];
-    __shared__ double s_red[CP_THREADS / 32][8];
-    __shared__ NearFrames s_nf;
-
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0) {
-        s_tile = (int)atomicAdd(&d.ticket[a.epoch & 1u], 1u);
+        const int tile = (int)atomicAdd(&d.ticket[a.epoch & 1u], 1u);
+        T.tile = tile;
+        T.r = tile < d.n_tiles ? d.tile_rep[tile] : 0;
+        T.maxcnt = 0;
         if (blockIdx.x == 0) d.ticket[(a.epoch + 1u) & 1u] = 0u;
     }
     __syncthreads();
-    const int tile = s_tile;
+    const int tile = T.tile;
     if (tile >= d.n_tiles) return;
-    if (tid == 0) {
-        s_r = d.tile_rep[tile];
-        s_rp = d.rep[s_r];
+    {
+        // the replica's constants, copied by all threads in parallel
+        const int *src = reinterpret_cast<const int *>(d.rep + T.r);
+        int *dst = reinterpret_cast<int *>(&T.rp);
+        for (int i = tid; i < (int)(sizeof(ReplicaDev) / sizeof(int)); i += CP_THREADS) dst[i] = src[i];
     }
-    __syncthreads();
-    const ReplicaDev &rp = s_rp;
-    const int r = s_r;
-    if (MIXED && (a.opts & CP_NEXT)) {
-        for (int i = tid; i < 3 * rp.n_col; i += CP_THREADS) {
-            s_nf.Ci[i] = d.colCi[3 * rp.col_off + i];
-            s_nf.Cf[i] = d.colXf[3 * rp.col_off + i];
-        }
-        for (int j = tid; j < rp.n_col; j += CP_THREADS) s_nf.Rb[j] = d.colRb_f[rp.col_off + j];
-    }
-    const int gc0 = tile * CPT;            // global index of the tile's first cell
-    const int lc0 = gc0 - rp.cell_off;     // replica-local index of that cell
-
+    const int gc0 = tile * CPT;
     // counts of the tile's cells (consumed: reset for reuse two passes later)
+    int n = 0, x = 0;
     if (tid < CPT) {
-        int n = d.count[a.cur][gc0 + tid];
+        n = d.count[a.cur][gc0 + tid];
         d.count[a.cur][gc0 + tid] = 0;
         if (n > d.cap) {
             atomicMax(&d.err[ERR_OVERFLOW], (unsigned int)n);
             n = d.cap;
         }
-        s_cnt[tid] = n;
-        int x = n;
-        const int lane = tid & 31;
+        T.cnt[tid] = n;
+        x = n;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             int y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
-        if (lane == 31) s_wt[tid >> 5] = x;
-        s_ls[tid + 1] = x;   // inclusive within the warp for now
-    }
-    if (tid == 0) {
-        s_ls[0] = 0;
-        double s[3];
-        grid_shift(rp.seed, a.step, s);
-        s_sh[0] = s[0]; s_sh[1] = s[1]; s_sh[2] = s[2];
-        grid_shift(rp.seed, a.step + 1u, s);
-        s_shn[0] = s[0]; s_shn[1] = s[1]; s_shn[2] = s[2];
-        s_shnf[0] = (float)s[0]; s_shnf[1] = (float)s[1]; s_shnf[2] = (float)s[2];
+        const int mx = __reduce_max_sync(0xffffffffu, n);
+        if (lane == 31) T.wt[wid] = x;
+        if (lane == 0) atomicMax(&T.maxcnt, mx);
     }
     __syncthreads();
-    if (tid >= 32 && tid < CPT) s_ls[tid + 1] += s_wt[0];
+    const ReplicaDev &rp = T.rp;
+    if (tid < CPT) {
+        int pre = 0;
+        for (int w = 0; w < wid; ++w) pre += T.wt[w];
+        T.ls[tid + 1] = x + pre;
+    }
+    if (tid == 0) {
+        T.ls[0] = 0;
+        grid_shift(rp.seed, a.step, T.shf);
+        if (!MIXED) grid_shift(rp.seed, a.step, T.sh);
+    } else if (tid == 32) {
+        grid_shift(rp.seed, a.step + 1u, T.shnf);
+        if (!MIXED) grid_shift(rp.seed, a.step + 1u, T.shn);
+    }
+    if (MIXED && (a.opts & CP_NEXT)) {
+        for (int i = tid; i < 3 * rp.n_col; i += CP_THREADS) {
+            T.nf.Ci[i] = d.colCi[3 * rp.col_off + i];
+            T.nf.Cf[i] = d.colXf[3 * rp.col_off + i];
+        }
+        for (int j = tid; j < rp.n_col; j += CP_THREADS) T.nf.Rb[j] = d.colRb_f[rp.col_off + j];
+    }
     __syncthreads();
 
     // tile base by decoupled look-back: warp 0 inspects 32 predecessor tiles
     // at a time, sums aggregates back to the nearest inclusive prefix
     if (tid < 32) {
-        const int lane = tid;
         // 16-bit tag of this launch, never 0 (the initial state)
         const unsigned long long ep = (unsigned long long)(a.epoch % 65535u) + 1ull;
-        const unsigned long long total = (unsigned long long)s_ls[CPT];
+        const unsigned long long total = (unsigned long long)T.ls[CPT];
         if (lane == 0) st_release(&d.tile_state[tile], (ep << 48) | (1ull << 46) | total);
         unsigned long long prefix = 0;
         int t = tile - 1;
@@ -202,232 +604,46 @@ __global__ void __launch_bounds__(CP_THREADS) k_cellpass(Dev d, CellPassArgs a)
                 prefix = 0x3FFFFFFFull;   // pushes every write of this tile out of bounds
             }
             st_release(&d.tile_state[tile], (ep << 48) | (2ull << 46) | ((prefix + total) & LB_VALUE_MASK));
-            s_base = (int)(prefix > 0x3FFFFFFFull ? 0x3FFFFFFF : prefix);
+            T.base = (int)(prefix > 0x3FFFFFFFull ? 0x3FFFFFFF : prefix);
         }
     }
     __syncthreads();
-    const int base = s_base;
-    const int part_lo = rp.part_off, part_hi = rp.part_off + rp.n_part;
-    const int opts = a.opts;
-    const Rec *rin = reinterpret_cast<const Rec *>(d.rec[a.rin]);
-    Rec *rout = reinterpret_cast<Rec *>(d.rec[a.rout]);
 
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // T sum, cells, px, py, pz, ke, nB, n
-
-    int cb = 0;
-    while (cb < CPT) {
-        if (tid == 0) {
-            int ce = cb + 1;
-            while (ce < CPT && s_ls[ce + 1] - s_ls[cb] <= TP) ++ce;
-            s_ce = ce;
+    if (T.maxcnt <= WPC) {
+        // each warp: its own CPT / CP_WARPS cells, in batches of <= WPC particles
+        constexpr int CPW = CPT / CP_WARPS;
+        const int c0 = wid * CPW, c1 = c0 + CPW;
+        Rec *wrec = srec + wid * WPC;
+        int *went = ent + wid * WPC;
+        int *wsrt = srt + wid * WPC;
+        unsigned char *wcell = cellof + wid * WPC;
+        for (int cb = c0; cb < c1;) {
+            const int ce = batch_end(T.ls, cb, c1, WPC);
+            cells_batch<MIXED, 32>(d, a, T, lane, cb, ce, wrec, went, wsrt, wcell, acc);
+            cb = ce;
         }
-        __syncthreads();
-        const int ce = s_ce;
-        const int pofs = s_ls[cb];
-        const int nb = s_ls[ce] - pofs;
-
-        // A: bucket entries of the batch's cells
-        for (int j = tid; j < nb; j += CP_THREADS) {
-            const int jj = j + pofs;
-            int lo = cb, hi = ce - 1;
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (s_ls[mid] <= jj) lo = mid; else hi = mid - 1;
-            }
-            ent[j] = d.bucket[a.cur][(long long)(gc0 + lo) * d.cap + (jj - s_ls[lo])];
-            cellof[j] = (unsigned char)lo;
+    } else {
+        // a crowded tile: the whole CTA as one group
+        for (int cb = 0; cb < CPT;) {
+            const int ce = batch_end(T.ls, cb, CPT, TP);
+            cells_batch<MIXED, CP_THREADS>(d, a, T, tid, cb, ce, srec, ent, srt, cellof, acc);
+            cb = ce;
         }
-        __syncthreads();
-        // B: stable order inside each cell = increasing previous slot
-        for (int j = tid; j < nb; j += CP_THREADS) {
-            const int c = cellof[j];
-            const int lo = s_ls[c] - pofs, n = s_cnt[c];
-            const int e = ent[j];
-            int rank = 0;
-            for (int k = 0; k < n; ++k) rank += (ent[lo + k] < e) ? 1 : 0;
-            srt[lo + rank] = e;
-        }
-        __syncthreads();
-        // C: gather (and fly the records the MD kernel did not move)
-        for (int p = tid; p < nb; p += CP_THREADS) {
-            const int slot = srt[p];
-            Rec rec;
-            if (slot >= part_lo && slot < part_hi) {
-                rec = load_rec(rin + slot);
-            } else {
-                atomicOr(&d.err[ERR_BOUNDS], 1u);
-                rec = Rec{};
-            }
-            if ((opts & CP_FLIGHT) && !(rec.fid & F_PROP)) rec_flight(rp, rec);
-            rec.fid &= ~F_PROP;
-            srec[p] = rec;
-        }
-        __syncthreads();
-        // D: per-cell work
-        for (int c = cb + tid; c < ce; c += CP_THREADS) {
-            const int n = s_cnt[c];
-            const int lo = s_ls[c] - pofs;
-            const int lc = lc0 + c;
-            s_mode[c] = 0;
-            s_react[c] = -1;
-            if ((opts & CP_COLLIDE) && n >= 2) {
-                R sum[3] = {R(0), R(0), R(0)};
-                for (int i = 0; i < n; ++i)
-                    for (int k = 0; k < 3; ++k) sum[k] = sum[k] + srec[lo + i].v[k];
-                const int cx = lc % rp.L[0];
-                const int cz = lc / (rp.L[0] * rp.L[1]);
-                R vcm[3];
-                const bool wall_cell = rp.walls && (cz == 0 || cz == rp.nz - 1);
-                if (wall_cell && n < rp.rho_wall) {
-                    const int nv = rp.rho_wall - n;
-                    U4 w = philox((uint32_t)lc, a.step, P_VIRT, 0u, rp.seed);
-                    R g0, g1, g2, g3;
-                    box_muller(w.x, w.y, g0, g1);
-                    box_muller(w.z, w.w, g2, g3);
-                    const R sd = sqrt((R)nv * (R)rp.kT);
-                    const R gg[3] = {g0, g1, g2};
-                    for (int k = 0; k < 3; ++k) vcm[k] = (sum[k] + sd * gg[k]) / (R)(n + nv);
-                } else {
-                    for (int k = 0; k < 3; ++k) vcm[k] = sum[k] / (R)n;
-                }
-                int slab = -1;
-                for (int k = 0; k < rp.n_slabs; ++k)
-                    if ((double)cx >= rp.slab_x0[k] && (double)cx < rp.slab_x1[k]) { slab = k; break; }
-                if (slab >= 0) {
-                    // Anderson thermostat (MPC-AT): fresh relative velocities
-                    const R sd = slab_sd(rp, slab, R(0));
-                    R xs[3] = {R(0), R(0), R(0)};
-                    for (int i = 0; i < n; ++i) {
-                        U4 w = philox((uint32_t)lc, a.step, P_THERMO, (uint32_t)i, rp.seed);
-                        R g0, g1, g2, g3;
-                        box_muller(w.x, w.y, g0, g1);
-                        box_muller(w.z, w.w, g2, g3);
-                        const R gg[3] = {g0, g1, g2};
-                        for (int k = 0; k < 3; ++k) {
-                            const R xi = sd * gg[k];
-                            srec[lo + i].v[k] = xi;
-                            xs[k] = xs[k] + xi;
-                        }
-                    }
-                    for (int k = 0; k < 3; ++k) xs[k] = xs[k] / (R)n;
-                    for (int i = 0; i < n; ++i)
-                        for (int k = 0; k < 3; ++k) srec[lo + i].v[k] = vcm[k] + (srec[lo + i].v[k] - xs[k]);
-                    s_mode[c] = 2;
-                } else {
-                    R ax[3];
-                    rotation_axis<R>(rp.seed, a.step, (uint32_t)lc, ax);
-                    for (int k = 0; k < 3; ++k) { s_vcm[c][k] = vcm[k]; s_ax[c][k] = ax[k]; }
-                    s_mode[c] = 1;
-                }
-            }
-            if ((opts & CP_REACT) && rp.bulk_on && n > 0) {
-                int nbB = 0;
-                for (int i = 0; i < n; ++i) nbB += (srec[lo + i].fid & F_B) ? 1 : 0;
-                if (nbB > 0) {
-                    U4 w = philox((uint32_t)lc, a.step, P_REACT, 0u, rp.seed);
-                    if ((double)w.x < d.bulk_thr[rp.thr_off + nbB]) {
-                        const int pick = (int)(((unsigned long long)w.y * (unsigned long long)nbB) >> 32);
-                        for (int i = 0, seen = 0; i < n; ++i) {
-                            if (srec[lo + i].fid & F_B) {
-                                if (seen == pick) { s_react[c] = lo + i; break; }
-                                ++seen;
-                            }
-                        }
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        // E: apply, write, classify / bin for the next collision
-        for (int p = tid; p < nb; p += CP_THREADS) {
-            const int c = cellof[p];
-            Rec rec = srec[p];
-            if (s_mode[c] == 1) {
-                const R ca = r_ca(rp, R(0)), sa = r_sa(rp, R(0)), omc = r_omc(rp, R(0));
-                const R *vc = s_vcm[c];
-                const R *nh = s_ax[c];
-                const R u0 = rec.v[0] - vc[0], u1 = rec.v[1] - vc[1], u2 = rec.v[2] - vc[2];
-                // Rodrigues: R u = u cos a + (n x u) sin a + n (n.u)(1 - cos a)
-                const R dot = nh[0] * u0 + nh[1] * u1 + nh[2] * u2;
-                const R x0 = nh[1] * u2 - nh[2] * u1;
-                const R x1 = nh[2] * u0 - nh[0] * u2;
-                const R x2 = nh[0] * u1 - nh[1] * u0;
-                const R od = omc * dot;
-                rec.v[0] = vc[0] + (ca * u0 + sa * x0 + od * nh[0]);
-                rec.v[1] = vc[1] + (ca * u1 + sa * x1 + od * nh[1]);
-                rec.v[2] = vc[2] + (ca * u2 + sa * x2 + od * nh[2]);
-            }
-            if (s_react[c] == p) rec.fid &= ~(F_B | F_TAG);
-            const int gslot = base + pofs + p;
-            const bool inb = gslot >= part_lo && gslot < part_hi;
-            if (!inb) atomicOr(&d.err[ERR_BOUNDS], 1u);
-            if ((opts & CP_WRITE) && inb) store_rec(rout + gslot, rec);
-            srec[p] = rec;
-            if ((opts & CP_NEXT) && inb) {
-                if (rp.n_col > 0 && rec_near(d, rp, s_nf, rec)) {
-                    const int k = atomicAdd(&d.near_count[r], 1);
-                    if (k < rp.n_part) d.near_list[rp.part_off + k] = gslot;
-                    else atomicOr(&d.err[ERR_BOUNDS], 1u);
-                } else {
-                    Rec fl = rec;
-                    rec_flight(rp, fl);
-                    const int key = rec_key(rp, fl, s_shn, s_shnf);
-                    bin_particle(d, a.nxt, rp.cell_off + key, gslot);
-                }
-            }
-        }
-        __syncthreads();
-        // F: observables of the post-collision state (§1.4 temperature)
-        if (opts & CP_OBS) {
-            for (int c = cb + tid; c < ce; c += CP_THREADS) {
-                const int n = s_cnt[c];
-                const int lo = s_ls[c] - pofs;
-                // within a cell in the path's precision, across cells in FP64
-                R sum[3] = {R(0), R(0), R(0)};
-                R ke2 = R(0);
-                int nbB = 0;
-                for (int i = 0; i < n; ++i) {
-                    for (int k = 0; k < 3; ++k) {
-                        const R vk = srec[lo + i].v[k];
-                        sum[k] = sum[k] + vk;
-                        ke2 = ke2 + vk * vk;
-                    }
-                    nbB += (srec[lo + i].fid & F_B) ? 1 : 0;
-                }
-                if (n >= 2) {
-                    R vcm[3] = {sum[0] / (R)n, sum[1] / (R)n, sum[2] / (R)n};
-                    R ke = R(0);
-                    for (int i = 0; i < n; ++i)
-                        for (int k = 0; k < 3; ++k) {
-                            const R u = srec[lo + i].v[k] - vcm[k];
-                            ke = ke + u * u;
-                        }
-                    acc[0] += (double)(ke / (R)(n - 1));
-                    acc[1] += 1.0;
-                }
-                acc[2] += (double)sum[0]; acc[3] += (double)sum[1]; acc[4] += (double)sum[2];
-                acc[5] += 0.5 * (double)ke2;
-                acc[6] += (double)nbB;
-                acc[7] += (double)n;
-            }
-            __syncthreads();
-        }
-        cb = ce;
     }
 
-    if (opts & CP_OBS) {
-        const int lane = tid & 31, wid = tid >> 5;
+    if (a.opts & CP_OBS) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             double x = acc[k];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-            if (lane == 0) s_red[wid][k] = x;
+            if (lane == 0) T.red[wid][k] = x;
         }
         __syncthreads();
         if (tid < 8) {
             double x = 0.0;
-            for (int w = 0; w < CP_THREADS / 32; ++w) x += s_red[w][tid];
+            for (int w = 0; w < CP_WARPS; ++w) x += T.red[w][tid];
             d.obs_part[(long long)tile * 8 + tid] = x;
         }
     }
@@ -435,8 +651,8 @@ __global__ void __launch_bounds__(CP_THREADS) k_cellpass(Dev d, CellPassArgs a)
 
 size_t cellpass_smem(bool mixed)
 {
-    if (mixed) return (size_t)TP_M * (sizeof(RecM) + 2 * sizeof(int) + 1);
-    return (size_t)TP_D * (sizeof(RecD) + 2 * sizeof(int) + 1);
+    if (mixed) return (size_t)Traits<true>::TP * (sizeof(RecM) + 2 * sizeof(int) + 1);
+    return (size_t)Traits<false>::TP * (sizeof(RecD) + 2 * sizeof(int) + 1);
 }
 
 void launch_cellpass(bool mixed, const Dev &d, const CellPassArgs &a, cudaStream_t s)

@@ -22,10 +22,12 @@
 
 namespace rmpcd {
 
-constexpr int CPT = 64;            // cells per tile of the cell pass
+constexpr int CPT = 128;           // cells per tile of the cell pass
 constexpr int CP_THREADS = 256;    // threads per cell-pass CTA
-constexpr int TP_M = 1024;         // particles a mixed cell-pass CTA stages at once
-constexpr int TP_D = 768;          // particles an fp64 cell-pass CTA stages at once
+constexpr int CP_WARPS = CP_THREADS / 32;
+constexpr int CP_WPC_M = 192;      // particles one warp stages at once (mixed records)
+constexpr int CP_WPC_D = 96;       // particles one warp stages at once (fp64 records)
+constexpr int CP_MAX_CAP = 768;    // largest bucket_cap (a crowded tile uses the whole CTA)
 constexpr int MD_THREADS = 1024;   // threads of the near-field MD CTA (one per replica)
 constexpr int MAXC = 64;           // colloids per replica handled by the MD CTA
 constexpr int MAXB = 16;           // bonds per replica
@@ -54,6 +56,7 @@ struct ReplicaDev {
     double g[3];
     double gnorm, cat_thr, skin;
     double slab_x0[4], slab_x1[4], slab_sd[4];
+    int slab_lo[4], slab_hi[4];      // cx in slab k iff slab_lo <= cx < slab_hi
     double cc_eps, cc_sigma, cc_rc;
     float tau_f, dt_f, hdt_f, ca_f, sa_f, omc_f;
     float g_f[3];
@@ -78,7 +81,7 @@ struct Dev {
     unsigned int *err;           // [ERR_COUNT]
     double *obs_part;            // [n_tiles][8]
     double *obs_out;             // [n_rep][8]
-    const double *bulk_thr;      // per replica [cap + 1]: accept iff draw < thr[N_B]
+    const unsigned long long *bulk_thr;   // per replica [cap + 1]: accept iff draw < thr[N_B]
     double *colX, *colV;         // fp64 path: [n_col_total * 3], unwrapped
     int *colXi, *colCi;          // mixed path: unwrapped / wrapped integer cell [3n]
     float *colXf, *colVf;        // mixed path: FP32 offset in the cell, velocity [3n]
@@ -127,6 +130,12 @@ __device__ __forceinline__ void grid_shift(unsigned long long seed, uint32_t ste
 {
     U4 w = philox(0u, step, P_SHIFT, 0u, seed);
     s[0] = u24d(w.x); s[1] = u24d(w.y); s[2] = u24d(w.z);
+}
+// The same shift in FP32 (exact: 24-bit uniforms).
+__device__ __forceinline__ void grid_shift(unsigned long long seed, uint32_t step, float s[3])
+{
+    U4 w = philox(0u, step, P_SHIFT, 0u, seed);
+    s[0] = u24f(w.x); s[1] = u24f(w.y); s[2] = u24f(w.z);
 }
 
 // Uniform point on the unit sphere (Marsaglia 1972) for the rotation axis of
@@ -243,6 +252,15 @@ __device__ __forceinline__ uint32_t cw_make(int cx, int cy, int cz)
     return (uint32_t)cx | ((uint32_t)cy << 10) | ((uint32_t)cz << 20);
 }
 __device__ __forceinline__ int imod(int a, int L) { int m = a % L; return m < 0 ? m + L : m; }
+// a mod L for a within one box of [0, L) (the usual case: two selects); any
+// other a takes the integer division.
+__device__ __forceinline__ int wrap_cell(int a, int L)
+{
+    a = a >= L ? a - L : a;
+    a = a < 0 ? a + L : a;
+    if ((unsigned)a >= (unsigned)L) a = imod(a, L);
+    return a;
+}
 
 // ---------------------------------------------------------------------------
 // Free flight over time t (§1.1 streaming; §1.4 constant acceleration).
@@ -307,7 +325,7 @@ __device__ __forceinline__ void renorm_m(const ReplicaDev &rp, int c[3], float o
             if (c[2] < 0) { c[2] = 0; o[2] = 0.0f; }
             if (c[2] > rp.L[2] - 1) { c[2] = rp.L[2] - 1; o[2] = 1.0f; }
         } else {
-            c[d] = imod(c[d], rp.L[d]);
+            c[d] = wrap_cell(c[d], rp.L[d]);
         }
     }
 }
@@ -359,16 +377,19 @@ __device__ __forceinline__ int cell_key_d(const ReplicaDev &rp, const double x[3
     int c[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        long long k = (long long)floor(x[d] - s[d]);
+        const double f = floor(x[d] - s[d]);
         if (d == 2 && rp.walls) {
-            k += 1;
+            long long k = (long long)f + 1;
             if (k < 0) k = 0;
             if (k > rp.nz - 1) k = rp.nz - 1;
+            c[d] = (int)k;
+        } else if (f >= -1.0 && f < (double)rp.L[d]) {
+            c[d] = wrap_cell((int)f, rp.L[d]);
         } else {
-            k %= rp.L[d];
+            long long k = (long long)f % rp.L[d];
             if (k < 0) k += rp.L[d];
+            c[d] = (int)k;
         }
-        c[d] = (int)k;
     }
     return c[0] + rp.L[0] * (c[1] + rp.L[1] * c[2]);
 }
@@ -384,7 +405,7 @@ __device__ __forceinline__ int cell_key_m(const ReplicaDev &rp, const int cc[3],
             if (k < 0) k = 0;
             if (k > rp.nz - 1) k = rp.nz - 1;
         } else {
-            k = imod(k, rp.L[d]);
+            k = wrap_cell(k, rp.L[d]);
         }
         c[d] = k;
     }
