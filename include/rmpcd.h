@@ -214,6 +214,40 @@ rmpcd_status rmpcd_launch_count(const rmpcd_system *sys, int64_t *count);
  * failed rmpcd_create when sys is NULL).  Never NULL. */
 const char *rmpcd_last_error(const rmpcd_system *sys);
 
+/* --- observables without device allocation --------------------------------
+ * The paper has no counterpart of this entry point.  It computes what
+ * rmpcd_observables computes (the §1.4 temperature estimator plus totals) from
+ * caller-owned device arrays, and allocates no device memory: it reduces
+ * through one static device array of fixed size per device.  It serves
+ * callers that must not allocate where they measure: a monitor between the
+ * steps of a run whose device memory is wholly reserved by another pool (an
+ * allocation could fail), or a caller with work in flight on other streams
+ * (cudaFree synchronises the whole device).
+ *
+ * Inputs (device pointers, n entries each): cell[n] int32 cell keys, e.g. the
+ * `cell` output of rmpcd_get_state; entries outside [0, n_cells) are skipped
+ * entirely.  v[n][3] FP64 velocities, row-major.  flags[n] (may be NULL = all
+ * A): bit 0 = species B.  n_cells: number of cell keys, 1..RMPCD_NOALLOC_MAX_CELLS
+ * (for rmpcd_get_state keys: L[0] L[1] L[2], or L[0] L[1] (L[2] + 1) with walls).
+ * Output (device pointer, 8 doubles): out = {temperature, momentum x, y, z,
+ * kinetic energy, N_c (cells with N >= 2), N_B, particles counted}.
+ *
+ * The work is queued on `stream` (a cudaStream_t, NULL = legacy default
+ * stream) and is asynchronous; out is valid once that stream reaches it.
+ * The scratch is zeroed by the call itself, so nothing needs to be cleared
+ * between calls; `out` need not start at zero.  The first call on a device
+ * resolves that device's scratch address and loads the kernels (setup); make
+ * it before any stream capture begins.  Calls on one stream are ordered and
+ * safe; calls whose work overlaps on one device (other streams or host
+ * threads) share the scratch and race.  Sums use FP64 atomics: results agree
+ * with rmpcd_observables to rounding, not bit for bit.
+ * Errors (returned at once; rmpcd_last_error(NULL) describes them): EINVAL
+ * (n < 0, n_cells beyond the limit, NULL or misaligned pointers), ECUDA (setup
+ * or launch failed). */
+#define RMPCD_NOALLOC_MAX_CELLS 65536
+rmpcd_status rmpcd_observables_noalloc(const int32_t *cell, const double *v, const uint8_t *flags,
+                                       int64_t n, int32_t n_cells, double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -64,6 +64,7 @@ EXPORTS = [
     "rmpcd_get_colloids", "rmpcd_set_step", "rmpcd_get_step", "rmpcd_stream", "rmpcd_shift_and_sort",
     "rmpcd_collide", "rmpcd_react", "rmpcd_step", "rmpcd_observables", "rmpcd_sync", "rmpcd_launch_count",
     "rmpcd_last_error", "rmpcd_enable_timers", "rmpcd_read_timers", "rmpcd_set_tuning", "rmpcd_get_tuning",
+    "rmpcd_observables_noalloc",
 ]
 
 _LIB = None
@@ -102,6 +103,7 @@ def load():
     L.rmpcd_read_timers.argtypes = [vp, P(Timers), i32]
     L.rmpcd_set_tuning.argtypes = [vp, i32, i32]
     L.rmpcd_get_tuning.argtypes = [vp, P(i32), P(i32)]
+    L.rmpcd_observables_noalloc.argtypes = [vp, vp, vp, i64, i32, vp, vp]
     L.rmpcd_last_error.argtypes = [vp]
     L.rmpcd_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -335,3 +337,21 @@ class System:
         c = C.c_int64()
         self._check(self._lib.rmpcd_launch_count(self._h, C.byref(c)))
         return int(c.value)
+
+
+RMPCD_NOALLOC_MAX_CELLS = 65536
+
+
+def observables_noalloc(cell, v, flags, n_cells: int, out, stream=None) -> None:
+    """rmpcd_observables_noalloc on CUDA tensors: cell (int32, n), v (float64,
+    n x 3), flags (uint8, n, or None) and out (float64, 8), all contiguous on
+    the current device.  Queued on ``stream`` (default: torch's current
+    stream); out = [T, px, py, pz, kinetic, N_c, N_B, n counted]."""
+    L = load()
+    n = int(cell.numel())
+    st = L.rmpcd_observables_noalloc(C.c_void_p(cell.data_ptr()), C.c_void_p(v.data_ptr()),
+                                     None if flags is None else C.c_void_p(flags.data_ptr()), n, int(n_cells),
+                                     C.c_void_p(out.data_ptr()),
+                                     C.c_void_p(_default_stream() if stream is None else int(stream)))
+    if st != 0:
+        raise RmpcdError(st, L.rmpcd_last_error(None).decode())

@@ -97,6 +97,11 @@ static void tstop(rmpcd_system *sys, int phase, cudaEvent_t a)
 
 static std::string g_create_error;
 
+namespace rmpcd {
+// Message of a failure of a call that has no system (rmpcd_last_error(NULL)).
+void note_global_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace rmpcd
+
 // MD kernel choice (0 = the few-colloid kernel when allowed) and the cluster
 // sizes the tuner tries for it.
 static void set_md_kernel(rmpcd_system *sys, int req)
