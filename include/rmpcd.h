@@ -199,9 +199,9 @@ rmpcd_status rmpcd_read_timers(rmpcd_system *sys, rmpcd_timers *out, int32_t res
  *   0 (the default) times each candidate size three times on the first
  *   intervals of rmpcd_step (one synchronisation) and keeps the fastest.
  * md_kernel: 1 = general kernel; 2 = few-colloid kernel (every replica with at
- *   most 2 colloids and no colloid-colloid potential: each warp integrates
- *   the colloids itself, one barrier per sub-step); 0 (default) = 2 when
- *   allowed, else 1.
+ *   most 2 colloids, at most 1 bond and no colloid-colloid potential: every
+ *   warp integrates the colloids itself, one CTA barrier per sub-step);
+ *   0 (default) = 2 when allowed, else 1.
  * rmpcd_get_tuning reports the cluster size in use (0 while tuning) and the
  * kernel.  Errors: EINVAL. */
 rmpcd_status rmpcd_set_tuning(rmpcd_system *sys, int32_t md_cluster, int32_t md_kernel);

@@ -339,7 +339,8 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
     }
     sys->fast_ok = true;
     for (int r = 0; r < n_replicas; ++r)
-        if (params[r].n_colloids > MD_FAST_NC || params[r].cc_rc > 0.0) sys->fast_ok = false;
+        if (params[r].n_colloids > MD_FAST_NC || params[r].cc_rc > 0.0 || params[r].n_bonds > 1)
+            sys->fast_ok = false;
     // bulk reaction thresholds: accept iff draw < (1 - exp(-k N_B tau)) 2^32;
     // for an integer draw that is draw < ceil((1 - exp(-k N_B tau)) 2^32)
     std::vector<unsigned long long> thr((size_t)n_replicas * (bucket_cap + 1));

@@ -93,6 +93,7 @@ struct TileShared {
     ReplicaDev rp;
     NearFrames nf;
     int tile, r, base, maxcnt;
+    int next;   // first cell of the next chunk a warp may take
     int cnt[CPT], ls[CPT + 1], wt[CPT / 32];
     double sh[3], shn[3];     // fp64 path
     float shf[3], shnf[3];
@@ -101,6 +102,11 @@ struct TileShared {
     int mnear[CPT];   // 0: no particle of the cell can come near a colloid
     double red[CP_WARPS][8];
 };
+
+// Named barrier 1 hands the tile base from warp 0 (bar.arrive, once) to the
+// other warps (bar.sync, once each) without stopping warp 0.
+__device__ __forceinline__ void base_arrive() { asm volatile("bar.arrive 1, %0;" ::"n"(CP_THREADS) : "memory"); }
+__device__ __forceinline__ void base_wait() { asm volatile("bar.sync 1, %0;" ::"n"(CP_THREADS) : "memory"); }
 
 template <int G>
 __device__ __forceinline__ void group_sync()
@@ -347,7 +353,7 @@ __device__ __forceinline__ void cells_D_warp(const Dev &d, const CellPassArgs &a
 template <bool MIXED, int G>
 __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXED> &T, int gt, int cb, int ce,
                             typename Traits<MIXED>::Rec *srec, int *ent, int *srt, unsigned char *cellof,
-                            double acc[8])
+                            double acc[8], bool &have_base)
 {
     using Rec = typename Traits<MIXED>::Rec;
     using R = typename Traits<MIXED>::R;
@@ -361,15 +367,31 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
     const Rec *rin = reinterpret_cast<const Rec *>(d.rec[a.rin]);
     Rec *rout = reinterpret_cast<Rec *>(d.rec[a.rout]);
 
+    // Every thread owns at most K particles of a batch; the global loads and
+    // atomics of a stage are issued for all K before any result is used, so a
+    // thread waits for one memory round trip per stage, not one per particle.
+    constexpr int K = Traits<MIXED>::WPC / 32;
+    static_assert(Traits<MIXED>::TP == K * CP_THREADS, "batch size per thread");
+
     // A: the cell of every staged particle, then its bucket entry
     for (int c = cb + gt; c < ce; c += G) {
         const int lo = T.ls[c] - pofs, n = T.cnt[c];
         for (int i = 0; i < n; ++i) cellof[lo + i] = (unsigned char)(c - cb);
     }
     group_sync<G>();
-    for (int j = gt; j < nb; j += G) {
-        const int c = cb + cellof[j];
-        ent[j] = d.bucket[a.cur][(long long)(gc0 + c) * d.cap + (j + pofs - T.ls[c])];
+    {
+        int e[K];
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+            const int j = gt + u * G;
+            if (j < nb) {
+                const int c = cb + cellof[j];
+                e[u] = d.bucket[a.cur][(long long)(gc0 + c) * d.cap + (j + pofs - T.ls[c])];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < K; ++u)
+            if (gt + u * G < nb) ent[gt + u * G] = e[u];
     }
     group_sync<G>();
     // B: stable order inside each cell = increasing previous slot
@@ -382,17 +404,26 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
         srt[lo + rank] = e;
     }
     group_sync<G>();
-    // C: gather (and fly the records the MD kernel did not move)
-#pragma unroll 4
-    for (int p = gt; p < nb; p += G) {
-        const int slot = srt[p];
-        Rec rec;
-        if (slot >= part_lo && slot < part_hi) {
-            rec = load_rec(rin + slot);
-        } else {
-            atomicOr(&d.err[ERR_BOUNDS], 1u);
-            rec = Rec{};
+    // C: gather, then fly the records the MD kernel did not move
+    {
+        bool bad = false;
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+            const int p = gt + u * G;
+            if (p < nb) {
+                const int slot = srt[p];
+                const bool ok = slot >= part_lo && slot < part_hi;
+                bad |= !ok;
+                Rec rec = load_rec(rin + (ok ? slot : part_lo));
+                if (!ok) rec = Rec{};
+                srec[p] = rec;
+            }
         }
+        if (bad) atomicOr(&d.err[ERR_BOUNDS], 1u);
+    }
+#pragma unroll 1
+    for (int p = gt; p < nb; p += G) {
+        Rec rec = srec[p];
         if ((opts & CP_FLIGHT) && !(rec.fid & F_PROP)) rec_flight(rp, rec);
         rec.fid &= ~F_PROP;
         srec[p] = rec;
@@ -402,9 +433,15 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
     if constexpr (MIXED && G == 32) cells_D_warp(d, a, T, gt, cb, ce, pofs, srec);
     else cells_D_serial<MIXED, G>(d, a, T, gt, cb, ce, pofs, srec);
     group_sync<G>();
-    // E: apply, write, classify / bin for the next collision
-#pragma unroll 2
+    if (!have_base) {
+        base_wait();   // stages A-D do not need the tile base; E does
+        have_base = true;
+    }
+    // E: apply, write, classify for the next collision (the next cell of a
+    // far particle goes to ent[p], -1 for none)
+#pragma unroll 1
     for (int p = gt; p < nb; p += G) {
+        int nkey = -1;
         const int c = cb + cellof[p];
         Rec rec = srec[p];
         if (T.mode[c] == 1) {
@@ -436,9 +473,27 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
             } else {
                 Rec fl = rec;
                 rec_flight(rp, fl);
-                const int key = rec_key(rp, fl, T.shn, T.shnf);
-                bin_particle(d, a.nxt, rp.cell_off + key, gslot);
+                nkey = rp.cell_off + rec_key(rp, fl, T.shn, T.shnf);
             }
+        }
+        ent[p] = nkey;
+    }
+    // bin for the next collision: all count atomics, then the bucket writes
+    if (opts & CP_NEXT) {
+        int pos[K];
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+            const int p = gt + u * G;
+            const int key = p < nb ? ent[p] : -1;
+            pos[u] = key >= 0 ? atomicAdd(&d.count[a.nxt][key], 1) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+            if (pos[u] < 0) continue;
+            const int p = gt + u * G;
+            const int key = ent[p];
+            if (pos[u] < d.cap) d.bucket[a.nxt][(long long)key * d.cap + pos[u]] = T.base + pofs + p;
+            else atomicMax(&d.err[ERR_OVERFLOW], (unsigned int)(pos[u] + 1));
         }
     }
     group_sync<G>();
@@ -507,6 +562,7 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
         T.tile = tile;
         T.r = tile < d.n_tiles ? d.tile_rep[tile] : 0;
         T.maxcnt = 0;
+        T.next = 0;
         if (blockIdx.x == 0) d.ticket[(a.epoch + 1u) & 1u] = 0u;
     }
     __syncthreads();
@@ -564,7 +620,9 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
     __syncthreads();
 
     // tile base by decoupled look-back: warp 0 inspects 32 predecessor tiles
-    // at a time, sums aggregates back to the nearest inclusive prefix
+    // at a time, sums aggregates back to the nearest inclusive prefix.  On the
+    // warp path the other warps start on their cells meanwhile.
+    const bool warp_path = T.maxcnt <= WPC;
     if (tid < 32) {
         // 16-bit tag of this launch, never 0 (the initial state)
         const unsigned long long ep = (unsigned long long)(a.epoch % 65535u) + 1ull;
@@ -606,28 +664,45 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
             st_release(&d.tile_state[tile], (ep << 48) | (2ull << 46) | ((prefix + total) & LB_VALUE_MASK));
             T.base = (int)(prefix > 0x3FFFFFFFull ? 0x3FFFFFFF : prefix);
         }
+        __syncwarp();
+        if (warp_path) base_arrive();
     }
-    __syncthreads();
 
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // T sum, cells, px, py, pz, ke, nB, n
-    if (T.maxcnt <= WPC) {
-        // each warp: its own CPT / CP_WARPS cells, in batches of <= WPC particles
-        constexpr int CPW = CPT / CP_WARPS;
-        const int c0 = wid * CPW, c1 = c0 + CPW;
+    if (warp_path) {
+        // each warp takes chunks of CP_CHUNK cells as it becomes free (warp 0
+        // joins after the look-back) and runs them in batches of <= WPC
+        // particles; the observables pass assigns chunks statically so that
+        // its sums are reproducible
         Rec *wrec = srec + wid * WPC;
         int *went = ent + wid * WPC;
         int *wsrt = srt + wid * WPC;
         unsigned char *wcell = cellof + wid * WPC;
-        for (int cb = c0; cb < c1;) {
-            const int ce = batch_end(T.ls, cb, c1, WPC);
-            cells_batch<MIXED, 32>(d, a, T, lane, cb, ce, wrec, went, wsrt, wcell, acc);
-            cb = ce;
+        bool have_base = wid == 0;
+        for (int k = 0;; ++k) {
+            int c0;
+            if (a.opts & CP_OBS) {
+                c0 = (wid + CP_WARPS * k) * CP_CHUNK;
+            } else {
+                if (lane == 0) c0 = atomicAdd(&T.next, CP_CHUNK);
+                c0 = __shfl_sync(0xffffffffu, c0, 0);
+            }
+            if (c0 >= CPT) break;
+            const int c1 = c0 + CP_CHUNK;
+            for (int cb = c0; cb < c1;) {
+                const int ce = batch_end(T.ls, cb, c1, WPC);
+                cells_batch<MIXED, 32>(d, a, T, lane, cb, ce, wrec, went, wsrt, wcell, acc, have_base);
+                cb = ce;
+            }
         }
+        if (!have_base) base_wait();   // a warp that took no chunk still meets the barrier once
     } else {
         // a crowded tile: the whole CTA as one group
+        __syncthreads();
+        bool have_base = true;
         for (int cb = 0; cb < CPT;) {
             const int ce = batch_end(T.ls, cb, CPT, TP);
-            cells_batch<MIXED, CP_THREADS>(d, a, T, tid, cb, ce, srec, ent, srt, cellof, acc);
+            cells_batch<MIXED, CP_THREADS>(d, a, T, tid, cb, ce, srec, ent, srt, cellof, acc, have_base);
             cb = ce;
         }
     }

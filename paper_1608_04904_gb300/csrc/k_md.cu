@@ -496,7 +496,7 @@ __device__ void col_gather_w(const ReplicaDev &rp, MDShared<true> &S, int par, i
         if (lane == 0) colloid_colloid(rp, S, S.Fsum);
         __syncwarp();
     }
-    for (int l = lane; l < 3 * S.nc; l += 32) S.C.F[l / 3][l % 3] = __ll2float_rn(S.Fsum[l]) * 0x1p-40f;
+    for (int l = lane; l < 3 * S.nc; l += 32) S.C.F[l / 3][l % 3] = fixed40_to_float(S.Fsum[l]);
     __syncwarp();
 }
 

@@ -3,15 +3,22 @@
 // colloid-colloid potential: §1.1 velocity Verlet, §1.4 WCA forces and exact
 // RATTLE, §1.5 catalytic A -> B.
 //
-// Every thread of every CTA of the replica's cluster keeps the complete state
-// of the (at most MD_FAST_NC) colloids in registers and integrates it itself:
-// all threads compute identical colloid trajectories from the identical force
-// totals, so no thread waits for another to update the colloids, and the
-// colloid update needs no data exchange.  The colloid forces are 64-bit fixed-point
-// sums: per thread, per warp (shuffles), then one atomic add per warp and
-// component into a triple-buffered accumulator in the shared memory of CTA 0
-// of the cluster.  One barrier (the cluster barrier, or the CTA barrier for a
-// lone CTA) per sub-step separates the additions from the reads.
+// A thread-block cluster of CS CTAs integrates one replica.  The near
+// solvent sits in registers, spread over all threads of the cluster.  Every
+// warp keeps the colloid state lane-parallel (lane 3 j + t holds axis t of
+// colloid j) and integrates it itself from the force totals, so the colloid
+// update needs no hand-off between warps.  One round per force evaluation:
+//   every warp: colloid positions to all lanes (shuffles), the force on each
+//               of its particles, catalysis, the particle's move to the next
+//               round, warp sums of the reaction forces to shared memory;
+//   CTA barrier;
+//   warp 0:     the CTA's partials to every CTA of the cluster (st.async,
+//               counted on each CTA's mbarrier);
+//   every warp: waits for the round's partials, sums them, and runs the
+//               colloid second half kick + RATTLE velocity stage, first half
+//               kick + drift + RATTLE position stage.
+// Forces on the colloids are 64-bit fixed-point sums (2^-40), exact and
+// independent of the order of the near list and of the cluster size.
 //
 // The colloid arithmetic is the same, operation by operation, as the general
 // MD kernel's (FP64 for the fp64 path, integer cell + FP32 for the mixed path),
@@ -26,13 +33,11 @@ namespace cg = cooperative_groups;
 namespace rmpcd {
 
 constexpr int NC = MD_FAST_NC;
-
-// One warp per SM sub-partition; the CTA is small because every thread repeats
-// the colloid update.
-template <int CS> struct FGeom {
-    static constexpr int NT = 128;
-};
-constexpr int PPT = 4;   // near particles a thread keeps in registers
+constexpr int MDF_NT = 256;             // threads per CTA
+constexpr int MDF_NW = MDF_NT / 32;
+constexpr int MDF_PPT = 2;              // near particles a thread keeps in registers
+constexpr int MDF_SPIN_LIMIT = 1 << 22; // polls of one exchange before giving up (ERR_TIMEOUT)
+static_assert(NC == 2, "the lane layout below assumes at most two colloids (lanes 0..5)");
 
 struct __align__(16) FWorkM {
     int c[3];
@@ -53,240 +58,227 @@ struct __align__(16) FWorkD {
 };
 
 struct FShared {
-    unsigned long long tot[3][NC * 3];   // cluster totals (used in CTA 0)
+    unsigned long long part[2][16][8];   // [round parity][source CTA][colloid * 3 + axis]
+    unsigned long long mbar[2];          // one per parity: completes when the round's partials arrived
+    long long wpart[2][MDF_NW][8];       // [round parity][warp][colloid * 3 + axis]
     float sigf[NC], epsAf[NC], epsBf[NC], rc2f[NC];
     double sig[NC], epsA[NC], epsB[NC], rc2[NC];
     int cat[NC];
     int nn;
+    int dead;                            // an exchange timed out: stop waiting
 };
 
-// --- complete colloid state in every thread ----------------------------------
-// mixed: unwrapped integer cell, wrapped cell, FP32 offset in [0,1), FP32
-// velocity and force (the same representation as the general MD kernel)
-struct ColRM {
-    int Xi[NC][3], Ci[NC][3], Xoi[NC][3], X0i[NC][3];
-    float Xf[NC][3], Xof[NC][3], X0f[NC][3], V[NC][3], F[NC][3], invM[NC];
+// --- colloid state, lane-parallel ---------------------------------------------
+// Lane l < 3 nc holds colloid j = l / 3, axis t = l % 3; the bond of a dimer
+// always joins colloids 0 and 1, so the other end of a lane's component is
+// lane l +- 3.  Lanes >= 3 nc carry copies that are never stored.
+struct LaneM {   // integer cell + FP32 offset in [0,1) (mixed path)
+    int Xi, Ci, Xoi, X0i;
+    float Xf, Xof, X0f, V, F, invM;
 };
-// fp64: unwrapped positions (same operations as the FP64 oracle)
-struct ColRD {
-    double X[NC][3], V[NC][3], F[NC][3], Xold[NC][3], X0[NC][3], Xw[NC][3], M[NC];
+struct LaneD {   // unwrapped FP64 position (fp64 path)
+    double X, V, F, Xold, X0, Xw, M;
 };
 
-__device__ __forceinline__ void carry(const ReplicaDev &rp, ColRM &C, int j, int t)
+// Sum over lanes 0..2, in lane order (every lane gets the result): the
+// component sum of a 3-vector held by axis lanes.
+__device__ __forceinline__ float sum3(float a)
 {
-    const float fl = floorf(C.Xf[j][t]);
-    int k = (int)fl;
-    float f = C.Xf[j][t] - fl;
+    return (__shfl_sync(0xffffffffu, a, 0) + __shfl_sync(0xffffffffu, a, 1)) + __shfl_sync(0xffffffffu, a, 2);
+}
+__device__ __forceinline__ double sum3(double a)
+{
+    return (__shfl_sync(0xffffffffu, a, 0) + __shfl_sync(0xffffffffu, a, 1)) + __shfl_sync(0xffffffffu, a, 2);
+}
+
+// Carry of the FP32 offset into the integer cell.  The offset stays within
+// (-1, 2) in practice, where floor() is -1, 0 or 1 and is found by compares
+// (the same f = x - floor(x) as the general case, signed zero included).
+__device__ __forceinline__ void carry(const ReplicaDev &rp, LaneM &C, int t)
+{
+    const float x = C.Xf;
+    float fl;
+    int k;
+    if (fabsf(x - 0.5f) < 1.5f) {
+        fl = x >= 1.0f ? 1.0f : (x < 0.0f ? -1.0f : copysignf(0.0f, x));
+        k = x >= 1.0f ? 1 : (x < 0.0f ? -1 : 0);
+    } else {
+        fl = floorf(x);
+        k = (int)fl;
+    }
+    float f = x - fl;
     if (f >= 1.0f) { f = 0.0f; k += 1; }
-    C.Xf[j][t] = f;
-    C.Xi[j][t] += k;
-    int ci = C.Ci[j][t] + k;
+    C.Xf = f;
+    C.Xi += k;
+    int ci = C.Ci + k;
     if (ci >= rp.L[t] || ci < 0) ci = imod(ci, rp.L[t]);
-    C.Ci[j][t] = ci;
+    C.Ci = ci;
 }
 
-__device__ __forceinline__ void kick_drift(const ReplicaDev &rp, ColRM &C, int nc)
+__device__ __forceinline__ void set_force(LaneM &C, long long tot) { C.F = fixed40_to_float(tot); }
+__device__ __forceinline__ void set_force(LaneD &C, long long tot) { C.F = (double)tot * 0x1p-40; }
+
+__device__ __forceinline__ void kick_drift(const ReplicaDev &rp, LaneM &C, int t)
 {
-#pragma unroll
-    for (int j = 0; j < NC; ++j) {
-        if (j >= nc) continue;
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            C.V[j][t] = fmaf(rp.hdt_f, C.F[j][t] * C.invM[j], C.V[j][t]);
-            C.Xoi[j][t] = C.Xi[j][t];
-            C.Xof[j][t] = C.Xf[j][t];
-            C.Xf[j][t] = fmaf(rp.dt_f, C.V[j][t], C.Xf[j][t]);
-            carry(rp, C, j, t);
-        }
-    }
+    C.V = fmaf(rp.hdt_f, C.F * C.invM, C.V);
+    C.Xoi = C.Xi;
+    C.Xof = C.Xf;
+    C.Xf = fmaf(rp.dt_f, C.V, C.Xf);
+    carry(rp, C, t);
+}
+__device__ __forceinline__ void kick_drift(const ReplicaDev &rp, LaneD &C, int)
+{
+    C.V = fma(rp.hdt, C.F / C.M, C.V);
+    C.Xold = C.X;
+    C.X = fma(rp.dt, C.V, C.X);
 }
 
-// Exact RATTLE position stage (Andersen 1983) for each bond.  With at most
-// two colloids every bond joins colloids 0 and 1; the order of its ends does
-// not matter (swapping them negates the bond vector exactly), and fixed
-// indices keep the colloid arrays in registers.
-__device__ __forceinline__ void rattle_pos(const ReplicaDev &rp, ColRM &C, const BondDev *bond, int nbond)
+// Exact RATTLE position stage (Andersen 1983) for the bond 0-1 of length dd.
+// a_end: this lane belongs to colloid 0 (the bond's first end).
+__device__ __forceinline__ void rattle_pos(const ReplicaDev &rp, LaneM &C, int t, float dd, float idt, bool a_end,
+                                           int other)
 {
-    const float idt = 1.0f / rp.dt_f;
-    for (int k = 0; k < nbond; ++k) {
-        constexpr int a = 0, b = 1;
-        const float dd = (float)bond[k].d;
-        float ro[3], rn[3];
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            ro[t] = (float)(C.Xoi[a][t] - C.Xoi[b][t]) + (C.Xof[a][t] - C.Xof[b][t]);
-            rn[t] = (float)(C.Xi[a][t] - C.Xi[b][t]) + (C.Xf[a][t] - C.Xf[b][t]);
-        }
-        const float inv = C.invM[a] + C.invM[b];
-        const float oo = ro[0] * ro[0] + ro[1] * ro[1] + ro[2] * ro[2];
-        const float on = rn[0] * ro[0] + rn[1] * ro[1] + rn[2] * ro[2];
-        const float nn = rn[0] * rn[0] + rn[1] * rn[1] + rn[2] * rn[2];
-        const float qa = inv * inv * oo;
-        const float qb = 2.0f * inv * on;
-        const float qc = nn - dd * dd;
-        float disc = qb * qb - 4.0f * qa * qc;
-        if (disc < 0.0f) disc = 0.0f;
-        const float q = -0.5f * (qb + copysignf(sqrtf(disc), qb));
-        const float gmul = qc / q;
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            const float ca = gmul * ro[t] * C.invM[a];
-            const float cb = gmul * ro[t] * C.invM[b];
-            C.Xf[a][t] += ca;
-            C.Xf[b][t] -= cb;
-            C.V[a][t] += ca * idt;
-            C.V[b][t] -= cb * idt;
-            carry(rp, C, a, t);
-            carry(rp, C, b, t);
-        }
+    const int oXoi = __shfl_sync(0xffffffffu, C.Xoi, other), oXi = __shfl_sync(0xffffffffu, C.Xi, other);
+    const float oXof = __shfl_sync(0xffffffffu, C.Xof, other), oXf = __shfl_sync(0xffffffffu, C.Xf, other);
+    const float oinvM = __shfl_sync(0xffffffffu, C.invM, other);
+    const float ro = a_end ? (float)(C.Xoi - oXoi) + (C.Xof - oXof) : (float)(oXoi - C.Xoi) + (oXof - C.Xof);
+    const float rn = a_end ? (float)(C.Xi - oXi) + (C.Xf - oXf) : (float)(oXi - C.Xi) + (oXf - C.Xf);
+    const float ia = a_end ? C.invM : oinvM, ib = a_end ? oinvM : C.invM;
+    const float inv = ia + ib;
+    const float oo = sum3(ro * ro), on = sum3(rn * ro), nn = sum3(rn * rn);
+    const float qa = inv * inv * oo;
+    const float qb = 2.0f * inv * on;
+    const float qc = nn - dd * dd;
+    float disc = qb * qb - 4.0f * qa * qc;
+    if (disc < 0.0f) disc = 0.0f;
+    const float q = -0.5f * (qb + copysignf(sqrtf(disc), qb));
+    const float gmul = qc / q;
+    if (a_end) {
+        const float ca = gmul * ro * ia;
+        C.Xf += ca;
+        C.V += ca * idt;
+    } else {
+        const float cb = gmul * ro * ib;
+        C.Xf -= cb;
+        C.V -= cb * idt;
     }
+    carry(rp, C, t);
 }
-
-__device__ __forceinline__ void kick_rattle_vel(const ReplicaDev &rp, ColRM &C, int nc, const BondDev *bond, int nbond)
+__device__ __forceinline__ void rattle_pos(const ReplicaDev &rp, LaneD &C, int, double dd, double, bool a_end,
+                                           int other)
 {
-#pragma unroll
-    for (int j = 0; j < NC; ++j) {
-        if (j >= nc) continue;
-#pragma unroll
-        for (int t = 0; t < 3; ++t) C.V[j][t] = fmaf(rp.hdt_f, C.F[j][t] * C.invM[j], C.V[j][t]);
-    }
-    for (int k = 0; k < nbond; ++k) {
-        constexpr int a = 0, b = 1;
-        float r[3], dv[3];
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            r[t] = (float)(C.Xi[a][t] - C.Xi[b][t]) + (C.Xf[a][t] - C.Xf[b][t]);
-            dv[t] = C.V[a][t] - C.V[b][t];
-        }
-        const float inv = C.invM[a] + C.invM[b];
-        const float rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-        const float rv = dv[0] * r[0] + dv[1] * r[1] + dv[2] * r[2];
-        const float kk = rv / (rr * inv);
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            C.V[a][t] -= kk * r[t] * C.invM[a];
-            C.V[b][t] += kk * r[t] * C.invM[b];
-        }
+    const double oXold = __shfl_sync(0xffffffffu, C.Xold, other), oX = __shfl_sync(0xffffffffu, C.X, other);
+    const double oM = __shfl_sync(0xffffffffu, C.M, other);
+    const double ro = a_end ? C.Xold - oXold : oXold - C.Xold;
+    const double rn = a_end ? C.X - oX : oX - C.X;
+    const double Ma = a_end ? C.M : oM, Mb = a_end ? oM : C.M;
+    const double inv = 1.0 / Ma + 1.0 / Mb;
+    const double oo = sum3(ro * ro), on = sum3(rn * ro), nn = sum3(rn * rn);
+    const double qa = inv * inv * oo;
+    const double qb = 2.0 * inv * on;
+    const double qc = nn - dd * dd;
+    double disc = qb * qb - 4.0 * qa * qc;
+    if (disc < 0.0) disc = 0.0;
+    const double q = -0.5 * (qb + copysign(sqrt(disc), qb));
+    const double gmul = qc / q;
+    if (a_end) {
+        const double ca = gmul * ro / Ma;
+        C.X = C.X + ca;
+        C.V = C.V + ca / rp.dt;
+    } else {
+        const double cb = gmul * ro / Mb;
+        C.X = C.X - cb;
+        C.V = C.V - cb / rp.dt;
     }
 }
 
-__device__ __forceinline__ void kick_drift(const ReplicaDev &rp, ColRD &C, int nc)
+// Second half kick and RATTLE velocity stage.
+__device__ __forceinline__ void kick_rattle_vel(const ReplicaDev &rp, LaneM &C, int nbond, bool a_end, int other)
 {
-#pragma unroll
-    for (int j = 0; j < NC; ++j) {
-        if (j >= nc) continue;
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            C.V[j][t] = fma(rp.hdt, C.F[j][t] / C.M[j], C.V[j][t]);
-            C.Xold[j][t] = C.X[j][t];
-            C.X[j][t] = fma(rp.dt, C.V[j][t], C.X[j][t]);
-        }
-    }
+    C.V = fmaf(rp.hdt_f, C.F * C.invM, C.V);
+    if (nbond == 0) return;
+    const int oXi = __shfl_sync(0xffffffffu, C.Xi, other);
+    const float oXf = __shfl_sync(0xffffffffu, C.Xf, other), oV = __shfl_sync(0xffffffffu, C.V, other);
+    const float oinvM = __shfl_sync(0xffffffffu, C.invM, other);
+    const float r = a_end ? (float)(C.Xi - oXi) + (C.Xf - oXf) : (float)(oXi - C.Xi) + (oXf - C.Xf);
+    const float dv = a_end ? C.V - oV : oV - C.V;
+    const float ia = a_end ? C.invM : oinvM, ib = a_end ? oinvM : C.invM;
+    const float inv = ia + ib;
+    const float rr = sum3(r * r), rv = sum3(dv * r);
+    const float kk = rv / (rr * inv);
+    if (a_end) C.V -= kk * r * ia;
+    else C.V += kk * r * ib;
+}
+__device__ __forceinline__ void kick_rattle_vel(const ReplicaDev &rp, LaneD &C, int nbond, bool a_end, int other)
+{
+    C.V = fma(rp.hdt, C.F / C.M, C.V);
+    if (nbond == 0) return;
+    const double oX = __shfl_sync(0xffffffffu, C.X, other), oV = __shfl_sync(0xffffffffu, C.V, other);
+    const double oM = __shfl_sync(0xffffffffu, C.M, other);
+    const double r = a_end ? C.X - oX : oX - C.X;
+    const double dv = a_end ? C.V - oV : oV - C.V;
+    const double Ma = a_end ? C.M : oM, Mb = a_end ? oM : C.M;
+    const double inv = 1.0 / Ma + 1.0 / Mb;
+    const double rr = sum3(r * r), rv = sum3(dv * r);
+    const double kk = rv / (rr * inv);
+    if (a_end) C.V = C.V - kk * r / Ma;
+    else C.V = C.V + kk * r / Mb;
 }
 
-__device__ __forceinline__ void rattle_pos(const ReplicaDev &rp, ColRD &C, const BondDev *bond, int nbond)
+__device__ __forceinline__ void frames(const ReplicaDev &, LaneM &, int) {}
+__device__ __forceinline__ void frames(const ReplicaDev &rp, LaneD &C, int t)
 {
-    const double dt = rp.dt;
-    for (int k = 0; k < nbond; ++k) {
-        constexpr int a = 0, b = 1;
-        const double dd = bond[k].d;
-        double ro[3], rn[3];
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            ro[t] = C.Xold[a][t] - C.Xold[b][t];
-            rn[t] = C.X[a][t] - C.X[b][t];
-        }
-        const double inv = 1.0 / C.M[a] + 1.0 / C.M[b];
-        const double oo = ro[0] * ro[0] + ro[1] * ro[1] + ro[2] * ro[2];
-        const double on = rn[0] * ro[0] + rn[1] * ro[1] + rn[2] * ro[2];
-        const double nn = rn[0] * rn[0] + rn[1] * rn[1] + rn[2] * rn[2];
-        const double qa = inv * inv * oo;
-        const double qb = 2.0 * inv * on;
-        const double qc = nn - dd * dd;
-        double disc = qb * qb - 4.0 * qa * qc;
-        if (disc < 0.0) disc = 0.0;
-        const double q = -0.5 * (qb + copysign(sqrt(disc), qb));
-        const double gmul = qc / q;
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            const double ca = gmul * ro[t] / C.M[a];
-            const double cb = gmul * ro[t] / C.M[b];
-            C.X[a][t] = C.X[a][t] + ca;
-            C.X[b][t] = C.X[b][t] - cb;
-            C.V[a][t] = C.V[a][t] + ca / dt;
-            C.V[b][t] = C.V[b][t] - cb / dt;
-        }
-    }
+    const double L = (double)rp.L[t];
+    C.Xw = C.X - L * floor(C.X / L);
 }
 
-__device__ __forceinline__ void kick_rattle_vel(const ReplicaDev &rp, ColRD &C, int nc, const BondDev *bond, int nbond)
+// --- colloid positions seen by the particles ------------------------------------
+struct ColPM {
+    int Ci[NC][3];
+    float Xf[NC][3];
+};
+struct ColPD {
+    double Xw[NC][3];
+};
+__device__ __forceinline__ void broadcast(const LaneM &C, ColPM &P)
 {
 #pragma unroll
-    for (int j = 0; j < NC; ++j) {
-        if (j >= nc) continue;
-#pragma unroll
-        for (int t = 0; t < 3; ++t) C.V[j][t] = fma(rp.hdt, C.F[j][t] / C.M[j], C.V[j][t]);
-    }
-    for (int k = 0; k < nbond; ++k) {
-        constexpr int a = 0, b = 1;
-        double r[3], dv[3];
+    for (int j = 0; j < NC; ++j)
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
-            r[t] = C.X[a][t] - C.X[b][t];
-            dv[t] = C.V[a][t] - C.V[b][t];
+            P.Ci[j][t] = __shfl_sync(0xffffffffu, C.Ci, 3 * j + t);
+            P.Xf[j][t] = __shfl_sync(0xffffffffu, C.Xf, 3 * j + t);
         }
-        const double inv = 1.0 / C.M[a] + 1.0 / C.M[b];
-        const double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-        const double rv = dv[0] * r[0] + dv[1] * r[1] + dv[2] * r[2];
-        const double kk = rv / (rr * inv);
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            C.V[a][t] = C.V[a][t] - kk * r[t] / C.M[a];
-            C.V[b][t] = C.V[b][t] + kk * r[t] / C.M[b];
-        }
-    }
 }
-
-__device__ __forceinline__ void frames(const ReplicaDev &, ColRM &, int) {}
-__device__ __forceinline__ void frames(const ReplicaDev &rp, ColRD &C, int nc)
+__device__ __forceinline__ void broadcast(const LaneD &C, ColPD &P)
 {
 #pragma unroll
-    for (int j = 0; j < NC; ++j) {
-        if (j >= nc) continue;
+    for (int j = 0; j < NC; ++j)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const double L = (double)rp.L[k];
-            C.Xw[j][k] = C.X[j][k] - L * floor(C.X[j][k] / L);
-        }
-    }
-}
-
-__device__ __forceinline__ void set_forces(ColRM &C, const long long *tot, int nc)
-{
-#pragma unroll
-    for (int j = 0; j < NC; ++j) {
-        if (j >= nc) continue;
-#pragma unroll
-        for (int t = 0; t < 3; ++t) C.F[j][t] = __ll2float_rn(tot[3 * j + t]) * 0x1p-40f;
-    }
-}
-__device__ __forceinline__ void set_forces(ColRD &C, const long long *tot, int nc)
-{
-#pragma unroll
-    for (int j = 0; j < NC; ++j) {
-        if (j >= nc) continue;
-#pragma unroll
-        for (int t = 0; t < 3; ++t) C.F[j][t] = (double)tot[3 * j + t] * 0x1p-40;
-    }
+        for (int t = 0; t < 3; ++t) P.Xw[j][t] = __shfl_sync(0xffffffffu, C.Xw, 3 * j + t);
 }
 
 // --- particle side ----------------------------------------------------------
+// round(f 2^40) to the nearest even integer, exactly as one float -> int64
+// conversion would give it, by two 32-bit conversions: with h = f 2^9
+// rounded to an integer, f - h 2^-9 is exact (Sterbenz) and at most 2^-10 in
+// magnitude, and h 2^31 is even, so the ties round the same way.  Valid for
+// |f| < 2^22.
+__device__ __forceinline__ long long fx40(float f)
+{
+    const float h = rintf(f * 0x1p9f);
+    const float r = f - h * 0x1p-9f;
+    return ((long long)__float2int_rn(h) << 31) + (long long)__float2int_rn(r * 0x1p40f);
+}
+
 // WCA force on one solvent particle (§1.4); the reaction on colloid j goes to
-// acc in fixed point.
-__device__ __forceinline__ void pforce(const ReplicaDev &rp, const FShared &S, const ColRM &C, int nc, FWorkM &w,
-                                       long long acc[NC][3])
+// acc in fixed point.  inside: the particle is within the cut-off of a
+// catalytic colloid (§1.5).
+__device__ __forceinline__ void pforce(const ReplicaDev &rp, const FShared &S, const ColPM &C, int nc, FWorkM &w,
+                                       long long acc[NC][3], bool &inside)
 {
     w.f[0] = w.f[1] = w.f[2] = 0.0f;
+    inside = false;
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
         if (j >= nc) continue;
@@ -297,6 +289,7 @@ __device__ __forceinline__ void pforce(const ReplicaDev &rp, const FShared &S, c
         const float eps = (w.fid & F_B) ? S.epsBf[j] : S.epsAf[j];
         const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
         if (r2 < S.rc2f[j]) {
+            inside = inside || S.cat[j];
             const float ir2 = 1.0f / r2;
             const float s2 = S.sigf[j] * S.sigf[j] * ir2;
             const float s6 = s2 * s2 * s2;
@@ -305,7 +298,7 @@ __device__ __forceinline__ void pforce(const ReplicaDev &rp, const FShared &S, c
             for (int k = 0; k < 3; ++k) {
                 const float fk = fr * d[k];
                 w.f[k] = w.f[k] + fk;
-                acc[j][k] -= __float2ll_rn(fk * 0x1p40f);
+                acc[j][k] -= fx40(fk);
             }
         }
     }
@@ -313,10 +306,11 @@ __device__ __forceinline__ void pforce(const ReplicaDev &rp, const FShared &S, c
     for (int k = 0; k < 3; ++k) w.f[k] = w.f[k] + rp.g_f[k];
 }
 
-__device__ __forceinline__ void pforce(const ReplicaDev &rp, const FShared &S, const ColRD &C, int nc, FWorkD &w,
-                                       long long acc[NC][3])
+__device__ __forceinline__ void pforce(const ReplicaDev &rp, const FShared &S, const ColPD &C, int nc, FWorkD &w,
+                                       long long acc[NC][3], bool &inside)
 {
     w.f[0] = w.f[1] = w.f[2] = 0.0;
+    inside = false;
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
         if (j >= nc) continue;
@@ -325,6 +319,7 @@ __device__ __forceinline__ void pforce(const ReplicaDev &rp, const FShared &S, c
         const double eps = (w.fid & F_B) ? S.epsB[j] : S.epsA[j];
         const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
         if (r2 < S.rc2[j]) {
+            inside = inside || S.cat[j];
             const double ir2 = 1.0 / r2;
             const double s2 = S.sig[j] * S.sig[j] * ir2;
             const double s6 = s2 * s2 * s2;
@@ -339,37 +334,6 @@ __device__ __forceinline__ void pforce(const ReplicaDev &rp, const FShared &S, c
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) w.f[k] = w.f[k] + rp.g[k];
-}
-
-__device__ __forceinline__ bool pinside(const ReplicaDev &rp, const FShared &S, const ColRM &C, int nc,
-                                        const FWorkM &w)
-{
-    bool in = false;
-#pragma unroll
-    for (int j = 0; j < NC; ++j) {
-        if (j >= nc) continue;
-        if (!S.cat[j]) continue;
-        float d[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) d[k] = (float)(w.c[k] - C.Ci[j][k]) + (w.o[k] - C.Xf[j][k]);
-        min_image(rp, d);
-        in = in || (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < S.rc2f[j]);
-    }
-    return in;
-}
-__device__ __forceinline__ bool pinside(const ReplicaDev &rp, const FShared &S, const ColRD &C, int nc,
-                                        const FWorkD &w)
-{
-    bool in = false;
-#pragma unroll
-    for (int j = 0; j < NC; ++j) {
-        if (j >= nc) continue;
-        if (!S.cat[j]) continue;
-        double d[3] = {w.x[0] - C.Xw[j][0], w.x[1] - C.Xw[j][1], w.x[2] - C.Xw[j][2]};
-        min_image(rp, d);
-        in = in || (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < S.rc2[j]);
-    }
-    return in;
 }
 
 // A tagged A particle that has left every catalytic range becomes B with
@@ -389,6 +353,9 @@ __device__ __forceinline__ uint32_t fcatalysis(const ReplicaDev &rp, uint32_t fi
     return fid;
 }
 
+// Velocity-Verlet particle update between two force evaluations: the second
+// half kick of the last sub-step (when there was one), the first half kick
+// and the drift of the next.
 __device__ __forceinline__ void pkick_drift(const ReplicaDev &rp, FWorkM &w, bool second)
 {
 #pragma unroll
@@ -422,59 +389,8 @@ __device__ __forceinline__ long long warp_sum64(long long x)
     return ((long long)H << 32) + ((long long)M << 16) + (long long)Lo;
 }
 
-// Warp sums of the fixed-point partials added into the round's buffer of the
-// cluster accumulator (CTA 0's shared memory).
-template <int CS>
-__device__ __forceinline__ void contribute(cg::cluster_group &cl, FShared &S, long long acc[NC][3], int nc, int buf,
-                                           int lane)
-{
-    unsigned long long mine = 0ull;
-#pragma unroll
-    for (int j = 0; j < NC; ++j) {
-        if (j >= nc) continue;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const long long x = warp_sum64(acc[j][k]);
-            if (lane == 3 * j + k) mine = (unsigned long long)x;
-        }
-    }
-    if (lane < 3 * nc && mine != 0ull) {
-        unsigned long long *dst = &S.tot[buf][lane];
-        if (CS > 1) dst = cl.map_shared_rank(dst, 0);
-        atomicAdd(dst, mine);
-    }
-}
-
-// Every thread reads the round's totals (broadcast reads of CTA 0's buffer).
-template <int CS>
-__device__ __forceinline__ void read_totals(cg::cluster_group &cl, FShared &S, int buf, int nc, long long *tot)
-{
-    unsigned long long *src = &S.tot[buf][0];
-    if (CS > 1) src = cl.map_shared_rank(src, 0);
-#pragma unroll
-    for (int i = 0; i < 3 * NC; ++i)
-        tot[i] = i < 3 * nc ? (long long)((volatile unsigned long long *)src)[i] : 0ll;
-}
-
-template <int CS>
-__device__ __forceinline__ void round_barrier(cg::cluster_group &cl)
-{
-    if (CS > 1) cl.sync();
-    else __syncthreads();
-}
-
-
-__device__ __forceinline__ void zero_acc(long long acc[NC][3])
-{
-#pragma unroll
-    for (int j = 0; j < NC; ++j)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) acc[j][k] = 0;
-}
-
-template <bool MIXED, typename ColR, typename W>
-__device__ __forceinline__ void load_particle(const Dev &d, const ReplicaDev &rp, const FShared &S, const ColR &C, int nc,
-                                              int slot, int rbuf, W &w, long long acc[NC][3])
+template <bool MIXED, typename W>
+__device__ __forceinline__ void load_particle(const Dev &d, int slot, int rbuf, W &w)
 {
     w.slot = slot;
     if constexpr (MIXED) {
@@ -486,16 +402,19 @@ __device__ __forceinline__ void load_particle(const Dev &d, const ReplicaDev &rp
         for (int q = 0; q < 3; ++q) { w.x[q] = rec.x[q]; w.v[q] = rec.v[q]; }
         w.fid = rec.fid;
     }
-    pforce(rp, S, C, nc, w, acc);
 }
 
-template <typename ColR, typename W>
-__device__ __forceinline__ void substep_particle(const ReplicaDev &rp, const FShared &S, const ColR &C, int nc, W &w,
-                                                 long long acc[NC][3], uint32_t step, int s)
+// One round of one particle: the force at its current position (round > 0:
+// then the catalytic test of sub-step round - 1), and, unless this was the
+// last round, the move to its position of the next round.
+template <typename ColT, typename W>
+__device__ __forceinline__ void round_particle(const ReplicaDev &rp, const FShared &S, const ColT &P, int nc, W &w,
+                                               long long acc[NC][3], uint32_t step, int round, int n_md)
 {
-    pkick_drift(rp, w, s > 0);
-    pforce(rp, S, C, nc, w, acc);
-    w.fid = fcatalysis(rp, w.fid, pinside(rp, S, C, nc, w), step, s);
+    bool inside;
+    pforce(rp, S, P, nc, w, acc, inside);
+    if (round > 0) w.fid = fcatalysis(rp, w.fid, inside, step, round - 1);
+    if (round < n_md) pkick_drift(rp, w, round > 0);
 }
 
 __device__ __forceinline__ void finish_particle(const Dev &d, const ReplicaDev &rp, FWorkM &w, const double sh[3],
@@ -528,159 +447,277 @@ __device__ __forceinline__ void finish_particle(const Dev &d, const ReplicaDev &
     if (do_bin) bin_particle(d, bbuf, rp.cell_off + cell_key_d(rp, w.x, sh), w.slot);
 }
 
+// --- the cluster exchange of the force partials -------------------------------
+// Warp 0 of every CTA writes the CTA's six fixed-point partials into slot
+// [rank] of every CTA's buffer for the round's parity with st.async; the bytes
+// are counted on that CTA's mbarrier for the parity, whose single arrival is
+// warp 0's own expect-tx.  Every warp waits for the phase and sums the slots
+// in rank order.  Round r + 2 reuses the buffer and the barrier of round r: a
+// CTA sends round r + 2 only after its CTA barrier of round r + 2, which all
+// its warps reach after reading round r, and after every CTA sent round
+// r + 1, which each does after its own warps read round r.
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t a, int rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_async_v2(uint32_t a, unsigned long long x, unsigned long long y, uint32_t bar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.u64 [%0], {%1, %2}, [%3];" ::"r"(a),
+                 "l"(x), "l"(y), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint32_t a, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, unsigned bytes)
+{
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(a),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t a, unsigned parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+
+constexpr unsigned MDF_TX_BYTES = 6 * 8;   // partials one CTA sends to one CTA per round
+
+// Warp 0 of a CTA: its CTA's partials (lane l < 6 holds component l) to every
+// CTA of the cluster, as three 16-byte st.async per destination spread over
+// the lanes.
+template <int CS>
+__device__ __forceinline__ void send_partials(FShared &S, int rank, int b, int lane, long long mine)
+{
+    const uint32_t bar = smem_addr(&S.mbar[b]);
+    if (lane == 0) mbar_expect_tx(bar, (unsigned)(CS * MDF_TX_BYTES));
+    const uint32_t src = smem_addr(&S.part[b][rank][0]);
+#pragma unroll
+    for (int k = 0; k < (3 * CS + 31) / 32; ++k) {
+        const int item = lane + 32 * k;   // destination item / 3, pair item % 3
+        const int pi = item % 3;
+        const long long x = __shfl_sync(0xffffffffu, mine, 2 * pi);
+        const long long y = __shfl_sync(0xffffffffu, mine, 2 * pi + 1);
+        if (item < 3 * CS) {
+            const int q = item / 3;
+            st_async_v2(cluster_addr(src + 16u * (uint32_t)pi, q), (unsigned long long)x, (unsigned long long)y,
+                        cluster_addr(bar, q));
+        }
+    }
+}
+
 template <bool MIXED, int CS>
-__global__ void __launch_bounds__(FGeom<CS>::NT, 1) k_md_fast(Dev d, uint32_t step, int rbuf, int bbuf, int do_bin)
+__global__ void __launch_bounds__(MDF_NT, 1) k_md_fast(Dev d, uint32_t step, int rbuf, int bbuf, int do_bin)
 {
     using W = typename std::conditional<MIXED, FWorkM, FWorkD>::type;
-    using ColR = typename std::conditional<MIXED, ColRM, ColRD>::type;
-    constexpr int NT = FGeom<CS>::NT;
+    using Lane = typename std::conditional<MIXED, LaneM, LaneD>::type;
+    using ColP = typename std::conditional<MIXED, ColPM, ColPD>::type;
+    using R = typename std::conditional<MIXED, float, double>::type;
     __shared__ FShared S;
     __shared__ ReplicaDev s_rp;
-    __shared__ BondDev s_bond[MAXB];
     cg::cluster_group cl = cg::this_cluster();
     const int r = blockIdx.x / CS;
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int rank = CS == 1 ? 0 : (int)cl.block_rank();
     if (tid == 0) s_rp = d.rep[r];
     __syncthreads();
     const ReplicaDev &rp = s_rp;
     if (rp.n_col == 0) return;   // uniform over the cluster
-    const int nc = rp.n_col, nbond = rp.n_bond;
-    if (tid == 0) S.nn = min(d.near_count[r], rp.n_part);
+    const int nc = rp.n_col, nbond = rp.n_bond, n_md = rp.n_md;
+    if (tid == 0) {
+        S.nn = min(d.near_count[r], rp.n_part);
+        S.dead = 0;
+        if (CS > 1) {
+            mbar_init(smem_addr(&S.mbar[0]), 1u);
+            mbar_init(smem_addr(&S.mbar[1]), 1u);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+    }
     if (tid < nc) {
         const int g = rp.col_off + tid;
         S.sig[tid] = d.colSig[g]; S.epsA[tid] = d.colEpsA[g]; S.epsB[tid] = d.colEpsB[g]; S.rc2[tid] = d.colRc2[g];
-        S.sigf[tid] = d.colSig_f[g]; S.epsAf[tid] = d.colEpsA_f[g]; S.epsBf[tid] = d.colEpsB_f[g];
+        S.sigf[tid] = d.colSig_f[g];
+        S.epsAf[tid] = d.colEpsA_f[g]; S.epsBf[tid] = d.colEpsB_f[g];
         S.rc2f[tid] = d.colRc2_f[g];
         S.cat[tid] = d.colCat[g];
     }
-    if (tid < nbond) s_bond[tid] = d.bonds[rp.bond_off + tid];
-    if (tid < 3 * 3 * NC) (&S.tot[0][0])[tid] = 0ull;
 
-    // the complete colloid state, in every thread
-    ColR C;
-#pragma unroll
-    for (int j = 0; j < NC; ++j) {
-        const int g = rp.col_off + (j < nc ? j : 0);
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            if constexpr (MIXED) {
-                C.Xi[j][t] = d.colXi[3 * g + t];
-                C.Xf[j][t] = d.colXf[3 * g + t];
-                C.Ci[j][t] = d.colCi[3 * g + t];
-                C.V[j][t] = d.colVf[3 * g + t];
-                C.Xoi[j][t] = C.Xi[j][t]; C.Xof[j][t] = C.Xf[j][t];
-                C.X0i[j][t] = C.Xi[j][t]; C.X0f[j][t] = C.Xf[j][t];
-                C.F[j][t] = 0.0f;
-            } else {
-                C.X[j][t] = d.colX[3 * g + t];
-                C.V[j][t] = d.colV[3 * g + t];
-                C.Xold[j][t] = C.X[j][t]; C.X0[j][t] = C.X[j][t];
-                C.F[j][t] = 0.0;
-            }
+    // this lane's colloid component (lanes >= 3 nc: a copy of component 0)
+    const int cl_l = lane < 3 * nc ? lane : 0;
+    const int cj = cl_l / 3, ct = cl_l % 3;
+    const bool a_end = cj == 0;
+    const int other = nc == 2 ? (cj == 0 ? cl_l + 3 : cl_l - 3) : cl_l;
+    const R bond_d = nbond > 0 ? (R)d.bonds[rp.bond_off].d : R(0);
+    Lane C;
+    {
+        const int g = rp.col_off + cj;
+        if constexpr (MIXED) {
+            C.Xi = d.colXi[3 * g + ct];
+            C.Xf = d.colXf[3 * g + ct];
+            C.Ci = d.colCi[3 * g + ct];
+            C.V = d.colVf[3 * g + ct];
+            C.Xoi = C.Xi; C.Xof = C.Xf;
+            C.X0i = C.Xi; C.X0f = C.Xf;
+            C.F = 0.0f;
+            C.invM = d.colInvM_f[g];
+        } else {
+            C.X = d.colX[3 * g + ct];
+            C.V = d.colV[3 * g + ct];
+            C.Xold = C.X; C.X0 = C.X;
+            C.F = 0.0;
+            C.M = d.colM[g];
         }
-        if constexpr (MIXED) C.invM[j] = d.colInvM_f[g];
-        else C.M[j] = d.colM[g];
     }
-    frames(rp, C, nc);
+    frames(rp, C, ct);
+    const R idt = R(1) / (MIXED ? (R)rp.dt_f : (R)rp.dt);
     __syncthreads();
-    // every CTA has read near_count before CTA 0 may reset it
+    // every CTA has read near_count and set up its barriers before any
+    // remote access and before CTA 0 resets the count
     if (CS > 1) cl.sync();
 
     const int nn = S.nn;
     const int *list = d.near_list + rp.part_off;
     W *work = reinterpret_cast<W *>(d.md_work) + rp.part_off;
-    const int first = rank * NT + tid;
-    const int stride = CS * NT;
-    const int over = first + PPT * stride;   // beyond the registers: global memory
-    long long acc[NC][3];
-    long long tot[3 * NC];
-    W reg[PPT];
-    // round 0: forces at the start of the interval
-    zero_acc(acc);
+    const int first = rank * MDF_NT + tid;
+    const int stride = CS * MDF_NT;
+    const int over = first + MDF_PPT * stride;   // beyond the registers: global memory
+    W reg[MDF_PPT];
 #pragma unroll
-    for (int p = 0; p < PPT; ++p)
-        if (first + p * stride < nn) load_particle<MIXED>(d, rp, S, C, nc, list[first + p * stride], rbuf, reg[p], acc);
+    for (int p = 0; p < MDF_PPT; ++p)
+        if (first + p * stride < nn) load_particle<MIXED>(d, list[first + p * stride], rbuf, reg[p]);
     for (int k = over; k < nn; k += stride) {
         W w;
-        load_particle<MIXED>(d, rp, S, C, nc, list[k], rbuf, w, acc);
+        load_particle<MIXED>(d, list[k], rbuf, w);
         work[k] = w;
     }
-    contribute<CS>(cl, S, acc, nc, 0, lane);
-    round_barrier<CS>(cl);
-    read_totals<CS>(cl, S, 0, nc, tot);
-    set_forces(C, tot, nc);
 
-    for (int s = 0; s < rp.n_md; ++s) {
-        const int buf = (s + 1) % 3;
-        // CTA 0 clears the buffer of round s + 2 (last read before this barrier)
-        if (rank == 0 && tid < 3 * nc) S.tot[(s + 2) % 3][tid] = 0ull;
-        // colloids: first half kick, drift, RATTLE position stage
-        kick_drift(rp, C, nc);
-        rattle_pos(rp, C, s_bond, nbond);
-        frames(rp, C, nc);
-        // solvent: second half kick of the previous sub-step, first half
-        // kick and drift of this one, new forces, catalytic conversion
-        zero_acc(acc);
+    long long acc[NC][3];
+    // round 0: forces at the start of the interval; round k (1 <= k <= n_md):
+    // forces at the end of sub-step k - 1
+    for (int round = 0; round <= n_md; ++round) {
+        const int b = round & 1;
+        ColP P;
+        broadcast(C, P);
 #pragma unroll
-        for (int p = 0; p < PPT; ++p)
-            if (first + p * stride < nn) substep_particle(rp, S, C, nc, reg[p], acc, step, s);
+        for (int j = 0; j < NC; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) acc[j][k] = 0;
+#pragma unroll
+        for (int p = 0; p < MDF_PPT; ++p)
+            if (first + p * stride < nn) round_particle(rp, S, P, nc, reg[p], acc, step, round, n_md);
         for (int k = over; k < nn; k += stride) {
             W w = work[k];
-            substep_particle(rp, S, C, nc, w, acc, step, s);
+            round_particle(rp, S, P, nc, w, acc, step, round, n_md);
             work[k] = w;
         }
-        contribute<CS>(cl, S, acc, nc, buf, lane);
-        round_barrier<CS>(cl);
-        read_totals<CS>(cl, S, buf, nc, tot);
-        set_forces(C, tot, nc);
-        // colloids: second half kick, RATTLE velocity stage
-        kick_rattle_vel(rp, C, nc, s_bond, nbond);
+        long long ws = 0;
+#pragma unroll
+        for (int j = 0; j < NC; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const long long x = warp_sum64(acc[j][k]);
+                if (lane == 3 * j + k) ws = x;
+            }
+        if (lane < 3 * NC) S.wpart[b][wid][lane] = ws;
+        __syncthreads();
+        // the CTA's partials (lane l < 6: component l, warps in order)
+        long long tot = 0;
+        if (lane < 3 * NC)
+#pragma unroll
+            for (int w = 0; w < MDF_NW; ++w) tot += S.wpart[b][w][lane];
+        if constexpr (CS > 1) {
+            if (wid == 0) send_partials<CS>(S, rank, b, lane, tot);
+            const uint32_t bar = smem_addr(&S.mbar[b]);
+            const unsigned parity = (unsigned)(round >> 1) & 1u;
+            if (!S.dead) {
+                int spins = 0;
+                while (!mbar_try_wait_cluster(bar, parity)) {
+                    if (++spins > MDF_SPIN_LIMIT) {
+                        if (lane == 0) {
+                            atomicOr(&d.err[ERR_TIMEOUT], 1u);
+                            S.dead = 1;
+                        }
+                        break;
+                    }
+                }
+                __syncwarp();
+            }
+            tot = 0;
+            if (lane < 3 * NC)
+#pragma unroll
+                for (int q = 0; q < CS; ++q) tot += (long long)S.part[b][q][lane];
+        }
+        // the colloids: force of this round, end of sub-step round - 1
+        // (second half kick, RATTLE velocity stage), start of sub-step round
+        // (first half kick, drift, RATTLE position stage)
+        set_force(C, __shfl_sync(0xffffffffu, tot, cl_l));
+        if (round > 0) kick_rattle_vel(rp, C, nbond, a_end, other);
+        if (round < n_md) {
+            kick_drift(rp, C, ct);
+            if (nbond > 0) rattle_pos(rp, C, ct, bond_d, idt, a_end, other);
+            frames(rp, C, ct);
+        }
     }
 
     // last half kick, wrap, write back (and bin for the collision of `step`)
     double sh[3];
     grid_shift(rp.seed, step, sh);
 #pragma unroll
-    for (int p = 0; p < PPT; ++p)
+    for (int p = 0; p < MDF_PPT; ++p)
         if (first + p * stride < nn) finish_particle(d, rp, reg[p], sh, rbuf, bbuf, do_bin);
     for (int k = over; k < nn; k += stride) {
         W w = work[k];
         finish_particle(d, rp, w, sh, rbuf, bbuf, do_bin);
     }
-    // CTA 0, thread 0: colloids back to memory, skin check, near list reset
-    if (rank == 0 && tid == 0) {
-        bool bad = false;
-#pragma unroll
-        for (int j = 0; j < NC; ++j) {
-            if (j >= nc) continue;
-            const int g = rp.col_off + j;
+    // CTA 0, warp 0: colloids back to memory, skin check, near list reset
+    if (rank == 0 && wid == 0) {
+        const int g = rp.col_off + cj;
+        R e;
+        if constexpr (MIXED) e = (float)(C.Xi - C.X0i) + (C.Xf - C.X0f);
+        else e = C.X - C.X0;
+        const R e0 = __shfl_sync(0xffffffffu, e, 3 * cj), e1 = __shfl_sync(0xffffffffu, e, 3 * cj + 1);
+        const R e2 = __shfl_sync(0xffffffffu, e, 3 * cj + 2);
+        if (lane < 3 * nc) {
             if constexpr (MIXED) {
-                float e[3];
-                for (int t = 0; t < 3; ++t) {
-                    d.colXi[3 * g + t] = C.Xi[j][t];
-                    d.colXf[3 * g + t] = C.Xf[j][t];
-                    d.colVf[3 * g + t] = C.V[j][t];
-                    d.colCi[3 * g + t] = C.Ci[j][t];
-                    e[t] = (float)(C.Xi[j][t] - C.X0i[j][t]) + (C.Xf[j][t] - C.X0f[j][t]);
-                }
-                const float dd = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
-                if (!(dd <= rp.skin_f * rp.skin_f)) bad = true;
+                d.colXi[3 * g + ct] = C.Xi;
+                d.colXf[3 * g + ct] = C.Xf;
+                d.colVf[3 * g + ct] = C.V;
+                d.colCi[3 * g + ct] = C.Ci;
+            } else {
+                d.colX[3 * g + ct] = C.X;
+                d.colV[3 * g + ct] = C.V;
+            }
+        }
+        bool bad = false;
+        if (lane < 3 * nc && ct == 0) {
+            if constexpr (MIXED) {
+                const float dd = e0 * e0 + e1 * e1 + e2 * e2;
+                bad = !(dd <= rp.skin_f * rp.skin_f);
             } else {
                 double dd = 0.0;
-                for (int t = 0; t < 3; ++t) {
-                    d.colX[3 * g + t] = C.X[j][t];
-                    d.colV[3 * g + t] = C.V[j][t];
-                    const double e = C.X[j][t] - C.X0[j][t];
-                    dd = dd + e * e;
-                }
-                if (!(dd <= rp.skin * rp.skin)) bad = true;
+                dd = dd + e0 * e0;
+                dd = dd + e1 * e1;
+                dd = dd + e2 * e2;
+                bad = !(dd <= rp.skin * rp.skin);
             }
         }
         if (bad) atomicAdd(&d.err[ERR_SKIN], 1u);
-        d.near_count[r] = 0;
+        if (lane == 0) d.near_count[r] = 0;
     }
-    if (CS > 1) cl.sync();   // CTA 0's accumulator outlives every remote access
+    if (CS > 1) cl.sync();   // no CTA leaves while another may still write its shared memory
 }
 
 template <bool MIXED, int CS>
@@ -689,7 +726,7 @@ static void launch_fast_cs(const Dev &d, uint32_t step, int rbuf, int bbuf, int 
     if (CS > 8) cudaFuncSetAttribute(k_md_fast<MIXED, CS>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(d.n_rep * CS), 1, 1);
-    cfg.blockDim = dim3(FGeom<CS>::NT, 1, 1);
+    cfg.blockDim = dim3(MDF_NT, 1, 1);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -718,7 +755,7 @@ int md_fast_max_cluster(bool mixed)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(16, 1, 1);
-    cfg.blockDim = dim3(FGeom<16>::NT, 1, 1);
+    cfg.blockDim = dim3(MDF_NT, 1, 1);
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 16;

@@ -25,6 +25,7 @@ namespace rmpcd {
 constexpr int CPT = 128;           // cells per tile of the cell pass
 constexpr int CP_THREADS = 256;    // threads per cell-pass CTA
 constexpr int CP_WARPS = CP_THREADS / 32;
+constexpr int CP_CHUNK = 8;        // cells a warp of the cell pass takes at a time
 constexpr int CP_WPC_M = 192;      // particles one warp stages at once (mixed records)
 constexpr int CP_WPC_D = 96;       // particles one warp stages at once (fp64 records)
 constexpr int CP_MAX_CAP = 768;    // largest bucket_cap (a crowded tile uses the whole CTA)
@@ -479,6 +480,16 @@ __device__ __forceinline__ bool near_test_m(const ReplicaDev &rp, int nc, const 
         if (r2 < R * R) return true;
     }
     return false;
+}
+
+// x 2^-40 of a 64-bit fixed-point force total as FP32, by two 32-bit
+// conversions (within one unit in the last place of the correctly rounded
+// value; a 64-bit conversion has several times the latency).
+__device__ __forceinline__ float fixed40_to_float(long long x)
+{
+    const int hi = (int)(x >> 32);
+    const unsigned lo = (unsigned)x;
+    return fmaf((float)hi, 0x1p-8f, (float)lo * 0x1p-40f);
 }
 
 // Acquire / release accesses for the look-back scan.
