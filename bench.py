@@ -40,7 +40,8 @@ UNIT = "particle-steps/s"
 ALG_BYTES = {"mixed": 64, "fp64": 112}
 L2_FLUSH_BYTES = 256 << 20
 KERNEL_NAMES = {"cellpass": "k_cellpass", "md": "k_md", "prime": "k_particles", "obs": "k_obs_reduce"}
-KERNEL_SOURCES = ["rmpcd_common.cuh", "rmpcd_kernels.cuh", "k_cellpass.cu", "k_md.cu", "k_particles.cu"]
+KERNEL_SOURCES = ["rmpcd_common.cuh", "rmpcd_kernels.cuh", "k_cellpass.cu", "k_md.cu", "k_md_fast.cu",
+                  "k_particles.cu", "capi.cu"]
 
 
 def workload(name, precision, seed_offset=0):
@@ -328,6 +329,9 @@ def main():
     phases = {k: v_ for k, v_ in timers.items() if v_["launches"] > 0}
     dominant = max(phases, key=lambda k: phases[k]["ms"])
     peak, peak_src = measured_peaks()
+    kernel_names = dict(KERNEL_NAMES)
+    if obs["md_kernel"] == 2:
+        kernel_names["md"] = "k_md_fast"
     kernels = {}
     for k, t in phases.items():
         avg_ms = t["ms"] / t["launches"]
@@ -335,20 +339,25 @@ def main():
         if k == "cellpass":
             alg = n * ALG_BYTES[args.precision]
             entry.update({"alg_bytes_per_launch": alg, "achieved_gbs": alg / (avg_ms / 1e3) / 1e9})
-        kernels[KERNEL_NAMES[k]] = entry
+        if k == "md":
+            entry["us_per_substep"] = 1e3 * avg_ms / cfg["n_md"]
+        kernels[kernel_names[k]] = entry
     cp = phases["cellpass"]
     cp_avg_s = cp["ms"] / cp["launches"] / 1e3
     alg = n * ALG_BYTES[args.precision]
     achieved = alg / cp_avg_s / 1e9
     roofline = {"kernel": "k_cellpass", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": ncu_traffic("k_cellpass", args.workload, args.precision),
-                "peak_source": f"{peak_src} hbm_gbs", "dominant_kernel": KERNEL_NAMES[dominant],
+                "peak_source": f"{peak_src} hbm_gbs", "dominant_kernel": kernel_names[dominant],
                 "alg_bytes_per_particle": ALG_BYTES[args.precision]}
     if dominant == "md":
         md = phases["md"]
-        roofline["note"] = ("k_md (near-colloid velocity-Verlet, %d dependent sub-steps in one CTA) takes %.0f%% of "
-                            "the step and is latency-bound; the HBM roofline is that of the cell pass"
-                            % (cfg["n_md"], 100 * md["ms"] / sum(p["ms"] for p in phases.values())))
+        roofline["note"] = ("%s (near-colloid velocity-Verlet: %d dependent sub-steps on one thread-block cluster, "
+                            "%.2f us each) takes %.0f%% of the step and is latency-bound (no DRAM or ALU roof "
+                            "applies); the HBM roofline reported is that of the cell pass, the bandwidth-bound "
+                            "part of the step" % (kernel_names["md"], cfg["n_md"],
+                                                  1e3 * md["ms"] / md["launches"] / cfg["n_md"],
+                                                  100 * md["ms"] / sum(p["ms"] for p in phases.values())))
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,

@@ -256,7 +256,8 @@ __device__ __forceinline__ void cells_D_warp8(const Dev &d, const CellPassArgs &
             vcm[1] = (s1 + sd * g1) / (float)(n + nv);
             vcm[2] = (s2 + sd * g2) / (float)(n + nv);
         } else {
-            vcm[0] = s0 / (float)n; vcm[1] = s1 / (float)n; vcm[2] = s2 / (float)n;
+            const float inv = __frcp_rn((float)n);
+            vcm[0] = s0 * inv; vcm[1] = s1 * inv; vcm[2] = s2 * inv;
         }
     }
     int slab = -1;
@@ -274,6 +275,11 @@ __device__ __forceinline__ void cells_D_warp8(const Dev &d, const CellPassArgs &
         }
 #pragma unroll
     for (int o = 1; o < 4; o <<= 1) u2 = fmaxf(u2, __shfl_xor_sync(0xffffffffu, u2, o));
+    // lanes 0 and 1 of a cell draw together: the first rotation-axis attempt
+    // and the bulk-reaction draw (one Philox evaluation for both)
+    U4 w0 = {0u, 0u, 0u, 0u};
+    if (q < 2 && (q == 0 ? collide : ((opts & CP_REACT) && rp.bulk_on && nB > 0)))
+        w0 = philox((uint32_t)lc, a.step, q == 0 ? P_ROT : P_REACT, 0u, rp.seed);
     if (!cv) return;
     if (q == 0) {
         T.mode[c] = 0;
@@ -299,14 +305,14 @@ __device__ __forceinline__ void cells_D_warp8(const Dev &d, const CellPassArgs &
             T.mode[c] = 2;
         } else if (collide) {
             float ax[3];
-            rotation_axis<float>(rp.seed, a.step, (uint32_t)lc, ax);
+            rotation_axis_from<float>(rp.seed, a.step, (uint32_t)lc, w0, ax);
             for (int k = 0; k < 3; ++k) { T.vcm[c][k] = vcm[k]; T.ax[c][k] = ax[k]; }
             T.mode[c] = 1;
         }
     } else if (q == 1) {
         T.react[c] = -1;
         if ((opts & CP_REACT) && rp.bulk_on && nB > 0) {
-            U4 w = philox((uint32_t)lc, a.step, P_REACT, 0u, rp.seed);
+            const U4 &w = w0;
             if ((unsigned long long)w.x < d.bulk_thr[rp.thr_off + nB]) {
                 const int pick = (int)(((unsigned long long)w.y * (unsigned long long)nB) >> 32);
                 for (int i = 0, seen = 0; i < n; ++i) {

@@ -135,10 +135,7 @@ __device__ __forceinline__ void force_m(const ReplicaDev &rp, MDShared<true> &S,
         const float eps = (fid & F_B) ? S.epsBf[j] : S.epsAf[j];
         const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
         if (r2 < S.rc2f[j]) {
-            const float ir2 = 1.0f / r2;
-            const float s2 = S.sigf[j] * S.sigf[j] * ir2;
-            const float s6 = s2 * s2 * s2;
-            const float fr = 24.0f * eps * s6 * (2.0f * s6 - 1.0f) * ir2;
+            const float fr = wca_fr_m(eps, S.sigf[j], r2);
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const float fk = fr * d[k];
@@ -401,7 +398,7 @@ __device__ void rattle_pos_w(const ReplicaDev &rp, MDShared<true> &S, int lane)
         float disc = qb * qb - 4.0f * qa * qc;
         if (disc < 0.0f) disc = 0.0f;
         const float q = -0.5f * (qb + copysignf(sqrtf(disc), qb));
-        const float gmul = qc / q;
+        const float gmul = fdiv_m(qc, q);
         __syncwarp();
         if (lane < 3) {
             const float ca = gmul * ro * C.invM[a];
@@ -428,7 +425,7 @@ __device__ void rattle_vel_w(MDShared<true> &S, int lane)
         const float dv = C.V[a][t] - C.V[b][t];
         const float inv = C.invM[a] + C.invM[b];
         const float rr = sum3(r * r), rv = sum3(dv * r);
-        const float kk = rv / (rr * inv);
+        const float kk = fdiv_m(rv, rr * inv);
         __syncwarp();
         if (lane < 3) {
             C.V[a][t] -= kk * r * C.invM[a];

@@ -152,7 +152,7 @@ __device__ __forceinline__ void rattle_pos(const ReplicaDev &rp, LaneM &C, int t
     float disc = qb * qb - 4.0f * qa * qc;
     if (disc < 0.0f) disc = 0.0f;
     const float q = -0.5f * (qb + copysignf(sqrtf(disc), qb));
-    const float gmul = qc / q;
+    const float gmul = fdiv_m(qc, q);
     if (a_end) {
         const float ca = gmul * ro * ia;
         C.Xf += ca;
@@ -205,7 +205,7 @@ __device__ __forceinline__ void kick_rattle_vel(const ReplicaDev &rp, LaneM &C, 
     const float ia = a_end ? C.invM : oinvM, ib = a_end ? oinvM : C.invM;
     const float inv = ia + ib;
     const float rr = sum3(r * r), rv = sum3(dv * r);
-    const float kk = rv / (rr * inv);
+    const float kk = fdiv_m(rv, rr * inv);
     if (a_end) C.V -= kk * r * ia;
     else C.V += kk * r * ib;
 }
@@ -273,37 +273,36 @@ __device__ __forceinline__ long long fx40(float f)
 
 // WCA force on one solvent particle (§1.4); the reaction on colloid j goes to
 // acc in fixed point.  inside: the particle is within the cut-off of a
-// catalytic colloid (§1.5).
+// catalytic colloid (§1.5).  Both colloids are evaluated without branches so
+// that their dependency chains overlap; a colloid out of range contributes
+// nothing (selects, so the sums are the same as with a branch).
 __device__ __forceinline__ void pforce(const ReplicaDev &rp, const FShared &S, const ColPM &C, int nc, FWorkM &w,
                                        long long acc[NC][3], bool &inside)
 {
-    w.f[0] = w.f[1] = w.f[2] = 0.0f;
-    inside = false;
+    float d[NC][3], fr[NC];
+    bool in[NC];
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
-        if (j >= nc) continue;
-        float d[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) d[k] = (float)(w.c[k] - C.Ci[j][k]) + (w.o[k] - C.Xf[j][k]);
-        min_image(rp, d);
+        for (int k = 0; k < 3; ++k) d[j][k] = (float)(w.c[k] - C.Ci[j][k]) + (w.o[k] - C.Xf[j][k]);
+        min_image(rp, d[j]);
         const float eps = (w.fid & F_B) ? S.epsBf[j] : S.epsAf[j];
-        const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-        if (r2 < S.rc2f[j]) {
-            inside = inside || S.cat[j];
-            const float ir2 = 1.0f / r2;
-            const float s2 = S.sigf[j] * S.sigf[j] * ir2;
-            const float s6 = s2 * s2 * s2;
-            const float fr = 24.0f * eps * s6 * (2.0f * s6 - 1.0f) * ir2;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const float fk = fr * d[k];
-                w.f[k] = w.f[k] + fk;
-                acc[j][k] -= fx40(fk);
-            }
-        }
+        const float r2 = d[j][0] * d[j][0] + d[j][1] * d[j][1] + d[j][2] * d[j][2];
+        in[j] = j < nc && r2 < S.rc2f[j];
+        fr[j] = wca_fr_m(eps, S.sigf[j], r2);
     }
+    inside = (in[0] && S.cat[0]) || (in[1] && S.cat[1]);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) w.f[k] = w.f[k] + rp.g_f[k];
+    for (int k = 0; k < 3; ++k) {
+        float f = 0.0f;
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            const float fk = fr[j] * d[j][k];
+            f = in[j] ? f + fk : f;
+            acc[j][k] -= in[j] ? fx40(fk) : 0ll;
+        }
+        w.f[k] = f + rp.g_f[k];
+    }
 }
 
 __device__ __forceinline__ void pforce(const ReplicaDev &rp, const FShared &S, const ColPD &C, int nc, FWorkD &w,

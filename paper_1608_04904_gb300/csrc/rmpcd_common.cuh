@@ -139,33 +139,63 @@ __device__ __forceinline__ void grid_shift(unsigned long long seed, uint32_t ste
     s[0] = u24f(w.x); s[1] = u24f(w.y); s[2] = u24f(w.z);
 }
 
+// x as R with one rounding, for |x| <= 2^48: hi 2^24 + lo with both parts
+// exact in FP32 and FP64, summed by one fma (64-bit integer conversions take
+// several times as long on this GPU).
+__device__ __forceinline__ float exact_to_R(long long x, float)
+{
+    return fmaf((float)(int)(x >> 24), 0x1p24f, (float)(int)(x & 0xFFFFFF));
+}
+__device__ __forceinline__ double exact_to_R(long long x, double)
+{
+    return fma((double)(int)(x >> 24), 0x1p24, (double)(int)(x & 0xFFFFFF));
+}
+
+// One Marsaglia (1972) attempt for the rotation axis: two candidate pairs
+// from the four words of a draw; true and n set when one is accepted.  The
+// acceptance test is exact integer arithmetic.
+template <typename R>
+__device__ __forceinline__ bool axis_attempt(const U4 &w, R n[3])
+{
+    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int pair = 0; pair < 2; ++pair) {
+        const int A = 2 * (int)(ws[2 * pair] >> 8) + 1 - (1 << 24);
+        const int B = 2 * (int)(ws[2 * pair + 1] >> 8) + 1 - (1 << 24);
+        const long long S = (long long)A * A + (long long)B * B;
+        if (S < (1ll << 48)) {
+            // 1 - s and 1 - 2s are formed as exact integers before the one
+            // rounding to R: no cancellation near the poles in FP32, and in
+            // FP64 the same values as (1 - s), (1 - 2 s) computed directly.
+            const R a = (R)A * (R)0x1p-24;
+            const R b = (R)B * (R)0x1p-24;
+            const R q = sqrt(exact_to_R((1ll << 48) - S, R(0)) * (R)0x1p-48);
+            n[0] = R(2) * a * q;
+            n[1] = R(2) * b * q;
+            n[2] = exact_to_R((1ll << 48) - 2 * S, R(0)) * (R)0x1p-48;
+            return true;
+        }
+    }
+    return false;
+}
+
 // Uniform point on the unit sphere (Marsaglia 1972) for the rotation axis of
 // one cell; the acceptance test is exact integer arithmetic.
 template <typename R>
 __device__ __forceinline__ void rotation_axis(unsigned long long seed, uint32_t step, uint32_t cell, R n[3])
 {
-    for (uint32_t attempt = 0; attempt < 16u; ++attempt) {
-        U4 w = philox(cell, step, P_ROT, attempt, seed);
-        uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-        for (int pair = 0; pair < 2; ++pair) {
-            long long A = 2 * (long long)(ws[2 * pair] >> 8) + 1 - (1 << 24);
-            long long B = 2 * (long long)(ws[2 * pair + 1] >> 8) + 1 - (1 << 24);
-            long long S = A * A + B * B;
-            if (S < (1ll << 48)) {
-                // 1 - s and 1 - 2s are formed as exact integers before the one
-                // rounding to R: no cancellation near the poles in FP32, and in
-                // FP64 the same values as (1 - s), (1 - 2 s) computed directly.
-                R a = (R)A * (R)0x1p-24;
-                R b = (R)B * (R)0x1p-24;
-                R q = sqrt((R)((1ll << 48) - S) * (R)0x1p-48);
-                n[0] = R(2) * a * q;
-                n[1] = R(2) * b * q;
-                n[2] = (R)((1ll << 48) - 2 * S) * (R)0x1p-48;
-                return;
-            }
-        }
-    }
+    for (uint32_t attempt = 0; attempt < 16u; ++attempt)
+        if (axis_attempt(philox(cell, step, P_ROT, attempt, seed), n)) return;
+    n[0] = R(0); n[1] = R(0); n[2] = R(1);
+}
+// The same, given the first attempt's draw w0 = philox(cell, step, P_ROT, 0).
+template <typename R>
+__device__ __forceinline__ void rotation_axis_from(unsigned long long seed, uint32_t step, uint32_t cell, const U4 &w0,
+                                                   R n[3])
+{
+    if (axis_attempt(w0, n)) return;
+    for (uint32_t attempt = 1; attempt < 16u; ++attempt)
+        if (axis_attempt(philox(cell, step, P_ROT, attempt, seed), n)) return;
     n[0] = R(0); n[1] = R(0); n[2] = R(1);
 }
 
@@ -480,6 +510,22 @@ __device__ __forceinline__ bool near_test_m(const ReplicaDev &rp, int nc, const 
         if (r2 < R * R) return true;
     }
     return false;
+}
+
+// Mixed-path MD arithmetic shared by both MD kernels (so that they agree bit
+// for bit).  Divisions on the sub-step's critical path use the hardware
+// reciprocal (MUFU, within 2 ulp) rather than an IEEE division, which takes
+// about twice as long on this GPU.
+__device__ __forceinline__ float fdiv_m(float a, float b) { return __fdividef(a, b); }
+
+// WCA force magnitude over distance, F(r) / r = 24 eps s^6 (2 s^6 - 1) / r^2
+// with s^2 = sigma^2 / r^2 (§1.4), for r^2 inside the cut-off.
+__device__ __forceinline__ float wca_fr_m(float eps, float sig, float r2)
+{
+    const float ir2 = fdiv_m(1.0f, r2);
+    const float s2 = sig * sig * ir2;
+    const float s6 = s2 * s2 * s2;
+    return 24.0f * eps * s6 * (2.0f * s6 - 1.0f) * ir2;
 }
 
 // x 2^-40 of a 64-bit fixed-point force total as FP32, by two 32-bit
