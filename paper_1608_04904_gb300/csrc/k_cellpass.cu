@@ -38,7 +38,7 @@ template <> struct Traits<false> {
 };
 
 // --- per-record helpers ----------------------------------------------------
-__device__ __forceinline__ void rec_flight(const ReplicaDev &rp, RecM &r)
+__device__ __forceinline__ void rec_flight(const HotM &rp, RecM &r)
 {
     int c[3] = {cw_get(r.cw, 0), cw_get(r.cw, 1), cw_get(r.cw, 2)};
     flight_m(rp, c, r.o, r.v);
@@ -47,7 +47,7 @@ __device__ __forceinline__ void rec_flight(const ReplicaDev &rp, RecM &r)
 __device__ __forceinline__ void rec_flight(const ReplicaDev &rp, RecD &r) { flight_d(rp, r.x, r.v); }
 
 // s: the shift in FP64; sf: the same shift in FP32 (exact: 24-bit uniforms)
-__device__ __forceinline__ int rec_key(const ReplicaDev &rp, const RecM &r, const double *, const float *sf)
+__device__ __forceinline__ int rec_key(const HotM &rp, const RecM &r, const double *, const float *sf)
 {
     int c[3] = {cw_get(r.cw, 0), cw_get(r.cw, 1), cw_get(r.cw, 2)};
     return cell_key_m(rp, c, r.o, sf);
@@ -64,15 +64,25 @@ struct NearFrames {
     float Rb[MAXC];
 };
 
-__device__ __forceinline__ bool rec_near(const Dev &, const ReplicaDev &rp, const NearFrames &nf, const RecM &r)
+__device__ __forceinline__ bool rec_near(const Dev &, const HotM &rp, int nc, const NearFrames &nf, const RecM &r)
 {
     int c[3] = {cw_get(r.cw, 0), cw_get(r.cw, 1), cw_get(r.cw, 2)};
-    return near_test_m(rp, rp.n_col, nf.Ci, nf.Cf, nf.Rb, c, r.o, r.v);
+    return near_test_m(rp, nc, nf.Ci, nf.Cf, nf.Rb, c, r.o, r.v);
 }
-__device__ __forceinline__ bool rec_near(const Dev &d, const ReplicaDev &rp, const NearFrames &, const RecD &r)
+__device__ __forceinline__ bool rec_near(const Dev &d, const ReplicaDev &rp, int, const NearFrames &, const RecD &r)
 {
     return near_test_d(d, rp, r.x, r.v);
 }
+
+// What the per-particle loops read of the replica: a register copy for the
+// mixed path, the shared-memory struct for the fp64 path.
+template <bool MIXED> struct HotPick;
+template <> struct HotPick<true> {
+    static __device__ __forceinline__ const HotM &get(const ReplicaDev &, const HotM &h) { return h; }
+};
+template <> struct HotPick<false> {
+    static __device__ __forceinline__ const ReplicaDev &get(const ReplicaDev &r, const HotM &) { return r; }
+};
 
 __device__ __forceinline__ float slab_sd(const ReplicaDev &rp, int k, float) { return rp.slab_sd_f[k]; }
 __device__ __forceinline__ double slab_sd(const ReplicaDev &rp, int k, double) { return rp.slab_sd[k]; }
@@ -372,6 +382,12 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
     const int opts = a.opts;
     const Rec *rin = reinterpret_cast<const Rec *>(d.rec[a.rin]);
     Rec *rout = reinterpret_cast<Rec *>(d.rec[a.rout]);
+    // register copies of what the per-particle loops read
+    const HotM hm = hot_m(rp);
+    const auto &hp = HotPick<MIXED>::get(rp, hm);
+    const R ca = r_ca(rp, R(0)), sa = r_sa(rp, R(0)), omc = r_omc(rp, R(0));
+    const int n_col = rp.n_col;
+    const float shnf[3] = {T.shnf[0], T.shnf[1], T.shnf[2]};
 
     // Every thread owns at most K particles of a batch; the global loads and
     // atomics of a stage are issued for all K before any result is used, so a
@@ -430,7 +446,7 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
 #pragma unroll 1
     for (int p = gt; p < nb; p += G) {
         Rec rec = srec[p];
-        if ((opts & CP_FLIGHT) && !(rec.fid & F_PROP)) rec_flight(rp, rec);
+        if ((opts & CP_FLIGHT) && !(rec.fid & F_PROP)) rec_flight(hp, rec);
         rec.fid &= ~F_PROP;
         srec[p] = rec;
     }
@@ -451,7 +467,6 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
         const int c = cb + cellof[p];
         Rec rec = srec[p];
         if (T.mode[c] == 1) {
-            const R ca = r_ca(rp, R(0)), sa = r_sa(rp, R(0)), omc = r_omc(rp, R(0));
             const R *vc = T.vcm[c];
             const R *nh = T.ax[c];
             const R u0 = rec.v[0] - vc[0], u1 = rec.v[1] - vc[1], u2 = rec.v[2] - vc[2];
@@ -472,14 +487,14 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
         if ((opts & CP_WRITE) && inb) store_rec(rout + gslot, rec);
         if (opts & CP_OBS) srec[p] = rec;
         if ((opts & CP_NEXT) && inb) {
-            if (rp.n_col > 0 && T.mnear[c] && rec_near(d, rp, T.nf, rec)) {
+            if (n_col > 0 && T.mnear[c] && rec_near(d, hp, n_col, T.nf, rec)) {
                 const int k = atomicAdd(&d.near_count[T.r], 1);
                 if (k < rp.n_part) d.near_list[rp.part_off + k] = gslot;
                 else atomicOr(&d.err[ERR_BOUNDS], 1u);
             } else {
                 Rec fl = rec;
-                rec_flight(rp, fl);
-                nkey = rp.cell_off + rec_key(rp, fl, T.shn, T.shnf);
+                rec_flight(hp, fl);
+                nkey = rp.cell_off + rec_key(hp, fl, T.shn, shnf);
             }
         }
         ent[p] = nkey;

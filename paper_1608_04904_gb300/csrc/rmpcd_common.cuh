@@ -68,6 +68,23 @@ struct ReplicaDev {
 
 struct BondDev { int a, b; double d; };
 
+// The replica constants the mixed per-particle code reads (flight, cell key,
+// minimum image, near test), as a value the compiler keeps in registers: a
+// reference into shared memory would be reloaded after every shared store.
+struct HotM {
+    int L[3];
+    int nz, walls, has_g;
+    float tau_f;
+    float g_f[3];
+};
+__device__ __forceinline__ HotM hot_m(const ReplicaDev &rp)
+{
+    HotM h;
+    for (int k = 0; k < 3; ++k) { h.L[k] = rp.L[k]; h.g_f[k] = rp.g_f[k]; }
+    h.nz = rp.nz; h.walls = rp.walls; h.has_g = rp.has_g; h.tau_f = rp.tau_f;
+    return h;
+}
+
 // All device pointers of a system (passed by value to every kernel).
 struct Dev {
     const ReplicaDev *rep;
@@ -344,7 +361,8 @@ __device__ __forceinline__ void flight_d(const ReplicaDev &rp, double x[3], doub
 
 // Mixed precision: position = integer cell + FP32 offset.  Renormalise the
 // offset to [0,1) and carry into the cell index (periodic axes wrap).
-__device__ __forceinline__ void renorm_m(const ReplicaDev &rp, int c[3], float o[3])
+template <class P>
+__device__ __forceinline__ void renorm_m(const P &rp, int c[3], float o[3])
 {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -361,7 +379,8 @@ __device__ __forceinline__ void renorm_m(const ReplicaDev &rp, int c[3], float o
     }
 }
 
-__device__ __forceinline__ void fly_m(const ReplicaDev &rp, float o[3], float v[3], float t)
+template <class P>
+__device__ __forceinline__ void fly_m(const P &rp, float o[3], float v[3], float t)
 {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -373,7 +392,8 @@ __device__ __forceinline__ void fly_m(const ReplicaDev &rp, float o[3], float v[
     }
 }
 
-__device__ __forceinline__ void flight_m(const ReplicaDev &rp, int c[3], float o[3], float v[3])
+template <class P>
+__device__ __forceinline__ void flight_m(const P &rp, int c[3], float o[3], float v[3])
 {
     const float tau = rp.tau_f;
     if (rp.walls) {
@@ -425,7 +445,8 @@ __device__ __forceinline__ int cell_key_d(const ReplicaDev &rp, const double x[3
     return c[0] + rp.L[0] * (c[1] + rp.L[1] * c[2]);
 }
 
-__device__ __forceinline__ int cell_key_m(const ReplicaDev &rp, const int cc[3], const float o[3], const float s[3])
+template <class P>
+__device__ __forceinline__ int cell_key_m(const P &rp, const int cc[3], const float o[3], const float s[3])
 {
     int c[3];
 #pragma unroll
@@ -444,8 +465,8 @@ __device__ __forceinline__ int cell_key_m(const ReplicaDev &rp, const int cc[3],
 }
 
 // Minimum image along periodic axes, |d| < 1.5 L assumed.
-template <typename R>
-__device__ __forceinline__ void min_image(const ReplicaDev &rp, R d[3])
+template <typename R, class P>
+__device__ __forceinline__ void min_image(const P &rp, R d[3])
 {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -496,7 +517,8 @@ __device__ __forceinline__ bool near_test_d(const Dev &d, const ReplicaDev &rp, 
 
 // Mixed path: colloids as wrapped integer cell Ci + FP32 offset Cf (stride 3),
 // so the test needs no FP64 arithmetic.
-__device__ __forceinline__ bool near_test_m(const ReplicaDev &rp, int nc, const int *Ci, const float *Cf,
+template <class P>
+__device__ __forceinline__ bool near_test_m(const P &rp, int nc, const int *Ci, const float *Cf,
                                             const float *Rb, const int c[3], const float o[3], const float v[3])
 {
     const float st = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * rp.tau_f;
