@@ -45,25 +45,38 @@ KERNEL_SOURCES = ["rmpcd_common.cuh", "rmpcd_kernels.cuh", "k_cellpass.cu", "k_m
 
 
 def workload(name, precision, seed_offset=0):
+    """The workload as a list of replicas (cfg, colloids, bonds) and a description."""
     from paper_1608_04904_gb300 import synth
     if name == "dimer32":
-        cfg, col, bonds = synth.dimer32(precision=precision, seed=2 + seed_offset)
+        reps = [synth.dimer32(precision=precision, seed=2 + seed_offset)]
         desc = ("reactive sphere dimer (C+N, sigma 2, M 100, bond 4.5), 32^3 periodic box, rho 10, "
                 "327680 solvent, 50 MD sub-steps dt 0.01, alpha 90 deg, tau 0.5, kT 1/3, p_cat 1, bulk k 0.01")
     elif name == "dimer64":
-        cfg, col, bonds = synth.dimer32(precision=precision, seed=2 + seed_offset, L=64)
+        reps = [synth.dimer32(precision=precision, seed=2 + seed_offset, L=64)]
         desc = ("reactive sphere dimer as dimer32 in a 64^3 periodic box, rho 10, 2621440 solvent "
                 "(larger than L2; profiling case)")
     elif name == "sphere16":
-        cfg, col, bonds = synth.sphere16(precision=precision, seed=1 + seed_offset)
+        reps = [synth.sphere16(precision=precision, seed=1 + seed_offset)]
         desc = "one WCA sphere (sigma 2, M 200), 16^3 periodic box, rho 10, 40960 solvent, 50 MD sub-steps"
     elif name == "poiseuille128":
-        cfg, col, bonds = synth.poiseuille(precision=precision, seed=3 + seed_offset)
+        reps = [synth.poiseuille(precision=precision, seed=3 + seed_offset)]
         desc = ("Poiseuille channel 128^3 with stick walls in z, rho 10, 20971520 solvent, g 0.001 x, "
                 "alpha 130 deg, tau 1")
+    elif name == "thermal":
+        reps = [synth.thermal(precision=precision, seed=5 + seed_offset)]
+        desc = ("thermal-gradient suspension 256x64x64, rho 10, 10485760 solvent, 64 WCA spheres (sigma 2.5, "
+                "M 150), colloid LJ eps 1 sigma 5.5 cut 2.5 sigma, MPC-AT slabs [0,8) kT 1.2 and [128,136) kT 0.8, "
+                "50 MD sub-steps dt 0.01")
+    elif name == "batch256":
+        sides = synth.batch_sides(256, seed=4)
+        reps = [synth.batch_sphere(L, seed=4 + r + 1000 * seed_offset, precision=precision)
+                for r, L in enumerate(sides)]
+        desc = ("256 independent replicas in one launch per kernel, cube sides drawn from {16,20,24,32,40,48} "
+                "(seed 4), rho 10, one WCA sphere of radius 4 each (stand-in for the bead-built Janus particle), "
+                "alpha 130 deg, tau 0.5, 25 MD sub-steps dt 0.02")
     else:
         raise SystemExit(f"unknown workload {name}")
-    return cfg, col, bonds, desc
+    return reps, desc
 
 
 def kernel_hash():
@@ -153,7 +166,8 @@ def cpu_baseline(name, precision, budget_s=15.0):
     from oracle import oracle
     from paper_1608_04904_gb300 import synth
     oracle.build()
-    cfg, col, bonds, _ = workload(name, precision)
+    reps, _ = workload(name, precision)
+    cfg, col, bonds = reps[0]
     x, v, fl = synth.solvent(cfg, col, seed=cfg["seed"] + 100)
     o = oracle.OracleSystem(cfg, x, v, fl, colloids=synth.colloid_arrays(col) if col else None, bonds=bonds)
     o.step(1)
@@ -166,15 +180,17 @@ def cpu_baseline(name, precision, budget_s=15.0):
         if (el >= budget_s and k >= 2) or k >= 10000:
             break
     return {"value": len(x) * k / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{k} full collision intervals of the workload ({len(x)} solvent) after 1 warm-up, "
-                      f"{el:.1f} s, single-threaded FP64 C oracle", "seconds": el}
+            "sample": f"{k} full collision intervals of {'the first replica of ' if len(reps) > 1 else ''}the "
+                      f"workload ({len(x)} solvent) after 1 warm-up, {el:.1f} s, single-threaded FP64 C oracle",
+            "seconds": el}
 
 
 def run_reference(args, ws, rank):
     if rank != 0:
         return
     from paper_1608_04904_gb300 import synth
-    cfg, col, bonds, desc = workload(args.workload, args.precision)
+    reps, desc = workload(args.workload, args.precision)
+    cfg, col, bonds = reps[0]
     from oracle import oracle
     oracle.build()
     x, v, fl = synth.solvent(cfg, col, seed=cfg["seed"] + 100)
@@ -206,14 +222,23 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def timed_run(api, torch, cfg, col, bonds, x, v, fl, precision, steps, warmup, flush, dev_index, sample_clocks,
+def make_system(api, reps, states, precision, stream):
+    s = api.System([dict(cfg=cfg, n=len(st[0]), colloids=col, bonds=bonds) for (cfg, col, bonds), st in
+                    zip(reps, states)], precision=precision, bucket_cap=reps[0][0].get("bucket_cap", 64),
+                   stream=stream)
+    for r, (x, v, fl) in enumerate(states):
+        s.set_state(r, x, v, fl)
+    return s
+
+
+def timed_run(api, torch, reps, states, precision, steps, warmup, flush, dev_index, sample_clocks,
               barrier, md_cluster=0, md_kernel=0):
     stream = torch.cuda.current_stream()
-    s = api.System.single(cfg, len(x), col, bonds, precision=precision, stream=stream)
+    s = make_system(api, reps, states, precision, stream)
     s.set_tuning(md_cluster, md_kernel)
-    s.set_state(0, x, v, fl)
-    # warm-up, including the 12 tuning intervals of the MD cluster size
-    for _ in range(max(warmup, 13 if (col and md_cluster == 0) else 0)):   # 3 trials x <= 4 sizes
+    has_col = any(col for _, col, _ in reps)
+    # warm-up, including the tuning intervals of the MD cluster size
+    for _ in range(max(warmup, 16 if (has_col and md_cluster == 0) else 0)):   # 3 trials x <= 5 sizes
         s.step(1)
     torch.cuda.synchronize()
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -245,28 +270,31 @@ def timed_run(api, torch, cfg, col, bonds, x, v, fl, precision, steps, warmup, f
     return ms, timers, launches, clocks, obs
 
 
-def e2e_run(api, torch, cfg, col, bonds, x, v, fl, precision, steps):
+def e2e_run(api, torch, reps, states, precision, steps):
     """Same metric through the public API with pinned host buffers: every step
     copies the state in, runs one interval and reads the state back."""
-    n = len(x)
     pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
-    xh, vh, fh = pin((n, 3), torch.float64), pin((n, 3), torch.float64), pin((n,), torch.uint8)
-    xh[:], vh[:], fh[:] = x, v, fl
-    out = {"x": pin((n, 3), torch.float64), "v": pin((n, 3), torch.float64), "flags": pin((n,), torch.uint8)}
-    s = api.System.single(cfg, n, col, bonds, precision=precision, stream=torch.cuda.current_stream())
-    s.set_state(0, xh, vh, fh)
+    hin, hout = [], []
+    for x, v, fl in states:
+        n = len(x)
+        a = {"x": pin((n, 3), torch.float64), "v": pin((n, 3), torch.float64), "flags": pin((n,), torch.uint8)}
+        a["x"][:], a["v"][:], a["flags"][:] = x, v, fl
+        hin.append(a)
+        hout.append({"x": pin((n, 3), torch.float64), "v": pin((n, 3), torch.float64),
+                     "flags": pin((n,), torch.uint8)})
+    n = sum(len(st[0]) for st in states)
+    s = make_system(api, reps, states, precision, torch.cuda.current_stream())
     s.step(1)
-    s.get_state(0, out=out)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
-        s.set_state(0, xh, vh, fh)
+        for r in range(len(states)):
+            s.set_state(r, hin[r]["x"], hin[r]["v"], hin[r]["flags"])
         s.step(1)
-        s.get_state(0, out=out)
+        for r in range(len(states)):
+            s.get_state(r, out=hout[r])
         # the state read back is the next step's input
-        xh, out["x"] = out["x"], xh
-        vh, out["v"] = out["v"], vh
-        fh, out["flags"] = out["flags"], fh
+        hin, hout = hout, hin
     el = time.perf_counter() - t0
     s.close()
     per = n * (24 + 24 + 1)
@@ -280,7 +308,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="dimer32", choices=["dimer32", "dimer64", "sphere16", "poiseuille128"])
+    ap.add_argument("--workload", default="dimer32",
+                    choices=["dimer32", "dimer64", "sphere16", "poiseuille128", "thermal", "batch256"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--md-cluster", type=int, default=0, help="MD CTAs per replica (0 = autotune)")
     ap.add_argument("--md-kernel", type=int, default=0, help="MD kernel: 0 auto, 1 general, 2 few-colloid")
@@ -309,12 +338,13 @@ def main():
     build.build()
     api.load()
 
-    cfg, col, bonds, desc = workload(args.workload, args.precision, seed_offset=rank)
-    x, v, fl = synth.solvent(cfg, col, seed=cfg["seed"] + 100)
-    n = len(x)
+    reps, desc = workload(args.workload, args.precision, seed_offset=rank)
+    states = [synth.solvent(cfg, col, seed=cfg["seed"] + 100) for cfg, col, _ in reps]
+    cfg = reps[0][0]
+    n = sum(len(st[0]) for st in states)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    ms, timers, launches, clocks, obs = timed_run(api, torch, cfg, col, bonds, x, v, fl, args.precision,
+    ms, timers, launches, clocks, obs = timed_run(api, torch, reps, states, args.precision,
                                                   args.steps, args.warmup, flush, local, rank == 0, barrier,
                                                   args.md_cluster, args.md_kernel)
     ms_max = ms
@@ -340,7 +370,7 @@ def main():
             alg = n * ALG_BYTES[args.precision]
             entry.update({"alg_bytes_per_launch": alg, "achieved_gbs": alg / (avg_ms / 1e3) / 1e9})
         if k == "md":
-            entry["us_per_substep"] = 1e3 * avg_ms / cfg["n_md"]
+            entry["us_per_substep"] = 1e3 * avg_ms / max(c["n_md"] for c, _, _ in reps)
         kernels[kernel_names[k]] = entry
     cp = phases["cellpass"]
     cp_avg_s = cp["ms"] / cp["launches"] / 1e3
@@ -363,7 +393,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {desc}", "n_solvent": n, "precision": args.precision,
+        "config": {"workload": f"{args.workload}: {desc}", "n_solvent": n, "n_replicas": len(reps),
+                   "precision": args.precision,
                    "parallelism": "replicas" if ws > 1 else "single",
                    "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
                    "timing": "CUDA events around each rmpcd_step(1) on the library's stream",
@@ -373,14 +404,14 @@ def main():
     }
     if rank == 0 and not args.no_fp64 and args.precision == "mixed":
         k64 = max(20, args.steps // 4)
-        ms64, t64, _, _, _ = timed_run(api, torch, cfg, col, bonds, x, v, fl, "fp64", k64, args.warmup, flush, local,
+        ms64, t64, _, _, _ = timed_run(api, torch, reps, states, "fp64", k64, args.warmup, flush, local,
                                        False, lambda: None, args.md_cluster, args.md_kernel)
         v64 = n * k64 / (ms64 / 1e3)
         line["fp64"] = {"value": v64, "ms_per_step": ms64 / k64, "steps": k64,
                         "cellpass_avg_us": 1e3 * t64["cellpass"]["ms"] / t64["cellpass"]["launches"]}
         line["speedup_mixed_over_fp64"] = (n * args.steps / (ms / 1e3)) / v64
     if rank == 0 and not args.no_e2e:
-        line["e2e"] = e2e_run(api, torch, cfg, col, bonds, x, v, fl, args.precision, min(args.steps, 200))
+        line["e2e"] = e2e_run(api, torch, reps, states, args.precision, min(args.steps, 200))
     if rank == 0 and not args.no_cpu and ws == 1:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.precision)
     if ws > 1:

@@ -93,9 +93,6 @@ __device__ __forceinline__ double r_sa(const ReplicaDev &rp, double) { return rp
 __device__ __forceinline__ float r_omc(const ReplicaDev &rp, float) { return rp.omc_f; }
 __device__ __forceinline__ double r_omc(const ReplicaDev &rp, double) { return rp.omc; }
 
-constexpr unsigned long long LB_VALUE_MASK = (1ull << 46) - 1ull;
-constexpr int LB_SPIN_LIMIT = 1 << 22;
-
 // Per-tile state shared by the groups of one CTA.
 template <bool MIXED>
 struct TileShared {
@@ -645,46 +642,8 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
     // warp path the other warps start on their cells meanwhile.
     const bool warp_path = T.maxcnt <= WPC;
     if (tid < 32) {
-        // 16-bit tag of this launch, never 0 (the initial state)
-        const unsigned long long ep = (unsigned long long)(a.epoch % 65535u) + 1ull;
-        const unsigned long long total = (unsigned long long)T.ls[CPT];
-        if (lane == 0) st_release(&d.tile_state[tile], (ep << 48) | (1ull << 46) | total);
-        unsigned long long prefix = 0;
-        int t = tile - 1;
-        int spins = 0;
-        bool ok = true;
-        while (t >= 0) {
-            const int idx = t - lane;
-            unsigned long long flag = 2ull, val = 0ull;   // before tile 0: inclusive prefix 0
-            if (idx >= 0) {
-                const unsigned long long w = ld_acquire(&d.tile_state[idx]);
-                flag = ((w >> 48) == ep) ? ((w >> 46) & 3ull) : 0ull;
-                val = w & LB_VALUE_MASK;
-            }
-            const unsigned incl = __ballot_sync(0xffffffffu, flag == 2ull);
-            const unsigned ready = __ballot_sync(0xffffffffu, flag != 0ull);
-            const int first = incl ? __ffs(incl) - 1 : 31;
-            const unsigned need = (first == 31) ? 0xffffffffu : ((2u << first) - 1u);
-            if ((ready & need) != need) {
-                if (++spins > LB_SPIN_LIMIT) { ok = false; break; }
-                __nanosleep(32);
-                continue;
-            }
-            unsigned long long part = (lane <= first) ? val : 0ull;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
-            prefix += __shfl_sync(0xffffffffu, part, 0);
-            if (incl) break;
-            t -= 32;
-        }
-        if (lane == 0) {
-            if (!ok) {
-                atomicOr(&d.err[ERR_TIMEOUT], 1u);
-                prefix = 0x3FFFFFFFull;   // pushes every write of this tile out of bounds
-            }
-            st_release(&d.tile_state[tile], (ep << 48) | (2ull << 46) | ((prefix + total) & LB_VALUE_MASK));
-            T.base = (int)(prefix > 0x3FFFFFFFull ? 0x3FFFFFFF : prefix);
-        }
+        const int base = tile_lookback(d, a.epoch, tile, T.ls[CPT], lane);
+        if (lane == 0) T.base = base;
         __syncwarp();
         if (warp_path) base_arrive();
     }

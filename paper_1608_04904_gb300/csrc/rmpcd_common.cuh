@@ -572,4 +572,58 @@ __device__ __forceinline__ void st_release(unsigned long long *p, unsigned long 
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Tile base by decoupled look-back (Merrill & Garland 2016), run by one full
+// warp: publishes the tile's aggregate, inspects 32 predecessor tiles at a
+// time summing aggregates back to the nearest inclusive prefix, publishes the
+// tile's inclusive prefix and returns its exclusive prefix (in every lane).
+// Tiles are taken in ticket order, so every predecessor has started.  Words
+// carry a 16-bit tag of the launch (never 0, the initial state), a 2-bit flag
+// (1 aggregate, 2 inclusive prefix) and a 46-bit value.  A wait that runs out
+// sets ERR_TIMEOUT and returns a base that puts every write out of bounds.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long LB_VALUE_MASK = (1ull << 46) - 1ull;
+constexpr int LB_SPIN_LIMIT = 1 << 22;
+
+__device__ __forceinline__ int tile_lookback(const Dev &d, uint32_t epoch, int tile, int total, int lane)
+{
+    const unsigned long long ep = (unsigned long long)(epoch % 65535u) + 1ull;
+    if (lane == 0) st_release(&d.tile_state[tile], (ep << 48) | (1ull << 46) | (unsigned long long)total);
+    unsigned long long prefix = 0;
+    int t = tile - 1;
+    int spins = 0;
+    bool ok = true;
+    while (t >= 0) {
+        const int idx = t - lane;
+        unsigned long long flag = 2ull, val = 0ull;   // before tile 0: inclusive prefix 0
+        if (idx >= 0) {
+            const unsigned long long w = ld_acquire(&d.tile_state[idx]);
+            flag = ((w >> 48) == ep) ? ((w >> 46) & 3ull) : 0ull;
+            val = w & LB_VALUE_MASK;
+        }
+        const unsigned incl = __ballot_sync(0xffffffffu, flag == 2ull);
+        const unsigned ready = __ballot_sync(0xffffffffu, flag != 0ull);
+        const int first = incl ? __ffs(incl) - 1 : 31;
+        const unsigned need = (first == 31) ? 0xffffffffu : ((2u << first) - 1u);
+        if ((ready & need) != need) {
+            if (++spins > LB_SPIN_LIMIT) { ok = false; break; }
+            __nanosleep(32);
+            continue;
+        }
+        unsigned long long part = (lane <= first) ? val : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+        prefix += __shfl_sync(0xffffffffu, part, 0);
+        if (incl) break;
+        t -= 32;
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok) prefix = 0x3FFFFFFFull;   // pushes every write of this tile out of bounds
+    if (lane == 0) {
+        if (!ok) atomicOr(&d.err[ERR_TIMEOUT], 1u);
+        st_release(&d.tile_state[tile], (ep << 48) | (2ull << 46) | ((prefix + (unsigned long long)total) & LB_VALUE_MASK));
+    }
+    return (int)(prefix > 0x3FFFFFFFull ? 0x3FFFFFFF : prefix);
+}
+
 }  // namespace rmpcd

@@ -104,6 +104,34 @@ def colloid_arrays(col) -> dict:
     }
 
 
+def _inside_any(x, centers, radii, L):
+    """Mask of the points x that lie within radius of any centre (minimum
+    image), testing only the points in the cells around each centre."""
+    bad = np.zeros(len(x), dtype=bool)
+    if len(centers) == 0 or len(x) == 0:
+        return bad
+    cells = np.floor(x).astype(np.int64) % L
+    key = cells[:, 0] + L[0] * (cells[:, 1] + L[1] * cells[:, 2])
+    order = np.argsort(key, kind="stable")
+    skey = key[order]
+    for c, r in zip(centers, radii):
+        c = np.mod(c, L)
+        lo = np.floor(c - r).astype(np.int64)
+        hi = np.floor(c + r).astype(np.int64)
+        rng_ = [np.arange(lo[d], hi[d] + 1) % L[d] for d in range(3)]
+        cz, cy, cx_ = np.meshgrid(rng_[2], rng_[1], rng_[0], indexing="ij")
+        want = np.unique((cx_ + L[0] * (cy + L[1] * cz)).ravel())
+        a = np.searchsorted(skey, want, side="left")
+        b = np.searchsorted(skey, want, side="right")
+        idx = np.concatenate([order[i:j] for i, j in zip(a, b)]) if len(want) else np.zeros(0, np.int64)
+        if len(idx) == 0:
+            continue
+        d = x[idx] - c
+        d -= L * np.round(d / L)
+        bad[idx[(d * d).sum(1) < r * r]] = True
+    return bad
+
+
 def solvent(cfg, col=(), n=None, seed=None, frac_b=0.0, tag_frac=0.0, exclude=True, exclude_factor=None):
     """Uniform positions (multiples of 2^-24) outside every colloid's cut-off
     (or outside ``exclude_factor * sigma`` when given),
@@ -128,11 +156,7 @@ def solvent(cfg, col=(), n=None, seed=None, frac_b=0.0, tag_frac=0.0, exclude=Tr
         if not exclude or len(col) == 0:
             todo = todo[:0]
             break
-        bad = np.zeros(k, dtype=bool)
-        for j in range(len(col)):
-            d = x[todo] - np.mod(cx[j], L)
-            d -= L * np.round(d / L)
-            bad |= (d * d).sum(1) < rcs[j] ** 2
+        bad = _inside_any(x[todo], cx, rcs, L)
         todo = todo[bad]
     v = rng.standard_normal((n, 3)) * math.sqrt(cfg["kT"])
     if n > 0:
@@ -150,3 +174,17 @@ def solvent(cfg, col=(), n=None, seed=None, frac_b=0.0, tag_frac=0.0, exclude=Tr
 def batch_sides(n_replicas, seed=4):
     rng = np.random.Generator(np.random.PCG64(seed))
     return [int(s) for s in rng.choice([16, 20, 24, 32, 40, 48], size=n_replicas)]
+
+
+def batch_sphere(side, seed, precision="mixed"):
+    """One replica of the batched ensemble: a cube of the given side at
+    density 10 holding one WCA sphere of radius 4 (sigma 4) at the centre with
+    the mass of the displaced solvent (neutral buoyancy), alpha 130 deg,
+    tau 0.5, 25 MD sub-steps of dt 0.02.  The sphere stands in for the
+    bead-built Janus particle of the same radius."""
+    L = (side, side, side)
+    cfg = base_config(L=L, alpha=math.radians(130.0), tau=0.5, n_md=25, kT=1.0, seed=seed, precision=precision)
+    m = 10.0 * 4.0 / 3.0 * math.pi * 4.0 ** 3
+    c = side / 2.0
+    col = [dict(x=(c, c, c), v=(0.0, 0.0, 0.0), mass=m, sigma=4.0, eps_A=1.0, eps_B=1.0, catalytic=1)]
+    return cfg, col, []
