@@ -201,7 +201,10 @@ rmpcd_status rmpcd_read_timers(rmpcd_system *sys, rmpcd_timers *out, int32_t res
  * md_kernel: 1 = general kernel; 2 = few-colloid kernel (every replica with at
  *   most 2 colloids, at most 1 bond and no colloid-colloid potential: every
  *   warp integrates the colloids itself, one CTA barrier per sub-step);
- *   0 (default) = 2 when allowed, else 1.
+ *   3 = wide kernel (mixed path: one cooperative launch over all SMs per
+ *   replica with colloids, one grid barrier per sub-step; md_cluster 0 or 1);
+ *   0 (default) = 2 when allowed, else 3 for the mixed path with at most 4
+ *   replicas with colloids, else 1.
  * rmpcd_get_tuning reports the cluster size in use (0 while tuning) and the
  * kernel.  Errors: EINVAL. */
 rmpcd_status rmpcd_set_tuning(rmpcd_system *sys, int32_t md_cluster, int32_t md_kernel);

@@ -63,6 +63,8 @@ struct rmpcd_system {
     int md_best = 4;
     int md_fast_max = 8;              // largest cluster the device runs for the few-colloid kernel
     std::vector<int> md_cand;         // cluster sizes the tuner tries
+    int md_wide_grid = 0;             // co-resident CTAs of the wide MD kernel (0: unavailable)
+    std::vector<int> wide_reps;       // replicas with colloids (wide kernel: one launch each)
     std::vector<Pending> md_trials;   // phase field holds the cluster size
 };
 
@@ -104,12 +106,23 @@ void note_global_error(const std::string &msg) { g_create_error = msg; }
 
 // MD kernel choice (0 = the few-colloid kernel when allowed) and the cluster
 // sizes the tuner tries for it.
+// The wide kernel by default: mixed path, a few replicas (one cooperative
+// launch each) with more colloids than the few-colloid kernel takes.
+static bool wide_default(const rmpcd_system *sys)
+{
+    return sys->mixed && sys->md_wide_grid > 0 && !sys->fast_ok && sys->wide_reps.size() <= 4;
+}
+
 static void set_md_kernel(rmpcd_system *sys, int req)
 {
     sys->md_kernel_req = req;
-    sys->md_kernel = req ? req : (sys->fast_ok ? 2 : 1);
+    sys->md_kernel = req ? req : (sys->fast_ok ? 2 : (wide_default(sys) ? 3 : 1));
     sys->md_cand.clear();
-    if (sys->md_kernel == 2) {
+    if (sys->md_kernel == 3) {
+        sys->md_cand = {1};   // one grid over all SMs: nothing to tune
+        sys->md_best = 1;
+        sys->md_tuned = true;
+    } else if (sys->md_kernel == 2) {
         sys->md_cand = {2, 4, 8};
         if (sys->md_fast_max >= 16) sys->md_cand.push_back(16);
         sys->md_best = 8;
@@ -412,6 +425,7 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
     AL(&d.colXi, 3 * n_col);
     AL(&d.colCi, 3 * n_col);
     AL(&d.colXf, 3 * n_col);
+    AL(&d.md_wide, 1);
     AL(&d.colVf, 3 * n_col);
     AL(&dRb, n_col);
     AL(&dIM, n_col);
@@ -463,6 +477,7 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
     zero(d.ticket, sizeof(unsigned int) * 2);
     zero(d.err, sizeof(unsigned int) * ERR_COUNT);
     zero(d.obs_out, sizeof(double) * 8 * n_replicas);
+    if (st == RMPCD_OK) zero(d.md_wide, sizeof(MdWideGlobal));
     if (st == RMPCD_OK) st = cuda_check(sys, cudaStreamSynchronize(s), "create sync");
     if (st != RMPCD_OK) {
         g_create_error = sys->err;
@@ -486,6 +501,9 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
     d.n_tiles = (int)n_tiles;
     d.n_total = (int)n_total;
     if (sys->fast_ok && sys->any_colloids) sys->md_fast_max = md_fast_max_cluster(sys->mixed);
+    if (sys->mixed && sys->any_colloids) sys->md_wide_grid = md_wide_grid();
+    for (int r = 0; r < n_replicas; ++r)
+        if (params[r].n_colloids > 0) sys->wide_reps.push_back(r);
     set_md_kernel(sys, 0);
     *out = sys;
     return RMPCD_OK;
@@ -707,9 +725,11 @@ rmpcd_status rmpcd_stream(rmpcd_system *sys)
     if ((st = after_launch(sys, sys->n_total > 0 ? 1 : 0)) != RMPCD_OK) return st;
     if (sys->any_colloids) {
         const int cs = sys->md_fixed ? sys->md_fixed : sys->md_best;
-        if (sys->md_kernel == 2) launch_md_fast(sys->mixed, sys->d, sys->step, sys->cur, 0, 0, cs, sys->stream);
+        if (sys->md_kernel == 3)
+            launch_md_wide(sys->d, sys->wide_reps, sys->md_wide_grid, sys->step, sys->cur, 0, 0, sys->stream);
+        else if (sys->md_kernel == 2) launch_md_fast(sys->mixed, sys->d, sys->step, sys->cur, 0, 0, cs, sys->stream);
         else launch_md(sys->mixed, sys->d, sys->step, sys->cur, 0, 0, cs, sys->stream);
-        if ((st = after_launch(sys, 1)) != RMPCD_OK) return st;
+        if ((st = after_launch(sys, sys->md_kernel == 3 ? (int)sys->wide_reps.size() : 1)) != RMPCD_OK) return st;
     }
     sys->has_sort = false;
     sys->obs_valid = false;
@@ -804,11 +824,16 @@ rmpcd_status rmpcd_step(rmpcd_system *sys, int32_t n_intervals)
             cudaEvent_t tev;
             const int cs = md_cluster_for_launch(sys, &tev);
             tstart(sys, &ev);
-            if (sys->md_kernel == 2) launch_md_fast(sys->mixed, sys->d, sys->step, sys->cur, sys->bcur, 1, cs, sys->stream);
+            if (sys->md_kernel == 3)
+                launch_md_wide(sys->d, sys->wide_reps, sys->md_wide_grid, sys->step, sys->cur, sys->bcur, 1,
+                               sys->stream);
+            else if (sys->md_kernel == 2)
+                launch_md_fast(sys->mixed, sys->d, sys->step, sys->cur, sys->bcur, 1, cs, sys->stream);
             else launch_md(sys->mixed, sys->d, sys->step, sys->cur, sys->bcur, 1, cs, sys->stream);
             tstop(sys, 1, ev);
             md_trial_done(sys, cs, tev);
-            if ((st = after_launch(sys, 1)) != RMPCD_OK) return st;
+            if ((st = after_launch(sys, sys->md_kernel == 3 ? (int)sys->wide_reps.size() : 1)) != RMPCD_OK)
+                return st;
         }
         CellPassArgs a{CP_FLIGHT | CP_COLLIDE | CP_REACT | CP_NEXT | CP_WRITE, sys->step, sys->bcur, sys->bcur ^ 1,
                        sys->cur, sys->cur ^ 1, next_epoch(sys)};
@@ -893,11 +918,15 @@ rmpcd_status rmpcd_read_timers(rmpcd_system *sys, rmpcd_timers *out, int32_t res
 rmpcd_status rmpcd_set_tuning(rmpcd_system *sys, int32_t md_cluster, int32_t md_kernel)
 {
     if (!sys) return RMPCD_EINVAL;
-    if (md_kernel < 0 || md_kernel > 2) return fail(sys, RMPCD_EINVAL, "md_kernel must be 0, 1 or 2");
+    if (md_kernel < 0 || md_kernel > 3) return fail(sys, RMPCD_EINVAL, "md_kernel must be 0, 1, 2 or 3");
     if (md_kernel == 2 && !sys->fast_ok)
-        return fail(sys, RMPCD_EINVAL, "the few-colloid MD kernel needs <= %d colloids and no colloid-colloid potential",
-                    MD_FAST_NC);
-    const int kern = md_kernel ? md_kernel : (sys->fast_ok ? 2 : 1);
+        return fail(sys, RMPCD_EINVAL, "the few-colloid MD kernel needs <= %d colloids, <= 1 bond and no "
+                    "colloid-colloid potential", MD_FAST_NC);
+    if (md_kernel == 3 && !(sys->mixed && sys->md_wide_grid > 0))
+        return fail(sys, RMPCD_EINVAL, "the wide MD kernel needs the mixed path and cooperative launch");
+    const int kern = md_kernel ? md_kernel : (sys->fast_ok ? 2 : (wide_default(sys) ? 3 : 1));
+    if (kern == 3 && md_cluster > 1)
+        return fail(sys, RMPCD_EINVAL, "the wide MD kernel takes no cluster size (0 or 1)");
     const int maxc = kern == 2 ? sys->md_fast_max : 8;
     if (md_cluster != 0 && md_cluster != 1 && md_cluster != 2 && md_cluster != 4 && md_cluster != 8 &&
         !(md_cluster == 16 && maxc >= 16))

@@ -17,6 +17,7 @@
 // particle-colloid separation is an integer difference plus FP32 offsets.
 #include <cooperative_groups.h>
 #include <type_traits>
+#include <vector>
 
 #include "rmpcd_kernels.cuh"
 
@@ -116,7 +117,8 @@ __device__ __forceinline__ void force_d(const ReplicaDev &rp, MDShared<false> &S
 }
 
 // Mixed: separation from the wrapped colloid cell and offset, FP32 only.
-__device__ __forceinline__ void sep_m(const ReplicaDev &rp, const MDShared<true> &S, int j, const int c[3],
+template <class SH>
+__device__ __forceinline__ void sep_m(const ReplicaDev &rp, const SH &S, int j, const int c[3],
                                       const float o[3], float d[3])
 {
 #pragma unroll
@@ -166,7 +168,8 @@ __device__ __forceinline__ bool inside_cat_d(const ReplicaDev &rp, const MDShare
     return false;
 }
 
-__device__ __forceinline__ bool inside_cat_m(const ReplicaDev &rp, const MDShared<true> &S, const int c[3],
+template <class SH>
+__device__ __forceinline__ bool inside_cat_m(const ReplicaDev &rp, const SH &S, const int c[3],
                                              const float o[3])
 {
     for (int j = 0; j < S.nc; ++j) {
@@ -380,7 +383,8 @@ __device__ __forceinline__ float col_sep1(const ColM &C, int a, int b, int t)
 }
 
 // RATTLE position stage for every bond (warp 0; lanes 0..2 = axes).
-__device__ void rattle_pos_w(const ReplicaDev &rp, MDShared<true> &S, int lane)
+template <class SH>
+__device__ void rattle_pos_w(const ReplicaDev &rp, SH &S, int lane)
 {
     ColM &C = S.C;
     const float idt = 1.0f / rp.dt_f;
@@ -415,7 +419,8 @@ __device__ void rattle_pos_w(const ReplicaDev &rp, MDShared<true> &S, int lane)
 }
 
 // RATTLE velocity stage (warp 0).
-__device__ void rattle_vel_w(MDShared<true> &S, int lane)
+template <class SH>
+__device__ void rattle_vel_w(SH &S, int lane)
 {
     ColM &C = S.C;
     for (int k = 0; k < S.nbond; ++k) {
@@ -435,31 +440,42 @@ __device__ void rattle_vel_w(MDShared<true> &S, int lane)
     }
 }
 
+// One colloid-colloid pair (mixed path): the fixed-point LJ force on a
+// (b receives -q); false when the pair is beyond the cut-off.
+template <class SH>
+__device__ __forceinline__ bool cc_pair_m(const ReplicaDev &rp, const SH &S, int a, int b, long long q[3])
+{
+    const float rc = (float)rp.cc_rc, sg = (float)rp.cc_sigma, ep = (float)rp.cc_eps;
+    float d[3];
+    for (int t = 0; t < 3; ++t) d[t] = (float)(S.C.Ci[a][t] - S.C.Ci[b][t]) + (S.C.Xf[a][t] - S.C.Xf[b][t]);
+    min_image(rp, d);
+    const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (!(r2 < rc * rc)) return false;
+    const float ir2 = 1.0f / r2;
+    const float s2 = sg * sg * ir2;
+    const float s6 = s2 * s2 * s2;
+    const float fr = 24.0f * ep * s6 * (2.0f * s6 - 1.0f) * ir2;
+    for (int k = 0; k < 3; ++k) q[k] = __float2ll_rn(fr * d[k] * 0x1p40f);
+    return true;
+}
+
 __device__ void colloid_colloid(const ReplicaDev &rp, MDShared<true> &S, long long *Fq)
 {
     if (!(rp.cc_rc > 0.0)) return;
-    const float rc = (float)rp.cc_rc, sg = (float)rp.cc_sigma, ep = (float)rp.cc_eps;
     for (int a = 0; a < S.nc; ++a)
         for (int b = a + 1; b < S.nc; ++b) {
             if (bonded(S.bond, S.nbond, a, b)) continue;
-            float d[3];
-            for (int t = 0; t < 3; ++t) d[t] = (float)(S.C.Ci[a][t] - S.C.Ci[b][t]) + (S.C.Xf[a][t] - S.C.Xf[b][t]);
-            min_image(rp, d);
-            const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-            if (!(r2 < rc * rc)) continue;
-            const float ir2 = 1.0f / r2;
-            const float s2 = sg * sg * ir2;
-            const float s6 = s2 * s2 * s2;
-            const float fr = 24.0f * ep * s6 * (2.0f * s6 - 1.0f) * ir2;
+            long long q[3];
+            if (!cc_pair_m(rp, S, a, b, q)) continue;
             for (int k = 0; k < 3; ++k) {
-                const long long q = __float2ll_rn(fr * d[k] * 0x1p40f);
-                Fq[3 * a + k] += q;
-                Fq[3 * b + k] -= q;
+                Fq[3 * a + k] += q[k];
+                Fq[3 * b + k] -= q[k];
             }
         }
 }
 
-__device__ void col_load(const Dev &d, const ReplicaDev &rp, MDShared<true> &S, int j)
+template <class SH>
+__device__ void col_load(const Dev &d, const ReplicaDev &rp, SH &S, int j)
 {
     const int g = rp.col_off + j;
     for (int k = 0; k < 3; ++k) {
@@ -498,7 +514,8 @@ __device__ void col_gather_w(const ReplicaDev &rp, MDShared<true> &S, int par, i
 }
 
 // Warp 0: first half kick, drift, carry, RATTLE position stage.
-__device__ void col_kick_drift_w(const ReplicaDev &rp, MDShared<true> &S, int lane)
+template <class SH>
+__device__ void col_kick_drift_w(const ReplicaDev &rp, SH &S, int lane)
 {
     for (int l = lane; l < 3 * S.nc; l += 32) {
         const int j = l / 3, t = l % 3;
@@ -514,7 +531,8 @@ __device__ void col_kick_drift_w(const ReplicaDev &rp, MDShared<true> &S, int la
 }
 
 // Warp 0: second half kick, RATTLE velocity stage.
-__device__ void col_kick_w(const ReplicaDev &rp, MDShared<true> &S, int lane)
+template <class SH>
+__device__ void col_kick_w(const ReplicaDev &rp, SH &S, int lane)
 {
     for (int l = lane; l < 3 * S.nc; l += 32) {
         const int j = l / 3, t = l % 3;
@@ -524,7 +542,8 @@ __device__ void col_kick_w(const ReplicaDev &rp, MDShared<true> &S, int lane)
     rattle_vel_w(S, lane);
 }
 
-__device__ void col_store(const Dev &d, const ReplicaDev &rp, MDShared<true> &S)
+template <class SH>
+__device__ void col_store(const Dev &d, const ReplicaDev &rp, SH &S)
 {
     bool bad = false;
     const float skin = rp.skin_f;
@@ -792,6 +811,354 @@ __global__ void __launch_bounds__(MDGeom<CS>::NT, 1) k_md(Dev d, uint32_t step, 
     if (CS > 1) cl.sync();
     if (rp.n_col <= NCR) md_body<MIXED, true, CS>(d, S, rp, cl, step, rbuf, bbuf, do_bin, r);
     else md_body<MIXED, false, CS>(d, S, rp, cl, step, rbuf, bbuf, do_bin, r);
+}
+
+// ===========================================================================
+// Wide MD kernel (mixed path): one replica with many colloids, whose near
+// solvent is too large for one thread-block cluster.  A cooperative grid of
+// CTAs covers all SMs; every CTA keeps an identical copy of the colloids in
+// shared memory and integrates it with the general kernel's warp-0 code, from
+// force totals gathered once per sub-step through device memory and one
+// grid-wide barrier.  Each near particle keeps the (at most MDW_KC) colloids it
+// can reach during the interval, found once at the start with the near-list
+// radius plus a margin, so a force evaluation visits a few colloids instead
+// of all; a particle with more candidates scans every colloid.  Colloid pairs
+// within reach of the LJ cut-off (distance plus two skins) are listed once.
+// The forces are the same exact fixed-point sums as in the general kernel, so
+// both give bit-identical results.
+// ===========================================================================
+constexpr int MDW_NT = 256;
+constexpr int MDW_PPT = 2;             // near particles a thread keeps in registers
+constexpr int MDW_KC = 4;              // candidate colloids per particle
+constexpr int MDW_MAXP = 1024;         // listed colloid pairs
+constexpr float MDW_MARGIN = 1.5f;     // added to the near radius for the candidate test
+constexpr int MDW_SPIN_LIMIT = 1 << 24;
+
+struct WideShared {
+    ColM C;
+    float sigf[MAXC], epsAf[MAXC], epsBf[MAXC], rc2f[MAXC], Rbf[MAXC];
+    int cat[MAXC];
+    BondDev bond[MAXB];
+    unsigned long long Fq[MAXC * 3];   // this CTA's fixed-point partials
+    long long Fsum[MAXC * 3];          // the grid total
+    short pa[MDW_MAXP], pb[MDW_MAXP];
+    int npairs, all_pairs;
+    int nc, nbond, nn;
+    unsigned gen;                      // grid barrier generation seen by this CTA
+    int dead;                          // a grid barrier timed out: stop waiting
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier over co-resident CTAs: thread 0 of each CTA arrives on a
+// counter; the last one resets it and advances the generation the others
+// wait for (bounded: ERR_TIMEOUT, after which this CTA stops waiting).
+__device__ __forceinline__ void wide_barrier(const Dev &d, WideShared &S)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        MdWideGlobal *g = d.md_wide;
+        const unsigned gen = S.gen;
+        __threadfence();
+        if (atomicAdd(&g->count, 1u) == gridDim.x - 1u) {
+            g->count = 0u;
+            __threadfence();
+            st_release_u32(&g->gen, gen + 1u);
+        } else if (!S.dead) {
+            int spins = 0;
+            while (ld_acquire_u32(&g->gen) == gen) {
+                if (++spins > MDW_SPIN_LIMIT) {
+                    atomicOr(&d.err[ERR_TIMEOUT], 1u);
+                    S.dead = 1;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        S.gen = gen + 1u;
+    }
+    __syncthreads();
+}
+
+// Candidate colloids of a particle, packed 8 bits each into w.p0; the count
+// (or MDW_KC + 1: scan every colloid) into w.p1.
+__device__ __forceinline__ void wide_candidates(const ReplicaDev &rp, const WideShared &S, WorkM &w)
+{
+    const float st = sqrtf(w.v[0] * w.v[0] + w.v[1] * w.v[1] + w.v[2] * w.v[2]) * rp.tau_f;
+    unsigned packed = 0u;
+    int k = 0;
+    for (int j = 0; j < S.nc; ++j) {
+        float d[3];
+        sep_m(rp, S, j, w.c, w.o, d);
+        const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        const float R = S.Rbf[j] + st + MDW_MARGIN;
+        if (r2 < R * R) {
+            if (k < MDW_KC) packed |= (unsigned)j << (8 * k);
+            ++k;
+        }
+    }
+    w.p0 = __uint_as_float(packed);
+    w.p1 = __int_as_float(k > MDW_KC ? MDW_KC + 1 : k);
+}
+
+// The general kernel's force on one particle (atomic path), over the
+// particle's candidates in increasing colloid order; inside: within the
+// cut-off of a catalytic colloid.
+__device__ __forceinline__ void force_wide(const ReplicaDev &rp, WideShared &S, WorkM &w, bool &inside)
+{
+    w.f[0] = w.f[1] = w.f[2] = 0.0f;
+    inside = false;
+    const int ncand = __float_as_int(w.p1);
+    const unsigned packed = __float_as_uint(w.p0);
+    const int jn = ncand > MDW_KC ? S.nc : ncand;
+    for (int q = 0; q < jn; ++q) {
+        const int j = ncand > MDW_KC ? q : (int)((packed >> (8 * q)) & 0xFFu);
+        float d[3];
+        sep_m(rp, S, j, w.c, w.o, d);
+        const float eps = (w.fid & F_B) ? S.epsBf[j] : S.epsAf[j];
+        const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (r2 < S.rc2f[j]) {
+            inside = inside || S.cat[j];
+            const float fr = wca_fr_m(eps, S.sigf[j], r2);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float fk = fr * d[k];
+                w.f[k] = w.f[k] + fk;
+                const long long q64 = __float2ll_rn(fk * 0x1p40f);
+                atomicAdd(&S.Fq[3 * j + k], (unsigned long long)(-q64));
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) w.f[k] = w.f[k] + rp.g_f[k];
+}
+
+// One sub-step of a particle after the colloids moved: kicks, drift, force,
+// catalysis (s < 0: only the force, at the start of the interval).
+__device__ __forceinline__ void wide_particle(const ReplicaDev &rp, WideShared &S, WorkM &w, uint32_t step, int s)
+{
+    if (s >= 0) {
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            if (s > 0) w.v[t] = fmaf(rp.hdt_f, w.f[t], w.v[t]);
+            w.v[t] = fmaf(rp.hdt_f, w.f[t], w.v[t]);
+            w.o[t] = fmaf(rp.dt_f, w.v[t], w.o[t]);
+        }
+    }
+    bool inside;
+    force_wide(rp, S, w, inside);
+    if (s >= 0) w.fid = catalysis(rp, w.fid, inside, step, s);
+}
+
+// After a CTA barrier: this CTA's partials into the grid accumulator of round
+// `round` (three buffers: round r is zeroed by CTA 0 after the barrier of
+// round r - 1), the grid barrier, then warp 0 forms the colloid forces.
+__device__ __forceinline__ void wide_reduce(const Dev &d, const ReplicaDev &rp, WideShared &S, int round)
+{
+    MdWideGlobal *g = d.md_wide;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int b = round % 3;
+    __syncthreads();
+    for (int i = tid; i < 3 * S.nc; i += MDW_NT)
+        if (S.Fq[i] != 0ull) atomicAdd(&g->acc[b][i], S.Fq[i]);
+    wide_barrier(d, S);
+    if (tid < 32) {
+        for (int l = lane; l < 3 * S.nc; l += 32) S.Fsum[l] = (long long)__ldcg(&g->acc[b][l]);
+        __syncwarp();
+        if (rp.cc_rc > 0.0) {
+            const int np = S.all_pairs ? S.nc * S.nc : S.npairs;
+            for (int p = lane; p < np; p += 32) {
+                int a, c;
+                if (S.all_pairs) {
+                    a = p / S.nc;
+                    c = p % S.nc;
+                    if (c <= a || bonded(S.bond, S.nbond, a, c)) continue;
+                } else {
+                    a = S.pa[p];
+                    c = S.pb[p];
+                }
+                long long q[3];
+                if (!cc_pair_m(rp, S, a, c, q)) continue;
+                for (int k = 0; k < 3; ++k) {
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&S.Fsum[3 * a + k]), (unsigned long long)q[k]);
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&S.Fsum[3 * c + k]), (unsigned long long)(-q[k]));
+                }
+            }
+            __syncwarp();
+        }
+        for (int l = lane; l < 3 * S.nc; l += 32) S.C.F[l / 3][l % 3] = fixed40_to_float(S.Fsum[l]);
+        __syncwarp();
+    }
+    if (blockIdx.x == 0)
+        for (int i = tid; i < 3 * S.nc; i += MDW_NT) g->acc[(round + 2) % 3][i] = 0ull;
+}
+
+__global__ void __launch_bounds__(MDW_NT) k_md_wide(Dev d, int r, uint32_t step, int rbuf, int bbuf, int do_bin)
+{
+    __shared__ WideShared S;
+    __shared__ ReplicaDev s_rp;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) {
+        s_rp = d.rep[r];
+        S.gen = ld_acquire_u32(&d.md_wide->gen);
+        S.dead = 0;
+        S.npairs = 0;
+        S.all_pairs = 0;
+    }
+    __syncthreads();
+    const ReplicaDev &rp = s_rp;
+    if (rp.n_col == 0) return;   // uniform over the grid
+    if (tid == 0) {
+        S.nc = rp.n_col;
+        S.nbond = rp.n_bond;
+        S.nn = min(d.near_count[r], rp.n_part);
+    }
+    for (int j = tid; j < rp.n_col; j += MDW_NT) {
+        const int g = rp.col_off + j;
+        col_load(d, rp, S, j);
+        S.sigf[j] = d.colSig_f[g]; S.epsAf[j] = d.colEpsA_f[g]; S.epsBf[j] = d.colEpsB_f[g];
+        S.rc2f[j] = d.colRc2_f[g];
+        S.Rbf[j] = d.colRb_f[g];
+        S.cat[j] = d.colCat[g];
+    }
+    if (tid < rp.n_bond) S.bond[tid] = d.bonds[rp.bond_off + tid];
+    for (int i = tid; i < 3 * rp.n_col; i += MDW_NT) S.Fq[i] = 0ull;
+    __syncthreads();
+    if (rp.cc_rc > 0.0) {
+        // colloid pairs that can come within the cut-off this interval: each
+        // colloid moves at most `skin` (a violation is reported)
+        const float reach = (float)rp.cc_rc + 2.0f * rp.skin_f + 1e-3f;
+        for (int p = tid; p < S.nc * S.nc; p += MDW_NT) {
+            const int a = p / S.nc, c = p % S.nc;
+            if (c <= a || bonded(S.bond, S.nbond, a, c)) continue;
+            float dd[3];
+            for (int t = 0; t < 3; ++t) dd[t] = (float)(S.C.Ci[a][t] - S.C.Ci[c][t]) + (S.C.Xf[a][t] - S.C.Xf[c][t]);
+            min_image(rp, dd);
+            if (dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2] < reach * reach) {
+                const int k = atomicAdd(&S.npairs, 1);
+                if (k < MDW_MAXP) { S.pa[k] = (short)a; S.pb[k] = (short)c; }
+                else S.all_pairs = 1;
+            }
+        }
+    }
+    __syncthreads();
+
+    const int nn = S.nn;
+    const int *list = d.near_list + rp.part_off;
+    WorkM *work = reinterpret_cast<WorkM *>(d.md_work) + rp.part_off;
+    const int first = blockIdx.x * MDW_NT + tid;
+    const int stride = gridDim.x * MDW_NT;
+    const int over = first + MDW_PPT * stride;
+    WorkM reg[MDW_PPT];
+    auto load_w = [&](int k, WorkM &w) {
+        const int slot = list[k];
+        w.slot = slot;
+        const RecM rec = load_rec(reinterpret_cast<const RecM *>(d.rec[rbuf]) + slot);
+        for (int t = 0; t < 3; ++t) { w.c[t] = cw_get(rec.cw, t); w.o[t] = rec.o[t]; w.v[t] = rec.v[t]; }
+        w.fid = rec.fid;
+        wide_candidates(rp, S, w);
+    };
+    // forces at the start of the interval
+#pragma unroll
+    for (int p = 0; p < MDW_PPT; ++p)
+        if (first + p * stride < nn) {
+            load_w(first + p * stride, reg[p]);
+            wide_particle(rp, S, reg[p], step, -1);
+        }
+    for (int k = over; k < nn; k += stride) {
+        WorkM w;
+        load_w(k, w);
+        wide_particle(rp, S, w, step, -1);
+        work[k] = w;
+    }
+    wide_reduce(d, rp, S, 0);
+    __syncthreads();
+
+    for (int s = 0; s < rp.n_md; ++s) {
+        // colloids: first half kick, drift, RATTLE position stage
+        if (wid == 0) col_kick_drift_w(rp, S, lane);
+        for (int i = tid; i < 3 * S.nc; i += MDW_NT) S.Fq[i] = 0ull;
+        __syncthreads();
+        // solvent: second half kick of the previous sub-step, first half kick
+        // and drift of this one, new forces, catalytic conversion
+#pragma unroll
+        for (int p = 0; p < MDW_PPT; ++p)
+            if (first + p * stride < nn) wide_particle(rp, S, reg[p], step, s);
+        for (int k = over; k < nn; k += stride) {
+            WorkM w = work[k];
+            wide_particle(rp, S, w, step, s);
+            work[k] = w;
+        }
+        wide_reduce(d, rp, S, s + 1);
+        // colloids: second half kick, RATTLE velocity stage
+        if (wid == 0) col_kick_w(rp, S, lane);
+        __syncthreads();
+    }
+
+    // last half kick, wrap, write back (and bin for the collision of `step`)
+    double sh[3];
+    grid_shift(rp.seed, step, sh);
+    const float sf[3] = {(float)sh[0], (float)sh[1], (float)sh[2]};
+    auto finish = [&](WorkM &w) {
+        for (int t = 0; t < 3; ++t) w.v[t] = fmaf(rp.hdt_f, w.f[t], w.v[t]);
+        renorm_m(rp, w.c, w.o);
+        RecM rec;
+        rec.cw = cw_make(w.c[0], w.c[1], w.c[2]);
+        for (int t = 0; t < 3; ++t) { rec.o[t] = w.o[t]; rec.v[t] = w.v[t]; }
+        rec.fid = do_bin ? (w.fid | F_PROP) : (w.fid & ~F_PROP);
+        store_rec(reinterpret_cast<RecM *>(d.rec[rbuf]) + w.slot, rec);
+        if (do_bin) bin_particle(d, bbuf, rp.cell_off + cell_key_m(rp, w.c, w.o, sf), w.slot);
+    };
+#pragma unroll
+    for (int p = 0; p < MDW_PPT; ++p)
+        if (first + p * stride < nn) finish(reg[p]);
+    for (int k = over; k < nn; k += stride) {
+        WorkM w = work[k];
+        finish(w);
+    }
+    if (blockIdx.x == 0 && tid == 0) {
+        col_store(d, rp, S);
+        d.near_count[r] = 0;   // every CTA read it before the first grid barrier
+    }
+}
+
+// Co-resident CTAs the wide kernel can launch on this device (0: unsupported).
+int md_wide_grid()
+{
+    int dev = 0, sms = 0, per = 0, coop = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_md_wide, MDW_NT, 0) != cudaSuccess) per = 0;
+    cudaGetLastError();
+    return coop ? sms * per : 0;
+}
+
+void launch_md_wide(const Dev &d, const std::vector<int> &reps, int grid, uint32_t step, int rbuf, int bbuf,
+                    int do_bin, cudaStream_t s)
+{
+    for (int r : reps) {
+        cudaMemsetAsync(d.md_wide->acc, 0, sizeof(d.md_wide->acc), s);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)grid, 1, 1);
+        cfg.blockDim = dim3(MDW_NT, 1, 1);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, k_md_wide, d, r, step, rbuf, bbuf, do_bin);
+    }
 }
 
 template <bool MIXED, int CS>

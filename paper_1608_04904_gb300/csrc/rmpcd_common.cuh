@@ -85,6 +85,13 @@ __device__ __forceinline__ HotM hot_m(const ReplicaDev &rp)
     return h;
 }
 
+// Grid-wide scratch of the wide MD kernel: force accumulators of three
+// consecutive rounds and the grid barrier.
+struct MdWideGlobal {
+    unsigned long long acc[3][MAXC * 3];
+    unsigned int count, gen;
+};
+
 // All device pointers of a system (passed by value to every kernel).
 struct Dev {
     const ReplicaDev *rep;
@@ -110,6 +117,7 @@ struct Dev {
     const int *colCat;
     const BondDev *bonds;
     void *md_work;               // near-particle working state
+    MdWideGlobal *md_wide;       // wide MD kernel scratch
     int cap;
     int n_rep;
     int n_tiles;

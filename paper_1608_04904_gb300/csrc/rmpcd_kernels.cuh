@@ -1,6 +1,8 @@
 // rmpcd_kernels.cuh -- host-side launchers of the sm_103a kernels (internal).
 #pragma once
 
+#include <vector>
+
 #include "rmpcd_common.cuh"
 
 namespace rmpcd {
@@ -37,6 +39,11 @@ constexpr int MD_FAST_NC = 2;
 // cs: 1, 2, 4, 8 or 16 (16 when md_fast_max_cluster allows it)
 void launch_md_fast(bool mixed, const Dev &d, uint32_t step, int rbuf, int bbuf, int do_bin, int cs, cudaStream_t s);
 int md_fast_max_cluster(bool mixed);
+// The wide MD kernel (mixed path, many colloids): one cooperative launch of
+// `grid` CTAs per listed replica; md_wide_grid() gives the co-resident grid.
+void launch_md_wide(const Dev &d, const std::vector<int> &reps, int grid, uint32_t step, int rbuf, int bbuf,
+                    int do_bin, cudaStream_t s);
+int md_wide_grid();
 void launch_set_state(bool mixed, const Dev &d, int replica, int n, const double *x, const double *v,
                       const uint8_t *flags, int rbuf, cudaStream_t s);
 void launch_get_state(bool mixed, const Dev &d, int replica, int n, int rbuf, double *x, double *v, uint8_t *flags,

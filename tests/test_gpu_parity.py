@@ -380,13 +380,17 @@ def test_md_launch_choices_do_not_change_results(precision):
     cluster size (and the autotuned choice) gives bit-identical states."""
     cfg, col, bonds, x, v, fl = _dimer(precision, bulk_rate=0.05)
     ref = None
-    for kern in (1, 2):
+    for kern in (1, 2, 3):
         for cs in (1, 2, 4, 8, 16, 0):
+            if kern == 3 and cs > 1:
+                continue   # the wide kernel takes no cluster size
             g = gpu(cfg, x, v, fl, col, bonds, precision=precision)
             try:
                 g.set_tuning(cs, kern)
             except api.RmpcdError:
-                assert cs == 16   # 16-CTA clusters: few-colloid kernel on capable devices only
+                # 16-CTA clusters: few-colloid kernel on capable devices only;
+                # the wide kernel: mixed path only
+                assert cs == 16 or (kern == 3 and precision == "fp64")
                 continue
             g.step(14 if cs == 0 else 3)
             if cs == 0:
@@ -400,3 +404,26 @@ def test_md_launch_choices_do_not_change_results(precision):
                 for key in st:
                     assert np.array_equal(st[key], ref[0][key]), (kern, cs, key)
                 assert np.array_equal(cx, ref[1])
+
+
+def test_wide_md_kernel_matches_general_many_colloids():
+    """Six spheres with colloid-colloid LJ (mixed path): the wide cooperative
+    MD kernel gives the general kernel's states bit for bit."""
+    cfg = synth.base_config(L=(48, 32, 32), alpha=np.radians(130.0), tau=0.5, n_md=20, kT=1.0,
+                            cc_lj=(1.0, 3.0, 7.5), seed=7, precision="mixed")
+    rng = np.random.Generator(np.random.PCG64(8))
+    pos = [(8.0, 8.0, 8.0), (16.0, 9.0, 9.0), (30.0, 20.0, 12.0), (38.0, 24.0, 20.0), (10.0, 24.0, 24.0),
+           (24.0, 16.0, 26.0)]
+    col = [dict(x=p, v=tuple(rng.normal(0.0, 0.05, 3)), mass=120.0, sigma=2.0, eps_A=1.0, eps_B=0.5,
+                catalytic=int(k % 2)) for k, p in enumerate(pos)]
+    x, v, fl = synth.solvent(cfg, col, seed=9, frac_b=0.2)
+    out = []
+    for kern in (1, 3):
+        g = gpu(cfg, x, v, fl, col, [], precision="mixed")
+        g.set_tuning(1 if kern == 1 else 0, kern)
+        g.step(3)
+        out.append((g.get_state(), g.get_colloids(0)))
+    for key in out[0][0]:
+        assert np.array_equal(out[0][0][key], out[1][0][key]), key
+    assert np.array_equal(out[0][1]["x"], out[1][1]["x"])
+    assert np.array_equal(out[0][1]["v"], out[1][1]["v"])
