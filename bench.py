@@ -233,7 +233,16 @@ def make_system(api, reps, states, precision, stream):
 
 def timed_run(api, torch, reps, states, precision, steps, warmup, flush, dev_index, sample_clocks,
               barrier, md_cluster=0, md_kernel=0):
-    stream = torch.cuda.current_stream()
+    # a stream of its own: intervals replay as CUDA graphs (the legacy
+    # default stream cannot be captured)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        return _timed_run(api, torch, reps, states, precision, steps, warmup, flush, dev_index, sample_clocks,
+                          barrier, md_cluster, md_kernel, stream)
+
+
+def _timed_run(api, torch, reps, states, precision, steps, warmup, flush, dev_index, sample_clocks,
+               barrier, md_cluster, md_kernel, stream):
     s = make_system(api, reps, states, precision, stream)
     s.set_tuning(md_cluster, md_kernel)
     has_col = any(col for _, col, _ in reps)
@@ -243,8 +252,6 @@ def timed_run(api, torch, reps, states, precision, steps, warmup, flush, dev_ind
     torch.cuda.synchronize()
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    s.enable_timers(True)
-    s.read_timers(reset=True)
     launches0 = s.launch_count()
     clk = ClockSampler(dev_index) if sample_clocks else None
     if clk:
@@ -262,6 +269,13 @@ def timed_run(api, torch, reps, states, precision, steps, warmup, flush, dev_ind
     clocks = clk.stop() if clk else None
     launches = s.launch_count() - launches0
     ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+    # per-kernel times: a further run with the library's timers (events
+    # around each launch, so direct launches instead of graphs)
+    s.enable_timers(True)
+    s.read_timers(reset=True)
+    for _ in range(min(steps, 200)):
+        flush.zero_()
+        s.step(1)
     timers = s.read_timers(reset=True)
     s.enable_timers(False)
     obs = s.observables(0)
@@ -397,7 +411,8 @@ def main():
                    "precision": args.precision,
                    "parallelism": "replicas" if ws > 1 else "single",
                    "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
-                   "timing": "CUDA events around each rmpcd_step(1) on the library's stream",
+                   "timing": "CUDA events around each rmpcd_step(1) on the library's stream (intervals replayed "
+                             "as CUDA graphs); per-kernel times from a further run with the library's timers",
                    "md_cluster": obs["md_cluster"], "md_kernel": obs["md_kernel"]},
         "roofline": roofline, "kernels": kernels, "gpu_launches": launches, "clocks": clocks,
         "observables": {"temperature": obs["temperature"], "n_B": obs["n_B"], "kT": cfg["kT"]},

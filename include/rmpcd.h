@@ -210,6 +210,14 @@ rmpcd_status rmpcd_read_timers(rmpcd_system *sys, rmpcd_timers *out, int32_t res
 rmpcd_status rmpcd_set_tuning(rmpcd_system *sys, int32_t md_cluster, int32_t md_kernel);
 rmpcd_status rmpcd_get_tuning(const rmpcd_system *sys, int32_t *md_cluster, int32_t *md_kernel);
 
+/* CUDA graphs for rmpcd_step (on by default): once the MD launch geometry is
+ * settled (cluster size fixed or tuned) and timers are off, each fused
+ * interval replays a captured graph of its launches (one per buffer parity;
+ * the collision index is read and advanced on the device).  The legacy
+ * default stream cannot be captured: a system created on it launches
+ * directly.  Results are identical either way.  Errors: EINVAL. */
+rmpcd_status rmpcd_set_graphs(rmpcd_system *sys, int32_t on);
+
 /* Count of this library's kernel launches since creation (for accounting). */
 rmpcd_status rmpcd_launch_count(const rmpcd_system *sys, int64_t *count);
 

@@ -64,7 +64,7 @@ EXPORTS = [
     "rmpcd_get_colloids", "rmpcd_set_step", "rmpcd_get_step", "rmpcd_stream", "rmpcd_shift_and_sort",
     "rmpcd_collide", "rmpcd_react", "rmpcd_step", "rmpcd_observables", "rmpcd_sync", "rmpcd_launch_count",
     "rmpcd_last_error", "rmpcd_enable_timers", "rmpcd_read_timers", "rmpcd_set_tuning", "rmpcd_get_tuning",
-    "rmpcd_observables_noalloc",
+    "rmpcd_observables_noalloc", "rmpcd_set_graphs",
 ]
 
 _LIB = None
@@ -102,6 +102,7 @@ def load():
     L.rmpcd_enable_timers.argtypes = [vp, i32]
     L.rmpcd_read_timers.argtypes = [vp, P(Timers), i32]
     L.rmpcd_set_tuning.argtypes = [vp, i32, i32]
+    L.rmpcd_set_graphs.argtypes = [vp, i32]
     L.rmpcd_get_tuning.argtypes = [vp, P(i32), P(i32)]
     L.rmpcd_observables_noalloc.argtypes = [vp, vp, vp, i64, i32, vp, vp]
     L.rmpcd_last_error.argtypes = [vp]
@@ -326,6 +327,9 @@ class System:
 
     def set_tuning(self, md_cluster=0, md_kernel=0):
         self._check(self._lib.rmpcd_set_tuning(self._h, int(md_cluster), int(md_kernel)))
+
+    def set_graphs(self, on=True):
+        self._check(self._lib.rmpcd_set_graphs(self._h, 1 if on else 0))
 
     def get_tuning(self):
         """(md_cluster, md_kernel) in use; md_cluster is 0 while tuning."""

@@ -43,7 +43,6 @@ struct rmpcd_system {
     bool has_sort = false;
     uint32_t sort_step = 0;
     bool obs_valid = false;
-    uint32_t epoch = 0;
     long long launches = 0;
     std::string err;
     // per-phase timers
@@ -66,7 +65,14 @@ struct rmpcd_system {
     int md_wide_grid = 0;             // co-resident CTAs of the wide MD kernel (0: unavailable)
     std::vector<int> wide_reps;       // replicas with colloids (wide kernel: one launch each)
     std::vector<Pending> md_trials;   // phase field holds the cluster size
+    // CUDA graphs of one fused interval, one per (record, bucket) buffer
+    // parity; built once the MD launch geometry is settled
+    bool graphs_on = true;
+    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int graph_nodes = 0;              // kernel launches per replay
 };
+
+static void drop_graphs(rmpcd_system *sys);
 
 static cudaEvent_t pool_event(rmpcd_system *sys)
 {
@@ -286,6 +292,7 @@ void rmpcd_destroy(rmpcd_system *sys)
 {
     if (!sys) return;
     cudaStreamSynchronize(sys->stream);
+    drop_graphs(sys);
     for (void *p : sys->allocs) cudaFree(p);
     for (auto &q : sys->pending) { sys->ev_pool.push_back(q.a); sys->ev_pool.push_back(q.b); }
     for (auto &q : sys->md_trials) { sys->ev_pool.push_back(q.a); sys->ev_pool.push_back(q.b); }
@@ -426,6 +433,7 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
     AL(&d.colCi, 3 * n_col);
     AL(&d.colXf, 3 * n_col);
     AL(&d.md_wide, 1);
+    AL(&d.ctl, 1);
     AL(&d.colVf, 3 * n_col);
     AL(&dRb, n_col);
     AL(&dIM, n_col);
@@ -478,6 +486,7 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
     zero(d.err, sizeof(unsigned int) * ERR_COUNT);
     zero(d.obs_out, sizeof(double) * 8 * n_replicas);
     if (st == RMPCD_OK) zero(d.md_wide, sizeof(MdWideGlobal));
+    if (st == RMPCD_OK) zero(d.ctl, sizeof(Ctl));
     if (st == RMPCD_OK) st = cuda_check(sys, cudaStreamSynchronize(s), "create sync");
     if (st != RMPCD_OK) {
         g_create_error = sys->err;
@@ -514,12 +523,15 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
 // ----------------------------------------------------------------------------
 // pipeline helpers
 // ----------------------------------------------------------------------------
-// Launch counter of the cell pass: its parity selects the ticket counter,
-// consecutive launches alternate; the kernel derives its look-back tag from it.
-static uint32_t next_epoch(rmpcd_system *sys)
+// Drop the captured interval graphs (the MD launch geometry changed).
+static void drop_graphs(rmpcd_system *sys)
 {
-    sys->epoch += 1u;
-    return sys->epoch;
+    for (auto &row : sys->graph)
+        for (auto &g : row)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
 }
 
 // Drop a primed fused pipeline (pending bins and near lists).
@@ -541,7 +553,7 @@ static rmpcd_status rebin_pass(rmpcd_system *sys, uint32_t grid_step, int opts, 
     launch_particles(sys->mixed, sys->d, PM_BIN, grid_step, sys->cur, b, sys->stream);
     rmpcd_status st = after_launch(sys, 1);
     if (st != RMPCD_OK) return st;
-    CellPassArgs a{opts, grid_step, b, b ^ 1, sys->cur, sys->cur ^ 1, next_epoch(sys)};
+    CellPassArgs a{opts, grid_step, b, b ^ 1, sys->cur, sys->cur ^ 1};
     launch_cellpass(sys->mixed, sys->d, a, sys->stream);
     st = after_launch(sys, 1);
     if (st != RMPCD_OK) return st;
@@ -706,7 +718,8 @@ rmpcd_status rmpcd_set_step(rmpcd_system *sys, uint32_t step)
     rmpcd_status st = unprime(sys);
     if (st != RMPCD_OK) return st;
     sys->step = step;
-    return RMPCD_OK;
+    launch_set_step(sys->d, step, sys->stream);
+    return after_launch(sys, 1);
 }
 
 rmpcd_status rmpcd_get_step(const rmpcd_system *sys, uint32_t *step)
@@ -803,6 +816,62 @@ static void md_trial_done(rmpcd_system *sys, int cs, cudaEvent_t a)
     sys->md_tuned = true;
 }
 
+// The launches of one fused interval on buffers (cur, bcur), the step taken
+// from the control block (STEP_DEVICE) and advanced by the cell pass; timers
+// and the MD tuner wrap the launches when active.  Returns the launch count.
+static int launch_interval(rmpcd_system *sys, int cur, int bcur, bool instrument)
+{
+    int n = 0;
+    cudaEvent_t ev = nullptr, tev = nullptr;
+    if (sys->any_colloids) {
+        const int cs = instrument ? md_cluster_for_launch(sys, &tev) : (sys->md_fixed ? sys->md_fixed : sys->md_best);
+        if (instrument) tstart(sys, &ev);
+        if (sys->md_kernel == 3) {
+            launch_md_wide(sys->d, sys->wide_reps, sys->md_wide_grid, STEP_DEVICE, cur, bcur, 1, sys->stream);
+            n += (int)sys->wide_reps.size();
+        } else {
+            if (sys->md_kernel == 2) launch_md_fast(sys->mixed, sys->d, STEP_DEVICE, cur, bcur, 1, cs, sys->stream);
+            else launch_md(sys->mixed, sys->d, STEP_DEVICE, cur, bcur, 1, cs, sys->stream);
+            n += 1;
+        }
+        if (instrument) {
+            tstop(sys, 1, ev);
+            md_trial_done(sys, cs, tev);
+        }
+    }
+    CellPassArgs a{CP_FLIGHT | CP_COLLIDE | CP_REACT | CP_NEXT | CP_WRITE | CP_ADVANCE, STEP_DEVICE, bcur, bcur ^ 1,
+                   cur, cur ^ 1};
+    if (instrument) tstart(sys, &ev);
+    launch_cellpass(sys->mixed, sys->d, a, sys->stream);
+    if (instrument) tstop(sys, 2, ev);
+    return n + 1;
+}
+
+// The graph of one fused interval on buffers (cur, bcur), captured on first
+// use; nullptr when capture is not possible on this stream.
+static cudaGraphExec_t interval_graph(rmpcd_system *sys, int cur, int bcur)
+{
+    cudaGraphExec_t &ge = sys->graph[cur][bcur];
+    if (ge) return ge;
+    if (sys->stream == nullptr) return nullptr;   // the legacy default stream cannot be captured
+    if (cudaStreamBeginCapture(sys->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    const int n = launch_interval(sys, cur, bcur, false);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(sys->stream, &g);
+    if (e == cudaSuccess && g) e = cudaGraphInstantiate(&ge, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ge = nullptr;
+        return nullptr;
+    }
+    sys->graph_nodes = n;
+    return ge;
+}
+
 rmpcd_status rmpcd_step(rmpcd_system *sys, int32_t n_intervals)
 {
     if (!sys) return RMPCD_EINVAL;
@@ -819,35 +888,36 @@ rmpcd_status rmpcd_step(rmpcd_system *sys, int32_t n_intervals)
         if ((st = after_launch(sys, sys->n_total > 0 ? 1 : 0)) != RMPCD_OK) return st;
         sys->primed = true;
     }
-    for (int i = 0; i < n_intervals; ++i) {
-        if (sys->any_colloids) {
-            cudaEvent_t tev;
-            const int cs = md_cluster_for_launch(sys, &tev);
-            tstart(sys, &ev);
-            if (sys->md_kernel == 3)
-                launch_md_wide(sys->d, sys->wide_reps, sys->md_wide_grid, sys->step, sys->cur, sys->bcur, 1,
-                               sys->stream);
-            else if (sys->md_kernel == 2)
-                launch_md_fast(sys->mixed, sys->d, sys->step, sys->cur, sys->bcur, 1, cs, sys->stream);
-            else launch_md(sys->mixed, sys->d, sys->step, sys->cur, sys->bcur, 1, cs, sys->stream);
-            tstop(sys, 1, ev);
-            md_trial_done(sys, cs, tev);
-            if ((st = after_launch(sys, sys->md_kernel == 3 ? (int)sys->wide_reps.size() : 1)) != RMPCD_OK)
-                return st;
+    int left = n_intervals;
+    while (left > 0) {
+        // a captured graph of the interval once nothing on the host side
+        // watches single launches (timers, the MD tuner)
+        const bool settled = !sys->any_colloids || sys->md_fixed || sys->md_tuned;
+        cudaGraphExec_t ge = nullptr;
+        if (sys->graphs_on && settled && !sys->timing) ge = interval_graph(sys, sys->cur, sys->bcur);
+        if (ge) {
+            CK(cudaGraphLaunch(ge, sys->stream));
+            if ((st = after_launch(sys, sys->graph_nodes)) != RMPCD_OK) return st;
+        } else {
+            const int n = launch_interval(sys, sys->cur, sys->bcur, true);
+            if ((st = after_launch(sys, n)) != RMPCD_OK) return st;
         }
-        CellPassArgs a{CP_FLIGHT | CP_COLLIDE | CP_REACT | CP_NEXT | CP_WRITE, sys->step, sys->bcur, sys->bcur ^ 1,
-                       sys->cur, sys->cur ^ 1, next_epoch(sys)};
-        tstart(sys, &ev);
-        launch_cellpass(sys->mixed, sys->d, a, sys->stream);
-        tstop(sys, 2, ev);
-        if ((st = after_launch(sys, 1)) != RMPCD_OK) return st;
         sys->cur ^= 1;
         sys->bcur ^= 1;
         sys->sort_step = sys->step;
         sys->step += 1u;
+        left -= 1;
     }
     sys->has_sort = true;
     sys->obs_valid = false;   // observables are computed on request
+    return RMPCD_OK;
+}
+
+// Capture and replay of fused intervals as CUDA graphs (on by default).
+rmpcd_status rmpcd_set_graphs(rmpcd_system *sys, int32_t on)
+{
+    if (!sys) return RMPCD_EINVAL;
+    sys->graphs_on = on != 0;
     return RMPCD_OK;
 }
 
@@ -932,6 +1002,7 @@ rmpcd_status rmpcd_set_tuning(rmpcd_system *sys, int32_t md_cluster, int32_t md_
         !(md_cluster == 16 && maxc >= 16))
         return fail(sys, RMPCD_EINVAL, "md_cluster must be 0 (tune), 1, 2, 4, 8%s", maxc >= 16 ? " or 16" : "");
     set_md_kernel(sys, md_kernel);
+    drop_graphs(sys);
     sys->md_fixed = md_cluster;
     if (md_cluster == 0) {
         sys->md_tuned = false;

@@ -100,6 +100,7 @@ struct TileShared {
     ReplicaDev rp;
     NearFrames nf;
     int tile, r, base, maxcnt;
+    uint32_t epoch, step;     // this launch's counter and collision index (from the control block)
     int next;   // first cell of the next chunk a warp may take
     int cnt[CPT], ls[CPT + 1], wt[CPT / 32];
     double sh[3], shn[3];     // fp64 path
@@ -562,7 +563,7 @@ __device__ __forceinline__ int batch_end(const int *ls, int cb, int cend, int ca
 }
 
 template <bool MIXED>
-__global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, CellPassArgs a)
+__global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, CellPassArgs a0)
 {
     using Rec = typename Traits<MIXED>::Rec;
     constexpr int WPC = Traits<MIXED>::WPC;
@@ -576,14 +577,28 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0) {
-        const int tile = (int)atomicAdd(&d.ticket[a.epoch & 1u], 1u);
+        // the launch counter and the step, read before the ticket is taken:
+        // the CTA with the last ticket advances them after every CTA has read
+        const uint32_t epoch = *(volatile uint32_t *)&d.ctl->epoch;
+        const uint32_t step = resolve_step(d, a0.step);
+        __threadfence();
+        const int tile = (int)atomicAdd(&d.ticket[epoch & 1u], 1u);
         T.tile = tile;
+        T.epoch = epoch;
+        T.step = step;
         T.r = tile < d.n_tiles ? d.tile_rep[tile] : 0;
         T.maxcnt = 0;
         T.next = 0;
-        if (blockIdx.x == 0) d.ticket[(a.epoch + 1u) & 1u] = 0u;
+        if (blockIdx.x == 0) d.ticket[(epoch + 1u) & 1u] = 0u;
+        if (tile == d.n_tiles - 1) {
+            __threadfence();
+            d.ctl->epoch = epoch + 1u;
+            if (a0.opts & CP_ADVANCE) d.ctl->step = step + 1u;
+        }
     }
     __syncthreads();
+    CellPassArgs a = a0;
+    a.step = T.step;
     const int tile = T.tile;
     if (tile >= d.n_tiles) return;
     {
@@ -642,7 +657,7 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
     // warp path the other warps start on their cells meanwhile.
     const bool warp_path = T.maxcnt <= WPC;
     if (tid < 32) {
-        const int base = tile_lookback(d, a.epoch, tile, T.ls[CPT], lane);
+        const int base = tile_lookback(d, T.epoch, tile, T.ls[CPT], lane);
         if (lane == 0) T.base = base;
         __syncwarp();
         if (warp_path) base_arrive();

@@ -778,6 +778,7 @@ __device__ void md_body(const Dev &d, MDShared<MIXED> &S, const ReplicaDev &rp, 
 template <bool MIXED, int CS>
 __global__ void __launch_bounds__(MDGeom<CS>::NT, 1) k_md(Dev d, uint32_t step, int rbuf, int bbuf, int do_bin)
 {
+    step = resolve_step(d, step);   // STEP_DEVICE: the step of the control block
     __shared__ MDShared<MIXED> S;
     __shared__ ReplicaDev s_rp;
     cg::cluster_group cl = cg::this_cluster();
@@ -1004,6 +1005,7 @@ __device__ __forceinline__ void wide_reduce(const Dev &d, const ReplicaDev &rp, 
 
 __global__ void __launch_bounds__(MDW_NT) k_md_wide(Dev d, int r, uint32_t step, int rbuf, int bbuf, int do_bin)
 {
+    step = resolve_step(d, step);   // STEP_DEVICE: the step of the control block
     __shared__ WideShared S;
     __shared__ ReplicaDev s_rp;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;

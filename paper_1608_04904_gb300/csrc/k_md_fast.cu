@@ -521,6 +521,7 @@ __device__ __forceinline__ void send_partials(FShared &S, int rank, int b, int l
 template <bool MIXED, int CS>
 __global__ void __launch_bounds__(MDF_NT, 1) k_md_fast(Dev d, uint32_t step, int rbuf, int bbuf, int do_bin)
 {
+    step = resolve_step(d, step);   // STEP_DEVICE: the step of the control block
     using W = typename std::conditional<MIXED, FWorkM, FWorkD>::type;
     using Lane = typename std::conditional<MIXED, LaneM, LaneD>::type;
     using ColP = typename std::conditional<MIXED, ColPM, ColPD>::type;

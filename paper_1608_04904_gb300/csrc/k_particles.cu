@@ -116,6 +116,7 @@ __global__ void k_get_state_d(Dev d, int r, int n, int rbuf, double *x, double *
 template <bool MIXED>
 __global__ void k_particles(Dev d, int mode, uint32_t step, int rbuf, int bbuf)
 {
+    step = resolve_step(d, step);   // STEP_DEVICE: the step of the control block
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n_total) return;
     const int r = replica_of(d, i);
@@ -194,6 +195,10 @@ __global__ void k_obs_reduce(Dev d)
     }
     if (tid < 8) d.obs_out[r * 8 + tid] = part[0][tid];
 }
+
+__global__ void k_set_step(Dev d, uint32_t step) { d.ctl->step = step; }
+
+void launch_set_step(const Dev &d, uint32_t step, cudaStream_t s) { k_set_step<<<1, 1, 0, s>>>(d, step); }
 
 void launch_set_state(bool mixed, const Dev &d, int replica, int n, const double *x, const double *v,
                       const uint8_t *flags, int rbuf, cudaStream_t s)

@@ -85,6 +85,17 @@ __device__ __forceinline__ HotM hot_m(const ReplicaDev &rp)
     return h;
 }
 
+// Device-resident interval control: the collision index of the next fused
+// interval and the launch counter of the cell pass (ticket parity and
+// look-back tag).  Kernels launched with step == STEP_DEVICE read the step
+// here; the cell pass advances both, so a captured CUDA graph of intervals
+// replays without any argument update.
+struct Ctl {
+    uint32_t step;
+    uint32_t epoch;
+};
+constexpr uint32_t STEP_DEVICE = 0xFFFFFFFFu;
+
 // Grid-wide scratch of the wide MD kernel: force accumulators of three
 // consecutive rounds and the grid barrier.
 struct MdWideGlobal {
@@ -118,11 +129,17 @@ struct Dev {
     const BondDev *bonds;
     void *md_work;               // near-particle working state
     MdWideGlobal *md_wide;       // wide MD kernel scratch
+    Ctl *ctl;                    // interval control (step, cell-pass launch counter)
     int cap;
     int n_rep;
     int n_tiles;
     int n_total;
 };
+
+__device__ __forceinline__ uint32_t resolve_step(const Dev &d, uint32_t step)
+{
+    return step == STEP_DEVICE ? *(volatile const uint32_t *)&d.ctl->step : step;
+}
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): 10 rounds of the

@@ -14,21 +14,23 @@ enum CellPassOpt {
     CP_REACT = 4,     // bulk B -> A reaction
     CP_NEXT = 8,      // classify and bin every written record for the next collision
     CP_OBS = 16,      // per-tile observable partial sums
-    CP_WRITE = 32     // write the gathered (sorted) records to the output buffer
+    CP_WRITE = 32,    // write the gathered (sorted) records to the output buffer
+    CP_ADVANCE = 64   // advance the device step after the pass (fused intervals)
 };
 
 struct CellPassArgs {
     int opts;
-    uint32_t step;     // collision index: grid shift, rotation axes, reactions
+    uint32_t step;     // collision index: grid shift, rotation axes, reactions (STEP_DEVICE: Ctl::step)
     int cur;           // count / bucket buffer consumed
     int nxt;           // count / bucket buffer filled by CP_NEXT
     int rin, rout;     // record buffers
-    uint32_t epoch;    // launch counter: parity picks the ticket, (epoch % 65535) + 1 tags the look-back
 };
 
 enum ParticleMode { PM_STREAM = 0, PM_BIN = 1, PM_PRIME = 2 };
 
 void launch_cellpass(bool mixed, const Dev &d, const CellPassArgs &a, cudaStream_t s);
+// Set the device step (Ctl::step) on the stream.
+void launch_set_step(const Dev &d, uint32_t step, cudaStream_t s);
 void launch_particles(bool mixed, const Dev &d, int mode, uint32_t step, int rbuf, int bbuf, cudaStream_t s);
 // cs: CTAs per replica cluster, one of MD_CLUSTER_SIZES (results do not depend on it)
 extern const int MD_CLUSTER_SIZES[4];

@@ -427,3 +427,29 @@ def test_wide_md_kernel_matches_general_many_colloids():
         assert np.array_equal(out[0][0][key], out[1][0][key]), key
     assert np.array_equal(out[0][1]["x"], out[1][1]["x"])
     assert np.array_equal(out[0][1]["v"], out[1][1]["v"])
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_graph_replay_equals_direct_launches(precision):
+    """Intervals replayed from captured CUDA graphs (device-resident step)
+    give the same states as direct launches, also across rmpcd_set_step."""
+    import torch
+    cfg, col, bonds, x, v, fl = _dimer(precision, bulk_rate=0.05)
+    outs = []
+    for graphs in (True, False):
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            g = api.System.single(cfg, len(x), col, bonds, precision=precision, stream=stream)
+            g.set_graphs(graphs)
+            g.set_tuning(2, 0)
+            g.set_state(0, x, v, fl)
+            g.step(3)
+            g.set_step(40)
+            g.step(2)
+            assert g.get_step() == 42
+            outs.append((g.get_state(), g.get_colloids(0)["x"], g.observables(0)["temperature"]))
+            g.close()
+    for key in outs[0][0]:
+        assert np.array_equal(outs[0][0][key], outs[1][0][key]), key
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2] == outs[1][2]
