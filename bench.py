@@ -224,7 +224,7 @@ def run_reference(args, ws, rank):
 
 def make_system(api, reps, states, precision, stream):
     s = api.System([dict(cfg=cfg, n=len(st[0]), colloids=col, bonds=bonds) for (cfg, col, bonds), st in
-                    zip(reps, states)], precision=precision, bucket_cap=reps[0][0].get("bucket_cap", 64),
+                    zip(reps, states)], precision=precision, bucket_cap=reps[0][0].get("bucket_cap", 0),
                    stream=stream)
     for r, (x, v, fl) in enumerate(states):
         s.set_state(r, x, v, fl)
@@ -280,6 +280,7 @@ def _timed_run(api, torch, reps, states, precision, steps, warmup, flush, dev_in
     s.enable_timers(False)
     obs = s.observables(0)
     obs["md_cluster"], obs["md_kernel"] = s.get_tuning()
+    obs["bucket_cap"] = s.bucket_cap()
     s.close()
     return ms, timers, launches, clocks, obs
 
@@ -413,7 +414,8 @@ def main():
                    "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
                    "timing": "CUDA events around each rmpcd_step(1) on the library's stream (intervals replayed "
                              "as CUDA graphs); per-kernel times from a further run with the library's timers",
-                   "md_cluster": obs["md_cluster"], "md_kernel": obs["md_kernel"]},
+                   "md_cluster": obs["md_cluster"], "md_kernel": obs["md_kernel"],
+                   "bucket_cap": obs["bucket_cap"]},
         "roofline": roofline, "kernels": kernels, "gpu_launches": launches, "clocks": clocks,
         "observables": {"temperature": obs["temperature"], "n_B": obs["n_B"], "kT": cfg["kT"]},
     }

@@ -108,7 +108,11 @@ typedef struct {
  * concatenated in replica order (params[r].n_colloids / n_bonds entries each;
  * may be NULL when all counts are 0).  precision: rmpcd_precision.
  * bucket_cap: most particles one cell may hold (1..768; 64 is safe at
- * density 10).  stream: a cudaStream_t, or NULL for the legacy default
+ * density 10), or 0: picked automatically (the bucket-width autotuner:
+ * 1.25x the count above which a Poisson cell count at the densest replica
+ * occurs with probability < 1e-4 per collision, in multiples of 8, then
+ * grown to 1.5x the largest count whenever a binning or a run comes within
+ * 80 % of it).  stream: a cudaStream_t, or NULL for the legacy default
  * stream.  Solvent state is all zero until rmpcd_set_state.
  * Errors: EINVAL (bad sizes or parameters), ENOMEM, ECUDA. */
 rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_replicas,
@@ -217,6 +221,9 @@ rmpcd_status rmpcd_get_tuning(const rmpcd_system *sys, int32_t *md_cluster, int3
  * default stream cannot be captured: a system created on it launches
  * directly.  Results are identical either way.  Errors: EINVAL. */
 rmpcd_status rmpcd_set_graphs(rmpcd_system *sys, int32_t on);
+
+/* The bucket width in use (the automatic one when created with 0). */
+rmpcd_status rmpcd_get_bucket_cap(const rmpcd_system *sys, int32_t *cap);
 
 /* Count of this library's kernel launches since creation (for accounting). */
 rmpcd_status rmpcd_launch_count(const rmpcd_system *sys, int64_t *count);

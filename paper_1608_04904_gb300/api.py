@@ -64,7 +64,7 @@ EXPORTS = [
     "rmpcd_get_colloids", "rmpcd_set_step", "rmpcd_get_step", "rmpcd_stream", "rmpcd_shift_and_sort",
     "rmpcd_collide", "rmpcd_react", "rmpcd_step", "rmpcd_observables", "rmpcd_sync", "rmpcd_launch_count",
     "rmpcd_last_error", "rmpcd_enable_timers", "rmpcd_read_timers", "rmpcd_set_tuning", "rmpcd_get_tuning",
-    "rmpcd_observables_noalloc", "rmpcd_set_graphs",
+    "rmpcd_observables_noalloc", "rmpcd_set_graphs", "rmpcd_get_bucket_cap",
 ]
 
 _LIB = None
@@ -103,6 +103,7 @@ def load():
     L.rmpcd_read_timers.argtypes = [vp, P(Timers), i32]
     L.rmpcd_set_tuning.argtypes = [vp, i32, i32]
     L.rmpcd_set_graphs.argtypes = [vp, i32]
+    L.rmpcd_get_bucket_cap.argtypes = [vp, P(i32)]
     L.rmpcd_get_tuning.argtypes = [vp, P(i32), P(i32)]
     L.rmpcd_observables_noalloc.argtypes = [vp, vp, vp, i64, i32, vp, vp]
     L.rmpcd_last_error.argtypes = [vp]
@@ -211,7 +212,7 @@ class System:
     @classmethod
     def single(cls, cfg, n, colloids=(), bonds=(), precision=None, bucket_cap=None, stream=None):
         precision = precision or cfg.get("precision", "mixed")
-        bucket_cap = bucket_cap or cfg.get("bucket_cap", 64)
+        bucket_cap = cfg.get("bucket_cap", 64) if bucket_cap is None else bucket_cap
         return cls([dict(cfg=cfg, n=n, colloids=list(colloids), bonds=list(bonds))], precision, bucket_cap, stream)
 
     def close(self):
@@ -327,6 +328,11 @@ class System:
 
     def set_tuning(self, md_cluster=0, md_kernel=0):
         self._check(self._lib.rmpcd_set_tuning(self._h, int(md_cluster), int(md_kernel)))
+
+    def bucket_cap(self) -> int:
+        c = C.c_int32()
+        self._check(self._lib.rmpcd_get_bucket_cap(self._h, C.byref(c)))
+        return int(c.value)
 
     def set_graphs(self, on=True):
         self._check(self._lib.rmpcd_set_graphs(self._h, 1 if on else 0))

@@ -68,6 +68,12 @@ struct rmpcd_system {
     // CUDA graphs of one fused interval, one per (record, bucket) buffer
     // parity; built once the MD launch geometry is settled
     bool graphs_on = true;
+    // bucket width: fixed, or picked from the densities and grown on the
+    // largest cell count seen (bucket_cap = 0 at creation)
+    bool cap_auto = false;
+    unsigned int *maxcnt_host = nullptr;   // pinned: largest cell count of the last fused run
+    cudaEvent_t maxcnt_ev = nullptr;
+    bool maxcnt_pending = false;
     cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     int graph_nodes = 0;              // kernel launches per replay
 };
@@ -293,11 +299,91 @@ void rmpcd_destroy(rmpcd_system *sys)
     if (!sys) return;
     cudaStreamSynchronize(sys->stream);
     drop_graphs(sys);
+    if (sys->maxcnt_host) cudaFreeHost(sys->maxcnt_host);
+    if (sys->maxcnt_ev) cudaEventDestroy(sys->maxcnt_ev);
     for (void *p : sys->allocs) cudaFree(p);
     for (auto &q : sys->pending) { sys->ev_pool.push_back(q.a); sys->ev_pool.push_back(q.b); }
     for (auto &q : sys->md_trials) { sys->ev_pool.push_back(q.a); sys->ev_pool.push_back(q.b); }
     for (cudaEvent_t e : sys->ev_pool) cudaEventDestroy(e);
     delete sys;
+}
+
+// Bucket width from the densities: 1.25 x the count above which a Poisson
+// cell count at the densest replica's mean occurs with probability below
+// 1e-4 over all cells of the system per collision (so that the largest
+// counts stay below the 80 % growth threshold), as a multiple of 8, >= 16.
+static int auto_cap(const rmpcd_params *p, int n_rep)
+{
+    long long cells = 0;
+    double m = 0.0;
+    for (int r = 0; r < n_rep; ++r) {
+        const long long c = (long long)p[r].L[0] * p[r].L[1] * (p[r].L[2] + (p[r].walls ? 1 : 0));
+        cells += c;
+        if (c > 0) m = std::max(m, (double)p[r].n_solvent / (double)c);
+    }
+    if (m <= 0.0) return 16;
+    // P(N > k) by summing the pmf upwards from the mean outwards (no underflow
+    // for the densities of interest)
+    int k = 0;
+    double pmf = exp(-m), cdf = pmf;
+    while (k < CP_MAX_CAP && (1.0 - cdf) * (double)cells >= 1e-4) {
+        ++k;
+        pmf *= m / (double)k;
+        cdf += pmf;
+    }
+    int cap = std::max(16, (((k + 1) * 5 / 4 + 7) / 8) * 8);
+    return std::min(cap, CP_MAX_CAP);
+}
+
+// Re-allocate the buckets for width `cap` (at a step boundary: the pending
+// bins are dropped and rebuilt by the next pass).
+static rmpcd_status set_bucket_cap(rmpcd_system *sys, int cap)
+{
+    CK(cudaStreamSynchronize(sys->stream));
+    drop_graphs(sys);
+    const size_t ncells = (size_t)sys->n_tiles * CPT;
+    for (int b = 0; b < 2; ++b) {
+        auto it = std::find(sys->allocs.begin(), sys->allocs.end(), static_cast<void *>(sys->d.bucket[b]));
+        if (it != sys->allocs.end()) sys->allocs.erase(it);
+        cudaFree(sys->d.bucket[b]);
+        sys->d.bucket[b] = nullptr;
+    }
+    rmpcd_status st = dalloc(sys, &sys->d.bucket[0], ncells * (size_t)cap);
+    if (st == RMPCD_OK) st = dalloc(sys, &sys->d.bucket[1], ncells * (size_t)cap);
+    if (st != RMPCD_OK) return st;
+    sys->cap = cap;
+    sys->d.cap = cap;
+    CK(cudaMemsetAsync(sys->d.count[0], 0, sizeof(int) * ncells, sys->stream));
+    CK(cudaMemsetAsync(sys->d.count[1], 0, sizeof(int) * ncells, sys->stream));
+    CK(cudaMemsetAsync(sys->d.near_count, 0, sizeof(int) * sys->n_rep, sys->stream));
+    sys->primed = false;
+    return RMPCD_OK;
+}
+
+// The width that leaves headroom above a largest cell count m.
+static int grown_cap(int m) { return std::min(CP_MAX_CAP, std::max(16, ((m * 3 / 2 + 7) / 8) * 8)); }
+
+// Automatic width: the largest count of count buffer b, measured now
+// (synchronises); true when the buckets had to grow (the bins are gone).
+static rmpcd_status check_counts(rmpcd_system *sys, int b, bool *grew)
+{
+    *grew = false;
+    CK(cudaMemsetAsync(sys->d.maxcnt, 0, sizeof(unsigned int), sys->stream));
+    launch_count_max(sys->d, b, sys->stream);
+    rmpcd_status st = after_launch(sys, 1);
+    if (st != RMPCD_OK) return st;
+    CK(cudaMemcpyAsync(sys->maxcnt_host, sys->d.maxcnt, sizeof(unsigned int), cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaMemsetAsync(sys->d.maxcnt, 0, sizeof(unsigned int), sys->stream));
+    CK(cudaStreamSynchronize(sys->stream));
+    const int m = (int)*sys->maxcnt_host;
+    if (m * 5 > sys->cap * 4 && sys->cap < CP_MAX_CAP) {
+        if ((st = set_bucket_cap(sys, grown_cap(m))) != RMPCD_OK) return st;
+        // the binning just measured is discarded and redone: an overflow it
+        // latched is not an error of the run
+        CK(cudaMemsetAsync(sys->d.err + ERR_OVERFLOW, 0, sizeof(unsigned int), sys->stream));
+        *grew = true;
+    }
+    return RMPCD_OK;
 }
 
 rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_replicas, const rmpcd_params *params,
@@ -308,7 +394,10 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
     if (precision != RMPCD_FP64 && precision != RMPCD_MIXED) return fail(nullptr, RMPCD_EINVAL, "unknown precision %d", precision);
     if (n_replicas < 1 || !params) return fail(nullptr, RMPCD_EINVAL, "need n_replicas >= 1 and params");
     const int max_cap = CP_MAX_CAP;
-    if (bucket_cap < 1 || bucket_cap > max_cap) return fail(nullptr, RMPCD_EINVAL, "bucket_cap %d not in [1,%d]", bucket_cap, max_cap);
+    const bool cap_auto = bucket_cap == 0;
+    if (cap_auto) bucket_cap = auto_cap(params, n_replicas);
+    if (bucket_cap < 1 || bucket_cap > max_cap)
+        return fail(nullptr, RMPCD_EINVAL, "bucket_cap %d not in [1,%d] (0 = automatic)", bucket_cap, max_cap);
     long long n_total = 0, n_tiles = 0, n_col = 0, n_bond = 0;
     for (int r = 0; r < n_replicas; ++r) {
         if ((params[r].n_colloids > 0 && !colloids) || (params[r].n_bonds > 0 && !bonds))
@@ -328,6 +417,7 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
     sys->mixed = precision == RMPCD_MIXED;
     sys->n_rep = n_replicas;
     sys->cap = bucket_cap;
+    sys->cap_auto = cap_auto;
     sys->stream = static_cast<cudaStream_t>(stream);
     sys->params.assign(params, params + n_replicas);
     sys->n_total = (int)n_total;
@@ -348,7 +438,7 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
         rp.cell_off = tile_off * CPT;
         rp.col_off = col_off;
         rp.bond_off = bond_off;
-        rp.thr_off = r * (bucket_cap + 1);
+        rp.thr_off = r * (CP_MAX_CAP + 1);   // sized for any bucket width
         for (int t = 0; t < rp.n_tiles; ++t) tile_rep[tile_off + t] = r;
         part_off += rp.n_part;
         tile_off += rp.n_tiles;
@@ -363,10 +453,10 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
             sys->fast_ok = false;
     // bulk reaction thresholds: accept iff draw < (1 - exp(-k N_B tau)) 2^32;
     // for an integer draw that is draw < ceil((1 - exp(-k N_B tau)) 2^32)
-    std::vector<unsigned long long> thr((size_t)n_replicas * (bucket_cap + 1));
+    std::vector<unsigned long long> thr((size_t)n_replicas * (CP_MAX_CAP + 1));
     for (int r = 0; r < n_replicas; ++r)
-        for (int nb = 0; nb <= bucket_cap; ++nb)
-            thr[(size_t)r * (bucket_cap + 1) + nb] = (unsigned long long)ceil(
+        for (int nb = 0; nb <= CP_MAX_CAP; ++nb)
+            thr[(size_t)r * (CP_MAX_CAP + 1) + nb] = (unsigned long long)ceil(
                 (1.0 - exp(-params[r].bulk_rate * (double)nb * params[r].tau)) * 4294967296.0);
     // colloid constants
     std::vector<double> cM(n_col), cS(n_col), cEA(n_col), cEB(n_col), cR2(n_col), cR(n_col), cX(3 * n_col), cV(3 * n_col);
@@ -434,6 +524,7 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
     AL(&d.colXf, 3 * n_col);
     AL(&d.md_wide, 1);
     AL(&d.ctl, 1);
+    AL(&d.maxcnt, 1);
     AL(&d.colVf, 3 * n_col);
     AL(&dRb, n_col);
     AL(&dIM, n_col);
@@ -487,6 +578,10 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
     zero(d.obs_out, sizeof(double) * 8 * n_replicas);
     if (st == RMPCD_OK) zero(d.md_wide, sizeof(MdWideGlobal));
     if (st == RMPCD_OK) zero(d.ctl, sizeof(Ctl));
+    if (st == RMPCD_OK) zero(d.maxcnt, sizeof(unsigned int));
+    if (st == RMPCD_OK && cudaMallocHost(&sys->maxcnt_host, sizeof(unsigned int)) != cudaSuccess) st = RMPCD_ENOMEM;
+    if (st == RMPCD_OK && cudaEventCreateWithFlags(&sys->maxcnt_ev, cudaEventDisableTiming) != cudaSuccess)
+        st = RMPCD_ECUDA;
     if (st == RMPCD_OK) st = cuda_check(sys, cudaStreamSynchronize(s), "create sync");
     if (st != RMPCD_OK) {
         g_create_error = sys->err;
@@ -553,6 +648,14 @@ static rmpcd_status rebin_pass(rmpcd_system *sys, uint32_t grid_step, int opts, 
     launch_particles(sys->mixed, sys->d, PM_BIN, grid_step, sys->cur, b, sys->stream);
     rmpcd_status st = after_launch(sys, 1);
     if (st != RMPCD_OK) return st;
+    if (sys->cap_auto) {
+        bool grew = false;
+        if ((st = check_counts(sys, b, &grew)) != RMPCD_OK) return st;
+        if (grew) {
+            launch_particles(sys->mixed, sys->d, PM_BIN, grid_step, sys->cur, b, sys->stream);
+            if ((st = after_launch(sys, 1)) != RMPCD_OK) return st;
+        }
+    }
     CellPassArgs a{opts, grid_step, b, b ^ 1, sys->cur, sys->cur ^ 1};
     launch_cellpass(sys->mixed, sys->d, a, sys->stream);
     st = after_launch(sys, 1);
@@ -879,7 +982,14 @@ rmpcd_status rmpcd_step(rmpcd_system *sys, int32_t n_intervals)
     if (n_intervals == 0) return RMPCD_OK;
     rmpcd_status st;
     cudaEvent_t ev;
-    if (!sys->primed) {
+    if (sys->cap_auto && sys->maxcnt_pending && cudaEventQuery(sys->maxcnt_ev) == cudaSuccess) {
+        // the largest cell count of the last run: grow before it overflows
+        sys->maxcnt_pending = false;
+        const int m = (int)*sys->maxcnt_host;
+        if (m * 5 > sys->cap * 4 && sys->cap < CP_MAX_CAP && (st = set_bucket_cap(sys, grown_cap(m))) != RMPCD_OK)
+            return st;
+    }
+    for (int attempt = 0; !sys->primed && attempt < 8; ++attempt) {
         // bins for the collision of `step`: far particles at their flown
         // position, near particles through the MD kernel
         tstart(sys, &ev);
@@ -887,6 +997,11 @@ rmpcd_status rmpcd_step(rmpcd_system *sys, int32_t n_intervals)
         tstop(sys, 0, ev);
         if ((st = after_launch(sys, sys->n_total > 0 ? 1 : 0)) != RMPCD_OK) return st;
         sys->primed = true;
+        if (sys->cap_auto) {
+            // a fresh state: measure the first binning before any pass uses it
+            bool grew = false;
+            if ((st = check_counts(sys, sys->bcur, &grew)) != RMPCD_OK) return st;
+        }
     }
     int left = n_intervals;
     while (left > 0) {
@@ -908,8 +1023,22 @@ rmpcd_status rmpcd_step(rmpcd_system *sys, int32_t n_intervals)
         sys->step += 1u;
         left -= 1;
     }
+    if (sys->cap_auto && !sys->maxcnt_pending) {
+        CK(cudaMemcpyAsync(sys->maxcnt_host, sys->d.maxcnt, sizeof(unsigned int), cudaMemcpyDeviceToHost,
+                           sys->stream));
+        CK(cudaMemsetAsync(sys->d.maxcnt, 0, sizeof(unsigned int), sys->stream));
+        CK(cudaEventRecord(sys->maxcnt_ev, sys->stream));
+        sys->maxcnt_pending = true;
+    }
     sys->has_sort = true;
     sys->obs_valid = false;   // observables are computed on request
+    return RMPCD_OK;
+}
+
+rmpcd_status rmpcd_get_bucket_cap(const rmpcd_system *sys, int32_t *cap)
+{
+    if (!sys || !cap) return RMPCD_EINVAL;
+    *cap = sys->cap;
     return RMPCD_OK;
 }
 

@@ -613,6 +613,8 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
     if (tid < CPT) {
         n = d.count[a.cur][gc0 + tid];
         d.count[a.cur][gc0 + tid] = 0;
+        const int mraw = __reduce_max_sync(0xffffffffu, n);
+        if (lane == 0 && mraw > 0) atomicMax(d.maxcnt, (unsigned int)mraw);   // for the bucket-width tuner
         if (n > d.cap) {
             atomicMax(&d.err[ERR_OVERFLOW], (unsigned int)n);
             n = d.cap;

@@ -1,6 +1,8 @@
 // k_particles.cu -- particle-parallel kernels: state conversion, the granular
 // interval flight and binning (§1.1 streaming, §1.4 grid shift and sort), and
 // the final reduction of the observables (§1.4 temperature estimator).
+#include <algorithm>
+
 #include "rmpcd_kernels.cuh"
 
 namespace rmpcd {
@@ -197,6 +199,24 @@ __global__ void k_obs_reduce(Dev d)
 }
 
 __global__ void k_set_step(Dev d, uint32_t step) { d.ctl->step = step; }
+
+// Largest count of count buffer b (bucket-width tuner).
+__global__ void k_count_max(Dev d, int b)
+{
+    const long long nc = (long long)d.n_tiles * CPT;
+    unsigned int m = 0u;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x)
+        m = max(m, (unsigned int)d.count[b][c]);
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m > 0u) atomicMax(d.maxcnt, m);
+}
+
+void launch_count_max(const Dev &d, int b, cudaStream_t s)
+{
+    const long long nc = (long long)d.n_tiles * CPT;
+    const int nb = (int)std::min<long long>((nc + 255) / 256, 4096);
+    if (nb > 0) k_count_max<<<nb, 256, 0, s>>>(d, b);
+}
 
 void launch_set_step(const Dev &d, uint32_t step, cudaStream_t s) { k_set_step<<<1, 1, 0, s>>>(d, step); }
 

@@ -130,6 +130,7 @@ struct Dev {
     void *md_work;               // near-particle working state
     MdWideGlobal *md_wide;       // wide MD kernel scratch
     Ctl *ctl;                    // interval control (step, cell-pass launch counter)
+    unsigned int *maxcnt;        // largest cell count seen (bucket-width tuner)
     int cap;
     int n_rep;
     int n_tiles;

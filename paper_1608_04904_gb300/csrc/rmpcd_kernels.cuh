@@ -31,6 +31,8 @@ enum ParticleMode { PM_STREAM = 0, PM_BIN = 1, PM_PRIME = 2 };
 void launch_cellpass(bool mixed, const Dev &d, const CellPassArgs &a, cudaStream_t s);
 // Set the device step (Ctl::step) on the stream.
 void launch_set_step(const Dev &d, uint32_t step, cudaStream_t s);
+// atomicMax of the largest count of count buffer b into d.maxcnt.
+void launch_count_max(const Dev &d, int b, cudaStream_t s);
 void launch_particles(bool mixed, const Dev &d, int mode, uint32_t step, int rbuf, int bbuf, cudaStream_t s);
 // cs: CTAs per replica cluster, one of MD_CLUSTER_SIZES (results do not depend on it)
 extern const int MD_CLUSTER_SIZES[4];

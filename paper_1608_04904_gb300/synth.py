@@ -37,7 +37,7 @@ def base_config(**kw) -> dict:
         "L": (16, 16, 16), "rho": 10, "kT": 1.0, "alpha": math.radians(130.0), "tau": 0.5,
         "n_md": 50, "walls": 0, "rho_wall": 0, "g": (0.0, 0.0, 0.0), "bulk_rate": 0.0,
         "cat_prob": 1.0, "skin": 0.5, "slabs": [], "cc_lj": None, "seed": 1,
-        "precision": "fp64", "bucket_cap": 64,
+        "precision": "fp64", "bucket_cap": 0,
     }
     cfg.update(kw)
     return cfg

@@ -92,7 +92,7 @@ def test_invalid_parameters_are_rejected(api, field, value, msg):
 
 def test_invalid_bucket_cap_and_precision(api):
     p = _params(api)
-    st, err = _create(api, p, cap=0)
+    st, err = _create(api, p, cap=-1)   # 0 is the automatic width
     assert st == 1 and "bucket_cap" in err
     st, err = _create(api, p, cap=100000)
     assert st == 1 and "bucket_cap" in err

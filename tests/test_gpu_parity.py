@@ -453,3 +453,27 @@ def test_graph_replay_equals_direct_launches(precision):
         assert np.array_equal(outs[0][0][key], outs[1][0][key]), key
     assert np.array_equal(outs[0][1], outs[1][1])
     assert outs[0][2] == outs[1][2]
+
+
+def test_automatic_bucket_width():
+    """bucket_cap = 0: the width follows the density, grows on a crowded
+    start, and the run equals one with a fixed wide bucket."""
+    cfg = synth.base_config(L=(16, 16, 16), precision="mixed", seed=3)
+    x, v, fl = synth.solvent(cfg, seed=4)
+    g = api.System.single(cfg, len(x), precision="mixed", bucket_cap=0)
+    cap0 = g.bucket_cap()
+    assert 16 <= cap0 <= 64 and cap0 % 8 == 0
+    g.close()
+    # 300 of the particles start in one cell
+    x = x.copy()
+    x[:300] = 5.0 + np.floor(np.random.default_rng(5).uniform(0.0, 1.0, (300, 3)) * 2**24) * 2.0**-24
+    runs = []
+    for cap in (0, 768):
+        g = api.System.single(cfg, len(x), precision="mixed", bucket_cap=cap)
+        g.set_state(0, x, v, fl)
+        g.step(2)
+        runs.append((g.get_state(), g.bucket_cap()))
+        g.close()
+    assert runs[0][1] > cap0   # the shifted grid splits the crowd over up to 8 cells
+    for key in runs[0][0]:
+        assert np.array_equal(runs[0][0][key], runs[1][0][key]), key
