@@ -122,6 +122,18 @@ def lib():
             L.orc_potential_energy.restype = d
             L.orc_temperature.argtypes = [i64, P(i64), P(i64), P(d), P(i64)]
             L.orc_temperature.restype = d
+            L.orc_quat_matrix.argtypes = [P(d), P(d)]
+            L.orc_body_inertia.argtypes = [C.c_int, P(d), d, P(d), P(d)]
+            L.orc_body_reach.argtypes = [C.c_int, P(d), d]
+            L.orc_body_reach.restype = d
+            L.orc_body_rotate.argtypes = [P(d), d, P(d), P(d)]
+            L.orc_interval_body.argtypes = [P(Params), u32, i64, P(d), P(d), P(u8), P(u32),
+                                            C.c_int, P(d), P(d), P(d), P(i32), d, d,
+                                            P(d), P(d), P(d), P(d), C.c_int, P(u8)]
+            L.orc_interval_body.restype = C.c_int
+            L.orc_body_forces.argtypes = [P(Params), i64, P(d), P(u8), C.c_int, P(d), P(d), P(d), P(i32),
+                                          d, P(d), P(d), P(d), P(d), P(d)]
+            L.orc_body_forces.restype = d
             _lib = L
     return _lib
 
@@ -200,6 +212,83 @@ def forces(cfg, x, flags, colloids):
     return f, F
 
 
+# --------------------------------------------------------------------------
+# rigid composite colloid (bead body)
+# --------------------------------------------------------------------------
+class Body:
+    """Rigid bead body: centre of mass x, v; quaternion q (w, x, y, z, body ->
+    space); body-frame angular momentum l; beads b[nb, 3] in the principal
+    frame relative to x, each with eps_A, eps_B and a catalytic flag; bead
+    mass and the common WCA sigma."""
+
+    def __init__(self, d: dict):
+        self.x = np.array(d["x"], dtype=np.float64).reshape(3)
+        self.v = np.array(d["v"], dtype=np.float64).reshape(3)
+        self.q = np.array(d["q"], dtype=np.float64).reshape(4)
+        self.l = np.array(d["l"], dtype=np.float64).reshape(3)
+        self.b = np.ascontiguousarray(d["b"], dtype=np.float64).reshape(-1, 3).copy()
+        nb = len(self.b)
+        self.epsA = np.ascontiguousarray(np.broadcast_to(d["eps_A"], nb), dtype=np.float64)
+        self.epsB = np.ascontiguousarray(np.broadcast_to(d["eps_B"], nb), dtype=np.float64)
+        self.cat = np.ascontiguousarray(np.broadcast_to(d["catalytic"], nb), dtype=np.int32)
+        self.bead_mass = float(d["bead_mass"])
+        self.sigma = float(d["sigma"])
+
+    @property
+    def nb(self) -> int:
+        return len(self.b)
+
+    def inertia(self):
+        """(M, I[3]) from the beads."""
+        M = C.c_double(0.0)
+        I = np.zeros(3)
+        lib().orc_body_inertia(self.nb, _ptr(self.b, C.c_double), self.bead_mass, C.byref(M), _ptr(I, C.c_double))
+        return float(M.value), I
+
+    def matrix(self) -> np.ndarray:
+        return quat_matrix(self.q)
+
+    def state(self) -> dict:
+        return {"x": self.x.copy(), "v": self.v.copy(), "q": self.q.copy(), "l": self.l.copy()}
+
+
+def quat_matrix(q) -> np.ndarray:
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    R = np.zeros((3, 3))
+    lib().orc_quat_matrix(_ptr(q, C.c_double), _ptr(R, C.c_double))
+    return R
+
+
+def body_rotate(I, dt, q, l, steps: int = 1):
+    """Free rotation of a rigid body over `steps` sub-steps of dt (returns new q, l)."""
+    I = np.ascontiguousarray(I, dtype=np.float64)
+    q = np.array(q, dtype=np.float64)
+    l = np.array(l, dtype=np.float64)
+    for _ in range(steps):
+        lib().orc_body_rotate(_ptr(I, C.c_double), dt, _ptr(q, C.c_double), _ptr(l, C.c_double))
+    return q, l
+
+
+def body_reach(b, sigma) -> float:
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    return float(lib().orc_body_reach(len(b), _ptr(b, C.c_double), sigma))
+
+
+def body_forces(cfg, x, flags, body: "Body"):
+    """Solvent forces, body force, space torque and WCA energy of a configuration."""
+    p = make_params(cfg)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    flags = np.ascontiguousarray(flags, dtype=np.uint8)
+    f = np.zeros_like(x)
+    F = np.zeros(3)
+    T = np.zeros(3)
+    d = C.c_double
+    e = lib().orc_body_forces(C.byref(p), len(x), _ptr(x, d), _ptr(flags, C.c_uint8), body.nb,
+                              _ptr(body.b, d), _ptr(body.epsA, d), _ptr(body.epsB, d), _ptr(body.cat, C.c_int32),
+                              body.sigma, _ptr(body.x, d), _ptr(body.q, d), _ptr(f, d), _ptr(F, d), _ptr(T, d))
+    return f, F, T, float(e)
+
+
 class SkinError(RuntimeError):
     """A colloid moved further than the skin during one interval."""
 
@@ -212,7 +301,8 @@ class OracleSystem:
     the counter of the catalytic draw.
     """
 
-    def __init__(self, cfg: dict, x, v, flags=None, ids=None, colloids=None, bonds=None, step: int = 0):
+    def __init__(self, cfg: dict, x, v, flags=None, ids=None, colloids=None, bonds=None, step: int = 0,
+                 body=None):
         self.cfg = dict(cfg)
         self.p = make_params(cfg)
         n = len(x)
@@ -233,6 +323,9 @@ class OracleSystem:
         self.ba = np.ascontiguousarray([b[0] for b in bonds], dtype=np.int32)
         self.bb = np.ascontiguousarray([b[1] for b in bonds], dtype=np.int32)
         self.bd = np.ascontiguousarray([b[2] for b in bonds], dtype=np.float64)
+        self.body = None if body is None else Body(body)
+        if self.body is not None and len(self.M):
+            raise ValueError("a replica holds either colloids or one rigid body")
         self.step_index = int(step)
         self.ncells = int(lib().orc_n_cells(C.byref(self.p)))
         self.key = None
@@ -250,6 +343,16 @@ class OracleSystem:
         """Interval motion: MD sub-steps near colloids, free flight elsewhere."""
         L = lib()
         d, u8, u32, i32 = C.c_double, C.c_uint8, C.c_uint32, C.c_int32
+        if self.body is not None:
+            B = self.body
+            rc = L.orc_interval_body(C.byref(self.p), self.step_index, self.n, _ptr(self.x, d), _ptr(self.v, d),
+                                     _ptr(self.flags, u8), _ptr(self.id, u32), B.nb, _ptr(B.b, d),
+                                     _ptr(B.epsA, d), _ptr(B.epsB, d), _ptr(B.cat, i32), B.bead_mass, B.sigma,
+                                     _ptr(B.x, d), _ptr(B.v, d), _ptr(B.q, d), _ptr(B.l, d),
+                                     1 if all_substep else 0, _ptr(self.near, u8))
+            if rc != 0:
+                raise SkinError("body displacement exceeded the skin")
+            return
         nc = len(self.M)
         rc = L.orc_interval(C.byref(self.p), self.step_index, self.n, _ptr(self.x, d), _ptr(self.v, d),
                             _ptr(self.flags, u8), _ptr(self.id, u32), nc, _ptr(self.X, d), _ptr(self.V, d),
@@ -303,16 +406,25 @@ class OracleSystem:
 
     def potential_energy(self) -> float:
         d, i32 = C.c_double, C.c_int32
+        if self.body is not None:
+            return body_forces(self.cfg, self.x, self.flags, self.body)[3]
         return float(lib().orc_potential_energy(
             C.byref(self.p), self.n, _ptr(self.x, d), _ptr(self.flags, C.c_uint8), len(self.M),
             _ptr(self.X, d), _ptr(self.sig, d), _ptr(self.epsA, d), _ptr(self.epsB, d),
             len(self.ba), _ptr(self.ba, i32), _ptr(self.bb, i32)))
 
     def kinetic_energy(self) -> float:
-        return 0.5 * float((self.v ** 2).sum()) + 0.5 * float((self.M[:, None] * self.V ** 2).sum())
+        e = 0.5 * float((self.v ** 2).sum()) + 0.5 * float((self.M[:, None] * self.V ** 2).sum())
+        if self.body is not None:
+            M, I = self.body.inertia()
+            e += 0.5 * M * float(self.body.v @ self.body.v) + 0.5 * float((self.body.l ** 2 / I).sum())
+        return e
 
     def momentum(self) -> np.ndarray:
-        return self.v.sum(0) + (self.M[:, None] * self.V).sum(0)
+        p = self.v.sum(0) + (self.M[:, None] * self.V).sum(0)
+        if self.body is not None:
+            p = p + self.body.inertia()[0] * self.body.v
+        return p
 
     def colloids(self) -> dict:
         return {"x": self.X.copy(), "v": self.V.copy()}

@@ -18,7 +18,9 @@
  *     cut-off purely repulsive 12-6 LJ (WCA) potential, Verlet/cell lists
  *     sharing the MPCD sort, exact RATTLE for the dimer, counter-based RNG, and
  *     the cell-frame temperature estimator.
- *   - §1.5 (Applications): catalytic A->B conversion at one sphere of the dimer.
+ *   - §1.5 (Applications): catalytic A->B conversion at one sphere of the dimer,
+ *     and the composite Janus particle, whose bead network moves here as one
+ *     rigid body (reading; see the rigid-body section at the end).
  *   - §1.1 / Appendix A: bulk RMPCD reaction B->A at a given rate.
  * Where the paper is silent the readings listed in the design doc are used; each
  * function below says which one it relies on.
@@ -772,5 +774,298 @@ double orc_potential_energy(const orc_params *p, int64_t n, const double *x, con
             }
     }
     free(Xw);
+    return e;
+}
+
+/* ======================================================================== */
+/* Rigid composite colloid: the Janus particle of §1.5, a sphere of WCA      */
+/* beads (§1.4 holds its bead network together by an iterative RATTLE).      */
+/* Reading: the network moves as one rigid body, which keeps every bead      */
+/* distance exactly as the constraints do.                                   */
+/*   state: centre of mass X (unwrapped), its velocity V, unit quaternion    */
+/*   q = (w, x, y, z) taking the body frame to the space frame, and the      */
+/*   angular momentum l in the body frame.                                   */
+/*   geometry: n_b beads of mass m_b at fixed positions b_j, relative to X,  */
+/*   in the body's principal frame; M = n_b m_b and the principal moments    */
+/*   I_k = sum_j m_b (|b_j|^2 - b_jk^2).  All beads share sigma; each has    */
+/*   its own eps_A, eps_B and catalytic flag.                                */
+/*   forces: WCA between every solvent particle and every bead; the pair     */
+/*   force f on the particle puts -f on the body and the torque              */
+/*   -(R b_j) x f, both summed in 64-bit fixed point (2^-40) so the totals   */
+/*   do not depend on the order of the pairs.                                */
+/*   motion per sub-step dt: half kick of V (by F / M) and of l (by the      */
+/*   body-frame torque R^T T), drift of X, free rotation by the symmetric    */
+/*   splitting R_1(dt/2) R_2(dt/2) R_3(dt) R_2(dt/2) R_1(dt/2) of Dullweber, */
+/*   Leimkuhler & McLachlan (J. Chem. Phys. 107, 5840 (1997)), new forces,   */
+/*   second half kick.  R_k(h) turns the body about its principal axis k by  */
+/*   the angle phi with tan(phi / 2) = h l_k / (2 I_k), the Cayley form of   */
+/*   the exact angle h l_k / I_k (second order like the splitting itself,    */
+/*   and built from +, -, *, / and sqrt only, so it is reproducible bit for  */
+/*   bit): q <- q (1, tan(phi/2) e_k), normalised after the five turns, and  */
+/*   l <- rotation of l by -phi about e_k.                                   */
+/*   near radius: max_j |b_j| + r_c (the body's bounding sphere) in place of */
+/*   a sphere's r_c; the skin bounds the displacement of X.                  */
+/* ======================================================================== */
+typedef struct {
+    int nb;
+    const double *b;          /* [nb*3] principal frame, relative to X        */
+    const double *epsA, *epsB;
+    const int32_t *cat;
+    double sigma, rc2;
+    double R[3][3];           /* body -> space                                */
+    double Xw[3];             /* wrapped centre of mass                       */
+    double *rb;               /* [nb*3] R b_j                                 */
+    double *Xb;               /* [nb*3] Xw + R b_j                            */
+} body_t;
+
+/* Rotation matrix of a unit quaternion (w, x, y, z). */
+void orc_quat_matrix(const double q[4], double R[3][3])
+{
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0][0] = 1.0 - 2.0 * (y * y + z * z);
+    R[0][1] = 2.0 * (x * y - w * z);
+    R[0][2] = 2.0 * (x * z + w * y);
+    R[1][0] = 2.0 * (x * y + w * z);
+    R[1][1] = 1.0 - 2.0 * (x * x + z * z);
+    R[1][2] = 2.0 * (y * z - w * x);
+    R[2][0] = 2.0 * (x * z - w * y);
+    R[2][1] = 2.0 * (y * z + w * x);
+    R[2][2] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+/* Mass and principal moments of a bead set (the diagonal of the inertia
+ * tensor; the beads must be given in the principal frame). */
+void orc_body_inertia(int nb, const double *b, double m_b, double *M, double I[3])
+{
+    I[0] = I[1] = I[2] = 0.0;
+    for (int j = 0; j < nb; ++j) {
+        const double *bj = b + 3 * j;
+        I[0] = I[0] + m_b * (bj[1] * bj[1] + bj[2] * bj[2]);
+        I[1] = I[1] + m_b * (bj[2] * bj[2] + bj[0] * bj[0]);
+        I[2] = I[2] + m_b * (bj[0] * bj[0] + bj[1] * bj[1]);
+    }
+    *M = (double)nb * m_b;
+}
+
+/* Radius of the bounding sphere of the beads' interaction ranges. */
+double orc_body_reach(int nb, const double *b, double sigma)
+{
+    double bmax = 0.0;
+    for (int j = 0; j < nb; ++j) {
+        const double *bj = b + 3 * j;
+        double r = sqrt(bj[0] * bj[0] + bj[1] * bj[1] + bj[2] * bj[2]);
+        if (r > bmax) bmax = r;
+    }
+    return bmax + sqrt(orc_wca_rc2(sigma));
+}
+
+/* Free rotation over one sub-step dt (the splitting above). */
+void orc_body_rotate(const double I[3], double dt, double q[4], double l[3])
+{
+    static const int axis[5] = {0, 1, 2, 1, 0};
+    double h[5];
+    h[0] = 0.5 * dt; h[1] = 0.5 * dt; h[2] = dt; h[3] = 0.5 * dt; h[4] = 0.5 * dt;
+    for (int s = 0; s < 5; ++s) {
+        int k = axis[s], a = (k + 1) % 3, b = (k + 2) % 3;
+        double t = 0.5 * (h[s] * l[k] / I[k]);      /* tan(phi / 2)              */
+        double tt = t * t;
+        double inv = 1.0 / (1.0 + tt);
+        double c = (1.0 - tt) * inv;                 /* cos(phi)                  */
+        double sn = (2.0 * t) * inv;                 /* sin(phi)                  */
+        /* l turns by -phi about e_k */
+        double la = c * l[a] + sn * l[b];
+        double lb = c * l[b] - sn * l[a];
+        l[a] = la;
+        l[b] = lb;
+        /* q <- q (1, t e_k) */
+        double w = q[0], v[3] = {q[1], q[2], q[3]};
+        q[0] = w - t * v[k];
+        q[1 + k] = v[k] + t * w;
+        q[1 + a] = v[a] + t * v[b];
+        q[1 + b] = v[b] - t * v[a];
+    }
+    double nq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    for (int i = 0; i < 4; ++i) q[i] = q[i] / nq;
+}
+
+/* Bead positions for the current X and q. */
+static void body_frames(const orc_params *p, body_t *B, const double *X, const double q[4])
+{
+    orc_quat_matrix(q, B->R);
+    wrapped(p, X, B->Xw);
+    for (int j = 0; j < B->nb; ++j) {
+        const double *bj = B->b + 3 * j;
+        for (int t = 0; t < 3; ++t) {
+            double r = B->R[t][0] * bj[0] + B->R[t][1] * bj[1] + B->R[t][2] * bj[2];
+            B->rb[3 * j + t] = r;
+            B->Xb[3 * j + t] = B->Xw[t] + r;
+        }
+    }
+}
+
+/* Force on one solvent particle from all beads (ascending bead order); adds
+ * the reaction and its torque into Fq, Tq.  Returns 1 if the particle is
+ * inside a catalytic bead's range. */
+static int body_solvent_force(const orc_params *p, const body_t *B, const double *x, uint8_t fl,
+                              double f[3], int64_t Fq[3], int64_t Tq[3], double *energy)
+{
+    int inside = 0;
+    f[0] = f[1] = f[2] = 0.0;
+    for (int j = 0; j < B->nb; ++j) {
+        const double *Xb = B->Xb + 3 * j;
+        double d[3] = {x[0] - Xb[0], x[1] - Xb[1], x[2] - Xb[2]};
+        min_image(p, d);
+        double fj[3], ej = 0.0;
+        double eps = (fl & F_B) ? B->epsB[j] : B->epsA[j];
+        if (orc_wca_force(d, B->sigma, eps, B->rc2, fj, energy ? &ej : NULL)) {
+            const double *r = B->rb + 3 * j;
+            double c[3] = {r[1] * fj[2] - r[2] * fj[1], r[2] * fj[0] - r[0] * fj[2], r[0] * fj[1] - r[1] * fj[0]};
+            for (int k = 0; k < 3; ++k) {
+                f[k] = f[k] + fj[k];
+                Fq[k] -= llrint(fj[k] * FX_SCALE);
+                Tq[k] -= llrint(c[k] * FX_SCALE);
+            }
+            if (energy) *energy = *energy + ej;
+            if (B->cat[j]) inside = 1;
+        }
+    }
+    return inside;
+}
+
+/* Body force F, space torque T and body-frame torque from fixed-point sums. */
+static void body_totals(const body_t *B, const int64_t Fq[3], const int64_t Tq[3], double F[3], double tb[3])
+{
+    double T[3];
+    for (int k = 0; k < 3; ++k) { F[k] = (double)Fq[k] * FX_INV; T[k] = (double)Tq[k] * FX_INV; }
+    for (int k = 0; k < 3; ++k) tb[k] = B->R[0][k] * T[0] + B->R[1][k] * T[1] + B->R[2][k] * T[2];
+}
+
+/* Catalytic tag / conversion of one A particle (§1.5), as in orc_interval. */
+static void catalytic_step(const orc_params *p, uint8_t *fl, uint32_t id, int in, uint32_t step, int s)
+{
+    if (*fl & F_B) return;
+    if (in) { *fl |= F_TAG; return; }
+    if (!(*fl & F_TAG)) return;
+    int go = 1;
+    if (p->cat_prob < 1.0) {
+        uint32_t w[4];
+        draw(p->seed, id, step, P_CAT, (uint32_t)s, w);
+        go = (double)w[0] < p->cat_prob * 4294967296.0;
+    }
+    *fl = (uint8_t)(*fl & ~F_TAG);
+    if (go) *fl |= F_B;
+}
+
+/* One collision interval of solvent + rigid body motion: as orc_interval,
+ * with the body in place of the colloids.  X, V, q, l are updated in place.
+ * Returns 0, or 1 if X moved further than skin. */
+int orc_interval_body(const orc_params *p, uint32_t step, int64_t n, double *x, double *v,
+                      uint8_t *flags, const uint32_t *id,
+                      int nb, const double *b, const double *epsA, const double *epsB, const int32_t *cat,
+                      double m_b, double sigma, double *X, double *V, double *q, double *l,
+                      int all_substep, uint8_t *near_out)
+{
+    double M, I[3];
+    orc_body_inertia(nb, b, m_b, &M, I);
+    double reach = orc_body_reach(nb, b, sigma);
+    body_t B = {nb, b, epsA, epsB, cat, sigma, orc_wca_rc2(sigma), {{0}}, {0}, NULL, NULL};
+    B.rb = (double *)malloc(sizeof(double) * 3 * (size_t)(nb > 0 ? nb : 1));
+    B.Xb = (double *)malloc(sizeof(double) * 3 * (size_t)(nb > 0 ? nb : 1));
+    body_frames(p, &B, X, q);
+    double X0[3] = {X[0], X[1], X[2]};
+    double gnorm = sqrt(p->g[0] * p->g[0] + p->g[1] * p->g[1] + p->g[2] * p->g[2]);
+
+    /* classification against the bounding sphere */
+    uint8_t *near = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+    int64_t n_near = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (all_substep) { near[i] = 1; ++n_near; continue; }
+        double *vi = v + 3 * i;
+        double speed = sqrt(vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]);
+        double d[3] = {x[3 * i] - B.Xw[0], x[3 * i + 1] - B.Xw[1], x[3 * i + 2] - B.Xw[2]};
+        min_image(p, d);
+        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        double R = reach + speed * p->tau + 0.5 * gnorm * p->tau * p->tau + p->skin;
+        if (r2 < R * R) { near[i] = 1; ++n_near; }
+    }
+    if (near_out) memcpy(near_out, near, (size_t)n);
+    orc_flight(p, n, x, v, near);
+
+    int64_t *list = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_near > 0 ? n_near : 1));
+    for (int64_t i = 0, k = 0; i < n; ++i) if (near[i]) list[k++] = i;
+    double *f = (double *)malloc(sizeof(double) * 3 * (size_t)(n_near > 0 ? n_near : 1));
+    double dt = p->tau / (double)p->n_md;
+    double hdt = 0.5 * dt;
+    int64_t Fq[3], Tq[3];
+    double F[3], tb[3];
+
+    /* forces at the start of the interval */
+    memset(Fq, 0, sizeof Fq); memset(Tq, 0, sizeof Tq);
+    for (int64_t k = 0; k < n_near; ++k) {
+        int64_t i = list[k];
+        body_solvent_force(p, &B, x + 3 * i, flags[i], f + 3 * k, Fq, Tq, NULL);
+        for (int t = 0; t < 3; ++t) f[3 * k + t] = f[3 * k + t] + p->g[t];
+    }
+    body_totals(&B, Fq, Tq, F, tb);
+
+    for (int s = 0; s < p->n_md; ++s) {
+        /* body: half kick, drift, free rotation */
+        for (int t = 0; t < 3; ++t) {
+            V[t] = fma(hdt, F[t] / M, V[t]);
+            l[t] = fma(hdt, tb[t], l[t]);
+            X[t] = fma(dt, V[t], X[t]);
+        }
+        orc_body_rotate(I, dt, q, l);
+        body_frames(p, &B, X, q);
+        /* solvent: half kick, drift */
+        for (int64_t k = 0; k < n_near; ++k) {
+            int64_t i = list[k];
+            for (int t = 0; t < 3; ++t) {
+                v[3 * i + t] = fma(hdt, f[3 * k + t], v[3 * i + t]);
+                x[3 * i + t] = fma(dt, v[3 * i + t], x[3 * i + t]);
+            }
+        }
+        /* new forces, catalytic conversion, second half kicks */
+        memset(Fq, 0, sizeof Fq); memset(Tq, 0, sizeof Tq);
+        for (int64_t k = 0; k < n_near; ++k) {
+            int64_t i = list[k];
+            int in = body_solvent_force(p, &B, x + 3 * i, flags[i], f + 3 * k, Fq, Tq, NULL);
+            for (int t = 0; t < 3; ++t) f[3 * k + t] = f[3 * k + t] + p->g[t];
+            catalytic_step(p, flags + i, id[i], in, step, s);
+        }
+        body_totals(&B, Fq, Tq, F, tb);
+        for (int t = 0; t < 3; ++t) {
+            V[t] = fma(hdt, F[t] / M, V[t]);
+            l[t] = fma(hdt, tb[t], l[t]);
+        }
+        for (int64_t k = 0; k < n_near; ++k) {
+            int64_t i = list[k];
+            for (int t = 0; t < 3; ++t) v[3 * i + t] = fma(hdt, f[3 * k + t], v[3 * i + t]);
+        }
+    }
+    for (int64_t k = 0; k < n_near; ++k) wrap_periodic(p, x + 3 * list[k]);
+
+    double dd = 0.0;
+    for (int t = 0; t < 3; ++t) { double e = X[t] - X0[t]; dd = dd + e * e; }
+    int status = (dd <= p->skin * p->skin) ? 0 : 1;   /* NaN counts as a violation */
+    free(B.rb); free(B.Xb); free(near); free(list); free(f);
+    return status;
+}
+
+/* Solvent forces f[n*3], body force F, space torque T and the WCA energy of
+ * a configuration (for the tests). */
+double orc_body_forces(const orc_params *p, int64_t n, const double *x, const uint8_t *flags,
+                       int nb, const double *b, const double *epsA, const double *epsB, const int32_t *cat,
+                       double sigma, const double *X, const double *q, double *f, double *F, double *T)
+{
+    body_t B = {nb, b, epsA, epsB, cat, sigma, orc_wca_rc2(sigma), {{0}}, {0}, NULL, NULL};
+    B.rb = (double *)malloc(sizeof(double) * 3 * (size_t)(nb > 0 ? nb : 1));
+    B.Xb = (double *)malloc(sizeof(double) * 3 * (size_t)(nb > 0 ? nb : 1));
+    body_frames(p, &B, X, q);
+    int64_t Fq[3] = {0, 0, 0}, Tq[3] = {0, 0, 0};
+    double e = 0.0;
+    for (int64_t i = 0; i < n; ++i) body_solvent_force(p, &B, x + 3 * i, flags[i], f + 3 * i, Fq, Tq, &e);
+    for (int k = 0; k < 3; ++k) { F[k] = (double)Fq[k] * FX_INV; T[k] = (double)Tq[k] * FX_INV; }
+    free(B.rb); free(B.Xb);
     return e;
 }

@@ -21,7 +21,8 @@ Workloads (stand-ins for the paper's ``experiments/``, §1.5 and Appendix A):
 * ``thermal256`` -- 256 x 64 x 64, 64 WCA spheres (sigma 2.5, M 150), MPC-AT
   slabs at kT 1.2 / 0.8, colloid-colloid LJ (``single_sphere_thermo_trap``).
 * ``batch``      -- independent replicas with cubic sides drawn from
-  {16, 20, 24, 32, 40, 48}.
+  {16, 20, 24, 32, 40, 48}, each holding one Janus particle built from 100-300
+  beads on a sphere of radius 4 (``single_janus_pbc``).
 """
 from __future__ import annotations
 
@@ -188,3 +189,92 @@ def batch_sphere(side, seed, precision="mixed"):
     c = side / 2.0
     col = [dict(x=(c, c, c), v=(0.0, 0.0, 0.0), mass=m, sigma=4.0, eps_A=1.0, eps_B=1.0, catalytic=1)]
     return cfg, col, []
+
+
+def fibonacci_sphere(nb: int, radius: float) -> np.ndarray:
+    """nb nearly uniform points on a sphere (Fibonacci lattice): heights
+    z_j = 1 - (2 j + 1) / nb, azimuths j times the golden angle."""
+    j = np.arange(nb, dtype=np.float64)
+    z = 1.0 - (2.0 * j + 1.0) / nb
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    phi = j * (math.pi * (3.0 - math.sqrt(5.0)))
+    return radius * np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
+
+
+def matrix_quaternion(R) -> np.ndarray:
+    """Unit quaternion (w, x, y, z) of a proper rotation matrix (Shepperd's
+    branch on the largest diagonal term)."""
+    R = np.asarray(R, dtype=np.float64)
+    t = np.trace(R)
+    if t > 0:
+        s = 2.0 * math.sqrt(1.0 + t)
+        q = [0.25 * s, (R[2, 1] - R[1, 2]) / s, (R[0, 2] - R[2, 0]) / s, (R[1, 0] - R[0, 1]) / s]
+    else:
+        i = int(np.argmax(np.diag(R)))
+        j, k = (i + 1) % 3, (i + 2) % 3
+        s = 2.0 * math.sqrt(1.0 + R[i, i] - R[j, j] - R[k, k])
+        q = [0.0] * 4
+        q[0] = (R[k, j] - R[j, k]) / s
+        q[1 + i] = 0.25 * s
+        q[1 + j] = (R[j, i] + R[i, j]) / s
+        q[1 + k] = (R[k, i] + R[i, k]) / s
+    q = np.asarray(q)
+    return q / np.linalg.norm(q)
+
+
+def janus_body(nb: int, center, seed: int, radius: float = 4.0, rho: float = 10.0, sigma: float = 1.0,
+               eps_A=1.0, eps_B=1.0, kT: float = 1.0, thermal: bool = True) -> dict:
+    """A Janus particle of nb beads on a Fibonacci sphere of the given radius,
+    catalytic where the construction frame has z > 0, with equal bead masses
+    totalling rho (4/3) pi radius^3 (neutral buoyancy).  The beads are centred
+    and expressed in the principal frame of their inertia tensor; the
+    orientation q maps that frame back onto the construction frame.  With
+    ``thermal`` the centre-of-mass velocity and body-frame angular momentum
+    are drawn from Maxwell-Boltzmann at kT, else both are zero."""
+    rng = np.random.Generator(np.random.PCG64(seed + 7919))
+    b0 = fibonacci_sphere(nb, radius)
+    cat = (b0[:, 2] > 0.0).astype(np.int32)
+    b0 = b0 - b0.mean(axis=0)
+    m_b = rho * 4.0 / 3.0 * math.pi * radius ** 3 / nb
+    It = m_b * ((b0 * b0).sum() * np.eye(3) - b0.T @ b0)
+    w, E = np.linalg.eigh(It)
+    if np.linalg.det(E) < 0:
+        E[:, 2] = -E[:, 2]
+    b = b0 @ E                        # b0 = E b  (rows: b = E^T b0)
+    q = matrix_quaternion(E)
+    M = m_b * nb
+    Ib = m_b * np.array([(b[:, 1] ** 2 + b[:, 2] ** 2).sum(), (b[:, 2] ** 2 + b[:, 0] ** 2).sum(),
+                         (b[:, 0] ** 2 + b[:, 1] ** 2).sum()])
+    if thermal:
+        v = rng.standard_normal(3) * math.sqrt(kT / M)
+        l = rng.standard_normal(3) * np.sqrt(kT * Ib)
+    else:
+        v = np.zeros(3)
+        l = np.zeros(3)
+    return {"x": np.asarray(center, dtype=np.float64), "v": v, "q": q, "l": l, "b": b,
+            "eps_A": np.broadcast_to(np.asarray(eps_A, np.float64), nb).copy(),
+            "eps_B": np.broadcast_to(np.asarray(eps_B, np.float64), nb).copy(),
+            "catalytic": cat, "bead_mass": m_b, "sigma": sigma}
+
+
+def body_exclusion(body) -> list:
+    """A pseudo-colloid whose cut-off covers the body's bounding sphere, for
+    ``solvent(..., col=...)``: no solvent starts inside the bead shell."""
+    b = np.asarray(body["b"])
+    reach = float(np.sqrt((b * b).sum(1)).max()) + WCA_RC_FACTOR * body["sigma"]
+    return [dict(x=tuple(body["x"]), sigma=reach / WCA_RC_FACTOR)]
+
+
+def batch_janus(side, seed, precision="mixed", nb=None):
+    """One replica of the batched ensemble: a cube of the given side at
+    density 10 holding one Janus particle of nb beads (drawn from
+    U{100..300} with the replica's seed when not given) on a sphere of radius 4
+    at the centre, sigma_b = 1, eps = 1, catalytic hemisphere (A -> B with
+    probability 1), alpha 130 deg, tau 0.5, 25 MD sub-steps of dt 0.02."""
+    L = (side, side, side)
+    cfg = base_config(L=L, alpha=math.radians(130.0), tau=0.5, n_md=25, kT=1.0, seed=seed, precision=precision)
+    if nb is None:
+        nb = int(np.random.Generator(np.random.PCG64(seed + 104729)).integers(100, 301))
+    c = side / 2.0
+    body = janus_body(nb, (c, c, c), seed)
+    return cfg, body
