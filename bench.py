@@ -41,11 +41,11 @@ ALG_BYTES = {"mixed": 64, "fp64": 112}
 L2_FLUSH_BYTES = 256 << 20
 KERNEL_NAMES = {"cellpass": "k_cellpass", "md": "k_md", "prime": "k_particles", "obs": "k_obs_reduce"}
 KERNEL_SOURCES = ["rmpcd_common.cuh", "rmpcd_kernels.cuh", "k_cellpass.cu", "k_md.cu", "k_md_fast.cu",
-                  "k_particles.cu", "capi.cu"]
+                  "k_md_body.cu", "k_particles.cu", "capi.cu"]
 
 
 def workload(name, precision, seed_offset=0):
-    """The workload as a list of replicas (cfg, colloids, bonds) and a description."""
+    """The workload as a list of replicas (cfg, colloids, bonds, body) and a description."""
     from paper_1608_04904_gb300 import synth
     if name == "dimer32":
         reps = [synth.dimer32(precision=precision, seed=2 + seed_offset)]
@@ -69,14 +69,33 @@ def workload(name, precision, seed_offset=0):
                 "50 MD sub-steps dt 0.01")
     elif name == "batch256":
         sides = synth.batch_sides(256, seed=4)
-        reps = [synth.batch_sphere(L, seed=4 + r + 1000 * seed_offset, precision=precision)
-                for r, L in enumerate(sides)]
+        reps = []
+        for r, L in enumerate(sides):
+            cfg, body = synth.batch_janus(L, seed=4 + r + 1000 * seed_offset, precision=precision)
+            reps.append((cfg, [], [], body))
         desc = ("256 independent replicas in one launch per kernel, cube sides drawn from {16,20,24,32,40,48} "
-                "(seed 4), rho 10, one WCA sphere of radius 4 each (stand-in for the bead-built Janus particle), "
-                "alpha 130 deg, tau 0.5, 25 MD sub-steps dt 0.02")
+                "(seed 4), rho 10, one rigid Janus particle each (100-300 beads on a sphere of radius 4, "
+                "sigma_b 1, catalytic hemisphere A->B), alpha 130 deg, tau 0.5, 25 MD sub-steps dt 0.02")
+        return reps, desc
     else:
         raise SystemExit(f"unknown workload {name}")
-    return reps, desc
+    return [(cfg, col, bonds, None) for cfg, col, bonds in reps], desc
+
+
+def initial_state(rep):
+    """Seeded solvent of one replica, outside its colloids or body."""
+    from paper_1608_04904_gb300 import synth
+    cfg, col, bonds, body = rep
+    excl = col if body is None else synth.body_exclusion(body)
+    return synth.solvent(cfg, excl, seed=cfg["seed"] + 100)
+
+
+def oracle_system(oracle, rep, state):
+    from paper_1608_04904_gb300 import synth
+    cfg, col, bonds, body = rep
+    x, v, fl = state
+    return oracle.OracleSystem(cfg, x, v, fl, colloids=synth.colloid_arrays(col) if col else None, bonds=bonds,
+                               body=body)
 
 
 def kernel_hash():
@@ -167,9 +186,8 @@ def cpu_baseline(name, precision, budget_s=15.0):
     from paper_1608_04904_gb300 import synth
     oracle.build()
     reps, _ = workload(name, precision)
-    cfg, col, bonds = reps[0]
-    x, v, fl = synth.solvent(cfg, col, seed=cfg["seed"] + 100)
-    o = oracle.OracleSystem(cfg, x, v, fl, colloids=synth.colloid_arrays(col) if col else None, bonds=bonds)
+    x, v, fl = initial_state(reps[0])
+    o = oracle_system(oracle, reps[0], (x, v, fl))
     o.step(1)
     t0 = time.perf_counter()
     k = 0
@@ -190,11 +208,10 @@ def run_reference(args, ws, rank):
         return
     from paper_1608_04904_gb300 import synth
     reps, desc = workload(args.workload, args.precision)
-    cfg, col, bonds = reps[0]
     from oracle import oracle
     oracle.build()
-    x, v, fl = synth.solvent(cfg, col, seed=cfg["seed"] + 100)
-    o = oracle.OracleSystem(cfg, x, v, fl, colloids=synth.colloid_arrays(col) if col else None, bonds=bonds)
+    x, v, fl = initial_state(reps[0])
+    o = oracle_system(oracle, reps[0], (x, v, fl))
     for _ in range(args.warmup):
         o.step(1)
     budget = 150.0
@@ -223,9 +240,9 @@ def run_reference(args, ws, rank):
 
 
 def make_system(api, reps, states, precision, stream):
-    s = api.System([dict(cfg=cfg, n=len(st[0]), colloids=col, bonds=bonds) for (cfg, col, bonds), st in
-                    zip(reps, states)], precision=precision, bucket_cap=reps[0][0].get("bucket_cap", 0),
-                   stream=stream)
+    s = api.System([dict(cfg=cfg, n=len(st[0]), colloids=col, bonds=bonds, body=body)
+                    for (cfg, col, bonds, body), st in zip(reps, states)], precision=precision,
+                   bucket_cap=reps[0][0].get("bucket_cap", 0), stream=stream)
     for r, (x, v, fl) in enumerate(states):
         s.set_state(r, x, v, fl)
     return s
@@ -245,7 +262,7 @@ def _timed_run(api, torch, reps, states, precision, steps, warmup, flush, dev_in
                barrier, md_cluster, md_kernel, stream):
     s = make_system(api, reps, states, precision, stream)
     s.set_tuning(md_cluster, md_kernel)
-    has_col = any(col for _, col, _ in reps)
+    has_col = any(col for _, col, _, _ in reps)
     # warm-up, including the tuning intervals of the MD cluster size
     for _ in range(max(warmup, 16 if (has_col and md_cluster == 0) else 0)):   # 3 trials x <= 5 sizes
         s.step(1)
@@ -354,7 +371,7 @@ def main():
     api.load()
 
     reps, desc = workload(args.workload, args.precision, seed_offset=rank)
-    states = [synth.solvent(cfg, col, seed=cfg["seed"] + 100) for cfg, col, _ in reps]
+    states = [initial_state(r) for r in reps]
     cfg = reps[0][0]
     n = sum(len(st[0]) for st in states)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -375,7 +392,9 @@ def main():
     dominant = max(phases, key=lambda k: phases[k]["ms"])
     peak, peak_src = measured_peaks()
     kernel_names = dict(KERNEL_NAMES)
-    if obs["md_kernel"] == 2:
+    if any(r[3] is not None for r in reps):
+        kernel_names["md"] = "k_md_body"
+    elif obs["md_kernel"] == 2:
         kernel_names["md"] = "k_md_fast"
     kernels = {}
     for k, t in phases.items():
@@ -385,7 +404,7 @@ def main():
             alg = n * ALG_BYTES[args.precision]
             entry.update({"alg_bytes_per_launch": alg, "achieved_gbs": alg / (avg_ms / 1e3) / 1e9})
         if k == "md":
-            entry["us_per_substep"] = 1e3 * avg_ms / max(c["n_md"] for c, _, _ in reps)
+            entry["us_per_substep"] = 1e3 * avg_ms / max(r[0]["n_md"] for r in reps)
         kernels[kernel_names[k]] = entry
     cp = phases["cellpass"]
     cp_avg_s = cp["ms"] / cp["launches"] / 1e3

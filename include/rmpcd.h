@@ -8,7 +8,8 @@
  * thermostat, random grid shift, body force, bounce-back walls with virtual
  * particles, WCA colloid-solvent potential, Verlet/cell lists sharing the MPCD
  * sort, exact RATTLE for the dimer, counter-based RNG, temperature estimator),
- * §1.5 (catalytic A -> B at the dimer's C sphere) and Appendix A (parameters).
+ * §1.5 (catalytic A -> B at the dimer's C sphere, the bead-built Janus
+ * particle) and Appendix A (parameters).
  *
  * Conventions for every entry point:
  *   - Every call returns an rmpcd_status; no call prints or aborts.
@@ -90,6 +91,33 @@ typedef struct {
     double d;
 } rmpcd_bond;
 
+/* A rigid composite colloid: the Janus particle of §1.5, a network of WCA
+ * beads that moves as one rigid body (§1.4 holds the network together by
+ * constraints; a rigid body keeps every bead distance exactly).  State: the
+ * centre of mass x (unwrapped) and its velocity v, the unit quaternion
+ * q = (w, x, y, z) taking the body frame to the space frame, and the angular
+ * momentum l in the body frame.  Every bead has mass bead_mass and WCA sigma
+ * `sigma` (cut-off 2^(1/6) sigma). */
+typedef struct {
+    double x[3], v[3];
+    double q[4];
+    double l[3];
+    double bead_mass, sigma;
+    int32_t n_beads;
+    int32_t pad;
+} rmpcd_body;
+
+/* One bead: position relative to the centre of mass in the body's principal
+ * frame, WCA epsilon towards A and B solvent, catalytic flag (§1.5). */
+typedef struct {
+    double b[3];
+    double eps_A, eps_B;
+    int32_t catalytic;
+    int32_t pad;
+} rmpcd_bead;
+
+#define RMPCD_MAX_BEADS 1024
+
 /* Observables of one replica after the last collision (§1.4 temperature
  * estimator; totals accumulated in FP64). */
 typedef struct {
@@ -141,6 +169,27 @@ rmpcd_status rmpcd_get_state(rmpcd_system *sys, int32_t replica, double *x, doub
 /* Colloids of one replica (host arrays of params.n_colloids entries). */
 rmpcd_status rmpcd_set_colloids(rmpcd_system *sys, int32_t replica, const rmpcd_colloid *c, int32_t n);
 rmpcd_status rmpcd_get_colloids(rmpcd_system *sys, int32_t replica, rmpcd_colloid *c, int32_t n);
+
+/* Give one replica a rigid bead body, or replace its body (geometry and
+ * state).  The replica must have been created with no colloids, no bonds and
+ * no walls.  beads[body->n_beads], 1 <= n_beads <= RMPCD_MAX_BEADS, centred
+ * (|sum b| <= 1e-9 n_beads max|b|) and in the principal frame (off-diagonal
+ * inertia <= 1e-9 of its trace); bead_mass, sigma > 0; |q| = 1 within 1e-9;
+ * the box must hold twice the body's reach (max|b| + 2^(1/6) sigma) plus
+ * twice the skin.  M = n_beads bead_mass; principal moments
+ * I_k = sum_j bead_mass (|b_j|^2 - b_jk^2).  The body moves by velocity
+ * Verlet for x and the principal-axis splitting of the free rotation
+ * (turns about axes 1, 2, 3, 2, 1 over dt/2, dt/2, dt, dt/2, dt/2, each by
+ * the angle phi with tan(phi/2) = h l_k / (2 I_k)); solvent within
+ * reach + |v| tau + |g| tau^2/2 + skin of x takes the MD sub-steps.  Discards
+ * a primed fused pipeline; synchronises.  Errors: EINVAL, ENOMEM, ECUDA. */
+rmpcd_status rmpcd_set_body(rmpcd_system *sys, int32_t replica, const rmpcd_body *body,
+                            const rmpcd_bead *beads);
+
+/* The body of one replica (state as of the last completed interval; beads
+ * are not returned).  Synchronises and returns latched device errors.
+ * Errors: EINVAL (no body), ECUDA, EOVERFLOW, ESKIN, ETIMEOUT. */
+rmpcd_status rmpcd_get_body(rmpcd_system *sys, int32_t replica, rmpcd_body *body);
 
 /* Collision counter that keys every random draw of the next interval. */
 rmpcd_status rmpcd_set_step(rmpcd_system *sys, uint32_t step);

@@ -47,6 +47,19 @@ class Bond(C.Structure):
     _fields_ = [("a", C.c_int32), ("b", C.c_int32), ("d", C.c_double)]
 
 
+class Body(C.Structure):
+    _fields_ = [("x", C.c_double * 3), ("v", C.c_double * 3), ("q", C.c_double * 4), ("l", C.c_double * 3),
+                ("bead_mass", C.c_double), ("sigma", C.c_double), ("n_beads", C.c_int32), ("pad", C.c_int32)]
+
+
+class Bead(C.Structure):
+    _fields_ = [("b", C.c_double * 3), ("eps_A", C.c_double), ("eps_B", C.c_double), ("catalytic", C.c_int32),
+                ("pad", C.c_int32)]
+
+
+MAX_BEADS = 1024
+
+
 class Obs(C.Structure):
     _fields_ = [("temperature", C.c_double), ("momentum", C.c_double * 3), ("kinetic", C.c_double),
                 ("n_cells_used", C.c_int64), ("n_B", C.c_int64), ("n_solvent", C.c_int64),
@@ -64,7 +77,7 @@ EXPORTS = [
     "rmpcd_get_colloids", "rmpcd_set_step", "rmpcd_get_step", "rmpcd_stream", "rmpcd_shift_and_sort",
     "rmpcd_collide", "rmpcd_react", "rmpcd_step", "rmpcd_observables", "rmpcd_sync", "rmpcd_launch_count",
     "rmpcd_last_error", "rmpcd_enable_timers", "rmpcd_read_timers", "rmpcd_set_tuning", "rmpcd_get_tuning",
-    "rmpcd_observables_noalloc", "rmpcd_set_graphs", "rmpcd_get_bucket_cap",
+    "rmpcd_observables_noalloc", "rmpcd_set_graphs", "rmpcd_get_bucket_cap", "rmpcd_set_body", "rmpcd_get_body",
 ]
 
 _LIB = None
@@ -92,6 +105,8 @@ def load():
     L.rmpcd_get_state.argtypes = [vp, i32, vp, vp, vp, vp, vp, i64, i32]
     L.rmpcd_set_colloids.argtypes = [vp, i32, P(Colloid), i32]
     L.rmpcd_get_colloids.argtypes = [vp, i32, P(Colloid), i32]
+    L.rmpcd_set_body.argtypes = [vp, i32, P(Body), P(Bead)]
+    L.rmpcd_get_body.argtypes = [vp, i32, P(Body)]
     L.rmpcd_set_step.argtypes = [vp, u32]
     L.rmpcd_get_step.argtypes = [vp, P(u32)]
     for name in ("rmpcd_stream", "rmpcd_shift_and_sort", "rmpcd_collide", "rmpcd_react", "rmpcd_sync"):
@@ -170,8 +185,9 @@ class System:
     """A set of independent replicas on the current CUDA device.
 
     ``replicas``: list of dicts with keys ``cfg`` (parameter dict), ``n``
-    (solvent count), ``colloids`` (list of dicts) and ``bonds`` (list of
-    ``(a, b, d)``).
+    (solvent count), ``colloids`` (list of dicts), ``bonds`` (list of
+    ``(a, b, d)``) and optionally ``body`` (a rigid bead body, see
+    ``set_body``; such a replica has no colloids).
     """
 
     def __init__(self, replicas, precision: str = "mixed", bucket_cap: int = 64, stream=None):
@@ -208,6 +224,9 @@ class System:
         if st != 0:
             raise RmpcdError(st, self._lib.rmpcd_last_error(None).decode())
         self._h = handle
+        for r, rep in enumerate(self.replicas):
+            if rep.get("body") is not None:
+                self.set_body(r, rep["body"])
 
     @classmethod
     def single(cls, cfg, n, colloids=(), bonds=(), precision=None, bucket_cap=None, stream=None):
@@ -283,6 +302,39 @@ class System:
         self._check(self._lib.rmpcd_get_colloids(self._h, replica, arr, k))
         return {"x": np.array([list(arr[j].x) for j in range(k)]).reshape(k, 3),
                 "v": np.array([list(arr[j].v) for j in range(k)]).reshape(k, 3)}
+
+    def set_body(self, replica, body):
+        """Rigid bead body of one replica: dict with x, v (centre of mass), q
+        (w, x, y, z), l (body-frame angular momentum), b[nb, 3] (principal
+        frame), eps_A, eps_B (per bead or scalar), catalytic (per bead or
+        scalar), bead_mass, sigma."""
+        b = np.ascontiguousarray(body["b"], dtype=np.float64).reshape(-1, 3)
+        nb = len(b)
+        eA = np.broadcast_to(np.asarray(body["eps_A"], np.float64), nb)
+        eB = np.broadcast_to(np.asarray(body["eps_B"], np.float64), nb)
+        cat = np.broadcast_to(np.asarray(body["catalytic"], np.int32), nb)
+        B = Body()
+        B.x[:] = [float(a) for a in body["x"]]
+        B.v[:] = [float(a) for a in body["v"]]
+        B.q[:] = [float(a) for a in body["q"]]
+        B.l[:] = [float(a) for a in body["l"]]
+        B.bead_mass = float(body["bead_mass"])
+        B.sigma = float(body["sigma"])
+        B.n_beads = nb
+        beads = (Bead * max(1, nb))()
+        for j in range(nb):
+            beads[j].b[:] = [float(a) for a in b[j]]
+            beads[j].eps_A = float(eA[j])
+            beads[j].eps_B = float(eB[j])
+            beads[j].catalytic = int(cat[j])
+        self._check(self._lib.rmpcd_set_body(self._h, replica, C.byref(B), beads))
+
+    def get_body(self, replica=0) -> dict:
+        """State of a replica's body: x, v, q, l (numpy arrays)."""
+        B = Body()
+        self._check(self._lib.rmpcd_get_body(self._h, replica, C.byref(B)))
+        return {"x": np.array(list(B.x)), "v": np.array(list(B.v)), "q": np.array(list(B.q)),
+                "l": np.array(list(B.l))}
 
     def set_step(self, step):
         self._check(self._lib.rmpcd_set_step(self._h, int(step)))

@@ -76,6 +76,23 @@ struct rmpcd_system {
     bool maxcnt_pending = false;
     cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     int graph_nodes = 0;              // kernel launches per replay
+    // rigid bead bodies: per replica host copy (n_beads = 0: none), the
+    // device arrays (rebuilt when a body is set) and the colloid slot that
+    // stands for each body in the near-list test
+    struct BodyHost {
+        rmpcd_body b{};
+        std::vector<rmpcd_bead> beads;
+        BodyDev dev{};
+        std::vector<int> gstart;
+        std::vector<unsigned short> glist;
+    };
+    std::vector<BodyHost> bodies;
+    bool any_body = false;
+    int nb_max = 0;
+    std::vector<void *> body_allocs;  // bead and grid arrays
+    double *col_rc = nullptr;         // writable colloid constants (body slots)
+    float *col_rb = nullptr;
+    size_t work_bytes = 0;            // md_work size
 };
 
 static void drop_graphs(rmpcd_system *sys);
@@ -216,6 +233,7 @@ static void fill_rep(ReplicaDev &rp, const rmpcd_params &p)
     rp.n_tiles = (rp.n_cells + CPT - 1) / CPT;
     rp.n_col = p.n_colloids;
     rp.n_bond = p.n_bonds;
+    rp.body = -1;
     rp.bulk_on = p.bulk_rate > 0.0 ? 1 : 0;
     rp.has_g = (p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0) ? 1 : 0;
     rp.kT = p.kT;
@@ -302,6 +320,7 @@ void rmpcd_destroy(rmpcd_system *sys)
     if (sys->maxcnt_host) cudaFreeHost(sys->maxcnt_host);
     if (sys->maxcnt_ev) cudaEventDestroy(sys->maxcnt_ev);
     for (void *p : sys->allocs) cudaFree(p);
+    for (void *p : sys->body_allocs) cudaFree(p);
     for (auto &q : sys->pending) { sys->ev_pool.push_back(q.a); sys->ev_pool.push_back(q.b); }
     for (auto &q : sys->md_trials) { sys->ev_pool.push_back(q.a); sys->ev_pool.push_back(q.b); }
     for (cudaEvent_t e : sys->ev_pool) cudaEventDestroy(e);
@@ -514,22 +533,26 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
     AL(&d.obs_part, (size_t)n_tiles * 8);
     AL(&d.obs_out, (size_t)n_replicas * 8);
     AL(&dthr, thr.size());
-    AL(&d.colX, 3 * n_col);
-    AL(&d.colV, 3 * n_col);
-    AL(&dM, n_col); AL(&dS, n_col); AL(&dEA, n_col); AL(&dEB, n_col); AL(&dR2, n_col); AL(&dR, n_col);
-    AL(&dfS, n_col); AL(&dfEA, n_col); AL(&dfEB, n_col); AL(&dfR2, n_col); AL(&dfR, n_col);
-    AL(&dCat, n_col);
-    AL(&d.colXi, 3 * n_col);
-    AL(&d.colCi, 3 * n_col);
-    AL(&d.colXf, 3 * n_col);
+    // colloid arrays hold one spare slot per replica (n_col + r) for a body
+    const long long n_slot = n_col + n_replicas;
+    AL(&d.colX, 3 * n_slot);
+    AL(&d.colV, 3 * n_slot);
+    AL(&dM, n_slot); AL(&dS, n_slot); AL(&dEA, n_slot); AL(&dEB, n_slot); AL(&dR2, n_slot); AL(&dR, n_slot);
+    AL(&dfS, n_slot); AL(&dfEA, n_slot); AL(&dfEB, n_slot); AL(&dfR2, n_slot); AL(&dfR, n_slot);
+    AL(&dCat, n_slot);
+    AL(&d.colXi, 3 * n_slot);
+    AL(&d.colCi, 3 * n_slot);
+    AL(&d.colXf, 3 * n_slot);
     AL(&d.md_wide, 1);
     AL(&d.ctl, 1);
     AL(&d.maxcnt, 1);
-    AL(&d.colVf, 3 * n_col);
-    AL(&dRb, n_col);
-    AL(&dIM, n_col);
+    AL(&d.colVf, 3 * n_slot);
+    AL(&dRb, n_slot);
+    AL(&dIM, n_slot);
     AL(&dB, n_bond);
-    AL(&work, (sys->mixed ? 64 : 80) * (size_t)(sys->any_colloids ? n_total : 1));
+    AL(&d.body, n_replicas);
+    sys->work_bytes = (sys->mixed ? 64 : 80) * (size_t)(sys->any_colloids ? n_total : 1);
+    AL(&work, sys->work_bytes);
     AL(&sys->stage_x, 3 * (size_t)sys->max_part);
     AL(&sys->stage_v, 3 * (size_t)sys->max_part);
     AL(&sys->stage_f, (size_t)sys->max_part);
@@ -597,6 +620,9 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
     d.colSig_f = dfS; d.colEpsA_f = dfEA; d.colEpsB_f = dfEB; d.colRc2_f = dfR2; d.colRc_f = dfR;
     d.colCat = dCat;
     d.colRb_f = dRb;
+    sys->col_rc = dR;
+    sys->col_rb = dRb;
+    sys->bodies.resize(n_replicas);
     d.colInvM_f = dIM;
     d.bonds = dB;
     d.md_work = work;
@@ -754,7 +780,8 @@ rmpcd_status rmpcd_set_colloids(rmpcd_system *sys, int32_t replica, const rmpcd_
     if (!sys) return RMPCD_EINVAL;
     if (replica < 0 || replica >= sys->n_rep) return fail(sys, RMPCD_EINVAL, "replica %d out of range", replica);
     const ReplicaDev &rp = sys->rep[replica];
-    if (n != rp.n_col || (n > 0 && !c)) return fail(sys, RMPCD_EINVAL, "replica %d has %d colloids", replica, rp.n_col);
+    const int ncol = sys->params[replica].n_colloids;
+    if (n != ncol || (n > 0 && !c)) return fail(sys, RMPCD_EINVAL, "replica %d has %d colloids", replica, ncol);
     rmpcd_status st = unprime(sys);
     if (st != RMPCD_OK) return st;
     std::vector<double> X(3 * n), V(3 * n);
@@ -783,7 +810,8 @@ rmpcd_status rmpcd_get_colloids(rmpcd_system *sys, int32_t replica, rmpcd_colloi
     if (!sys) return RMPCD_EINVAL;
     if (replica < 0 || replica >= sys->n_rep) return fail(sys, RMPCD_EINVAL, "replica %d out of range", replica);
     const ReplicaDev &rp = sys->rep[replica];
-    if (n != rp.n_col || (n > 0 && !c)) return fail(sys, RMPCD_EINVAL, "replica %d has %d colloids", replica, rp.n_col);
+    const int ncol = sys->params[replica].n_colloids;
+    if (n != ncol || (n > 0 && !c)) return fail(sys, RMPCD_EINVAL, "replica %d has %d colloids", replica, ncol);
     std::vector<double> X(3 * n + 1), V(3 * n + 1);
     std::vector<int> Xi(3 * n + 1);
     std::vector<float> Xf(3 * n + 1), Vf(3 * n + 1);
@@ -846,6 +874,10 @@ rmpcd_status rmpcd_stream(rmpcd_system *sys)
         else if (sys->md_kernel == 2) launch_md_fast(sys->mixed, sys->d, sys->step, sys->cur, 0, 0, cs, sys->stream);
         else launch_md(sys->mixed, sys->d, sys->step, sys->cur, 0, 0, cs, sys->stream);
         if ((st = after_launch(sys, sys->md_kernel == 3 ? (int)sys->wide_reps.size() : 1)) != RMPCD_OK) return st;
+    }
+    if (sys->any_body) {
+        launch_md_body(sys->mixed, sys->d, sys->nb_max, sys->step, sys->cur, 0, 0, sys->stream);
+        if ((st = after_launch(sys, 1)) != RMPCD_OK) return st;
     }
     sys->has_sort = false;
     sys->obs_valid = false;
@@ -941,6 +973,12 @@ static int launch_interval(rmpcd_system *sys, int cur, int bcur, bool instrument
             tstop(sys, 1, ev);
             md_trial_done(sys, cs, tev);
         }
+    }
+    if (sys->any_body) {
+        if (instrument) tstart(sys, &ev);
+        launch_md_body(sys->mixed, sys->d, sys->nb_max, STEP_DEVICE, cur, bcur, 1, sys->stream);
+        if (instrument) tstop(sys, 1, ev);
+        n += 1;
     }
     CellPassArgs a{CP_FLIGHT | CP_COLLIDE | CP_REACT | CP_NEXT | CP_WRITE | CP_ADVANCE, STEP_DEVICE, bcur, bcur ^ 1,
                    cur, cur ^ 1};
@@ -1154,6 +1192,248 @@ rmpcd_status rmpcd_launch_count(const rmpcd_system *sys, int64_t *count)
     if (!sys || !count) return RMPCD_EINVAL;
     *count = sys->launches;
     return RMPCD_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------------------
+// rigid bead bodies
+// ----------------------------------------------------------------------------
+// Lookup grid of a body in its frame: gn^3 cubic cells of side h over
+// [glo, glo + gn h)^3 around the centre; cell c lists, in ascending order,
+// every bead whose distance to the cell's box is below the cut-off plus a
+// margin.  The margin covers the FP32 rounding of a particle's body-frame
+// position and of its cell index, so a bead within the cut-off of a particle
+// is always in the particle's list, and a particle outside the grid reaches
+// no bead.
+static void build_body_grid(rmpcd_system::BodyHost &H)
+{
+    BodyDev &D = H.dev;
+    const double margin = 0.0625;
+    const double B = D.reach + margin;
+    const double h0 = std::max(0.5, 2.0 * B / 32.0);
+    const int gn = std::max(1, (int)ceil(2.0 * B / h0));
+    D.gn = gn;
+    D.glo = (float)(-B);
+    D.ginv = (float)(1.0 / h0);
+    const double lo = (double)D.glo, h = 1.0 / (double)D.ginv;
+    const double rcm = sqrt(D.rc2) + margin;
+    const int ncell = gn * gn * gn;
+    std::vector<std::vector<unsigned short>> lists((size_t)ncell);
+    for (int j = 0; j < D.nb; ++j) {
+        const double *b = H.beads[j].b;
+        int a[3], e[3];
+        for (int k = 0; k < 3; ++k) {
+            a[k] = std::max(0, (int)floor((b[k] - rcm - lo) / h));
+            e[k] = std::min(gn - 1, (int)floor((b[k] + rcm - lo) / h));
+        }
+        for (int iz = a[2]; iz <= e[2]; ++iz)
+            for (int iy = a[1]; iy <= e[1]; ++iy)
+                for (int ix = a[0]; ix <= e[0]; ++ix) {
+                    const int id[3] = {ix, iy, iz};
+                    double dd = 0.0;
+                    for (int k = 0; k < 3; ++k) {
+                        const double c0 = lo + id[k] * h, c1 = c0 + h;
+                        const double t = b[k] < c0 ? c0 - b[k] : (b[k] > c1 ? b[k] - c1 : 0.0);
+                        dd += t * t;
+                    }
+                    if (dd < rcm * rcm) lists[(size_t)ix + gn * ((size_t)iy + gn * iz)].push_back((unsigned short)j);
+                }
+    }
+    H.gstart.assign((size_t)ncell + 1, 0);
+    H.glist.clear();
+    for (int c = 0; c < ncell; ++c) {
+        H.gstart[c] = (int)H.glist.size();
+        H.glist.insert(H.glist.end(), lists[c].begin(), lists[c].end());
+    }
+    H.gstart[ncell] = (int)H.glist.size();
+}
+
+// Concatenated bead and grid arrays of all bodies (offsets written into each
+// body's constants), uploaded into fresh buffers.
+static rmpcd_status upload_bodies(rmpcd_system *sys)
+{
+    std::vector<double> bb, be;
+    std::vector<float> bef;
+    std::vector<int> bc, gs;
+    std::vector<unsigned short> gl;
+    sys->nb_max = 0;
+    for (auto &H : sys->bodies) {
+        if (H.beads.empty()) continue;
+        H.dev.bead_off = (int)bc.size();
+        H.dev.gstart_off = (int)gs.size();
+        H.dev.glist_off = (int)gl.size();
+        for (const rmpcd_bead &e : H.beads) {
+            for (int k = 0; k < 3; ++k) bb.push_back(e.b[k]);
+            be.push_back(e.eps_A);
+            be.push_back(e.eps_B);
+            bef.push_back((float)e.eps_A);
+            bef.push_back((float)e.eps_B);
+            bc.push_back(e.catalytic ? 1 : 0);
+        }
+        gs.insert(gs.end(), H.gstart.begin(), H.gstart.end());
+        gl.insert(gl.end(), H.glist.begin(), H.glist.end());
+        sys->nb_max = std::max(sys->nb_max, H.dev.nb);
+    }
+    CK(cudaStreamSynchronize(sys->stream));
+    for (void *p : sys->body_allocs) cudaFree(p);
+    sys->body_allocs.clear();
+    auto put = [&](const void **dst, const void *src, size_t bytes) -> rmpcd_status {
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
+        if (e != cudaSuccess) return cuda_check(sys, e, "cudaMalloc (bodies)");
+        sys->body_allocs.push_back(p);
+        *dst = p;
+        return cuda_check(sys, cudaMemcpyAsync(p, src, bytes, cudaMemcpyHostToDevice, sys->stream), "upload (bodies)");
+    };
+    rmpcd_status st = RMPCD_OK;
+    Dev &d = sys->d;
+    if (st == RMPCD_OK) st = put(reinterpret_cast<const void **>(&d.bead_b), bb.data(), sizeof(double) * bb.size());
+    if (st == RMPCD_OK) st = put(reinterpret_cast<const void **>(&d.bead_eps), be.data(), sizeof(double) * be.size());
+    if (st == RMPCD_OK) st = put(reinterpret_cast<const void **>(&d.bead_eps_f), bef.data(), sizeof(float) * bef.size());
+    if (st == RMPCD_OK) st = put(reinterpret_cast<const void **>(&d.bead_cat), bc.data(), sizeof(int) * bc.size());
+    if (st == RMPCD_OK) st = put(reinterpret_cast<const void **>(&d.grid_start), gs.data(), sizeof(int) * gs.size());
+    if (st == RMPCD_OK)
+        st = put(reinterpret_cast<const void **>(&d.grid_list), gl.data(), sizeof(unsigned short) * gl.size());
+    return st;
+}
+
+extern "C" {
+
+rmpcd_status rmpcd_set_body(rmpcd_system *sys, int32_t replica, const rmpcd_body *body, const rmpcd_bead *beads)
+{
+    if (!sys) return RMPCD_EINVAL;
+    if (replica < 0 || replica >= sys->n_rep) return fail(sys, RMPCD_EINVAL, "replica %d out of range", replica);
+    if (!body || !beads) return fail(sys, RMPCD_EINVAL, "body and beads are required");
+    const rmpcd_params &p = sys->params[replica];
+    if (p.n_colloids != 0 || p.n_bonds != 0 || p.walls)
+        return fail(sys, RMPCD_EINVAL, "replica %d: a body needs a replica created with no colloids, bonds or walls", replica);
+    const int nb = body->n_beads;
+    if (nb < 1 || nb > RMPCD_MAX_BEADS) return fail(sys, RMPCD_EINVAL, "n_beads %d not in [1,%d]", nb, RMPCD_MAX_BEADS);
+    const double mb = body->bead_mass, sig = body->sigma;
+    if (!(mb > 0.0) || !(sig > 0.0) || !std::isfinite(mb) || !std::isfinite(sig))
+        return fail(sys, RMPCD_EINVAL, "bead_mass and sigma must be finite and > 0");
+    bool fin = true;
+    for (int k = 0; k < 3; ++k) fin = fin && std::isfinite(body->x[k]) && std::isfinite(body->v[k]) && std::isfinite(body->l[k]);
+    for (int k = 0; k < 4; ++k) fin = fin && std::isfinite(body->q[k]);
+    if (!fin) return fail(sys, RMPCD_EINVAL, "body state not finite");
+    const double qn = body->q[0] * body->q[0] + body->q[1] * body->q[1] + body->q[2] * body->q[2] + body->q[3] * body->q[3];
+    if (!(fabs(qn - 1.0) <= 1e-9)) return fail(sys, RMPCD_EINVAL, "q must be a unit quaternion");
+    // mass, principal moments and reach, computed as the FP64 definition does
+    double I[3] = {0.0, 0.0, 0.0}, off[3] = {0.0, 0.0, 0.0}, sum[3] = {0.0, 0.0, 0.0}, bmax = 0.0;
+    for (int j = 0; j < nb; ++j) {
+        const double *b = beads[j].b;
+        if (!std::isfinite(b[0]) || !std::isfinite(b[1]) || !std::isfinite(b[2]) || !std::isfinite(beads[j].eps_A) ||
+            !std::isfinite(beads[j].eps_B) || beads[j].eps_A < 0.0 || beads[j].eps_B < 0.0)
+            return fail(sys, RMPCD_EINVAL, "bead %d: position and epsilons must be finite, epsilons >= 0", j);
+        I[0] = I[0] + mb * (b[1] * b[1] + b[2] * b[2]);
+        I[1] = I[1] + mb * (b[2] * b[2] + b[0] * b[0]);
+        I[2] = I[2] + mb * (b[0] * b[0] + b[1] * b[1]);
+        off[0] += mb * b[0] * b[1];
+        off[1] += mb * b[0] * b[2];
+        off[2] += mb * b[1] * b[2];
+        for (int k = 0; k < 3; ++k) sum[k] += b[k];
+        const double r = sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+        if (r > bmax) bmax = r;
+    }
+    if (!(I[0] > 0.0 && I[1] > 0.0 && I[2] > 0.0)) return fail(sys, RMPCD_EINVAL, "principal moments must be > 0");
+    for (int k = 0; k < 3; ++k) {
+        if (!(fabs(sum[k]) <= 1e-9 * nb * bmax)) return fail(sys, RMPCD_EINVAL, "beads are not centred on the centre of mass");
+        if (!(fabs(off[k]) <= 1e-9 * (I[0] + I[1] + I[2])))
+            return fail(sys, RMPCD_EINVAL, "beads are not in the principal frame (off-diagonal inertia)");
+    }
+    const double rc2 = sig * sig * cbrt(2.0);
+    const double reach = bmax + sqrt(rc2);
+    if (2.0 * reach + 2.0 * p.skin >= (double)std::min(p.L[0], std::min(p.L[1], p.L[2])))
+        return fail(sys, RMPCD_EINVAL, "replica %d: box too small for the body's reach", replica);
+
+    rmpcd_status st = unprime(sys);
+    if (st != RMPCD_OK) return st;
+    CK(cudaStreamSynchronize(sys->stream));
+    drop_graphs(sys);
+    // the other bodies' state lives on the device
+    std::vector<BodyDev> all(sys->n_rep);
+    CK(cudaMemcpy(all.data(), sys->d.body, sizeof(BodyDev) * sys->n_rep, cudaMemcpyDeviceToHost));
+    for (int r = 0; r < sys->n_rep; ++r)
+        if (!sys->bodies[r].beads.empty()) {
+            BodyDev &D = sys->bodies[r].dev;
+            for (int k = 0; k < 3; ++k) { D.X[k] = all[r].X[k]; D.V[k] = all[r].V[k]; D.l[k] = all[r].l[k]; }
+            for (int k = 0; k < 4; ++k) D.q[k] = all[r].q[k];
+        }
+    rmpcd_system::BodyHost &H = sys->bodies[replica];
+    H.b = *body;
+    H.beads.assign(beads, beads + nb);
+    BodyDev &D = H.dev;
+    std::memset(&D, 0, sizeof D);
+    for (int k = 0; k < 3; ++k) { D.X[k] = body->x[k]; D.V[k] = body->v[k]; D.l[k] = body->l[k]; D.I[k] = I[k]; }
+    for (int k = 0; k < 4; ++k) D.q[k] = body->q[k];
+    D.M = (double)nb * mb;
+    D.sigma = sig;
+    D.rc2 = rc2;
+    D.reach = reach;
+    D.sigma_f = (float)sig;
+    D.rc2_f = (float)rc2;
+    D.nb = nb;
+    build_body_grid(H);
+    if ((st = upload_bodies(sys)) != RMPCD_OK) return st;
+    for (int r = 0; r < sys->n_rep; ++r) all[r] = sys->bodies[r].dev;
+    CK(cudaMemcpyAsync(sys->d.body, all.data(), sizeof(BodyDev) * sys->n_rep, cudaMemcpyHostToDevice, sys->stream));
+
+    // the body's colloid slot: centre and reach for the near-list test
+    const int g = sys->n_col + replica;
+    rmpcd_colloid c{};
+    for (int k = 0; k < 3; ++k) { c.x[k] = body->x[k]; c.v[k] = body->v[k]; }
+    int Xi[3], Ci[3];
+    float Xf[3], Vf[3];
+    split_colloid(c, p, Xi, Xf, Ci, Vf);
+    const double gn = sqrt(p.g[0] * p.g[0] + p.g[1] * p.g[1] + p.g[2] * p.g[2]);
+    const float rb = (float)(reach + 0.5 * gn * p.tau * p.tau + p.skin);
+    cudaStream_t s = sys->stream;
+    CK(cudaMemcpyAsync(sys->d.colX + 3 * g, c.x, sizeof(double) * 3, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(sys->d.colV + 3 * g, c.v, sizeof(double) * 3, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(sys->d.colXi + 3 * g, Xi, sizeof Xi, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(sys->d.colXf + 3 * g, Xf, sizeof Xf, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(sys->d.colCi + 3 * g, Ci, sizeof Ci, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(sys->d.colVf + 3 * g, Vf, sizeof Vf, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(sys->col_rc + g, &reach, sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(sys->col_rb + g, &rb, sizeof(float), cudaMemcpyHostToDevice, s));
+    ReplicaDev &rp = sys->rep[replica];
+    rp.n_col = 1;
+    rp.col_off = g;
+    rp.body = replica;
+    CK(cudaMemcpyAsync(const_cast<ReplicaDev *>(sys->d.rep) + replica, &rp, sizeof rp, cudaMemcpyHostToDevice, s));
+    // working state of the near particles
+    const size_t need = (sys->mixed ? 64 : 80) * (size_t)std::max(sys->n_total, 1);
+    if (sys->work_bytes < need) {
+        CK(cudaStreamSynchronize(s));
+        auto it = std::find(sys->allocs.begin(), sys->allocs.end(), sys->d.md_work);
+        if (it != sys->allocs.end()) sys->allocs.erase(it);
+        cudaFree(sys->d.md_work);
+        sys->d.md_work = nullptr;
+        unsigned char *w = nullptr;
+        if ((st = dalloc(sys, &w, need)) != RMPCD_OK) return st;
+        sys->d.md_work = w;
+        sys->work_bytes = need;
+    }
+    CK(prepare_md_body(sys->mixed, sys->nb_max));
+    sys->any_body = true;
+    CK(cudaStreamSynchronize(s));
+    return RMPCD_OK;
+}
+
+rmpcd_status rmpcd_get_body(rmpcd_system *sys, int32_t replica, rmpcd_body *out)
+{
+    if (!sys || !out) return RMPCD_EINVAL;
+    if (replica < 0 || replica >= sys->n_rep) return fail(sys, RMPCD_EINVAL, "replica %d out of range", replica);
+    const rmpcd_system::BodyHost &H = sys->bodies[replica];
+    if (H.beads.empty()) return fail(sys, RMPCD_EINVAL, "replica %d has no body", replica);
+    BodyDev D;
+    CK(cudaMemcpyAsync(&D, sys->d.body + replica, sizeof D, cudaMemcpyDeviceToHost, sys->stream));
+    rmpcd_status st = check_errors(sys);
+    *out = H.b;
+    for (int k = 0; k < 3; ++k) { out->x[k] = D.X[k]; out->v[k] = D.V[k]; out->l[k] = D.l[k]; }
+    for (int k = 0; k < 4; ++k) out->q[k] = D.q[k];
+    return st;
 }
 
 }  // extern "C"

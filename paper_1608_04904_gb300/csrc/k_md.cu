@@ -181,23 +181,6 @@ __device__ __forceinline__ bool inside_cat_m(const ReplicaDev &rp, const SH &S, 
     return false;
 }
 
-// A tagged A particle that has left every catalytic range becomes B with
-// probability cat_prob (§1.5); an A particle inside a range is tagged.
-__device__ __forceinline__ uint32_t catalysis(const ReplicaDev &rp, uint32_t fid, bool inside, uint32_t step, int s)
-{
-    if (fid & F_B) return fid;
-    if (inside) return fid | F_TAG;
-    if (!(fid & F_TAG)) return fid;
-    bool go = true;
-    if (rp.cat_thr < 4294967296.0) {
-        U4 w = philox(fid & ID_MASK, step, P_CAT, (uint32_t)s, rp.seed);
-        go = (double)w.x < rp.cat_thr;
-    }
-    fid &= ~F_TAG;
-    if (go) fid |= F_B;
-    return fid;
-}
-
 __device__ __forceinline__ bool bonded(const BondDev *bond, int nbond, int a, int b)
 {
     for (int k = 0; k < nbond; ++k)
@@ -787,7 +770,7 @@ __global__ void __launch_bounds__(MDGeom<CS>::NT, 1) k_md(Dev d, uint32_t step, 
     if (tid == 0) s_rp = d.rep[r];
     __syncthreads();
     const ReplicaDev &rp = s_rp;
-    if (rp.n_col == 0) return;   // uniform over the cluster
+    if (rp.n_col == 0 || rp.body >= 0) return;   // uniform over the cluster (bodies: k_md_body)
     if (tid == 0) {
         S.nc = rp.n_col;
         S.nbond = rp.n_bond;

@@ -1,0 +1,523 @@
+// k_md_body.cu -- near-field MD of one collision interval for the replicas
+// whose colloid is a rigid bead body: the Janus particle of §1.5, a network
+// of WCA beads (§1.4) that moves as one rigid body.
+//
+// Per sub-step dt (§1.1 velocity Verlet):
+//   body:    V += dt/2 F/M, l += dt/2 R^T T, X += dt V, free rotation by the
+//            symmetric principal-axis splitting R_1(dt/2) R_2(dt/2) R_3(dt)
+//            R_2(dt/2) R_1(dt/2) (Dullweber, Leimkuhler & McLachlan, J. Chem.
+//            Phys. 107, 5840 (1997)), each turn R_k(h) by the angle phi with
+//            tan(phi/2) = h l_k / (2 I_k): q <- q (1, tan(phi/2) e_k), l turned
+//            by -phi about e_k; q normalised after the five turns;
+//   solvent: v += dt/2 f, x += dt v;
+//   forces:  WCA between each near particle and the beads it reaches; the
+//            pair force f on the particle puts -f and the torque -(R b_j) x f
+//            on the body;
+//   kicks:   V += dt/2 F/M, l += dt/2 R^T T, v += dt/2 f;
+//   §1.5:    an A particle inside a catalytic bead's range is tagged, a tagged
+//            one that has left every such range becomes B.
+//
+// One CTA of MDB_NT threads per replica runs all n_md sub-steps.  Thread 0
+// integrates the body in FP64 (both precisions); after every turn the CTA
+// recomputes the bead offsets R b_j in shared memory.  A particle finds the
+// beads it can reach through a lookup grid in the body frame, built on the
+// host once per body: the grid cell of the particle's body-frame position
+// lists, in ascending order, every bead whose cut-off plus a margin reaches
+// the cell, so the FP64 path adds the same pair forces in the same order as
+// a scan over all beads.  Body force and torque are summed as 64-bit fixed
+// point (2^-40): per thread, per warp by shuffles, then over the warps, so
+// the totals do not depend on the order of the near list.
+#include <type_traits>
+
+#include "rmpcd_kernels.cuh"
+
+namespace rmpcd {
+
+constexpr int MDB_NT = 1024;
+constexpr int MDB_NW = MDB_NT / 32;
+
+struct __align__(16) BWorkM {
+    int c[3];
+    uint32_t fid;
+    float o[3];
+    int slot;
+    float v[3];
+    float p0;
+    float f[3];
+    float p1;
+};
+struct __align__(16) BWorkD {
+    double x[3];
+    double v[3];
+    double f[3];
+    uint32_t fid;
+    int slot;
+};
+
+// Body state and per-sub-step frames; bead arrays follow in dynamic shared
+// memory (see bead_layout).
+struct BodyShared {
+    double X[3], V[3], q[4], l[3], X0[3];
+    double R[3][3];
+    double Xw[3];
+    double F[3], tb[3];
+    double M, I[3], sigma, rc2;
+    float Rf[3][3];
+    float Cf[3];
+    int Ci[3];
+    float sigma_f, rc2_f, glo, ginv;
+    int gn, nb, nn;
+    const int *gstart;
+    const unsigned short *glist;
+    unsigned long long wpart[MDB_NW][6];
+};
+
+// Dynamic shared memory: FP64 path b[3nb], rb[3nb], Xb[3nb], eps[2nb] (double),
+// cat[nb]; mixed path rb[3nb] (float), eps[2nb] (float), cat[nb].
+struct BeadSmem {
+    double *b, *rb, *Xb, *eps;
+    float *rbf, *epsf;
+    int *cat;
+};
+
+template <bool MIXED>
+__host__ __device__ inline size_t bead_smem_bytes(int nb)
+{
+    return MIXED ? (size_t)nb * (3 * sizeof(double) + 3 * sizeof(float) + 2 * sizeof(float) + sizeof(int))
+                 : (size_t)nb * (11 * sizeof(double) + sizeof(int));
+}
+
+template <bool MIXED>
+__device__ inline BeadSmem bead_layout(unsigned char *p, int nb)
+{
+    BeadSmem B{};
+    B.b = reinterpret_cast<double *>(p);
+    p += sizeof(double) * 3 * nb;
+    if (MIXED) {
+        B.rbf = reinterpret_cast<float *>(p);
+        p += sizeof(float) * 3 * nb;
+        B.epsf = reinterpret_cast<float *>(p);
+        p += sizeof(float) * 2 * nb;
+    } else {
+        B.rb = reinterpret_cast<double *>(p);
+        p += sizeof(double) * 3 * nb;
+        B.Xb = reinterpret_cast<double *>(p);
+        p += sizeof(double) * 3 * nb;
+        B.eps = reinterpret_cast<double *>(p);
+        p += sizeof(double) * 2 * nb;
+    }
+    B.cat = reinterpret_cast<int *>(p);
+    return B;
+}
+
+// --- body integrator (thread 0, FP64) ----------------------------------------
+__device__ void body_frames(const ReplicaDev &rp, BodyShared &S)
+{
+    const double w = S.q[0], x = S.q[1], y = S.q[2], z = S.q[3];
+    S.R[0][0] = 1.0 - 2.0 * (y * y + z * z);
+    S.R[0][1] = 2.0 * (x * y - w * z);
+    S.R[0][2] = 2.0 * (x * z + w * y);
+    S.R[1][0] = 2.0 * (x * y + w * z);
+    S.R[1][1] = 1.0 - 2.0 * (x * x + z * z);
+    S.R[1][2] = 2.0 * (y * z - w * x);
+    S.R[2][0] = 2.0 * (x * z - w * y);
+    S.R[2][1] = 2.0 * (y * z + w * x);
+    S.R[2][2] = 1.0 - 2.0 * (x * x + y * y);
+    wrapped_colloid(rp, S.X, S.Xw);
+    for (int k = 0; k < 3; ++k) {
+        for (int t = 0; t < 3; ++t) S.Rf[k][t] = (float)S.R[k][t];
+        const double fl = floor(S.Xw[k]);
+        int c = (int)fl;
+        float o = (float)(S.Xw[k] - fl);
+        if (o >= 1.0f) { o = 0.0f; c += 1; }
+        if (c >= rp.L[k]) c -= rp.L[k];
+        S.Ci[k] = c;
+        S.Cf[k] = o;
+    }
+}
+
+__device__ void body_kick(BodyShared &S, double hdt)
+{
+    for (int t = 0; t < 3; ++t) {
+        S.V[t] = fma(hdt, S.F[t] / S.M, S.V[t]);
+        S.l[t] = fma(hdt, S.tb[t], S.l[t]);
+    }
+}
+
+__device__ void body_kick_drift_rotate(BodyShared &S, double dt, double hdt)
+{
+    for (int t = 0; t < 3; ++t) {
+        S.V[t] = fma(hdt, S.F[t] / S.M, S.V[t]);
+        S.l[t] = fma(hdt, S.tb[t], S.l[t]);
+        S.X[t] = fma(dt, S.V[t], S.X[t]);
+    }
+    double q[4] = {S.q[0], S.q[1], S.q[2], S.q[3]};
+    double l[3] = {S.l[0], S.l[1], S.l[2]};
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int k = (s == 2) ? 2 : (s == 1 || s == 3) ? 1 : 0;
+        const int a = (k + 1) % 3, b = (k + 2) % 3;
+        const double h = (s == 2) ? dt : 0.5 * dt;
+        const double t = 0.5 * (h * l[k] / S.I[k]);
+        const double tt = t * t;
+        const double inv = 1.0 / (1.0 + tt);
+        const double c = (1.0 - tt) * inv;
+        const double sn = (2.0 * t) * inv;
+        const double la = c * l[a] + sn * l[b];
+        const double lb = c * l[b] - sn * l[a];
+        l[a] = la;
+        l[b] = lb;
+        const double w = q[0], v0 = q[1 + k], va = q[1 + a], vb = q[1 + b];
+        q[0] = w - t * v0;
+        q[1 + k] = v0 + t * w;
+        q[1 + a] = va + t * vb;
+        q[1 + b] = vb - t * va;
+    }
+    const double nq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    for (int i = 0; i < 4; ++i) S.q[i] = q[i] / nq;
+    for (int i = 0; i < 3; ++i) S.l[i] = l[i];
+}
+
+// Fixed-point totals of the warps -> F and the body-frame torque R^T T.
+__device__ void body_totals(BodyShared &S)
+{
+    long long Q[6] = {0, 0, 0, 0, 0, 0};
+    for (int w = 0; w < MDB_NW; ++w)
+        for (int i = 0; i < 6; ++i) Q[i] += (long long)S.wpart[w][i];
+    double T[3];
+    for (int k = 0; k < 3; ++k) {
+        S.F[k] = (double)Q[k] * 0x1p-40;
+        T[k] = (double)Q[3 + k] * 0x1p-40;
+    }
+    for (int k = 0; k < 3; ++k) S.tb[k] = S.R[0][k] * T[0] + S.R[1][k] * T[1] + S.R[2][k] * T[2];
+}
+
+// Bead offsets R b_j (and FP64 positions Xw + R b_j) for the current frame.
+template <bool MIXED>
+__device__ void bead_frames(BodyShared &S, const BeadSmem &B)
+{
+    for (int j = threadIdx.x; j < S.nb; j += MDB_NT) {
+        const double b0 = B.b[3 * j], b1 = B.b[3 * j + 1], b2 = B.b[3 * j + 2];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const double r = S.R[t][0] * b0 + S.R[t][1] * b1 + S.R[t][2] * b2;
+            if (MIXED) {
+                B.rbf[3 * j + t] = (float)r;
+            } else {
+                B.rb[3 * j + t] = r;
+                B.Xb[3 * j + t] = S.Xw[t] + r;
+            }
+        }
+    }
+}
+
+// Lookup-grid range of a body-frame position u: [beg, end) in the list.
+__device__ __forceinline__ void grid_range(const BodyShared &S, const float dc[3], int &beg, int &end)
+{
+    int id[3];
+    bool in = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float u = S.Rf[0][k] * dc[0] + S.Rf[1][k] * dc[1] + S.Rf[2][k] * dc[2];
+        const float g = (u - S.glo) * S.ginv;
+        in = in && g >= 0.0f && g < (float)S.gn;
+        id[k] = (int)g;
+    }
+    beg = end = 0;
+    if (in) {
+        const int cell = id[0] + S.gn * (id[1] + S.gn * id[2]);
+        beg = __ldg(S.gstart + cell);
+        end = __ldg(S.gstart + cell + 1);
+    }
+}
+
+__device__ __forceinline__ void add_fixed(long long acc[6], const float fk[3], const float rb[3])
+{
+    const float c[3] = {rb[1] * fk[2] - rb[2] * fk[1], rb[2] * fk[0] - rb[0] * fk[2], rb[0] * fk[1] - rb[1] * fk[0]};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        acc[k] -= __float2ll_rn(fk[k] * 0x1p40f);
+        acc[3 + k] -= __float2ll_rn(c[k] * 0x1p40f);
+    }
+}
+
+// Mixed: force on one particle (cell c, offset o) from the beads it reaches.
+__device__ __forceinline__ bool body_force_m(const ReplicaDev &rp, const BodyShared &S, const BeadSmem &B,
+                                             const int c[3], const float o[3], uint32_t fid, float f[3],
+                                             long long acc[6])
+{
+    float dc[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dc[k] = (float)(c[k] - S.Ci[k]) + (o[k] - S.Cf[k]);
+    min_image(rp, dc);
+    int beg, end;
+    grid_range(S, dc, beg, end);
+    f[0] = f[1] = f[2] = 0.0f;
+    bool inside = false;
+    const int isb = (fid & F_B) ? 1 : 0;
+    for (int e = beg; e < end; ++e) {
+        const int j = __ldg(S.glist + e);
+        const float rb[3] = {B.rbf[3 * j], B.rbf[3 * j + 1], B.rbf[3 * j + 2]};
+        const float d[3] = {dc[0] - rb[0], dc[1] - rb[1], dc[2] - rb[2]};
+        const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (r2 < S.rc2_f) {
+            const float fr = wca_fr_m(B.epsf[2 * j + isb], S.sigma_f, r2);
+            const float fk[3] = {fr * d[0], fr * d[1], fr * d[2]};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) f[k] = f[k] + fk[k];
+            add_fixed(acc, fk, rb);
+            inside = inside || B.cat[j] != 0;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) f[k] = f[k] + rp.g_f[k];
+    return inside;
+}
+
+// FP64: the same sums as the FP64 definition (ascending bead order).
+__device__ __forceinline__ bool body_force_d(const ReplicaDev &rp, const BodyShared &S, const BeadSmem &B,
+                                             const double x[3], uint32_t fid, double f[3], long long acc[6])
+{
+    double dcd[3] = {x[0] - S.Xw[0], x[1] - S.Xw[1], x[2] - S.Xw[2]};
+    min_image(rp, dcd);
+    const float dc[3] = {(float)dcd[0], (float)dcd[1], (float)dcd[2]};
+    int beg, end;
+    grid_range(S, dc, beg, end);
+    f[0] = f[1] = f[2] = 0.0;
+    bool inside = false;
+    const int isb = (fid & F_B) ? 1 : 0;
+    for (int e = beg; e < end; ++e) {
+        const int j = __ldg(S.glist + e);
+        double d[3] = {x[0] - B.Xb[3 * j], x[1] - B.Xb[3 * j + 1], x[2] - B.Xb[3 * j + 2]};
+        min_image(rp, d);
+        const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (r2 < S.rc2) {
+            const double eps = B.eps[2 * j + isb];
+            const double ir2 = 1.0 / r2;
+            const double s2 = S.sigma * S.sigma * ir2;
+            const double s6 = s2 * s2 * s2;
+            const double fr = 24.0 * eps * s6 * (2.0 * s6 - 1.0) * ir2;
+            const double fk[3] = {fr * d[0], fr * d[1], fr * d[2]};
+            const double *r = B.rb + 3 * j;
+            const double cr[3] = {r[1] * fk[2] - r[2] * fk[1], r[2] * fk[0] - r[0] * fk[2], r[0] * fk[1] - r[1] * fk[0]};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                f[k] = f[k] + fk[k];
+                acc[k] -= __double2ll_rn(fk[k] * 0x1p40);
+                acc[3 + k] -= __double2ll_rn(cr[k] * 0x1p40);
+            }
+            inside = inside || B.cat[j] != 0;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) f[k] = f[k] + rp.g[k];
+    return inside;
+}
+
+// Warp sums of the fixed-point partials into S.wpart[warp].
+__device__ __forceinline__ void warp_partials6(BodyShared &S, const long long acc[6])
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        long long x = acc[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) S.wpart[wid][i] = (unsigned long long)x;
+    }
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(MDB_NT, 1) k_md_body(Dev d, uint32_t step, int rbuf, int bbuf, int do_bin)
+{
+    step = resolve_step(d, step);   // STEP_DEVICE: the step of the control block
+    using W = typename std::conditional<MIXED, BWorkM, BWorkD>::type;
+    __shared__ BodyShared S;
+    __shared__ ReplicaDev s_rp;
+    extern __shared__ __align__(16) unsigned char bead_raw[];
+    const int r = blockIdx.x;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_rp = d.rep[r];
+    __syncthreads();
+    const ReplicaDev &rp = s_rp;
+    if (rp.body < 0) return;   // uniform over the CTA
+    const BodyDev &bd = d.body[rp.body];
+    if (tid == 0) {
+        for (int k = 0; k < 3; ++k) {
+            S.X[k] = bd.X[k]; S.V[k] = bd.V[k]; S.l[k] = bd.l[k]; S.X0[k] = bd.X[k]; S.I[k] = bd.I[k];
+        }
+        for (int k = 0; k < 4; ++k) S.q[k] = bd.q[k];
+        S.M = bd.M; S.sigma = bd.sigma; S.rc2 = bd.rc2;
+        S.sigma_f = bd.sigma_f; S.rc2_f = bd.rc2_f; S.glo = bd.glo; S.ginv = bd.ginv;
+        S.gn = bd.gn; S.nb = bd.nb;
+        S.gstart = d.grid_start + bd.gstart_off;
+        S.glist = d.grid_list + bd.glist_off;
+        S.nn = min(d.near_count[r], rp.n_part);
+        body_frames(rp, S);
+    }
+    __syncthreads();
+    const int nb = S.nb, nn = S.nn;
+    const BeadSmem B = bead_layout<MIXED>(bead_raw, nb);
+    for (int j = tid; j < nb; j += MDB_NT) {
+        const int g = bd.bead_off + j;
+        for (int t = 0; t < 3; ++t) B.b[3 * j + t] = d.bead_b[3 * g + t];
+        if (MIXED) {
+            B.epsf[2 * j] = d.bead_eps_f[2 * g];
+            B.epsf[2 * j + 1] = d.bead_eps_f[2 * g + 1];
+        } else {
+            B.eps[2 * j] = d.bead_eps[2 * g];
+            B.eps[2 * j + 1] = d.bead_eps[2 * g + 1];
+        }
+        B.cat[j] = d.bead_cat[g];
+    }
+    __syncthreads();
+    bead_frames<MIXED>(S, B);
+    __syncthreads();
+
+    const int *list = d.near_list + rp.part_off;
+    W *work = reinterpret_cast<W *>(d.md_work) + rp.part_off;
+    long long acc[6];
+
+    // forces at the start of the interval
+#pragma unroll
+    for (int i = 0; i < 6; ++i) acc[i] = 0;
+    for (int k = tid; k < nn; k += MDB_NT) {
+        W w;
+        const int slot = list[k];
+        w.slot = slot;
+        if constexpr (MIXED) {
+            RecM rec = load_rec(reinterpret_cast<const RecM *>(d.rec[rbuf]) + slot);
+            for (int t = 0; t < 3; ++t) { w.c[t] = cw_get(rec.cw, t); w.o[t] = rec.o[t]; w.v[t] = rec.v[t]; }
+            w.fid = rec.fid;
+            body_force_m(rp, S, B, w.c, w.o, w.fid, w.f, acc);
+        } else {
+            RecD rec = load_rec(reinterpret_cast<const RecD *>(d.rec[rbuf]) + slot);
+            for (int t = 0; t < 3; ++t) { w.x[t] = rec.x[t]; w.v[t] = rec.v[t]; }
+            w.fid = rec.fid;
+            body_force_d(rp, S, B, w.x, w.fid, w.f, acc);
+        }
+        work[k] = w;
+    }
+    warp_partials6(S, acc);
+    __syncthreads();
+    if (tid == 0) body_totals(S);
+
+    const double dt = rp.dt, hdt = rp.hdt;
+    for (int s = 0; s < rp.n_md; ++s) {
+        if (tid == 0) {
+            body_kick_drift_rotate(S, dt, hdt);
+            body_frames(rp, S);
+        }
+        __syncthreads();
+        bead_frames<MIXED>(S, B);
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 6; ++i) acc[i] = 0;
+        for (int k = tid; k < nn; k += MDB_NT) {
+            W w = work[k];
+            bool in;
+            if constexpr (MIXED) {
+                const float hdtf = rp.hdt_f, dtf = rp.dt_f;
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    if (s > 0) w.v[t] = fmaf(hdtf, w.f[t], w.v[t]);
+                    w.v[t] = fmaf(hdtf, w.f[t], w.v[t]);
+                    w.o[t] = fmaf(dtf, w.v[t], w.o[t]);
+                }
+                in = body_force_m(rp, S, B, w.c, w.o, w.fid, w.f, acc);
+            } else {
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    if (s > 0) w.v[t] = fma(hdt, w.f[t], w.v[t]);
+                    w.v[t] = fma(hdt, w.f[t], w.v[t]);
+                    w.x[t] = fma(dt, w.v[t], w.x[t]);
+                }
+                in = body_force_d(rp, S, B, w.x, w.fid, w.f, acc);
+            }
+            w.fid = catalysis(rp, w.fid, in, step, s);
+            work[k] = w;
+        }
+        warp_partials6(S, acc);
+        __syncthreads();
+        if (tid == 0) {
+            body_totals(S);
+            body_kick(S, hdt);
+        }
+    }
+
+    // last half kick, wrap, write back (and bin for the collision of `step`)
+    double sh[3];
+    grid_shift(rp.seed, step, sh);
+    for (int k = tid; k < nn; k += MDB_NT) {
+        W w = work[k];
+        if constexpr (MIXED) {
+            for (int t = 0; t < 3; ++t) w.v[t] = fmaf(rp.hdt_f, w.f[t], w.v[t]);
+            renorm_m(rp, w.c, w.o);
+            RecM rec;
+            rec.cw = cw_make(w.c[0], w.c[1], w.c[2]);
+            for (int t = 0; t < 3; ++t) { rec.o[t] = w.o[t]; rec.v[t] = w.v[t]; }
+            rec.fid = do_bin ? (w.fid | F_PROP) : (w.fid & ~F_PROP);
+            store_rec(reinterpret_cast<RecM *>(d.rec[rbuf]) + w.slot, rec);
+            if (do_bin) {
+                float sf[3] = {(float)sh[0], (float)sh[1], (float)sh[2]};
+                bin_particle(d, bbuf, rp.cell_off + cell_key_m(rp, w.c, w.o, sf), w.slot);
+            }
+        } else {
+            for (int t = 0; t < 3; ++t) w.v[t] = fma(hdt, w.f[t], w.v[t]);
+            wrap_periodic_d(rp, w.x);
+            RecD rec;
+            for (int t = 0; t < 3; ++t) { rec.x[t] = w.x[t]; rec.v[t] = w.v[t]; }
+            rec.fid = do_bin ? (w.fid | F_PROP) : (w.fid & ~F_PROP);
+            rec.u0 = 0u;
+            rec.u1 = 0.0;
+            store_rec(reinterpret_cast<RecD *>(d.rec[rbuf]) + w.slot, rec);
+            if (do_bin) bin_particle(d, bbuf, rp.cell_off + cell_key_d(rp, w.x, sh), w.slot);
+        }
+    }
+    if (tid == 0) {
+        // body state, and its centre as the replica's near-list colloid
+        BodyDev &bw = d.body[rp.body];
+        double dd = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            bw.X[k] = S.X[k]; bw.V[k] = S.V[k]; bw.l[k] = S.l[k];
+            const double e = S.X[k] - S.X0[k];
+            dd = dd + e * e;
+        }
+        for (int k = 0; k < 4; ++k) bw.q[k] = S.q[k];
+        if (!(dd <= rp.skin * rp.skin)) atomicAdd(&d.err[ERR_SKIN], 1u);
+        const int g = rp.col_off;
+        body_frames(rp, S);
+        for (int k = 0; k < 3; ++k) {
+            d.colX[3 * g + k] = S.X[k];
+            d.colV[3 * g + k] = S.V[k];
+            const double fl = floor(S.X[k]);
+            d.colXi[3 * g + k] = (int)fl;
+            d.colXf[3 * g + k] = S.Cf[k];
+            d.colCi[3 * g + k] = S.Ci[k];
+            d.colVf[3 * g + k] = (float)S.V[k];
+        }
+        d.near_count[r] = 0;
+    }
+}
+
+size_t md_body_smem(bool mixed, int nb_max)
+{
+    return mixed ? bead_smem_bytes<true>(nb_max) : bead_smem_bytes<false>(nb_max);
+}
+
+cudaError_t prepare_md_body(bool mixed, int nb_max)
+{
+    const int bytes = (int)md_body_smem(mixed, nb_max);
+    if (mixed) return cudaFuncSetAttribute(k_md_body<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return cudaFuncSetAttribute(k_md_body<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+void launch_md_body(bool mixed, const Dev &d, int nb_max, uint32_t step, int rbuf, int bbuf, int do_bin,
+                    cudaStream_t s)
+{
+    const size_t bytes = md_body_smem(mixed, nb_max);
+    if (mixed) k_md_body<true><<<d.n_rep, MDB_NT, bytes, s>>>(d, step, rbuf, bbuf, do_bin);
+    else k_md_body<false><<<d.n_rep, MDB_NT, bytes, s>>>(d, step, rbuf, bbuf, do_bin);
+}
+
+}  // namespace rmpcd

@@ -32,6 +32,7 @@ constexpr int CP_MAX_CAP = 768;    // largest bucket_cap (a crowded tile uses th
 constexpr int MD_THREADS = 1024;   // threads of the near-field MD CTA (one per replica)
 constexpr int MAXC = 64;           // colloids per replica handled by the MD CTA
 constexpr int MAXB = 16;           // bonds per replica
+constexpr int MAXBEADS = 1024;     // beads of a rigid body
 
 constexpr uint32_t F_B = 1u << 29;
 constexpr uint32_t F_TAG = 1u << 30;
@@ -52,7 +53,8 @@ struct ReplicaDev {
     int tile_off, n_tiles;
     int n_col, col_off, n_bond, bond_off;
     int bulk_on, has_g;
-    int thr_off, pad;
+    int thr_off;
+    int body;               // index of the replica's rigid bead body, -1: none
     double kT, tau, dt, hdt, ca, sa, omc;
     double g[3];
     double gnorm, cat_thr, skin;
@@ -84,6 +86,24 @@ __device__ __forceinline__ HotM hot_m(const ReplicaDev &rp)
     h.nz = rp.nz; h.walls = rp.walls; h.has_g = rp.has_g; h.tau_f = rp.tau_f;
     return h;
 }
+
+// A rigid bead body (the Janus particle): FP64 state, constants, and the
+// body-frame lookup grid whose cell lists every bead that a particle in the
+// cell can reach, in ascending bead order.
+struct BodyDev {
+    double X[3], V[3], q[4], l[3];   // centre of mass (unwrapped), its velocity,
+                                     // orientation (w, x, y, z), body-frame angular momentum
+    double M, I[3];                  // mass, principal moments
+    double sigma, rc2, reach;        // bead WCA sigma, cut-off^2, max|b| + cut-off
+    float sigma_f, rc2_f;
+    float glo, ginv;                 // grid cell of body-frame u: floor((u - glo) ginv) per axis
+    int gn;                          // grid cells per axis
+    int nb;                          // beads [bead_off, bead_off + nb)
+    int bead_off;
+    int gstart_off;                  // gn^3 + 1 list offsets at grid_start + gstart_off
+    int glist_off;                   // list entries at grid_list + glist_off
+    int pad;
+};
 
 // Device-resident interval control: the collision index of the next fused
 // interval and the launch counter of the cell pass (ticket parity and
@@ -131,6 +151,13 @@ struct Dev {
     MdWideGlobal *md_wide;       // wide MD kernel scratch
     Ctl *ctl;                    // interval control (step, cell-pass launch counter)
     unsigned int *maxcnt;        // largest cell count seen (bucket-width tuner)
+    BodyDev *body;               // rigid bead bodies
+    const double *bead_b;        // [3 * bead] body-frame bead positions
+    const double *bead_eps;      // [2 * bead] eps_A, eps_B
+    const float *bead_eps_f;
+    const int *bead_cat;
+    const int *grid_start;       // lookup-grid list offsets
+    const unsigned short *grid_list;
     int cap;
     int n_rep;
     int n_tiles;
@@ -558,6 +585,23 @@ __device__ __forceinline__ bool near_test_m(const P &rp, int nc, const int *Ci, 
         if (r2 < R * R) return true;
     }
     return false;
+}
+
+// A tagged A particle that has left every catalytic range becomes B with
+// probability cat_prob (§1.5); an A particle inside a range is tagged.
+__device__ __forceinline__ uint32_t catalysis(const ReplicaDev &rp, uint32_t fid, bool inside, uint32_t step, int s)
+{
+    if (fid & F_B) return fid;
+    if (inside) return fid | F_TAG;
+    if (!(fid & F_TAG)) return fid;
+    bool go = true;
+    if (rp.cat_thr < 4294967296.0) {
+        U4 w = philox(fid & ID_MASK, step, P_CAT, (uint32_t)s, rp.seed);
+        go = (double)w.x < rp.cat_thr;
+    }
+    fid &= ~F_TAG;
+    if (go) fid |= F_B;
+    return fid;
 }
 
 // Mixed-path MD arithmetic shared by both MD kernels (so that they agree bit
