@@ -17,9 +17,14 @@
 //   §1.5:    an A particle inside a catalytic bead's range is tagged, a tagged
 //            one that has left every such range becomes B.
 //
-// One CTA of MDB_NT threads per replica runs all n_md sub-steps.  Thread 0
-// integrates the body in FP64 (both precisions); after every turn the CTA
-// recomputes the bead offsets R b_j in shared memory.  A particle finds the
+// One CTA of MDB_NT threads per replica runs all n_md sub-steps; two CTAs
+// share an SM, so one replica's serial body update overlaps the other's
+// force pass.  Thread 0 integrates the body in FP64 on both paths: FP32
+// rounding of the orientation accumulates over the sub-steps into bead
+// positions that the steep bead potential turns into force errors well above
+// the mixed path's tolerance, and the body update is a small part of the
+// kernel's time.  After every turn the CTA recomputes the bead offsets R b_j
+// (FP64, rounded to FP32 on the mixed path) in shared memory.  A particle finds the
 // beads it can reach through a lookup grid in the body frame, built on the
 // host once per body: the grid cell of the particle's body-frame position
 // lists, in ascending order, every bead whose cut-off plus a margin reaches
@@ -33,19 +38,18 @@
 
 namespace rmpcd {
 
-constexpr int MDB_NT = 1024;
+constexpr int MDB_NT = 512;
 constexpr int MDB_NW = MDB_NT / 32;
 
 struct __align__(16) BWorkM {
-    int c[3];
+    uint32_t cw;
     uint32_t fid;
-    float o[3];
     int slot;
+    float o[3];
     float v[3];
-    float p0;
     float f[3];
-    float p1;
 };
+static_assert(sizeof(BWorkM) == 48, "mixed MD work record is three 16-byte words");
 struct __align__(16) BWorkD {
     double x[3];
     double v[3];
@@ -57,11 +61,13 @@ struct __align__(16) BWorkD {
 // Body state and per-sub-step frames; bead arrays follow in dynamic shared
 // memory (see bead_layout).
 struct BodyShared {
+    // FP64 path
     double X[3], V[3], q[4], l[3], X0[3];
     double R[3][3];
     double Xw[3];
     double F[3], tb[3];
     double M, I[3], sigma, rc2;
+    // both: rotation in FP32 (lookup grid, mixed forces), wrapped centre cell
     float Rf[3][3];
     float Cf[3];
     int Ci[3];
@@ -73,7 +79,7 @@ struct BodyShared {
 };
 
 // Dynamic shared memory: FP64 path b[3nb], rb[3nb], Xb[3nb], eps[2nb] (double),
-// cat[nb]; mixed path rb[3nb] (float), eps[2nb] (float), cat[nb].
+// cat[nb]; mixed path b[3nb] (double), rb[3nb], eps[2nb] (float), cat[nb].
 struct BeadSmem {
     double *b, *rb, *Xb, *eps;
     float *rbf, *epsf;
@@ -83,7 +89,7 @@ struct BeadSmem {
 template <bool MIXED>
 __host__ __device__ inline size_t bead_smem_bytes(int nb)
 {
-    return MIXED ? (size_t)nb * (3 * sizeof(double) + 3 * sizeof(float) + 2 * sizeof(float) + sizeof(int))
+    return MIXED ? (size_t)nb * (3 * sizeof(double) + 5 * sizeof(float) + sizeof(int))
                  : (size_t)nb * (11 * sizeof(double) + sizeof(int));
 }
 
@@ -91,14 +97,16 @@ template <bool MIXED>
 __device__ inline BeadSmem bead_layout(unsigned char *p, int nb)
 {
     BeadSmem B{};
-    B.b = reinterpret_cast<double *>(p);
-    p += sizeof(double) * 3 * nb;
     if (MIXED) {
+        B.b = reinterpret_cast<double *>(p);
+        p += sizeof(double) * 3 * nb;
         B.rbf = reinterpret_cast<float *>(p);
         p += sizeof(float) * 3 * nb;
         B.epsf = reinterpret_cast<float *>(p);
         p += sizeof(float) * 2 * nb;
     } else {
+        B.b = reinterpret_cast<double *>(p);
+        p += sizeof(double) * 3 * nb;
         B.rb = reinterpret_cast<double *>(p);
         p += sizeof(double) * 3 * nb;
         B.Xb = reinterpret_cast<double *>(p);
@@ -197,13 +205,15 @@ template <bool MIXED>
 __device__ void bead_frames(BodyShared &S, const BeadSmem &B)
 {
     for (int j = threadIdx.x; j < S.nb; j += MDB_NT) {
-        const double b0 = B.b[3 * j], b1 = B.b[3 * j + 1], b2 = B.b[3 * j + 2];
+        if (MIXED) {
+            const double b0 = B.b[3 * j], b1 = B.b[3 * j + 1], b2 = B.b[3 * j + 2];
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            const double r = S.R[t][0] * b0 + S.R[t][1] * b1 + S.R[t][2] * b2;
-            if (MIXED) {
-                B.rbf[3 * j + t] = (float)r;
-            } else {
+            for (int t = 0; t < 3; ++t) B.rbf[3 * j + t] = (float)(S.R[t][0] * b0 + S.R[t][1] * b1 + S.R[t][2] * b2);
+        } else {
+            const double b0 = B.b[3 * j], b1 = B.b[3 * j + 1], b2 = B.b[3 * j + 2];
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                const double r = S.R[t][0] * b0 + S.R[t][1] * b1 + S.R[t][2] * b2;
                 B.rb[3 * j + t] = r;
                 B.Xb[3 * j + t] = S.Xw[t] + r;
             }
@@ -328,7 +338,7 @@ __device__ __forceinline__ void warp_partials6(BodyShared &S, const long long ac
 }
 
 template <bool MIXED>
-__global__ void __launch_bounds__(MDB_NT, 1) k_md_body(Dev d, uint32_t step, int rbuf, int bbuf, int do_bin)
+__global__ void __launch_bounds__(MDB_NT, 2) k_md_body(Dev d, uint32_t step, int rbuf, int bbuf, int do_bin)
 {
     step = resolve_step(d, step);   // STEP_DEVICE: the step of the control block
     using W = typename std::conditional<MIXED, BWorkM, BWorkD>::type;
@@ -387,9 +397,11 @@ __global__ void __launch_bounds__(MDB_NT, 1) k_md_body(Dev d, uint32_t step, int
         w.slot = slot;
         if constexpr (MIXED) {
             RecM rec = load_rec(reinterpret_cast<const RecM *>(d.rec[rbuf]) + slot);
-            for (int t = 0; t < 3; ++t) { w.c[t] = cw_get(rec.cw, t); w.o[t] = rec.o[t]; w.v[t] = rec.v[t]; }
+            for (int t = 0; t < 3; ++t) { w.o[t] = rec.o[t]; w.v[t] = rec.v[t]; }
+            w.cw = rec.cw;
             w.fid = rec.fid;
-            body_force_m(rp, S, B, w.c, w.o, w.fid, w.f, acc);
+            const int c[3] = {cw_get(rec.cw, 0), cw_get(rec.cw, 1), cw_get(rec.cw, 2)};
+            body_force_m(rp, S, B, c, w.o, w.fid, w.f, acc);
         } else {
             RecD rec = load_rec(reinterpret_cast<const RecD *>(d.rec[rbuf]) + slot);
             for (int t = 0; t < 3; ++t) { w.x[t] = rec.x[t]; w.v[t] = rec.v[t]; }
@@ -424,7 +436,8 @@ __global__ void __launch_bounds__(MDB_NT, 1) k_md_body(Dev d, uint32_t step, int
                     w.v[t] = fmaf(hdtf, w.f[t], w.v[t]);
                     w.o[t] = fmaf(dtf, w.v[t], w.o[t]);
                 }
-                in = body_force_m(rp, S, B, w.c, w.o, w.fid, w.f, acc);
+                const int c[3] = {cw_get(w.cw, 0), cw_get(w.cw, 1), cw_get(w.cw, 2)};
+                in = body_force_m(rp, S, B, c, w.o, w.fid, w.f, acc);
             } else {
 #pragma unroll
                 for (int t = 0; t < 3; ++t) {
@@ -452,15 +465,16 @@ __global__ void __launch_bounds__(MDB_NT, 1) k_md_body(Dev d, uint32_t step, int
         W w = work[k];
         if constexpr (MIXED) {
             for (int t = 0; t < 3; ++t) w.v[t] = fmaf(rp.hdt_f, w.f[t], w.v[t]);
-            renorm_m(rp, w.c, w.o);
+            int c[3] = {cw_get(w.cw, 0), cw_get(w.cw, 1), cw_get(w.cw, 2)};
+            renorm_m(rp, c, w.o);
             RecM rec;
-            rec.cw = cw_make(w.c[0], w.c[1], w.c[2]);
+            rec.cw = cw_make(c[0], c[1], c[2]);
             for (int t = 0; t < 3; ++t) { rec.o[t] = w.o[t]; rec.v[t] = w.v[t]; }
             rec.fid = do_bin ? (w.fid | F_PROP) : (w.fid & ~F_PROP);
             store_rec(reinterpret_cast<RecM *>(d.rec[rbuf]) + w.slot, rec);
             if (do_bin) {
                 float sf[3] = {(float)sh[0], (float)sh[1], (float)sh[2]};
-                bin_particle(d, bbuf, rp.cell_off + cell_key_m(rp, w.c, w.o, sf), w.slot);
+                bin_particle(d, bbuf, rp.cell_off + cell_key_m(rp, c, w.o, sf), w.slot);
             }
         } else {
             for (int t = 0; t < 3; ++t) w.v[t] = fma(hdt, w.f[t], w.v[t]);
@@ -477,6 +491,7 @@ __global__ void __launch_bounds__(MDB_NT, 1) k_md_body(Dev d, uint32_t step, int
     if (tid == 0) {
         // body state, and its centre as the replica's near-list colloid
         BodyDev &bw = d.body[rp.body];
+        const int g = rp.col_off;
         double dd = 0.0;
         for (int k = 0; k < 3; ++k) {
             bw.X[k] = S.X[k]; bw.V[k] = S.V[k]; bw.l[k] = S.l[k];
@@ -484,18 +499,17 @@ __global__ void __launch_bounds__(MDB_NT, 1) k_md_body(Dev d, uint32_t step, int
             dd = dd + e * e;
         }
         for (int k = 0; k < 4; ++k) bw.q[k] = S.q[k];
-        if (!(dd <= rp.skin * rp.skin)) atomicAdd(&d.err[ERR_SKIN], 1u);
-        const int g = rp.col_off;
+        const bool bad = !(dd <= rp.skin * rp.skin);
         body_frames(rp, S);
         for (int k = 0; k < 3; ++k) {
             d.colX[3 * g + k] = S.X[k];
             d.colV[3 * g + k] = S.V[k];
-            const double fl = floor(S.X[k]);
-            d.colXi[3 * g + k] = (int)fl;
+            d.colXi[3 * g + k] = (int)floor(S.X[k]);
             d.colXf[3 * g + k] = S.Cf[k];
             d.colCi[3 * g + k] = S.Ci[k];
             d.colVf[3 * g + k] = (float)S.V[k];
         }
+        if (bad) atomicAdd(&d.err[ERR_SKIN], 1u);
         d.near_count[r] = 0;
     }
 }
