@@ -22,9 +22,12 @@
 // force pass.  Thread 0 integrates the body in FP64 on both paths: FP32
 // rounding of the orientation accumulates over the sub-steps into bead
 // positions that the steep bead potential turns into force errors well above
-// the mixed path's tolerance, and the body update is a small part of the
-// kernel's time.  After every turn the CTA recomputes the bead offsets R b_j
-// (FP64, rounded to FP32 on the mixed path) in shared memory.  A particle finds the
+// the mixed path's tolerance.  FP64 division is slow on this GPU, so the
+// mixed path's integrator has none on its sub-step chain (reciprocals of M
+// and I_k precomputed, Newton reciprocal and inverse square root from an
+// FP32 seed); the FP64 path keeps the FP64 definition's divisions.  After
+// every turn the CTA recomputes the bead offsets R b_j (FP64, rounded to FP32
+// on the mixed path) in shared memory.  A particle finds the
 // beads it can reach through a lookup grid in the body frame, built on the
 // host once per body: the grid cell of the particle's body-frame position
 // lists, in ascending order, every bead whose cut-off plus a margin reaches
@@ -41,15 +44,17 @@ namespace rmpcd {
 constexpr int MDB_NT = 512;
 constexpr int MDB_NW = MDB_NT / 32;
 
+// Mixed path work record: cell word, id|flags, FP32 offset and the
+// half-step velocity v + dt/2 f of the leapfrog form of velocity Verlet (the
+// same update; the record needs no force and the slot is re-read from the
+// near list at the end).
 struct __align__(16) BWorkM {
     uint32_t cw;
     uint32_t fid;
-    int slot;
     float o[3];
     float v[3];
-    float f[3];
 };
-static_assert(sizeof(BWorkM) == 48, "mixed MD work record is three 16-byte words");
+static_assert(sizeof(BWorkM) == 32, "mixed MD work record is two 16-byte words");
 struct __align__(16) BWorkD {
     double x[3];
     double v[3];
@@ -67,11 +72,14 @@ struct BodyShared {
     double Xw[3];
     double F[3], tb[3];
     double M, I[3], sigma, rc2;
+    // mixed path integrator constants: 1/M, 0.5 h_s / I_k of the five turns
+    double invM, ct[5];
     // both: rotation in FP32 (lookup grid, mixed forces), wrapped centre cell
     float Rf[3][3];
     float Cf[3];
     int Ci[3];
     float sigma_f, rc2_f, glo, ginv;
+    float reach2_f;                  // beyond this squared distance from the centre no bead is in range
     int gn, nb, nn;
     const int *gstart;
     const unsigned short *glist;
@@ -186,6 +194,91 @@ __device__ void body_kick_drift_rotate(BodyShared &S, double dt, double hdt)
     for (int i = 0; i < 3; ++i) S.l[i] = l[i];
 }
 
+// --- mixed path: the same integrator without divisions on the chain ---------
+// FP64 reciprocal of x in [1, 2): FP32 seed and two Newton steps (error far
+// below one FP64 ulp before the last rounding).
+__device__ __forceinline__ double rcp_nr(double x)
+{
+    double y = (double)__frcp_rn((float)x);
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
+
+// 1/sqrt(x) for x near 1: FP32 seed and two Newton steps.
+__device__ __forceinline__ double rsqrt_nr(double x)
+{
+    double y = (double)rsqrtf((float)x);
+    y = y * (1.5 - 0.5 * x * y * y);
+    return y * (1.5 - 0.5 * x * y * y);
+}
+
+__device__ void body_kick_fast(BodyShared &S, double hdt)
+{
+    for (int t = 0; t < 3; ++t) {
+        S.V[t] = fma(hdt, S.F[t] * S.invM, S.V[t]);
+        S.l[t] = fma(hdt, S.tb[t], S.l[t]);
+    }
+}
+
+__device__ void body_kick_drift_rotate_fast(BodyShared &S, double dt, double hdt)
+{
+    for (int t = 0; t < 3; ++t) {
+        S.V[t] = fma(hdt, S.F[t] * S.invM, S.V[t]);
+        S.l[t] = fma(hdt, S.tb[t], S.l[t]);
+        S.X[t] = fma(dt, S.V[t], S.X[t]);
+    }
+    double q[4] = {S.q[0], S.q[1], S.q[2], S.q[3]};
+    double l[3] = {S.l[0], S.l[1], S.l[2]};
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int k = (s == 2) ? 2 : (s == 1 || s == 3) ? 1 : 0;
+        const int a = (k + 1) % 3, b = (k + 2) % 3;
+        const double t = S.ct[s] * l[k];
+        const double tt = t * t;
+        const double inv = rcp_nr(1.0 + tt);
+        const double c = (1.0 - tt) * inv;
+        const double sn = (2.0 * t) * inv;
+        const double la = c * l[a] + sn * l[b];
+        const double lb = c * l[b] - sn * l[a];
+        l[a] = la;
+        l[b] = lb;
+        const double w = q[0], v0 = q[1 + k], va = q[1 + a], vb = q[1 + b];
+        q[0] = w - t * v0;
+        q[1 + k] = v0 + t * w;
+        q[1 + a] = va + t * vb;
+        q[1 + b] = vb - t * va;
+    }
+    const double g = rsqrt_nr(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    for (int i = 0; i < 4; ++i) S.q[i] = q[i] * g;
+    for (int i = 0; i < 3; ++i) S.l[i] = l[i];
+}
+
+// Frame of the mixed path: R, the wrapped centre's cell and FP32 offset.
+__device__ void body_frames_fast(const ReplicaDev &rp, BodyShared &S)
+{
+    const double w = S.q[0], x = S.q[1], y = S.q[2], z = S.q[3];
+    S.R[0][0] = 1.0 - 2.0 * (y * y + z * z);
+    S.R[0][1] = 2.0 * (x * y - w * z);
+    S.R[0][2] = 2.0 * (x * z + w * y);
+    S.R[1][0] = 2.0 * (x * y + w * z);
+    S.R[1][1] = 1.0 - 2.0 * (x * x + z * z);
+    S.R[1][2] = 2.0 * (y * z - w * x);
+    S.R[2][0] = 2.0 * (x * z - w * y);
+    S.R[2][1] = 2.0 * (y * z + w * x);
+    S.R[2][2] = 1.0 - 2.0 * (x * x + y * y);
+    for (int k = 0; k < 3; ++k) {
+        for (int t = 0; t < 3; ++t) S.Rf[k][t] = (float)S.R[k][t];
+        const double fl = floor(S.X[k]);
+        int c = (int)fl;
+        float o = (float)(S.X[k] - fl);
+        if (o >= 1.0f) { o = 0.0f; c += 1; }
+        S.Ci[k] = imod(c, rp.L[k]);
+        S.Cf[k] = o;
+    }
+}
+
 // Fixed-point totals of the warps -> F and the body-frame torque R^T T.
 __device__ void body_totals(BodyShared &S)
 {
@@ -221,9 +314,14 @@ __device__ void bead_frames(BodyShared &S, const BeadSmem &B)
     }
 }
 
-// Lookup-grid range of a body-frame position u: [beg, end) in the list.
+// Lookup-grid range of a body-frame position u: [beg, end) in the list.  A
+// particle farther from the centre than the reach (max |b| + cut-off, plus a
+// margin far above the FP32 rounding of dc) has no bead in range and skips
+// the lookup.
 __device__ __forceinline__ void grid_range(const BodyShared &S, const float dc[3], int &beg, int &end)
 {
+    beg = end = 0;
+    if (!(dc[0] * dc[0] + dc[1] * dc[1] + dc[2] * dc[2] < S.reach2_f)) return;
     int id[3];
     bool in = true;
 #pragma unroll
@@ -233,7 +331,6 @@ __device__ __forceinline__ void grid_range(const BodyShared &S, const float dc[3
         in = in && g >= 0.0f && g < (float)S.gn;
         id[k] = (int)g;
     }
-    beg = end = 0;
     if (in) {
         const int cell = id[0] + S.gn * (id[1] + S.gn * id[2]);
         beg = __ldg(S.gstart + cell);
@@ -265,8 +362,10 @@ __device__ __forceinline__ bool body_force_m(const ReplicaDev &rp, const BodySha
     f[0] = f[1] = f[2] = 0.0f;
     bool inside = false;
     const int isb = (fid & F_B) ? 1 : 0;
+    int jn = beg < end ? __ldg(S.glist + beg) : 0;
     for (int e = beg; e < end; ++e) {
-        const int j = __ldg(S.glist + e);
+        const int j = jn;
+        if (e + 1 < end) jn = __ldg(S.glist + e + 1);   // next index in flight during this pair
         const float rb[3] = {B.rbf[3 * j], B.rbf[3 * j + 1], B.rbf[3 * j + 2]};
         const float d[3] = {dc[0] - rb[0], dc[1] - rb[1], dc[2] - rb[2]};
         const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -296,8 +395,10 @@ __device__ __forceinline__ bool body_force_d(const ReplicaDev &rp, const BodySha
     f[0] = f[1] = f[2] = 0.0;
     bool inside = false;
     const int isb = (fid & F_B) ? 1 : 0;
+    int jn = beg < end ? __ldg(S.glist + beg) : 0;
     for (int e = beg; e < end; ++e) {
-        const int j = __ldg(S.glist + e);
+        const int j = jn;
+        if (e + 1 < end) jn = __ldg(S.glist + e + 1);
         double d[3] = {x[0] - B.Xb[3 * j], x[1] - B.Xb[3 * j + 1], x[2] - B.Xb[3 * j + 2]};
         min_image(rp, d);
         const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -337,6 +438,38 @@ __device__ __forceinline__ void warp_partials6(BodyShared &S, const long long ac
     }
 }
 
+// Mixed path, one sub-step of one near particle: drift by the half-step
+// velocity, force, catalysis, then the kick to the next half step (or, at
+// the last sub-step, to the full step).
+__device__ __forceinline__ void substep_m(const ReplicaDev &rp, const BodyShared &S, const BeadSmem &B, BWorkM &w,
+                                          long long acc[6], uint32_t step, int s, bool last)
+{
+#pragma unroll
+    for (int t = 0; t < 3; ++t) w.o[t] = fmaf(rp.dt_f, w.v[t], w.o[t]);
+    const int c[3] = {cw_get(w.cw, 0), cw_get(w.cw, 1), cw_get(w.cw, 2)};
+    float f[3];
+    const bool in = body_force_m(rp, S, B, c, w.o, w.fid, f, acc);
+    w.fid = catalysis(rp, w.fid, in, step, s);
+    const float h = last ? rp.hdt_f : rp.dt_f;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) w.v[t] = fmaf(h, f[t], w.v[t]);
+}
+
+// Mixed path: write one particle back after the interval (and bin it for the
+// collision of `step`).
+__device__ __forceinline__ void finish_m(const Dev &d, const ReplicaDev &rp, int rbuf, int bbuf, int do_bin,
+                                         const float sf[3], BWorkM &w, int slot)
+{
+    int c[3] = {cw_get(w.cw, 0), cw_get(w.cw, 1), cw_get(w.cw, 2)};
+    renorm_m(rp, c, w.o);
+    RecM rec;
+    rec.cw = cw_make(c[0], c[1], c[2]);
+    for (int t = 0; t < 3; ++t) { rec.o[t] = w.o[t]; rec.v[t] = w.v[t]; }
+    rec.fid = do_bin ? (w.fid | F_PROP) : (w.fid & ~F_PROP);
+    store_rec(reinterpret_cast<RecM *>(d.rec[rbuf]) + slot, rec);
+    if (do_bin) bin_particle(d, bbuf, rp.cell_off + cell_key_m(rp, c, w.o, sf), slot);
+}
+
 template <bool MIXED>
 __global__ void __launch_bounds__(MDB_NT, 2) k_md_body(Dev d, uint32_t step, int rbuf, int bbuf, int do_bin)
 {
@@ -357,13 +490,20 @@ __global__ void __launch_bounds__(MDB_NT, 2) k_md_body(Dev d, uint32_t step, int
             S.X[k] = bd.X[k]; S.V[k] = bd.V[k]; S.l[k] = bd.l[k]; S.X0[k] = bd.X[k]; S.I[k] = bd.I[k];
         }
         for (int k = 0; k < 4; ++k) S.q[k] = bd.q[k];
+        S.invM = 1.0 / bd.M;
+        for (int s = 0; s < 5; ++s) {
+            const int k = (s == 2) ? 2 : (s == 1 || s == 3) ? 1 : 0;
+            S.ct[s] = 0.5 * ((s == 2) ? rp.dt : 0.5 * rp.dt) / bd.I[k];
+        }
         S.M = bd.M; S.sigma = bd.sigma; S.rc2 = bd.rc2;
         S.sigma_f = bd.sigma_f; S.rc2_f = bd.rc2_f; S.glo = bd.glo; S.ginv = bd.ginv;
         S.gn = bd.gn; S.nb = bd.nb;
+        S.reach2_f = (float)((bd.reach + 1e-3) * (bd.reach + 1e-3) * (1.0 + 1e-4));
         S.gstart = d.grid_start + bd.gstart_off;
         S.glist = d.grid_list + bd.glist_off;
         S.nn = min(d.near_count[r], rp.n_part);
-        body_frames(rp, S);
+        if (MIXED) body_frames_fast(rp, S);
+        else body_frames(rp, S);
     }
     __syncthreads();
     const int nb = S.nb, nn = S.nn;
@@ -394,15 +534,16 @@ __global__ void __launch_bounds__(MDB_NT, 2) k_md_body(Dev d, uint32_t step, int
     for (int k = tid; k < nn; k += MDB_NT) {
         W w;
         const int slot = list[k];
-        w.slot = slot;
         if constexpr (MIXED) {
             RecM rec = load_rec(reinterpret_cast<const RecM *>(d.rec[rbuf]) + slot);
-            for (int t = 0; t < 3; ++t) { w.o[t] = rec.o[t]; w.v[t] = rec.v[t]; }
             w.cw = rec.cw;
             w.fid = rec.fid;
             const int c[3] = {cw_get(rec.cw, 0), cw_get(rec.cw, 1), cw_get(rec.cw, 2)};
-            body_force_m(rp, S, B, c, w.o, w.fid, w.f, acc);
+            float f[3];
+            body_force_m(rp, S, B, c, rec.o, w.fid, f, acc);
+            for (int t = 0; t < 3; ++t) { w.o[t] = rec.o[t]; w.v[t] = fmaf(rp.hdt_f, f[t], rec.v[t]); }
         } else {
+            w.slot = slot;
             RecD rec = load_rec(reinterpret_cast<const RecD *>(d.rec[rbuf]) + slot);
             for (int t = 0; t < 3; ++t) { w.x[t] = rec.x[t]; w.v[t] = rec.v[t]; }
             w.fid = rec.fid;
@@ -415,68 +556,70 @@ __global__ void __launch_bounds__(MDB_NT, 2) k_md_body(Dev d, uint32_t step, int
     if (tid == 0) body_totals(S);
 
     const double dt = rp.dt, hdt = rp.hdt;
+    double sh[3];
+    grid_shift(rp.seed, step, sh);
+    const float sf[3] = {(float)sh[0], (float)sh[1], (float)sh[2]};
     for (int s = 0; s < rp.n_md; ++s) {
         if (tid == 0) {
-            body_kick_drift_rotate(S, dt, hdt);
-            body_frames(rp, S);
+            if (MIXED) {
+                body_kick_drift_rotate_fast(S, dt, hdt);
+                body_frames_fast(rp, S);
+            } else {
+                body_kick_drift_rotate(S, dt, hdt);
+                body_frames(rp, S);
+            }
         }
         __syncthreads();
         bead_frames<MIXED>(S, B);
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 6; ++i) acc[i] = 0;
-        for (int k = tid; k < nn; k += MDB_NT) {
-            W w = work[k];
-            bool in;
-            if constexpr (MIXED) {
-                const float hdtf = rp.hdt_f, dtf = rp.dt_f;
-#pragma unroll
-                for (int t = 0; t < 3; ++t) {
-                    if (s > 0) w.v[t] = fmaf(hdtf, w.f[t], w.v[t]);
-                    w.v[t] = fmaf(hdtf, w.f[t], w.v[t]);
-                    w.o[t] = fmaf(dtf, w.v[t], w.o[t]);
+        if constexpr (MIXED) {
+            // two particles per iteration: both records are loaded before either is used
+            const bool last = s + 1 == rp.n_md;
+            for (int k = tid; k < nn; k += 2 * MDB_NT) {
+                const int k1 = k + MDB_NT;
+                const bool two = k1 < nn;
+                BWorkM w0 = work[k];
+                BWorkM w1 = two ? work[k1] : w0;
+                substep_m(rp, S, B, w0, acc, step, s, last);
+                if (two) substep_m(rp, S, B, w1, acc, step, s, last);
+                if (!last) {
+                    work[k] = w0;
+                    if (two) work[k1] = w1;
+                } else {
+                    finish_m(d, rp, rbuf, bbuf, do_bin, sf, w0, list[k]);
+                    if (two) finish_m(d, rp, rbuf, bbuf, do_bin, sf, w1, list[k1]);
                 }
-                const int c[3] = {cw_get(w.cw, 0), cw_get(w.cw, 1), cw_get(w.cw, 2)};
-                in = body_force_m(rp, S, B, c, w.o, w.fid, w.f, acc);
-            } else {
+            }
+        } else {
+            for (int k = tid; k < nn; k += MDB_NT) {
+                W w = work[k];
 #pragma unroll
                 for (int t = 0; t < 3; ++t) {
                     if (s > 0) w.v[t] = fma(hdt, w.f[t], w.v[t]);
                     w.v[t] = fma(hdt, w.f[t], w.v[t]);
                     w.x[t] = fma(dt, w.v[t], w.x[t]);
                 }
-                in = body_force_d(rp, S, B, w.x, w.fid, w.f, acc);
+                const bool in = body_force_d(rp, S, B, w.x, w.fid, w.f, acc);
+                w.fid = catalysis(rp, w.fid, in, step, s);
+                work[k] = w;
             }
-            w.fid = catalysis(rp, w.fid, in, step, s);
-            work[k] = w;
         }
         warp_partials6(S, acc);
         __syncthreads();
         if (tid == 0) {
             body_totals(S);
-            body_kick(S, hdt);
+            if (MIXED) body_kick_fast(S, hdt);
+            else body_kick(S, hdt);
         }
     }
 
-    // last half kick, wrap, write back (and bin for the collision of `step`)
-    double sh[3];
-    grid_shift(rp.seed, step, sh);
-    for (int k = tid; k < nn; k += MDB_NT) {
-        W w = work[k];
-        if constexpr (MIXED) {
-            for (int t = 0; t < 3; ++t) w.v[t] = fmaf(rp.hdt_f, w.f[t], w.v[t]);
-            int c[3] = {cw_get(w.cw, 0), cw_get(w.cw, 1), cw_get(w.cw, 2)};
-            renorm_m(rp, c, w.o);
-            RecM rec;
-            rec.cw = cw_make(c[0], c[1], c[2]);
-            for (int t = 0; t < 3; ++t) { rec.o[t] = w.o[t]; rec.v[t] = w.v[t]; }
-            rec.fid = do_bin ? (w.fid | F_PROP) : (w.fid & ~F_PROP);
-            store_rec(reinterpret_cast<RecM *>(d.rec[rbuf]) + w.slot, rec);
-            if (do_bin) {
-                float sf[3] = {(float)sh[0], (float)sh[1], (float)sh[2]};
-                bin_particle(d, bbuf, rp.cell_off + cell_key_m(rp, c, w.o, sf), w.slot);
-            }
-        } else {
+    // FP64 path: last half kick, wrap, write back (and bin for the collision
+    // of `step`); the mixed path did this in its last sub-step
+    if constexpr (!MIXED) {
+        for (int k = tid; k < nn; k += MDB_NT) {
+            W w = work[k];
             for (int t = 0; t < 3; ++t) w.v[t] = fma(hdt, w.f[t], w.v[t]);
             wrap_periodic_d(rp, w.x);
             RecD rec;
@@ -500,7 +643,8 @@ __global__ void __launch_bounds__(MDB_NT, 2) k_md_body(Dev d, uint32_t step, int
         }
         for (int k = 0; k < 4; ++k) bw.q[k] = S.q[k];
         const bool bad = !(dd <= rp.skin * rp.skin);
-        body_frames(rp, S);
+        if (MIXED) body_frames_fast(rp, S);
+        else body_frames(rp, S);
         for (int k = 0; k < 3; ++k) {
             d.colX[3 * g + k] = S.X[k];
             d.colV[3 * g + k] = S.V[k];
