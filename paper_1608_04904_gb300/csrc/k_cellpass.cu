@@ -133,13 +133,15 @@ __device__ __forceinline__ void cells_D_serial(const Dev &d, const CellPassArgs 
     const ReplicaDev &rp = T.rp;
     const int lc0 = T.tile * CPT - rp.cell_off;
     const int opts = a.opts;
+    const bool want_near = MIXED && (opts & CP_NEXT) && rp.n_col > 0;
     for (int c = cb + gt; c < ce; c += G) {
         const int n = T.cnt[c];
         const int lo = T.ls[c] - pofs;
         const int lc = lc0 + c;
         T.mode[c] = 0;
         T.react[c] = -1;
-        T.mnear[c] = 1;
+        T.mnear[c] = MIXED ? 0 : 1;
+        int slab = -1;
         if ((opts & CP_COLLIDE) && n >= 2) {
             R sum[3] = {R(0), R(0), R(0)};
             for (int i = 0; i < n; ++i)
@@ -161,7 +163,6 @@ __device__ __forceinline__ void cells_D_serial(const Dev &d, const CellPassArgs 
             } else {
                 for (int k = 0; k < 3; ++k) vcm[k] = sum[k] / (R)n;
             }
-            int slab = -1;
             for (int k = 0; k < rp.n_slabs; ++k)
                 if (cx >= rp.slab_lo[k] && cx < rp.slab_hi[k]) { slab = k; break; }
             if (slab >= 0) {
@@ -190,6 +191,39 @@ __device__ __forceinline__ void cells_D_serial(const Dev &d, const CellPassArgs 
                 for (int k = 0; k < 3; ++k) { T.vcm[c][k] = vcm[k]; T.ax[c][k] = ax[k]; }
                 T.mode[c] = 1;
             }
+        }
+        if (want_near && n > 0) {
+            // can a particle of the cell come near a colloid in the next
+            // interval?  Its post-collision speed is at most |v_cm| + max
+            // |v - v_cm| (the rotation keeps |v - v_cm|) and it lies within
+            // sqrt(3)/2 of the cell centre on this step's grid
+            int mn = 1;
+            if (slab < 0) {
+                R s3[3] = {R(0), R(0), R(0)};
+                for (int i = 0; i < n; ++i)
+                    for (int k = 0; k < 3; ++k) s3[k] = s3[k] + srec[lo + i].v[k];
+                const R inv = R(1) / (R)n;
+                const R vc[3] = {s3[0] * inv, s3[1] * inv, s3[2] * inv};
+                R u2 = R(0);
+                for (int i = 0; i < n; ++i) {
+                    const R a0 = srec[lo + i].v[0] - vc[0], a1 = srec[lo + i].v[1] - vc[1],
+                            a2 = srec[lo + i].v[2] - vc[2];
+                    u2 = max(u2, a0 * a0 + a1 * a1 + a2 * a2);
+                }
+                const float vb = (float)(sqrt(vc[0] * vc[0] + vc[1] * vc[1] + vc[2] * vc[2]) + sqrt(u2));
+                const int t = lc / rp.L[0];
+                const int kc[3] = {lc % rp.L[0], t % rp.L[1], rp.walls ? t / rp.L[1] - 1 : t / rp.L[1]};
+                mn = 0;
+                for (int j = 0; j < rp.n_col && !mn; ++j) {
+                    float dd[3];
+                    for (int k = 0; k < 3; ++k)
+                        dd[k] = (float)(kc[k] - T.nf.Ci[3 * j + k]) + ((0.5f + T.shf[k]) - T.nf.Cf[3 * j + k]);
+                    min_image(rp, dd);
+                    const float dist = sqrtf(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+                    if (dist - 0.8661f < T.nf.Rb[j] + vb * rp.tau_f + 1e-3f) mn = 1;
+                }
+            }
+            T.mnear[c] = mn;
         }
         if ((opts & CP_REACT) && rp.bulk_on && n > 0) {
             int nbB = 0;
@@ -454,7 +488,17 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
     else cells_D_serial<MIXED, G>(d, a, T, gt, cb, ce, pofs, srec);
     group_sync<G>();
     if (!have_base) {
-        base_wait();   // stages A-D do not need the tile base; E does
+        // stages A-D do not need the tile base; E does
+        if constexpr (G == 32) {
+            base_wait();
+        } else {
+            // the aggregate went out in the prologue; warp 0 scans back now
+            if (gt < 32) {
+                const int base = tile_lookback(d, T.epoch, T.tile, T.ls[CPT], gt, false);
+                if (gt == 0) T.base = base;
+            }
+            __syncthreads();
+        }
         have_base = true;
     }
     // E: apply, write, classify for the next collision (the next cell of a
@@ -656,13 +700,19 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
 
     // tile base by decoupled look-back: warp 0 inspects 32 predecessor tiles
     // at a time, sums aggregates back to the nearest inclusive prefix.  On the
-    // warp path the other warps start on their cells meanwhile.
-    const bool warp_path = T.maxcnt <= WPC;
-    if (tid < 32) {
-        const int base = tile_lookback(d, T.epoch, tile, T.ls[CPT], lane);
-        if (lane == 0) T.base = base;
-        __syncwarp();
-        if (warp_path) base_arrive();
+    // warp path warp 0 does it now and the other warps start on their cells
+    // meanwhile; on the CTA path the tile's aggregate is published now and the
+    // scan waits until the first batch needs the base (before stage E).
+    const bool warp_path = false;
+    if (warp_path) {
+        if (tid < 32) {
+            const int base = tile_lookback(d, T.epoch, tile, T.ls[CPT], lane);
+            if (lane == 0) T.base = base;
+            __syncwarp();
+            base_arrive();
+        }
+    } else if (tid == 0) {
+        tile_publish(d, T.epoch, tile, T.ls[CPT]);
     }
 
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // T sum, cells, px, py, pz, ke, nB, n
@@ -694,9 +744,8 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
         }
         if (!have_base) base_wait();   // a warp that took no chunk still meets the barrier once
     } else {
-        // a crowded tile: the whole CTA as one group
-        __syncthreads();
-        bool have_base = true;
+        // the whole CTA as one group
+        bool have_base = false;
         for (int cb = 0; cb < CPT;) {
             const int ce = batch_end(T.ls, cb, CPT, TP);
             cells_batch<MIXED, CP_THREADS>(d, a, T, tid, cb, ce, srec, ent, srt, cellof, acc, have_base);

@@ -644,9 +644,10 @@ __device__ __forceinline__ void st_release(unsigned long long *p, unsigned long 
 
 // ---------------------------------------------------------------------------
 // Tile base by decoupled look-back (Merrill & Garland 2016), run by one full
-// warp: publishes the tile's aggregate, inspects 32 predecessor tiles at a
-// time summing aggregates back to the nearest inclusive prefix, publishes the
-// tile's inclusive prefix and returns its exclusive prefix (in every lane).
+// warp: publishes the tile's aggregate (unless the caller already did, by
+// tile_publish), inspects 32 predecessor tiles at a time summing aggregates
+// back to the nearest inclusive prefix, publishes the tile's inclusive prefix
+// and returns its exclusive prefix (in every lane).
 // Tiles are taken in ticket order, so every predecessor has started.  Words
 // carry a 16-bit tag of the launch (never 0, the initial state), a 2-bit flag
 // (1 aggregate, 2 inclusive prefix) and a 46-bit value.  A wait that runs out
@@ -655,10 +656,17 @@ __device__ __forceinline__ void st_release(unsigned long long *p, unsigned long 
 constexpr unsigned long long LB_VALUE_MASK = (1ull << 46) - 1ull;
 constexpr int LB_SPIN_LIMIT = 1 << 22;
 
-__device__ __forceinline__ int tile_lookback(const Dev &d, uint32_t epoch, int tile, int total, int lane)
+__device__ __forceinline__ void tile_publish(const Dev &d, uint32_t epoch, int tile, int total)
 {
     const unsigned long long ep = (unsigned long long)(epoch % 65535u) + 1ull;
-    if (lane == 0) st_release(&d.tile_state[tile], (ep << 48) | (1ull << 46) | (unsigned long long)total);
+    st_release(&d.tile_state[tile], (ep << 48) | (1ull << 46) | (unsigned long long)total);
+}
+
+__device__ __forceinline__ int tile_lookback(const Dev &d, uint32_t epoch, int tile, int total, int lane,
+                                             bool publish = true)
+{
+    const unsigned long long ep = (unsigned long long)(epoch % 65535u) + 1ull;
+    if (publish && lane == 0) tile_publish(d, epoch, tile, total);
     unsigned long long prefix = 0;
     int t = tile - 1;
     int spins = 0;
