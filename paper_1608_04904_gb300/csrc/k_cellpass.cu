@@ -11,10 +11,13 @@
 // particle counts, found by a single-pass decoupled look-back (Merrill &
 // Garland 2016) over tiles taken in ticket order.
 //
-// After the tile base is known each warp handles CPT / CP_WARPS cells on its
-// own (warp-synchronous, no CTA barrier), so the warps' memory traffic
-// overlaps freely.  A tile with a cell too crowded for one warp's staging
-// area runs the same stages with the whole CTA as one group instead.
+// The CTA stages the tile's particles (in batches of whole cells when they
+// exceed the staging area) and runs the stages with all its threads: one
+// thread per particle for the gather, rotation, write and binning, one thread
+// per cell for the cell sums and the per-cell draws.  The tile's aggregate is
+// published at once and the look-back scan runs only when the first batch
+// needs the base (before its writes), so the gather and the per-cell work of
+// a tile overlap the wait for its predecessors.
 //
 // Per particle this reads its bucket entry (4 B) and its record (32 B mixed /
 // 64 B fp64) and writes its record and its next bucket entry: one pass over
@@ -27,14 +30,14 @@ template <bool MIXED> struct Traits;
 template <> struct Traits<true> {
     using Rec = RecM;
     using R = float;
-    static constexpr int WPC = CP_WPC_M;
-    static constexpr int TP = CP_WARPS * WPC;
+    static constexpr int K = CP_STAGE_M;        // staged particles per thread
+    static constexpr int TP = K * CP_THREADS;
 };
 template <> struct Traits<false> {
     using Rec = RecD;
     using R = double;
-    static constexpr int WPC = CP_WPC_D;
-    static constexpr int TP = CP_WARPS * WPC;
+    static constexpr int K = CP_STAGE_D;
+    static constexpr int TP = K * CP_THREADS;
 };
 
 // --- per-record helpers ----------------------------------------------------
@@ -101,7 +104,6 @@ struct TileShared {
     NearFrames nf;
     int tile, r, base, maxcnt;
     uint32_t epoch, step;     // this launch's counter and collision index (from the control block)
-    int next;   // first cell of the next chunk a warp may take
     int cnt[CPT], ls[CPT + 1], wt[CPT / 32];
     double sh[3], shn[3];     // fp64 path
     float shf[3], shnf[3];
@@ -111,22 +113,10 @@ struct TileShared {
     double red[CP_WARPS][8];
 };
 
-// Named barrier 1 hands the tile base from warp 0 (bar.arrive, once) to the
-// other warps (bar.sync, once each) without stopping warp 0.
-__device__ __forceinline__ void base_arrive() { asm volatile("bar.arrive 1, %0;" ::"n"(CP_THREADS) : "memory"); }
-__device__ __forceinline__ void base_wait() { asm volatile("bar.sync 1, %0;" ::"n"(CP_THREADS) : "memory"); }
-
-template <int G>
-__device__ __forceinline__ void group_sync()
-{
-    if (G == 32) __syncwarp();
-    else __syncthreads();
-}
-
 // Stage D, one thread per cell, particles summed in sorted order (the same
 // order as the FP64 oracle).
-template <bool MIXED, int G>
-__device__ __forceinline__ void cells_D_serial(const Dev &d, const CellPassArgs &a, TileShared<MIXED> &T, int gt,
+template <bool MIXED>
+__device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, TileShared<MIXED> &T, int gt,
                                                int cb, int ce, int pofs, typename Traits<MIXED>::Rec *srec)
 {
     using R = typename Traits<MIXED>::R;
@@ -134,7 +124,7 @@ __device__ __forceinline__ void cells_D_serial(const Dev &d, const CellPassArgs 
     const int lc0 = T.tile * CPT - rp.cell_off;
     const int opts = a.opts;
     const bool want_near = MIXED && (opts & CP_NEXT) && rp.n_col > 0;
-    for (int c = cb + gt; c < ce; c += G) {
+    for (int c = cb + gt; c < ce; c += CP_THREADS) {
         const int n = T.cnt[c];
         const int lo = T.ls[c] - pofs;
         const int lc = lc0 + c;
@@ -244,170 +234,19 @@ __device__ __forceinline__ void cells_D_serial(const Dev &d, const CellPassArgs 
     }
 }
 
-// Stage D of the mixed path for a warp: four lanes per cell.  Sums, the
-// bound on post-collision speeds and the species count are split over the
-// lanes and combined by shuffles; lane 0 of the cell draws the rotation axis
-// (or runs MPC-AT), lane 1 the bulk reaction, lane 3 tests whether any
-// particle of the cell can come near a colloid during the next interval.
-__device__ __forceinline__ void cells_D_warp8(const Dev &d, const CellPassArgs &a, TileShared<true> &T, int lane,
-                                              int cb, int ce, int pofs, RecM *srec)
-{
-    const ReplicaDev &rp = T.rp;
-    const int lc0 = T.tile * CPT - rp.cell_off;
-    const int opts = a.opts;
-    const int q = lane & 3;
-    const int c = cb + (lane >> 2);
-    const bool cv = c < ce;
-    const int n = cv ? T.cnt[c] : 0;
-    const int lo = cv ? T.ls[c] - pofs : 0;
-    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
-    int nB = 0;
-    for (int i = q; i < n; i += 4) {
-        const RecM &r = srec[lo + i];
-        s0 += r.v[0]; s1 += r.v[1]; s2 += r.v[2];
-        nB += (r.fid & F_B) ? 1 : 0;
-    }
-#pragma unroll
-    for (int o = 1; o < 4; o <<= 1) {
-        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-        nB += __shfl_xor_sync(0xffffffffu, nB, o);
-    }
-    const int lc = lc0 + c;
-    int cx = 0, cy = 0, cz = 0;
-    if (cv) {
-        cx = lc % rp.L[0];
-        const int t = lc / rp.L[0];
-        cy = t % rp.L[1];
-        cz = t / rp.L[1];
-    }
-    const bool collide = cv && (opts & CP_COLLIDE) && n >= 2;
-    float vcm[3] = {0.0f, 0.0f, 0.0f};
-    if (n > 0) {
-        const bool wall_cell = rp.walls && (cz == 0 || cz == rp.nz - 1);
-        if (collide && wall_cell && n < rp.rho_wall) {
-            // virtual particles fill the wall cell up to rho_wall (§1.4)
-            const int nv = rp.rho_wall - n;
-            U4 w = philox((uint32_t)lc, a.step, P_VIRT, 0u, rp.seed);
-            float g0, g1, g2, g3;
-            box_muller(w.x, w.y, g0, g1);
-            box_muller(w.z, w.w, g2, g3);
-            const float sd = sqrtf((float)nv * (float)rp.kT);
-            vcm[0] = (s0 + sd * g0) / (float)(n + nv);
-            vcm[1] = (s1 + sd * g1) / (float)(n + nv);
-            vcm[2] = (s2 + sd * g2) / (float)(n + nv);
-        } else {
-            const float inv = __frcp_rn((float)n);
-            vcm[0] = s0 * inv; vcm[1] = s1 * inv; vcm[2] = s2 * inv;
-        }
-    }
-    int slab = -1;
-    if (collide)
-        for (int k = 0; k < rp.n_slabs; ++k)
-            if (cx >= rp.slab_lo[k] && cx < rp.slab_hi[k]) { slab = k; break; }
-    // bound on the post-collision speeds of the cell: |v'| <= |v_cm| + max |v - v_cm|
-    float u2 = 0.0f;
-    const bool want_near = cv && (opts & CP_NEXT) && rp.n_col > 0;
-    if (want_near)
-        for (int i = q; i < n; i += 4) {
-            const RecM &r = srec[lo + i];
-            const float a0 = r.v[0] - vcm[0], a1 = r.v[1] - vcm[1], a2 = r.v[2] - vcm[2];
-            u2 = fmaxf(u2, a0 * a0 + a1 * a1 + a2 * a2);
-        }
-#pragma unroll
-    for (int o = 1; o < 4; o <<= 1) u2 = fmaxf(u2, __shfl_xor_sync(0xffffffffu, u2, o));
-    // lanes 0 and 1 of a cell draw together: the first rotation-axis attempt
-    // and the bulk-reaction draw (one Philox evaluation for both)
-    U4 w0 = {0u, 0u, 0u, 0u};
-    if (q < 2 && (q == 0 ? collide : ((opts & CP_REACT) && rp.bulk_on && nB > 0)))
-        w0 = philox((uint32_t)lc, a.step, q == 0 ? P_ROT : P_REACT, 0u, rp.seed);
-    if (!cv) return;
-    if (q == 0) {
-        T.mode[c] = 0;
-        if (collide && slab >= 0) {
-            // Anderson thermostat (MPC-AT): fresh relative velocities
-            const float sd = rp.slab_sd_f[slab];
-            float xs[3] = {0.0f, 0.0f, 0.0f};
-            for (int i = 0; i < n; ++i) {
-                U4 w = philox((uint32_t)lc, a.step, P_THERMO, (uint32_t)i, rp.seed);
-                float g0, g1, g2, g3;
-                box_muller(w.x, w.y, g0, g1);
-                box_muller(w.z, w.w, g2, g3);
-                const float gg[3] = {g0, g1, g2};
-                for (int k = 0; k < 3; ++k) {
-                    const float xi = sd * gg[k];
-                    srec[lo + i].v[k] = xi;
-                    xs[k] = xs[k] + xi;
-                }
-            }
-            for (int k = 0; k < 3; ++k) xs[k] = xs[k] / (float)n;
-            for (int i = 0; i < n; ++i)
-                for (int k = 0; k < 3; ++k) srec[lo + i].v[k] = vcm[k] + (srec[lo + i].v[k] - xs[k]);
-            T.mode[c] = 2;
-        } else if (collide) {
-            float ax[3];
-            rotation_axis_from<float>(rp.seed, a.step, (uint32_t)lc, w0, ax);
-            for (int k = 0; k < 3; ++k) { T.vcm[c][k] = vcm[k]; T.ax[c][k] = ax[k]; }
-            T.mode[c] = 1;
-        }
-    } else if (q == 1) {
-        T.react[c] = -1;
-        if ((opts & CP_REACT) && rp.bulk_on && nB > 0) {
-            const U4 &w = w0;
-            if ((unsigned long long)w.x < d.bulk_thr[rp.thr_off + nB]) {
-                const int pick = (int)(((unsigned long long)w.y * (unsigned long long)nB) >> 32);
-                for (int i = 0, seen = 0; i < n; ++i) {
-                    if (srec[lo + i].fid & F_B) {
-                        if (seen == pick) { T.react[c] = lo + i; break; }
-                        ++seen;
-                    }
-                }
-            }
-        }
-    } else if (q == 3) {
-        int mn = 1;
-        if (want_near && slab < 0) {
-            // the cell's particles lie within sqrt(3)/2 of its centre on this
-            // step's grid; compare with every colloid's near radius bound
-            const float vb = sqrtf(vcm[0] * vcm[0] + vcm[1] * vcm[1] + vcm[2] * vcm[2]) + sqrtf(u2);
-            const int kc[3] = {cx, cy, rp.walls ? cz - 1 : cz};
-            mn = 0;
-            for (int j = 0; j < rp.n_col && !mn; ++j) {
-                float dd[3];
-                for (int k = 0; k < 3; ++k)
-                    dd[k] = (float)(kc[k] - T.nf.Ci[3 * j + k]) + ((0.5f + T.shf[k]) - T.nf.Cf[3 * j + k]);
-                min_image(rp, dd);
-                const float dist = sqrtf(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
-                if (dist - 0.8661f < T.nf.Rb[j] + vb * rp.tau_f + 1e-3f) mn = 1;
-            }
-        } else if (!want_near) {
-            mn = 0;
-        }
-        T.mnear[c] = mn;
-    }
-}
-
-// Stage D of the mixed path for a warp, eight cells at a time.
-__device__ __forceinline__ void cells_D_warp(const Dev &d, const CellPassArgs &a, TileShared<true> &T, int lane,
-                                             int cb, int ce, int pofs, RecM *srec)
-{
-    for (int c8 = cb; c8 < ce; c8 += 8) cells_D_warp8(d, a, T, lane, c8, ce, pofs, srec);
-}
-
-// The stages of the cell pass for the cells [cb, ce) of the tile, run by a
-// group of G threads (one warp, or the whole CTA), gt = thread index in the
-// group.  srec/ent/srt/cellof are the group's staging arrays (>= the batch).
-template <bool MIXED, int G>
+// The stages of the cell pass for the cells [cb, ce) of the tile, run by the
+// whole CTA (gt = thread index).  srec/ent/cellof are the staging arrays
+// (>= the batch).
+template <bool MIXED>
 __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXED> &T, int gt, int cb, int ce,
-                            typename Traits<MIXED>::Rec *srec, int *ent, int *srt, unsigned char *cellof,
-                            double acc[8], bool &have_base)
+                            typename Traits<MIXED>::Rec *srec, int *ent, unsigned char *cellof, double acc[8],
+                            bool &have_base)
 {
     using Rec = typename Traits<MIXED>::Rec;
     using R = typename Traits<MIXED>::R;
+    constexpr int G = CP_THREADS;
     const ReplicaDev &rp = T.rp;
     const int gc0 = T.tile * CPT;
-    const int lc0 = gc0 - rp.cell_off;
     const int pofs = T.ls[cb];
     const int nb = T.ls[ce] - pofs;
     const int part_lo = rp.part_off, part_hi = rp.part_off + rp.n_part;
@@ -422,17 +261,16 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
     const float shnf[3] = {T.shnf[0], T.shnf[1], T.shnf[2]};
 
     // Every thread owns at most K particles of a batch; the global loads and
-    // atomics of a stage are issued for all K before any result is used, so a
-    // thread waits for one memory round trip per stage, not one per particle.
-    constexpr int K = Traits<MIXED>::WPC / 32;
-    static_assert(Traits<MIXED>::TP == K * CP_THREADS, "batch size per thread");
+    // atomics of a stage are issued for all of them before any result is
+    // used, so a thread waits for one memory round trip per stage.
+    constexpr int K = Traits<MIXED>::K;
 
     // A: the cell of every staged particle, then its bucket entry
     for (int c = cb + gt; c < ce; c += G) {
         const int lo = T.ls[c] - pofs, n = T.cnt[c];
         for (int i = 0; i < n; ++i) cellof[lo + i] = (unsigned char)(c - cb);
     }
-    group_sync<G>();
+    __syncthreads();
     {
         int e[K];
 #pragma unroll
@@ -447,58 +285,61 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
         for (int u = 0; u < K; ++u)
             if (gt + u * G < nb) ent[gt + u * G] = e[u];
     }
-    group_sync<G>();
-    // B: stable order inside each cell = increasing previous slot
-    for (int j = gt; j < nb; j += G) {
-        const int c = cb + cellof[j];
-        const int lo = T.ls[c] - pofs, n = T.cnt[c];
-        const int e = ent[j];
-        int rank = 0;
-        for (int k = 0; k < n; ++k) rank += (ent[lo + k] < e) ? 1 : 0;
-        srt[lo + rank] = e;
-    }
-    group_sync<G>();
-    // C: gather, then fly the records the MD kernel did not move
+    __syncthreads();
+    // B+C: each record is requested first, then its place in the cell is
+    // found (stable order = increasing previous slot) while the load is in
+    // flight; it flies (unless the MD kernel moved it) and lands in sorted
+    // position
     {
+        constexpr int H = 2;             // records held in registers at once
         bool bad = false;
 #pragma unroll
-        for (int u = 0; u < K; ++u) {
-            const int p = gt + u * G;
-            if (p < nb) {
-                const int slot = srt[p];
-                const bool ok = slot >= part_lo && slot < part_hi;
-                bad |= !ok;
-                Rec rec = load_rec(rin + (ok ? slot : part_lo));
-                if (!ok) rec = Rec{};
-                srec[p] = rec;
+        for (int h = 0; h < K; h += H) {
+            Rec rec[H];
+            int slot[H];
+#pragma unroll
+            for (int u = 0; u < H; ++u) {
+                const int j = gt + (h + u) * G;
+                slot[u] = -1;
+                if (h + u < K && j < nb) {
+                    const int e = ent[j];
+                    const bool ok = e >= part_lo && e < part_hi;
+                    bad |= !ok;
+                    slot[u] = e;
+                    rec[u] = load_rec(rin + (ok ? e : part_lo));
+                    if (!ok) rec[u] = Rec{};
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < H; ++u) {
+                const int j = gt + (h + u) * G;
+                if (h + u < K && j < nb) {
+                    const int c = cb + cellof[j];
+                    const int lo = T.ls[c] - pofs, n = T.cnt[c];
+                    const int e = slot[u];
+                    int rank = 0;
+                    for (int k = 0; k < n; ++k) rank += (ent[lo + k] < e) ? 1 : 0;
+                    Rec r = rec[u];
+                    if ((opts & CP_FLIGHT) && !(r.fid & F_PROP)) rec_flight(hp, r);
+                    r.fid &= ~F_PROP;
+                    srec[lo + rank] = r;
+                }
             }
         }
         if (bad) atomicOr(&d.err[ERR_BOUNDS], 1u);
     }
-#pragma unroll 1
-    for (int p = gt; p < nb; p += G) {
-        Rec rec = srec[p];
-        if ((opts & CP_FLIGHT) && !(rec.fid & F_PROP)) rec_flight(hp, rec);
-        rec.fid &= ~F_PROP;
-        srec[p] = rec;
-    }
-    group_sync<G>();
+    __syncthreads();
     // D: per-cell work
-    if constexpr (MIXED && G == 32) cells_D_warp(d, a, T, gt, cb, ce, pofs, srec);
-    else cells_D_serial<MIXED, G>(d, a, T, gt, cb, ce, pofs, srec);
-    group_sync<G>();
+    cells_D<MIXED>(d, a, T, gt, cb, ce, pofs, srec);
+    __syncthreads();
     if (!have_base) {
-        // stages A-D do not need the tile base; E does
-        if constexpr (G == 32) {
-            base_wait();
-        } else {
-            // the aggregate went out in the prologue; warp 0 scans back now
-            if (gt < 32) {
-                const int base = tile_lookback(d, T.epoch, T.tile, T.ls[CPT], gt, false);
-                if (gt == 0) T.base = base;
-            }
-            __syncthreads();
+        // stages A-D do not need the tile base; E does.  The aggregate went
+        // out in the prologue; warp 0 scans back now.
+        if (gt < 32) {
+            const int base = tile_lookback(d, T.epoch, T.tile, T.ls[CPT], gt, false);
+            if (gt == 0) T.base = base;
         }
+        __syncthreads();
         have_base = true;
     }
     // E: apply, write, classify for the next collision (the next cell of a
@@ -559,7 +400,7 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
             else atomicMax(&d.err[ERR_OVERFLOW], (unsigned int)(pos[u] + 1));
         }
     }
-    group_sync<G>();
+    __syncthreads();
     // F: observables of the post-collision state (§1.4 temperature)
     if (opts & CP_OBS) {
         for (int c = cb + gt; c < ce; c += G) {
@@ -593,7 +434,7 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
             acc[6] += (double)nbB;
             acc[7] += (double)n;
         }
-        group_sync<G>();
+        __syncthreads();
     }
 }
 
@@ -601,6 +442,7 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
 // least one cell; a single cell never exceeds bucket_cap <= cap).
 __device__ __forceinline__ int batch_end(const int *ls, int cb, int cend, int cap)
 {
+    if (ls[cend] - ls[cb] <= cap) return cend;   // the usual case: the rest fits
     int ce = cb + 1;
     while (ce < cend && ls[ce + 1] - ls[cb] <= cap) ++ce;
     return ce;
@@ -610,13 +452,11 @@ template <bool MIXED>
 __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, CellPassArgs a0)
 {
     using Rec = typename Traits<MIXED>::Rec;
-    constexpr int WPC = Traits<MIXED>::WPC;
     constexpr int TP = Traits<MIXED>::TP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Rec *srec = reinterpret_cast<Rec *>(smem_raw);
     int *ent = reinterpret_cast<int *>(srec + TP);
-    int *srt = ent + TP;
-    unsigned char *cellof = reinterpret_cast<unsigned char *>(srt + TP);
+    unsigned char *cellof = reinterpret_cast<unsigned char *>(ent + TP);
     __shared__ TileShared<MIXED> T;
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -632,7 +472,6 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
         T.step = step;
         T.r = tile < d.n_tiles ? d.tile_rep[tile] : 0;
         T.maxcnt = 0;
-        T.next = 0;
         if (blockIdx.x == 0) d.ticket[(epoch + 1u) & 1u] = 0u;
         if (tile == d.n_tiles - 1) {
             __threadfence();
@@ -698,59 +537,17 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
     }
     __syncthreads();
 
-    // tile base by decoupled look-back: warp 0 inspects 32 predecessor tiles
-    // at a time, sums aggregates back to the nearest inclusive prefix.  On the
-    // warp path warp 0 does it now and the other warps start on their cells
-    // meanwhile; on the CTA path the tile's aggregate is published now and the
-    // scan waits until the first batch needs the base (before stage E).
-    const bool warp_path = false;
-    if (warp_path) {
-        if (tid < 32) {
-            const int base = tile_lookback(d, T.epoch, tile, T.ls[CPT], lane);
-            if (lane == 0) T.base = base;
-            __syncwarp();
-            base_arrive();
-        }
-    } else if (tid == 0) {
-        tile_publish(d, T.epoch, tile, T.ls[CPT]);
-    }
+    // tile base by decoupled look-back (warp 0): the tile's aggregate goes
+    // out now, the scan over predecessors waits until the first batch needs
+    // the base (stage E)
+    if (tid == 0) tile_publish(d, T.epoch, tile, T.ls[CPT]);
 
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // T sum, cells, px, py, pz, ke, nB, n
-    if (warp_path) {
-        // each warp takes chunks of CP_CHUNK cells as it becomes free (warp 0
-        // joins after the look-back) and runs them in batches of <= WPC
-        // particles; the observables pass assigns chunks statically so that
-        // its sums are reproducible
-        Rec *wrec = srec + wid * WPC;
-        int *went = ent + wid * WPC;
-        int *wsrt = srt + wid * WPC;
-        unsigned char *wcell = cellof + wid * WPC;
-        bool have_base = wid == 0;
-        for (int k = 0;; ++k) {
-            int c0;
-            if (a.opts & CP_OBS) {
-                c0 = (wid + CP_WARPS * k) * CP_CHUNK;
-            } else {
-                if (lane == 0) c0 = atomicAdd(&T.next, CP_CHUNK);
-                c0 = __shfl_sync(0xffffffffu, c0, 0);
-            }
-            if (c0 >= CPT) break;
-            const int c1 = c0 + CP_CHUNK;
-            for (int cb = c0; cb < c1;) {
-                const int ce = batch_end(T.ls, cb, c1, WPC);
-                cells_batch<MIXED, 32>(d, a, T, lane, cb, ce, wrec, went, wsrt, wcell, acc, have_base);
-                cb = ce;
-            }
-        }
-        if (!have_base) base_wait();   // a warp that took no chunk still meets the barrier once
-    } else {
-        // the whole CTA as one group
-        bool have_base = false;
-        for (int cb = 0; cb < CPT;) {
-            const int ce = batch_end(T.ls, cb, CPT, TP);
-            cells_batch<MIXED, CP_THREADS>(d, a, T, tid, cb, ce, srec, ent, srt, cellof, acc, have_base);
-            cb = ce;
-        }
+    bool have_base = false;
+    for (int cb = 0; cb < CPT;) {
+        const int ce = batch_end(T.ls, cb, CPT, TP);
+        cells_batch<MIXED>(d, a, T, tid, cb, ce, srec, ent, cellof, acc, have_base);
+        cb = ce;
     }
 
     if (a.opts & CP_OBS) {
@@ -772,8 +569,8 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
 
 size_t cellpass_smem(bool mixed)
 {
-    if (mixed) return (size_t)Traits<true>::TP * (sizeof(RecM) + 2 * sizeof(int) + 1);
-    return (size_t)Traits<false>::TP * (sizeof(RecD) + 2 * sizeof(int) + 1);
+    if (mixed) return (size_t)Traits<true>::TP * (sizeof(RecM) + sizeof(int) + 1);
+    return (size_t)Traits<false>::TP * (sizeof(RecD) + sizeof(int) + 1);
 }
 
 void launch_cellpass(bool mixed, const Dev &d, const CellPassArgs &a, cudaStream_t s)

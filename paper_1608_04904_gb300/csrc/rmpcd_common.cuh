@@ -25,9 +25,8 @@ namespace rmpcd {
 constexpr int CPT = 128;           // cells per tile of the cell pass
 constexpr int CP_THREADS = 256;    // threads per cell-pass CTA
 constexpr int CP_WARPS = CP_THREADS / 32;
-constexpr int CP_CHUNK = 8;        // cells a warp of the cell pass takes at a time
-constexpr int CP_WPC_M = 192;      // particles one warp stages at once (mixed records)
-constexpr int CP_WPC_D = 96;       // particles one warp stages at once (fp64 records)
+constexpr int CP_STAGE_M = 6;      // particles a cell-pass thread stages at once (mixed records)
+constexpr int CP_STAGE_D = 3;      // particles a cell-pass thread stages at once (fp64 records)
 constexpr int CP_MAX_CAP = 768;    // largest bucket_cap (a crowded tile uses the whole CTA)
 constexpr int MD_THREADS = 1024;   // threads of the near-field MD CTA (one per replica)
 constexpr int MAXC = 64;           // colloids per replica handled by the MD CTA
