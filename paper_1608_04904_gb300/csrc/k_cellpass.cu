@@ -96,6 +96,15 @@ __device__ __forceinline__ double r_sa(const ReplicaDev &rp, double) { return rp
 __device__ __forceinline__ float r_omc(const ReplicaDev &rp, float) { return rp.omc_f; }
 __device__ __forceinline__ double r_omc(const ReplicaDev &rp, double) { return rp.omc; }
 
+// 16-byte asynchronous copy global -> shared, cached in L2 only (every
+// record is read once per pass).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Per-tile state shared by the groups of one CTA.
 template <bool MIXED>
 struct TileShared {
@@ -286,47 +295,44 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
             if (gt + u * G < nb) ent[gt + u * G] = e[u];
     }
     __syncthreads();
-    // B+C: each record is requested first, then its place in the cell is
-    // found (stable order = increasing previous slot) while the load is in
-    // flight; it flies (unless the MD kernel moved it) and lands in sorted
-    // position
+    // B: the place of every staged particle in its cell (stable order =
+    // increasing previous slot); its record is copied there asynchronously
+    // as soon as the place is known, so all of a thread's gathers are in
+    // flight together and overlap the remaining rank loops
     {
-        constexpr int H = 2;             // records held in registers at once
         bool bad = false;
 #pragma unroll
-        for (int h = 0; h < K; h += H) {
-            Rec rec[H];
-            int slot[H];
+        for (int u = 0; u < K; ++u) {
+            const int j = gt + u * G;
+            if (j < nb) {
+                const int c = cb + cellof[j];
+                const int lo = T.ls[c] - pofs, n = T.cnt[c];
+                const int e = ent[j];
+                int rank = 0;
+                for (int k = 0; k < n; ++k) rank += (ent[lo + k] < e) ? 1 : 0;
+                Rec *dst = srec + lo + rank;
+                if (e >= part_lo && e < part_hi) {
+                    const char *src = reinterpret_cast<const char *>(rin + e);
 #pragma unroll
-            for (int u = 0; u < H; ++u) {
-                const int j = gt + (h + u) * G;
-                slot[u] = -1;
-                if (h + u < K && j < nb) {
-                    const int e = ent[j];
-                    const bool ok = e >= part_lo && e < part_hi;
-                    bad |= !ok;
-                    slot[u] = e;
-                    rec[u] = load_rec(rin + (ok ? e : part_lo));
-                    if (!ok) rec[u] = Rec{};
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < H; ++u) {
-                const int j = gt + (h + u) * G;
-                if (h + u < K && j < nb) {
-                    const int c = cb + cellof[j];
-                    const int lo = T.ls[c] - pofs, n = T.cnt[c];
-                    const int e = slot[u];
-                    int rank = 0;
-                    for (int k = 0; k < n; ++k) rank += (ent[lo + k] < e) ? 1 : 0;
-                    Rec r = rec[u];
-                    if ((opts & CP_FLIGHT) && !(r.fid & F_PROP)) rec_flight(hp, r);
-                    r.fid &= ~F_PROP;
-                    srec[lo + rank] = r;
+                    for (int q = 0; q < (int)(sizeof(Rec) / 16); ++q)
+                        cp_async16(reinterpret_cast<char *>(dst) + 16 * q, src + 16 * q);
+                } else {
+                    bad = true;
+                    *dst = Rec{};
                 }
             }
         }
+        cp_async_wait_all();
         if (bad) atomicOr(&d.err[ERR_BOUNDS], 1u);
+    }
+    __syncthreads();
+    // C: fly the records the MD kernel did not move
+#pragma unroll 1
+    for (int p = gt; p < nb; p += G) {
+        Rec rec = srec[p];
+        if ((opts & CP_FLIGHT) && !(rec.fid & F_PROP)) rec_flight(hp, rec);
+        rec.fid &= ~F_PROP;
+        srec[p] = rec;
     }
     __syncthreads();
     // D: per-cell work
