@@ -528,7 +528,7 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
     AL(&d.near_list, n_total);
     AL(&d.near_count, n_replicas);
     AL(&d.tile_state, n_tiles);
-    AL(&d.ticket, 2);
+    AL(&d.ticket, 4);
     AL(&d.err, ERR_COUNT);
     AL(&d.obs_part, (size_t)n_tiles * 8);
     AL(&d.obs_out, (size_t)n_replicas * 8);
@@ -596,7 +596,7 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
     zero(d.count[1], sizeof(int) * ncells);
     zero(d.near_count, sizeof(int) * n_replicas);
     zero(d.tile_state, sizeof(unsigned long long) * n_tiles);
-    zero(d.ticket, sizeof(unsigned int) * 2);
+    zero(d.ticket, sizeof(unsigned int) * 4);
     zero(d.err, sizeof(unsigned int) * ERR_COUNT);
     zero(d.obs_out, sizeof(double) * 8 * n_replicas);
     if (st == RMPCD_OK) zero(d.md_wide, sizeof(MdWideGlobal));

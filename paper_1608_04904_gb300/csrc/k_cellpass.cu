@@ -22,6 +22,8 @@
 // Per particle this reads its bucket entry (4 B) and its record (32 B mixed /
 // 64 B fp64) and writes its record and its next bucket entry: one pass over
 // the solvent per collision.
+#include <algorithm>
+
 #include "rmpcd_kernels.cuh"
 
 namespace rmpcd {
@@ -111,7 +113,7 @@ struct TileShared {
     using R = typename Traits<MIXED>::R;
     ReplicaDev rp;
     NearFrames nf;
-    int tile, r, base, maxcnt;
+    int tile, next_tile, r, base;
     uint32_t epoch, step;     // this launch's counter and collision index (from the control block)
     int cnt[CPT], ls[CPT + 1], wt[CPT / 32];
     double sh[3], shn[3];     // fp64 path
@@ -249,7 +251,7 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
 template <bool MIXED>
 __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXED> &T, int gt, int cb, int ce,
                             typename Traits<MIXED>::Rec *srec, int *ent, unsigned char *cellof, double acc[8],
-                            bool &have_base)
+                            bool &have_base, int &npref, bool &pref)
 {
     using Rec = typename Traits<MIXED>::Rec;
     using R = typename Traits<MIXED>::R;
@@ -280,6 +282,12 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
         for (int i = 0; i < n; ++i) cellof[lo + i] = (unsigned char)(c - cb);
     }
     __syncthreads();
+    if (pref) {
+        // the next tile's counts, read now and used when this tile is done
+        const int nt = T.next_tile;
+        if (gt < CPT && nt < d.n_tiles) npref = d.count[a.cur][nt * CPT + gt];
+        pref = false;
+    }
     {
         int e[K];
 #pragma unroll
@@ -467,108 +475,127 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0) {
-        // the launch counter and the step, read before the ticket is taken:
-        // the CTA with the last ticket advances them after every CTA has read
+        // the launch counter and the step, read before the first ticket is
+        // taken; the last CTA to finish advances them, after every CTA has read
         const uint32_t epoch = *(volatile uint32_t *)&d.ctl->epoch;
         const uint32_t step = resolve_step(d, a0.step);
         __threadfence();
-        const int tile = (int)atomicAdd(&d.ticket[epoch & 1u], 1u);
-        T.tile = tile;
+        T.tile = (int)atomicAdd(&d.ticket[epoch & 1u], 1u);
         T.epoch = epoch;
         T.step = step;
-        T.r = tile < d.n_tiles ? d.tile_rep[tile] : 0;
-        T.maxcnt = 0;
         if (blockIdx.x == 0) d.ticket[(epoch + 1u) & 1u] = 0u;
-        if (tile == d.n_tiles - 1) {
-            __threadfence();
-            d.ctl->epoch = epoch + 1u;
-            if (a0.opts & CP_ADVANCE) d.ctl->step = step + 1u;
-        }
     }
     __syncthreads();
     CellPassArgs a = a0;
     a.step = T.step;
-    const int tile = T.tile;
-    if (tile >= d.n_tiles) return;
-    {
-        // the replica's constants, copied by all threads in parallel
-        const int *src = reinterpret_cast<const int *>(d.rep + T.r);
-        int *dst = reinterpret_cast<int *>(&T.rp);
-        for (int i = tid; i < (int)(sizeof(ReplicaDev) / sizeof(int)); i += CP_THREADS) dst[i] = src[i];
-    }
-    const int gc0 = tile * CPT;
-    // counts of the tile's cells (consumed: reset for reuse two passes later)
-    int n = 0, x = 0;
-    if (tid < CPT) {
-        n = d.count[a.cur][gc0 + tid];
-        d.count[a.cur][gc0 + tid] = 0;
-        const int mraw = __reduce_max_sync(0xffffffffu, n);
-        if (lane == 0 && mraw > 0) atomicMax(d.maxcnt, (unsigned int)mraw);   // for the bucket-width tuner
-        if (n > d.cap) {
-            atomicMax(&d.err[ERR_OVERFLOW], (unsigned int)n);
-            n = d.cap;
+    // Persistent CTA: tiles in ticket order.  The next ticket is taken when a
+    // tile starts and that tile's counts are read during the current one, so
+    // the chain ticket -> counts is off the critical path; the replica's
+    // constants are reloaded only when the replica changes.
+    int cur_r = -1;
+    int npref = 0;
+    if (tid < CPT && T.tile < d.n_tiles) npref = d.count[a.cur][T.tile * CPT + tid];
+    for (;;) {
+        const int tile = T.tile;
+        if (tile >= d.n_tiles) break;
+        if (tid == 0) T.r = d.tile_rep[tile];
+        __syncthreads();
+        const ReplicaDev &rp = T.rp;
+        if (T.r != cur_r) {
+            cur_r = T.r;
+            const int *src = reinterpret_cast<const int *>(d.rep + cur_r);
+            int *dst = reinterpret_cast<int *>(&T.rp);
+            for (int i = tid; i < (int)(sizeof(ReplicaDev) / sizeof(int)); i += CP_THREADS) dst[i] = src[i];
+            __syncthreads();
+            if (tid == 0) {
+                grid_shift(rp.seed, a.step, T.shf);
+                if (!MIXED) grid_shift(rp.seed, a.step, T.sh);
+            } else if (tid == 32) {
+                grid_shift(rp.seed, a.step + 1u, T.shnf);
+                if (!MIXED) grid_shift(rp.seed, a.step + 1u, T.shn);
+            }
+            if (MIXED && (a.opts & CP_NEXT)) {
+                for (int i = tid; i < 3 * rp.n_col; i += CP_THREADS) {
+                    T.nf.Ci[i] = d.colCi[3 * rp.col_off + i];
+                    T.nf.Cf[i] = d.colXf[3 * rp.col_off + i];
+                }
+                for (int j = tid; j < rp.n_col; j += CP_THREADS) T.nf.Rb[j] = d.colRb_f[rp.col_off + j];
+            }
         }
-        T.cnt[tid] = n;
-        x = n;
+        const int gc0 = tile * CPT;
+        // counts of the tile's cells (consumed: reset for reuse two passes later)
+        int x = 0;
+        if (tid < CPT) {
+            int n = npref;
+            d.count[a.cur][gc0 + tid] = 0;
+            const int mraw = __reduce_max_sync(0xffffffffu, n);
+            if (lane == 0 && mraw > 0) atomicMax(d.maxcnt, (unsigned int)mraw);   // for the bucket-width tuner
+            if (n > d.cap) {
+                atomicMax(&d.err[ERR_OVERFLOW], (unsigned int)n);
+                n = d.cap;
+            }
+            T.cnt[tid] = n;
+            x = n;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        const int mx = __reduce_max_sync(0xffffffffu, n);
-        if (lane == 31) T.wt[wid] = x;
-        if (lane == 0) atomicMax(&T.maxcnt, mx);
-    }
-    __syncthreads();
-    const ReplicaDev &rp = T.rp;
-    if (tid < CPT) {
-        int pre = 0;
-        for (int w = 0; w < wid; ++w) pre += T.wt[w];
-        T.ls[tid + 1] = x + pre;
-    }
-    if (tid == 0) {
-        T.ls[0] = 0;
-        grid_shift(rp.seed, a.step, T.shf);
-        if (!MIXED) grid_shift(rp.seed, a.step, T.sh);
-    } else if (tid == 32) {
-        grid_shift(rp.seed, a.step + 1u, T.shnf);
-        if (!MIXED) grid_shift(rp.seed, a.step + 1u, T.shn);
-    }
-    if (MIXED && (a.opts & CP_NEXT)) {
-        for (int i = tid; i < 3 * rp.n_col; i += CP_THREADS) {
-            T.nf.Ci[i] = d.colCi[3 * rp.col_off + i];
-            T.nf.Cf[i] = d.colXf[3 * rp.col_off + i];
-        }
-        for (int j = tid; j < rp.n_col; j += CP_THREADS) T.nf.Rb[j] = d.colRb_f[rp.col_off + j];
-    }
-    __syncthreads();
-
-    // tile base by decoupled look-back (warp 0): the tile's aggregate goes
-    // out now, the scan over predecessors waits until the first batch needs
-    // the base (stage E)
-    if (tid == 0) tile_publish(d, T.epoch, tile, T.ls[CPT]);
-
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // T sum, cells, px, py, pz, ke, nB, n
-    bool have_base = false;
-    for (int cb = 0; cb < CPT;) {
-        const int ce = batch_end(T.ls, cb, CPT, TP);
-        cells_batch<MIXED>(d, a, T, tid, cb, ce, srec, ent, cellof, acc, have_base);
-        cb = ce;
-    }
-
-    if (a.opts & CP_OBS) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            double x = acc[k];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-            if (lane == 0) T.red[wid][k] = x;
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) T.wt[wid] = x;
         }
         __syncthreads();
-        if (tid < 8) {
-            double x = 0.0;
-            for (int w = 0; w < CP_WARPS; ++w) x += T.red[w][tid];
-            d.obs_part[(long long)tile * 8 + tid] = x;
+        if (tid < CPT) {
+            int pre = 0;
+            for (int w = 0; w < wid; ++w) pre += T.wt[w];
+            T.ls[tid + 1] = x + pre;
+        }
+        if (tid == 0) T.ls[0] = 0;
+        __syncthreads();
+
+        // tile base by decoupled look-back (warp 0): the tile's aggregate goes
+        // out now, the scan over predecessors waits until the first batch
+        // needs the base (stage E); the next ticket is taken now
+        if (tid == 0) {
+            tile_publish(d, T.epoch, tile, T.ls[CPT]);
+            T.next_tile = (int)atomicAdd(&d.ticket[T.epoch & 1u], 1u);
+        }
+
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // T sum, cells, px, py, pz, ke, nB, n
+        bool have_base = false, pref = true;
+        for (int cb = 0; cb < CPT;) {
+            const int ce = batch_end(T.ls, cb, CPT, TP);
+            cells_batch<MIXED>(d, a, T, tid, cb, ce, srec, ent, cellof, acc, have_base, npref, pref);
+            cb = ce;
+        }
+
+        if (a.opts & CP_OBS) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                double v = acc[k];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                if (lane == 0) T.red[wid][k] = v;
+            }
+            __syncthreads();
+            if (tid < 8) {
+                double v = 0.0;
+                for (int w = 0; w < CP_WARPS; ++w) v += T.red[w][tid];
+                d.obs_part[(long long)tile * 8 + tid] = v;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) T.tile = T.next_tile;
+        __syncthreads();
+    }
+    // the last CTA to finish advances the interval control
+    if (tid == 0) {
+        __threadfence();
+        const unsigned done = atomicAdd(&d.ticket[2 + (T.epoch & 1u)], 1u);
+        if (done == gridDim.x - 1) {
+            d.ticket[2 + (T.epoch & 1u)] = 0u;
+            __threadfence();
+            d.ctl->epoch = T.epoch + 1u;
+            if (a0.opts & CP_ADVANCE) d.ctl->step = T.step + 1u;
         }
     }
 }
@@ -579,17 +606,36 @@ size_t cellpass_smem(bool mixed)
     return (size_t)Traits<false>::TP * (sizeof(RecD) + sizeof(int) + 1);
 }
 
+// Co-resident CTAs of the persistent cell pass on the current device.
+static int cellpass_grid(bool mixed)
+{
+    static int cached[2][64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int &g = cached[mixed ? 1 : 0][dev & 63];
+    if (g == 0) {
+        const size_t sm = cellpass_smem(mixed);
+        int per_sm = 0, n_sm = 0;
+        if (mixed) {
+            cudaFuncSetAttribute(k_cellpass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cellpass<true>, CP_THREADS, sm);
+        } else {
+            cudaFuncSetAttribute(k_cellpass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cellpass<false>, CP_THREADS, sm);
+        }
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        g = std::max(1, per_sm) * std::max(1, n_sm);
+    }
+    return g;
+}
+
 void launch_cellpass(bool mixed, const Dev &d, const CellPassArgs &a, cudaStream_t s)
 {
     if (d.n_tiles == 0) return;
     const size_t sm = cellpass_smem(mixed);
-    if (mixed) {
-        cudaFuncSetAttribute(k_cellpass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_cellpass<true><<<d.n_tiles, CP_THREADS, sm, s>>>(d, a);
-    } else {
-        cudaFuncSetAttribute(k_cellpass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_cellpass<false><<<d.n_tiles, CP_THREADS, sm, s>>>(d, a);
-    }
+    const int grid = std::min(d.n_tiles, cellpass_grid(mixed));
+    if (mixed) k_cellpass<true><<<grid, CP_THREADS, sm, s>>>(d, a);
+    else k_cellpass<false><<<grid, CP_THREADS, sm, s>>>(d, a);
 }
 
 }  // namespace rmpcd

@@ -132,7 +132,7 @@ struct Dev {
     int *near_list;              // per replica region [part_off, part_off + n_part)
     int *near_count;             // [n_rep]
     unsigned long long *tile_state;  // decoupled look-back, one word per tile
-    unsigned int *ticket;        // [2]
+    unsigned int *ticket;        // [4]: tile tickets, finished CTAs (per launch parity)
     unsigned int *err;           // [ERR_COUNT]
     double *obs_part;            // [n_tiles][8]
     double *obs_out;             // [n_rep][8]
@@ -647,7 +647,9 @@ __device__ __forceinline__ void st_release(unsigned long long *p, unsigned long 
 // tile_publish), inspects 32 predecessor tiles at a time summing aggregates
 // back to the nearest inclusive prefix, publishes the tile's inclusive prefix
 // and returns its exclusive prefix (in every lane).
-// Tiles are taken in ticket order, so every predecessor has started.  Words
+// Tiles are taken in ticket order by resident CTAs, each finishing its tiles
+// in that order, so every predecessor is held by a CTA that will publish it
+// without waiting on this tile.  Words
 // carry a 16-bit tag of the launch (never 0, the initial state), a 2-bit flag
 // (1 aggregate, 2 inclusive prefix) and a 46-bit value.  A wait that runs out
 // sets ERR_TIMEOUT and returns a base that puts every write out of bounds.
