@@ -44,8 +44,10 @@ KERNEL_SOURCES = ["rmpcd_common.cuh", "rmpcd_kernels.cuh", "k_cellpass.cu", "k_m
                   "k_md_body.cu", "k_particles.cu", "capi.cu"]
 
 
-def workload(name, precision, seed_offset=0):
-    """The workload as a list of replicas (cfg, colloids, bonds, body) and a description."""
+def workload(name, precision, seed_offset=0, n_replicas=None):
+    """The workload as a list of replicas (cfg, colloids, bonds, body) and a description.
+    n_replicas keeps the first replicas of the batched ensemble only (a smaller
+    case of the same kernels, for profiling)."""
     from paper_1608_04904_gb300 import synth
     if name == "dimer32":
         reps = [synth.dimer32(precision=precision, seed=2 + seed_offset)]
@@ -68,12 +70,12 @@ def workload(name, precision, seed_offset=0):
                 "M 150), colloid LJ eps 1 sigma 5.5 cut 2.5 sigma, MPC-AT slabs [0,8) kT 1.2 and [128,136) kT 0.8, "
                 "50 MD sub-steps dt 0.01")
     elif name == "batch256":
-        sides = synth.batch_sides(256, seed=4)
+        sides = synth.batch_sides(256, seed=4)[:n_replicas]
         reps = []
         for r, L in enumerate(sides):
             cfg, body = synth.batch_janus(L, seed=4 + r + 1000 * seed_offset, precision=precision)
             reps.append((cfg, [], [], body))
-        desc = ("256 independent replicas in one launch per kernel, cube sides drawn from {16,20,24,32,40,48} "
+        desc = (f"{len(sides)} independent replicas in one launch per kernel, cube sides drawn from {{16,20,24,32,40,48}} "
                 "(seed 4), rho 10, one rigid Janus particle each (100-300 beads on a sphere of radius 4, "
                 "sigma_b 1, catalytic hemisphere A->B), alpha 130 deg, tau 0.5, 25 MD sub-steps dt 0.02")
         return reps, desc
@@ -348,6 +350,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--replicas", type=int, default=None,
+                    help="batch256 only: keep the first N replicas (a smaller case for profiling)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     ws, rank, local = dist_setup()
@@ -370,7 +374,7 @@ def main():
     build.build()
     api.load()
 
-    reps, desc = workload(args.workload, args.precision, seed_offset=rank)
+    reps, desc = workload(args.workload, args.precision, seed_offset=rank, n_replicas=args.replicas)
     states = [initial_state(r) for r in reps]
     cfg = reps[0][0]
     n = sum(len(st[0]) for st in states)
