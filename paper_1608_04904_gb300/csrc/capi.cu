@@ -627,6 +627,9 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
     d.bonds = dB;
     d.md_work = work;
     d.cap = bucket_cap;
+    d.many_col = 0;
+    for (int r = 0; r < n_replicas; ++r)
+        if (params[r].n_colloids >= CP_NEAR_CAND_MIN) d.many_col = 1;
     d.n_rep = n_replicas;
     d.n_tiles = (int)n_tiles;
     d.n_total = (int)n_total;

@@ -69,6 +69,24 @@ struct NearFrames {
     float Rb[MAXC];
 };
 
+// The near test of the mixed path over the colloids of a bit mask.
+__device__ __forceinline__ bool near_test_mask(const HotM &rp, unsigned long long mask, const NearFrames &nf,
+                                               const int c[3], const float o[3], const float v[3])
+{
+    const float st = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * rp.tau_f;
+    for (; mask; mask &= mask - 1ull) {
+        const int j = __ffsll((long long)mask) - 1;
+        float dd[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dd[k] = (float)(c[k] - nf.Ci[3 * j + k]) + (o[k] - nf.Cf[3 * j + k]);
+        min_image(rp, dd);
+        const float r2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
+        const float R = nf.Rb[j] + st;
+        if (r2 < R * R) return true;
+    }
+    return false;
+}
+
 __device__ __forceinline__ bool rec_near(const Dev &, const HotM &rp, int nc, const NearFrames &nf, const RecM &r)
 {
     int c[3] = {cw_get(r.cw, 0), cw_get(r.cw, 1), cw_get(r.cw, 2)};
@@ -77,6 +95,20 @@ __device__ __forceinline__ bool rec_near(const Dev &, const HotM &rp, int nc, co
 __device__ __forceinline__ bool rec_near(const Dev &d, const ReplicaDev &rp, int, const NearFrames &, const RecD &r)
 {
     return near_test_d(d, rp, r.x, r.v);
+}
+// The many-colloid variant (mixed path): the batch's candidate colloids, or
+// every colloid where the cell has no speed bound (all).
+__device__ __forceinline__ bool rec_near_cand(const HotM &rp, int nc, const NearFrames &nf, const RecM &r,
+                                              unsigned long long mask, bool all)
+{
+    int c[3] = {cw_get(r.cw, 0), cw_get(r.cw, 1), cw_get(r.cw, 2)};
+    if (all) return near_test_m(rp, nc, nf.Ci, nf.Cf, nf.Rb, c, r.o, r.v);
+    return near_test_mask(rp, mask, nf, c, r.o, r.v);
+}
+__device__ __forceinline__ bool rec_near_cand(const ReplicaDev &, int, const NearFrames &, const RecD &,
+                                              unsigned long long, bool)
+{
+    return false;   // not used: the candidate path is the mixed path's
 }
 
 // What the per-particle loops read of the replica: a register copy for the
@@ -119,14 +151,17 @@ struct TileShared {
     double sh[3], shn[3];     // fp64 path
     float shf[3], shnf[3];
     R vcm[CPT][3], ax[CPT][3];
-    int mode[CPT], react[CPT];
-    int mnear[CPT];   // 0: no particle of the cell can come near a colloid
+    int react[CPT];
+    unsigned char mode[CPT];    // 0: untouched, 1: SRD rotation, 2: MPC-AT
+    unsigned char mnear[CPT];   // 0: no particle of the cell can come near a colloid
+    float vbc[CPT];   // bound on the cell's post-collision speeds (< 0: none, MPC-AT)
+    unsigned long long cand;   // colloids that can reach the batch (many-colloid replicas)
     double red[CP_WARPS][8];
 };
 
 // Stage D, one thread per cell, particles summed in sorted order (the same
 // order as the FP64 oracle).
-template <bool MIXED>
+template <bool MIXED, bool MANY>
 __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, TileShared<MIXED> &T, int gt,
                                                int cb, int ce, int pofs, typename Traits<MIXED>::Rec *srec)
 {
@@ -197,8 +232,10 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
             // can a particle of the cell come near a colloid in the next
             // interval?  Its post-collision speed is at most |v_cm| + max
             // |v - v_cm| (the rotation keeps |v - v_cm|) and it lies within
-            // sqrt(3)/2 of the cell centre on this step's grid
+            // sqrt(3)/2 of the cell centre on this step's grid.  With many
+            // colloids the test runs after the batch's candidates are known.
             int mn = 1;
+            if (MANY) T.vbc[c] = -1.0f;
             if (slab < 0) {
                 R s3[3] = {R(0), R(0), R(0)};
                 for (int i = 0; i < n; ++i)
@@ -212,10 +249,11 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
                     u2 = max(u2, a0 * a0 + a1 * a1 + a2 * a2);
                 }
                 const float vb = (float)(sqrt(vc[0] * vc[0] + vc[1] * vc[1] + vc[2] * vc[2]) + sqrt(u2));
+                if (MANY) T.vbc[c] = vb;
                 const int t = lc / rp.L[0];
                 const int kc[3] = {lc % rp.L[0], t % rp.L[1], rp.walls ? t / rp.L[1] - 1 : t / rp.L[1]};
                 mn = 0;
-                for (int j = 0; j < rp.n_col && !mn; ++j) {
+                for (int j = 0; j < (MANY ? 0 : rp.n_col) && !mn; ++j) {
                     float dd[3];
                     for (int k = 0; k < 3; ++k)
                         dd[k] = (float)(kc[k] - T.nf.Ci[3 * j + k]) + ((0.5f + T.shf[k]) - T.nf.Cf[3 * j + k]);
@@ -245,10 +283,84 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
     }
 }
 
+// Many-colloid replicas (mixed path), after stage D: warp 0 finds the
+// colloids that any particle of the batch can reach during the next interval
+// -- distance from the colloid to the box of the batch's cells on this
+// step's grid below its near-list radius plus the batch's largest
+// post-collision speed times tau -- and then every cell tests only those
+// (cells without a speed bound, MPC-AT, keep every colloid).
+template <bool MIXED>
+__device__ void near_candidates(TileShared<MIXED> &T, int gt, int cb, int ce)
+{
+    const ReplicaDev &rp = T.rp;
+    const int lc0 = T.tile * CPT - rp.cell_off;
+    if (gt < 32) {
+        int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-1, -1, -1};
+        float vmax = 0.0f;
+        for (int c = cb + gt; c < ce; c += 32) {
+            const int lc = lc0 + c;
+            const int t = lc / rp.L[0];
+            const int kc[3] = {lc % rp.L[0], t % rp.L[1], t / rp.L[1]};
+            for (int k = 0; k < 3; ++k) { lo[k] = min(lo[k], kc[k]); hi[k] = max(hi[k], kc[k]); }
+            if (T.cnt[c] > 0) vmax = fmaxf(vmax, T.vbc[c]);
+        }
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = __reduce_min_sync(0xffffffffu, lo[k]);
+            hi[k] = __reduce_max_sync(0xffffffffu, hi[k]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        unsigned long long m = 0ull;
+        for (int h = 0; h < 2; ++h) {
+            const int j = gt + 32 * h;
+            bool reach = false;
+            if (j < rp.n_col) {
+                float d2 = 0.0f;
+                for (int k = 0; k < 3; ++k) {
+                    const float L = (float)rp.L[k];
+                    const float a = (float)lo[k] + T.shf[k], b = (float)hi[k] + 1.0f + T.shf[k];
+                    const float X = (float)T.nf.Ci[3 * j + k] + T.nf.Cf[3 * j + k];
+                    float dk = 0.0f;
+                    if (b - a < L) {
+                        dk = 1e30f;
+                        for (int s = -1; s <= 1; ++s) {
+                            const float y = X + (float)s * L;
+                            dk = fminf(dk, fmaxf(0.0f, fmaxf(a - y, y - b)));
+                        }
+                    }
+                    d2 += dk * dk;
+                }
+                reach = sqrtf(d2) < T.nf.Rb[j] + vmax * rp.tau_f + 1e-3f;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, reach);
+            m |= (unsigned long long)bal << (32 * h);
+        }
+        if (gt == 0) T.cand = m;
+    }
+    __syncthreads();
+    for (int c = cb + gt; c < ce; c += CP_THREADS) {
+        if (T.cnt[c] == 0 || T.vbc[c] < 0.0f) continue;   // empty cell: no test; MPC-AT: mnear already 1
+        const int lc = lc0 + c;
+        const int t = lc / rp.L[0];
+        const int kc[3] = {lc % rp.L[0], t % rp.L[1], t / rp.L[1]};
+        int mn = 0;
+        for (unsigned long long m = T.cand; m && !mn; m &= m - 1ull) {
+            const int j = __ffsll((long long)m) - 1;
+            float dd[3];
+            for (int k = 0; k < 3; ++k)
+                dd[k] = (float)(kc[k] - T.nf.Ci[3 * j + k]) + ((0.5f + T.shf[k]) - T.nf.Cf[3 * j + k]);
+            min_image(rp, dd);
+            const float dist = sqrtf(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+            if (dist - 0.8661f < T.nf.Rb[j] + T.vbc[c] * rp.tau_f + 1e-3f) mn = 1;
+        }
+        T.mnear[c] = mn;
+    }
+}
+
 // The stages of the cell pass for the cells [cb, ce) of the tile, run by the
 // whole CTA (gt = thread index).  srec/ent/cellof are the staging arrays
 // (>= the batch).
-template <bool MIXED>
+template <bool MIXED, bool MANY>
 __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXED> &T, int gt, int cb, int ce,
                             typename Traits<MIXED>::Rec *srec, int *ent, unsigned char *cellof, double acc[8],
                             bool &have_base, int &npref, bool &pref)
@@ -344,8 +456,14 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
     }
     __syncthreads();
     // D: per-cell work
-    cells_D<MIXED>(d, a, T, gt, cb, ce, pofs, srec);
+    cells_D<MIXED, MANY>(d, a, T, gt, cb, ce, pofs, srec);
     __syncthreads();
+    if constexpr (MANY) {
+        if (opts & CP_NEXT) {
+            near_candidates(T, gt, cb, ce);
+            __syncthreads();
+        }
+    }
     if (!have_base) {
         // stages A-D do not need the tile base; E does.  The aggregate went
         // out in the prologue; warp 0 scans back now.
@@ -384,7 +502,10 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
         if ((opts & CP_WRITE) && inb) store_rec(rout + gslot, rec);
         if (opts & CP_OBS) srec[p] = rec;
         if ((opts & CP_NEXT) && inb) {
-            if (n_col > 0 && T.mnear[c] && rec_near(d, hp, n_col, T.nf, rec)) {
+            bool near;
+            if constexpr (MANY) near = T.mnear[c] && rec_near_cand(hp, n_col, T.nf, rec, T.cand, T.vbc[c] < 0.0f);
+            else near = n_col > 0 && T.mnear[c] && rec_near(d, hp, n_col, T.nf, rec);
+            if (near) {
                 const int k = atomicAdd(&d.near_count[T.r], 1);
                 if (k < rp.n_part) d.near_list[rp.part_off + k] = gslot;
                 else atomicOr(&d.err[ERR_BOUNDS], 1u);
@@ -462,7 +583,9 @@ __device__ __forceinline__ int batch_end(const int *ls, int cb, int cend, int ca
     return ce;
 }
 
-template <bool MIXED>
+// MANY: the system has a replica with at least CP_NEAR_CAND_MIN colloids
+// (mixed path only): near tests through per-batch candidate colloids.
+template <bool MIXED, bool MANY>
 __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, CellPassArgs a0)
 {
     using Rec = typename Traits<MIXED>::Rec;
@@ -564,7 +687,7 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
         bool have_base = false, pref = true;
         for (int cb = 0; cb < CPT;) {
             const int ce = batch_end(T.ls, cb, CPT, TP);
-            cells_batch<MIXED>(d, a, T, tid, cb, ce, srec, ent, cellof, acc, have_base, npref, pref);
+            cells_batch<MIXED, MANY>(d, a, T, tid, cb, ce, srec, ent, cellof, acc, have_base, npref, pref);
             cb = ce;
         }
 
@@ -607,35 +730,38 @@ size_t cellpass_smem(bool mixed)
 }
 
 // Co-resident CTAs of the persistent cell pass on the current device.
-static int cellpass_grid(bool mixed)
+template <bool MIXED, bool MANY>
+static int cellpass_grid()
 {
-    static int cached[2][64] = {};
+    static int cached[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
-    int &g = cached[mixed ? 1 : 0][dev & 63];
+    int &g = cached[dev & 63];
     if (g == 0) {
-        const size_t sm = cellpass_smem(mixed);
+        const size_t sm = cellpass_smem(MIXED);
         int per_sm = 0, n_sm = 0;
-        if (mixed) {
-            cudaFuncSetAttribute(k_cellpass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cellpass<true>, CP_THREADS, sm);
-        } else {
-            cudaFuncSetAttribute(k_cellpass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cellpass<false>, CP_THREADS, sm);
-        }
+        cudaFuncSetAttribute(k_cellpass<MIXED, MANY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cellpass<MIXED, MANY>, CP_THREADS, sm);
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
         g = std::max(1, per_sm) * std::max(1, n_sm);
     }
     return g;
 }
 
+template <bool MIXED, bool MANY>
+static void launch_cp(const Dev &d, const CellPassArgs &a, cudaStream_t s)
+{
+    const size_t sm = cellpass_smem(MIXED);
+    const int grid = std::min(d.n_tiles, cellpass_grid<MIXED, MANY>());
+    k_cellpass<MIXED, MANY><<<grid, CP_THREADS, sm, s>>>(d, a);
+}
+
 void launch_cellpass(bool mixed, const Dev &d, const CellPassArgs &a, cudaStream_t s)
 {
     if (d.n_tiles == 0) return;
-    const size_t sm = cellpass_smem(mixed);
-    const int grid = std::min(d.n_tiles, cellpass_grid(mixed));
-    if (mixed) k_cellpass<true><<<grid, CP_THREADS, sm, s>>>(d, a);
-    else k_cellpass<false><<<grid, CP_THREADS, sm, s>>>(d, a);
+    if (!mixed) launch_cp<false, false>(d, a, s);
+    else if (d.many_col) launch_cp<true, true>(d, a, s);
+    else launch_cp<true, false>(d, a, s);
 }
 
 }  // namespace rmpcd

@@ -28,6 +28,7 @@ constexpr int CP_WARPS = CP_THREADS / 32;
 constexpr int CP_STAGE_M = 6;      // particles a cell-pass thread stages at once (mixed records)
 constexpr int CP_STAGE_D = 3;      // particles a cell-pass thread stages at once (fp64 records)
 constexpr int CP_MAX_CAP = 768;    // largest bucket_cap (a crowded tile uses the whole CTA)
+constexpr int CP_NEAR_CAND_MIN = 5;   // colloids from which the mixed cell pass filters them per batch
 constexpr int MD_THREADS = 1024;   // threads of the near-field MD CTA (one per replica)
 constexpr int MAXC = 64;           // colloids per replica handled by the MD CTA
 constexpr int MAXB = 16;           // bonds per replica
@@ -158,6 +159,7 @@ struct Dev {
     const int *grid_start;       // lookup-grid list offsets
     const unsigned short *grid_list;
     int cap;
+    int many_col;                // 1: some replica has >= CP_NEAR_CAND_MIN colloids
     int n_rep;
     int n_tiles;
     int n_total;
