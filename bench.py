@@ -269,6 +269,9 @@ def _timed_run(api, torch, reps, states, precision, steps, warmup, flush, dev_in
     for _ in range(max(warmup, 16 if (has_col and md_cluster == 0) else 0)):   # 3 trials x <= 5 sizes
         s.step(1)
     torch.cuda.synchronize()
+    # rigid bodies: centre of mass before the timed steps (for the MSD)
+    body_reps = [r for r, rep in enumerate(reps) if rep[3] is not None]
+    x0 = [s.get_body(r)["x"] for r in body_reps]
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     launches0 = s.launch_count()
@@ -287,6 +290,13 @@ def _timed_run(api, torch, reps, states, precision, steps, warmup, flush, dev_in
     barrier()
     clocks = clk.stop() if clk else None
     launches = s.launch_count() - launches0
+    msd = None
+    if body_reps:
+        import numpy as np
+        d2 = np.array([float(((s.get_body(r)["x"] - a) ** 2).sum()) for r, a in zip(body_reps, x0)])
+        msd = {"intervals": steps, "time": steps * reps[body_reps[0]][0]["tau"], "mean": float(d2.mean()),
+               "min": float(d2.min()), "max": float(d2.max()), "replicas": len(d2),
+               "per_replica_first8": [round(float(v), 6) for v in d2[:8]]}
     ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
     # per-kernel times: a further run with the library's timers (events
     # around each launch, so direct launches instead of graphs)
@@ -300,6 +310,7 @@ def _timed_run(api, torch, reps, states, precision, steps, warmup, flush, dev_in
     obs = s.observables(0)
     obs["md_cluster"], obs["md_kernel"] = s.get_tuning()
     obs["bucket_cap"] = s.bucket_cap()
+    obs["msd"] = msd
     s.close()
     return ms, timers, launches, clocks, obs
 
@@ -442,6 +453,9 @@ def main():
         "roofline": roofline, "kernels": kernels, "gpu_launches": launches, "clocks": clocks,
         "observables": {"temperature": obs["temperature"], "n_B": obs["n_B"], "kT": cfg["kT"]},
     }
+    if obs.get("msd"):
+        # mean squared displacement of the bodies' centres over the timed intervals (per replica)
+        line["observables"]["body_msd"] = obs["msd"]
     if rank == 0 and not args.no_fp64 and args.precision == "mixed":
         k64 = max(20, args.steps // 4)
         ms64, t64, _, _, _ = timed_run(api, torch, reps, states, "fp64", k64, args.warmup, flush, local,
