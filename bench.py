@@ -181,6 +181,24 @@ def dist_setup():
     return ws, rank, local
 
 
+def job_throughput(ms, n_local, steps, device=None):
+    """Whole-job particle-steps/s and the job's time in ms: every rank's
+    particles (independent replicas, weak scaling) over the slowest rank's
+    time.  Without an initialised process group of more than one rank, the
+    local values."""
+    import torch
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        tm = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        tn = torch.tensor([float(n_local)], dtype=torch.float64, device=device)
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tn, op=dist.ReduceOp.SUM)
+        ms, n_all = float(tm.item()), float(tn.item())
+    else:
+        n_all = float(n_local)
+    return n_all * steps / (ms / 1e3), ms
+
+
 def cpu_baseline(name, precision, budget_s=15.0):
     """The oracle, as it stands, on the host cores: full collision intervals of
     the same workload until the time budget is spent (after one warm-up)."""
@@ -394,13 +412,7 @@ def main():
     ms, timers, launches, clocks, obs = timed_run(api, torch, reps, states, args.precision,
                                                   args.steps, args.warmup, flush, local, rank == 0, barrier,
                                                   args.md_cluster, args.md_kernel)
-    ms_max = ms
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = ws * n * args.steps / (ms_max / 1e3)
+    value, ms_max = job_throughput(ms, n, args.steps, device="cuda")
 
     # roofline of the dominant kernel (CUDA events around each launch on the library's stream)
     phases = {k: v_ for k, v_ in timers.items() if v_["launches"] > 0}
