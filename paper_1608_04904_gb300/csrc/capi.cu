@@ -89,6 +89,7 @@ struct rmpcd_system {
     std::vector<BodyHost> bodies;
     bool any_body = false;
     int nb_max = 0;
+    int grid_room = 0;                // shared-memory room for the lookup grids (0: global)
     std::vector<void *> body_allocs;  // bead and grid arrays
     double *col_rc = nullptr;         // writable colloid constants (body slots)
     float *col_rb = nullptr;
@@ -879,7 +880,7 @@ rmpcd_status rmpcd_stream(rmpcd_system *sys)
         if ((st = after_launch(sys, sys->md_kernel == 3 ? (int)sys->wide_reps.size() : 1)) != RMPCD_OK) return st;
     }
     if (sys->any_body) {
-        launch_md_body(sys->mixed, sys->d, sys->nb_max, sys->step, sys->cur, 0, 0, sys->stream);
+        launch_md_body(sys->mixed, sys->d, sys->nb_max, sys->grid_room, sys->step, sys->cur, 0, 0, sys->stream);
         if ((st = after_launch(sys, 1)) != RMPCD_OK) return st;
     }
     sys->has_sort = false;
@@ -979,7 +980,7 @@ static int launch_interval(rmpcd_system *sys, int cur, int bcur, bool instrument
     }
     if (sys->any_body) {
         if (instrument) tstart(sys, &ev);
-        launch_md_body(sys->mixed, sys->d, sys->nb_max, STEP_DEVICE, cur, bcur, 1, sys->stream);
+        launch_md_body(sys->mixed, sys->d, sys->nb_max, sys->grid_room, STEP_DEVICE, cur, bcur, 1, sys->stream);
         if (instrument) tstop(sys, 1, ev);
         n += 1;
     }
@@ -1261,6 +1262,7 @@ static rmpcd_status upload_bodies(rmpcd_system *sys)
     std::vector<int> bc, gs;
     std::vector<unsigned short> gl;
     sys->nb_max = 0;
+    long long grid_entries = 0;
     for (auto &H : sys->bodies) {
         if (H.beads.empty()) continue;
         H.dev.bead_off = (int)bc.size();
@@ -1277,7 +1279,13 @@ static rmpcd_status upload_bodies(rmpcd_system *sys)
         gs.insert(gs.end(), H.gstart.begin(), H.gstart.end());
         gl.insert(gl.end(), H.glist.begin(), H.glist.end());
         sys->nb_max = std::max(sys->nb_max, H.dev.nb);
+        grid_entries = std::max(grid_entries, (long long)(H.gstart.size() + H.glist.size()));
     }
+    // 16-bit offsets in shared memory need every list below 65536 entries
+    bool small = true;
+    for (auto &H : sys->bodies)
+        if (!H.beads.empty() && H.glist.size() >= 65536) small = false;
+    sys->grid_room = small ? md_body_grid_room(sys->mixed, sys->nb_max, grid_entries) : 0;
     CK(cudaStreamSynchronize(sys->stream));
     for (void *p : sys->body_allocs) cudaFree(p);
     sys->body_allocs.clear();
@@ -1418,7 +1426,7 @@ rmpcd_status rmpcd_set_body(rmpcd_system *sys, int32_t replica, const rmpcd_body
         sys->d.md_work = w;
         sys->work_bytes = need;
     }
-    CK(prepare_md_body(sys->mixed, sys->nb_max));
+    CK(prepare_md_body(sys->mixed, sys->nb_max, sys->grid_room));
     sys->any_body = true;
     CK(cudaStreamSynchronize(s));
     return RMPCD_OK;

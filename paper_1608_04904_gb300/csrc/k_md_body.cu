@@ -83,6 +83,8 @@ struct BodyShared {
     int gn, nb, nn;
     const int *gstart;
     const unsigned short *glist;
+    const unsigned short *gs16, *gl16;   // the lookup grid copied to shared memory (gsm: in use)
+    int gsm;
     unsigned long long wpart[MDB_NW][6];
 };
 
@@ -333,8 +335,13 @@ __device__ __forceinline__ void grid_range(const BodyShared &S, const float dc[3
     }
     if (in) {
         const int cell = id[0] + S.gn * (id[1] + S.gn * id[2]);
-        beg = __ldg(S.gstart + cell);
-        end = __ldg(S.gstart + cell + 1);
+        if (S.gsm) {
+            beg = S.gs16[cell];
+            end = S.gs16[cell + 1];
+        } else {
+            beg = __ldg(S.gstart + cell);
+            end = __ldg(S.gstart + cell + 1);
+        }
     }
 }
 
@@ -362,10 +369,11 @@ __device__ __forceinline__ bool body_force_m(const ReplicaDev &rp, const BodySha
     f[0] = f[1] = f[2] = 0.0f;
     bool inside = false;
     const int isb = (fid & F_B) ? 1 : 0;
-    int jn = beg < end ? __ldg(S.glist + beg) : 0;
+    const unsigned short *gl = S.gsm ? S.gl16 : S.glist;
+    int jn = beg < end ? gl[beg] : 0;
     for (int e = beg; e < end; ++e) {
         const int j = jn;
-        if (e + 1 < end) jn = __ldg(S.glist + e + 1);   // next index in flight during this pair
+        if (e + 1 < end) jn = gl[e + 1];   // next index in flight during this pair
         const float rb[3] = {B.rbf[3 * j], B.rbf[3 * j + 1], B.rbf[3 * j + 2]};
         const float d[3] = {dc[0] - rb[0], dc[1] - rb[1], dc[2] - rb[2]};
         const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -395,10 +403,11 @@ __device__ __forceinline__ bool body_force_d(const ReplicaDev &rp, const BodySha
     f[0] = f[1] = f[2] = 0.0;
     bool inside = false;
     const int isb = (fid & F_B) ? 1 : 0;
-    int jn = beg < end ? __ldg(S.glist + beg) : 0;
+    const unsigned short *gl = S.gsm ? S.gl16 : S.glist;
+    int jn = beg < end ? gl[beg] : 0;
     for (int e = beg; e < end; ++e) {
         const int j = jn;
-        if (e + 1 < end) jn = __ldg(S.glist + e + 1);
+        if (e + 1 < end) jn = gl[e + 1];
         double d[3] = {x[0] - B.Xb[3 * j], x[1] - B.Xb[3 * j + 1], x[2] - B.Xb[3 * j + 2]};
         min_image(rp, d);
         const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -470,8 +479,11 @@ __device__ __forceinline__ void finish_m(const Dev &d, const ReplicaDev &rp, int
     if (do_bin) bin_particle(d, bbuf, rp.cell_off + cell_key_m(rp, c, w.o, sf), slot);
 }
 
+// gsm_bytes: room for the lookup grid at the start of the dynamic shared
+// memory, ahead of the bead arrays (0: the grid is read from global memory).
 template <bool MIXED>
-__global__ void __launch_bounds__(MDB_NT, 2) k_md_body(Dev d, uint32_t step, int rbuf, int bbuf, int do_bin)
+__global__ void __launch_bounds__(MDB_NT, 2) k_md_body(Dev d, uint32_t step, int rbuf, int bbuf, int do_bin,
+                                                       int gsm_bytes)
 {
     step = resolve_step(d, step);   // STEP_DEVICE: the step of the control block
     using W = typename std::conditional<MIXED, BWorkM, BWorkD>::type;
@@ -507,7 +519,24 @@ __global__ void __launch_bounds__(MDB_NT, 2) k_md_body(Dev d, uint32_t step, int
     }
     __syncthreads();
     const int nb = S.nb, nn = S.nn;
-    const BeadSmem B = bead_layout<MIXED>(bead_raw, nb);
+    const BeadSmem B = bead_layout<MIXED>(bead_raw + gsm_bytes, nb);
+    {
+        // the lookup grid into shared memory when it fits the room reserved
+        const int ncell = S.gn * S.gn * S.gn + 1;
+        const int nlist = __ldg(S.gstart + ncell - 1);
+        const bool fits = gsm_bytes > 0 && 2 * (ncell + nlist) <= gsm_bytes;
+        unsigned short *gs = reinterpret_cast<unsigned short *>(bead_raw);
+        unsigned short *gl = gs + ncell;
+        if (fits) {
+            for (int i = tid; i < ncell; i += MDB_NT) gs[i] = (unsigned short)__ldg(S.gstart + i);
+            for (int i = tid; i < nlist; i += MDB_NT) gl[i] = __ldg(S.glist + i);
+        }
+        if (tid == 0) {
+            S.gsm = fits ? 1 : 0;
+            S.gs16 = gs;
+            S.gl16 = gl;
+        }
+    }
     for (int j = tid; j < nb; j += MDB_NT) {
         const int g = bd.bead_off + j;
         for (int t = 0; t < 3; ++t) B.b[3 * j + t] = d.bead_b[3 * g + t];
@@ -658,24 +687,33 @@ __global__ void __launch_bounds__(MDB_NT, 2) k_md_body(Dev d, uint32_t step, int
     }
 }
 
-size_t md_body_smem(bool mixed, int nb_max)
+size_t md_body_smem(bool mixed, int nb_max, int grid_bytes)
 {
-    return mixed ? bead_smem_bytes<true>(nb_max) : bead_smem_bytes<false>(nb_max);
+    return (size_t)grid_bytes + (mixed ? bead_smem_bytes<true>(nb_max) : bead_smem_bytes<false>(nb_max));
 }
 
-cudaError_t prepare_md_body(bool mixed, int nb_max)
+// Room for the lookup grid in shared memory: the largest body's grid (16-bit
+// offsets and bead indices) when two CTAs still share an SM; else 0.
+int md_body_grid_room(bool mixed, int nb_max, long long grid_entries_max)
 {
-    const int bytes = (int)md_body_smem(mixed, nb_max);
+    const long long bytes = ((2 * grid_entries_max + 15) / 16) * 16;
+    const long long total = bytes + (long long)(mixed ? bead_smem_bytes<true>(nb_max) : bead_smem_bytes<false>(nb_max));
+    return total <= 108 * 1024 ? (int)bytes : 0;
+}
+
+cudaError_t prepare_md_body(bool mixed, int nb_max, int grid_bytes)
+{
+    const int bytes = (int)md_body_smem(mixed, nb_max, grid_bytes);
     if (mixed) return cudaFuncSetAttribute(k_md_body<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     return cudaFuncSetAttribute(k_md_body<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-void launch_md_body(bool mixed, const Dev &d, int nb_max, uint32_t step, int rbuf, int bbuf, int do_bin,
-                    cudaStream_t s)
+void launch_md_body(bool mixed, const Dev &d, int nb_max, int grid_bytes, uint32_t step, int rbuf, int bbuf,
+                    int do_bin, cudaStream_t s)
 {
-    const size_t bytes = md_body_smem(mixed, nb_max);
-    if (mixed) k_md_body<true><<<d.n_rep, MDB_NT, bytes, s>>>(d, step, rbuf, bbuf, do_bin);
-    else k_md_body<false><<<d.n_rep, MDB_NT, bytes, s>>>(d, step, rbuf, bbuf, do_bin);
+    const size_t bytes = md_body_smem(mixed, nb_max, grid_bytes);
+    if (mixed) k_md_body<true><<<d.n_rep, MDB_NT, bytes, s>>>(d, step, rbuf, bbuf, do_bin, grid_bytes);
+    else k_md_body<false><<<d.n_rep, MDB_NT, bytes, s>>>(d, step, rbuf, bbuf, do_bin, grid_bytes);
 }
 
 }  // namespace rmpcd

@@ -51,9 +51,12 @@ int md_wide_grid();
 // Rigid bead bodies: one CTA per replica (replicas without a body return at
 // once); nb_max = the most beads of any body.  prepare_md_body sets the
 // kernel's shared-memory limit for nb_max (not a stream operation).
-void launch_md_body(bool mixed, const Dev &d, int nb_max, uint32_t step, int rbuf, int bbuf, int do_bin,
-                    cudaStream_t s);
-cudaError_t prepare_md_body(bool mixed, int nb_max);
+// grid_bytes: shared-memory room for the lookup grids (md_body_grid_room;
+// 0: read from global memory).
+void launch_md_body(bool mixed, const Dev &d, int nb_max, int grid_bytes, uint32_t step, int rbuf, int bbuf,
+                    int do_bin, cudaStream_t s);
+cudaError_t prepare_md_body(bool mixed, int nb_max, int grid_bytes);
+int md_body_grid_room(bool mixed, int nb_max, long long grid_entries_max);
 void launch_set_state(bool mixed, const Dev &d, int replica, int n, const double *x, const double *v,
                       const uint8_t *flags, int rbuf, cudaStream_t s);
 void launch_get_state(bool mixed, const Dev &d, int replica, int n, int rbuf, double *x, double *v, uint8_t *flags,
