@@ -3,13 +3,14 @@
 // collision, bulk B -> A reaction, and (fused) free flight + binning of every
 // particle for the next collision.
 //
-// One CTA owns a tile of CPT consecutive cells of one replica.  Its particles
-// are the bucket entries of those cells; within a cell they are put back in
-// increasing storage slot order, which makes the sort stable and the result
-// independent of the atomic order in which the buckets were filled.  The
-// tile's first output slot is the exclusive prefix of all earlier tiles'
-// particle counts, found by a single-pass decoupled look-back (Merrill &
-// Garland 2016) over tiles taken in ticket order.
+// The work is cut into tiles of CPT consecutive cells of one replica.  As many
+// CTAs as fit on the GPU run persistently, each taking tiles in ticket order.
+// A tile's particles are the bucket entries of its cells; within a cell they
+// are put back in increasing storage slot order, which makes the sort stable
+// and the result independent of the atomic order in which the buckets were
+// filled.  The tile's first output slot is the exclusive prefix of all
+// earlier tiles' particle counts, found by a single-pass decoupled look-back
+// (Merrill & Garland 2016) over tiles taken in ticket order.
 //
 // The CTA stages the tile's particles (in batches of whole cells when they
 // exceed the staging area) and runs the stages with all its threads: one
@@ -139,7 +140,7 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Per-tile state shared by the groups of one CTA.
+// Per-tile state shared by the threads of one CTA.
 template <bool MIXED>
 struct TileShared {
     using R = typename Traits<MIXED>::R;
@@ -159,8 +160,8 @@ struct TileShared {
     double red[CP_WARPS][8];
 };
 
-// Stage D, one thread per cell, particles summed in sorted order (the same
-// order as the FP64 oracle).
+// Stage D, one thread per cell, particles summed in sorted order (the order
+// of the FP64 definition).
 template <bool MIXED, bool MANY>
 __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, TileShared<MIXED> &T, int gt,
                                                int cb, int ce, int pofs, typename Traits<MIXED>::Rec *srec)
