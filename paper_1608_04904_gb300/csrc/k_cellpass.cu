@@ -40,7 +40,10 @@ template <> struct Traits<false> {
     using Rec = RecD;
     using R = double;
     static constexpr int K = CP_STAGE_D;
-    static constexpr int TP = K * CP_THREADS;
+    // 1408 64-byte records: a whole tile (1280 particles at density 10, the
+    // Poisson tail included) in one batch, with two CTAs per SM
+    static constexpr int TP = 1408;
+    static_assert(TP <= K * CP_THREADS, "each thread stages at most K particles");
 };
 
 // --- per-record helpers ----------------------------------------------------

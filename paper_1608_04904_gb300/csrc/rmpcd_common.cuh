@@ -26,7 +26,7 @@ constexpr int CPT = 128;           // cells per tile of the cell pass
 constexpr int CP_THREADS = 256;    // threads per cell-pass CTA
 constexpr int CP_WARPS = CP_THREADS / 32;
 constexpr int CP_STAGE_M = 6;      // particles a cell-pass thread stages at once (mixed records)
-constexpr int CP_STAGE_D = 3;      // particles a cell-pass thread stages at once (fp64 records)
+constexpr int CP_STAGE_D = 6;      // particles a cell-pass thread stages at once (fp64 records)
 constexpr int CP_MAX_CAP = 768;    // largest bucket_cap (a crowded tile uses the whole CTA)
 constexpr int CP_NEAR_CAND_MIN = 5;   // colloids from which the mixed cell pass filters them per batch
 constexpr int MD_THREADS = 1024;   // threads of the near-field MD CTA (one per replica)
