@@ -17,7 +17,7 @@
  *     asynchronous, except where a call says it synchronises.  Errors raised
  *     by kernels (bucket overflow, skin violation, a look-back that timed out)
  *     are latched on the device and returned by the next synchronising call
- *     (rmpcd_sync, rmpcd_get_state, rmpcd_observables).
+ *     (rmpcd_sync, rmpcd_get_state, rmpcd_observables, rmpcd_profile).
  *   - Host buffers passed in are copied before the call returns (or, for
  *     on_device = 0 outputs, filled before it returns); the library never keeps
  *     a caller's pointer.  All device memory of a system is owned by the
@@ -227,6 +227,36 @@ rmpcd_status rmpcd_step(rmpcd_system *sys, int32_t n_intervals);
 /* Observables of one replica on the grid of the last collision (computed by
  * one extra cell pass over the stored state when requested).  Synchronises. */
 rmpcd_status rmpcd_observables(rmpcd_system *sys, int32_t replica, rmpcd_obs *out);
+
+/* One bin of a slab profile (rmpcd_profile). */
+#define RMPCD_MAX_PROFILE_BINS 512
+typedef struct {
+    int64_t n;             /* solvent particles in the bin                                */
+    int64_t n_B;           /* of which species B                                          */
+    double v_sum[3];       /* sum of v_k over the bin, each term rounded to 2^-32         */
+    double v2_sum[3];      /* sum of v_k^2 over the bin, each term rounded to 2^-24       */
+} rmpcd_profile_bin;
+
+/* Slab profile of one replica's solvent along one axis, for the flow profile
+ * v_x(z) between the walls of a Poiseuille set-up and the slab temperatures and
+ * species concentrations across a thermal or chemical gradient (paper,
+ * §"Applications of RMPCDMD": poiseuille_flow, chemotactic_cell,
+ * single_sphere_thermo_trap; the histogram routine of the `common` module).
+ * The stored state is read as it is (the positions after the last step or
+ * rmpcd_set_state).  Bin b holds the particles with
+ * floor(x_axis * n_bins / L[axis]) == b, clamped to 0..n_bins-1 (a particle at
+ * x = L[2] on a wall axis lands in the last bin).  The sums are fixed point:
+ * every term is rounded to nearest-even on its grid (2^-32 for v_k, 2^-24 for
+ * v_k^2) and summed as a 64-bit integer, so the result does not depend on the
+ * summation order and is the same on every run; it is exact while
+ * |sum v_k| < 2^31 and sum v_k^2 < 2^39 per bin.  Mean flow of a bin:
+ * v_sum / n; slab temperature (mass 1, the bin's mean flow removed):
+ * sum_k (v2_sum[k] - v_sum[k]^2 / n) / (3 (n - 1)).
+ * axis: 0, 1 or 2.  n_bins: 1..RMPCD_MAX_PROFILE_BINS.  out[n_bins]: host
+ * array owned by the caller.  Synchronises.
+ * Errors: EINVAL (bad replica, axis or n_bins, NULL out), ECUDA, and any
+ * latched device error. */
+rmpcd_status rmpcd_profile(rmpcd_system *sys, int32_t replica, int32_t axis, int32_t n_bins, rmpcd_profile_bin *out);
 
 /* Wait for all queued work and return latched device errors. */
 rmpcd_status rmpcd_sync(rmpcd_system *sys);

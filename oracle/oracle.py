@@ -428,3 +428,44 @@ class OracleSystem:
 
     def colloids(self) -> dict:
         return {"x": self.X.copy(), "v": self.V.copy()}
+
+
+# -- slab profile ----------------------------------------------------------------
+def slab_profile(L_axis: int, x_axis, v, flags, n_bins: int) -> dict:
+    """Slab histogram of the solvent along one axis: the flow profile of the
+    Poiseuille set-up, the slab temperatures of the thermal-gradient set-up and
+    the species profile of the chemotactic set-up (§"Applications of RMPCDMD";
+    the histogram routine of the ``common`` module).
+
+    Definition: particle i falls in bin floor(x_i * n_bins / L), clamped to
+    [0, n_bins).  Per bin: the count, the count of species B (flag bit 0), the
+    sum of v_k with every term first rounded (ties to even) to a multiple of
+    2^-32, and the sum of v_k^2 with every term rounded to a multiple of 2^-24.
+    The rounded terms are summed as exact integers."""
+    x = np.asarray(x_axis, np.float64)
+    v = np.asarray(v, np.float64).reshape(-1, 3)
+    fl = np.zeros(len(x), np.uint8) if flags is None else np.asarray(flags, np.uint8)
+    b = np.floor(x * float(n_bins) / float(L_axis))
+    b = np.clip(b, 0, n_bins - 1).astype(np.int64)
+    n = np.bincount(b, minlength=n_bins).astype(np.int64)
+    nB = np.bincount(b, weights=(fl & 1).astype(np.float64), minlength=n_bins).astype(np.int64)
+    s1 = np.zeros((n_bins, 3), np.int64)
+    s2 = np.zeros((n_bins, 3), np.int64)
+    for k in range(3):
+        np.add.at(s1[:, k], b, np.rint(v[:, k] * 2.0 ** 32).astype(np.int64))
+        np.add.at(s2[:, k], b, np.rint(v[:, k] * v[:, k] * 2.0 ** 24).astype(np.int64))
+    return {"n": n, "n_B": nB, "v_sum": s1.astype(np.float64) * 2.0 ** -32,
+            "v2_sum": s2.astype(np.float64) * 2.0 ** -24}
+
+
+def slab_fields(p: dict) -> dict:
+    """Mean flow u_b = v_sum / n and slab temperature (unit mass, the slab's
+    own mean flow removed, N - 1 in the denominator as in the cell estimator
+    of §1.4): T_b = sum_k (v2_sum_k - v_sum_k^2 / n) / (3 (n - 1)).  Bins with
+    fewer than 2 particles give NaN."""
+    n = p["n"].astype(np.float64)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        u = p["v_sum"] / n[:, None]
+        T = (p["v2_sum"] - p["v_sum"] ** 2 / n[:, None]).sum(1) / (3.0 * (n - 1.0))
+    T[n < 2] = np.nan
+    return {"u": u, "T": T, "c_B": np.where(n > 0, p["n_B"] / np.maximum(n, 1), np.nan)}

@@ -66,6 +66,13 @@ class Obs(C.Structure):
                 ("step", C.c_uint32), ("pad", C.c_uint32)]
 
 
+MAX_PROFILE_BINS = 512
+
+
+class ProfileBin(C.Structure):
+    _fields_ = [("n", C.c_int64), ("n_B", C.c_int64), ("v_sum", C.c_double * 3), ("v2_sum", C.c_double * 3)]
+
+
 class Timers(C.Structure):
     _fields_ = [("launches", C.c_int64 * 4), ("ms", C.c_double * 4)]
 
@@ -78,6 +85,7 @@ EXPORTS = [
     "rmpcd_collide", "rmpcd_react", "rmpcd_step", "rmpcd_observables", "rmpcd_sync", "rmpcd_launch_count",
     "rmpcd_last_error", "rmpcd_enable_timers", "rmpcd_read_timers", "rmpcd_set_tuning", "rmpcd_get_tuning",
     "rmpcd_observables_noalloc", "rmpcd_set_graphs", "rmpcd_get_bucket_cap", "rmpcd_set_body", "rmpcd_get_body",
+    "rmpcd_profile",
 ]
 
 _LIB = None
@@ -113,6 +121,7 @@ def load():
         getattr(L, name).argtypes = [vp]
     L.rmpcd_step.argtypes = [vp, i32]
     L.rmpcd_observables.argtypes = [vp, i32, P(Obs)]
+    L.rmpcd_profile.argtypes = [vp, i32, i32, i32, P(ProfileBin)]
     L.rmpcd_launch_count.argtypes = [vp, P(i64)]
     L.rmpcd_enable_timers.argtypes = [vp, i32]
     L.rmpcd_read_timers.argtypes = [vp, P(Timers), i32]
@@ -369,6 +378,18 @@ class System:
         return {"temperature": o.temperature, "momentum": np.array(list(o.momentum)), "kinetic": o.kinetic,
                 "n_cells_used": int(o.n_cells_used), "n_B": int(o.n_B), "n_solvent": int(o.n_solvent),
                 "step": int(o.step)}
+
+    def profile(self, replica=0, axis=2, n_bins=None) -> dict:
+        """rmpcd_profile: per-bin solvent count, B count and fixed-point sums of
+        v_k and v_k^2 along `axis` (n_bins defaults to one bin per cell)."""
+        if n_bins is None:
+            n_bins = int(self.replicas[replica]["cfg"]["L"][axis])
+        out = (ProfileBin * max(int(n_bins), 1))()
+        self._check(self._lib.rmpcd_profile(self._h, replica, int(axis), int(n_bins), out))
+        a = np.frombuffer(out, dtype=np.dtype([("n", "<i8"), ("n_B", "<i8"), ("v_sum", "<f8", 3),
+                                                ("v2_sum", "<f8", 3)]))
+        return {"n": a["n"].copy(), "n_B": a["n_B"].copy(), "v_sum": a["v_sum"].copy(),
+                "v2_sum": a["v2_sum"].copy()}
 
     def enable_timers(self, on=True):
         self._check(self._lib.rmpcd_enable_timers(self._h, 1 if on else 0))

@@ -35,6 +35,7 @@ struct rmpcd_system {
     uint8_t *stage_f = nullptr;
     uint32_t *stage_id = nullptr;
     int32_t *stage_cell = nullptr;
+    unsigned long long *prof_acc = nullptr;   // [PROF_MAX_BINS * PROF_FIELDS] slab-profile sums
     // pipeline state
     uint32_t step = 0;
     int cur = 0;        // record buffer holding the state
@@ -554,6 +555,7 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
     AL(&d.body, n_replicas);
     sys->work_bytes = (sys->mixed ? 64 : 80) * (size_t)(sys->any_colloids ? n_total : 1);
     AL(&work, sys->work_bytes);
+    AL(&sys->prof_acc, (size_t)PROF_MAX_BINS * PROF_FIELDS);
     AL(&sys->stage_x, 3 * (size_t)sys->max_part);
     AL(&sys->stage_v, 3 * (size_t)sys->max_part);
     AL(&sys->stage_f, (size_t)sys->max_part);
@@ -1119,6 +1121,38 @@ rmpcd_status rmpcd_observables(rmpcd_system *sys, int32_t replica, rmpcd_obs *ou
     out->n_B = (int64_t)o[6];
     out->n_solvent = (int64_t)o[7];
     out->step = sys->sort_step;
+    return st;
+}
+
+static_assert(RMPCD_MAX_PROFILE_BINS <= PROF_MAX_BINS, "profile bins exceed the kernel's shared sums");
+
+rmpcd_status rmpcd_profile(rmpcd_system *sys, int32_t replica, int32_t axis, int32_t n_bins, rmpcd_profile_bin *out)
+{
+    if (!sys || !out) return RMPCD_EINVAL;
+    if (replica < 0 || replica >= sys->n_rep) return fail(sys, RMPCD_EINVAL, "replica %d out of range", replica);
+    if (axis < 0 || axis > 2) return fail(sys, RMPCD_EINVAL, "axis %d is not 0, 1 or 2", axis);
+    if (n_bins < 1 || n_bins > RMPCD_MAX_PROFILE_BINS)
+        return fail(sys, RMPCD_EINVAL, "n_bins %d outside 1..%d", n_bins, RMPCD_MAX_PROFILE_BINS);
+    const size_t words = (size_t)n_bins * PROF_FIELDS;
+    CK(cudaMemsetAsync(sys->prof_acc, 0, words * sizeof(unsigned long long), sys->stream));
+    launch_profile(sys->mixed, sys->d, replica, sys->rep[replica].n_part, sys->cur, axis, n_bins, sys->prof_acc,
+                   sys->stream);
+    rmpcd_status st = after_launch(sys, 1);
+    if (st != RMPCD_OK) return st;
+    std::vector<unsigned long long> h(words);
+    CK(cudaMemcpyAsync(h.data(), sys->prof_acc, words * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       sys->stream));
+    st = check_errors(sys);   // synchronises
+    for (int b = 0; b < n_bins; ++b) {
+        const unsigned long long *a = h.data() + (size_t)b * PROF_FIELDS;
+        rmpcd_profile_bin &o = out[b];
+        o.n = (int64_t)a[0];
+        o.n_B = (int64_t)a[1];
+        for (int k = 0; k < 3; ++k) {
+            o.v_sum[k] = (double)(long long)a[2 + k] * 0x1p-32;
+            o.v2_sum[k] = (double)(long long)a[5 + k] * 0x1p-24;
+        }
+    }
     return st;
 }
 

@@ -198,6 +198,51 @@ __global__ void k_obs_reduce(Dev d)
     if (tid < 8) d.obs_out[r * 8 + tid] = part[0][tid];
 }
 
+// Slab profile of one replica along one axis (the flow profile of the
+// Poiseuille set-up and the slab temperatures of the thermal-gradient set-up,
+// §"Applications of RMPCDMD"; the histogram routine of the `common` module).
+// Bin b = floor(x_axis * n_bins / L_axis), clamped to [0, n_bins).  Per bin:
+// count, B count, sum v_k in units of 2^-32 and sum v_k^2 in units of 2^-24,
+// each term rounded to nearest-even before the integer sum, so the result is
+// exact and independent of the summation order.  Integer sums wrap modulo
+// 2^64; only the final value must fit (|sum v_k| < 2^31, sum v_k^2 < 2^39).
+template <bool MIXED>
+__global__ void __launch_bounds__(256) k_profile(Dev d, int r, int rbuf, int axis, int n_bins, unsigned long long *acc)
+{
+    __shared__ unsigned long long sh[PROF_MAX_BINS * PROF_FIELDS];
+    for (int k = threadIdx.x; k < n_bins * PROF_FIELDS; k += blockDim.x) sh[k] = 0ull;
+    __syncthreads();
+    const ReplicaDev &rp = d.rep[r];
+    const double nb = (double)n_bins, len = (double)rp.L[axis];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rp.n_part; i += gridDim.x * blockDim.x) {
+        double x, v[3];
+        uint32_t fid;
+        if (MIXED) {
+            RecM rec = load_rec(reinterpret_cast<const RecM *>(d.rec[rbuf]) + rp.part_off + i);
+            x = (double)cw_get(rec.cw, axis) + (double)rec.o[axis];
+            for (int k = 0; k < 3; ++k) v[k] = (double)rec.v[k];
+            fid = rec.fid;
+        } else {
+            RecD rec = load_rec(reinterpret_cast<const RecD *>(d.rec[rbuf]) + rp.part_off + i);
+            x = rec.x[axis];
+            for (int k = 0; k < 3; ++k) v[k] = rec.v[k];
+            fid = rec.fid;
+        }
+        int b = (int)floor(x * nb / len);
+        b = b < 0 ? 0 : (b > n_bins - 1 ? n_bins - 1 : b);
+        unsigned long long *s = sh + PROF_FIELDS * b;
+        atomicAdd(s, 1ull);
+        if (fid & F_B) atomicAdd(s + 1, 1ull);
+        for (int k = 0; k < 3; ++k) {
+            atomicAdd(s + 2 + k, (unsigned long long)__double2ll_rn(v[k] * 0x1p32));
+            atomicAdd(s + 5 + k, (unsigned long long)__double2ll_rn(v[k] * v[k] * 0x1p24));
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_bins * PROF_FIELDS; k += blockDim.x)
+        if (sh[k]) atomicAdd(acc + k, sh[k]);
+}
+
 __global__ void k_set_step(Dev d, uint32_t step) { d.ctl->step = step; }
 
 // Largest count of count buffer b (bucket-width tuner).
@@ -244,6 +289,18 @@ void launch_particles(bool mixed, const Dev &d, int mode, uint32_t step, int rbu
     int nb = (d.n_total + 255) / 256;
     if (mixed) k_particles<true><<<nb, 256, 0, s>>>(d, mode, step, rbuf, bbuf);
     else k_particles<false><<<nb, 256, 0, s>>>(d, mode, step, rbuf, bbuf);
+}
+
+void launch_profile(bool mixed, const Dev &d, int replica, int n, int rbuf, int axis, int n_bins,
+                    unsigned long long *acc, cudaStream_t s)
+{
+    if (n <= 0) return;
+    // one pass over the replica; a few CTAs per SM so each bin's shared
+    // partials are merged into the global sums only once per CTA
+    int nb = (n + 255) / 256;
+    if (nb > 4 * 152) nb = 4 * 152;
+    if (mixed) k_profile<true><<<nb, 256, 0, s>>>(d, replica, rbuf, axis, n_bins, acc);
+    else k_profile<false><<<nb, 256, 0, s>>>(d, replica, rbuf, axis, n_bins, acc);
 }
 
 void launch_obs_reduce(const Dev &d, cudaStream_t s)

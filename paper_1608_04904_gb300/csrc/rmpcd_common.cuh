@@ -23,6 +23,8 @@
 namespace rmpcd {
 
 constexpr int CPT = 128;           // cells per tile of the cell pass
+constexpr int PROF_MAX_BINS = 512; // most bins of one slab profile
+constexpr int PROF_FIELDS = 8;     // count, B count, sum v_k (3), sum v_k^2 (3)
 constexpr int CP_THREADS = 256;    // threads per cell-pass CTA
 constexpr int CP_WARPS = CP_THREADS / 32;
 constexpr int CP_STAGE_M = 6;      // particles a cell-pass thread stages at once (mixed records)

@@ -62,6 +62,9 @@ void launch_set_state(bool mixed, const Dev &d, int replica, int n, const double
 void launch_get_state(bool mixed, const Dev &d, int replica, int n, int rbuf, double *x, double *v, uint8_t *flags,
                       uint32_t *id, int32_t *cell, int has_sort, uint32_t sort_step, cudaStream_t s);
 void launch_obs_reduce(const Dev &d, cudaStream_t s);
+// Slab profile of one replica (n particles) into acc[n_bins * PROF_FIELDS] (zeroed by the caller).
+void launch_profile(bool mixed, const Dev &d, int replica, int n, int rbuf, int axis, int n_bins,
+                    unsigned long long *acc, cudaStream_t s);
 size_t cellpass_smem(bool mixed);
 
 }  // namespace rmpcd
