@@ -66,17 +66,26 @@ struct FShared {
     int cat[NC];
     int nn;
     int dead;                            // an exchange timed out: stop waiting
+    int pCi[NC][3];                      // colloid positions of the round (warp 0 writes them):
+    float pXf[NC][3];                    //   mixed, cell + offset
+    double pXw[NC][3];                   //   FP64, wrapped
 };
 
-// --- colloid state, lane-parallel ---------------------------------------------
-// Lane l < 3 nc holds colloid j = l / 3, axis t = l % 3; the bond of a dimer
-// always joins colloids 0 and 1, so the other end of a lane's component is
-// lane l +- 3.  Lanes >= 3 nc carry copies that are never stored.
-struct LaneM {   // integer cell + FP32 offset in [0,1) (mixed path)
-    int Xi, Ci, Xoi, X0i;
-    float Xf, Xof, X0f, V, F, invM;
+// --- colloid state ------------------------------------------------------------
+// Mixed path: every lane holds the whole colloid state (both colloids, all
+// axes) and integrates it itself, so no shuffle sits on the colloid chain and
+// the particles read the colloid positions from registers.  The operations
+// and their order are those of the general MD kernel, component by component,
+// so both kernels give bit-identical results.
+struct ColM {    // integer cell + FP32 offset in [0,1)
+    int Xi[NC][3], Ci[NC][3];
+    float Xf[NC][3], V[NC][3];
+    float invM[NC];
 };
-struct LaneD {   // unwrapped FP64 position (fp64 path)
+// FP64 path: lane l < 3 nc holds colloid j = l / 3, axis t = l % 3; the bond
+// of a dimer always joins colloids 0 and 1, so the other end of a lane's
+// component is lane l +- 3.  Lanes >= 3 nc carry copies that are never stored.
+struct LaneD {   // unwrapped FP64 position
     double X, V, F, Xold, X0, Xw, M;
 };
 
@@ -91,41 +100,31 @@ __device__ __forceinline__ double sum3(double a)
     return (__shfl_sync(0xffffffffu, a, 0) + __shfl_sync(0xffffffffu, a, 1)) + __shfl_sync(0xffffffffu, a, 2);
 }
 
-// Carry of the FP32 offset into the integer cell.  The offset stays within
-// (-1, 2) in practice, where floor() is -1, 0 or 1 and is found by compares
-// (the same f = x - floor(x) as the general case, signed zero included).
-__device__ __forceinline__ void carry(const ReplicaDev &rp, LaneM &C, int t)
+// Carry of the FP32 offset into the integer cell: f = x - floor(x) (signed
+// zero included), k = floor(x), with no branch, so that the carries of the
+// six components overlap.  The wrapped cell moves one box length up or down
+// by selects; a colloid that crossed more than a box length in one sub-step
+// is left out of [0, L) here and put back by wrap_cells.
+__device__ __forceinline__ void carry(const ReplicaDev &rp, int &Xi, int &Ci, float &Xf, int t)
 {
-    const float x = C.Xf;
-    float fl;
-    int k;
-    if (fabsf(x - 0.5f) < 1.5f) {
-        fl = x >= 1.0f ? 1.0f : (x < 0.0f ? -1.0f : copysignf(0.0f, x));
-        k = x >= 1.0f ? 1 : (x < 0.0f ? -1 : 0);
-    } else {
-        fl = floorf(x);
-        k = (int)fl;
-    }
+    const float x = Xf;
+    const float fl = floorf(x);
+    int k = (int)fl;
     float f = x - fl;
-    if (f >= 1.0f) { f = 0.0f; k += 1; }
-    C.Xf = f;
-    C.Xi += k;
-    int ci = C.Ci + k;
-    if (ci >= rp.L[t] || ci < 0) ci = imod(ci, rp.L[t]);
-    C.Ci = ci;
+    const bool one = f >= 1.0f;
+    f = one ? 0.0f : f;
+    k += one ? 1 : 0;
+    Xf = f;
+    Xi += k;
+    const int L = rp.L[t];
+    int ci = Ci + k;
+    ci = ci < 0 ? ci + L : ci;
+    ci = ci >= L ? ci - L : ci;
+    Ci = ci;
 }
 
-__device__ __forceinline__ void set_force(LaneM &C, long long tot) { C.F = fixed40_to_float(tot); }
 __device__ __forceinline__ void set_force(LaneD &C, long long tot) { C.F = (double)tot * 0x1p-40; }
 
-__device__ __forceinline__ void kick_drift(const ReplicaDev &rp, LaneM &C, int t)
-{
-    C.V = fmaf(rp.hdt_f, C.F * C.invM, C.V);
-    C.Xoi = C.Xi;
-    C.Xof = C.Xf;
-    C.Xf = fmaf(rp.dt_f, C.V, C.Xf);
-    carry(rp, C, t);
-}
 __device__ __forceinline__ void kick_drift(const ReplicaDev &rp, LaneD &C, int)
 {
     C.V = fma(rp.hdt, C.F / C.M, C.V);
@@ -133,19 +132,79 @@ __device__ __forceinline__ void kick_drift(const ReplicaDev &rp, LaneD &C, int)
     C.X = fma(rp.dt, C.V, C.X);
 }
 
-// Exact RATTLE position stage (Andersen 1983) for the bond 0-1 of length dd.
-// a_end: this lane belongs to colloid 0 (the bond's first end).
-__device__ __forceinline__ void rattle_pos(const ReplicaDev &rp, LaneM &C, int t, float dd, float idt, bool a_end,
-                                           int other)
+// Wrapped cells back in [0, L) after a sub-step that moved a colloid by more
+// than a box length (one uniform branch per update, never taken in practice).
+__device__ __forceinline__ void wrap_cells(const ReplicaDev &rp, ColM &C)
 {
-    const int oXoi = __shfl_sync(0xffffffffu, C.Xoi, other), oXi = __shfl_sync(0xffffffffu, C.Xi, other);
-    const float oXof = __shfl_sync(0xffffffffu, C.Xof, other), oXf = __shfl_sync(0xffffffffu, C.Xf, other);
-    const float oinvM = __shfl_sync(0xffffffffu, C.invM, other);
-    const float ro = a_end ? (float)(C.Xoi - oXoi) + (C.Xof - oXof) : (float)(oXoi - C.Xoi) + (oXof - C.Xof);
-    const float rn = a_end ? (float)(C.Xi - oXi) + (C.Xf - oXf) : (float)(oXi - C.Xi) + (oXf - C.Xf);
-    const float ia = a_end ? C.invM : oinvM, ib = a_end ? oinvM : C.invM;
+    bool out = false;
+#pragma unroll
+    for (int j = 0; j < NC; ++j)
+#pragma unroll
+        for (int t = 0; t < 3; ++t) out = out || (unsigned)C.Ci[j][t] >= (unsigned)rp.L[t];
+    if (out)
+#pragma unroll
+        for (int j = 0; j < NC; ++j)
+#pragma unroll
+            for (int t = 0; t < 3; ++t) C.Ci[j][t] = imod(C.Ci[j][t], rp.L[t]);
+}
+
+// Mixed path, whole state per lane.  Second half kick and RATTLE velocity
+// stage of the bond 0-1 (Andersen 1983).
+__device__ __forceinline__ void col_kick_rattle_vel(const ReplicaDev &rp, ColM &C, const float F[NC][3], int nc,
+                                                    int nbond)
+{
+    // (with one colloid, slot 1 holds a copy that is integrated but never used)
+#pragma unroll
+    for (int j = 0; j < NC; ++j)
+#pragma unroll
+        for (int t = 0; t < 3; ++t) C.V[j][t] = fmaf(rp.hdt_f, F[j][t] * C.invM[j], C.V[j][t]);
+    if (nbond == 0) return;
+    float r[3], dv[3];
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        r[t] = (float)(C.Xi[0][t] - C.Xi[1][t]) + (C.Xf[0][t] - C.Xf[1][t]);
+        dv[t] = C.V[0][t] - C.V[1][t];
+    }
+    const float ia = C.invM[0], ib = C.invM[1];
     const float inv = ia + ib;
-    const float oo = sum3(ro * ro), on = sum3(rn * ro), nn = sum3(rn * rn);
+    const float rr = (r[0] * r[0] + r[1] * r[1]) + r[2] * r[2];
+    const float rv = (dv[0] * r[0] + dv[1] * r[1]) + dv[2] * r[2];
+    const float kk = fdiv_m(rv, rr * inv);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        C.V[0][t] -= kk * r[t] * ia;
+        C.V[1][t] += kk * r[t] * ib;
+    }
+}
+
+// First half kick, drift and exact RATTLE position stage (bond length dd).
+__device__ __forceinline__ void col_kick_drift_rattle(const ReplicaDev &rp, ColM &C, const float F[NC][3], int nc,
+                                                      int nbond, float dd, float idt)
+{
+    int Xoi[NC][3];
+    float Xof[NC][3];
+#pragma unroll
+    for (int j = 0; j < NC; ++j)
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            C.V[j][t] = fmaf(rp.hdt_f, F[j][t] * C.invM[j], C.V[j][t]);
+            Xoi[j][t] = C.Xi[j][t];
+            Xof[j][t] = C.Xf[j][t];
+            C.Xf[j][t] = fmaf(rp.dt_f, C.V[j][t], C.Xf[j][t]);
+            carry(rp, C.Xi[j][t], C.Ci[j][t], C.Xf[j][t], t);
+        }
+    if (nbond == 0) { wrap_cells(rp, C); return; }
+    float ro[3], rn[3];
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        ro[t] = (float)(Xoi[0][t] - Xoi[1][t]) + (Xof[0][t] - Xof[1][t]);
+        rn[t] = (float)(C.Xi[0][t] - C.Xi[1][t]) + (C.Xf[0][t] - C.Xf[1][t]);
+    }
+    const float ia = C.invM[0], ib = C.invM[1];
+    const float inv = ia + ib;
+    const float oo = (ro[0] * ro[0] + ro[1] * ro[1]) + ro[2] * ro[2];
+    const float on = (rn[0] * ro[0] + rn[1] * ro[1]) + rn[2] * ro[2];
+    const float nn = (rn[0] * rn[0] + rn[1] * rn[1]) + rn[2] * rn[2];
     const float qa = inv * inv * oo;
     const float qb = 2.0f * inv * on;
     const float qc = nn - dd * dd;
@@ -153,17 +212,22 @@ __device__ __forceinline__ void rattle_pos(const ReplicaDev &rp, LaneM &C, int t
     if (disc < 0.0f) disc = 0.0f;
     const float q = -0.5f * (qb + copysignf(sqrtf(disc), qb));
     const float gmul = fdiv_m(qc, q);
-    if (a_end) {
-        const float ca = gmul * ro * ia;
-        C.Xf += ca;
-        C.V += ca * idt;
-    } else {
-        const float cb = gmul * ro * ib;
-        C.Xf -= cb;
-        C.V -= cb * idt;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        const float ca = gmul * ro[t] * ia;
+        C.Xf[0][t] += ca;
+        C.V[0][t] += ca * idt;
+        carry(rp, C.Xi[0][t], C.Ci[0][t], C.Xf[0][t], t);
+        const float cb = gmul * ro[t] * ib;
+        C.Xf[1][t] -= cb;
+        C.V[1][t] -= cb * idt;
+        carry(rp, C.Xi[1][t], C.Ci[1][t], C.Xf[1][t], t);
     }
-    carry(rp, C, t);
+    wrap_cells(rp, C);
 }
+
+// FP64 path, lane-parallel: exact RATTLE position stage for the bond 0-1.
+// a_end: this lane belongs to colloid 0 (the bond's first end).
 __device__ __forceinline__ void rattle_pos(const ReplicaDev &rp, LaneD &C, int, double dd, double, bool a_end,
                                            int other)
 {
@@ -192,23 +256,7 @@ __device__ __forceinline__ void rattle_pos(const ReplicaDev &rp, LaneD &C, int, 
     }
 }
 
-// Second half kick and RATTLE velocity stage.
-__device__ __forceinline__ void kick_rattle_vel(const ReplicaDev &rp, LaneM &C, int nbond, bool a_end, int other)
-{
-    C.V = fmaf(rp.hdt_f, C.F * C.invM, C.V);
-    if (nbond == 0) return;
-    const int oXi = __shfl_sync(0xffffffffu, C.Xi, other);
-    const float oXf = __shfl_sync(0xffffffffu, C.Xf, other), oV = __shfl_sync(0xffffffffu, C.V, other);
-    const float oinvM = __shfl_sync(0xffffffffu, C.invM, other);
-    const float r = a_end ? (float)(C.Xi - oXi) + (C.Xf - oXf) : (float)(oXi - C.Xi) + (oXf - C.Xf);
-    const float dv = a_end ? C.V - oV : oV - C.V;
-    const float ia = a_end ? C.invM : oinvM, ib = a_end ? oinvM : C.invM;
-    const float inv = ia + ib;
-    const float rr = sum3(r * r), rv = sum3(dv * r);
-    const float kk = fdiv_m(rv, rr * inv);
-    if (a_end) C.V -= kk * r * ia;
-    else C.V += kk * r * ib;
-}
+// FP64 path: second half kick and RATTLE velocity stage.
 __device__ __forceinline__ void kick_rattle_vel(const ReplicaDev &rp, LaneD &C, int nbond, bool a_end, int other)
 {
     C.V = fma(rp.hdt, C.F / C.M, C.V);
@@ -225,14 +273,13 @@ __device__ __forceinline__ void kick_rattle_vel(const ReplicaDev &rp, LaneD &C, 
     else C.V = C.V + kk * r / Mb;
 }
 
-__device__ __forceinline__ void frames(const ReplicaDev &, LaneM &, int) {}
 __device__ __forceinline__ void frames(const ReplicaDev &rp, LaneD &C, int t)
 {
     const double L = (double)rp.L[t];
     C.Xw = C.X - L * floor(C.X / L);
 }
 
-// --- colloid positions seen by the particles ------------------------------------
+// --- colloid positions seen by the particles (FP64 path) --------------------------
 struct ColPM {
     int Ci[NC][3];
     float Xf[NC][3];
@@ -240,22 +287,38 @@ struct ColPM {
 struct ColPD {
     double Xw[NC][3];
 };
-__device__ __forceinline__ void broadcast(const LaneM &C, ColPM &P)
+__device__ __forceinline__ void read_positions(const FShared &S, ColPM &P)
 {
 #pragma unroll
     for (int j = 0; j < NC; ++j)
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
-            P.Ci[j][t] = __shfl_sync(0xffffffffu, C.Ci, 3 * j + t);
-            P.Xf[j][t] = __shfl_sync(0xffffffffu, C.Xf, 3 * j + t);
+            P.Ci[j][t] = S.pCi[j][t];
+            P.Xf[j][t] = S.pXf[j][t];
         }
 }
-__device__ __forceinline__ void broadcast(const LaneD &C, ColPD &P)
+__device__ __forceinline__ void read_positions(const FShared &S, ColPD &P)
 {
 #pragma unroll
     for (int j = 0; j < NC; ++j)
 #pragma unroll
-        for (int t = 0; t < 3; ++t) P.Xw[j][t] = __shfl_sync(0xffffffffu, C.Xw, 3 * j + t);
+        for (int t = 0; t < 3; ++t) P.Xw[j][t] = S.pXw[j][t];
+}
+// Warp 0: the colloid positions of the next round for every warp of the CTA.
+__device__ __forceinline__ void write_positions(FShared &S, const ColM &C, const LaneD &, int lane)
+{
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < NC; ++j)
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                S.pCi[j][t] = C.Ci[j][t];
+                S.pXf[j][t] = C.Xf[j][t];
+            }
+}
+__device__ __forceinline__ void write_positions_d(FShared &S, const LaneD &C, int lane)
+{
+    if (lane < 3 * NC) S.pXw[lane / 3][lane % 3] = C.Xw;
 }
 
 // --- particle side ----------------------------------------------------------
@@ -276,7 +339,36 @@ __device__ __forceinline__ long long fx40(float f)
 // catalytic colloid (§1.5).  Both colloids are evaluated without branches so
 // that their dependency chains overlap; a colloid out of range contributes
 // nothing (selects, so the sums are the same as with a branch).
-__device__ __forceinline__ void pforce(const ReplicaDev &rp, const FShared &S, const ColPM &C, int nc, FWorkM &w,
+// Per-replica constants of the mixed particle force, held in registers for
+// the whole interval (shared memory would be re-read after every barrier).
+struct PConstM {
+    float sig[NC], epsA[NC], epsB[NC], rc2[NC];
+    bool cat[NC];
+    float L[3], hL[3], g[3];
+    bool wrap_z;   // z periodic (no walls)
+    int nc;
+};
+__device__ __forceinline__ void load_pconst(const ReplicaDev &rp, const FShared &S, PConstM &K)
+{
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        K.sig[j] = S.sigf[j];
+        K.epsA[j] = S.epsAf[j];
+        K.epsB[j] = S.epsBf[j];
+        K.rc2[j] = S.rc2f[j];
+        K.cat[j] = S.cat[j] != 0;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        K.L[k] = (float)rp.L[k];
+        K.hL[k] = 0.5f * K.L[k];
+        K.g[k] = rp.g_f[k];
+    }
+    K.wrap_z = !rp.walls;
+    K.nc = rp.n_col;
+}
+
+__device__ __forceinline__ void pforce(const ReplicaDev &, const PConstM &K, const ColPM &C, int, FWorkM &w,
                                        long long acc[NC][3], bool &inside)
 {
     float d[NC][3], fr[NC];
@@ -284,14 +376,19 @@ __device__ __forceinline__ void pforce(const ReplicaDev &rp, const FShared &S, c
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) d[j][k] = (float)(w.c[k] - C.Ci[j][k]) + (w.o[k] - C.Xf[j][k]);
-        min_image(rp, d[j]);
-        const float eps = (w.fid & F_B) ? S.epsBf[j] : S.epsAf[j];
+        for (int k = 0; k < 3; ++k) {
+            const float dk = (float)(w.c[k] - C.Ci[j][k]) + (w.o[k] - C.Xf[j][k]);
+            // minimum image by selects (periodic axes)
+            float m = dk > K.hL[k] ? dk - K.L[k] : dk;
+            m = dk < -K.hL[k] ? dk + K.L[k] : m;
+            d[j][k] = (k < 2 || K.wrap_z) ? m : dk;
+        }
+        const float eps = (w.fid & F_B) ? K.epsB[j] : K.epsA[j];
         const float r2 = d[j][0] * d[j][0] + d[j][1] * d[j][1] + d[j][2] * d[j][2];
-        in[j] = j < nc && r2 < S.rc2f[j];
-        fr[j] = wca_fr_m(eps, S.sigf[j], r2);
+        in[j] = j < K.nc && r2 < K.rc2[j];
+        fr[j] = wca_fr_m(eps, K.sig[j], r2);
     }
-    inside = (in[0] && S.cat[0]) || (in[1] && S.cat[1]);
+    inside = (in[0] && K.cat[0]) || (in[1] && K.cat[1]);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         float f = 0.0f;
@@ -301,7 +398,7 @@ __device__ __forceinline__ void pforce(const ReplicaDev &rp, const FShared &S, c
             f = in[j] ? f + fk : f;
             acc[j][k] -= in[j] ? fx40(fk) : 0ll;
         }
-        w.f[k] = f + rp.g_f[k];
+        w.f[k] = f + K.g[k];
     }
 }
 
@@ -406,12 +503,12 @@ __device__ __forceinline__ void load_particle(const Dev &d, int slot, int rbuf, 
 // One round of one particle: the force at its current position (round > 0:
 // then the catalytic test of sub-step round - 1), and, unless this was the
 // last round, the move to its position of the next round.
-template <typename ColT, typename W>
-__device__ __forceinline__ void round_particle(const ReplicaDev &rp, const FShared &S, const ColT &P, int nc, W &w,
+template <typename KT, typename ColT, typename W>
+__device__ __forceinline__ void round_particle(const ReplicaDev &rp, const KT &K, const ColT &P, int nc, W &w,
                                                long long acc[NC][3], uint32_t step, int round, int n_md)
 {
     bool inside;
-    pforce(rp, S, P, nc, w, acc, inside);
+    pforce(rp, K, P, nc, w, acc, inside);
     if (round > 0) w.fid = fcatalysis(rp, w.fid, inside, step, round - 1);
     if (round < n_md) pkick_drift(rp, w, round > 0);
 }
@@ -518,13 +615,42 @@ __device__ __forceinline__ void send_partials(FShared &S, int rank, int b, int l
     }
 }
 
+// Every warp waits for the partials of round `round` (parity b) from every
+// CTA of the cluster and sums them in rank order (lane l < 6: component l).
+// Without a cluster the CTA's own sum `tot` is the total.
+template <int CS>
+__device__ __forceinline__ long long exchange_partials(const Dev &d, FShared &S, int b, int round, int lane,
+                                                       long long tot)
+{
+    if constexpr (CS > 1) {
+        const uint32_t bar = smem_addr(&S.mbar[b]);
+        const unsigned parity = (unsigned)(round >> 1) & 1u;
+        if (!S.dead) {
+            int spins = 0;
+            while (!mbar_try_wait_cluster(bar, parity)) {
+                if (++spins > MDF_SPIN_LIMIT) {
+                    if (lane == 0) {
+                        atomicOr(&d.err[ERR_TIMEOUT], 1u);
+                        S.dead = 1;
+                    }
+                    break;
+                }
+            }
+            __syncwarp();
+        }
+        tot = 0;
+        if (lane < 3 * NC)
+#pragma unroll
+            for (int q = 0; q < CS; ++q) tot += (long long)S.part[b][q][lane];
+    }
+    return tot;
+}
+
 template <bool MIXED, int CS>
 __global__ void __launch_bounds__(MDF_NT, 1) k_md_fast(Dev d, uint32_t step, int rbuf, int bbuf, int do_bin)
 {
     step = resolve_step(d, step);   // STEP_DEVICE: the step of the control block
     using W = typename std::conditional<MIXED, FWorkM, FWorkD>::type;
-    using Lane = typename std::conditional<MIXED, LaneM, LaneD>::type;
-    using ColP = typename std::conditional<MIXED, ColPM, ColPD>::type;
     using R = typename std::conditional<MIXED, float, double>::type;
     __shared__ FShared S;
     __shared__ ReplicaDev s_rp;
@@ -555,40 +681,50 @@ __global__ void __launch_bounds__(MDF_NT, 1) k_md_fast(Dev d, uint32_t step, int
         S.cat[tid] = d.colCat[g];
     }
 
-    // this lane's colloid component (lanes >= 3 nc: a copy of component 0)
+    const R bond_d = nbond > 0 ? (R)d.bonds[rp.bond_off].d : R(0);
+    const R idt = R(1) / (MIXED ? (R)rp.dt_f : (R)rp.dt);
+    // colloid state: mixed, the whole state in every lane; FP64, lane l < 3 nc
+    // holds component l (lanes beyond: a copy of component 0)
+    ColM CM;
+    LaneD CD;
     const int cl_l = lane < 3 * nc ? lane : 0;
     const int cj = cl_l / 3, ct = cl_l % 3;
     const bool a_end = cj == 0;
     const int other = nc == 2 ? (cj == 0 ? cl_l + 3 : cl_l - 3) : cl_l;
-    const R bond_d = nbond > 0 ? (R)d.bonds[rp.bond_off].d : R(0);
-    Lane C;
-    {
-        const int g = rp.col_off + cj;
-        if constexpr (MIXED) {
-            C.Xi = d.colXi[3 * g + ct];
-            C.Xf = d.colXf[3 * g + ct];
-            C.Ci = d.colCi[3 * g + ct];
-            C.V = d.colVf[3 * g + ct];
-            C.Xoi = C.Xi; C.Xof = C.Xf;
-            C.X0i = C.Xi; C.X0f = C.Xf;
-            C.F = 0.0f;
-            C.invM = d.colInvM_f[g];
-        } else {
-            C.X = d.colX[3 * g + ct];
-            C.V = d.colV[3 * g + ct];
-            C.Xold = C.X; C.X0 = C.X;
-            C.F = 0.0;
-            C.M = d.colM[g];
+    if constexpr (MIXED) {
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            const int g = rp.col_off + (j < nc ? j : 0);
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                CM.Xi[j][t] = d.colXi[3 * g + t];
+                CM.Xf[j][t] = d.colXf[3 * g + t];
+                CM.Ci[j][t] = d.colCi[3 * g + t];
+                CM.V[j][t] = d.colVf[3 * g + t];
+            }
+            CM.invM[j] = d.colInvM_f[g];
         }
+    } else {
+        const int g = rp.col_off + cj;
+        CD.X = d.colX[3 * g + ct];
+        CD.V = d.colV[3 * g + ct];
+        CD.Xold = CD.X; CD.X0 = CD.X;
+        CD.F = 0.0;
+        CD.M = d.colM[g];
+        frames(rp, CD, ct);
     }
-    frames(rp, C, ct);
-    const R idt = R(1) / (MIXED ? (R)rp.dt_f : (R)rp.dt);
+    if (wid == 0) {
+        if constexpr (MIXED) write_positions(S, CM, CD, lane);
+        else write_positions_d(S, CD, lane);
+    }
     __syncthreads();
     // every CTA has read near_count and set up its barriers before any
     // remote access and before CTA 0 resets the count
     if (CS > 1) cl.sync();
 
     const int nn = S.nn;
+    PConstM K;
+    load_pconst(rp, S, K);
     const int *list = d.near_list + rp.part_off;
     W *work = reinterpret_cast<W *>(d.md_work) + rp.part_off;
     const int first = rank * MDF_NT + tid;
@@ -605,23 +741,42 @@ __global__ void __launch_bounds__(MDF_NT, 1) k_md_fast(Dev d, uint32_t step, int
     }
 
     long long acc[NC][3];
+    bool ins[MDF_PPT];
+    using ColP = typename std::conditional<MIXED, ColPM, ColPD>::type;
     // round 0: forces at the start of the interval; round k (1 <= k <= n_md):
-    // forces at the end of sub-step k - 1
+    // forces at the end of sub-step k - 1.  Per round: every warp computes
+    // its particles' forces and the warp sums of the reactions; after a CTA
+    // barrier warp 0 sends the CTA's partials, waits for every CTA's, and
+    // integrates the colloids, while the other warps move their particles;
+    // a second CTA barrier publishes the new colloid positions.
     for (int round = 0; round <= n_md; ++round) {
         const int b = round & 1;
         ColP P;
-        broadcast(C, P);
+        read_positions(S, P);
 #pragma unroll
         for (int j = 0; j < NC; ++j)
 #pragma unroll
             for (int k = 0; k < 3; ++k) acc[j][k] = 0;
+        // forces on the register particles; the particles beyond the
+        // registers also take their whole round here (one pass over memory)
+        if constexpr (MIXED) {
 #pragma unroll
-        for (int p = 0; p < MDF_PPT; ++p)
-            if (first + p * stride < nn) round_particle(rp, S, P, nc, reg[p], acc, step, round, n_md);
-        for (int k = over; k < nn; k += stride) {
-            W w = work[k];
-            round_particle(rp, S, P, nc, w, acc, step, round, n_md);
-            work[k] = w;
+            for (int p = 0; p < MDF_PPT; ++p)
+                if (first + p * stride < nn) pforce(rp, K, P, nc, reg[p], acc, ins[p]);
+            for (int k = over; k < nn; k += stride) {
+                W w = work[k];
+                round_particle(rp, K, P, nc, w, acc, step, round, n_md);
+                work[k] = w;
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < MDF_PPT; ++p)
+                if (first + p * stride < nn) pforce(rp, S, P, nc, reg[p], acc, ins[p]);
+            for (int k = over; k < nn; k += stride) {
+                W w = work[k];
+                round_particle(rp, S, P, nc, w, acc, step, round, n_md);
+                work[k] = w;
+            }
         }
         long long ws = 0;
 #pragma unroll
@@ -633,43 +788,52 @@ __global__ void __launch_bounds__(MDF_NT, 1) k_md_fast(Dev d, uint32_t step, int
             }
         if (lane < 3 * NC) S.wpart[b][wid][lane] = ws;
         __syncthreads();
-        // the CTA's partials (lane l < 6: component l, warps in order)
         long long tot = 0;
-        if (lane < 3 * NC)
-#pragma unroll
-            for (int w = 0; w < MDF_NW; ++w) tot += S.wpart[b][w][lane];
-        if constexpr (CS > 1) {
-            if (wid == 0) send_partials<CS>(S, rank, b, lane, tot);
-            const uint32_t bar = smem_addr(&S.mbar[b]);
-            const unsigned parity = (unsigned)(round >> 1) & 1u;
-            if (!S.dead) {
-                int spins = 0;
-                while (!mbar_try_wait_cluster(bar, parity)) {
-                    if (++spins > MDF_SPIN_LIMIT) {
-                        if (lane == 0) {
-                            atomicOr(&d.err[ERR_TIMEOUT], 1u);
-                            S.dead = 1;
-                        }
-                        break;
-                    }
-                }
-                __syncwarp();
-            }
-            tot = 0;
+        if (wid == 0) {
+            // the CTA's partials (lane l < 6: component l, warps in order)
             if (lane < 3 * NC)
 #pragma unroll
-                for (int q = 0; q < CS; ++q) tot += (long long)S.part[b][q][lane];
+                for (int w = 0; w < MDF_NW; ++w) tot += S.wpart[b][w][lane];
+            if constexpr (CS > 1) send_partials<CS>(S, rank, b, lane, tot);
         }
-        // the colloids: force of this round, end of sub-step round - 1
-        // (second half kick, RATTLE velocity stage), start of sub-step round
-        // (first half kick, drift, RATTLE position stage)
-        set_force(C, __shfl_sync(0xffffffffu, tot, cl_l));
-        if (round > 0) kick_rattle_vel(rp, C, nbond, a_end, other);
-        if (round < n_md) {
-            kick_drift(rp, C, ct);
-            if (nbond > 0) rattle_pos(rp, C, ct, bond_d, idt, a_end, other);
-            frames(rp, C, ct);
+        // the register particles' catalytic test of sub-step round - 1 and
+        // their move to the next round need only their own force: done while
+        // the partials travel
+#pragma unroll
+        for (int p = 0; p < MDF_PPT; ++p)
+            if (first + p * stride < nn) {
+                if (round > 0) reg[p].fid = fcatalysis(rp, reg[p].fid, ins[p], step, round - 1);
+                if (round < n_md) pkick_drift(rp, reg[p], round > 0);
+            }
+        if (wid == 0) {
+            tot = exchange_partials<CS>(d, S, b, round, lane, tot);
+            // the colloids: force of this round, end of sub-step round - 1
+            // (second half kick, RATTLE velocity stage), start of sub-step
+            // round (first half kick, drift, RATTLE position stage)
+            if constexpr (MIXED) {
+                const float fl = fixed40_to_float(tot);
+                float F[NC][3];
+#pragma unroll
+                for (int j = 0; j < NC; ++j)
+#pragma unroll
+                    for (int t = 0; t < 3; ++t) F[j][t] = __shfl_sync(0xffffffffu, fl, 3 * j + t);
+                if (round > 0) col_kick_rattle_vel(rp, CM, F, nc, nbond);
+                if (round < n_md) {
+                    col_kick_drift_rattle(rp, CM, F, nc, nbond, bond_d, idt);
+                    write_positions(S, CM, CD, lane);
+                }
+            } else {
+                set_force(CD, __shfl_sync(0xffffffffu, tot, cl_l));
+                if (round > 0) kick_rattle_vel(rp, CD, nbond, a_end, other);
+                if (round < n_md) {
+                    kick_drift(rp, CD, ct);
+                    if (nbond > 0) rattle_pos(rp, CD, ct, bond_d, idt, a_end, other);
+                    frames(rp, CD, ct);
+                    write_positions_d(S, CD, lane);
+                }
+            }
         }
+        __syncthreads();
     }
 
     // last half kick, wrap, write back (and bin for the collision of `step`)
@@ -684,37 +848,48 @@ __global__ void __launch_bounds__(MDF_NT, 1) k_md_fast(Dev d, uint32_t step, int
     }
     // CTA 0, warp 0: colloids back to memory, skin check, near list reset
     if (rank == 0 && wid == 0) {
-        const int g = rp.col_off + cj;
-        R e;
-        if constexpr (MIXED) e = (float)(C.Xi - C.X0i) + (C.Xf - C.X0f);
-        else e = C.X - C.X0;
-        const R e0 = __shfl_sync(0xffffffffu, e, 3 * cj), e1 = __shfl_sync(0xffffffffu, e, 3 * cj + 1);
-        const R e2 = __shfl_sync(0xffffffffu, e, 3 * cj + 2);
-        if (lane < 3 * nc) {
-            if constexpr (MIXED) {
-                d.colXi[3 * g + ct] = C.Xi;
-                d.colXf[3 * g + ct] = C.Xf;
-                d.colVf[3 * g + ct] = C.V;
-                d.colCi[3 * g + ct] = C.Ci;
-            } else {
-                d.colX[3 * g + ct] = C.X;
-                d.colV[3 * g + ct] = C.V;
+        if constexpr (MIXED) {
+            if (lane == 0) {
+#pragma unroll
+                for (int j = 0; j < NC; ++j) {
+                    if (j >= nc) continue;
+                    const int g = rp.col_off + j;
+                    float e[3];
+#pragma unroll
+                    for (int t = 0; t < 3; ++t) {
+                        // displacement over the interval, against the stored start
+                        e[t] = (float)(CM.Xi[j][t] - d.colXi[3 * g + t]) + (CM.Xf[j][t] - d.colXf[3 * g + t]);
+                    }
+#pragma unroll
+                    for (int t = 0; t < 3; ++t) {
+                        d.colXi[3 * g + t] = CM.Xi[j][t];
+                        d.colXf[3 * g + t] = CM.Xf[j][t];
+                        d.colVf[3 * g + t] = CM.V[j][t];
+                        d.colCi[3 * g + t] = CM.Ci[j][t];
+                    }
+                    const float dd = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+                    if (!(dd <= rp.skin_f * rp.skin_f)) atomicAdd(&d.err[ERR_SKIN], 1u);
+                }
             }
-        }
-        bool bad = false;
-        if (lane < 3 * nc && ct == 0) {
-            if constexpr (MIXED) {
-                const float dd = e0 * e0 + e1 * e1 + e2 * e2;
-                bad = !(dd <= rp.skin_f * rp.skin_f);
-            } else {
+        } else {
+            const int g = rp.col_off + cj;
+            const double e = CD.X - CD.X0;
+            const double e0 = __shfl_sync(0xffffffffu, e, 3 * cj), e1 = __shfl_sync(0xffffffffu, e, 3 * cj + 1);
+            const double e2 = __shfl_sync(0xffffffffu, e, 3 * cj + 2);
+            if (lane < 3 * nc) {
+                d.colX[3 * g + ct] = CD.X;
+                d.colV[3 * g + ct] = CD.V;
+            }
+            bool bad = false;
+            if (lane < 3 * nc && ct == 0) {
                 double dd = 0.0;
                 dd = dd + e0 * e0;
                 dd = dd + e1 * e1;
                 dd = dd + e2 * e2;
                 bad = !(dd <= rp.skin * rp.skin);
             }
+            if (bad) atomicAdd(&d.err[ERR_SKIN], 1u);
         }
-        if (bad) atomicAdd(&d.err[ERR_SKIN], 1u);
         if (lane == 0) d.near_count[r] = 0;
     }
     if (CS > 1) cl.sync();   // no CTA leaves while another may still write its shared memory
