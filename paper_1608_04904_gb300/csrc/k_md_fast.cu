@@ -72,15 +72,18 @@ struct FShared {
 };
 
 // --- colloid state ------------------------------------------------------------
-// Mixed path: every lane holds the whole colloid state (both colloids, all
-// axes) and integrates it itself, so no shuffle sits on the colloid chain and
-// the particles read the colloid positions from registers.  The operations
-// and their order are those of the general MD kernel, component by component,
-// so both kernels give bit-identical results.
-struct ColM {    // integer cell + FP32 offset in [0,1)
-    int Xi[NC][3], Ci[NC][3];
-    float Xf[NC][3], V[NC][3];
-    float invM[NC];
+// Mixed path (warp 0 integrates the colloids): lane l < 3 nc owns colloid
+// j = l / 3, axis t = l % 3 (lanes beyond: a copy of component 0) and does the
+// per-component work; every lane keeps a copy of all positions (refreshed by
+// one shuffle round after each move) for the dot products of RATTLE, which
+// each lane evaluates itself.  The operations and their order are those of
+// the general MD kernel, so both kernels give bit-identical results.
+struct ColL {
+    int Xi, Ci;                 // own component: unwrapped and wrapped cell
+    float Xf, V, invM;          //   offset in [0,1), velocity, 1 / mass
+    int Xa[NC][3];              // all components: unwrapped cells
+    float Xfa[NC][3];           //   and offsets
+    float invMa[NC];
 };
 // FP64 path: lane l < 3 nc holds colloid j = l / 3, axis t = l % 3; the bond
 // of a dimer always joins colloids 0 and 1, so the other end of a lane's
@@ -88,6 +91,13 @@ struct ColM {    // integer cell + FP32 offset in [0,1)
 struct LaneD {   // unwrapped FP64 position
     double X, V, F, Xold, X0, Xw, M;
 };
+
+// (float)i for |i| < 2^22, exactly, on the integer and FP32 pipes: the bits
+// of 1.5 2^23 + i, minus 1.5 2^23.  Cell differences here are below 2^11.
+__device__ __forceinline__ float small_i2f(int i)
+{
+    return __int_as_float(0x4B400000 + i) - 12582912.0f;
+}
 
 // Sum over lanes 0..2, in lane order (every lane gets the result): the
 // component sum of a 3-vector held by axis lanes.
@@ -132,98 +142,100 @@ __device__ __forceinline__ void kick_drift(const ReplicaDev &rp, LaneD &C, int)
     C.X = fma(rp.dt, C.V, C.X);
 }
 
-// Wrapped cells back in [0, L) after a sub-step that moved a colloid by more
-// than a box length (one uniform branch per update, never taken in practice).
-__device__ __forceinline__ void wrap_cells(const ReplicaDev &rp, ColM &C)
-{
-    bool out = false;
-#pragma unroll
-    for (int j = 0; j < NC; ++j)
-#pragma unroll
-        for (int t = 0; t < 3; ++t) out = out || (unsigned)C.Ci[j][t] >= (unsigned)rp.L[t];
-    if (out)
-#pragma unroll
-        for (int j = 0; j < NC; ++j)
-#pragma unroll
-            for (int t = 0; t < 3; ++t) C.Ci[j][t] = imod(C.Ci[j][t], rp.L[t]);
-}
+// Own-component value of a 3-vector held in every lane.
+__device__ __forceinline__ float pick3(const float a[3], int t) { return t == 0 ? a[0] : (t == 1 ? a[1] : a[2]); }
 
-// Mixed path, whole state per lane.  Second half kick and RATTLE velocity
-// stage of the bond 0-1 (Andersen 1983).
-__device__ __forceinline__ void col_kick_rattle_vel(const ReplicaDev &rp, ColM &C, const float F[NC][3], int nc,
-                                                    int nbond)
+// Every lane: all positions from their owner lanes.
+__device__ __forceinline__ void share_positions(ColL &C)
 {
-    // (with one colloid, slot 1 holds a copy that is integrated but never used)
-#pragma unroll
-    for (int j = 0; j < NC; ++j)
-#pragma unroll
-        for (int t = 0; t < 3; ++t) C.V[j][t] = fmaf(rp.hdt_f, F[j][t] * C.invM[j], C.V[j][t]);
-    if (nbond == 0) return;
-    float r[3], dv[3];
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-        r[t] = (float)(C.Xi[0][t] - C.Xi[1][t]) + (C.Xf[0][t] - C.Xf[1][t]);
-        dv[t] = C.V[0][t] - C.V[1][t];
-    }
-    const float ia = C.invM[0], ib = C.invM[1];
-    const float inv = ia + ib;
-    const float rr = (r[0] * r[0] + r[1] * r[1]) + r[2] * r[2];
-    const float rv = (dv[0] * r[0] + dv[1] * r[1]) + dv[2] * r[2];
-    const float kk = fdiv_m(rv, rr * inv);
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-        C.V[0][t] -= kk * r[t] * ia;
-        C.V[1][t] += kk * r[t] * ib;
-    }
-}
-
-// First half kick, drift and exact RATTLE position stage (bond length dd).
-__device__ __forceinline__ void col_kick_drift_rattle(const ReplicaDev &rp, ColM &C, const float F[NC][3], int nc,
-                                                      int nbond, float dd, float idt)
-{
-    int Xoi[NC][3];
-    float Xof[NC][3];
 #pragma unroll
     for (int j = 0; j < NC; ++j)
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
-            C.V[j][t] = fmaf(rp.hdt_f, F[j][t] * C.invM[j], C.V[j][t]);
-            Xoi[j][t] = C.Xi[j][t];
-            Xof[j][t] = C.Xf[j][t];
-            C.Xf[j][t] = fmaf(rp.dt_f, C.V[j][t], C.Xf[j][t]);
-            carry(rp, C.Xi[j][t], C.Ci[j][t], C.Xf[j][t], t);
+            C.Xa[j][t] = __shfl_sync(0xffffffffu, C.Xi, 3 * j + t);
+            C.Xfa[j][t] = __shfl_sync(0xffffffffu, C.Xf, 3 * j + t);
         }
-    if (nbond == 0) { wrap_cells(rp, C); return; }
-    float ro[3], rn[3];
+}
+
+// Second half kick and RATTLE velocity stage of the bond 0-1 (Andersen
+// 1983).  F: this lane's component of the force.
+__device__ __forceinline__ void col_kick_rattle_vel(const ReplicaDev &rp, ColL &C, float F, int cj, int ct, int nbond)
+{
+    C.V = fmaf(rp.hdt_f, F * C.invM, C.V);
+    if (nbond == 0) return;
+    float Va[NC][3];
+#pragma unroll
+    for (int j = 0; j < NC; ++j)
+#pragma unroll
+        for (int t = 0; t < 3; ++t) Va[j][t] = __shfl_sync(0xffffffffu, C.V, 3 * j + t);
+    float r[3], dv[3];
 #pragma unroll
     for (int t = 0; t < 3; ++t) {
-        ro[t] = (float)(Xoi[0][t] - Xoi[1][t]) + (Xof[0][t] - Xof[1][t]);
-        rn[t] = (float)(C.Xi[0][t] - C.Xi[1][t]) + (C.Xf[0][t] - C.Xf[1][t]);
+        r[t] = small_i2f(C.Xa[0][t] - C.Xa[1][t]) + (C.Xfa[0][t] - C.Xfa[1][t]);
+        dv[t] = Va[0][t] - Va[1][t];
     }
-    const float ia = C.invM[0], ib = C.invM[1];
+    const float ia = C.invMa[0], ib = C.invMa[1];
     const float inv = ia + ib;
-    const float oo = (ro[0] * ro[0] + ro[1] * ro[1]) + ro[2] * ro[2];
-    const float on = (rn[0] * ro[0] + rn[1] * ro[1]) + rn[2] * ro[2];
-    const float nn = (rn[0] * rn[0] + rn[1] * rn[1]) + rn[2] * rn[2];
-    const float qa = inv * inv * oo;
-    const float qb = 2.0f * inv * on;
-    const float qc = nn - dd * dd;
-    float disc = qb * qb - 4.0f * qa * qc;
-    if (disc < 0.0f) disc = 0.0f;
-    const float q = -0.5f * (qb + copysignf(sqrtf(disc), qb));
-    const float gmul = fdiv_m(qc, q);
+    const float rr = (r[0] * r[0] + r[1] * r[1]) + r[2] * r[2];
+    const float rv = (dv[0] * r[0] + dv[1] * r[1]) + dv[2] * r[2];
+    const float kk = fdiv_m(rv, rr * inv);
+    const float ro = pick3(r, ct);
+    if (cj == 0) C.V -= kk * ro * ia;
+    else C.V += kk * ro * ib;
+}
+
+// First half kick, drift and exact RATTLE position stage (bond length dd);
+// ends with every lane holding the new positions.
+__device__ __forceinline__ void col_kick_drift_rattle(const ReplicaDev &rp, ColL &C, float F, int cj, int ct,
+                                                      int nbond, float dd, float idt)
+{
+    C.V = fmaf(rp.hdt_f, F * C.invM, C.V);
+    C.Xf = fmaf(rp.dt_f, C.V, C.Xf);
+    carry(rp, C.Xi, C.Ci, C.Xf, ct);
+    if (nbond > 0) {
+        int Xn[NC][3];
+        float Xfn[NC][3];
 #pragma unroll
-    for (int t = 0; t < 3; ++t) {
-        const float ca = gmul * ro[t] * ia;
-        C.Xf[0][t] += ca;
-        C.V[0][t] += ca * idt;
-        carry(rp, C.Xi[0][t], C.Ci[0][t], C.Xf[0][t], t);
-        const float cb = gmul * ro[t] * ib;
-        C.Xf[1][t] -= cb;
-        C.V[1][t] -= cb * idt;
-        carry(rp, C.Xi[1][t], C.Ci[1][t], C.Xf[1][t], t);
+        for (int j = 0; j < NC; ++j)
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                Xn[j][t] = __shfl_sync(0xffffffffu, C.Xi, 3 * j + t);
+                Xfn[j][t] = __shfl_sync(0xffffffffu, C.Xf, 3 * j + t);
+            }
+        // old positions: the copy from the end of the previous move
+        float ro[3], rn[3];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            ro[t] = small_i2f(C.Xa[0][t] - C.Xa[1][t]) + (C.Xfa[0][t] - C.Xfa[1][t]);
+            rn[t] = small_i2f(Xn[0][t] - Xn[1][t]) + (Xfn[0][t] - Xfn[1][t]);
+        }
+        const float ia = C.invMa[0], ib = C.invMa[1];
+        const float inv = ia + ib;
+        const float oo = (ro[0] * ro[0] + ro[1] * ro[1]) + ro[2] * ro[2];
+        const float on = (rn[0] * ro[0] + rn[1] * ro[1]) + rn[2] * ro[2];
+        const float nn = (rn[0] * rn[0] + rn[1] * rn[1]) + rn[2] * rn[2];
+        const float qa = inv * inv * oo;
+        const float qb = 2.0f * inv * on;
+        const float qc = nn - dd * dd;
+        float disc = qb * qb - 4.0f * qa * qc;
+        if (disc < 0.0f) disc = 0.0f;
+        const float q = -0.5f * (qb + copysignf(sqrtf(disc), qb));
+        const float gmul = fdiv_m(qc, q);
+        const float rot = pick3(ro, ct);
+        if (cj == 0) {
+            const float ca = gmul * rot * ia;
+            C.Xf += ca;
+            C.V += ca * idt;
+        } else {
+            const float cb = gmul * rot * ib;
+            C.Xf -= cb;
+            C.V -= cb * idt;
+        }
+        carry(rp, C.Xi, C.Ci, C.Xf, ct);
     }
-    wrap_cells(rp, C);
+    // a colloid that crossed more than a box length in one sub-step
+    if ((unsigned)C.Ci >= (unsigned)rp.L[ct]) C.Ci = imod(C.Ci, rp.L[ct]);
+    share_positions(C);
 }
 
 // FP64 path, lane-parallel: exact RATTLE position stage for the bond 0-1.
@@ -305,16 +317,12 @@ __device__ __forceinline__ void read_positions(const FShared &S, ColPD &P)
         for (int t = 0; t < 3; ++t) P.Xw[j][t] = S.pXw[j][t];
 }
 // Warp 0: the colloid positions of the next round for every warp of the CTA.
-__device__ __forceinline__ void write_positions(FShared &S, const ColM &C, const LaneD &, int lane)
+__device__ __forceinline__ void write_positions(FShared &S, const ColL &C, int lane, int nc)
 {
-    if (lane == 0)
-#pragma unroll
-        for (int j = 0; j < NC; ++j)
-#pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                S.pCi[j][t] = C.Ci[j][t];
-                S.pXf[j][t] = C.Xf[j][t];
-            }
+    if (lane < 3 * nc) {
+        S.pCi[lane / 3][lane % 3] = C.Ci;
+        S.pXf[lane / 3][lane % 3] = C.Xf;
+    }
 }
 __device__ __forceinline__ void write_positions_d(FShared &S, const LaneD &C, int lane)
 {
@@ -547,11 +555,12 @@ __device__ __forceinline__ void finish_particle(const Dev &d, const ReplicaDev &
 // Warp 0 of every CTA writes the CTA's six fixed-point partials into slot
 // [rank] of every CTA's buffer for the round's parity with st.async; the bytes
 // are counted on that CTA's mbarrier for the parity, whose single arrival is
-// warp 0's own expect-tx.  Every warp waits for the phase and sums the slots
-// in rank order.  Round r + 2 reuses the buffer and the barrier of round r: a
-// CTA sends round r + 2 only after its CTA barrier of round r + 2, which all
-// its warps reach after reading round r, and after every CTA sent round
-// r + 1, which each does after its own warps read round r.
+// the expect-tx thread 0 posts at the start of the round.  Warp 0 waits for
+// the phase and sums the slots in rank order.  Round r + 2 reuses the buffer
+// and the barrier of round r: a CTA sends round r + 2 only after its warp 0
+// read round r, and after every CTA sent round r + 1, which each does after
+// its own warp 0 read round r; thread 0 posts round r + 2's expect-tx after
+// it saw round r's phase complete.
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -592,31 +601,50 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t a, unsigned parit
 
 constexpr unsigned MDF_TX_BYTES = 6 * 8;   // partials one CTA sends to one CTA per round
 
-// Warp 0 of a CTA: its CTA's partials (lane l < 6 holds component l) to every
-// CTA of the cluster, as three 16-byte st.async per destination spread over
-// the lanes.
+// Remote addresses of warp 0's st.async items, computed once per launch:
+// item = lane + 32 k goes to CTA item / 3 and carries pair item % 3 of the
+// six partials, into slot [rank] of that CTA's buffer for each parity.
 template <int CS>
-__device__ __forceinline__ void send_partials(FShared &S, int rank, int b, int lane, long long mine)
+struct SendPlan {
+    static constexpr int K = (3 * CS + 31) / 32;
+    uint32_t dst[2][K], bar[2][K];
+};
+template <int CS>
+__device__ __forceinline__ void plan_sends(FShared &S, int rank, int lane, SendPlan<CS> &P)
 {
-    const uint32_t bar = smem_addr(&S.mbar[b]);
-    if (lane == 0) mbar_expect_tx(bar, (unsigned)(CS * MDF_TX_BYTES));
-    const uint32_t src = smem_addr(&S.part[b][rank][0]);
 #pragma unroll
-    for (int k = 0; k < (3 * CS + 31) / 32; ++k) {
-        const int item = lane + 32 * k;   // destination item / 3, pair item % 3
-        const int pi = item % 3;
-        const long long x = __shfl_sync(0xffffffffu, mine, 2 * pi);
-        const long long y = __shfl_sync(0xffffffffu, mine, 2 * pi + 1);
-        if (item < 3 * CS) {
-            const int q = item / 3;
-            st_async_v2(cluster_addr(src + 16u * (uint32_t)pi, q), (unsigned long long)x, (unsigned long long)y,
-                        cluster_addr(bar, q));
+    for (int b = 0; b < 2; ++b) {
+        const uint32_t src = smem_addr(&S.part[b][rank][0]), bar = smem_addr(&S.mbar[b]);
+#pragma unroll
+        for (int k = 0; k < SendPlan<CS>::K; ++k) {
+            const int item = lane + 32 * k;
+            const int q = item < 3 * CS ? item / 3 : 0;
+            P.dst[b][k] = cluster_addr(src + 16u * (uint32_t)(item % 3), q);
+            P.bar[b][k] = cluster_addr(bar, q);
         }
     }
 }
 
-// Every warp waits for the partials of round `round` (parity b) from every
-// CTA of the cluster and sums them in rank order (lane l < 6: component l).
+// Warp 0 of a CTA: its CTA's partials (lane l < 6 holds component l) to every
+// CTA of the cluster, as three 16-byte st.async per destination spread over
+// the lanes.  The expected byte count of the round was posted at its start.
+template <int CS>
+__device__ __forceinline__ void send_partials(const SendPlan<CS> &P, int b, int lane, long long mine)
+{
+#pragma unroll
+    for (int k = 0; k < SendPlan<CS>::K; ++k) {
+        const int item = lane + 32 * k;
+        const int pi = item % 3;
+        const long long x = __shfl_sync(0xffffffffu, mine, 2 * pi);
+        const long long y = __shfl_sync(0xffffffffu, mine, 2 * pi + 1);
+        if (item < 3 * CS)
+            st_async_v2(b ? P.dst[1][k] : P.dst[0][k], (unsigned long long)x, (unsigned long long)y,
+                        b ? P.bar[1][k] : P.bar[0][k]);
+    }
+}
+
+// Warp 0 waits for the partials of round `round` (parity b) from every CTA
+// of the cluster and sums them in rank order (lane l < 6: component l).
 // Without a cluster the CTA's own sum `tot` is the total.
 template <int CS>
 __device__ __forceinline__ long long exchange_partials(const Dev &d, FShared &S, int b, int round, int lane,
@@ -683,27 +711,24 @@ __global__ void __launch_bounds__(MDF_NT, 1) k_md_fast(Dev d, uint32_t step, int
 
     const R bond_d = nbond > 0 ? (R)d.bonds[rp.bond_off].d : R(0);
     const R idt = R(1) / (MIXED ? (R)rp.dt_f : (R)rp.dt);
-    // colloid state: mixed, the whole state in every lane; FP64, lane l < 3 nc
-    // holds component l (lanes beyond: a copy of component 0)
-    ColM CM;
+    // colloid state: lane l < 3 nc owns component l (lanes beyond: a copy of
+    // component 0); mixed, every lane also keeps all positions
+    ColL CM;
     LaneD CD;
     const int cl_l = lane < 3 * nc ? lane : 0;
     const int cj = cl_l / 3, ct = cl_l % 3;
     const bool a_end = cj == 0;
     const int other = nc == 2 ? (cj == 0 ? cl_l + 3 : cl_l - 3) : cl_l;
     if constexpr (MIXED) {
+        const int g = rp.col_off + cj;
+        CM.Xi = d.colXi[3 * g + ct];
+        CM.Xf = d.colXf[3 * g + ct];
+        CM.Ci = d.colCi[3 * g + ct];
+        CM.V = d.colVf[3 * g + ct];
+        CM.invM = d.colInvM_f[g];
 #pragma unroll
-        for (int j = 0; j < NC; ++j) {
-            const int g = rp.col_off + (j < nc ? j : 0);
-#pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                CM.Xi[j][t] = d.colXi[3 * g + t];
-                CM.Xf[j][t] = d.colXf[3 * g + t];
-                CM.Ci[j][t] = d.colCi[3 * g + t];
-                CM.V[j][t] = d.colVf[3 * g + t];
-            }
-            CM.invM[j] = d.colInvM_f[g];
-        }
+        for (int j = 0; j < NC; ++j) CM.invMa[j] = d.colInvM_f[rp.col_off + (j < nc ? j : 0)];
+        share_positions(CM);
     } else {
         const int g = rp.col_off + cj;
         CD.X = d.colX[3 * g + ct];
@@ -714,7 +739,7 @@ __global__ void __launch_bounds__(MDF_NT, 1) k_md_fast(Dev d, uint32_t step, int
         frames(rp, CD, ct);
     }
     if (wid == 0) {
-        if constexpr (MIXED) write_positions(S, CM, CD, lane);
+        if constexpr (MIXED) write_positions(S, CM, lane, nc);
         else write_positions_d(S, CD, lane);
     }
     __syncthreads();
@@ -723,6 +748,8 @@ __global__ void __launch_bounds__(MDF_NT, 1) k_md_fast(Dev d, uint32_t step, int
     if (CS > 1) cl.sync();
 
     const int nn = S.nn;
+    SendPlan<CS> plan;
+    if constexpr (CS > 1) plan_sends<CS>(S, rank, lane, plan);
     PConstM K;
     load_pconst(rp, S, K);
     const int *list = d.near_list + rp.part_off;
@@ -751,6 +778,10 @@ __global__ void __launch_bounds__(MDF_NT, 1) k_md_fast(Dev d, uint32_t step, int
     // a second CTA barrier publishes the new colloid positions.
     for (int round = 0; round <= n_md; ++round) {
         const int b = round & 1;
+        // the byte count this round's barrier expects (its previous phase, two
+        // rounds ago, has completed: warp 0 waited for it)
+        if constexpr (CS > 1)
+            if (tid == 0 && !S.dead) mbar_expect_tx(smem_addr(&S.mbar[b]), (unsigned)(CS * MDF_TX_BYTES));
         ColP P;
         read_positions(S, P);
 #pragma unroll
@@ -794,7 +825,7 @@ __global__ void __launch_bounds__(MDF_NT, 1) k_md_fast(Dev d, uint32_t step, int
             if (lane < 3 * NC)
 #pragma unroll
                 for (int w = 0; w < MDF_NW; ++w) tot += S.wpart[b][w][lane];
-            if constexpr (CS > 1) send_partials<CS>(S, rank, b, lane, tot);
+            if constexpr (CS > 1) send_partials<CS>(plan, b, lane, tot);
         }
         // the register particles' catalytic test of sub-step round - 1 and
         // their move to the next round need only their own force: done while
@@ -811,16 +842,11 @@ __global__ void __launch_bounds__(MDF_NT, 1) k_md_fast(Dev d, uint32_t step, int
             // (second half kick, RATTLE velocity stage), start of sub-step
             // round (first half kick, drift, RATTLE position stage)
             if constexpr (MIXED) {
-                const float fl = fixed40_to_float(tot);
-                float F[NC][3];
-#pragma unroll
-                for (int j = 0; j < NC; ++j)
-#pragma unroll
-                    for (int t = 0; t < 3; ++t) F[j][t] = __shfl_sync(0xffffffffu, fl, 3 * j + t);
-                if (round > 0) col_kick_rattle_vel(rp, CM, F, nc, nbond);
+                const float F = fixed40_to_float(tot);   // lane l < 6: component l
+                if (round > 0) col_kick_rattle_vel(rp, CM, F, cj, ct, nbond);
                 if (round < n_md) {
-                    col_kick_drift_rattle(rp, CM, F, nc, nbond, bond_d, idt);
-                    write_positions(S, CM, CD, lane);
+                    col_kick_drift_rattle(rp, CM, F, cj, ct, nbond, bond_d, idt);
+                    write_positions(S, CM, lane, nc);
                 }
             } else {
                 set_force(CD, __shfl_sync(0xffffffffu, tot, cl_l));
@@ -849,27 +875,21 @@ __global__ void __launch_bounds__(MDF_NT, 1) k_md_fast(Dev d, uint32_t step, int
     // CTA 0, warp 0: colloids back to memory, skin check, near list reset
     if (rank == 0 && wid == 0) {
         if constexpr (MIXED) {
-            if (lane == 0) {
-#pragma unroll
-                for (int j = 0; j < NC; ++j) {
-                    if (j >= nc) continue;
-                    const int g = rp.col_off + j;
-                    float e[3];
-#pragma unroll
-                    for (int t = 0; t < 3; ++t) {
-                        // displacement over the interval, against the stored start
-                        e[t] = (float)(CM.Xi[j][t] - d.colXi[3 * g + t]) + (CM.Xf[j][t] - d.colXf[3 * g + t]);
-                    }
-#pragma unroll
-                    for (int t = 0; t < 3; ++t) {
-                        d.colXi[3 * g + t] = CM.Xi[j][t];
-                        d.colXf[3 * g + t] = CM.Xf[j][t];
-                        d.colVf[3 * g + t] = CM.V[j][t];
-                        d.colCi[3 * g + t] = CM.Ci[j][t];
-                    }
-                    const float dd = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
-                    if (!(dd <= rp.skin_f * rp.skin_f)) atomicAdd(&d.err[ERR_SKIN], 1u);
-                }
+            // displacement over the interval, against the stored start
+            const int g = rp.col_off + cj;
+            const float e = (float)(CM.Xi - d.colXi[3 * g + ct]) + (CM.Xf - d.colXf[3 * g + ct]);
+            const float e0 = __shfl_sync(0xffffffffu, e, 3 * cj), e1 = __shfl_sync(0xffffffffu, e, 3 * cj + 1);
+            const float e2 = __shfl_sync(0xffffffffu, e, 3 * cj + 2);
+            __syncwarp();   // every lane has read the start before it is overwritten
+            if (lane < 3 * nc) {
+                d.colXi[3 * g + ct] = CM.Xi;
+                d.colXf[3 * g + ct] = CM.Xf;
+                d.colVf[3 * g + ct] = CM.V;
+                d.colCi[3 * g + ct] = CM.Ci;
+            }
+            if (lane < 3 * nc && ct == 0) {
+                const float dd = e0 * e0 + e1 * e1 + e2 * e2;
+                if (!(dd <= rp.skin_f * rp.skin_f)) atomicAdd(&d.err[ERR_SKIN], 1u);
             }
         } else {
             const int g = rp.col_off + cj;
