@@ -147,6 +147,18 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
                           const rmpcd_params *params, const rmpcd_colloid *colloids,
                           const rmpcd_bond *bonds, int32_t bucket_cap, void *stream);
 
+/* Device memory that rmpcd_create would allocate for the same arguments: the
+ * sum of its device buffers, each rounded up to 256 bytes (the CUDA allocator
+ * may round further).  Not included: the CUDA context, captured CUDA graphs,
+ * and the bead arrays and lookup grids that rmpcd_set_body adds later.
+ * Validates the arguments exactly as rmpcd_create does (bucket_cap 0 is sized
+ * by the same autotuner rule) and makes no CUDA call, so it works on a host
+ * without a GPU.  bytes: host output.  Errors: EINVAL (same cases as
+ * rmpcd_create, or bytes NULL). */
+rmpcd_status rmpcd_workspace_size(int32_t precision, int32_t n_replicas, const rmpcd_params *params,
+                                  const rmpcd_colloid *colloids, const rmpcd_bond *bonds, int32_t bucket_cap,
+                                  size_t *bytes);
+
 /* Release every device buffer of the system.  NULL is accepted. */
 void rmpcd_destroy(rmpcd_system *sys);
 

@@ -85,7 +85,7 @@ EXPORTS = [
     "rmpcd_collide", "rmpcd_react", "rmpcd_step", "rmpcd_observables", "rmpcd_sync", "rmpcd_launch_count",
     "rmpcd_last_error", "rmpcd_enable_timers", "rmpcd_read_timers", "rmpcd_set_tuning", "rmpcd_get_tuning",
     "rmpcd_observables_noalloc", "rmpcd_set_graphs", "rmpcd_get_bucket_cap", "rmpcd_set_body", "rmpcd_get_body",
-    "rmpcd_profile",
+    "rmpcd_profile", "rmpcd_workspace_size",
 ]
 
 _LIB = None
@@ -122,6 +122,7 @@ def load():
     L.rmpcd_step.argtypes = [vp, i32]
     L.rmpcd_observables.argtypes = [vp, i32, P(Obs)]
     L.rmpcd_profile.argtypes = [vp, i32, i32, i32, P(ProfileBin)]
+    L.rmpcd_workspace_size.argtypes = [i32, i32, P(Params), P(Colloid), P(Bond), i32, P(C.c_size_t)]
     L.rmpcd_launch_count.argtypes = [vp, P(i64)]
     L.rmpcd_enable_timers.argtypes = [vp, i32]
     L.rmpcd_read_timers.argtypes = [vp, P(Timers), i32]
@@ -190,6 +191,39 @@ def _default_stream():
     return 0
 
 
+def _marshal(replicas):
+    """Params, colloid and bond arrays of rmpcd_create for a list of replicas."""
+    n = len(replicas)
+    params = (Params * n)()
+    cols, bonds = [], []
+    for r, rep in enumerate(replicas):
+        cl = list(rep.get("colloids", []) or [])
+        bl = list(rep.get("bonds", []) or [])
+        params[r] = make_params(rep["cfg"], rep["n"], len(cl), len(bl))
+        cols += [_colloid(c) for c in cl]
+        for a, b, dd in bl:
+            bo = Bond()
+            bo.a, bo.b, bo.d = int(a), int(b), float(dd)
+            bonds.append(bo)
+    carr = (Colloid * max(1, len(cols)))(*cols)
+    barr = (Bond * max(1, len(bonds)))(*bonds)
+    return params, carr, barr, cols, bonds
+
+
+def workspace_size(replicas, precision: str = "mixed", bucket_cap: int = 64) -> int:
+    """rmpcd_workspace_size: device bytes System(replicas, precision, bucket_cap)
+    would allocate (no GPU needed)."""
+    L = load()
+    params, carr, barr, cols, bonds = _marshal(list(replicas))
+    out = C.c_size_t(0)
+    prec = RMPCD_MIXED if precision == "mixed" else RMPCD_FP64
+    st = L.rmpcd_workspace_size(prec, len(replicas), params, carr if cols else None, barr if bonds else None,
+                                int(bucket_cap), C.byref(out))
+    if st != 0:
+        raise RmpcdError(st, L.rmpcd_last_error(None).decode())
+    return int(out.value)
+
+
 class System:
     """A set of independent replicas on the current CUDA device.
 
@@ -204,23 +238,9 @@ class System:
         self.precision = precision
         self.replicas = list(replicas)
         n = len(self.replicas)
-        params = (Params * n)()
-        cols, bonds = [], []
-        self.n = []
-        self.n_col = []
-        for r, rep in enumerate(self.replicas):
-            cl = list(rep.get("colloids", []) or [])
-            bl = list(rep.get("bonds", []) or [])
-            params[r] = make_params(rep["cfg"], rep["n"], len(cl), len(bl))
-            cols += [_colloid(c) for c in cl]
-            for a, b, dd in bl:
-                bo = Bond()
-                bo.a, bo.b, bo.d = int(a), int(b), float(dd)
-                bonds.append(bo)
-            self.n.append(int(rep["n"]))
-            self.n_col.append(len(cl))
-        carr = (Colloid * max(1, len(cols)))(*cols)
-        barr = (Bond * max(1, len(bonds)))(*bonds)
+        params, carr, barr, cols, bonds = _marshal(self.replicas)
+        self.n = [int(rep["n"]) for rep in self.replicas]
+        self.n_col = [len(list(rep.get("colloids", []) or [])) for rep in self.replicas]
         if stream is None:
             stream = _default_stream()
         elif hasattr(stream, "cuda_stream"):

@@ -36,6 +36,8 @@ struct rmpcd_system {
     uint32_t *stage_id = nullptr;
     int32_t *stage_cell = nullptr;
     unsigned long long *prof_acc = nullptr;   // [PROF_MAX_BINS * PROF_FIELDS] slab-profile sums
+    bool dry = false;          // sizing only (rmpcd_workspace_size): count bytes, allocate nothing
+    size_t dry_bytes = 0;
     // pipeline state
     uint32_t step = 0;
     int cur = 0;        // record buffer holding the state
@@ -213,6 +215,10 @@ static rmpcd_status dalloc(rmpcd_system *sys, T **p, size_t count)
 {
     *p = nullptr;
     if (count == 0) count = 1;
+    if (sys->dry) {
+        sys->dry_bytes += (count * sizeof(T) + 255) / 256 * 256;
+        return RMPCD_OK;
+    }
     void *q = nullptr;
     cudaError_t e = cudaMalloc(&q, count * sizeof(T));
     if (e != cudaSuccess) return cuda_check(sys, e, "cudaMalloc");
@@ -407,8 +413,11 @@ static rmpcd_status check_counts(rmpcd_system *sys, int b, bool *grew)
     return RMPCD_OK;
 }
 
-rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_replicas, const rmpcd_params *params,
-                          const rmpcd_colloid *colloids, const rmpcd_bond *bonds, int32_t bucket_cap, void *stream)
+// rmpcd_create, or with dry != NULL only its validation and the sum of its
+// device buffers (nothing allocated, no CUDA call).
+static rmpcd_status create_system(rmpcd_system **out, int32_t precision, int32_t n_replicas,
+                                  const rmpcd_params *params, const rmpcd_colloid *colloids, const rmpcd_bond *bonds,
+                                  int32_t bucket_cap, void *stream, size_t *dry)
 {
     if (!out) return fail(nullptr, RMPCD_EINVAL, "out is NULL");
     *out = nullptr;
@@ -435,6 +444,7 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
     if (n_tiles * CPT * (long long)bucket_cap > 0x7FFFFFFFll) return fail(nullptr, RMPCD_EINVAL, "cells x bucket_cap too large");
 
     rmpcd_system *sys = new rmpcd_system();
+    sys->dry = dry != nullptr;
     sys->mixed = precision == RMPCD_MIXED;
     sys->n_rep = n_replicas;
     sys->cap = bucket_cap;
@@ -562,6 +572,11 @@ rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_repli
     AL(&sys->stage_id, (size_t)sys->max_part);
     AL(&sys->stage_cell, (size_t)sys->max_part);
 #undef AL
+    if (sys->dry) {
+        *dry = sys->dry_bytes;
+        delete sys;
+        return RMPCD_OK;
+    }
     if (st != RMPCD_OK) {
         g_create_error = sys->err;
         rmpcd_destroy(sys);
@@ -716,6 +731,22 @@ static rmpcd_status check_errors(rmpcd_system *sys)
 }
 
 extern "C" {
+
+rmpcd_status rmpcd_create(rmpcd_system **out, int32_t precision, int32_t n_replicas, const rmpcd_params *params,
+                          const rmpcd_colloid *colloids, const rmpcd_bond *bonds, int32_t bucket_cap, void *stream)
+{
+    return create_system(out, precision, n_replicas, params, colloids, bonds, bucket_cap, stream, nullptr);
+}
+
+rmpcd_status rmpcd_workspace_size(int32_t precision, int32_t n_replicas, const rmpcd_params *params,
+                                  const rmpcd_colloid *colloids, const rmpcd_bond *bonds, int32_t bucket_cap,
+                                  size_t *bytes)
+{
+    if (!bytes) return fail(nullptr, RMPCD_EINVAL, "bytes is NULL");
+    *bytes = 0;
+    rmpcd_system *tmp = nullptr;
+    return create_system(&tmp, precision, n_replicas, params, colloids, bonds, bucket_cap, nullptr, bytes);
+}
 
 rmpcd_status rmpcd_set_state(rmpcd_system *sys, int32_t replica, const double *x, const double *v,
                              const uint8_t *flags, int64_t n, int32_t on_device)

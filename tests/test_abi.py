@@ -40,7 +40,8 @@ def test_struct_layouts_match_header(api, tmp_path):
     if gcc is None:
         pytest.skip("gcc not available")
     structs = {"rmpcd_params": api.Params, "rmpcd_colloid": api.Colloid, "rmpcd_bond": api.Bond,
-               "rmpcd_obs": api.Obs, "rmpcd_timers": api.Timers}
+               "rmpcd_obs": api.Obs, "rmpcd_timers": api.Timers, "rmpcd_body": api.Body, "rmpcd_bead": api.Bead,
+               "rmpcd_profile_bin": api.ProfileBin}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rmpcd.h"', "int main(void){"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
@@ -132,3 +133,44 @@ def test_null_arguments(api):
     lib.rmpcd_destroy(None)
     h = C.c_void_p()
     assert lib.rmpcd_create(C.byref(h), 1, 0, None, None, None, 64, None) == 1
+
+
+def _dimer_replica(**kw):
+    from paper_1608_04904_gb300 import synth
+    cfg, col, bonds = synth.dimer32(precision="mixed", **kw)
+    return dict(cfg=cfg, n=int(cfg["rho"] * 32 ** 3), colloids=col, bonds=bonds)
+
+
+def test_workspace_size_counts_the_buffers_without_a_gpu(api):
+    """rmpcd_workspace_size makes no CUDA call.  Its answer grows with the
+    bucket width by exactly the two bucket arrays (cells x width x 4 bytes
+    each, rounded to 256), with the particle count by at least the two record
+    buffers, and the FP64 records (64 B) need more than the mixed ones (32 B)."""
+    rep = _dimer_replica()
+    cells = 32 ** 3
+    r256 = lambda b: (b + 255) // 256 * 256
+    a = api.workspace_size([rep], "mixed", 48)
+    b = api.workspace_size([rep], "mixed", 64)
+    assert b - a == 2 * (r256(cells * 64 * 4) - r256(cells * 48 * 4))
+    big = dict(rep, n=rep["n"] + 8192)
+    assert api.workspace_size([big], "mixed", 48) - a >= 2 * 32 * 8192
+    assert api.workspace_size([rep], "fp64", 48) - a >= 2 * 32 * rep["n"]
+    # two replicas need the sum of the per-replica buffers, give or take the
+    # per-system ones
+    two = api.workspace_size([rep, rep], "mixed", 48)
+    assert a < two < 2 * a
+    # bucket_cap 0: the autotuned width, which at density 10 is 32..64
+    auto = api.workspace_size([rep], "mixed", 0)
+    assert api.workspace_size([rep], "mixed", 32) <= auto <= b
+
+
+def test_workspace_size_rejects_what_create_rejects(api):
+    from paper_1608_04904_gb300 import synth
+    rep = _dimer_replica()
+    with pytest.raises(api.RmpcdError):
+        api.workspace_size([dict(rep, cfg=dict(rep["cfg"], L=(1, 32, 32)))], "mixed", 48)
+    with pytest.raises(api.RmpcdError):
+        api.workspace_size([rep], "mixed", 100000)
+    lib = api.load()
+    p = api.make_params(synth.base_config(), 100)
+    assert lib.rmpcd_workspace_size(1, 1, p, None, None, 64, None) == 1
