@@ -182,10 +182,17 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
         T.react[c] = -1;
         T.mnear[c] = MIXED ? 0 : 1;
         int slab = -1;
-        if ((opts & CP_COLLIDE) && n >= 2) {
-            R sum[3] = {R(0), R(0), R(0)};
+        const bool coll = (opts & CP_COLLIDE) && n >= 2;
+        const bool nearq = want_near && n > 0;
+        // the cell's velocity sum, in sorted order: for the collision and for
+        // the near bound (stage D leaves the velocities unchanged outside
+        // MPC-AT slabs, where the bound is not taken)
+        R sum[3] = {R(0), R(0), R(0)};
+        if (coll || nearq)
             for (int i = 0; i < n; ++i)
                 for (int k = 0; k < 3; ++k) sum[k] = sum[k] + srec[lo + i].v[k];
+        int nbB = -1;   // B count, when the near bound's loop has taken it
+        if (coll) {
             const int cx = lc % rp.L[0];
             const int cz = lc / (rp.L[0] * rp.L[1]);
             R vcm[3];
@@ -232,7 +239,7 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
                 T.mode[c] = 1;
             }
         }
-        if (want_near && n > 0) {
+        if (nearq) {
             // can a particle of the cell come near a colloid in the next
             // interval?  Its post-collision speed is at most |v_cm| + max
             // |v - v_cm| (the rotation keeps |v - v_cm|) and it lies within
@@ -241,17 +248,17 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
             int mn = 1;
             if (MANY) T.vbc[c] = -1.0f;
             if (slab < 0) {
-                R s3[3] = {R(0), R(0), R(0)};
-                for (int i = 0; i < n; ++i)
-                    for (int k = 0; k < 3; ++k) s3[k] = s3[k] + srec[lo + i].v[k];
                 const R inv = R(1) / (R)n;
-                const R vc[3] = {s3[0] * inv, s3[1] * inv, s3[2] * inv};
+                const R vc[3] = {sum[0] * inv, sum[1] * inv, sum[2] * inv};
                 R u2 = R(0);
+                int nb_ = 0;
                 for (int i = 0; i < n; ++i) {
                     const R a0 = srec[lo + i].v[0] - vc[0], a1 = srec[lo + i].v[1] - vc[1],
                             a2 = srec[lo + i].v[2] - vc[2];
                     u2 = max(u2, a0 * a0 + a1 * a1 + a2 * a2);
+                    nb_ += (srec[lo + i].fid & F_B) ? 1 : 0;
                 }
+                nbB = nb_;
                 const float vb = (float)(sqrt(vc[0] * vc[0] + vc[1] * vc[1] + vc[2] * vc[2]) + sqrt(u2));
                 if (MANY) T.vbc[c] = vb;
                 const int t = lc / rp.L[0];
@@ -269,8 +276,10 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
             T.mnear[c] = mn;
         }
         if ((opts & CP_REACT) && rp.bulk_on && n > 0) {
-            int nbB = 0;
-            for (int i = 0; i < n; ++i) nbB += (srec[lo + i].fid & F_B) ? 1 : 0;
+            if (nbB < 0) {
+                nbB = 0;
+                for (int i = 0; i < n; ++i) nbB += (srec[lo + i].fid & F_B) ? 1 : 0;
+            }
             if (nbB > 0) {
                 U4 w = philox((uint32_t)lc, a.step, P_REACT, 0u, rp.seed);
                 if ((unsigned long long)w.x < d.bulk_thr[rp.thr_off + nbB]) {
@@ -479,7 +488,7 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
         have_base = true;
     }
     // E: apply, write, classify for the next collision (the next cell of a
-    // far particle goes to ent[p], -1 for none)
+    // far particle goes to ent[p]; -2 marks a near particle, -1 neither)
 #pragma unroll 1
     for (int p = gt; p < nb; p += G) {
         int nkey = -1;
@@ -510,9 +519,7 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
             if constexpr (MANY) near = T.mnear[c] && rec_near_cand(hp, n_col, T.nf, rec, T.cand, T.vbc[c] < 0.0f);
             else near = n_col > 0 && T.mnear[c] && rec_near(d, hp, n_col, T.nf, rec);
             if (near) {
-                const int k = atomicAdd(&d.near_count[T.r], 1);
-                if (k < rp.n_part) d.near_list[rp.part_off + k] = gslot;
-                else atomicOr(&d.err[ERR_BOUNDS], 1u);
+                nkey = -2;
             } else {
                 Rec fl = rec;
                 rec_flight(hp, fl);
@@ -521,14 +528,46 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
         }
         ent[p] = nkey;
     }
-    // bin for the next collision: all count atomics, then the bucket writes
+    // bin for the next collision: all count atomics, then the bucket writes;
+    // the near particles join the near list with one atomic per warp, in
+    // flight together with the count atomics
     if (opts & CP_NEXT) {
+        int mine = 0;
+        const bool appends = n_col > 0;   // uniform: replicas without colloids skip the near list
+        if (appends)
+#pragma unroll
+            for (int u = 0; u < K; ++u) {
+                const int p = gt + u * G;
+                mine += (p < nb && ent[p] == -2) ? 1 : 0;
+            }
+        int incl = mine;
+        if (appends)
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if ((gt & 31) >= o) incl += y;
+            }
+        const int wtot = appends ? __shfl_sync(0xffffffffu, incl, 31) : 0;
+        int nbase = 0;
+        if ((gt & 31) == 31 && wtot > 0) nbase = atomicAdd(&d.near_count[T.r], wtot);
         int pos[K];
 #pragma unroll
         for (int u = 0; u < K; ++u) {
             const int p = gt + u * G;
             const int key = p < nb ? ent[p] : -1;
             pos[u] = key >= 0 ? atomicAdd(&d.count[a.nxt][key], 1) : -1;
+        }
+        if (wtot > 0) {
+            int k = __shfl_sync(0xffffffffu, nbase, 31) + incl - mine;
+#pragma unroll
+            for (int u = 0; u < K; ++u) {
+                const int p = gt + u * G;
+                if (p < nb && ent[p] == -2) {
+                    if (k < rp.n_part) d.near_list[rp.part_off + k] = T.base + pofs + p;
+                    else atomicOr(&d.err[ERR_BOUNDS], 1u);
+                    ++k;
+                }
+            }
         }
 #pragma unroll
         for (int u = 0; u < K; ++u) {
@@ -649,6 +688,10 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
                 for (int j = tid; j < rp.n_col; j += CP_THREADS) T.nf.Rb[j] = d.colRb_f[rp.col_off + j];
             }
         }
+        // the next ticket, taken now so that its round trip overlaps the
+        // count scan (tickets stay in order per CTA)
+        unsigned nt_next = 0u;
+        if (tid == 0) nt_next = atomicAdd(&d.ticket[T.epoch & 1u], 1u);
         const int gc0 = tile * CPT;
         // counts of the tile's cells (consumed: reset for reuse two passes later)
         int x = 0;
@@ -681,10 +724,10 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
 
         // tile base by decoupled look-back (warp 0): the tile's aggregate goes
         // out now, the scan over predecessors waits until the first batch
-        // needs the base (stage E); the next ticket is taken now
+        // needs the base (stage E)
         if (tid == 0) {
             tile_publish(d, T.epoch, tile, T.ls[CPT]);
-            T.next_tile = (int)atomicAdd(&d.ticket[T.epoch & 1u], 1u);
+            T.next_tile = (int)nt_next;
         }
 
         double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // T sum, cells, px, py, pz, ke, nB, n

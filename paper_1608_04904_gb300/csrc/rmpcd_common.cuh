@@ -648,7 +648,7 @@ __device__ __forceinline__ void st_release(unsigned long long *p, unsigned long 
 // ---------------------------------------------------------------------------
 // Tile base by decoupled look-back (Merrill & Garland 2016), run by one full
 // warp: publishes the tile's aggregate (unless the caller already did, by
-// tile_publish), inspects 32 predecessor tiles at a time summing aggregates
+// tile_publish), inspects 32 predecessor tiles, then 128 at a time, summing aggregates
 // back to the nearest inclusive prefix, publishes the tile's inclusive prefix
 // and returns its exclusive prefix (in every lane).
 // Tiles are taken in ticket order by resident CTAs, each finishing its tiles
@@ -660,6 +660,7 @@ __device__ __forceinline__ void st_release(unsigned long long *p, unsigned long 
 // ---------------------------------------------------------------------------
 constexpr unsigned long long LB_VALUE_MASK = (1ull << 46) - 1ull;
 constexpr int LB_SPIN_LIMIT = 1 << 22;
+constexpr int LB_W = 4;   // 32-tile windows the look-back inspects per round trip
 
 __device__ __forceinline__ void tile_publish(const Dev &d, uint32_t epoch, int tile, int total)
 {
@@ -676,29 +677,56 @@ __device__ __forceinline__ int tile_lookback(const Dev &d, uint32_t epoch, int t
     int t = tile - 1;
     int spins = 0;
     bool ok = true;
+    int nw = 1;   // windows per round: one first, LB_W once a scan has to go further back
     while (t >= 0) {
-        const int idx = t - lane;
-        unsigned long long flag = 2ull, val = 0ull;   // before tile 0: inclusive prefix 0
-        if (idx >= 0) {
-            const unsigned long long w = ld_acquire(&d.tile_state[idx]);
-            flag = ((w >> 48) == ep) ? ((w >> 46) & 3ull) : 0ull;
-            val = w & LB_VALUE_MASK;
+        // nw windows of 32 predecessors per round trip: position q = 32 u +
+        // lane is tile t - q (windows beyond nw read as not ready)
+        unsigned long long flag[LB_W], val[LB_W];
+#pragma unroll
+        for (int u = 0; u < LB_W; ++u) {
+            const int idx = t - lane - 32 * u;
+            flag[u] = u < nw ? 2ull : 0ull;   // before tile 0: inclusive prefix 0
+            val[u] = 0ull;
+            if (u < nw && idx >= 0) {
+                const unsigned long long w = ld_acquire(&d.tile_state[idx]);
+                flag[u] = ((w >> 48) == ep) ? ((w >> 46) & 3ull) : 0ull;
+                val[u] = w & LB_VALUE_MASK;
+            }
         }
-        const unsigned incl = __ballot_sync(0xffffffffu, flag == 2ull);
-        const unsigned ready = __ballot_sync(0xffffffffu, flag != 0ull);
-        const int first = incl ? __ffs(incl) - 1 : 31;
-        const unsigned need = (first == 31) ? 0xffffffffu : ((2u << first) - 1u);
-        if ((ready & need) != need) {
+        // the nearest inclusive prefix, and every position up to it ready
+        int first = -1;
+        bool ready_all = true;
+#pragma unroll
+        for (int u = 0; u < LB_W; ++u) {
+            if (u >= nw) break;
+            const unsigned incl = __ballot_sync(0xffffffffu, flag[u] == 2ull);
+            const unsigned ready = __ballot_sync(0xffffffffu, flag[u] != 0ull);
+            if (first < 0) {
+                if (incl) {
+                    const int f = __ffs(incl) - 1;
+                    const unsigned need = (f == 31) ? 0xffffffffu : ((2u << f) - 1u);
+                    ready_all = ready_all && (ready & need) == need;
+                    first = 32 * u + f;
+                } else {
+                    ready_all = ready_all && ready == 0xffffffffu;
+                }
+            }
+        }
+        if (!ready_all) {
             if (++spins > LB_SPIN_LIMIT) { ok = false; break; }
             __nanosleep(32);
             continue;
         }
-        unsigned long long part = (lane <= first) ? val : 0ull;
+        unsigned long long part = 0;
+#pragma unroll
+        for (int u = 0; u < LB_W; ++u)
+            if (u < nw && (first < 0 || 32 * u + lane <= first)) part += val[u];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
         prefix += __shfl_sync(0xffffffffu, part, 0);
-        if (incl) break;
-        t -= 32;
+        if (first >= 0) break;
+        t -= 32 * nw;
+        nw = LB_W;
     }
     ok = __all_sync(0xffffffffu, ok);
     if (!ok) prefix = 0x3FFFFFFFull;   // pushes every write of this tile out of bounds
