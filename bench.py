@@ -40,8 +40,9 @@ UNIT = "particle-steps/s"
 ALG_BYTES = {"mixed": 64, "fp64": 112}
 L2_FLUSH_BYTES = 256 << 20
 KERNEL_NAMES = {"cellpass": "k_cellpass", "md": "k_md", "prime": "k_particles", "obs": "k_obs_reduce"}
-KERNEL_SOURCES = ["rmpcd_common.cuh", "rmpcd_kernels.cuh", "k_cellpass.cu", "k_md.cu", "k_md_fast.cu",
-                  "k_md_body.cu", "k_particles.cu", "capi.cu"]
+# sources that decide a kernel's memory traffic: the kernel, the shared
+# headers and the host code that sizes its buffers and launch
+KERNEL_SOURCES = {"k_cellpass": ["rmpcd_common.cuh", "rmpcd_kernels.cuh", "k_cellpass.cu", "capi.cu"]}
 
 
 def workload(name, precision, seed_offset=0, n_replicas=None):
@@ -100,9 +101,9 @@ def oracle_system(oracle, rep, state):
                                body=body)
 
 
-def kernel_hash():
+def kernel_hash(kernel="k_cellpass"):
     h = hashlib.sha256()
-    for s in KERNEL_SOURCES:
+    for s in KERNEL_SOURCES[kernel]:
         h.update(open(os.path.join(ROOT, "paper_1608_04904_gb300", "csrc", s), "rb").read())
     return h.hexdigest()[:16]
 
@@ -122,7 +123,7 @@ def ncu_traffic(kernel, workload_name, precision):
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("kernel_hash") != kernel_hash():
+    if d.get("kernel_hash") != kernel_hash(kernel):
         return None
     e = d.get("kernels", {}).get(f"{kernel}/{workload_name}/{precision}")
     return None if e is None else e.get("bytes_per_launch")
