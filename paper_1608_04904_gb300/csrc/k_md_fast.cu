@@ -379,7 +379,7 @@ __device__ __forceinline__ void load_pconst(const ReplicaDev &rp, const FShared 
 __device__ __forceinline__ void pforce(const ReplicaDev &, const PConstM &K, const ColPM &C, int, FWorkM &w,
                                        long long acc[NC][3], bool &inside)
 {
-    float d[NC][3], fr[NC];
+    float d[NC][3], r2[NC];
     bool in[NC];
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
@@ -391,23 +391,29 @@ __device__ __forceinline__ void pforce(const ReplicaDev &, const PConstM &K, con
             m = dk < -K.hL[k] ? dk + K.L[k] : m;
             d[j][k] = (k < 2 || K.wrap_z) ? m : dk;
         }
-        const float eps = (w.fid & F_B) ? K.epsB[j] : K.epsA[j];
-        const float r2 = d[j][0] * d[j][0] + d[j][1] * d[j][1] + d[j][2] * d[j][2];
-        in[j] = j < K.nc && r2 < K.rc2[j];
-        fr[j] = wca_fr_m(eps, K.sig[j], r2);
+        r2[j] = d[j][0] * d[j][0] + d[j][1] * d[j][1] + d[j][2] * d[j][2];
+        in[j] = j < K.nc && r2[j] < K.rc2[j];
     }
     inside = (in[0] && K.cat[0]) || (in[1] && K.cat[1]);
+    // the WCA force only inside the cut-off: most near particles are outside
+    // it, and a warp whose lanes all are skips the work (the near list comes
+    // in cell order, so a warp's particles are neighbours)
+    float f[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        float f = 0.0f;
+    for (int j = 0; j < NC; ++j) {
+        if (in[j]) {
+            const float eps = (w.fid & F_B) ? K.epsB[j] : K.epsA[j];
+            const float fr = wca_fr_m(eps, K.sig[j], r2[j]);
 #pragma unroll
-        for (int j = 0; j < NC; ++j) {
-            const float fk = fr[j] * d[j][k];
-            f = in[j] ? f + fk : f;
-            acc[j][k] -= in[j] ? fx40(fk) : 0ll;
+            for (int k = 0; k < 3; ++k) {
+                const float fk = fr * d[j][k];
+                f[k] = f[k] + fk;
+                acc[j][k] -= fx40(fk);
+            }
         }
-        w.f[k] = f + K.g[k];
     }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) w.f[k] = f[k] + K.g[k];
 }
 
 __device__ __forceinline__ void pforce(const ReplicaDev &rp, const FShared &S, const ColPD &C, int nc, FWorkD &w,
