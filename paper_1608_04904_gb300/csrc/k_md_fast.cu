@@ -4,19 +4,22 @@
 // RATTLE, §1.5 catalytic A -> B.
 //
 // A thread-block cluster of CS CTAs integrates one replica.  The near
-// solvent sits in registers, spread over all threads of the cluster.  Every
-// warp keeps the colloid state lane-parallel (lane 3 j + t holds axis t of
-// colloid j) and integrates it itself from the force totals, so the colloid
-// update needs no hand-off between warps.  One round per force evaluation:
-//   every warp: colloid positions to all lanes (shuffles), the force on each
-//               of its particles, catalysis, the particle's move to the next
-//               round, warp sums of the reaction forces to shared memory;
+// solvent sits in registers, spread over all threads of the cluster; warp 0
+// of every CTA holds the colloid state lane-parallel (lane 3 j + t holds
+// axis t of colloid j) and integrates it from the force totals.  One round
+// per force evaluation:
+//   every warp: the colloid positions from shared memory, the force on each
+//               of its particles (the WCA part only inside the cut-off),
+//               warp sums of the reaction forces to shared memory;
 //   CTA barrier;
 //   warp 0:     the CTA's partials to every CTA of the cluster (st.async,
 //               counted on each CTA's mbarrier);
-//   every warp: waits for the round's partials, sums them, and runs the
-//               colloid second half kick + RATTLE velocity stage, first half
-//               kick + drift + RATTLE position stage.
+//   every warp: its particles' catalytic test and move to the next round;
+//   warp 0:     waits for the round's partials, sums them, runs the colloid
+//               second half kick + RATTLE velocity stage, first half kick +
+//               drift + RATTLE position stage, and writes the new positions
+//               to shared memory;
+//   CTA barrier.
 // Forces on the colloids are 64-bit fixed-point sums (2^-40), exact and
 // independent of the order of the near list and of the cluster size.
 //
@@ -100,21 +103,17 @@ __device__ __forceinline__ float small_i2f(int i)
 }
 
 // Sum over lanes 0..2, in lane order (every lane gets the result): the
-// component sum of a 3-vector held by axis lanes.
-__device__ __forceinline__ float sum3(float a)
-{
-    return (__shfl_sync(0xffffffffu, a, 0) + __shfl_sync(0xffffffffu, a, 1)) + __shfl_sync(0xffffffffu, a, 2);
-}
+// component sum of a 3-vector held by axis lanes (FP64 path).
 __device__ __forceinline__ double sum3(double a)
 {
     return (__shfl_sync(0xffffffffu, a, 0) + __shfl_sync(0xffffffffu, a, 1)) + __shfl_sync(0xffffffffu, a, 2);
 }
 
 // Carry of the FP32 offset into the integer cell: f = x - floor(x) (signed
-// zero included), k = floor(x), with no branch, so that the carries of the
-// six components overlap.  The wrapped cell moves one box length up or down
+// zero included), k = floor(x), with no branch (branches here split the
+// colloid update into serial blocks).  The wrapped cell moves one box length up or down
 // by selects; a colloid that crossed more than a box length in one sub-step
-// is left out of [0, L) here and put back by wrap_cells.
+// is left out of [0, L) here and put back at the end of the update.
 __device__ __forceinline__ void carry(const ReplicaDev &rp, int &Xi, int &Ci, float &Xf, int t)
 {
     const float x = Xf;
