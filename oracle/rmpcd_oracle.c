@@ -22,8 +22,9 @@
  *     and the composite Janus particle, whose bead network moves here as one
  *     rigid body (reading; see the rigid-body section at the end).
  *   - §1.1 / Appendix A: bulk RMPCD reaction B->A at a given rate.
- * Where the paper is silent the readings listed in the design doc are used; each
- * function below says which one it relies on.
+ * Where the paper is silent this file takes a reading of it (the order of the
+ * steps in an interval, the rotation sense, the reaction rule, the near/far
+ * bound, ...); each function below states the reading it relies on.
  *
  * Conventions: cell side a = 1, solvent mass m = 1.  Everything is FP64.  The
  * file must be compiled with -ffp-contract=off so that every product and sum
