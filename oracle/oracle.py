@@ -134,6 +134,13 @@ def lib():
             L.orc_body_forces.argtypes = [P(Params), i64, P(d), P(u8), C.c_int, P(d), P(d), P(d), P(i32),
                                           d, P(d), P(d), P(d), P(d), P(d)]
             L.orc_body_forces.restype = d
+            L.orc_rattle_pos_iter.argtypes = [C.c_int, P(i32), P(i32), P(d), P(d), P(d), P(d), P(d), d, d, C.c_int]
+            L.orc_rattle_pos_iter.restype = C.c_int
+            L.orc_rattle_vel_iter.argtypes = [C.c_int, P(i32), P(i32), P(d), P(d), P(d), P(d), d, C.c_int]
+            L.orc_rattle_vel_iter.restype = C.c_int
+            L.orc_network_step.argtypes = [C.c_int, P(d), C.c_int, P(i32), P(i32), P(d), P(d), P(d), P(d), d, d,
+                                           C.c_int]
+            L.orc_network_step.restype = C.c_int
             _lib = L
     return _lib
 
@@ -469,3 +476,58 @@ def slab_fields(p: dict) -> dict:
         T = (p["v2_sum"] - p["v_sum"] ** 2 / n[:, None]).sum(1) / (3.0 * (n - 1.0))
     T[n < 2] = np.nan
     return {"u": u, "T": T, "c_B": np.where(n > 0, p["n_B"] / np.maximum(n, 1), np.nan)}
+
+
+# -- linked bead network (iterative RATTLE) ---------------------------------------
+def _links(links):
+    la = np.ascontiguousarray([a for a, _ in links], dtype=np.int32)
+    lb = np.ascontiguousarray([b for _, b in links], dtype=np.int32)
+    return la, lb
+
+
+def rattle_pos_iter(links, d, m, xold, x, v, dt, tol=1e-13, max_sweeps=10000):
+    """Iterative RATTLE position stage (§1.4, Andersen 1983) on copies of x, v.
+    Returns (x, v, sweeps); sweeps = -1 when the sweeps ran out."""
+    la, lb = _links(links)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    xold = np.ascontiguousarray(xold, dtype=np.float64)
+    x = np.array(x, dtype=np.float64)
+    v = np.array(v, dtype=np.float64)
+    dd = C.c_double
+    n = lib().orc_rattle_pos_iter(len(la), _ptr(la, C.c_int32), _ptr(lb, C.c_int32), _ptr(d, dd), _ptr(m, dd),
+                                  _ptr(xold, dd), _ptr(x, dd), _ptr(v, dd), dt, tol, max_sweeps)
+    return x, v, int(n)
+
+
+def rattle_vel_iter(links, d, m, x, v, tol=1e-13, max_sweeps=10000):
+    """Iterative RATTLE velocity stage on a copy of v.  Returns (v, sweeps)."""
+    la, lb = _links(links)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    v = np.array(v, dtype=np.float64)
+    dd = C.c_double
+    n = lib().orc_rattle_vel_iter(len(la), _ptr(la, C.c_int32), _ptr(lb, C.c_int32), _ptr(d, dd), _ptr(m, dd),
+                                  _ptr(x, dd), _ptr(v, dd), tol, max_sweeps)
+    return v, int(n)
+
+
+def network_steps(links, d, m, x, v, dt, steps, F=None, tol=1e-13, max_sweeps=10000):
+    """`steps` velocity-Verlet steps of a linked bead network (forces F held
+    fixed, or none).  Returns (x, v, largest sweep count or -1)."""
+    la, lb = _links(links)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    x = np.array(x, dtype=np.float64)
+    v = np.array(v, dtype=np.float64)
+    Fp = None if F is None else _ptr(np.ascontiguousarray(F, dtype=np.float64), C.c_double)
+    dd = C.c_double
+    worst = 0
+    for _ in range(steps):
+        n = lib().orc_network_step(len(m), _ptr(m, dd), len(la), _ptr(la, C.c_int32), _ptr(lb, C.c_int32),
+                                   _ptr(d, dd), Fp, _ptr(x, dd), _ptr(v, dd), dt, tol, max_sweeps)
+        if n < 0:
+            return x, v, -1
+        worst = max(worst, n)
+    return x, v, worst

@@ -201,6 +201,19 @@ def fibonacci_sphere(nb: int, radius: float) -> np.ndarray:
     return radius * np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
 
 
+def bead_links(x, factor: float = 1.35):
+    """Links of a bead network for the iterative-RATTLE model of the Janus
+    particle: every bead pair closer than `factor` times the median
+    nearest-neighbour distance (on a Fibonacci shell this joins each bead to
+    its ring of neighbours).  Returns (pairs, lengths)."""
+    x = np.asarray(x, dtype=np.float64)
+    dist = np.sqrt(((x[:, None, :] - x[None, :, :]) ** 2).sum(-1))
+    np.fill_diagonal(dist, np.inf)
+    cut = factor * float(np.median(dist.min(1)))
+    a, b = np.nonzero(np.triu(dist < cut, 1))
+    return [(int(i), int(j)) for i, j in zip(a, b)], dist[a, b]
+
+
 def matrix_quaternion(R) -> np.ndarray:
     """Unit quaternion (w, x, y, z) of a proper rotation matrix (Shepperd's
     branch on the largest diagonal term)."""
