@@ -141,6 +141,12 @@ def lib():
             L.orc_network_step.argtypes = [C.c_int, P(d), C.c_int, P(i32), P(i32), P(d), P(d), P(d), P(d), d, d,
                                            C.c_int]
             L.orc_network_step.restype = C.c_int
+            L.orc_interval_network.argtypes = [P(Params), u32, i64, P(d), P(d), P(u8), P(u32), C.c_int, P(d), P(d),
+                                               P(d), P(d), P(d), P(i32), d, C.c_int, P(i32), P(i32), P(d), d,
+                                               C.c_int, C.c_int, P(u8)]
+            L.orc_interval_network.restype = C.c_int
+            L.orc_network_energy.argtypes = [P(Params), i64, P(d), P(u8), C.c_int, P(d), P(d), P(d), P(i32), d]
+            L.orc_network_energy.restype = d
             _lib = L
     return _lib
 
@@ -531,3 +537,68 @@ def network_steps(links, d, m, x, v, dt, steps, F=None, tol=1e-13, max_sweeps=10
             return x, v, -1
         worst = max(worst, n)
     return x, v, worst
+
+
+class Network:
+    """Janus particle as beads held at fixed distances by iterative RATTLE:
+    bead positions xb (unwrapped) and velocities vb, masses mb, eps_A, eps_B,
+    catalytic flags, the common WCA sigma, links [(a, b)] of lengths d."""
+
+    def __init__(self, xb, vb, mb, epsA, epsB, cat, sigma, links, d):
+        self.xb = np.array(xb, dtype=np.float64).reshape(-1, 3)
+        self.vb = np.array(vb, dtype=np.float64).reshape(-1, 3)
+        nb = len(self.xb)
+        self.mb = np.ascontiguousarray(np.broadcast_to(mb, nb), dtype=np.float64)
+        self.epsA = np.ascontiguousarray(np.broadcast_to(epsA, nb), dtype=np.float64)
+        self.epsB = np.ascontiguousarray(np.broadcast_to(epsB, nb), dtype=np.float64)
+        self.cat = np.ascontiguousarray(np.broadcast_to(cat, nb), dtype=np.int32)
+        self.sigma = float(sigma)
+        self.la, self.lb = _links(links)
+        self.d = np.ascontiguousarray(d, dtype=np.float64)
+
+    @classmethod
+    def from_body(cls, body, links, d):
+        """The beads of a rigid-body description (dict or Body) moving with it."""
+        B = body if isinstance(body, Body) else Body(body)
+        R = quat_matrix(B.q)
+        _, I = B.inertia()
+        r = B.b @ R.T
+        w = R @ (B.l / I)
+        return cls(B.x + r, B.v + np.cross(w, r), B.bead_mass, B.epsA, B.epsB, B.cat, B.sigma, links, d)
+
+    def momentum(self) -> np.ndarray:
+        return (self.mb[:, None] * self.vb).sum(0)
+
+    def kinetic_energy(self) -> float:
+        return 0.5 * float((self.mb[:, None] * self.vb ** 2).sum())
+
+    def com(self) -> np.ndarray:
+        return (self.mb[:, None] * self.xb).sum(0) / self.mb.sum()
+
+
+def interval_network(cfg, x, v, flags, ids, net: Network, step: int = 0, all_substep: bool = False,
+                     tol: float = 1e-12, max_sweeps: int = 10000):
+    """One interval of solvent + bead network (in place).  Returns (status,
+    near mask): status 0, 1 (centre of mass beyond the skin) or 2 (RATTLE did
+    not converge)."""
+    p = make_params(cfg)
+    dd, u8, u32, i32 = C.c_double, C.c_uint8, C.c_uint32, C.c_int32
+    n = len(x)
+    near = np.zeros(max(n, 1), dtype=np.uint8)
+    rc = lib().orc_interval_network(C.byref(p), step, n, _ptr(x, dd), _ptr(v, dd), _ptr(flags, u8), _ptr(ids, u32),
+                                    len(net.mb), _ptr(net.xb, dd), _ptr(net.vb, dd), _ptr(net.mb, dd),
+                                    _ptr(net.epsA, dd), _ptr(net.epsB, dd), _ptr(net.cat, i32), net.sigma,
+                                    len(net.la), _ptr(net.la, i32), _ptr(net.lb, i32), _ptr(net.d, dd), tol,
+                                    max_sweeps, 1 if all_substep else 0, _ptr(near, u8))
+    return int(rc), near[:n].astype(bool)
+
+
+def network_energy(cfg, x, flags, net: Network) -> float:
+    """WCA energy between the solvent and the beads."""
+    p = make_params(cfg)
+    dd = C.c_double
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    flags = np.ascontiguousarray(flags, dtype=np.uint8)
+    return float(lib().orc_network_energy(C.byref(p), len(x), _ptr(x, dd), _ptr(flags, C.c_uint8), len(net.mb),
+                                          _ptr(net.xb, dd), _ptr(net.epsA, dd), _ptr(net.epsB, dd),
+                                          _ptr(net.cat, C.c_int32), net.sigma))

@@ -1175,3 +1175,176 @@ int orc_network_step(int nb, const double *m, int nl, const int32_t *la, const i
     if (sp < 0 || sv < 0) return -1;
     return sp > sv ? sp : sv;
 }
+
+/* Force on one solvent particle from every bead of a network (ascending bead
+ * order, wrapped bead positions Xw); the reaction goes to the bead's
+ * fixed-point sums Fq[3 nb].  Returns 1 if the particle is inside a
+ * catalytic bead's range. */
+static int network_solvent_force(const orc_params *p, int nb, const double *Xw, const double *epsA,
+                                 const double *epsB, const int32_t *cat, double sigma, double rc2, const double *x,
+                                 uint8_t fl, double f[3], int64_t *Fq, double *energy)
+{
+    int inside = 0;
+    f[0] = f[1] = f[2] = 0.0;
+    for (int j = 0; j < nb; ++j) {
+        double d[3] = {x[0] - Xw[3 * j], x[1] - Xw[3 * j + 1], x[2] - Xw[3 * j + 2]};
+        min_image(p, d);
+        double fj[3], ej = 0.0;
+        const double eps = (fl & F_B) ? epsB[j] : epsA[j];
+        if (orc_wca_force(d, sigma, eps, rc2, fj, energy ? &ej : NULL)) {
+            for (int k = 0; k < 3; ++k) {
+                f[k] = f[k] + fj[k];
+                Fq[3 * j + k] -= llrint(fj[k] * FX_SCALE);
+            }
+            if (energy) *energy = *energy + ej;
+            if (cat[j]) inside = 1;
+        }
+    }
+    return inside;
+}
+
+static void network_frames(const orc_params *p, int nb, const double *xb, double *Xw)
+{
+    for (int j = 0; j < nb; ++j) wrapped(p, xb + 3 * j, Xw + 3 * j);
+}
+
+static void network_com(int nb, const double *xb, const double *mb, double X[3], double *M)
+{
+    double s[3] = {0.0, 0.0, 0.0}, m = 0.0;
+    for (int j = 0; j < nb; ++j) {
+        m = m + mb[j];
+        for (int t = 0; t < 3; ++t) s[t] = s[t] + mb[j] * xb[3 * j + t];
+    }
+    for (int t = 0; t < 3; ++t) X[t] = s[t] / m;
+    *M = m;
+}
+
+/* One collision interval of solvent + a Janus particle made of beads held at
+ * fixed distances by iterative RATTLE (§1.4, §1.5): as orc_interval_body, but
+ * every bead is a point mass in the velocity-Verlet sub-steps, kicked by the
+ * reactions of its own bead-solvent forces, with the position stage after
+ * each drift and the velocity stage after each second half kick.  xb, vb
+ * (bead positions, unwrapped, and velocities) are updated in place.  Near
+ * particles: within the beads' bounding sphere about their centre of mass at
+ * the start (largest bead distance + r_c) plus |v| tau + |g| tau^2 / 2 +
+ * skin.  Returns 0; 1 if the centre of mass moved further than skin; 2 if a
+ * RATTLE stage did not converge within max_sweeps. */
+int orc_interval_network(const orc_params *p, uint32_t step, int64_t n, double *x, double *v, uint8_t *flags,
+                         const uint32_t *id, int nb, double *xb, double *vb, const double *mb, const double *epsA,
+                         const double *epsB, const int32_t *cat, double sigma, int nl, const int32_t *la,
+                         const int32_t *lb, const double *dl, double tol, int max_sweeps, int all_substep,
+                         uint8_t *near_out)
+{
+    const double rc2 = orc_wca_rc2(sigma);
+    double X0[3], M;
+    network_com(nb, xb, mb, X0, &M);
+    double reach = 0.0;
+    for (int j = 0; j < nb; ++j) {
+        double e2 = 0.0;
+        for (int t = 0; t < 3; ++t) { double e = xb[3 * j + t] - X0[t]; e2 = e2 + e * e; }
+        if (sqrt(e2) > reach) reach = sqrt(e2);
+    }
+    reach = reach + sqrt(rc2);
+    double X0w[3];
+    wrapped(p, X0, X0w);
+    const double gnorm = sqrt(p->g[0] * p->g[0] + p->g[1] * p->g[1] + p->g[2] * p->g[2]);
+    const size_t nb3 = 3 * (size_t)(nb > 0 ? nb : 1);
+    double *Xw = (double *)malloc(sizeof(double) * nb3);
+    double *xold = (double *)malloc(sizeof(double) * nb3);
+    double *Fb = (double *)malloc(sizeof(double) * nb3);
+    int64_t *Fq = (int64_t *)malloc(sizeof(int64_t) * nb3);
+    network_frames(p, nb, xb, Xw);
+
+    uint8_t *near = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+    int64_t n_near = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (all_substep) { near[i] = 1; ++n_near; continue; }
+        const double *vi = v + 3 * i;
+        const double speed = sqrt(vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]);
+        double d[3] = {x[3 * i] - X0w[0], x[3 * i + 1] - X0w[1], x[3 * i + 2] - X0w[2]};
+        min_image(p, d);
+        const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        const double R = reach + speed * p->tau + 0.5 * gnorm * p->tau * p->tau + p->skin;
+        if (r2 < R * R) { near[i] = 1; ++n_near; }
+    }
+    if (near_out) memcpy(near_out, near, (size_t)n);
+    orc_flight(p, n, x, v, near);
+
+    int64_t *list = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_near > 0 ? n_near : 1));
+    for (int64_t i = 0, k = 0; i < n; ++i) if (near[i]) list[k++] = i;
+    double *f = (double *)malloc(sizeof(double) * 3 * (size_t)(n_near > 0 ? n_near : 1));
+    const double dt = p->tau / (double)p->n_md;
+    const double hdt = 0.5 * dt;
+    int status = 0;
+
+    /* forces at the start of the interval */
+    memset(Fq, 0, sizeof(int64_t) * nb3);
+    for (int64_t k = 0; k < n_near; ++k) {
+        const int64_t i = list[k];
+        network_solvent_force(p, nb, Xw, epsA, epsB, cat, sigma, rc2, x + 3 * i, flags[i], f + 3 * k, Fq, NULL);
+        for (int t = 0; t < 3; ++t) f[3 * k + t] = f[3 * k + t] + p->g[t];
+    }
+    for (size_t c = 0; c < 3 * (size_t)nb; ++c) Fb[c] = (double)Fq[c] * FX_INV;
+
+    for (int s = 0; s < p->n_md; ++s) {
+        /* beads: half kick, drift, position stage */
+        for (int j = 0; j < nb; ++j)
+            for (int t = 0; t < 3; ++t) {
+                vb[3 * j + t] = fma(hdt, Fb[3 * j + t] / mb[j], vb[3 * j + t]);
+                xold[3 * j + t] = xb[3 * j + t];
+                xb[3 * j + t] = fma(dt, vb[3 * j + t], xb[3 * j + t]);
+            }
+        if (orc_rattle_pos_iter(nl, la, lb, dl, mb, xold, xb, vb, dt, tol, max_sweeps) < 0) status = 2;
+        network_frames(p, nb, xb, Xw);
+        /* solvent: half kick, drift */
+        for (int64_t k = 0; k < n_near; ++k) {
+            const int64_t i = list[k];
+            for (int t = 0; t < 3; ++t) {
+                v[3 * i + t] = fma(hdt, f[3 * k + t], v[3 * i + t]);
+                x[3 * i + t] = fma(dt, v[3 * i + t], x[3 * i + t]);
+            }
+        }
+        /* new forces, catalytic conversion, second half kicks, velocity stage */
+        memset(Fq, 0, sizeof(int64_t) * nb3);
+        for (int64_t k = 0; k < n_near; ++k) {
+            const int64_t i = list[k];
+            const int in = network_solvent_force(p, nb, Xw, epsA, epsB, cat, sigma, rc2, x + 3 * i, flags[i],
+                                                 f + 3 * k, Fq, NULL);
+            for (int t = 0; t < 3; ++t) f[3 * k + t] = f[3 * k + t] + p->g[t];
+            catalytic_step(p, flags + i, id[i], in, step, s);
+        }
+        for (size_t c = 0; c < 3 * (size_t)nb; ++c) Fb[c] = (double)Fq[c] * FX_INV;
+        for (int j = 0; j < nb; ++j)
+            for (int t = 0; t < 3; ++t) vb[3 * j + t] = fma(hdt, Fb[3 * j + t] / mb[j], vb[3 * j + t]);
+        if (orc_rattle_vel_iter(nl, la, lb, dl, mb, xb, vb, tol, max_sweeps) < 0) status = 2;
+        for (int64_t k = 0; k < n_near; ++k) {
+            const int64_t i = list[k];
+            for (int t = 0; t < 3; ++t) v[3 * i + t] = fma(hdt, f[3 * k + t], v[3 * i + t]);
+        }
+    }
+    for (int64_t k = 0; k < n_near; ++k) wrap_periodic(p, x + 3 * list[k]);
+
+    double X1[3];
+    network_com(nb, xb, mb, X1, &M);
+    double dd = 0.0;
+    for (int t = 0; t < 3; ++t) { const double e = X1[t] - X0[t]; dd = dd + e * e; }
+    if (status == 0 && !(dd <= p->skin * p->skin)) status = 1;   /* NaN counts as a violation */
+    free(Xw); free(xold); free(Fb); free(Fq); free(near); free(list); free(f);
+    return status;
+}
+
+/* WCA energy between the solvent and a bead network (for the tests). */
+double orc_network_energy(const orc_params *p, int64_t n, const double *x, const uint8_t *flags, int nb,
+                          const double *xb, const double *epsA, const double *epsB, const int32_t *cat, double sigma)
+{
+    const size_t nb3 = 3 * (size_t)(nb > 0 ? nb : 1);
+    double *Xw = (double *)malloc(sizeof(double) * nb3);
+    int64_t *Fq = (int64_t *)calloc(nb3, sizeof(int64_t));
+    network_frames(p, nb, xb, Xw);
+    const double rc2 = orc_wca_rc2(sigma);
+    double e = 0.0, f[3];
+    for (int64_t i = 0; i < n; ++i)
+        network_solvent_force(p, nb, Xw, epsA, epsB, cat, sigma, rc2, x + 3 * i, flags[i], f, Fq, &e);
+    free(Xw); free(Fq);
+    return e;
+}

@@ -113,3 +113,85 @@ def test_free_rotation_converges_to_the_rigid_body_at_second_order(orc):
     assert err[1] < 2e-3
     assert 3.0 < err[0] / err[1] < 5.5, err
     assert abs(ke[1] - ke0) < 1e-3 * ke0
+
+
+def _janus_case(orc, n_md=25, L=16, factor=2.0, seed=4):
+    """A spinning 60-bead Janus particle in a 16^3 solvent, as a rigid body and
+    as the same beads linked to their neighbours (a rigid shell)."""
+    cfg = synth.base_config(L=(L, L, L), alpha=np.radians(130.0), tau=0.5, n_md=n_md, kT=1.0, seed=seed)
+    body = synth.janus_body(60, (L / 2 + 0.3, L / 2 - 0.2, L / 2 + 0.1), seed=seed)
+    body["l"] = body["l"] * 20.0
+    x, v, fl = synth.solvent(cfg, synth.body_exclusion(body), seed=seed + 1, frac_b=0.2)
+    xb0 = body["x"] + body["b"] @ orc.quat_matrix(body["q"]).T
+    links, d = synth.bead_links(xb0, factor)
+    return cfg, body, links, d, x, v, fl
+
+
+def test_network_interval_conserves_momentum_energy_and_links(orc):
+    """One interval of solvent and bead network: total momentum to rounding
+    (the reactions are exact fixed-point sums), energy within 1e-4 relative
+    (velocity Verlet at dt 0.02), every link held in length and without
+    relative velocity along it, no skin violation."""
+    cfg, body, links, d, x, v, fl = _janus_case(orc)
+    net = orc.Network.from_body(body, links, d)
+    ids = np.arange(len(x), dtype=np.uint32)
+    p0 = v.sum(0) + net.momentum()
+    e0 = 0.5 * (v ** 2).sum() + net.kinetic_energy() + orc.network_energy(cfg, x, fl, net)
+    st, near = orc.interval_network(cfg, x, v, fl, ids, net)
+    assert st == 0 and near.sum() > 1000
+    p1 = v.sum(0) + net.momentum()
+    e1 = 0.5 * (v ** 2).sum() + net.kinetic_energy() + orc.network_energy(cfg, x, fl, net)
+    assert np.allclose(p1, p0, rtol=0, atol=1e-10)
+    assert abs(e1 - e0) < 1e-4 * e0
+    r = net.xb[net.la] - net.xb[net.lb]
+    assert np.abs(np.sqrt((r * r).sum(1)) - net.d).max() < 1e-10
+    # the velocity stage: no relative velocity along any link
+    w = net.vb[net.la] - net.vb[net.lb]
+    assert np.abs((w * r).sum(1)).max() < 1e-10 * net.d.max()
+
+
+def test_network_interval_free_flight_equals_substepping(orc):
+    """Particles beyond the bounding sphere fly freely; sub-stepping every
+    particle instead gives the same beads and near particles bit for bit and
+    the far particles within rounding."""
+    cfg, body, links, d, x, v, fl = _janus_case(orc)
+    ids = np.arange(len(x), dtype=np.uint32)
+    out = []
+    for all_sub in (False, True):
+        net = orc.Network.from_body(body, links, d)
+        xs, vs, fs = x.copy(), v.copy(), fl.copy()
+        st, near = orc.interval_network(cfg, xs, vs, fs, ids, net, all_substep=all_sub)
+        assert st == 0
+        out.append((xs, vs, fs, net, near))
+    (xa, va, fa, na, near), (xb, vb, fb, nb_, _) = out
+    assert np.array_equal(na.xb, nb_.xb) and np.array_equal(na.vb, nb_.vb)
+    assert np.array_equal(xa[near], xb[near]) and np.array_equal(va[near], vb[near])
+    assert np.array_equal(fa, fb)
+    assert np.allclose(xa[~near], xb[~near], rtol=0, atol=1e-12)
+    assert np.allclose(va[~near], vb[~near], rtol=0, atol=1e-14)
+
+
+def test_network_interval_converges_to_the_rigid_body_interval(orc):
+    """The linked shell moves as a rigid body, so its interval and the
+    rigid-body interval approximate the same motion with two different
+    second-order integrators: their solvent states and centres of mass
+    differ by O(dt^2) -- a fourth when the sub-step halves -- and the
+    catalytic flags agree."""
+    diffs = []
+    for n_md in (25, 50):
+        cfg, body, links, d, x, v, fl = _janus_case(orc, n_md=n_md)
+        net = orc.Network.from_body(body, links, d)
+        ids = np.arange(len(x), dtype=np.uint32)
+        xn, vn, fn = x.copy(), v.copy(), fl.copy()
+        st, _ = orc.interval_network(cfg, xn, vn, fn, ids, net, tol=1e-13)
+        assert st == 0
+        s = orc.OracleSystem(cfg, x.copy(), v.copy(), fl.copy(), body=body)
+        s.interval()
+        L = cfg["L"][0]
+        dx = np.abs(xn - s.x)
+        dx = np.minimum(dx, L - dx)
+        diffs.append((dx.max(), np.abs(vn - s.v).max(), np.abs(net.com() - s.body.x).max()))
+        assert np.array_equal(fn, s.flags)
+    for k in range(3):
+        assert 3.5 < diffs[0][k] / diffs[1][k] < 4.5, diffs
+    assert diffs[1][0] < 1e-6 and diffs[1][1] < 1e-5
