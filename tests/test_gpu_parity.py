@@ -9,7 +9,7 @@ import pytest
 
 from oracle import oracle as orc
 from paper_1608_04904_gb300 import api, build, synth
-from parity_util import by_id, near_boundary, pos_bad, vel_bad
+from parity_util import by_id, compare_step as _compare_step, near_boundary, pos_bad, vel_bad
 
 pytestmark = pytest.mark.gpu
 
@@ -172,32 +172,6 @@ def test_md_interval_parity(precision):
     r = gc["x"][0] - gc["x"][1]
     # exact RATTLE: to rounding of the path's precision
     assert abs(np.linalg.norm(r) - 4.5) < (1e-11 if precision == "fp64" else 1e-5)
-
-
-def _compare_step(cfg, st, o, precision):
-    """Compare a GPU state with the oracle's after full intervals."""
-    gid, gx, gv, gf, gc = by_id(st["id"], st["id"], st["x"], st["v"], st["flags"], st["cell"])
-    oid, ox, ov, of, oc = by_id(o.id, o.id, o.x, o.v, o.flags, o.key)
-    assert np.array_equal(gid, oid)
-    if precision == "fp64":
-        assert np.array_equal(st["id"], o.id)
-        assert np.array_equal(gc, oc)
-        assert np.array_equal(gf, of)
-        assert not pos_bad(gx, ox, cfg["L"], cfg.get("walls", 0), "fp64").any()
-        assert not vel_bad(gv, ov, cfg["kT"], "fp64").any()
-        return
-    # mixed: keys may differ for particles that FP32 flight puts on the other
-    # side of a cell plane; those cells are excluded from the velocity check
-    mism = gc != oc
-    s = o.shift
-    border = near_boundary(ox, s, 1e-4)
-    assert np.all(border[mism]), "key mismatch away from a cell boundary"
-    assert mism.sum() <= max(3, 1e-4 * len(gc))
-    badcells = np.isin(oc, oc[mism]) | np.isin(oc, gc[mism])
-    assert not pos_bad(gx, ox, cfg["L"], cfg.get("walls", 0), "mixed").any()
-    vb = vel_bad(gv, ov, cfg["kT"], "mixed") & ~badcells
-    assert vb.sum() <= 2, int(vb.sum())
-    assert (gf != of).sum() <= 2 + mism.sum()
 
 
 @pytest.mark.parametrize("precision", PRECS)
