@@ -4,7 +4,10 @@ pass per interval): every particle against the FP64 oracle after one step.
 
 - reactive sphere dimer in a 32^3 box at density 10 (327,680 solvent);
 - Poiseuille channel 128^3 between stick walls at density 10 (20,971,520
-  solvent, virtual wall particles, body force).
+  solvent, virtual wall particles, body force);
+- the thermal-gradient suspension 256x64x64 (10,485,760 solvent, 64 WCA
+  spheres with colloid-colloid LJ, two MPC-AT slabs), and its six-sphere
+  48x32x32 version.
 
 The comparison is the one of the reduced-size tests (keys, permutation and
 flags bit-exact on the FP64 path; the mixed path within 1e-5 with key
@@ -15,7 +18,7 @@ import pytest
 
 from oracle import oracle as orc
 from paper_1608_04904_gb300 import api, build, synth
-from parity_util import compare_step
+from parity_util import by_id, compare_step, near_boundary, pos_bad, vel_bad
 
 pytestmark = pytest.mark.gpu
 
@@ -65,3 +68,41 @@ def test_poiseuille128_full_size_step(precision):
     compare_step(cfg, st, o, precision)
     # the walls hold every particle
     assert st["x"][:, 2].min() >= 0.0 and st["x"][:, 2].max() <= cfg["L"][2]
+
+
+def _compare_many(cfg, st, o, precision, n_col):
+    """compare_step for many colloids: on the mixed path each colloid can
+    have a particle grazing its cut-off take the other branch in FP32, so the
+    counts allowed grow with the number of colloids."""
+    if precision == "fp64":
+        compare_step(cfg, st, o, precision)
+        return
+    gid, gx, gv, gf, gc = by_id(st["id"], st["id"], st["x"], st["v"], st["flags"], st["cell"])
+    oid, ox, ov, of, oc = by_id(o.id, o.id, o.x, o.v, o.flags, o.key)
+    assert np.array_equal(gid, oid)
+    mism = gc != oc
+    assert np.all(near_boundary(ox, o.shift, 1e-4)[mism]), "key mismatch away from a cell boundary"
+    assert mism.sum() <= max(3, 1e-4 * len(gc))
+    badcells = np.isin(oc, oc[mism]) | np.isin(oc, gc[mism])
+    allow = 2 + 2 * n_col
+    assert pos_bad(gx, ox, cfg["L"], cfg.get("walls", 0), "mixed").sum() <= allow
+    assert (vel_bad(gv, ov, cfg["kT"], "mixed") & ~badcells).sum() <= allow
+    assert (gf != of).sum() <= allow + mism.sum()
+
+
+@pytest.mark.parametrize("precision", PRECS)
+@pytest.mark.parametrize("size", ["six_spheres", "full"])
+def test_thermal_suspension_step(precision, size):
+    """Spheres with colloid-colloid LJ and MPC-AT slabs (the general FP64 MD
+    kernel, the wide mixed one) against the oracle after one fused step."""
+    if size == "full":
+        cfg, col, bonds = synth.thermal(precision=precision)
+    else:
+        cfg, col, bonds = synth.thermal(precision=precision, L=(48, 32, 32), n_spheres=6)
+    x, v, fl = synth.solvent(cfg, col, seed=cfg["seed"] + 100)
+    st, cols, o = _run(cfg, col, bonds, x, v, fl, precision, step=3)
+    _compare_many(cfg, st, o, precision, len(col))
+    tol = 1e-10 if precision == "fp64" else 1e-5
+    d = cols["x"] - o.X
+    d -= np.asarray(cfg["L"], float) * np.round(d / np.asarray(cfg["L"], float))
+    assert np.abs(d).max() < tol * max(cfg["L"])
