@@ -147,6 +147,10 @@ def lib():
             L.orc_interval_network.restype = C.c_int
             L.orc_network_energy.argtypes = [P(Params), i64, P(d), P(u8), C.c_int, P(d), P(d), P(d), P(i32), d]
             L.orc_network_energy.restype = d
+            L.orc_hilbert_index.argtypes = [C.c_int, u32, u32, u32]
+            L.orc_hilbert_index.restype = C.c_uint64
+            L.orc_hilbert_rank.argtypes = [P(i32), P(i64)]
+            L.orc_hilbert_rank.restype = C.c_int
             _lib = L
     return _lib
 
@@ -602,3 +606,18 @@ def network_energy(cfg, x, flags, net: Network) -> float:
     return float(lib().orc_network_energy(C.byref(p), len(x), _ptr(x, dd), _ptr(flags, C.c_uint8), len(net.mb),
                                           _ptr(net.xb, dd), _ptr(net.epsA, dd), _ptr(net.epsB, dd),
                                           _ptr(net.cat, C.c_int32), net.sigma))
+
+
+# -- Hilbert order of the cells ----------------------------------------------------
+def hilbert_index(m: int, x: int, y: int, z: int) -> int:
+    """Index of cell (x, y, z) on the 3-D Hilbert curve through the 2^m cube."""
+    return int(lib().orc_hilbert_index(int(m), int(x), int(y), int(z)))
+
+
+def hilbert_rank(L) -> np.ndarray:
+    """Place of every cell c = x + L0 (y + L1 z) in the Hilbert order of the box."""
+    Lc = np.ascontiguousarray([int(a) for a in L], dtype=np.int32)
+    rank = np.zeros(int(np.prod(Lc)), dtype=np.int64)
+    if lib().orc_hilbert_rank(_ptr(Lc, C.c_int32), _ptr(rank, C.c_int64)) != 0:
+        raise MemoryError("hilbert_rank")
+    return rank

@@ -1348,3 +1348,70 @@ double orc_network_energy(const orc_params *p, int64_t n, const double *x, const
     free(Xw); free(Fq);
     return e;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Hilbert order of the cells (§1.4: the paper sorts the solvent by compact  */
+/* Hilbert indices).  Reading: the cells of an L0 x L1 x L2 box are ranked   */
+/* by the index of the standard 3-D Hilbert curve through the smallest      */
+/* enclosing cube of side 2^m -- the order compact indices preserve -- and  */
+/* the rank is the cell's place in the sort.  The index follows Skilling's */
+/* transform (AIP Conf. Proc. 707, 2004): undo the excess rotations level   */
+/* by level, Gray-encode across the axes, then interleave the bits.         */
+/* ------------------------------------------------------------------------ */
+uint64_t orc_hilbert_index(int m, uint32_t x, uint32_t y, uint32_t z)
+{
+    uint32_t X[3] = {x, y, z};
+    if (m <= 0) return 0;
+    const uint32_t top = 1u << (m - 1);
+    /* rotations and reflections, from the coarsest level down */
+    for (uint32_t Q = top; Q > 1; Q >>= 1) {
+        const uint32_t P = Q - 1;
+        for (int i = 0; i < 3; ++i) {
+            if (X[i] & Q) {
+                X[0] ^= P;
+            } else {
+                const uint32_t t = (X[0] ^ X[i]) & P;
+                X[0] ^= t;
+                X[i] ^= t;
+            }
+        }
+    }
+    /* Gray encoding across the axes */
+    for (int i = 1; i < 3; ++i) X[i] ^= X[i - 1];
+    uint32_t t = 0;
+    for (uint32_t Q = top; Q > 1; Q >>= 1)
+        if (X[2] & Q) t ^= Q - 1;
+    for (int i = 0; i < 3; ++i) X[i] ^= t;
+    /* interleave: bit b of the index triple (X0, X1, X2), most significant first */
+    uint64_t h = 0;
+    for (int b = m - 1; b >= 0; --b)
+        for (int i = 0; i < 3; ++i) h = (h << 1) | ((X[i] >> b) & 1u);
+    return h;
+}
+
+static int cmp_u64_pair(const void *a, const void *b)
+{
+    const uint64_t *p = (const uint64_t *)a, *q = (const uint64_t *)b;
+    return (p[0] > q[0]) - (p[0] < q[0]);
+}
+
+/* rank[c] for every cell c = x + L0 (y + L1 z) of the box: its place in the
+ * Hilbert order.  Returns 0, or -1 if memory ran out. */
+int orc_hilbert_rank(const int32_t L[3], int64_t *rank)
+{
+    int m = 0;
+    const int32_t Lmax = L[0] > L[1] ? (L[0] > L[2] ? L[0] : L[2]) : (L[1] > L[2] ? L[1] : L[2]);
+    while ((1 << m) < Lmax) ++m;
+    const int64_t n = (int64_t)L[0] * L[1] * L[2];
+    uint64_t *pairs = (uint64_t *)malloc(sizeof(uint64_t) * 2 * (size_t)(n > 0 ? n : 1));
+    if (!pairs) return -1;
+    for (int64_t c = 0; c < n; ++c) {
+        const uint32_t x = (uint32_t)(c % L[0]), y = (uint32_t)((c / L[0]) % L[1]), z = (uint32_t)(c / ((int64_t)L[0] * L[1]));
+        pairs[2 * c] = orc_hilbert_index(m, x, y, z);
+        pairs[2 * c + 1] = (uint64_t)c;
+    }
+    qsort(pairs, (size_t)n, 2 * sizeof(uint64_t), cmp_u64_pair);
+    for (int64_t r = 0; r < n; ++r) rank[pairs[2 * r + 1]] = r;
+    free(pairs);
+    return 0;
+}
