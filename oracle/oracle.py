@@ -151,6 +151,8 @@ def lib():
             L.orc_hilbert_index.restype = C.c_uint64
             L.orc_hilbert_rank.argtypes = [P(i32), P(i64)]
             L.orc_hilbert_rank.restype = C.c_int
+            L.orc_species_reservoirs.argtypes = [P(Params), i64, P(i64), P(i64), P(u8), i32, i32, i32, i32]
+            L.orc_species_reservoirs.restype = None
             _lib = L
     return _lib
 
@@ -404,6 +406,17 @@ class OracleSystem:
         lib().orc_bulk_react(C.byref(self.p), self.step_index, self.ncells, _ptr(self.count, C.c_int64),
                              _ptr(self.start, C.c_int64), _ptr(self.flags, C.c_uint8))
 
+    def reservoirs(self) -> None:
+        """Species reservoirs of the chemotactic set-up (cfg["reservoirs"] =
+        ((ya0, ya1), (yb0, yb1)), y columns of the collision grid), if any."""
+        res = self.cfg.get("reservoirs")
+        if not res:
+            return
+        (ya0, ya1), (yb0, yb1) = res
+        lib().orc_species_reservoirs(C.byref(self.p), self.ncells, _ptr(self.count, C.c_int64),
+                                     _ptr(self.start, C.c_int64), _ptr(self.flags, C.c_uint8),
+                                     int(ya0), int(ya1), int(yb0), int(yb1))
+
     def step(self, k: int = 1, all_substep: bool = False) -> None:
         """k full collision intervals."""
         for _ in range(k):
@@ -411,6 +424,7 @@ class OracleSystem:
             self.shift_and_sort()
             self.collide()
             self.react()
+            self.reservoirs()
             self.step_index += 1
 
     # -- observables ---------------------------------------------------------

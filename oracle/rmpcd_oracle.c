@@ -1415,3 +1415,24 @@ int orc_hilbert_rank(const int32_t L[3], int64_t *rank)
     free(pairs);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Species reservoirs (§1.5 chemotactic_cell: a Poiseuille flow with a       */
+/* two-species gradient across it).  Reading: after each collision every     */
+/* particle of a cell whose y column on the collision grid lies in [ya0,     */
+/* ya1) becomes A, and in [yb0, yb1) becomes B (tags cleared); diffusion     */
+/* between the two layers sets up the gradient.                              */
+/* ------------------------------------------------------------------------ */
+void orc_species_reservoirs(const orc_params *p, int64_t n_cells, const int64_t *count, const int64_t *start,
+                            uint8_t *flags, int32_t ya0, int32_t ya1, int32_t yb0, int32_t yb1)
+{
+    for (int64_t c = 0; c < n_cells; ++c) {
+        const int32_t cy = (int32_t)((c / p->L[0]) % p->L[1]);
+        int to = -1;
+        if (cy >= ya0 && cy < ya1) to = 0;
+        else if (cy >= yb0 && cy < yb1) to = 1;
+        if (to < 0) continue;
+        for (int64_t k = start[c]; k < start[c] + count[c]; ++k)
+            flags[k] = (uint8_t)(to ? F_B : 0);
+    }
+}
