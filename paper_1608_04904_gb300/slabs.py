@@ -15,6 +15,14 @@ particles in the same order as on one rank, so the decomposed run equals the
 single-rank run bit for bit.  Because the grid shift moves every step, the
 columns a rank owns are those of the shifted grid, not fixed positions.
 
+With colloids, one rank integrates them: before each interval every rank
+sends it the particles that may come near a colloid (`within`, a
+conservative superset of the near list: the integrating rank's MD decides
+near or far exactly, and a far particle flies the same there as at home),
+and after the interval the colloid state is broadcast (`broadcast_array`).
+The colloid force sums are exact fixed-point sums, so their order does not
+matter and the decomposed run still equals the single-rank run.
+
 Transport is `torch.distributed` (gloo on CPU; NCCL for device tensors)."""
 from __future__ import annotations
 
@@ -83,3 +91,30 @@ def global_slots(key_sorted, n_cells: int, group=None) -> np.ndarray:
     lstart = np.concatenate([[0], np.cumsum(local)[:-1]])
     i = np.arange(len(key), dtype=np.int64)
     return gstart[key] + (i - lstart[key])
+
+
+def within(x, centers, radius, L, walls: bool = False) -> np.ndarray:
+    """Particles closer than radius[j] to some centers[j] (a scalar radius
+    applies to every centre; minimum image on the periodic axes): the routing
+    test that picks the particles to send to the rank integrating the
+    colloids."""
+    x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros(len(x), dtype=bool)
+    L = np.asarray(L, dtype=np.float64)
+    per = np.array([True, True, not walls])
+    centers = np.asarray(centers, dtype=np.float64).reshape(-1, 3)
+    radius = np.broadcast_to(np.asarray(radius, dtype=np.float64), (len(centers),))
+    for c, r in zip(centers, radius):
+        d = x - c
+        d[:, per] -= L[per] * np.round(d[:, per] / L[per])
+        out |= (d * d).sum(1) < float(r) * float(r)
+    return out
+
+
+def broadcast_array(a, src: int = 0, group=None) -> np.ndarray:
+    """The array held by rank src, on every rank (same shape and dtype on
+    all ranks), bit for bit."""
+    a = np.ascontiguousarray(a)
+    buf = torch.from_numpy(a.view(np.uint8).reshape(-1).copy())
+    dist.broadcast(buf, src=src, group=group)
+    return buf.numpy().view(a.dtype).reshape(a.shape)
