@@ -23,7 +23,8 @@ and after the interval the colloid state is broadcast (`broadcast_array`).
 The colloid force sums are exact fixed-point sums, so their order does not
 matter and the decomposed run still equals the single-rank run.
 
-Transport is `torch.distributed` (gloo on CPU; NCCL for device tensors)."""
+Transport is `torch.distributed` on host arrays (the gloo backend); a
+device version moves the same packed buffers as CUDA tensors over NCCL."""
 from __future__ import annotations
 
 import numpy as np
