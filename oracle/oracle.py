@@ -153,6 +153,8 @@ def lib():
             L.orc_hilbert_rank.restype = C.c_int
             L.orc_species_reservoirs.argtypes = [P(Params), i64, P(i64), P(i64), P(u8), i32, i32, i32, i32]
             L.orc_species_reservoirs.restype = None
+            L.orc_cc_forces.argtypes = [P(Params), C.c_int, P(d), C.c_int, P(i32), P(i32), P(d)]
+            L.orc_cc_forces.restype = None
             _lib = L
     return _lib
 
@@ -229,6 +231,18 @@ def forces(cfg, x, flags, colloids):
                      _ptr(np.ascontiguousarray(colloids["eps_B"], np.float64), C.c_double),
                      _ptr(f, C.c_double), _ptr(F, C.c_double))
     return f, F
+
+
+def cc_forces(cfg, X, bonds=()):
+    """Colloid-colloid LJ forces (fixed-point summed, bonded pairs excluded)."""
+    p = make_params(cfg)
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 3)
+    ba = np.ascontiguousarray([b[0] for b in bonds], dtype=np.int32)
+    bb = np.ascontiguousarray([b[1] for b in bonds], dtype=np.int32)
+    F = np.zeros_like(X)
+    lib().orc_cc_forces(C.byref(p), len(X), _ptr(X, C.c_double), len(ba), _ptr(ba, C.c_int32),
+                        _ptr(bb, C.c_int32), _ptr(F, C.c_double))
+    return F
 
 
 # --------------------------------------------------------------------------

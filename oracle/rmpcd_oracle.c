@@ -1436,3 +1436,17 @@ void orc_species_reservoirs(const orc_params *p, int64_t n_cells, const int64_t 
             flags[k] = (uint8_t)(to ? F_B : 0);
     }
 }
+
+/* Colloid-colloid LJ forces F[nc*3] of a configuration (bonded pairs
+ * excluded), as the interval sums them (for the tests). */
+void orc_cc_forces(const orc_params *p, int nc, const double *X, int n_bonds, const int32_t *ba,
+                   const int32_t *bb, double *F)
+{
+    double (*Xw)[3] = malloc(sizeof(double[3]) * (size_t)(nc > 0 ? nc : 1));
+    int64_t *Fq = (int64_t *)calloc((size_t)(3 * nc > 0 ? 3 * nc : 1), sizeof(int64_t));
+    for (int j = 0; j < nc; ++j) wrapped(p, X + 3 * j, Xw[j]);
+    colloids_t cs = {nc, (double *)X, NULL, NULL, NULL, NULL, NULL, NULL, NULL, n_bonds, ba, bb, NULL};
+    colloid_colloid(p, &cs, (const double (*)[3])Xw, Fq);
+    for (int j = 0; j < 3 * nc; ++j) F[j] = (double)Fq[j] * FX_INV;
+    free(Xw); free(Fq);
+}

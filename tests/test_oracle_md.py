@@ -175,3 +175,39 @@ def test_conversion_count_matches_tag_bookkeeping(orc):
     d = s.x[tagged] - np.mod(s.X[0], L)
     d -= L * np.round(d / L)
     assert np.all(np.linalg.norm(d, axis=1) < 2 ** (1 / 6) * 2.0)
+
+
+def test_colloid_lj_force_is_minus_gradient_of_the_shifted_energy(orc):
+    """Four spheres with colloid-colloid LJ (eps 1, sigma 3, cut 7.5): the
+    force on each sphere is minus the central-difference gradient of the
+    potential energy (energy shifted to zero at the cut); pairs beyond the cut
+    and bonded pairs add nothing."""
+    cfg = synth.base_config(L=(30, 30, 30), cc_lj=(1.0, 3.0, 7.5), seed=3)
+    X = np.array([[10.0, 10.0, 10.0], [13.6, 10.4, 9.8], [11.2, 14.1, 10.9], [24.0, 24.0, 24.0]])
+    col = [dict(x=tuple(p), v=(0.0, 0.0, 0.0), mass=100.0, sigma=1.0, eps_A=1.0, eps_B=1.0, catalytic=0)
+           for p in X]
+    F = orc.cc_forces(cfg, X)
+    assert np.all(F[3] == 0.0)                       # sphere 3 is beyond every cut
+    assert np.allclose(F.sum(0), 0.0, atol=1e-9)
+
+    def energy(Xs, bonds=()):
+        c = [dict(cc, x=tuple(p)) for cc, p in zip(col, Xs)]
+        o = orc.OracleSystem(cfg, np.zeros((0, 3)), np.zeros((0, 3)), colloids=synth.colloid_arrays(c),
+                             bonds=list(bonds))
+        return o.potential_energy()
+
+    h = 1e-5
+    for j in range(3):
+        for k in range(3):
+            Xp, Xm = X.copy(), X.copy()
+            Xp[j, k] += h
+            Xm[j, k] -= h
+            g = (energy(Xp) - energy(Xm)) / (2 * h)
+            assert abs(F[j, k] + g) < 1e-6 * max(1.0, abs(g)), (j, k, F[j, k], -g)
+    # shifted: a pair just inside the cut has (almost) zero energy
+    X2 = np.array([[10.0, 10.0, 10.0], [17.499, 10.0, 10.0]])
+    assert abs(energy(X2)) < 1e-3 and np.abs(orc.cc_forces(cfg, X2)).max() < 0.02
+    # a bonded pair is excluded
+    Fb = orc.cc_forces(cfg, X, bonds=[(0, 1, 3.7)])
+    F01 = orc.cc_forces(cfg, X[:2])
+    assert np.allclose(Fb[:2], F[:2] - F01, atol=1e-9)
