@@ -180,3 +180,30 @@ def test_mpc_at_slab_thermalises_and_conserves_cell_momentum(orc):
     T = s.temperature()
     se = 2.0 * math.sqrt(2.0 / (3.0 * (s.count[s.count >= 2] - 1).sum()))
     assert abs(T - 2.0) < 5 * se
+
+
+def test_mpc_at_slabs_drive_a_linear_temperature_profile(orc):
+    """Two MPC-AT slabs (kT 1.2 on [0, 2), 0.8 on [16, 18)) in a periodic
+    32-cell column: in steady state the slab temperatures hold inside the
+    slabs, the profile between them is linear (Fourier's law with a constant
+    conductivity) with a gradient close to (0.8 - 1.2) / 14 per cell (slightly
+    less: the slabs' edges take part of the drop), and the two halves of the
+    periodic column mirror each other about the slabs' mean centres."""
+    cfg = synth.base_config(L=(32, 8, 8), alpha=np.radians(130.0), tau=0.5, kT=1.0, seed=41,
+                            slabs=[(0.0, 2.0, 1.2), (16.0, 18.0, 0.8)])
+    x, v, fl = synth.solvent(cfg, seed=42)
+    o = orc.OracleSystem(cfg, x, v, fl)
+    o.step(200)
+    T = np.zeros(32)
+    for _ in range(400):
+        o.step(1)
+        T += orc.slab_fields(orc.slab_profile(32, o.x[:, 0], o.v, o.flags, 32))["T"]
+    T /= 400
+    assert abs(T[1] - 1.2) < 0.02 and abs(T[17] - 0.8) < 0.02
+    b = np.arange(4, 15)
+    slope, icpt = np.polyfit(b + 0.5, T[b], 1)
+    assert -0.4 / 14 * 1.15 < slope < -0.4 / 14 * 0.75, slope
+    assert np.abs(T[b] - (slope * (b + 0.5) + icpt)).max() < 0.015
+    # the slabs are columns of the shifted grid, [x0 + s, x1 + s) with s
+    # uniform in [0, 1): centred at 1.5 and 17.5, so bin b mirrors bin 34 - b
+    assert np.abs(T[b] - T[34 - b]).max() < 0.03
