@@ -123,7 +123,7 @@ def ncu_traffic(kernel, workload_name, precision):
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("kernel_hash") != kernel_hash(kernel):
+    if kernel not in KERNEL_SOURCES or d.get("kernel_hash") != kernel_hash(kernel):
         return None
     e = d.get("kernels", {}).get(f"{kernel}/{workload_name}/{precision}")
     return None if e is None else e.get("bytes_per_launch")
