@@ -76,3 +76,14 @@ def test_parallel_colour_sweep_equals_sequential_colour_order(orc):
     # and the colour order reaches the constraint surface like any order
     r = xs[[a for a, _ in links]] - xs[[b for _, b in links]]
     assert np.all(np.abs((r * r).sum(1) - d * d) <= 2 * tol * d * d * 1.0001)
+
+
+def test_coloring_rejects_bad_links():
+    import pytest
+    with pytest.raises(ValueError):
+        network.color_links([(0, 0)], 3)
+    with pytest.raises(ValueError):
+        network.color_links([(0, 3)], 3)
+    # a triangle needs three colours, a path two
+    assert sorted(network.color_links([(0, 1), (1, 2), (0, 2)], 3).tolist()) == [0, 1, 2]
+    assert network.color_links([(0, 1), (1, 2), (2, 3)], 4).tolist() == [0, 1, 0]
