@@ -212,8 +212,12 @@ void orc_gather(int64_t n, const int64_t *perm, const void *in, void *out, int64
 /*   MPC-AT in thermostat slabs: v_i <- v_cm + xi_i - <xi>, xi ~ N(0, kT_s)  */
 /*   walls: wall cells with 0 < N < rho_wall get rho_wall - N virtual        */
 /*   particles at rest on average, whose summed momentum is N(0, n_v kT).    */
-/* Cells with fewer than two particles are left unchanged.  v is in sorted  */
-/* order; count/start come from orc_counting_sort.                          */
+/*   A wall cell holding a single particle collides too: with its virtual    */
+/*   partners v_cm differs from v, so the rotation pulls it toward rest      */
+/*   (the no-slip condition of Lamura et al. 2001).                          */
+/* Other cells with fewer than two particles are left unchanged (a lone     */
+/* particle is its own v_cm).  v is in sorted order; count/start come from   */
+/* orc_counting_sort.                                                        */
 /* ------------------------------------------------------------------------ */
 static int slab_of(const orc_params *p, int64_t cx)
 {
@@ -229,16 +233,17 @@ void orc_collide(const orc_params *p, uint32_t step, int64_t n_cells,
     int64_t nz = p->L[2] + (p->walls ? 1 : 0);
     for (int64_t c = 0; c < n_cells; ++c) {
         int64_t N = count[c];
-        if (N < 2) continue;
-        double *vc = v + 3 * start[c];
         int64_t cx = c % p->L[0];
         int64_t cz = c / ((int64_t)p->L[0] * p->L[1]);
+        int wall_cell = p->walls && (cz == 0 || cz == nz - 1);
+        int virt = wall_cell && N > 0 && N < p->rho_wall;
+        if (N < 2 && !virt) continue;
+        double *vc = v + 3 * start[c];
         double sum[3] = {0.0, 0.0, 0.0};
         for (int64_t i = 0; i < N; ++i)
             for (int d = 0; d < 3; ++d) sum[d] = sum[d] + vc[3 * i + d];
         double vcm[3];
-        int wall_cell = p->walls && (cz == 0 || cz == nz - 1);
-        if (wall_cell && N < p->rho_wall) {
+        if (virt) {
             /* virtual particles fill the wall cell up to rho_wall (Lamura et al. 2001) */
             int64_t nv = p->rho_wall - N;
             uint32_t w[4];

@@ -163,6 +163,50 @@ struct TileShared {
     double red[CP_WARPS][8];
 };
 
+// Anderson thermostat (MPC-AT, §1.4) of one cell of n particles (v in
+// sorted order): v_i <- v_cm + xi_i - <xi>, xi ~ N(0, kT_slab), with
+// rho_wall - n virtual partners in v_cm when virt.  The per-cell momentum
+// sums are FP64 on both paths; the Gaussian draws are in the path's
+// precision R.
+template <typename R, class Rec>
+__device__ __forceinline__ void mpcat_cell(const ReplicaDev &rp, uint32_t step, uint32_t lc, int slab, int n,
+                                           bool virt, Rec *v)
+{
+    double sum[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k) sum[k] = sum[k] + (double)v[i].v[k];
+    double vcm[3];
+    if (virt) {
+        const int nv = rp.rho_wall - n;
+        U4 w = philox(lc, step, P_VIRT, 0u, rp.seed);
+        R g0, g1, g2, g3;
+        box_muller(w.x, w.y, g0, g1);
+        box_muller(w.z, w.w, g2, g3);
+        const double sd = sqrt((double)nv * rp.kT);
+        const double gg[3] = {(double)g0, (double)g1, (double)g2};
+        for (int k = 0; k < 3; ++k) vcm[k] = (sum[k] + sd * gg[k]) / (double)(n + nv);
+    } else {
+        for (int k = 0; k < 3; ++k) vcm[k] = sum[k] / (double)n;
+    }
+    const R sd = slab_sd(rp, slab, R(0));
+    double xs[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < n; ++i) {
+        U4 w = philox(lc, step, P_THERMO, (uint32_t)i, rp.seed);
+        R g0, g1, g2, g3;
+        box_muller(w.x, w.y, g0, g1);
+        box_muller(w.z, w.w, g2, g3);
+        const R gg[3] = {g0, g1, g2};
+        for (int k = 0; k < 3; ++k) {
+            const R xi = sd * gg[k];
+            v[i].v[k] = xi;
+            xs[k] = xs[k] + (double)xi;
+        }
+    }
+    for (int k = 0; k < 3; ++k) xs[k] = xs[k] / (double)n;
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k) v[i].v[k] = (R)(vcm[k] + ((double)v[i].v[k] - xs[k]));
+}
+
 // Stage D, one thread per cell, particles summed in sorted order (the order
 // of the FP64 definition).
 template <bool MIXED, bool MANY>
@@ -181,58 +225,44 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
         T.mode[c] = 0;
         T.react[c] = -1;
         T.mnear[c] = MIXED ? 0 : 1;
+        const int cx = lc % rp.L[0];
+        const int cz = lc / (rp.L[0] * rp.L[1]);
+        // a wall cell short of rho_wall collides with virtual partners, a
+        // single real particle included (its v_cm then differs from v)
+        const bool virt = rp.walls && (cz == 0 || cz == rp.nz - 1) && n > 0 && n < rp.rho_wall;
+        const bool coll = (opts & CP_COLLIDE) && (n >= 2 || virt);
         int slab = -1;
-        const bool coll = (opts & CP_COLLIDE) && n >= 2;
+        if (coll)
+            for (int k = 0; k < rp.n_slabs; ++k)
+                if (cx >= rp.slab_lo[k] && cx < rp.slab_hi[k]) { slab = k; break; }
         const bool nearq = want_near && n > 0;
-        // the cell's velocity sum, in sorted order: for the collision and for
-        // the near bound (stage D leaves the velocities unchanged outside
+        // the cell's velocity sum, in sorted order: for the SRD collision and
+        // for the near bound (stage D leaves the velocities unchanged outside
         // MPC-AT slabs, where the bound is not taken)
         R sum[3] = {R(0), R(0), R(0)};
-        if (coll || nearq)
+        if (slab < 0 && (coll || nearq))
             for (int i = 0; i < n; ++i)
                 for (int k = 0; k < 3; ++k) sum[k] = sum[k] + srec[lo + i].v[k];
         int nbB = -1;   // B count, when the near bound's loop has taken it
         if (coll) {
-            const int cx = lc % rp.L[0];
-            const int cz = lc / (rp.L[0] * rp.L[1]);
-            R vcm[3];
-            const bool wall_cell = rp.walls && (cz == 0 || cz == rp.nz - 1);
-            if (wall_cell && n < rp.rho_wall) {
-                // virtual particles fill the wall cell up to rho_wall (§1.4)
-                const int nv = rp.rho_wall - n;
-                U4 w = philox((uint32_t)lc, a.step, P_VIRT, 0u, rp.seed);
-                R g0, g1, g2, g3;
-                box_muller(w.x, w.y, g0, g1);
-                box_muller(w.z, w.w, g2, g3);
-                const R sd = sqrt((R)nv * (R)rp.kT);
-                const R gg[3] = {g0, g1, g2};
-                for (int k = 0; k < 3; ++k) vcm[k] = (sum[k] + sd * gg[k]) / (R)(n + nv);
-            } else {
-                for (int k = 0; k < 3; ++k) vcm[k] = sum[k] / (R)n;
-            }
-            for (int k = 0; k < rp.n_slabs; ++k)
-                if (cx >= rp.slab_lo[k] && cx < rp.slab_hi[k]) { slab = k; break; }
             if (slab >= 0) {
-                // Anderson thermostat (MPC-AT): fresh relative velocities
-                const R sd = slab_sd(rp, slab, R(0));
-                R xs[3] = {R(0), R(0), R(0)};
-                for (int i = 0; i < n; ++i) {
-                    U4 w = philox((uint32_t)lc, a.step, P_THERMO, (uint32_t)i, rp.seed);
+                mpcat_cell<R>(rp, a.step, (uint32_t)lc, slab, n, virt, srec + lo);
+                T.mode[c] = 2;
+            } else {
+                R vcm[3];
+                if (virt) {
+                    // virtual particles fill the wall cell up to rho_wall (§1.4)
+                    const int nv = rp.rho_wall - n;
+                    U4 w = philox((uint32_t)lc, a.step, P_VIRT, 0u, rp.seed);
                     R g0, g1, g2, g3;
                     box_muller(w.x, w.y, g0, g1);
                     box_muller(w.z, w.w, g2, g3);
+                    const R sd = sqrt((R)nv * (R)rp.kT);
                     const R gg[3] = {g0, g1, g2};
-                    for (int k = 0; k < 3; ++k) {
-                        const R xi = sd * gg[k];
-                        srec[lo + i].v[k] = xi;
-                        xs[k] = xs[k] + xi;
-                    }
+                    for (int k = 0; k < 3; ++k) vcm[k] = (sum[k] + sd * gg[k]) / (R)(n + nv);
+                } else {
+                    for (int k = 0; k < 3; ++k) vcm[k] = sum[k] / (R)n;
                 }
-                for (int k = 0; k < 3; ++k) xs[k] = xs[k] / (R)n;
-                for (int i = 0; i < n; ++i)
-                    for (int k = 0; k < 3; ++k) srec[lo + i].v[k] = vcm[k] + (srec[lo + i].v[k] - xs[k]);
-                T.mode[c] = 2;
-            } else {
                 R ax[3];
                 rotation_axis<R>(rp.seed, a.step, (uint32_t)lc, ax);
                 for (int k = 0; k < 3; ++k) { T.vcm[c][k] = vcm[k]; T.ax[c][k] = ax[k]; }
@@ -248,8 +278,12 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
             int mn = 1;
             if (MANY) T.vbc[c] = -1.0f;
             if (slab < 0) {
+                // the centre the rotation turns about: with virtual wall
+                // partners the collision's v_cm, else the cell's own mean
                 const R inv = R(1) / (R)n;
-                const R vc[3] = {sum[0] * inv, sum[1] * inv, sum[2] * inv};
+                R vc[3] = {sum[0] * inv, sum[1] * inv, sum[2] * inv};
+                if (coll && virt)
+                    for (int k = 0; k < 3; ++k) vc[k] = T.vcm[c][k];
                 R u2 = R(0);
                 int nb_ = 0;
                 for (int i = 0; i < n; ++i) {
@@ -584,31 +618,32 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
         for (int c = cb + gt; c < ce; c += G) {
             const int n = T.cnt[c];
             const int lo = T.ls[c] - pofs;
-            // within a cell in the path's precision, across cells in FP64
-            R sum[3] = {R(0), R(0), R(0)};
-            R ke2 = R(0);
+            // the conservation diagnostics: per-cell momentum and energy sums
+            // in FP64 on both paths (a pass with observables is not a timed one)
+            double sum[3] = {0.0, 0.0, 0.0};
+            double ke2 = 0.0;
             int nbB = 0;
             for (int i = 0; i < n; ++i) {
                 for (int k = 0; k < 3; ++k) {
-                    const R vk = srec[lo + i].v[k];
+                    const double vk = (double)srec[lo + i].v[k];
                     sum[k] = sum[k] + vk;
                     ke2 = ke2 + vk * vk;
                 }
                 nbB += (srec[lo + i].fid & F_B) ? 1 : 0;
             }
             if (n >= 2) {
-                R vcm[3] = {sum[0] / (R)n, sum[1] / (R)n, sum[2] / (R)n};
-                R ke = R(0);
+                const double vcm[3] = {sum[0] / (double)n, sum[1] / (double)n, sum[2] / (double)n};
+                double ke = 0.0;
                 for (int i = 0; i < n; ++i)
                     for (int k = 0; k < 3; ++k) {
-                        const R u = srec[lo + i].v[k] - vcm[k];
+                        const double u = (double)srec[lo + i].v[k] - vcm[k];
                         ke = ke + u * u;
                     }
-                acc[0] += (double)(ke / (R)(n - 1));
+                acc[0] += ke / (double)(n - 1);
                 acc[1] += 1.0;
             }
-            acc[2] += (double)sum[0]; acc[3] += (double)sum[1]; acc[4] += (double)sum[2];
-            acc[5] += 0.5 * (double)ke2;
+            acc[2] += sum[0]; acc[3] += sum[1]; acc[4] += sum[2];
+            acc[5] += 0.5 * ke2;
             acc[6] += (double)nbB;
             acc[7] += (double)n;
         }

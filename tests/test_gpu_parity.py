@@ -99,6 +99,34 @@ def test_fp64_srd_is_bit_exact():
 
 
 @pytest.mark.parametrize("precision", PRECS)
+def test_single_particle_wall_cells_collide(precision):
+    """A dilute channel (about two particles per cell) puts many wall cells at
+    one real particle; each collides with rho_wall - 1 virtual partners (§1.4),
+    on the GPU as in the oracle (fp64 bit for bit)."""
+    cfg = synth.base_config(L=(8, 8, 6), walls=1, rho_wall=10, precision=precision, seed=21)
+    x, v, fl = synth.solvent(cfg, n=800, seed=121)
+    g = gpu(cfg, x, v, fl, precision=precision, step=5)
+    g.shift_and_sort()
+    g.collide()
+    st = g.get_state()
+    o = oracle(cfg, x, v, fl, step=5)
+    o.shift_and_sort()
+    v_sorted = o.v.copy()
+    o.collide()
+    # the case exercises the rule: lone particles in wall layers that moved
+    nz = cfg["L"][2] + 1
+    layer = o.key // (cfg["L"][0] * cfg["L"][1])
+    lone = (o.count[o.key] == 1) & ((layer == 0) | (layer == nz - 1))
+    assert lone.sum() >= 10 and np.all(np.any(o.v[lone] != v_sorted[lone], axis=1))
+    assert np.array_equal(st["id"], o.id)
+    if precision == "fp64":
+        assert np.array_equal(st["v"], o.v)
+    else:
+        bad = vel_bad(st["v"], o.v, cfg["kT"], precision)
+        assert not bad.any(), (int(bad.sum()), np.abs(st["v"] - o.v).max())
+
+
+@pytest.mark.parametrize("precision", PRECS)
 @pytest.mark.parametrize("rate", [0.05, 1e6])
 def test_bulk_reaction_flags_bit_exact(precision, rate):
     cfg, x, v, fl = _case("rho10", precision, bulk_rate=rate)

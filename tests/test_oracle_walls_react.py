@@ -109,6 +109,41 @@ def test_virtual_particles_pull_wall_cells_toward_rest(orc):
     assert abs(s.v[:, 0].mean() - 1.0) < 1e-14
 
 
+def test_single_particle_wall_cell_collides_with_virtual_partners(orc):
+    """A wall cell holding ONE real particle still gets rho_wall - 1 virtual
+    partners (§1.4, virtual particles after Lamura et al. 2001): v_cm = (V +
+    P_v) / rho_wall differs from V, so the collision is not the identity.  With
+    f = 1 / rho_wall, E[v_cm] = f V and E[R] = (1 + 2 cos a) / 3, so the
+    particle's velocity after the collision averages f V + (1 + 2 cos a) / 3
+    (1 - f) V.  A rule that skips cells with N < 2 leaves it at V."""
+    alpha = math.radians(130.0)
+    rho_wall = 10
+    cfg = synth.base_config(L=(4, 4, 4), walls=1, rho_wall=rho_wall, alpha=alpha, kT=1.0)
+    x = np.array([[1.50, 2.50, 0.001]])
+    V = np.array([[1.0, -0.5, 0.25]])
+    got = []
+    for step in range(800):
+        s = orc.OracleSystem(cfg, x, V, step=step)
+        s.shift_and_sort()
+        if s.key[0] // 16 != 0:   # the particle must sit in the bottom wall layer
+            continue
+        s.collide()
+        got.append(s.v[0].copy())
+    got = np.asarray(got)
+    assert len(got) > 700
+    f = 1.0 / rho_wall
+    want = (f + (1.0 + 2.0 * math.cos(alpha)) / 3.0 * (1.0 - f)) * V[0]
+    se = got.std(axis=0) / math.sqrt(len(got))
+    assert np.all(np.abs(got.mean(axis=0) - want) < 4 * se), (got.mean(axis=0), want, se)
+    # every sample moved: the collision is never the identity here
+    assert np.all(np.abs(got - V).sum(axis=1) > 0)
+    # the same particle away from the walls is a lone particle: unchanged
+    s = orc.OracleSystem(cfg, x + [0.0, 0.0, 2.0], V)
+    s.shift_and_sort()
+    s.collide()
+    assert np.array_equal(s.v, V)
+
+
 def _cells(orc, cfg, nb_frac, seed):
     x, v, fl = synth.solvent(cfg, seed=seed, frac_b=nb_frac)
     s = orc.OracleSystem(cfg, x, v, fl)
