@@ -7,12 +7,15 @@ flight, grid shift, sort, collision, reactions), mixed FP32 path, with the FP64
 path on the same workload for comparison, and the HBM roofline fraction of the
 dominant kernel.
 
-Default workload: the reactive sphere-dimer nanomotor in a 32^3 box at density
-10 (327,680 solvent), 50 MD sub-steps of dt = 0.01 per collision, alpha = 90 deg,
-kT = 1/3, A -> B at the catalytic sphere and bulk B -> A at k = 0.01.
+Default workload: the batched ensemble of 256 independent replicas in one
+launch per kernel (cube sides drawn from {16, 20, 24, 32, 40, 48}, density 10,
+104,070,400 solvent in all), each holding one rigid Janus particle of 100-300
+beads with a catalytic hemisphere, alpha = 130 deg, tau = 0.5, 25 MD sub-steps
+of dt = 0.02 per collision: the mixed-FP32 batched MPCD step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload dimer32|sphere16|poiseuille128] [--precision mixed|fp64]
+                    [--workload batch256|dimer32|sphere16|poiseuille128|thermal]
+                    [--precision mixed|fp64]
 
 With torchrun (N > 1) every rank runs an independent replica of the workload
 (replicas only: the method has no data exchange between independent systems).
@@ -116,9 +119,12 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def ncu_traffic(kernel, workload_name, precision):
+def ncu_traffic(kernel, workload_name, precision, n_particles):
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or None
-    when absent or taken on a different kernel build."""
+    when absent or taken on a different kernel build.  An entry captured on a
+    smaller case of the same workload (bytes_per_particle) is scaled to the
+    launch by its particle count: the traffic of the cell pass grows in
+    proportion to the particles it moves."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
@@ -126,7 +132,11 @@ def ncu_traffic(kernel, workload_name, precision):
     if kernel not in KERNEL_SOURCES or d.get("kernel_hash") != kernel_hash(kernel):
         return None
     e = d.get("kernels", {}).get(f"{kernel}/{workload_name}/{precision}")
-    return None if e is None else e.get("bytes_per_launch")
+    if e is None:
+        return None
+    if "bytes_per_particle" in e:
+        return int(round(e["bytes_per_particle"] * n_particles))
+    return e.get("bytes_per_launch")
 
 
 class ClockSampler:
@@ -200,61 +210,121 @@ def job_throughput(ms, n_local, steps, device=None):
     return n_all * steps / (ms / 1e3), ms
 
 
-def cpu_baseline(name, precision, budget_s=15.0):
-    """The oracle, as it stands, on the host cores: full collision intervals of
-    the same workload until the time budget is spent (after one warm-up)."""
-    from oracle import oracle
-    from paper_1608_04904_gb300 import synth
-    oracle.build()
-    reps, _ = workload(name, precision)
-    x, v, fl = initial_state(reps[0])
-    o = oracle_system(oracle, reps[0], (x, v, fl))
-    o.step(1)
-    t0 = time.perf_counter()
-    k = 0
-    while True:
-        o.step(1)
-        k += 1
-        el = time.perf_counter() - t0
-        if (el >= budget_s and k >= 2) or k >= 10000:
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True,
+                             timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_sample(name, precision, max_particles=2_000_000):
+    """The replicas the CPU legs time: the workload itself, or for a batch its
+    first replicas up to about max_particles solvent (at least one)."""
+    reps, desc = workload(name, precision)
+    out, n = [], 0
+    for r in reps:
+        st = initial_state(r)
+        if out and n + len(st[0]) > max_particles:
             break
-    return {"value": len(x) * k / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{k} full collision intervals of {'the first replica of ' if len(reps) > 1 else ''}the "
-                      f"workload ({len(x)} solvent) after 1 warm-up, {el:.1f} s, single-threaded FP64 C oracle",
-            "seconds": el}
+        out.append((r, st))
+        n += len(st[0])
+    return out, n, len(reps), desc
+
+
+def time_oracle(oracle, sample, threads, budget_s, warmup=1, max_steps=10000):
+    """Full collision intervals of every sampled replica on `threads` OpenMP
+    threads until the budget is spent; returns (particle-steps/s, intervals, s)."""
+    used = oracle.set_threads(threads)
+    try:
+        systems = [oracle_system(oracle, r, st) for r, st in sample]
+        n = sum(len(st[0]) for _, st in sample)
+        for _ in range(warmup):
+            for o in systems:
+                o.step(1)
+        t0 = time.perf_counter()
+        k = 0
+        while True:
+            for o in systems:
+                o.step(1)
+            k += 1
+            el = time.perf_counter() - t0
+            if (el >= budget_s and k >= 2) or k >= max_steps:
+                break
+    finally:
+        oracle.set_threads(1)
+    return n * k / el, k, el, used
+
+
+def cpu_baseline(name, precision, budget_s=10.0):
+    """The oracle, as it stands, on the host cores, on one thread and on every
+    core (its OpenMP loops; results do not depend on the thread count): full
+    collision intervals of a bounded sample of the same workload."""
+    from oracle import oracle
+    oracle.build()
+    sample, n, n_rep, _ = oracle_sample(name, precision)
+    v1, k1, e1, _ = time_oracle(oracle, sample, 1, budget_s)
+    va, ka, ea, cores = time_oracle(oracle, sample, 0, budget_s)
+    what = (f"the first {len(sample)} of {n_rep} replicas of the workload" if n_rep > 1 else "the workload")
+    return {"value": va, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{ka} full collision intervals of {what} ({n} solvent) after 1 warm-up, {ea:.1f} s, "
+                      f"FP64 C oracle on {cores} OpenMP threads",
+            "seconds": ea, "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+            "single_thread": {"value": v1, "cores": 1, "intervals": k1, "seconds": e1}}
 
 
 def run_reference(args, ws, rank):
+    """The reference arm: the FP64 oracle on every host core (its OpenMP loops),
+    each step one full collision interval of a bounded sample of the workload
+    (a batch: its first replicas up to about 1 M solvent)."""
     if rank != 0:
         return
-    from paper_1608_04904_gb300 import synth
-    reps, desc = workload(args.workload, args.precision)
     from oracle import oracle
     oracle.build()
-    x, v, fl = initial_state(reps[0])
-    o = oracle_system(oracle, reps[0], (x, v, fl))
-    for _ in range(args.warmup):
-        o.step(1)
-    budget = 150.0
-    times = []
-    t_all = time.perf_counter()
-    for k in range(args.steps):
-        t0 = time.perf_counter()
-        o.step(1)
-        times.append(time.perf_counter() - t0)
-        if time.perf_counter() - t_all > budget:
-            break
+    sample, n, n_rep, desc = oracle_sample(args.workload, args.precision, max_particles=1_000_000)
+    cores = oracle.set_threads(0)
+    try:
+        systems = [oracle_system(oracle, r, st) for r, st in sample]
+        for _ in range(args.warmup):
+            for o in systems:
+                o.step(1)
+        budget = 150.0
+        times = []
+        t_all = time.perf_counter()
+        for k in range(args.steps):
+            t0 = time.perf_counter()
+            for o in systems:
+                o.step(1)
+            times.append(time.perf_counter() - t0)
+            if time.perf_counter() - t_all > budget:
+                break
+    finally:
+        oracle.set_threads(1)
     done = len(times)
     tot = sum(times)
-    value = len(x) * done / tot
+    value = n * done / tot
+    what = f"the first {len(sample)} of {n_rep} replicas ({n} solvent)" if n_rep > 1 else f"the workload ({n} solvent)"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": done,
         "warmup": args.warmup, "ms_per_step": 1e3 * tot / done, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {desc}", "n_solvent": len(x), "precision": "fp64 oracle"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{done} of {args.steps} requested full intervals (time budget {budget:.0f} s) "
-                                   f"after {args.warmup} warm-up"},
+        "config": {"workload": f"{args.workload}: {desc}", "n_solvent": n, "precision": "fp64 oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{done} of {args.steps} requested full intervals of {what} (time budget "
+                                   f"{budget:.0f} s) after {args.warmup} warm-up, {cores} OpenMP threads",
+                         "nproc": os.cpu_count(), "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -372,7 +442,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="dimer32",
+    ap.add_argument("--workload", default="batch256",
                     choices=["dimer32", "dimer64", "sphere16", "poiseuille128", "thermal", "batch256"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--md-cluster", type=int, default=0, help="MD CTAs per replica (0 = autotune)")
@@ -439,7 +509,7 @@ def main():
     alg = n * ALG_BYTES[args.precision]
     achieved = alg / cp_avg_s / 1e9
     roofline = {"kernel": "k_cellpass", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": ncu_traffic("k_cellpass", args.workload, args.precision),
+                "frac": achieved / peak, "traffic": ncu_traffic("k_cellpass", args.workload, args.precision, n),
                 "peak_source": f"{peak_src} hbm_gbs", "dominant_kernel": kernel_names[dominant],
                 "alg_bytes_per_particle": ALG_BYTES[args.precision]}
     if dominant == "md":

@@ -39,7 +39,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + ".tmp%d" % os.getpid()
         cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-               "-fno-fast-math", "-Wall", "-Wextra", "-Wno-unused-parameter",
+               "-fno-fast-math", "-fopenmp", "-Wall", "-Wextra", "-Wno-unused-parameter",
                "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
@@ -85,6 +85,16 @@ def make_params(cfg: dict) -> Params:
     return p
 
 
+def set_threads(n: int) -> int:
+    """OpenMP threads of the oracle's per-particle and per-cell loops (0 = every
+    core of the host); returns the count in use.  Results do not depend on it."""
+    return int(lib().orc_set_threads(int(n)))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
+
+
 def _ptr(a, t):
     return a.ctypes.data_as(C.POINTER(t))
 
@@ -96,6 +106,9 @@ def lib():
             L = C.CDLL(build())
             d, i64, u32, u8, i32 = C.c_double, C.c_int64, C.c_uint32, C.c_uint8, C.c_int32
             P = C.POINTER
+            L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_set_threads.restype = C.c_int
+            L.orc_get_threads.restype = C.c_int
             L.orc_philox4x32_10.argtypes = [P(u32), P(u32), P(u32)]
             L.orc_grid_shift.argtypes = [C.c_uint64, u32, P(d)]
             L.orc_rotation_axis.argtypes = [C.c_uint64, u32, u32, P(d)]
@@ -214,6 +227,16 @@ def counting_sort(key, ncells):
     lib().orc_counting_sort(len(key), _ptr(key, C.c_int32), ncells, _ptr(perm, C.c_int64),
                             _ptr(count, C.c_int64), _ptr(start, C.c_int64))
     return perm, count, start
+
+
+def gather(perm, a):
+    """out[j] = a[perm[j]] (rows of a contiguous array), by orc_gather."""
+    a = np.ascontiguousarray(a)
+    out = np.empty_like(a)
+    width = a.itemsize * (a.size // len(a) if len(a) else 1)
+    perm = np.ascontiguousarray(perm, dtype=np.int64)
+    lib().orc_gather(len(perm), _ptr(perm, C.c_int64), a.ctypes.data, out.ctypes.data, width)
+    return out
 
 
 def forces(cfg, x, flags, colloids):
@@ -403,12 +426,12 @@ class OracleSystem:
         L.orc_cell_keys(C.byref(self.p), self.n, _ptr(self.x, C.c_double), _ptr(s, C.c_double),
                         _ptr(key, C.c_int32))
         perm, count, start = counting_sort(key, self.ncells)
-        self.x = self.x[perm]
-        self.v = self.v[perm]
-        self.flags = self.flags[perm]
-        self.id = self.id[perm]
-        self.near = self.near[perm]
-        self.key = key[perm]
+        self.x = gather(perm, self.x)
+        self.v = gather(perm, self.v)
+        self.flags = gather(perm, self.flags)
+        self.id = gather(perm, self.id)
+        self.near = gather(perm, self.near)
+        self.key = gather(perm, key)
         self.perm, self.count, self.start = perm, count, start
         self.shift = s
 

@@ -36,6 +36,30 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Threads.  Loops whose iterations are independent (per particle or per    */
+/* cell) may run on several OpenMP threads; colloid and body force totals    */
+/* are exact 64-bit integer sums, so their reduction order does not matter.  */
+/* Results are bit-identical for every thread count.  Default: 1 thread.     */
+/* ------------------------------------------------------------------------ */
+static int g_threads = 1;
+
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    g_threads = n > 0 ? n : omp_get_num_procs();
+#else
+    (void)n;
+    g_threads = 1;
+#endif
+    return g_threads;
+}
+
+int orc_get_threads(void) { return g_threads; }
 
 /* ------------------------------------------------------------------------ */
 /* Parameters of one system (one replica).                                  */
@@ -164,6 +188,7 @@ int64_t orc_n_cells(const orc_params *p)
 void orc_cell_keys(const orc_params *p, int64_t n, const double *x, const double s[3], int32_t *key)
 {
     int64_t nz = p->L[2] + (p->walls ? 1 : 0);
+#pragma omp parallel for num_threads(g_threads) schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         int64_t c[3];
         for (int d = 0; d < 3; ++d) {
@@ -202,6 +227,7 @@ void orc_gather(int64_t n, const int64_t *perm, const void *in, void *out, int64
 {
     const char *src = (const char *)in;
     char *dst = (char *)out;
+#pragma omp parallel for num_threads(g_threads) schedule(static)
     for (int64_t j = 0; j < n; ++j)
         memcpy(dst + j * width, src + perm[j] * width, (size_t)width);
 }
@@ -231,6 +257,7 @@ void orc_collide(const orc_params *p, uint32_t step, int64_t n_cells,
 {
     double ca = cos(p->alpha), sa = sin(p->alpha), omc = 1.0 - ca;
     int64_t nz = p->L[2] + (p->walls ? 1 : 0);
+#pragma omp parallel for num_threads(g_threads) schedule(dynamic, 256)
     for (int64_t c = 0; c < n_cells; ++c) {
         int64_t N = count[c];
         int64_t cx = c % p->L[0];
@@ -308,6 +335,7 @@ void orc_bulk_react(const orc_params *p, uint32_t step, int64_t n_cells,
                     const int64_t *count, const int64_t *start, uint8_t *flags)
 {
     if (p->bulk_mode == 0) return;
+#pragma omp parallel for num_threads(g_threads) schedule(dynamic, 256)
     for (int64_t c = 0; c < n_cells; ++c) {
         int64_t N = count[c];
         uint8_t *fc = flags + start[c];
@@ -378,6 +406,7 @@ static void flight_one(const orc_params *p, double *x, double *v)
 
 void orc_flight(const orc_params *p, int64_t n, double *x, double *v, const uint8_t *near)
 {
+#pragma omp parallel for num_threads(g_threads) schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         if (near && near[i]) continue;
         flight_one(p, x + 3 * i, v + 3 * i);
@@ -605,6 +634,7 @@ int orc_interval(const orc_params *p, uint32_t step, int64_t n, double *x, doubl
     /* classification (Verlet-list radius r_c + skin, §1.4) */
     uint8_t *near = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
     int64_t n_near = 0;
+#pragma omp parallel for num_threads(g_threads) schedule(static) reduction(+ : n_near)
     for (int64_t i = 0; i < n; ++i) {
         if (all_substep) { near[i] = 1; ++n_near; continue; }
         double *vi = v + 3 * i;
@@ -631,6 +661,7 @@ int orc_interval(const orc_params *p, uint32_t step, int64_t n, double *x, doubl
 
     /* forces at the start of the interval */
     memset(Fq, 0, sizeof(int64_t) * 3 * (size_t)nc);
+#pragma omp parallel for num_threads(g_threads) schedule(static) reduction(+ : Fq[:3 * nc])
     for (int64_t k = 0; k < n_near; ++k) {
         int64_t i = list[k];
         solvent_force(p, &cs, (const double (*)[3])Xw, x + 3 * i, flags[i], f + 3 * k, Fq);
@@ -658,6 +689,7 @@ int orc_interval(const orc_params *p, uint32_t step, int64_t n, double *x, doubl
         }
         /* new forces, catalytic conversion, second half kick */
         memset(Fq, 0, sizeof(int64_t) * 3 * (size_t)nc);
+#pragma omp parallel for num_threads(g_threads) schedule(static) reduction(+ : Fq[:3 * nc])
         for (int64_t k = 0; k < n_near; ++k) {
             int64_t i = list[k];
             solvent_force(p, &cs, (const double (*)[3])Xw, x + 3 * i, flags[i], f + 3 * k, Fq);
@@ -985,6 +1017,7 @@ int orc_interval_body(const orc_params *p, uint32_t step, int64_t n, double *x, 
     /* classification against the bounding sphere */
     uint8_t *near = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
     int64_t n_near = 0;
+#pragma omp parallel for num_threads(g_threads) schedule(static) reduction(+ : n_near)
     for (int64_t i = 0; i < n; ++i) {
         if (all_substep) { near[i] = 1; ++n_near; continue; }
         double *vi = v + 3 * i;
@@ -1008,6 +1041,7 @@ int orc_interval_body(const orc_params *p, uint32_t step, int64_t n, double *x, 
 
     /* forces at the start of the interval */
     memset(Fq, 0, sizeof Fq); memset(Tq, 0, sizeof Tq);
+#pragma omp parallel for num_threads(g_threads) schedule(static) reduction(+ : Fq, Tq)
     for (int64_t k = 0; k < n_near; ++k) {
         int64_t i = list[k];
         body_solvent_force(p, &B, x + 3 * i, flags[i], f + 3 * k, Fq, Tq, NULL);
@@ -1034,6 +1068,7 @@ int orc_interval_body(const orc_params *p, uint32_t step, int64_t n, double *x, 
         }
         /* new forces, catalytic conversion, second half kicks */
         memset(Fq, 0, sizeof Fq); memset(Tq, 0, sizeof Tq);
+#pragma omp parallel for num_threads(g_threads) schedule(static) reduction(+ : Fq, Tq)
         for (int64_t k = 0; k < n_near; ++k) {
             int64_t i = list[k];
             int in = body_solvent_force(p, &B, x + 3 * i, flags[i], f + 3 * k, Fq, Tq, NULL);
@@ -1262,6 +1297,7 @@ int orc_interval_network(const orc_params *p, uint32_t step, int64_t n, double *
 
     uint8_t *near = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
     int64_t n_near = 0;
+#pragma omp parallel for num_threads(g_threads) schedule(static) reduction(+ : n_near)
     for (int64_t i = 0; i < n; ++i) {
         if (all_substep) { near[i] = 1; ++n_near; continue; }
         const double *vi = v + 3 * i;
