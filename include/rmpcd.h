@@ -325,8 +325,8 @@ const char *rmpcd_last_error(const rmpcd_system *sys);
 
 /* --- observables without device allocation --------------------------------
  * The paper has no counterpart of this entry point.  It computes what
- * rmpcd_observables computes (the §1.4 temperature estimator plus totals) from
- * caller-owned device arrays, and allocates no device memory: it reduces
+ * rmpcd_observables reports (the temperature, momentum, kinetic energy and
+ * counts) from caller-owned device arrays, and allocates no device memory: it reduces
  * through one static device array of fixed size per device.  It serves
  * callers that must not allocate where they measure: a monitor between the
  * steps of a run whose device memory is wholly reserved by another pool (an

@@ -445,11 +445,43 @@ class System:
 RMPCD_NOALLOC_MAX_CELLS = 65536
 
 
+def _check_noalloc_args(cell, v, flags, out) -> None:
+    """The C entry point sees raw pointers only: check dtypes, shapes, layout
+    and device here, so that no kernel reads or writes past a tensor."""
+    import torch
+    named = [("cell", cell, torch.int32), ("v", v, torch.float64), ("out", out, torch.float64)]
+    if flags is not None:
+        named.append(("flags", flags, torch.uint8))
+    for name, t, dt in named:
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch.Tensor")
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    n = int(cell.numel())
+    if cell.dim() != 1:
+        raise ValueError(f"cell must be 1-D, got shape {tuple(cell.shape)}")
+    if tuple(v.shape) != (n, 3):
+        raise ValueError(f"v must have shape ({n}, 3), got {tuple(v.shape)}")
+    if flags is not None and int(flags.numel()) != n:
+        raise ValueError(f"flags must have {n} entries, got {int(flags.numel())}")
+    if int(out.numel()) < 8:
+        raise ValueError(f"out must hold at least 8 doubles, got {int(out.numel())}")
+    dev = torch.cuda.current_device() if torch.cuda.is_available() else None
+    for name, t, _ in named:
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.device.index != dev:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{dev}")
+
+
 def observables_noalloc(cell, v, flags, n_cells: int, out, stream=None) -> None:
     """rmpcd_observables_noalloc on CUDA tensors: cell (int32, n), v (float64,
     n x 3), flags (uint8, n, or None) and out (float64, 8), all contiguous on
     the current device.  Queued on ``stream`` (default: torch's current
     stream); out = [T, px, py, pz, kinetic, N_c, N_B, n counted]."""
+    _check_noalloc_args(cell, v, flags, out)
     L = load()
     n = int(cell.numel())
     st = L.rmpcd_observables_noalloc(C.c_void_p(cell.data_ptr()), C.c_void_p(v.data_ptr()),

@@ -11,14 +11,13 @@ pass per interval): every particle against the FP64 oracle after one step.
 
 The comparison is the one of the reduced-size tests (keys, permutation and
 flags bit-exact on the FP64 path; the mixed path within 1e-5 with key
-mismatches only at cell planes, at most 1e-4 of the particles).  The module
-sorts last so that its long runs come after every other GPU test."""
+mismatches only at cell planes, at most 1e-4 of the particles)."""
 import numpy as np
 import pytest
 
 from oracle import oracle as orc
 from paper_1608_04904_gb300 import api, build, synth
-from parity_util import by_id, compare_step, near_boundary, pos_bad, vel_bad
+from parity_util import by_id, check_mixed_exceptions, compare_step, near_boundary, pos_bad, pos_diff, vel_bad
 
 pytestmark = pytest.mark.gpu
 
@@ -78,15 +77,17 @@ def _compare_many(cfg, st, o, precision, n_col):
         compare_step(cfg, st, o, precision)
         return
     gid, gx, gv, gf, gc = by_id(st["id"], st["id"], st["x"], st["v"], st["flags"], st["cell"])
-    oid, ox, ov, of, oc = by_id(o.id, o.id, o.x, o.v, o.flags, o.key)
+    oid, ox, ov, of, oc, onear = by_id(o.id, o.id, o.x, o.v, o.flags, o.key, o.near.astype(bool))
     assert np.array_equal(gid, oid)
     mism = gc != oc
     assert np.all(near_boundary(ox, o.shift, 1e-4)[mism]), "key mismatch away from a cell boundary"
     assert mism.sum() <= max(3, 1e-4 * len(gc))
     badcells = np.isin(oc, oc[mism]) | np.isin(oc, gc[mism])
     allow = 2 + 2 * n_col
-    assert pos_bad(gx, ox, cfg["L"], cfg.get("walls", 0), "mixed").sum() <= allow
-    assert (vel_bad(gv, ov, cfg["kT"], "mixed") & ~badcells).sum() <= allow
+    fd = gf != of
+    check_mixed_exceptions(pos_bad(gx, ox, cfg["L"], cfg.get("walls", 0), "mixed"), onear, fd, pos_diff(gx, ox, cfg["L"], cfg.get("walls", 0)), cfg["kT"],
+                           allow, "position")
+    check_mixed_exceptions(vel_bad(gv, ov, cfg["kT"], "mixed") & ~badcells, onear, fd, gv - ov, cfg["kT"], allow)
     assert (gf != of).sum() <= allow + mism.sum()
 
 

@@ -59,7 +59,7 @@ def test_noalloc_matches_observables_on_two_calls_in_a_row(lib, kind, precision)
     s.get_state(0, out=st)
     assert int(st["cell"].min()) >= 0 and int(st["cell"].max()) < n_cells
     vabs = float(st["v"].abs().sum(dim=0).max())
-    # the mixed path sums within a cell in FP32, the FP64 path in FP64
+    # both sum in FP64, in different orders (atomics here): the tolerance of each path's parity tests
     tol = 1e-5 if precision == "mixed" else 1e-12
     out = torch.empty(8, dtype=torch.float64, device=dev)
     for call in range(2):
@@ -74,3 +74,43 @@ def test_noalloc_matches_observables_on_two_calls_in_a_row(lib, kind, precision)
         assert abs(o[4] - ref["kinetic"]) <= tol * ref["kinetic"], (call, o[4], ref["kinetic"])
         assert np.all(np.abs(o[1:4] - ref["momentum"]) <= tol * vabs), (call, o[1:4], ref["momentum"])
     s.close()
+
+
+def test_binding_limit_matches_the_header():
+    """api.RMPCD_NOALLOC_MAX_CELLS is a copy of the header's macro: keep them equal."""
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                            "rmpcd.h")).read()
+    m = re.search(r"#define\s+RMPCD_NOALLOC_MAX_CELLS\s+(\d+)", hdr)
+    assert m and int(m.group(1)) == api.RMPCD_NOALLOC_MAX_CELLS
+
+
+def test_binding_rejects_bad_tensors_before_the_call():
+    """The binding checks dtype, shape, layout and device before handing raw
+    pointers to the library (no GPU needed: every case fails in Python)."""
+    torch = pytest.importorskip("torch")
+    n = 10
+    ok = dict(cell=torch.zeros(n, dtype=torch.int32), v=torch.zeros(n, 3, dtype=torch.float64),
+              flags=torch.zeros(n, dtype=torch.uint8), out=torch.zeros(8, dtype=torch.float64))
+    bad = [
+        ("v", torch.zeros(n, 3, dtype=torch.float32), "float64"),
+        ("cell", torch.zeros(n, dtype=torch.int64), "int32"),
+        ("flags", torch.zeros(n, dtype=torch.int32), "uint8"),
+        ("out", torch.zeros(8, dtype=torch.float32), "float64"),
+        ("v", torch.zeros(3, n, dtype=torch.float64).t(), "contiguous"),
+        ("v", torch.zeros(n - 1, 3, dtype=torch.float64), "shape"),
+        ("flags", torch.zeros(n - 1, dtype=torch.uint8), "entries"),
+        ("out", torch.zeros(7, dtype=torch.float64), "8 doubles"),
+        ("cell", torch.zeros(n, 1, dtype=torch.int32), "1-D"),
+    ]
+    for name, t, word in bad:
+        args = dict(ok)
+        args[name] = t
+        with pytest.raises(ValueError, match=word):
+            api.observables_noalloc(args["cell"], args["v"], args["flags"], 16, args["out"])
+    # well-formed host tensors are still refused: the library takes device pointers
+    with pytest.raises(ValueError, match="CUDA"):
+        api.observables_noalloc(ok["cell"], ok["v"], ok["flags"], 16, ok["out"])
+    with pytest.raises(ValueError, match="CUDA"):
+        api.observables_noalloc(ok["cell"], ok["v"], None, 16, ok["out"])
