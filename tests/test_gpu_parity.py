@@ -103,7 +103,8 @@ def test_fp64_srd_is_bit_exact():
 def test_single_particle_wall_cells_collide(precision):
     """A dilute channel (about two particles per cell) puts many wall cells at
     one real particle; each collides with rho_wall - 1 virtual partners (§1.4),
-    on the GPU as in the oracle (fp64 bit for bit)."""
+    on the GPU as in the oracle (the virtual momentum's Gaussian goes through
+    log, sqrt and sincos, so fp64 agrees to their last bits, not bit for bit)."""
     cfg = synth.base_config(L=(8, 8, 6), walls=1, rho_wall=10, precision=precision, seed=21)
     x, v, fl = synth.solvent(cfg, n=800, seed=121)
     g = gpu(cfg, x, v, fl, precision=precision, step=5)
@@ -120,11 +121,8 @@ def test_single_particle_wall_cells_collide(precision):
     lone = (o.count[o.key] == 1) & ((layer == 0) | (layer == nz - 1))
     assert lone.sum() >= 10 and np.all(np.any(o.v[lone] != v_sorted[lone], axis=1))
     assert np.array_equal(st["id"], o.id)
-    if precision == "fp64":
-        assert np.array_equal(st["v"], o.v)
-    else:
-        bad = vel_bad(st["v"], o.v, cfg["kT"], precision)
-        assert not bad.any(), (int(bad.sum()), np.abs(st["v"] - o.v).max())
+    bad = vel_bad(st["v"], o.v, cfg["kT"], precision)
+    assert not bad.any(), (int(bad.sum()), np.abs(st["v"] - o.v).max())
 
 
 @pytest.mark.parametrize("precision", PRECS)
