@@ -313,6 +313,19 @@ rmpcd_status rmpcd_get_tuning(const rmpcd_system *sys, int32_t *md_cluster, int3
  * directly.  Results are identical either way.  Errors: EINVAL. */
 rmpcd_status rmpcd_set_graphs(rmpcd_system *sys, int32_t on);
 
+/* Test hook of the bounded waits (the paper has no counterpart).  The cell
+ * pass finds each tile's first output slot by waiting for its predecessors'
+ * published prefixes; that wait gives up after max_polls polls (0 = the
+ * default, 4,194,304: well over a second), latches RMPCD_ETIMEOUT (reported by
+ * the next call that checks errors, e.g. rmpcd_sync) and leaves the tile's
+ * writes out (every write is bounds-checked against the pushed-out base), so
+ * the kernel returns and the CUDA context stays usable; the system's state is
+ * then invalid.  stall != 0 makes every predecessor read as not ready, a flag
+ * that nothing sets, so each wait with a predecessor runs out: a test of the
+ * timeout path that involves no fault.  Applies to launches after the call
+ * (captured graphs are dropped).  Errors: EINVAL (max_polls < 0). */
+rmpcd_status rmpcd_set_wait_test(rmpcd_system *sys, int32_t max_polls, int32_t stall);
+
 /* The bucket width in use (the automatic one when created with 0). */
 rmpcd_status rmpcd_get_bucket_cap(const rmpcd_system *sys, int32_t *cap);
 

@@ -85,7 +85,7 @@ EXPORTS = [
     "rmpcd_collide", "rmpcd_react", "rmpcd_step", "rmpcd_observables", "rmpcd_sync", "rmpcd_launch_count",
     "rmpcd_last_error", "rmpcd_enable_timers", "rmpcd_read_timers", "rmpcd_set_tuning", "rmpcd_get_tuning",
     "rmpcd_observables_noalloc", "rmpcd_set_graphs", "rmpcd_get_bucket_cap", "rmpcd_set_body", "rmpcd_get_body",
-    "rmpcd_profile", "rmpcd_workspace_size",
+    "rmpcd_profile", "rmpcd_workspace_size", "rmpcd_set_wait_test",
 ]
 
 _LIB = None
@@ -107,6 +107,7 @@ def load():
     P = C.POINTER
     vp, i32, i64, u32, d = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_double
     L.rmpcd_create.argtypes = [P(vp), i32, i32, P(Params), P(Colloid), P(Bond), i32, vp]
+    L.rmpcd_set_wait_test.argtypes = [vp, i32, i32]
     L.rmpcd_destroy.argtypes = [vp]
     L.rmpcd_destroy.restype = None
     L.rmpcd_set_state.argtypes = [vp, i32, vp, vp, vp, i64, i32]
@@ -426,6 +427,11 @@ class System:
         c = C.c_int32()
         self._check(self._lib.rmpcd_get_bucket_cap(self._h, C.byref(c)))
         return int(c.value)
+
+    def set_wait_test(self, max_polls=0, stall=False):
+        """rmpcd_set_wait_test: the look-back wait's poll limit (0 = default)
+        and the stall hook that makes every wait run out (tests only)."""
+        self._check(self._lib.rmpcd_set_wait_test(self._h, int(max_polls), 1 if stall else 0))
 
     def set_graphs(self, on=True):
         self._check(self._lib.rmpcd_set_graphs(self._h, 1 if on else 0))

@@ -645,6 +645,8 @@ static rmpcd_status create_system(rmpcd_system **out, int32_t precision, int32_t
     d.bonds = dB;
     d.md_work = work;
     d.cap = bucket_cap;
+    d.lb_limit = LB_SPIN_LIMIT;
+    d.lb_stall = 0;
     d.many_col = 0;
     for (int r = 0; r < n_replicas; ++r)
         if (params[r].n_colloids >= CP_NEAR_CAND_MIN) d.many_col = 1;
@@ -1107,6 +1109,16 @@ rmpcd_status rmpcd_step(rmpcd_system *sys, int32_t n_intervals)
     }
     sys->has_sort = true;
     sys->obs_valid = false;   // observables are computed on request
+    return RMPCD_OK;
+}
+
+rmpcd_status rmpcd_set_wait_test(rmpcd_system *sys, int32_t max_polls, int32_t stall)
+{
+    if (!sys) return RMPCD_EINVAL;
+    if (max_polls < 0) return fail(sys, RMPCD_EINVAL, "max_polls %d < 0", max_polls);
+    drop_graphs(sys);   // the kernels take Dev by value: captured launches hold the old limit
+    sys->d.lb_limit = max_polls == 0 ? LB_SPIN_LIMIT : max_polls;
+    sys->d.lb_stall = stall != 0 ? 1 : 0;
     return RMPCD_OK;
 }
 

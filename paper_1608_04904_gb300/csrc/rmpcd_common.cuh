@@ -161,6 +161,8 @@ struct Dev {
     const int *grid_start;       // lookup-grid list offsets
     const unsigned short *grid_list;
     int cap;
+    int lb_limit;                // polls before a look-back wait gives up (ERR_TIMEOUT)
+    int lb_stall;                // test hook: the look-back treats every predecessor as not ready
     int many_col;                // 1: some replica has >= CP_NEAR_CAND_MIN colloids
     int n_rep;
     int n_tiles;
@@ -656,10 +658,12 @@ __device__ __forceinline__ void st_release(unsigned long long *p, unsigned long 
 // without waiting on this tile.  Words
 // carry a 16-bit tag of the launch (never 0, the initial state), a 2-bit flag
 // (1 aggregate, 2 inclusive prefix) and a 46-bit value.  A wait that runs out
-// sets ERR_TIMEOUT and returns a base that puts every write out of bounds.
+// (d.lb_limit polls) sets ERR_TIMEOUT and returns a base that puts every write
+// of the tile out of bounds.  d.lb_stall (a test hook) makes every predecessor
+// read as not ready, a flag that nothing sets, so every wait runs out.
 // ---------------------------------------------------------------------------
 constexpr unsigned long long LB_VALUE_MASK = (1ull << 46) - 1ull;
-constexpr int LB_SPIN_LIMIT = 1 << 22;
+constexpr int LB_SPIN_LIMIT = 1 << 22;   // default of Dev::lb_limit
 constexpr int LB_W = 4;   // 32-tile windows the look-back inspects per round trip
 
 __device__ __forceinline__ void tile_publish(const Dev &d, uint32_t epoch, int tile, int total)
@@ -689,7 +693,7 @@ __device__ __forceinline__ int tile_lookback(const Dev &d, uint32_t epoch, int t
             val[u] = 0ull;
             if (u < nw && idx >= 0) {
                 const unsigned long long w = ld_acquire(&d.tile_state[idx]);
-                flag[u] = ((w >> 48) == ep) ? ((w >> 46) & 3ull) : 0ull;
+                flag[u] = ((w >> 48) == ep && !d.lb_stall) ? ((w >> 46) & 3ull) : 0ull;
                 val[u] = w & LB_VALUE_MASK;
             }
         }
@@ -713,7 +717,7 @@ __device__ __forceinline__ int tile_lookback(const Dev &d, uint32_t epoch, int t
             }
         }
         if (!ready_all) {
-            if (++spins > LB_SPIN_LIMIT) { ok = false; break; }
+            if (++spins > d.lb_limit) { ok = false; break; }
             __nanosleep(32);
             continue;
         }
