@@ -45,7 +45,7 @@ typedef enum {
     RMPCD_EINVAL = 1,     /* invalid argument or parameter combination          */
     RMPCD_ECUDA = 2,      /* a CUDA runtime call failed                          */
     RMPCD_ENOMEM = 3,     /* device allocation failed                            */
-    RMPCD_EOVERFLOW = 4,  /* a cell held more particles than bucket_cap          */
+    RMPCD_EOVERFLOW = 4,  /* a cell beyond 1536 particles, or the overflow list full */
     RMPCD_ESKIN = 5,      /* a colloid moved further than skin in one interval   */
     RMPCD_ETIMEOUT = 6,   /* a bounded device wait ran out (state is invalid)    */
     RMPCD_ESTATE = 7      /* call not valid in the current state                 */
@@ -135,8 +135,14 @@ typedef struct {
  * device.  params[n_replicas]; colloids and bonds are the replicas' lists
  * concatenated in replica order (params[r].n_colloids / n_bonds entries each;
  * may be NULL when all counts are 0).  precision: rmpcd_precision.
- * bucket_cap: most particles one cell may hold (1..768; 64 is safe at
- * density 10), or 0: picked automatically (the bucket-width autotuner:
+ * bucket_cap: width of a cell's bucket row (1..768), or 0: picked
+ * automatically.  A cell's entries past the width go to an overflow list
+ * (1024 + n_solvent/16 entries per buffer, read back by the cell pass of the
+ * tiles that need it, in canonical order like the rest): a crowded cell is
+ * not an error, though a width far below the typical count makes every tile
+ * scan the list.  A cell may hold at most 1536 particles (what the cell pass
+ * stages at once); beyond that, or with the list full, the run latches
+ * EOVERFLOW.  The automatic width (the bucket-width autotuner:
  * 1.25x the count above which a Poisson cell count at the densest replica
  * occurs with probability < 1e-4 per collision, in multiples of 8, then
  * grown to 1.5x the largest count whenever a binning or a run comes within

@@ -382,6 +382,7 @@ static rmpcd_status set_bucket_cap(rmpcd_system *sys, int cap)
     sys->d.cap = cap;
     CK(cudaMemsetAsync(sys->d.count[0], 0, sizeof(int) * ncells, sys->stream));
     CK(cudaMemsetAsync(sys->d.count[1], 0, sizeof(int) * ncells, sys->stream));
+    CK(cudaMemsetAsync(sys->d.ovf_n, 0, sizeof(unsigned int) * 2, sys->stream));
     CK(cudaMemsetAsync(sys->d.near_count, 0, sizeof(int) * sys->n_rep, sys->stream));
     sys->primed = false;
     return RMPCD_OK;
@@ -469,7 +470,7 @@ static rmpcd_status create_system(rmpcd_system **out, int32_t precision, int32_t
         rp.cell_off = tile_off * CPT;
         rp.col_off = col_off;
         rp.bond_off = bond_off;
-        rp.thr_off = r * (CP_MAX_CAP + 1);   // sized for any bucket width
+        rp.thr_off = r * (CP_MAX_CELL + 1);   // sized for any cell count
         for (int t = 0; t < rp.n_tiles; ++t) tile_rep[tile_off + t] = r;
         part_off += rp.n_part;
         tile_off += rp.n_tiles;
@@ -484,10 +485,10 @@ static rmpcd_status create_system(rmpcd_system **out, int32_t precision, int32_t
             sys->fast_ok = false;
     // bulk reaction thresholds: accept iff draw < (1 - exp(-k N_B tau)) 2^32;
     // for an integer draw that is draw < ceil((1 - exp(-k N_B tau)) 2^32)
-    std::vector<unsigned long long> thr((size_t)n_replicas * (CP_MAX_CAP + 1));
+    std::vector<unsigned long long> thr((size_t)n_replicas * (CP_MAX_CELL + 1));
     for (int r = 0; r < n_replicas; ++r)
-        for (int nb = 0; nb <= CP_MAX_CAP; ++nb)
-            thr[(size_t)r * (CP_MAX_CAP + 1) + nb] = (unsigned long long)ceil(
+        for (int nb = 0; nb <= CP_MAX_CELL; ++nb)
+            thr[(size_t)r * (CP_MAX_CELL + 1) + nb] = (unsigned long long)ceil(
                 (1.0 - exp(-params[r].bulk_rate * (double)nb * params[r].tau)) * 4294967296.0);
     // colloid constants
     std::vector<double> cM(n_col), cS(n_col), cEA(n_col), cEB(n_col), cR2(n_col), cR(n_col), cX(3 * n_col), cV(3 * n_col);
@@ -537,6 +538,12 @@ static rmpcd_status create_system(rmpcd_system **out, int32_t precision, int32_t
     AL(&d.count[1], ncells);
     AL(&d.bucket[0], ncells * bucket_cap);
     AL(&d.bucket[1], ncells * bucket_cap);
+    // overflow lists: entries of cells beyond bucket_cap (rare at the
+    // automatic width; a fixed narrow width leans on them)
+    const long long ovf_cap = 1024 + n_total / 16;
+    AL(&d.ovf[0], ovf_cap);
+    AL(&d.ovf[1], ovf_cap);
+    AL(&d.ovf_n, 2);
     AL(&d.near_list, n_total);
     AL(&d.near_count, n_replicas);
     AL(&d.tile_state, n_tiles);
@@ -612,6 +619,7 @@ static rmpcd_status create_system(rmpcd_system **out, int32_t precision, int32_t
     zero(r1, recsz * n_total);
     zero(d.count[0], sizeof(int) * ncells);
     zero(d.count[1], sizeof(int) * ncells);
+    zero(d.ovf_n, sizeof(unsigned int) * 2);
     zero(d.near_count, sizeof(int) * n_replicas);
     zero(d.tile_state, sizeof(unsigned long long) * n_tiles);
     zero(d.ticket, sizeof(unsigned int) * 4);
@@ -645,6 +653,7 @@ static rmpcd_status create_system(rmpcd_system **out, int32_t precision, int32_t
     d.bonds = dB;
     d.md_work = work;
     d.cap = bucket_cap;
+    d.ovf_cap = (int)ovf_cap;
     d.lb_limit = LB_SPIN_LIMIT;
     d.lb_stall = 0;
     d.many_col = 0;
@@ -685,6 +694,7 @@ static rmpcd_status unprime(rmpcd_system *sys)
     const size_t ncells = (size_t)sys->n_tiles * CPT;
     CK(cudaMemsetAsync(sys->d.count[0], 0, sizeof(int) * ncells, sys->stream));
     CK(cudaMemsetAsync(sys->d.count[1], 0, sizeof(int) * ncells, sys->stream));
+    CK(cudaMemsetAsync(sys->d.ovf_n, 0, sizeof(unsigned int) * 2, sys->stream));
     CK(cudaMemsetAsync(sys->d.near_count, 0, sizeof(int) * sys->n_rep, sys->stream));
     sys->primed = false;
     return RMPCD_OK;
@@ -726,8 +736,10 @@ static rmpcd_status check_errors(rmpcd_system *sys)
     if (e[ERR_TIMEOUT]) return fail(sys, RMPCD_ETIMEOUT, "a cell-pass look-back wait timed out; the state is invalid");
     if (e[ERR_BOUNDS]) return fail(sys, RMPCD_ESTATE, "inconsistent bins (slot out of range); the state is invalid");
     if (e[ERR_OVERFLOW])
-        return fail(sys, RMPCD_EOVERFLOW, "a cell held %u particles, above bucket_cap %d; raise bucket_cap", e[ERR_OVERFLOW],
-                    sys->cap);
+        return fail(sys, RMPCD_EOVERFLOW,
+                    "a cell held %u particles: beyond the %d a cell may hold, or the overflow list past bucket_cap %d "
+                    "(%d entries) ran full; the state is invalid", e[ERR_OVERFLOW], CP_MAX_CELL, sys->cap,
+                    sys->d.ovf_cap);
     if (e[ERR_SKIN]) return fail(sys, RMPCD_ESKIN, "a colloid moved further than skin in one interval (%u times)", e[ERR_SKIN]);
     return fail(sys, RMPCD_ESTATE, "device error");
 }

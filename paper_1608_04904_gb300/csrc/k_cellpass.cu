@@ -44,7 +44,9 @@ template <> struct Traits<false> {
     // Poisson tail included) in one batch, with two CTAs per SM
     static constexpr int TP = 1408;
     static_assert(TP <= K * CP_THREADS, "each thread stages at most K particles");
+    static_assert(TP <= CP_MAX_CELL, "reaction thresholds cover every cell count");
 };
+static_assert(Traits<true>::TP <= CP_MAX_CELL, "reaction thresholds cover every cell count");
 
 // --- per-record helpers ----------------------------------------------------
 __device__ __forceinline__ void rec_flight(const HotM &rp, RecM &r)
@@ -410,7 +412,7 @@ __device__ void near_candidates(TileShared<MIXED> &T, int gt, int cb, int ce)
 template <bool MIXED, bool MANY>
 __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXED> &T, int gt, int cb, int ce,
                             typename Traits<MIXED>::Rec *srec, int *ent, unsigned char *cellof, double acc[8],
-                            bool &have_base, int &npref, bool &pref)
+                            bool &have_base, int &npref, bool &pref, bool ovf)
 {
     using Rec = typename Traits<MIXED>::Rec;
     using R = typename Traits<MIXED>::R;
@@ -454,12 +456,30 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
             const int j = gt + u * G;
             if (j < nb) {
                 const int c = cb + cellof[j];
-                e[u] = d.bucket[a.cur][(long long)(gc0 + c) * d.cap + (j + pofs - T.ls[c])];
+                const int r = j + pofs - T.ls[c];
+                e[u] = r < d.cap ? d.bucket[a.cur][(long long)(gc0 + c) * d.cap + r] : -1;
             }
         }
 #pragma unroll
         for (int u = 0; u < K; ++u)
             if (gt + u * G < nb) ent[gt + u * G] = e[u];
+    }
+    if (ovf) {
+        // a cell of the tile holds more than bucket_cap: its further entries
+        // come from the overflow list, in any order (stage B ranks every
+        // entry of a cell by its slot).  T.react serves as the per-cell
+        // cursor; stage D rewrites it.
+        for (int c = cb + gt; c < ce; c += G) T.react[c] = d.cap;
+        __syncthreads();
+        const int no = min((int)*(volatile const unsigned int *)&d.ovf_n[a.cur], d.ovf_cap);
+        for (int k = gt; k < no; k += G) {
+            const int2 q = d.ovf[a.cur][k];
+            const int c = q.x - gc0;
+            if (c >= cb && c < ce) {
+                const int r = atomicAdd(&T.react[c], 1);
+                if (r < T.cnt[c]) ent[T.ls[c] - pofs + r] = q.y;
+            }
+        }
     }
     __syncthreads();
     // B: the place of every staged particle in its cell (stable order =
@@ -607,9 +627,7 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
         for (int u = 0; u < K; ++u) {
             if (pos[u] < 0) continue;
             const int p = gt + u * G;
-            const int key = ent[p];
-            if (pos[u] < d.cap) d.bucket[a.nxt][(long long)key * d.cap + pos[u]] = T.base + pofs + p;
-            else atomicMax(&d.err[ERR_OVERFLOW], (unsigned int)(pos[u] + 1));
+            bin_store(d, a.nxt, ent[p], pos[u], T.base + pofs + p);
         }
     }
     __syncthreads();
@@ -652,7 +670,7 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
 }
 
 // A run of cells from cb on whose particles fit `cap` staging slots (at
-// least one cell; a single cell never exceeds bucket_cap <= cap).
+// least one cell; a single cell holds at most cap particles).
 __device__ __forceinline__ int batch_end(const int *ls, int cb, int cend, int cap)
 {
     if (ls[cend] - ls[cb] <= cap) return cend;   // the usual case: the rest fits
@@ -730,15 +748,18 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
         const int gc0 = tile * CPT;
         // counts of the tile's cells (consumed: reset for reuse two passes later)
         int x = 0;
+        bool big = false;   // a cell of the tile holds more than bucket_cap
         if (tid < CPT) {
             int n = npref;
             d.count[a.cur][gc0 + tid] = 0;
             const int mraw = __reduce_max_sync(0xffffffffu, n);
             if (lane == 0 && mraw > 0) atomicMax(d.maxcnt, (unsigned int)mraw);   // for the bucket-width tuner
-            if (n > d.cap) {
+            if (n > TP) {
+                // more than a cell can stage: the step is invalid
                 atomicMax(&d.err[ERR_OVERFLOW], (unsigned int)n);
-                n = d.cap;
+                n = TP;
             }
+            big = n > d.cap;
             T.cnt[tid] = n;
             x = n;
 #pragma unroll
@@ -748,7 +769,7 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
             }
             if (lane == 31) T.wt[wid] = x;
         }
-        __syncthreads();
+        const bool tile_ovf = __syncthreads_or(big);
         if (tid < CPT) {
             int pre = 0;
             for (int w = 0; w < wid; ++w) pre += T.wt[w];
@@ -769,7 +790,7 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
         bool have_base = false, pref = true;
         for (int cb = 0; cb < CPT;) {
             const int ce = batch_end(T.ls, cb, CPT, TP);
-            cells_batch<MIXED, MANY>(d, a, T, tid, cb, ce, srec, ent, cellof, acc, have_base, npref, pref);
+            cells_batch<MIXED, MANY>(d, a, T, tid, cb, ce, srec, ent, cellof, acc, have_base, npref, pref, tile_ovf);
             cb = ce;
         }
 
@@ -798,6 +819,7 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
         const unsigned done = atomicAdd(&d.ticket[2 + (T.epoch & 1u)], 1u);
         if (done == gridDim.x - 1) {
             d.ticket[2 + (T.epoch & 1u)] = 0u;
+            d.ovf_n[a0.cur] = 0u;   // every CTA has read the consumed overflow list
             __threadfence();
             d.ctl->epoch = T.epoch + 1u;
             if (a0.opts & CP_ADVANCE) d.ctl->step = T.step + 1u;

@@ -29,7 +29,8 @@ constexpr int CP_THREADS = 256;    // threads per cell-pass CTA
 constexpr int CP_WARPS = CP_THREADS / 32;
 constexpr int CP_STAGE_M = 6;      // particles a cell-pass thread stages at once (mixed records)
 constexpr int CP_STAGE_D = 6;      // particles a cell-pass thread stages at once (fp64 records)
-constexpr int CP_MAX_CAP = 768;    // largest bucket_cap (a crowded tile uses the whole CTA)
+constexpr int CP_MAX_CAP = 768;    // largest bucket_cap
+constexpr int CP_MAX_CELL = 1536;  // most particles one cell may hold (the cell pass stages a cell at once)
 constexpr int CP_NEAR_CAND_MIN = 5;   // colloids from which the mixed cell pass filters them per batch
 constexpr int MD_THREADS = 1024;   // threads of the near-field MD CTA (one per replica)
 constexpr int MAXC = 64;           // colloids per replica handled by the MD CTA
@@ -132,6 +133,8 @@ struct Dev {
     void *rec[2];                // solvent records, double buffered
     int *count[2];               // particles per cell, double buffered
     int *bucket[2];              // [cell * cap + rank] -> storage slot
+    int2 *ovf[2];                // entries past bucket_cap: (cell, storage slot), any order
+    unsigned int *ovf_n;         // [2]: entries appended to ovf[b] (reset by the pass that consumes b)
     int *near_list;              // per replica region [part_off, part_off + n_part)
     int *near_count;             // [n_rep]
     unsigned long long *tile_state;  // decoupled look-back, one word per tile
@@ -161,6 +164,7 @@ struct Dev {
     const int *grid_start;       // lookup-grid list offsets
     const unsigned short *grid_list;
     int cap;
+    int ovf_cap;                 // entries each overflow list holds
     int lb_limit;                // polls before a look-back wait gives up (ERR_TIMEOUT)
     int lb_stall;                // test hook: the look-back treats every predecessor as not ready
     int many_col;                // 1: some replica has >= CP_NEAR_CAND_MIN colloids
@@ -545,14 +549,24 @@ __device__ __forceinline__ void wrapped_colloid(const ReplicaDev &rp, const doub
 }
 
 // ---------------------------------------------------------------------------
-// Bins: one particle into the cell's bucket.  Cells above cap raise
-// ERR_OVERFLOW (the entry is dropped; the step is then invalid).
+// Bins: one particle into its cell.  The first bucket_cap entries of a cell go
+// to its bucket row; the rest are appended to the buffer's overflow list,
+// which the cell pass reads for the cells that need it.  A full overflow list
+// raises ERR_OVERFLOW (the entry is dropped; the step is then invalid).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void bin_store(const Dev &d, int buf, int gcell, int r, int slot)
+{
+    if (r < d.cap) {
+        d.bucket[buf][(long long)gcell * d.cap + r] = slot;
+    } else {
+        const unsigned k = atomicAdd(&d.ovf_n[buf], 1u);
+        if (k < (unsigned)d.ovf_cap) d.ovf[buf][k] = make_int2(gcell, slot);
+        else atomicMax(&d.err[ERR_OVERFLOW], (unsigned int)(r + 1));
+    }
+}
 __device__ __forceinline__ void bin_particle(const Dev &d, int buf, int gcell, int slot)
 {
-    int r = atomicAdd(&d.count[buf][gcell], 1);
-    if (r < d.cap) d.bucket[buf][(long long)gcell * d.cap + r] = slot;
-    else atomicMax(&d.err[ERR_OVERFLOW], (unsigned int)(r + 1));
+    bin_store(d, buf, gcell, atomicAdd(&d.count[buf][gcell], 1), slot);
 }
 
 // Near-colloid test of §1.4's Verlet-list radius: may this particle come

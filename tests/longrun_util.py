@@ -35,15 +35,22 @@ def _min_image(d, L):
 
 
 class _Acc:
+    """Samples per replica as (interval index of the window end, value)."""
+
     def __init__(self, R):
         self.T = [[] for _ in range(R)]
         self.D = [[] for _ in range(R)]
         self.V = [[] for _ in range(R)]
 
     def result(self):
-        f = lambda a: np.array([np.mean(s) for s in a])
-        return {"T": f(self.T), "D": f(self.D), "V": f(self.V),
-                "samples": {"T": len(self.T[0]), "D": len(self.D[0]), "V": len(self.V[0])}}
+        return {"T": self.T, "D": self.D, "V": self.V}
+
+
+def per_replica(samples, k_max=None):
+    """Per-replica means of the samples whose window ends at or before k_max
+    (all samples when None): equal time windows on every side, since the
+    reactions heat the unthermostatted dimer system slowly."""
+    return np.array([np.mean([v for k, v in s if k_max is None or k <= k_max]) for s in samples])
 
 
 def _schedule(K, a, b, n_win, w):
@@ -71,7 +78,7 @@ def run_gpu(api, precision, R, warm, K, t_every=50, a=2, b=8, n_win=10, w=20, L=
     for k in range(K + 1):
         if k % t_every == 0 and k > 0:
             for r in range(R):
-                acc.T[r].append(s.observables(r)["temperature"])
+                acc.T[r].append((k, s.observables(r)["temperature"]))
         for j, t0 in enumerate(d_starts):
             if k in (t0, t0 + a, t0 + b):
                 for r in range(R):
@@ -85,13 +92,13 @@ def run_gpu(api, precision, R, warm, K, t_every=50, a=2, b=8, n_win=10, w=20, L=
                         db = _min_image(snaps.pop((j, b, r)) - x0, Lb)
                         msd_a = float((da * da).sum(1).mean())
                         msd_b = float((db * db).sum(1).mean())
-                        acc.D[r].append((msd_b - msd_a) / (6.0 * (b - a) * tau))
+                        acc.D[r].append((k, (msd_b - msd_a) / (6.0 * (b - a) * tau)))
         if k in vstart or k in v_starts:
             for r in range(R):
                 X = s.get_colloids(r)["x"]
                 if k in vstart:
                     X0, u = vstart[k][r]
-                    acc.V[r].append(float(np.dot(X.mean(0) - X0, u)) / (w * tau))
+                    acc.V[r].append((k, float(np.dot(X.mean(0) - X0, u)) / (w * tau)))
                 if k in v_starts and k + w <= K:
                     ax = X[1] - X[0]
                     vstart.setdefault(k + w, {})[r] = (X.mean(0), ax / np.linalg.norm(ax))
@@ -115,7 +122,7 @@ def run_oracle(orc, R, warm, K, t_every=50, a=2, b=8, n_win=10, w=20, L=16):
         vst = {}
         for k in range(K + 1):
             if k % t_every == 0 and k > 0:
-                acc.T[r].append(o.temperature())
+                acc.T[r].append((k, o.temperature()))
             for j, t0 in enumerate(d_starts):
                 if k in (t0, t0 + a, t0 + b):
                     snap[(j, k - t0)] = o.x[np.argsort(o.id)].copy()
@@ -123,11 +130,11 @@ def run_oracle(orc, R, warm, K, t_every=50, a=2, b=8, n_win=10, w=20, L=16):
                     x0 = snap.pop((j, 0))
                     da = _min_image(snap.pop((j, a)) - x0, Lb)
                     db = _min_image(snap.pop((j, b)) - x0, Lb)
-                    acc.D[r].append((float((db * db).sum(1).mean()) - float((da * da).sum(1).mean()))
-                                    / (6.0 * (b - a) * tau))
+                    acc.D[r].append((k, (float((db * db).sum(1).mean()) - float((da * da).sum(1).mean()))
+                                     / (6.0 * (b - a) * tau)))
             if k in vst:
                 X0, u = vst.pop(k)
-                acc.V[r].append(float(np.dot(o.X.mean(0) - X0, u)) / (w * tau))
+                acc.V[r].append((k, float(np.dot(o.X.mean(0) - X0, u)) / (w * tau)))
             if k in v_starts and k + w <= K:
                 ax = o.X[1] - o.X[0]
                 vst[k + w] = (o.X.mean(0).copy(), ax / np.linalg.norm(ax))

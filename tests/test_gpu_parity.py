@@ -315,12 +315,46 @@ def test_one_crowded_cell(precision):
     assert not vel_bad(st["v"], o.v, 1.0, precision).any()
 
 
+@pytest.mark.parametrize("precision", PRECS)
+def test_overflow_list_keeps_fused_steps_exact(precision):
+    """A bucket row of 8 at density 10: about a third of the cells spill into
+    the overflow list every collision, and a crowd of 300 particles puts a few
+    cells far past the row.  The cell pass reads the spilled entries back in
+    canonical order: fused steps equal the oracle (fp64 bit for bit) and no
+    EOVERFLOW is raised."""
+    cfg, col, bonds, x, v, fl = _dimer(precision, bulk_rate=0.05)
+    x = x.copy()
+    rng = np.random.Generator(np.random.PCG64(12))
+    x[:300] = 1.25 + np.floor(rng.uniform(0.0, 0.5, (300, 3)) * 2**24) * 2.0**-24
+    g = gpu(cfg, x, v, fl, col, bonds, precision=precision, cap=8, step=5)
+    o = oracle(cfg, x, v, fl, col, bonds, step=5)
+    for _ in range(3):
+        g.step(1)
+        o.step(1)
+        _compare_step(cfg, g.get_state(), o, precision)
+    assert o.count.max() > 8 and (o.count > 8).mean() > 0.1
+    assert g.bucket_cap() == 8
+
+
 def test_bucket_overflow_is_reported():
+    """EOVERFLOW remains for a cell beyond what the cell pass stages (1536
+    particles) and for a full overflow list."""
     cfg = synth.base_config(L=(4, 4, 4), precision="mixed")
-    n = 200
+    n = 1600
     x = np.full((n, 3), 1.5) + np.linspace(0, 0.01, n)[:, None]
     v = np.zeros((n, 3))
     g = gpu(cfg, x, v, None, precision="mixed", cap=64)
+    g.shift_and_sort()
+    with pytest.raises(api.RmpcdError) as e:
+        g.get_state()
+    assert e.value.code == "EOVERFLOW"
+    o = oracle(cfg, x, v, None)
+    o.shift_and_sort()
+    assert o.count.max() > 1536
+    # a one-entry row: nearly every particle spills, past the list's 1024 + n/16 entries
+    cfg = synth.base_config(L=(8, 8, 8), precision="mixed", seed=2)
+    x, v, fl = synth.solvent(cfg, seed=3)
+    g = gpu(cfg, x, v, fl, precision="mixed", cap=1)
     g.shift_and_sort()
     with pytest.raises(api.RmpcdError) as e:
         g.get_state()
