@@ -115,7 +115,7 @@ def lib():
             L.orc_n_cells.argtypes = [P(Params)]
             L.orc_n_cells.restype = i64
             L.orc_cell_keys.argtypes = [P(Params), i64, P(d), P(d), P(i32)]
-            L.orc_counting_sort.argtypes = [i64, P(i32), i64, P(i64), P(i64), P(i64)]
+            L.orc_counting_sort.argtypes = [i64, P(i32), P(u32), i64, P(i64), P(i64), P(i64)]
             L.orc_gather.argtypes = [i64, P(i64), C.c_void_p, C.c_void_p, i64]
             L.orc_collide.argtypes = [P(Params), u32, i64, P(i64), P(i64), P(d)]
             L.orc_bulk_react.argtypes = [P(Params), u32, i64, P(i64), P(i64), P(u8)]
@@ -219,12 +219,17 @@ def cell_keys(cfg, x, s) -> np.ndarray:
     return key
 
 
-def counting_sort(key, ncells):
+def counting_sort(key, ncells, ids=None):
+    """Order of the particles by (cell key, id); ids None: the index is the id."""
     key = np.ascontiguousarray(key, dtype=np.int32)
     perm = np.zeros(len(key), dtype=np.int64)
     count = np.zeros(ncells, dtype=np.int64)
     start = np.zeros(ncells, dtype=np.int64)
-    lib().orc_counting_sort(len(key), _ptr(key, C.c_int32), ncells, _ptr(perm, C.c_int64),
+    idp = None
+    if ids is not None:
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        idp = _ptr(ids, C.c_uint32)
+    lib().orc_counting_sort(len(key), _ptr(key, C.c_int32), idp, ncells, _ptr(perm, C.c_int64),
                             _ptr(count, C.c_int64), _ptr(start, C.c_int64))
     return perm, count, start
 
@@ -419,13 +424,13 @@ class OracleSystem:
             raise SkinError("colloid displacement exceeded the skin")
 
     def shift_and_sort(self) -> None:
-        """Random grid shift, cell keys and stable counting sort; reorders the state."""
+        """Random grid shift, cell keys and counting sort by (cell, id); reorders the state."""
         L = lib()
         s = grid_shift(self.p.seed, self.step_index)
         key = np.zeros(self.n, dtype=np.int32)
         L.orc_cell_keys(C.byref(self.p), self.n, _ptr(self.x, C.c_double), _ptr(s, C.c_double),
                         _ptr(key, C.c_int32))
-        perm, count, start = counting_sort(key, self.ncells)
+        perm, count, start = counting_sort(key, self.ncells, self.id)
         self.x = gather(perm, self.x)
         self.v = gather(perm, self.v)
         self.flags = gather(perm, self.flags)

@@ -207,9 +207,13 @@ void orc_cell_keys(const orc_params *p, int64_t n, const double *x, const double
     }
 }
 
-/* Stable counting sort by key: perm[j] = old index of the particle that takes
- * slot j; equal keys keep their old order.  count/start are per cell. */
-void orc_counting_sort(int64_t n, const int32_t *key, int64_t n_cells,
+/* Counting sort by key, particles of one cell in increasing id order:
+ * perm[j] = old index of the particle that takes slot j.  The paper sorts the
+ * particles by cell and leaves the order within a cell open; ordering by the
+ * particle's id makes it canonical whatever order the particles arrive in.
+ * Ids are unique within a system (NULL: the old index serves as the id).
+ * count/start are per cell. */
+void orc_counting_sort(int64_t n, const int32_t *key, const uint32_t *id, int64_t n_cells,
                        int64_t *perm, int64_t *count, int64_t *start)
 {
     for (int64_t c = 0; c < n_cells; ++c) count[c] = 0;
@@ -220,6 +224,17 @@ void orc_counting_sort(int64_t n, const int32_t *key, int64_t n_cells,
     for (int64_t c = 0; c < n_cells; ++c) fill[c] = start[c];
     for (int64_t i = 0; i < n; ++i) perm[fill[key[i]]++] = i;
     free(fill);
+    /* within each cell: insertion sort by id (cells hold a few particles) */
+    for (int64_t c = 0; c < n_cells; ++c) {
+        int64_t *p = perm + start[c];
+        for (int64_t a = 1; a < count[c]; ++a) {
+            int64_t q = p[a];
+            uint64_t kq = id ? id[q] : (uint64_t)q;
+            int64_t b = a - 1;
+            while (b >= 0 && (id ? (uint64_t)id[p[b]] : (uint64_t)p[b]) > kq) { p[b + 1] = p[b]; --b; }
+            p[b + 1] = q;
+        }
+    }
 }
 
 /* out[j] = in[perm[j]] for records of `width` bytes. */

@@ -36,13 +36,15 @@ struct rmpcd_system {
     uint32_t *stage_id = nullptr;
     int32_t *stage_cell = nullptr;
     unsigned long long *prof_acc = nullptr;   // [PROF_MAX_BINS * PROF_FIELDS] slab-profile sums
+    int *flat_fill = nullptr;                 // [n_rep] records placed by a flatten
     bool dry = false;          // sizing only (rmpcd_workspace_size): count bytes, allocate nothing
     size_t dry_bytes = 0;
     // pipeline state
     uint32_t step = 0;
     int cur = 0;        // record buffer holding the state
     int bcur = 0;       // count/bucket buffer of the next collision (fused)
-    bool primed = false;
+    bool primed = false;       // bins for the collision of `step` exist
+    bool in_rows = false;      // the state lives in record rows + near area (fused run), not in rec[cur]
     bool has_sort = false;
     uint32_t sort_step = 0;
     bool obs_valid = false;
@@ -362,22 +364,41 @@ static int auto_cap(const rmpcd_params *p, int n_rep)
     return std::min(cap, CP_MAX_CAP);
 }
 
-// Re-allocate the buckets for width `cap` (at a step boundary: the pending
-// bins are dropped and rebuilt by the next pass).
+// Bytes of one buffer of cell rows at width cap: a record (fused run) or a
+// slot number (flat layout) per place.
+static size_t row_bytes(const rmpcd_system *sys, int cap)
+{
+    const size_t recsz = sys->mixed ? sizeof(RecM) : sizeof(RecD);
+    return (size_t)sys->n_tiles * CPT * (size_t)cap * recsz;
+}
+
+static rmpcd_status flatten(rmpcd_system *sys);
+
+// Re-allocate the rows for width `cap` (at a step boundary: a fused run's
+// state is flattened first; pending bins are dropped and rebuilt by the next
+// pass).
 static rmpcd_status set_bucket_cap(rmpcd_system *sys, int cap)
 {
+    rmpcd_status st = flatten(sys);
+    if (st != RMPCD_OK) return st;
     CK(cudaStreamSynchronize(sys->stream));
     drop_graphs(sys);
     const size_t ncells = (size_t)sys->n_tiles * CPT;
     for (int b = 0; b < 2; ++b) {
-        auto it = std::find(sys->allocs.begin(), sys->allocs.end(), static_cast<void *>(sys->d.bucket[b]));
+        auto it = std::find(sys->allocs.begin(), sys->allocs.end(), sys->d.brec[b]);
         if (it != sys->allocs.end()) sys->allocs.erase(it);
-        cudaFree(sys->d.bucket[b]);
+        cudaFree(sys->d.brec[b]);
+        sys->d.brec[b] = nullptr;
         sys->d.bucket[b] = nullptr;
     }
-    rmpcd_status st = dalloc(sys, &sys->d.bucket[0], ncells * (size_t)cap);
-    if (st == RMPCD_OK) st = dalloc(sys, &sys->d.bucket[1], ncells * (size_t)cap);
+    unsigned char *rows[2] = {nullptr, nullptr};
+    st = dalloc(sys, &rows[0], row_bytes(sys, cap));
+    if (st == RMPCD_OK) st = dalloc(sys, &rows[1], row_bytes(sys, cap));
     if (st != RMPCD_OK) return st;
+    for (int b = 0; b < 2; ++b) {
+        sys->d.brec[b] = rows[b];
+        sys->d.bucket[b] = reinterpret_cast<int *>(rows[b]);
+    }
     sys->cap = cap;
     sys->d.cap = cap;
     CK(cudaMemsetAsync(sys->d.count[0], 0, sizeof(int) * ncells, sys->stream));
@@ -536,14 +557,23 @@ static rmpcd_status create_system(rmpcd_system **out, int32_t precision, int32_t
     AL(&r1, recsz * n_total);
     AL(&d.count[0], ncells);
     AL(&d.count[1], ncells);
-    AL(&d.bucket[0], ncells * bucket_cap);
-    AL(&d.bucket[1], ncells * bucket_cap);
-    // overflow lists: entries of cells beyond bucket_cap (rare at the
-    // automatic width; a fixed narrow width leans on them)
-    const long long ovf_cap = 1024 + n_total / 16;
+    // cell rows: a fused run's records, or the flat layout's slot numbers
+    // (same memory; one layout in use at a time)
+    unsigned char *rows0 = nullptr, *rows1 = nullptr;
+    AL(&rows0, (size_t)ncells * bucket_cap * recsz);
+    AL(&rows1, (size_t)ncells * bucket_cap * recsz);
+    // overflow lists: entries (and a fused run's records) of cells beyond
+    // bucket_cap (rare at the automatic width; a fixed narrow width leans on
+    // them)
+    const long long ovf_cap = 1024 + n_total / 8;
     AL(&d.ovf[0], ovf_cap);
     AL(&d.ovf[1], ovf_cap);
     AL(&d.ovf_n, 2);
+    unsigned char *orec0 = nullptr, *orec1 = nullptr, *nrec = nullptr;
+    AL(&orec0, (size_t)ovf_cap * recsz);
+    AL(&orec1, (size_t)ovf_cap * recsz);
+    AL(&nrec, (size_t)recsz * n_total);   // the near area of a fused run
+    AL(&sys->flat_fill, n_replicas);
     AL(&d.near_list, n_total);
     AL(&d.near_count, n_replicas);
     AL(&d.tile_state, n_tiles);
@@ -641,6 +671,13 @@ static rmpcd_status create_system(rmpcd_system **out, int32_t precision, int32_t
     d.tile_rep = dtile;
     d.rec[0] = r0;
     d.rec[1] = r1;
+    d.brec[0] = rows0;
+    d.brec[1] = rows1;
+    d.bucket[0] = reinterpret_cast<int *>(rows0);
+    d.bucket[1] = reinterpret_cast<int *>(rows1);
+    d.orec[0] = orec0;
+    d.orec[1] = orec1;
+    d.near_rec = nrec;
     d.bulk_thr = dthr;
     d.colM = dM; d.colSig = dS; d.colEpsA = dEA; d.colEpsB = dEB; d.colRc2 = dR2; d.colRc = dR;
     d.colSig_f = dfS; d.colEpsA_f = dfEA; d.colEpsB_f = dfEB; d.colRc2_f = dfR2; d.colRc_f = dfR;
@@ -687,9 +724,11 @@ static void drop_graphs(rmpcd_system *sys)
             }
 }
 
-// Drop a primed fused pipeline (pending bins and near lists).
+// Back to the flat layout: a fused run's state is flattened (sorted on the
+// grid of its last collision); pending bins of a primed run are dropped.
 static rmpcd_status unprime(rmpcd_system *sys)
 {
+    if (sys->in_rows) return flatten(sys);
     if (!sys->primed) return RMPCD_OK;
     const size_t ncells = (size_t)sys->n_tiles * CPT;
     CK(cudaMemsetAsync(sys->d.count[0], 0, sizeof(int) * ncells, sys->stream));
@@ -723,6 +762,29 @@ static rmpcd_status rebin_pass(rmpcd_system *sys, uint32_t grid_step, int opts, 
     return RMPCD_OK;
 }
 
+// A fused run's state (the record rows of buffer bcur, their overflow records
+// and the near area) back into the flat slots of rec[cur], sorted on the grid
+// of the last collision.  Sorting restores the canonical order (cell, id);
+// positions have not moved since that collision, so every particle's cell
+// key is the one it collided in.
+static rmpcd_status flatten(rmpcd_system *sys)
+{
+    if (!sys->in_rows) return RMPCD_OK;
+    sys->in_rows = false;
+    sys->primed = false;
+    const size_t ncells = (size_t)sys->n_tiles * CPT;
+    CK(cudaMemsetAsync(sys->flat_fill, 0, sizeof(int) * sys->n_rep, sys->stream));
+    launch_flatten(sys->mixed, sys->d, sys->bcur, sys->cur, sys->flat_fill, sys->stream);
+    rmpcd_status st = after_launch(sys, 4);
+    if (st != RMPCD_OK) return st;
+    CK(cudaMemsetAsync(sys->d.count[0], 0, sizeof(int) * ncells, sys->stream));
+    CK(cudaMemsetAsync(sys->d.count[1], 0, sizeof(int) * ncells, sys->stream));
+    CK(cudaMemsetAsync(sys->d.ovf_n, 0, sizeof(unsigned int) * 2, sys->stream));
+    CK(cudaMemsetAsync(sys->d.near_count, 0, sizeof(int) * sys->n_rep, sys->stream));
+    if (!sys->has_sort) return RMPCD_OK;
+    return rebin_pass(sys, sys->sort_step, CP_WRITE, 0);
+}
+
 static rmpcd_status check_errors(rmpcd_system *sys)
 {
     unsigned int e[ERR_COUNT];
@@ -734,12 +796,12 @@ static rmpcd_status check_errors(rmpcd_system *sys)
     CK(cudaMemsetAsync(sys->d.err, 0, sizeof e, sys->stream));
     CK(cudaStreamSynchronize(sys->stream));
     if (e[ERR_TIMEOUT]) return fail(sys, RMPCD_ETIMEOUT, "a cell-pass look-back wait timed out; the state is invalid");
-    if (e[ERR_BOUNDS]) return fail(sys, RMPCD_ESTATE, "inconsistent bins (slot out of range); the state is invalid");
     if (e[ERR_OVERFLOW])
         return fail(sys, RMPCD_EOVERFLOW,
                     "a cell held %u particles: beyond the %d a cell may hold, or the overflow list past bucket_cap %d "
                     "(%d entries) ran full; the state is invalid", e[ERR_OVERFLOW], CP_MAX_CELL, sys->cap,
                     sys->d.ovf_cap);
+    if (e[ERR_BOUNDS]) return fail(sys, RMPCD_ESTATE, "inconsistent bins (slot out of range); the state is invalid");
     if (e[ERR_SKIN]) return fail(sys, RMPCD_ESKIN, "a colloid moved further than skin in one interval (%u times)", e[ERR_SKIN]);
     return fail(sys, RMPCD_ESTATE, "device error");
 }
@@ -799,6 +861,8 @@ rmpcd_status rmpcd_get_state(rmpcd_system *sys, int32_t replica, double *x, doub
     if (replica < 0 || replica >= sys->n_rep) return fail(sys, RMPCD_EINVAL, "replica %d out of range", replica);
     const ReplicaDev &rp = sys->rep[replica];
     if (n != rp.n_part) return fail(sys, RMPCD_EINVAL, "n = %lld but replica %d has %d particles", (long long)n, replica, rp.n_part);
+    rmpcd_status st0 = unprime(sys);   // a fused run's state, flattened and sorted
+    if (st0 != RMPCD_OK) return st0;
     if (n > 0) {
         double *ox = x, *ov = v;
         uint8_t *of = flags;
@@ -1031,8 +1095,9 @@ static int launch_interval(rmpcd_system *sys, int cur, int bcur, bool instrument
         if (instrument) tstop(sys, 1, ev);
         n += 1;
     }
-    CellPassArgs a{CP_FLIGHT | CP_COLLIDE | CP_REACT | CP_NEXT | CP_WRITE | CP_ADVANCE, STEP_DEVICE, bcur, bcur ^ 1,
-                   cur, cur ^ 1};
+    // record rows bcur -> rows bcur ^ 1 and the near area (the flat buffers
+    // are not touched)
+    CellPassArgs a{CP_FLIGHT | CP_COLLIDE | CP_REACT | CP_NEXT | CP_ADVANCE, STEP_DEVICE, bcur, bcur ^ 1, cur, cur ^ 1};
     if (instrument) tstart(sys, &ev);
     launch_cellpass(sys->mixed, sys->d, a, sys->stream);
     if (instrument) tstop(sys, 2, ev);
@@ -1106,8 +1171,8 @@ rmpcd_status rmpcd_step(rmpcd_system *sys, int32_t n_intervals)
             const int n = launch_interval(sys, sys->cur, sys->bcur, true);
             if ((st = after_launch(sys, n)) != RMPCD_OK) return st;
         }
-        sys->cur ^= 1;
         sys->bcur ^= 1;
+        sys->in_rows = true;
         sys->sort_step = sys->step;
         sys->step += 1u;
         left -= 1;
@@ -1156,9 +1221,9 @@ rmpcd_status rmpcd_observables(rmpcd_system *sys, int32_t replica, rmpcd_obs *ou
     rmpcd_status st;
     if (!sys->obs_valid) {
         if (!sys->has_sort) return fail(sys, RMPCD_ESTATE, "no collision grid yet: sort or step first");
-        // rebin on the grid of the last sort into the free count buffer
-        const int b = sys->primed ? (sys->bcur ^ 1) : sys->bcur;
-        if ((st = rebin_pass(sys, sys->sort_step, CP_OBS, b)) != RMPCD_OK) return st;
+        // the flat state, rebinned on the grid of the last sort
+        if ((st = unprime(sys)) != RMPCD_OK) return st;
+        if ((st = rebin_pass(sys, sys->sort_step, CP_OBS, 0)) != RMPCD_OK) return st;
         launch_obs_reduce(sys->d, sys->stream);
         if ((st = after_launch(sys, 1)) != RMPCD_OK) return st;
         sys->obs_valid = true;
@@ -1189,6 +1254,8 @@ rmpcd_status rmpcd_profile(rmpcd_system *sys, int32_t replica, int32_t axis, int
     if (n_bins < 1 || n_bins > RMPCD_MAX_PROFILE_BINS)
         return fail(sys, RMPCD_EINVAL, "n_bins %d outside 1..%d", n_bins, RMPCD_MAX_PROFILE_BINS);
     const size_t words = (size_t)n_bins * PROF_FIELDS;
+    rmpcd_status st0 = unprime(sys);   // the flat state
+    if (st0 != RMPCD_OK) return st0;
     CK(cudaMemsetAsync(sys->prof_acc, 0, words * sizeof(unsigned long long), sys->stream));
     launch_profile(sys->mixed, sys->d, replica, sys->rep[replica].n_part, sys->cur, axis, n_bins, sys->prof_acc,
                    sys->stream);

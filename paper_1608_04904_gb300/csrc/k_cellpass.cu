@@ -1,28 +1,28 @@
 // k_cellpass.cu -- the per-cell pass of one collision (§1.4 of the RMPCDMD
-// paper, arXiv:1608.04904): sorted gather, SRD / MPC-AT / virtual-particle
-// collision, bulk B -> A reaction, and (fused) free flight + binning of every
-// particle for the next collision.
+// paper, arXiv:1608.04904): gather by cell, SRD / MPC-AT / virtual-particle
+// collision, bulk B -> A reaction, and (fused run) free flight + binning of
+// every particle for the next collision.
 //
 // The work is cut into tiles of CPT consecutive cells of one replica.  As many
 // CTAs as fit on the GPU run persistently, each taking tiles in ticket order.
-// A tile's particles are the bucket entries of its cells; within a cell they
-// are put back in increasing storage slot order, which makes the sort stable
-// and the result independent of the atomic order in which the buckets were
-// filled.  The tile's first output slot is the exclusive prefix of all
-// earlier tiles' particle counts, found by a single-pass decoupled look-back
-// (Merrill & Garland 2016) over tiles taken in ticket order.
-//
-// The CTA stages the tile's particles (in batches of whole cells when they
-// exceed the staging area) and runs the stages with all its threads: one
+// A CTA stages a tile's particles in shared memory (in batches of whole cells
+// when they exceed the staging area) in the order they arrive, then ranks the
+// particles of each cell by id: that rank is the canonical order in which a
+// cell's velocities are summed, its reaction partner counted and (flat
+// layout) its records written.  Stages run with all threads of the CTA: one
 // thread per particle for the gather, rotation, write and binning, one thread
-// per cell for the cell sums and the per-cell draws.  The tile's aggregate is
-// published at once and the look-back scan runs only when the first batch
-// needs the base (before its writes), so the gather and the per-cell work of
-// a tile overlap the wait for its predecessors.
+// per cell for the cell sums and the per-cell draws.
 //
-// Per particle this reads its bucket entry (4 B) and its record (32 B mixed /
-// 64 B fp64) and writes its record and its next bucket entry: one pass over
-// the solvent per collision.
+// Two layouts (see Dev):
+//   fused run (FUSED): a cell's records are read contiguously from its row;
+//     each far particle's record is written into the row of the cell it will
+//     occupy at the next collision (an atomic count gives its place), near
+//     particles into the near area.  One read and one write of each record,
+//     no index traffic, no global prefix: tiles are independent.
+//   flat layout: records come from flat slots through index buckets and are
+//     written to flat slots in canonical order; a tile's first slot is the
+//     exclusive prefix of all earlier tiles' particle counts, found by a
+//     single-pass decoupled look-back (Merrill & Garland 2016).
 #include <algorithm>
 
 #include "rmpcd_kernels.cuh"
@@ -144,6 +144,13 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+template <class Rec>
+__device__ __forceinline__ void cp_async_rec(Rec *dst, const Rec *src)
+{
+#pragma unroll
+    for (int q = 0; q < (int)(sizeof(Rec) / 16); ++q)
+        cp_async16(reinterpret_cast<char *>(dst) + 16 * q, reinterpret_cast<const char *>(src) + 16 * q);
+}
 
 // Per-tile state shared by the threads of one CTA.
 template <bool MIXED>
@@ -165,18 +172,17 @@ struct TileShared {
     double red[CP_WARPS][8];
 };
 
-// Anderson thermostat (MPC-AT, §1.4) of one cell of n particles (v in
-// sorted order): v_i <- v_cm + xi_i - <xi>, xi ~ N(0, kT_slab), with
-// rho_wall - n virtual partners in v_cm when virt.  The per-cell momentum
-// sums are FP64 on both paths; the Gaussian draws are in the path's
-// precision R.
+// Anderson thermostat (MPC-AT, §1.4) of one cell of n particles, the i-th in
+// canonical order at v[pm[i]]: v_i <- v_cm + xi_i - <xi>, xi ~ N(0, kT_slab),
+// with rho_wall - n virtual partners in v_cm when virt.  The per-cell momentum
+// sums are FP64 on both paths; the Gaussian draws are in the path's precision R.
 template <typename R, class Rec>
 __device__ __forceinline__ void mpcat_cell(const ReplicaDev &rp, uint32_t step, uint32_t lc, int slab, int n,
-                                           bool virt, Rec *v)
+                                           bool virt, Rec *v, const unsigned short *pm)
 {
     double sum[3] = {0.0, 0.0, 0.0};
     for (int i = 0; i < n; ++i)
-        for (int k = 0; k < 3; ++k) sum[k] = sum[k] + (double)v[i].v[k];
+        for (int k = 0; k < 3; ++k) sum[k] = sum[k] + (double)v[pm[i]].v[k];
     double vcm[3];
     if (virt) {
         const int nv = rp.rho_wall - n;
@@ -200,29 +206,33 @@ __device__ __forceinline__ void mpcat_cell(const ReplicaDev &rp, uint32_t step, 
         const R gg[3] = {g0, g1, g2};
         for (int k = 0; k < 3; ++k) {
             const R xi = sd * gg[k];
-            v[i].v[k] = xi;
+            v[pm[i]].v[k] = xi;
             xs[k] = xs[k] + (double)xi;
         }
     }
     for (int k = 0; k < 3; ++k) xs[k] = xs[k] / (double)n;
     for (int i = 0; i < n; ++i)
-        for (int k = 0; k < 3; ++k) v[i].v[k] = (R)(vcm[k] + ((double)v[i].v[k] - xs[k]));
+        for (int k = 0; k < 3; ++k) v[pm[i]].v[k] = (R)(vcm[k] + ((double)v[pm[i]].v[k] - xs[k]));
 }
 
-// Stage D, one thread per cell, particles summed in sorted order (the order
-// of the FP64 definition).
-template <bool MIXED, bool MANY>
+// Stage D, one thread per cell, particles summed in canonical order (the
+// order of the FP64 definition): the i-th particle of the cell at staging
+// index lo + perm[lo + i].
+template <bool MIXED, bool MANY, bool FUSED>
 __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, TileShared<MIXED> &T, int gt,
-                                               int cb, int ce, int pofs, typename Traits<MIXED>::Rec *srec)
+                                        int cb, int ce, int pofs, typename Traits<MIXED>::Rec *srec,
+                                        const unsigned short *perm)
 {
     using R = typename Traits<MIXED>::R;
     const ReplicaDev &rp = T.rp;
     const int lc0 = T.tile * CPT - rp.cell_off;
     const int opts = a.opts;
-    const bool want_near = MIXED && (opts & CP_NEXT) && rp.n_col > 0;
+    const bool want_near = FUSED && MIXED && (opts & CP_NEXT) && rp.n_col > 0;
     for (int c = cb + gt; c < ce; c += CP_THREADS) {
         const int n = T.cnt[c];
         const int lo = T.ls[c] - pofs;
+        const unsigned short *pm = perm + lo;
+        typename Traits<MIXED>::Rec *cr = srec + lo;
         const int lc = lc0 + c;
         T.mode[c] = 0;
         T.react[c] = -1;
@@ -238,17 +248,19 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
             for (int k = 0; k < rp.n_slabs; ++k)
                 if (cx >= rp.slab_lo[k] && cx < rp.slab_hi[k]) { slab = k; break; }
         const bool nearq = want_near && n > 0;
-        // the cell's velocity sum, in sorted order: for the SRD collision and
-        // for the near bound (stage D leaves the velocities unchanged outside
-        // MPC-AT slabs, where the bound is not taken)
+        // the cell's velocity sum, in canonical order: for the SRD collision
+        // and for the near bound (stage D leaves the velocities unchanged
+        // outside MPC-AT slabs, where the bound is not taken)
         R sum[3] = {R(0), R(0), R(0)};
         if (slab < 0 && (coll || nearq))
-            for (int i = 0; i < n; ++i)
-                for (int k = 0; k < 3; ++k) sum[k] = sum[k] + srec[lo + i].v[k];
+            for (int i = 0; i < n; ++i) {
+                const int q = pm[i];
+                for (int k = 0; k < 3; ++k) sum[k] = sum[k] + cr[q].v[k];
+            }
         int nbB = -1;   // B count, when the near bound's loop has taken it
         if (coll) {
             if (slab >= 0) {
-                mpcat_cell<R>(rp, a.step, (uint32_t)lc, slab, n, virt, srec + lo);
+                mpcat_cell<R>(rp, a.step, (uint32_t)lc, slab, n, virt, cr, pm);
                 T.mode[c] = 2;
             } else {
                 R vcm[3];
@@ -288,11 +300,10 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
                     for (int k = 0; k < 3; ++k) vc[k] = T.vcm[c][k];
                 R u2 = R(0);
                 int nb_ = 0;
-                for (int i = 0; i < n; ++i) {
-                    const R a0 = srec[lo + i].v[0] - vc[0], a1 = srec[lo + i].v[1] - vc[1],
-                            a2 = srec[lo + i].v[2] - vc[2];
+                for (int i = 0; i < n; ++i) {   // order-free: a maximum and a count
+                    const R a0 = cr[i].v[0] - vc[0], a1 = cr[i].v[1] - vc[1], a2 = cr[i].v[2] - vc[2];
                     u2 = max(u2, a0 * a0 + a1 * a1 + a2 * a2);
-                    nb_ += (srec[lo + i].fid & F_B) ? 1 : 0;
+                    nb_ += (cr[i].fid & F_B) ? 1 : 0;
                 }
                 nbB = nb_;
                 const float vb = (float)(sqrt(vc[0] * vc[0] + vc[1] * vc[1] + vc[2] * vc[2]) + sqrt(u2));
@@ -314,15 +325,17 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
         if ((opts & CP_REACT) && rp.bulk_on && n > 0) {
             if (nbB < 0) {
                 nbB = 0;
-                for (int i = 0; i < n; ++i) nbB += (srec[lo + i].fid & F_B) ? 1 : 0;
+                for (int i = 0; i < n; ++i) nbB += (cr[i].fid & F_B) ? 1 : 0;
             }
             if (nbB > 0) {
                 U4 w = philox((uint32_t)lc, a.step, P_REACT, 0u, rp.seed);
                 if ((unsigned long long)w.x < d.bulk_thr[rp.thr_off + nbB]) {
+                    // the pick-th B particle of the cell in canonical order
                     const int pick = (int)(((unsigned long long)w.y * (unsigned long long)nbB) >> 32);
                     for (int i = 0, seen = 0; i < n; ++i) {
-                        if (srec[lo + i].fid & F_B) {
-                            if (seen == pick) { T.react[c] = lo + i; break; }
+                        const int q = pm[i];
+                        if (cr[q].fid & F_B) {
+                            if (seen == pick) { T.react[c] = lo + q; break; }
                             ++seen;
                         }
                     }
@@ -407,12 +420,12 @@ __device__ void near_candidates(TileShared<MIXED> &T, int gt, int cb, int ce)
 }
 
 // The stages of the cell pass for the cells [cb, ce) of the tile, run by the
-// whole CTA (gt = thread index).  srec/ent/cellof are the staging arrays
-// (>= the batch).
-template <bool MIXED, bool MANY>
+// whole CTA (gt = thread index).  srec/ent/perm/cellof are the staging arrays
+// (>= the batch); ovf: a cell of the tile holds more than cap particles.
+template <bool MIXED, bool MANY, bool FUSED>
 __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXED> &T, int gt, int cb, int ce,
-                            typename Traits<MIXED>::Rec *srec, int *ent, unsigned char *cellof, double acc[8],
-                            bool &have_base, int &npref, bool &pref, bool ovf)
+                            typename Traits<MIXED>::Rec *srec, int *ent, unsigned short *perm,
+                            unsigned char *cellof, double acc[8], bool &have_base, int &npref, bool &pref, bool ovf)
 {
     using Rec = typename Traits<MIXED>::Rec;
     using R = typename Traits<MIXED>::R;
@@ -421,10 +434,7 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
     const int gc0 = T.tile * CPT;
     const int pofs = T.ls[cb];
     const int nb = T.ls[ce] - pofs;
-    const int part_lo = rp.part_off, part_hi = rp.part_off + rp.n_part;
     const int opts = a.opts;
-    const Rec *rin = reinterpret_cast<const Rec *>(d.rec[a.rin]);
-    Rec *rout = reinterpret_cast<Rec *>(d.rec[a.rout]);
     // register copies of what the per-particle loops read
     const HotM hm = hot_m(rp);
     const auto &hp = HotPick<MIXED>::get(rp, hm);
@@ -432,12 +442,13 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
     const int n_col = rp.n_col;
     const float shnf[3] = {T.shnf[0], T.shnf[1], T.shnf[2]};
 
-    // Every thread owns at most K particles of a batch; the global loads and
-    // atomics of a stage are issued for all of them before any result is
-    // used, so a thread waits for one memory round trip per stage.
+    // Every thread owns at most K particles of a batch (j = gt + u G); the
+    // global loads and atomics of a stage are issued for all of them before
+    // any result is used, so a thread waits for one memory round trip per
+    // stage.
     constexpr int K = Traits<MIXED>::K;
 
-    // A: the cell of every staged particle, then its bucket entry
+    // A: the cell of every staged particle
     for (int c = cb + gt; c < ce; c += G) {
         const int lo = T.ls[c] - pofs, n = T.cnt[c];
         for (int i = 0; i < n; ++i) cellof[lo + i] = (unsigned char)(c - cb);
@@ -449,7 +460,40 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
         if (gt < CPT && nt < d.n_tiles) npref = d.count[a.cur][nt * CPT + gt];
         pref = false;
     }
-    {
+    // B: every particle's record into the staging area, in arrival order
+    if constexpr (FUSED) {
+        // the first cap of a cell from its row, contiguous in memory
+        const Rec *rows = reinterpret_cast<const Rec *>(d.brec[a.cur]);
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+            const int j = gt + u * G;
+            if (j < nb) {
+                const int c = cb + cellof[j];
+                const int r = j + pofs - T.ls[c];
+                if (r < d.cap) cp_async_rec(srec + j, rows + (long long)(gc0 + c) * d.cap + r);
+            }
+        }
+        if (ovf) {
+            // the rest from the overflow records of the tile's cells (any
+            // order: the rank below orders them); T.react is the per-cell
+            // cursor, stage D rewrites it
+            for (int c = cb + gt; c < ce; c += G) T.react[c] = d.cap;
+            __syncthreads();
+            const int no = min((int)*(volatile const unsigned int *)&d.ovf_n[a.cur], d.ovf_cap);
+            const Rec *orec = reinterpret_cast<const Rec *>(d.orec[a.cur]);
+            for (int k = gt; k < no; k += G) {
+                const int2 q = d.ovf[a.cur][k];
+                const int c = q.x - gc0;
+                if (c >= cb && c < ce && q.y >= 0 && q.y < d.ovf_cap) {
+                    const int r = atomicAdd(&T.react[c], 1);
+                    if (r < T.cnt[c]) cp_async_rec(srec + T.ls[c] - pofs + r, orec + q.y);
+                }
+            }
+        }
+    } else {
+        // flat layout: slot numbers from the index buckets (past cap from the
+        // overflow entries), then the records from those slots
+        const int part_lo = rp.part_off, part_hi = rp.part_off + rp.n_part;
         int e[K];
 #pragma unroll
         for (int u = 0; u < K; ++u) {
@@ -463,56 +507,73 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
 #pragma unroll
         for (int u = 0; u < K; ++u)
             if (gt + u * G < nb) ent[gt + u * G] = e[u];
-    }
-    if (ovf) {
-        // a cell of the tile holds more than bucket_cap: its further entries
-        // come from the overflow list, in any order (stage B ranks every
-        // entry of a cell by its slot).  T.react serves as the per-cell
-        // cursor; stage D rewrites it.
-        for (int c = cb + gt; c < ce; c += G) T.react[c] = d.cap;
-        __syncthreads();
-        const int no = min((int)*(volatile const unsigned int *)&d.ovf_n[a.cur], d.ovf_cap);
-        for (int k = gt; k < no; k += G) {
-            const int2 q = d.ovf[a.cur][k];
-            const int c = q.x - gc0;
-            if (c >= cb && c < ce) {
-                const int r = atomicAdd(&T.react[c], 1);
-                if (r < T.cnt[c]) ent[T.ls[c] - pofs + r] = q.y;
+        if (ovf) {
+            for (int c = cb + gt; c < ce; c += G) T.react[c] = d.cap;
+            __syncthreads();
+            const int no = min((int)*(volatile const unsigned int *)&d.ovf_n[a.cur], d.ovf_cap);
+            for (int k = gt; k < no; k += G) {
+                const int2 q = d.ovf[a.cur][k];
+                const int c = q.x - gc0;
+                if (c >= cb && c < ce) {
+                    const int r = atomicAdd(&T.react[c], 1);
+                    if (r < T.cnt[c]) ent[T.ls[c] - pofs + r] = q.y;
+                }
             }
         }
-    }
-    __syncthreads();
-    // B: the place of every staged particle in its cell (stable order =
-    // increasing previous slot); its record is copied there asynchronously
-    // as soon as the place is known, so all of a thread's gathers are in
-    // flight together and overlap the remaining rank loops
-    {
+        __syncthreads();
+        const Rec *rin = reinterpret_cast<const Rec *>(d.rec[a.rin]);
         bool bad = false;
 #pragma unroll
         for (int u = 0; u < K; ++u) {
             const int j = gt + u * G;
             if (j < nb) {
-                const int c = cb + cellof[j];
-                const int lo = T.ls[c] - pofs, n = T.cnt[c];
-                const int e = ent[j];
-                int rank = 0;
-                for (int k = 0; k < n; ++k) rank += (ent[lo + k] < e) ? 1 : 0;
-                Rec *dst = srec + lo + rank;
-                if (e >= part_lo && e < part_hi) {
-                    const char *src = reinterpret_cast<const char *>(rin + e);
-#pragma unroll
-                    for (int q = 0; q < (int)(sizeof(Rec) / 16); ++q)
-                        cp_async16(reinterpret_cast<char *>(dst) + 16 * q, src + 16 * q);
+                const int s = ent[j];
+                if (s >= part_lo && s < part_hi) {
+                    cp_async_rec(srec + j, rin + s);
                 } else {
                     bad = true;
-                    *dst = Rec{};
+                    srec[j] = Rec{};
                 }
             }
         }
-        cp_async_wait_all();
         if (bad) atomicOr(&d.err[ERR_BOUNDS], 1u);
     }
+    cp_async_wait_all();
     __syncthreads();
+    // the id of every staged particle (a record missing after an overflow
+    // keeps stale contents; the run has latched the overflow)
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+        const int j = gt + u * G;
+        if (j < nb) ent[j] = (int)(srec[j].fid & ID_MASK);
+    }
+    __syncthreads();
+    // the canonical place of every particle in its cell: rank by id (ties,
+    // which valid states do not have, by staging place, so that the ranks
+    // always form a permutation)
+    int rk[K];
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+        const int j = gt + u * G;
+        if (j < nb) {
+            const int c = cb + cellof[j];
+            const int lo = T.ls[c] - pofs, n = T.cnt[c];
+            const int id = ent[j], me = j - lo;
+            int rank = 0;
+            for (int k = 0; k < n; ++k) {
+                const int o = ent[lo + k];
+                rank += (o < id || (o == id && k < me)) ? 1 : 0;
+            }
+            rk[u] = rank;
+            perm[lo + rank] = (unsigned short)me;
+        }
+    }
+    if constexpr (!FUSED) {
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < K; ++u)
+            if (gt + u * G < nb) ent[gt + u * G] = rk[u];   // the canonical place within the cell
+    }
     // C: fly the records the MD kernel did not move
 #pragma unroll 1
     for (int p = gt; p < nb; p += G) {
@@ -523,7 +584,7 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
     }
     __syncthreads();
     // D: per-cell work
-    cells_D<MIXED, MANY>(d, a, T, gt, cb, ce, pofs, srec);
+    cells_D<MIXED, MANY, FUSED>(d, a, T, gt, cb, ce, pofs, srec, perm);
     __syncthreads();
     if constexpr (MANY) {
         if (opts & CP_NEXT) {
@@ -531,9 +592,9 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
             __syncthreads();
         }
     }
-    if (!have_base) {
-        // stages A-D do not need the tile base; E does.  The aggregate went
-        // out in the prologue; warp 0 scans back now.
+    if (!FUSED && !have_base && (opts & CP_WRITE)) {
+        // stages A-D do not need the tile base; the flat write does.  The
+        // aggregate went out in the prologue; warp 0 scans back now.
         if (gt < 32) {
             const int base = tile_lookback(d, T.epoch, T.tile, T.ls[CPT], gt, false);
             if (gt == 0) T.base = base;
@@ -541,11 +602,11 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
         __syncthreads();
         have_base = true;
     }
-    // E: apply, write, classify for the next collision (the next cell of a
-    // far particle goes to ent[p]; -2 marks a near particle, -1 neither)
+    // E: apply and write (flat layout: at the canonical slot; fused run:
+    // classify for the next collision -- the next cell of a far particle goes
+    // to ent[p], -2 marks a near particle)
 #pragma unroll 1
     for (int p = gt; p < nb; p += G) {
-        int nkey = -1;
         const int c = cb + cellof[p];
         Rec rec = srec[p];
         if (T.mode[c] == 1) {
@@ -563,71 +624,82 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
             rec.v[2] = vc[2] + (ca * u2 + sa * x2 + od * nh[2]);
         }
         if (T.react[c] == p) rec.fid &= ~(F_B | F_TAG);
-        const int gslot = T.base + pofs + p;
-        const bool inb = gslot >= part_lo && gslot < part_hi;
-        if (!inb) atomicOr(&d.err[ERR_BOUNDS], 1u);
-        if ((opts & CP_WRITE) && inb) store_rec(rout + gslot, rec);
-        if (opts & CP_OBS) srec[p] = rec;
-        if ((opts & CP_NEXT) && inb) {
-            bool near;
-            if constexpr (MANY) near = T.mnear[c] && rec_near_cand(hp, n_col, T.nf, rec, T.cand, T.vbc[c] < 0.0f);
-            else near = n_col > 0 && T.mnear[c] && rec_near(d, hp, n_col, T.nf, rec);
-            if (near) {
-                nkey = -2;
-            } else {
-                Rec fl = rec;
-                rec_flight(hp, fl);
-                nkey = rp.cell_off + rec_key(hp, fl, T.shn, shnf);
-            }
-        }
-        ent[p] = nkey;
-    }
-    // bin for the next collision: all count atomics, then the bucket writes;
-    // the near particles join the near list with one atomic per warp, in
-    // flight together with the count atomics
-    if (opts & CP_NEXT) {
-        int mine = 0;
-        const bool appends = n_col > 0;   // uniform: replicas without colloids skip the near list
-        if (appends)
-#pragma unroll
-            for (int u = 0; u < K; ++u) {
-                const int p = gt + u * G;
-                mine += (p < nb && ent[p] == -2) ? 1 : 0;
-            }
-        int incl = mine;
-        if (appends)
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if ((gt & 31) >= o) incl += y;
-            }
-        const int wtot = appends ? __shfl_sync(0xffffffffu, incl, 31) : 0;
-        int nbase = 0;
-        if ((gt & 31) == 31 && wtot > 0) nbase = atomicAdd(&d.near_count[T.r], wtot);
-        int pos[K];
-#pragma unroll
-        for (int u = 0; u < K; ++u) {
-            const int p = gt + u * G;
-            const int key = p < nb ? ent[p] : -1;
-            pos[u] = key >= 0 ? atomicAdd(&d.count[a.nxt][key], 1) : -1;
-        }
-        if (wtot > 0) {
-            int k = __shfl_sync(0xffffffffu, nbase, 31) + incl - mine;
-#pragma unroll
-            for (int u = 0; u < K; ++u) {
-                const int p = gt + u * G;
-                if (p < nb && ent[p] == -2) {
-                    if (k < rp.n_part) d.near_list[rp.part_off + k] = T.base + pofs + p;
-                    else atomicOr(&d.err[ERR_BOUNDS], 1u);
-                    ++k;
+        if constexpr (FUSED) {
+            srec[p] = rec;
+            int nkey = -1;
+            if (opts & CP_NEXT) {
+                bool near;
+                if constexpr (MANY) near = T.mnear[c] && rec_near_cand(hp, n_col, T.nf, rec, T.cand, T.vbc[c] < 0.0f);
+                else near = n_col > 0 && T.mnear[c] && rec_near(d, hp, n_col, T.nf, rec);
+                if (near) {
+                    nkey = -2;
+                } else {
+                    Rec fl = rec;
+                    rec_flight(hp, fl);
+                    nkey = rp.cell_off + rec_key(hp, fl, T.shn, shnf);
                 }
             }
+            ent[p] = nkey;
+        } else {
+            if (opts & CP_WRITE) {
+                const int gslot = T.base + T.ls[c] + ent[p];
+                if (gslot >= rp.part_off && gslot < rp.part_off + rp.n_part)
+                    store_rec(reinterpret_cast<Rec *>(d.rec[a.rout]) + gslot, rec);
+                else
+                    atomicOr(&d.err[ERR_BOUNDS], 1u);
+            }
+            if (opts & CP_OBS) srec[p] = rec;
         }
+    }
+    if constexpr (FUSED) {
+        // bin for the next collision: all count atomics, then the record
+        // writes; the near particles join the near area with one atomic per
+        // warp, in flight together with the count atomics
+        if (opts & CP_NEXT) {
+            int mine = 0;
+            const bool appends = n_col > 0;   // uniform: replicas without colloids skip the near area
+            if (appends)
 #pragma unroll
-        for (int u = 0; u < K; ++u) {
-            if (pos[u] < 0) continue;
-            const int p = gt + u * G;
-            bin_store(d, a.nxt, ent[p], pos[u], T.base + pofs + p);
+                for (int u = 0; u < K; ++u) {
+                    const int p = gt + u * G;
+                    mine += (p < nb && ent[p] == -2) ? 1 : 0;
+                }
+            int incl = mine;
+            if (appends)
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if ((gt & 31) >= o) incl += y;
+                }
+            const int wtot = appends ? __shfl_sync(0xffffffffu, incl, 31) : 0;
+            int nbase = 0;
+            if ((gt & 31) == 31 && wtot > 0) nbase = atomicAdd(&d.near_count[T.r], wtot);
+            int pos[K];
+#pragma unroll
+            for (int u = 0; u < K; ++u) {
+                const int p = gt + u * G;
+                const int key = p < nb ? ent[p] : -1;
+                pos[u] = key >= 0 ? atomicAdd(&d.count[a.nxt][key], 1) : -1;
+            }
+            if (wtot > 0) {
+                int k = __shfl_sync(0xffffffffu, nbase, 31) + incl - mine;
+                Rec *near_rec = reinterpret_cast<Rec *>(d.near_rec) + rp.part_off;
+#pragma unroll
+                for (int u = 0; u < K; ++u) {
+                    const int p = gt + u * G;
+                    if (p < nb && ent[p] == -2) {
+                        if (k < rp.n_part) store_rec(near_rec + k, srec[p]);
+                        else atomicOr(&d.err[ERR_BOUNDS], 1u);
+                        ++k;
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < K; ++u) {
+                if (pos[u] < 0) continue;
+                const int p = gt + u * G;
+                bin_record_at(d, a.nxt, ent[p], pos[u], srec[p]);
+            }
         }
     }
     __syncthreads();
@@ -636,25 +708,28 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
         for (int c = cb + gt; c < ce; c += G) {
             const int n = T.cnt[c];
             const int lo = T.ls[c] - pofs;
+            const unsigned short *pm = perm + lo;
+            const Rec *cr = srec + lo;
             // the conservation diagnostics: per-cell momentum and energy sums
             // in FP64 on both paths (a pass with observables is not a timed one)
             double sum[3] = {0.0, 0.0, 0.0};
             double ke2 = 0.0;
             int nbB = 0;
             for (int i = 0; i < n; ++i) {
+                const Rec &ri = cr[pm[i]];
                 for (int k = 0; k < 3; ++k) {
-                    const double vk = (double)srec[lo + i].v[k];
+                    const double vk = (double)ri.v[k];
                     sum[k] = sum[k] + vk;
                     ke2 = ke2 + vk * vk;
                 }
-                nbB += (srec[lo + i].fid & F_B) ? 1 : 0;
+                nbB += (ri.fid & F_B) ? 1 : 0;
             }
             if (n >= 2) {
                 const double vcm[3] = {sum[0] / (double)n, sum[1] / (double)n, sum[2] / (double)n};
                 double ke = 0.0;
                 for (int i = 0; i < n; ++i)
                     for (int k = 0; k < 3; ++k) {
-                        const double u = (double)srec[lo + i].v[k] - vcm[k];
+                        const double u = (double)cr[pm[i]].v[k] - vcm[k];
                         ke = ke + u * u;
                     }
                 acc[0] += ke / (double)(n - 1);
@@ -679,9 +754,20 @@ __device__ __forceinline__ int batch_end(const int *ls, int cb, int cend, int ca
     return ce;
 }
 
+// Dynamic shared memory of the staging area: records, ids / ranks, canonical
+// order, cell of each staged particle.
+template <bool MIXED>
+constexpr size_t stage_bytes()
+{
+    return (size_t)Traits<MIXED>::TP *
+           (sizeof(typename Traits<MIXED>::Rec) + sizeof(int) + sizeof(unsigned short) + 1);
+}
+
 // MANY: the system has a replica with at least CP_NEAR_CAND_MIN colloids
 // (mixed path only): near tests through per-batch candidate colloids.
-template <bool MIXED, bool MANY>
+// FUSED: the fused run's layout (record rows in, record rows and near area
+// out); else the flat layout.
+template <bool MIXED, bool MANY, bool FUSED>
 __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, CellPassArgs a0)
 {
     using Rec = typename Traits<MIXED>::Rec;
@@ -689,7 +775,8 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Rec *srec = reinterpret_cast<Rec *>(smem_raw);
     int *ent = reinterpret_cast<int *>(srec + TP);
-    unsigned char *cellof = reinterpret_cast<unsigned char *>(ent + TP);
+    unsigned short *perm = reinterpret_cast<unsigned short *>(ent + TP);
+    unsigned char *cellof = reinterpret_cast<unsigned char *>(perm + TP);
     __shared__ TileShared<MIXED> T;
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -733,7 +820,7 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
                 grid_shift(rp.seed, a.step + 1u, T.shnf);
                 if (!MIXED) grid_shift(rp.seed, a.step + 1u, T.shn);
             }
-            if (MIXED && (a.opts & CP_NEXT)) {
+            if (MIXED && FUSED && (a.opts & CP_NEXT)) {
                 for (int i = tid; i < 3 * rp.n_col; i += CP_THREADS) {
                     T.nf.Ci[i] = d.colCi[3 * rp.col_off + i];
                     T.nf.Cf[i] = d.colXf[3 * rp.col_off + i];
@@ -748,7 +835,7 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
         const int gc0 = tile * CPT;
         // counts of the tile's cells (consumed: reset for reuse two passes later)
         int x = 0;
-        bool big = false;   // a cell of the tile holds more than bucket_cap
+        bool big = false;   // a cell of the tile holds more than cap
         if (tid < CPT) {
             int n = npref;
             d.count[a.cur][gc0 + tid] = 0;
@@ -778,11 +865,11 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
         if (tid == 0) T.ls[0] = 0;
         __syncthreads();
 
-        // tile base by decoupled look-back (warp 0): the tile's aggregate goes
-        // out now, the scan over predecessors waits until the first batch
-        // needs the base (stage E)
+        // flat write: tile base by decoupled look-back (warp 0); the tile's
+        // aggregate goes out now, the scan over predecessors waits until the
+        // first batch needs the base (stage E)
         if (tid == 0) {
-            tile_publish(d, T.epoch, tile, T.ls[CPT]);
+            if (!FUSED && (a.opts & CP_WRITE)) tile_publish(d, T.epoch, tile, T.ls[CPT]);
             T.next_tile = (int)nt_next;
         }
 
@@ -790,7 +877,8 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
         bool have_base = false, pref = true;
         for (int cb = 0; cb < CPT;) {
             const int ce = batch_end(T.ls, cb, CPT, TP);
-            cells_batch<MIXED, MANY>(d, a, T, tid, cb, ce, srec, ent, cellof, acc, have_base, npref, pref, tile_ovf);
+            cells_batch<MIXED, MANY, FUSED>(d, a, T, tid, cb, ce, srec, ent, perm, cellof, acc, have_base, npref,
+                                            pref, tile_ovf);
             cb = ce;
         }
 
@@ -827,14 +915,10 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
     }
 }
 
-size_t cellpass_smem(bool mixed)
-{
-    if (mixed) return (size_t)Traits<true>::TP * (sizeof(RecM) + sizeof(int) + 1);
-    return (size_t)Traits<false>::TP * (sizeof(RecD) + sizeof(int) + 1);
-}
+size_t cellpass_smem(bool mixed) { return mixed ? stage_bytes<true>() : stage_bytes<false>(); }
 
 // Co-resident CTAs of the persistent cell pass on the current device.
-template <bool MIXED, bool MANY>
+template <bool MIXED, bool MANY, bool FUSED>
 static int cellpass_grid()
 {
     static int cached[64] = {};
@@ -842,30 +926,37 @@ static int cellpass_grid()
     cudaGetDevice(&dev);
     int &g = cached[dev & 63];
     if (g == 0) {
-        const size_t sm = cellpass_smem(MIXED);
+        const size_t sm = stage_bytes<MIXED>();
         int per_sm = 0, n_sm = 0;
-        cudaFuncSetAttribute(k_cellpass<MIXED, MANY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cellpass<MIXED, MANY>, CP_THREADS, sm);
+        cudaFuncSetAttribute(k_cellpass<MIXED, MANY, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cellpass<MIXED, MANY, FUSED>, CP_THREADS, sm);
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
         g = std::max(1, per_sm) * std::max(1, n_sm);
     }
     return g;
 }
 
-template <bool MIXED, bool MANY>
+template <bool MIXED, bool MANY, bool FUSED>
 static void launch_cp(const Dev &d, const CellPassArgs &a, cudaStream_t s)
 {
-    const size_t sm = cellpass_smem(MIXED);
-    const int grid = std::min(d.n_tiles, cellpass_grid<MIXED, MANY>());
-    k_cellpass<MIXED, MANY><<<grid, CP_THREADS, sm, s>>>(d, a);
+    const size_t sm = stage_bytes<MIXED>();
+    const int grid = std::min(d.n_tiles, cellpass_grid<MIXED, MANY, FUSED>());
+    k_cellpass<MIXED, MANY, FUSED><<<grid, CP_THREADS, sm, s>>>(d, a);
 }
 
+// The fused run's pass reads and writes record rows (CP_NEXT, never
+// CP_WRITE); every other pass works on the flat layout (never CP_NEXT).
 void launch_cellpass(bool mixed, const Dev &d, const CellPassArgs &a, cudaStream_t s)
 {
     if (d.n_tiles == 0) return;
-    if (!mixed) launch_cp<false, false>(d, a, s);
-    else if (d.many_col) launch_cp<true, true>(d, a, s);
-    else launch_cp<true, false>(d, a, s);
+    if (a.opts & CP_NEXT) {
+        if (!mixed) launch_cp<false, false, true>(d, a, s);
+        else if (d.many_col) launch_cp<true, true, true>(d, a, s);
+        else launch_cp<true, false, true>(d, a, s);
+    } else {
+        if (!mixed) launch_cp<false, false, false>(d, a, s);
+        else launch_cp<true, false, false>(d, a, s);
+    }
 }
 
 }  // namespace rmpcd

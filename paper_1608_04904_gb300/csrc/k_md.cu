@@ -641,15 +641,14 @@ __device__ void md_body(const Dev &d, MDShared<MIXED> &S, const ReplicaDev &rp, 
     __syncthreads();
     for (int k = first; k < nn; k += stride) {
         W w;
-        const int slot = list[k];
-        w.slot = slot;
+        w.slot = do_bin ? -1 : list[k];   // flat slot: the write-back target of a granular interval
         if constexpr (MIXED) {
-            RecM rec = load_rec(reinterpret_cast<const RecM *>(d.rec[rbuf]) + slot);
+            RecM rec = load_near<RecM>(d, rp, k);
             for (int t = 0; t < 3; ++t) { w.c[t] = cw_get(rec.cw, t); w.o[t] = rec.o[t]; w.v[t] = rec.v[t]; }
             w.fid = rec.fid;
             force_m<REG>(rp, S, w.c, w.o, w.fid, w.f, acc);
         } else {
-            RecD rec = load_rec(reinterpret_cast<const RecD *>(d.rec[rbuf]) + slot);
+            RecD rec = load_near<RecD>(d, rp, k);
             for (int t = 0; t < 3; ++t) { w.x[t] = rec.x[t]; w.v[t] = rec.v[t]; }
             w.fid = rec.fid;
             force_d<REG>(rp, S, w.x, w.fid, w.f, acc);
@@ -731,11 +730,8 @@ __device__ void md_body(const Dev &d, MDShared<MIXED> &S, const ReplicaDev &rp, 
             rec.cw = cw_make(w.c[0], w.c[1], w.c[2]);
             for (int t = 0; t < 3; ++t) { rec.o[t] = w.o[t]; rec.v[t] = w.v[t]; }
             rec.fid = do_bin ? (w.fid | F_PROP) : (w.fid & ~F_PROP);
-            store_rec(reinterpret_cast<RecM *>(d.rec[rbuf]) + w.slot, rec);
-            if (do_bin) {
-                float sf[3] = {(float)sh[0], (float)sh[1], (float)sh[2]};
-                bin_particle(d, bbuf, rp.cell_off + cell_key_m(rp, w.c, w.o, sf), w.slot);
-            }
+            const float sf[3] = {(float)sh[0], (float)sh[1], (float)sh[2]};
+            put_near(d, rbuf, bbuf, do_bin, do_bin ? rp.cell_off + cell_key_m(rp, w.c, w.o, sf) : 0, w.slot, rec);
         } else {
             for (int t = 0; t < 3; ++t) w.v[t] = fma(hdt, w.f[t], w.v[t]);
             wrap_periodic_d(rp, w.x);
@@ -744,8 +740,7 @@ __device__ void md_body(const Dev &d, MDShared<MIXED> &S, const ReplicaDev &rp, 
             rec.fid = do_bin ? (w.fid | F_PROP) : (w.fid & ~F_PROP);
             rec.u0 = 0u;
             rec.u1 = 0.0;
-            store_rec(reinterpret_cast<RecD *>(d.rec[rbuf]) + w.slot, rec);
-            if (do_bin) bin_particle(d, bbuf, rp.cell_off + cell_key_d(rp, w.x, sh), w.slot);
+            put_near(d, rbuf, bbuf, do_bin, do_bin ? rp.cell_off + cell_key_d(rp, w.x, sh) : 0, w.slot, rec);
         }
     }
     __syncwarp();
@@ -1045,9 +1040,8 @@ __global__ void __launch_bounds__(MDW_NT) k_md_wide(Dev d, int r, uint32_t step,
     const int over = first + MDW_PPT * stride;
     WorkM reg[MDW_PPT];
     auto load_w = [&](int k, WorkM &w) {
-        const int slot = list[k];
-        w.slot = slot;
-        const RecM rec = load_rec(reinterpret_cast<const RecM *>(d.rec[rbuf]) + slot);
+        w.slot = do_bin ? -1 : list[k];   // flat slot: the write-back target of a granular interval
+        const RecM rec = load_near<RecM>(d, rp, k);
         for (int t = 0; t < 3; ++t) { w.c[t] = cw_get(rec.cw, t); w.o[t] = rec.o[t]; w.v[t] = rec.v[t]; }
         w.fid = rec.fid;
         wide_candidates(rp, S, w);
@@ -1100,8 +1094,7 @@ __global__ void __launch_bounds__(MDW_NT) k_md_wide(Dev d, int r, uint32_t step,
         rec.cw = cw_make(w.c[0], w.c[1], w.c[2]);
         for (int t = 0; t < 3; ++t) { rec.o[t] = w.o[t]; rec.v[t] = w.v[t]; }
         rec.fid = do_bin ? (w.fid | F_PROP) : (w.fid & ~F_PROP);
-        store_rec(reinterpret_cast<RecM *>(d.rec[rbuf]) + w.slot, rec);
-        if (do_bin) bin_particle(d, bbuf, rp.cell_off + cell_key_m(rp, w.c, w.o, sf), w.slot);
+        put_near(d, rbuf, bbuf, do_bin, do_bin ? rp.cell_off + cell_key_m(rp, w.c, w.o, sf) : 0, w.slot, rec);
     };
 #pragma unroll
     for (int p = 0; p < MDW_PPT; ++p)

@@ -475,8 +475,7 @@ __device__ __forceinline__ void finish_m(const Dev &d, const ReplicaDev &rp, int
     rec.cw = cw_make(c[0], c[1], c[2]);
     for (int t = 0; t < 3; ++t) { rec.o[t] = w.o[t]; rec.v[t] = w.v[t]; }
     rec.fid = do_bin ? (w.fid | F_PROP) : (w.fid & ~F_PROP);
-    store_rec(reinterpret_cast<RecM *>(d.rec[rbuf]) + slot, rec);
-    if (do_bin) bin_particle(d, bbuf, rp.cell_off + cell_key_m(rp, c, w.o, sf), slot);
+    put_near(d, rbuf, bbuf, do_bin, do_bin ? rp.cell_off + cell_key_m(rp, c, w.o, sf) : 0, slot, rec);
 }
 
 // gsm_bytes: room for the lookup grid at the start of the dynamic shared
@@ -562,9 +561,9 @@ __global__ void __launch_bounds__(MDB_NT, 2) k_md_body(Dev d, uint32_t step, int
     for (int i = 0; i < 6; ++i) acc[i] = 0;
     for (int k = tid; k < nn; k += MDB_NT) {
         W w;
-        const int slot = list[k];
+        const int slot = do_bin ? -1 : list[k];   // flat slot: the write-back target of a granular interval
         if constexpr (MIXED) {
-            RecM rec = load_rec(reinterpret_cast<const RecM *>(d.rec[rbuf]) + slot);
+            RecM rec = load_near<RecM>(d, rp, k);
             w.cw = rec.cw;
             w.fid = rec.fid;
             const int c[3] = {cw_get(rec.cw, 0), cw_get(rec.cw, 1), cw_get(rec.cw, 2)};
@@ -573,7 +572,7 @@ __global__ void __launch_bounds__(MDB_NT, 2) k_md_body(Dev d, uint32_t step, int
             for (int t = 0; t < 3; ++t) { w.o[t] = rec.o[t]; w.v[t] = fmaf(rp.hdt_f, f[t], rec.v[t]); }
         } else {
             w.slot = slot;
-            RecD rec = load_rec(reinterpret_cast<const RecD *>(d.rec[rbuf]) + slot);
+            RecD rec = load_near<RecD>(d, rp, k);
             for (int t = 0; t < 3; ++t) { w.x[t] = rec.x[t]; w.v[t] = rec.v[t]; }
             w.fid = rec.fid;
             body_force_d(rp, S, B, w.x, w.fid, w.f, acc);
@@ -617,8 +616,8 @@ __global__ void __launch_bounds__(MDB_NT, 2) k_md_body(Dev d, uint32_t step, int
                     work[k] = w0;
                     if (two) work[k1] = w1;
                 } else {
-                    finish_m(d, rp, rbuf, bbuf, do_bin, sf, w0, list[k]);
-                    if (two) finish_m(d, rp, rbuf, bbuf, do_bin, sf, w1, list[k1]);
+                    finish_m(d, rp, rbuf, bbuf, do_bin, sf, w0, do_bin ? -1 : list[k]);
+                    if (two) finish_m(d, rp, rbuf, bbuf, do_bin, sf, w1, do_bin ? -1 : list[k1]);
                 }
             }
         } else {
@@ -656,8 +655,7 @@ __global__ void __launch_bounds__(MDB_NT, 2) k_md_body(Dev d, uint32_t step, int
             rec.fid = do_bin ? (w.fid | F_PROP) : (w.fid & ~F_PROP);
             rec.u0 = 0u;
             rec.u1 = 0.0;
-            store_rec(reinterpret_cast<RecD *>(d.rec[rbuf]) + w.slot, rec);
-            if (do_bin) bin_particle(d, bbuf, rp.cell_off + cell_key_d(rp, w.x, sh), w.slot);
+            put_near(d, rbuf, bbuf, do_bin, do_bin ? rp.cell_off + cell_key_d(rp, w.x, sh) : 0, w.slot, rec);
         }
     }
     if (tid == 0) {

@@ -498,16 +498,19 @@ __device__ __forceinline__ long long warp_sum64(long long x)
     return ((long long)H << 32) + ((long long)M << 16) + (long long)Lo;
 }
 
+// Near particle k of the replica: its record from the near area; its flat
+// slot (the write-back target of a granular interval) from the near list.
 template <bool MIXED, typename W>
-__device__ __forceinline__ void load_particle(const Dev &d, int slot, int rbuf, W &w)
+__device__ __forceinline__ void load_particle(const Dev &d, const ReplicaDev &rp, int k, const int *list, int do_bin,
+                                              W &w)
 {
-    w.slot = slot;
+    w.slot = do_bin ? -1 : list[k];
     if constexpr (MIXED) {
-        RecM rec = load_rec(reinterpret_cast<const RecM *>(d.rec[rbuf]) + slot);
+        RecM rec = load_near<RecM>(d, rp, k);
         for (int q = 0; q < 3; ++q) { w.c[q] = cw_get(rec.cw, q); w.o[q] = rec.o[q]; w.v[q] = rec.v[q]; }
         w.fid = rec.fid;
     } else {
-        RecD rec = load_rec(reinterpret_cast<const RecD *>(d.rec[rbuf]) + slot);
+        RecD rec = load_near<RecD>(d, rp, k);
         for (int q = 0; q < 3; ++q) { w.x[q] = rec.x[q]; w.v[q] = rec.v[q]; }
         w.fid = rec.fid;
     }
@@ -535,11 +538,8 @@ __device__ __forceinline__ void finish_particle(const Dev &d, const ReplicaDev &
     rec.cw = cw_make(w.c[0], w.c[1], w.c[2]);
     for (int q = 0; q < 3; ++q) { rec.o[q] = w.o[q]; rec.v[q] = w.v[q]; }
     rec.fid = do_bin ? (w.fid | F_PROP) : (w.fid & ~F_PROP);
-    store_rec(reinterpret_cast<RecM *>(d.rec[rbuf]) + w.slot, rec);
-    if (do_bin) {
-        float sf[3] = {(float)sh[0], (float)sh[1], (float)sh[2]};
-        bin_particle(d, bbuf, rp.cell_off + cell_key_m(rp, w.c, w.o, sf), w.slot);
-    }
+    const float sf[3] = {(float)sh[0], (float)sh[1], (float)sh[2]};
+    put_near(d, rbuf, bbuf, do_bin, do_bin ? rp.cell_off + cell_key_m(rp, w.c, w.o, sf) : 0, w.slot, rec);
 }
 
 __device__ __forceinline__ void finish_particle(const Dev &d, const ReplicaDev &rp, FWorkD &w, const double sh[3],
@@ -552,8 +552,7 @@ __device__ __forceinline__ void finish_particle(const Dev &d, const ReplicaDev &
     rec.fid = do_bin ? (w.fid | F_PROP) : (w.fid & ~F_PROP);
     rec.u0 = 0u;
     rec.u1 = 0.0;
-    store_rec(reinterpret_cast<RecD *>(d.rec[rbuf]) + w.slot, rec);
-    if (do_bin) bin_particle(d, bbuf, rp.cell_off + cell_key_d(rp, w.x, sh), w.slot);
+    put_near(d, rbuf, bbuf, do_bin, do_bin ? rp.cell_off + cell_key_d(rp, w.x, sh) : 0, w.slot, rec);
 }
 
 // --- the cluster exchange of the force partials -------------------------------
@@ -765,10 +764,10 @@ __global__ void __launch_bounds__(MDF_NT, 1) k_md_fast(Dev d, uint32_t step, int
     W reg[MDF_PPT];
 #pragma unroll
     for (int p = 0; p < MDF_PPT; ++p)
-        if (first + p * stride < nn) load_particle<MIXED>(d, list[first + p * stride], rbuf, reg[p]);
+        if (first + p * stride < nn) load_particle<MIXED>(d, rp, first + p * stride, list, do_bin, reg[p]);
     for (int k = over; k < nn; k += stride) {
         W w;
-        load_particle<MIXED>(d, list[k], rbuf, w);
+        load_particle<MIXED>(d, rp, k, list, do_bin, w);
         work[k] = w;
     }
 

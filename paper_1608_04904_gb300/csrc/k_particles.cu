@@ -108,13 +108,29 @@ __global__ void k_get_state_d(Dev d, int r, int n, int rbuf, double *x, double *
 }
 
 // ---------------------------------------------------------------------------
-// Particle pass over every slot.
-//   PM_STREAM: near-colloid particles join the near list, the others fly over
-//              tau and are stored (granular interval motion).
-//   PM_BIN:    bin the stored positions on the grid of collision `step`.
-//   PM_PRIME:  like PM_STREAM, but far particles are binned at their flown
-//              position and stored unmoved (first interval of a fused run).
+// Particle pass over every flat slot.
+//   PM_STREAM: near-colloid particles join the near list (slot) and the near
+//              area (record), the others fly over tau and are stored
+//              (granular interval motion).
+//   PM_BIN:    bin the stored positions on the grid of collision `step`
+//              (index buckets of the flat layout).
+//   PM_PRIME:  first interval of a fused run: a far particle's record, unmoved,
+//              goes into the row of the cell of its flown position; near
+//              particles go to the near area for the MD kernel.
 // ---------------------------------------------------------------------------
+// Near particle: its slot into the near list, its record into the near area.
+template <class Rec>
+__device__ __forceinline__ void add_near(const Dev &d, int r, const ReplicaDev &rp, int slot, const Rec &rec)
+{
+    const int k = atomicAdd(&d.near_count[r], 1);
+    if (k < rp.n_part) {
+        d.near_list[rp.part_off + k] = slot;
+        store_rec(reinterpret_cast<Rec *>(d.near_rec) + rp.part_off + k, rec);
+    } else {
+        atomicOr(&d.err[ERR_BOUNDS], 1u);
+    }
+}
+
 template <bool MIXED>
 __global__ void k_particles(Dev d, int mode, uint32_t step, int rbuf, int bbuf)
 {
@@ -136,9 +152,7 @@ __global__ void k_particles(Dev d, int mode, uint32_t step, int rbuf, int bbuf)
         }
         if (rp.n_col > 0 && near_test_m(rp, rp.n_col, d.colCi + 3 * rp.col_off, d.colXf + 3 * rp.col_off,
                                         d.colRb_f + rp.col_off, c, rec.o, rec.v)) {
-            int k = atomicAdd(&d.near_count[r], 1);
-            if (k < rp.n_part) d.near_list[rp.part_off + k] = i;
-            else atomicOr(&d.err[ERR_BOUNDS], 1u);
+            add_near(d, r, rp, i, rec);
             return;
         }
         float o[3] = {rec.o[0], rec.o[1], rec.o[2]};
@@ -150,7 +164,7 @@ __global__ void k_particles(Dev d, int mode, uint32_t step, int rbuf, int bbuf)
             store_rec(recs + i, rec);
         } else {
             float sf[3] = {(float)s[0], (float)s[1], (float)s[2]};
-            bin_particle(d, bbuf, rp.cell_off + cell_key_m(rp, c, o, sf), i);
+            bin_record(d, bbuf, rp.cell_off + cell_key_m(rp, c, o, sf), rec);
         }
     } else {
         RecD *recs = reinterpret_cast<RecD *>(d.rec[rbuf]);
@@ -160,9 +174,7 @@ __global__ void k_particles(Dev d, int mode, uint32_t step, int rbuf, int bbuf)
             return;
         }
         if (rp.n_col > 0 && near_test_d(d, rp, rec.x, rec.v)) {
-            int k = atomicAdd(&d.near_count[r], 1);
-            if (k < rp.n_part) d.near_list[rp.part_off + k] = i;
-            else atomicOr(&d.err[ERR_BOUNDS], 1u);
+            add_near(d, r, rp, i, rec);
             return;
         }
         double x[3] = {rec.x[0], rec.x[1], rec.x[2]};
@@ -172,9 +184,82 @@ __global__ void k_particles(Dev d, int mode, uint32_t step, int rbuf, int bbuf)
             for (int k = 0; k < 3; ++k) { rec.x[k] = x[k]; rec.v[k] = v[k]; }
             store_rec(recs + i, rec);
         } else {
-            bin_particle(d, bbuf, rp.cell_off + cell_key_d(rp, x, s), i);
+            bin_record(d, bbuf, rp.cell_off + cell_key_d(rp, x, s), rec);
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Flatten a fused run's state: every record of the rows of buffer b, of its
+// overflow records and of the near area goes to the next free flat slot of its
+// replica (in no particular order; a sorting pass follows).  fill[r] counts the
+// records placed; it must end at n_part.
+// ---------------------------------------------------------------------------
+template <class Rec>
+__device__ __forceinline__ void flat_put(const Dev &d, int r, int fbuf, int *fill, const Rec &rec)
+{
+    const ReplicaDev &rp = d.rep[r];
+    const int k = atomicAdd(&fill[r], 1);
+    if (k < rp.n_part) store_rec(reinterpret_cast<Rec *>(d.rec[fbuf]) + rp.part_off + k, rec);
+    else atomicOr(&d.err[ERR_BOUNDS], 1u);
+}
+
+template <class Rec>
+__global__ void k_flatten_rows(Dev d, int b, int fbuf, int *fill)
+{
+    const long long nc = (long long)d.n_tiles * CPT;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < nc; g += (long long)gridDim.x * blockDim.x) {
+        const int n = min(d.count[b][g], d.cap);
+        if (n <= 0) continue;
+        const int r = d.tile_rep[g / CPT];
+        const Rec *row = reinterpret_cast<const Rec *>(d.brec[b]) + g * d.cap;
+        for (int i = 0; i < n; ++i) flat_put(d, r, fbuf, fill, load_rec(row + i));
+    }
+}
+
+template <class Rec>
+__global__ void k_flatten_ovf(Dev d, int b, int fbuf, int *fill)
+{
+    const int no = min((int)d.ovf_n[b], d.ovf_cap);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < no; k += gridDim.x * blockDim.x) {
+        const int2 q = d.ovf[b][k];
+        const long long nc = (long long)d.n_tiles * CPT;
+        if (q.x < 0 || q.x >= nc || q.y < 0 || q.y >= d.ovf_cap) { atomicOr(&d.err[ERR_BOUNDS], 1u); continue; }
+        flat_put(d, d.tile_rep[q.x / CPT], fbuf, fill, load_rec(reinterpret_cast<const Rec *>(d.orec[b]) + q.y));
+    }
+}
+
+template <class Rec>
+__global__ void k_flatten_near(Dev d, int fbuf, int *fill)
+{
+    const int r = blockIdx.y;
+    const ReplicaDev &rp = d.rep[r];
+    const int nn = min(d.near_count[r], rp.n_part);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nn; k += gridDim.x * blockDim.x)
+        flat_put(d, r, fbuf, fill, load_near<Rec>(d, rp, k));
+}
+
+__global__ void k_flatten_check(Dev d, const int *fill)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < d.n_rep; r += gridDim.x * blockDim.x)
+        if (fill[r] != d.rep[r].n_part) atomicOr(&d.err[ERR_BOUNDS], 1u);
+}
+
+void launch_flatten(bool mixed, const Dev &d, int b, int fbuf, int *fill, cudaStream_t s)
+{
+    const long long nc = (long long)d.n_tiles * CPT;
+    const int nb = (int)std::max<long long>(1, std::min<long long>((nc + 255) / 256, 8192));
+    const dim3 gn(64, (unsigned)std::max(1, d.n_rep));
+    if (mixed) {
+        k_flatten_rows<RecM><<<nb, 256, 0, s>>>(d, b, fbuf, fill);
+        k_flatten_ovf<RecM><<<64, 256, 0, s>>>(d, b, fbuf, fill);
+        k_flatten_near<RecM><<<gn, 256, 0, s>>>(d, fbuf, fill);
+    } else {
+        k_flatten_rows<RecD><<<nb, 256, 0, s>>>(d, b, fbuf, fill);
+        k_flatten_ovf<RecD><<<64, 256, 0, s>>>(d, b, fbuf, fill);
+        k_flatten_near<RecD><<<gn, 256, 0, s>>>(d, fbuf, fill);
+    }
+    k_flatten_check<<<1, 256, 0, s>>>(d, fill);
 }
 
 // Per replica: sum the per-tile partial observables in tile order.

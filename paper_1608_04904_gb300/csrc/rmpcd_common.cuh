@@ -127,15 +127,30 @@ struct MdWideGlobal {
 };
 
 // All device pointers of a system (passed by value to every kernel).
+//
+// Two layouts hold the solvent.  The flat one (rec[]) keeps every replica's
+// records in slots [part_off, part_off + n_part), sorted by the cells of a
+// collision after a sorting pass; the granular calls, the state transfers and
+// the observables work on it, through index buckets (bucket[]: slot numbers
+// per cell).  The fused run keeps the records themselves in per-cell rows
+// (brec[]: row `cell` holds that cell's records at [cell * cap, cell * cap +
+// count)), so that a collision reads each cell's particles contiguously and
+// writes each particle's record straight into the row of its next cell; the
+// particles near a colloid wait in near_rec for the MD kernel, which then bins
+// them into the rows.  bucket[b] and brec[b] share memory (one layout is in
+// use at a time).
 struct Dev {
     const ReplicaDev *rep;
     const int *tile_rep;         // tile -> replica
-    void *rec[2];                // solvent records, double buffered
+    void *rec[2];                // flat solvent records, double buffered
     int *count[2];               // particles per cell, double buffered
-    int *bucket[2];              // [cell * cap + rank] -> storage slot
-    int2 *ovf[2];                // entries past bucket_cap: (cell, storage slot), any order
+    int *bucket[2];              // flat layout: [cell * cap + rank] -> storage slot
+    void *brec[2];               // fused run: [cell * cap + rank] -> record (same memory as bucket[b])
+    int2 *ovf[2];                // entries past cap: (cell, slot) (flat layout) or (cell, index into orec)
+    void *orec[2];               // fused run: records of the overflow entries
     unsigned int *ovf_n;         // [2]: entries appended to ovf[b] (reset by the pass that consumes b)
-    int *near_list;              // per replica region [part_off, part_off + n_part)
+    void *near_rec;              // records of the near particles, per replica [part_off, part_off + near_count)
+    int *near_list;              // per replica: flat slot of each near particle (granular interval)
     int *near_count;             // [n_rep]
     unsigned long long *tile_state;  // decoupled look-back, one word per tile
     unsigned int *ticket;        // [4]: tile tickets, finished CTAs (per launch parity)
@@ -567,6 +582,47 @@ __device__ __forceinline__ void bin_store(const Dev &d, int buf, int gcell, int 
 __device__ __forceinline__ void bin_particle(const Dev &d, int buf, int gcell, int slot)
 {
     bin_store(d, buf, gcell, atomicAdd(&d.count[buf][gcell], 1), slot);
+}
+
+// Fused run: the record of a particle that takes place r of cell gcell (its
+// count before this particle) into the cell's row, or past cap into the
+// overflow records.  A full overflow list raises ERR_OVERFLOW.
+template <class Rec>
+__device__ __forceinline__ void bin_record_at(const Dev &d, int buf, int gcell, int r, const Rec &rec)
+{
+    if (r < d.cap) {
+        store_rec(reinterpret_cast<Rec *>(d.brec[buf]) + (long long)gcell * d.cap + r, rec);
+    } else {
+        const unsigned k = atomicAdd(&d.ovf_n[buf], 1u);
+        if (k < (unsigned)d.ovf_cap) {
+            store_rec(reinterpret_cast<Rec *>(d.orec[buf]) + k, rec);
+            d.ovf[buf][k] = make_int2(gcell, (int)k);
+        } else {
+            atomicMax(&d.err[ERR_OVERFLOW], (unsigned int)(r + 1));
+        }
+    }
+}
+template <class Rec>
+__device__ __forceinline__ void bin_record(const Dev &d, int buf, int gcell, const Rec &rec)
+{
+    bin_record_at(d, buf, gcell, atomicAdd(&d.count[buf][gcell], 1), rec);
+}
+
+// The record of near particle k of a replica (its copy in the near area).
+template <class Rec>
+__device__ __forceinline__ Rec load_near(const Dev &d, const ReplicaDev &rp, int k)
+{
+    return load_rec(reinterpret_cast<const Rec *>(d.near_rec) + rp.part_off + k);
+}
+
+// A near particle after its interval: binned into the rows of the collision
+// ahead (fused run: do_bin) or written back to its flat slot (granular call).
+template <class Rec>
+__device__ __forceinline__ void put_near(const Dev &d, int rbuf, int bbuf, int do_bin, int gcell, int slot,
+                                         const Rec &rec)
+{
+    if (do_bin) bin_record(d, bbuf, gcell, rec);
+    else store_rec(reinterpret_cast<Rec *>(d.rec[rbuf]) + slot, rec);
 }
 
 // Near-colloid test of §1.4's Verlet-list radius: may this particle come

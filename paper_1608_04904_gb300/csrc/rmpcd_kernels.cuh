@@ -62,6 +62,10 @@ void launch_set_state(bool mixed, const Dev &d, int replica, int n, const double
 void launch_get_state(bool mixed, const Dev &d, int replica, int n, int rbuf, double *x, double *v, uint8_t *flags,
                       uint32_t *id, int32_t *cell, int has_sort, uint32_t sort_step, cudaStream_t s);
 void launch_obs_reduce(const Dev &d, cudaStream_t s);
+// Gather a fused run's records (rows and overflow of buffer b, near area) into
+// the flat slots of buffer fbuf, unsorted; fill[n_rep] zeroed by the caller
+// counts them (4 launches).
+void launch_flatten(bool mixed, const Dev &d, int b, int fbuf, int *fill, cudaStream_t s);
 // Slab profile of one replica (n particles) into acc[n_bins * PROF_FIELDS] (zeroed by the caller).
 void launch_profile(bool mixed, const Dev &d, int replica, int n, int rbuf, int axis, int n_bins,
                     unsigned long long *acc, cudaStream_t s);

@@ -317,23 +317,24 @@ def test_one_crowded_cell(precision):
 
 @pytest.mark.parametrize("precision", PRECS)
 def test_overflow_list_keeps_fused_steps_exact(precision):
-    """A bucket row of 8 at density 10: about a third of the cells spill into
+    """A cell row of 16 at density 10: a few per cent of the cells spill into
     the overflow list every collision, and a crowd of 300 particles puts a few
-    cells far past the row.  The cell pass reads the spilled entries back in
+    cells far past the row.  The cell pass reads the spilled records back in
     canonical order: fused steps equal the oracle (fp64 bit for bit) and no
     EOVERFLOW is raised."""
     cfg, col, bonds, x, v, fl = _dimer(precision, bulk_rate=0.05)
     x = x.copy()
     rng = np.random.Generator(np.random.PCG64(12))
     x[:300] = 1.25 + np.floor(rng.uniform(0.0, 0.5, (300, 3)) * 2**24) * 2.0**-24
-    g = gpu(cfg, x, v, fl, col, bonds, precision=precision, cap=8, step=5)
+    g = gpu(cfg, x, v, fl, col, bonds, precision=precision, cap=16, step=5)
     o = oracle(cfg, x, v, fl, col, bonds, step=5)
-    for _ in range(3):
+    for k in range(3):
         g.step(1)
         o.step(1)
+        if k == 0:
+            assert o.count.max() > 32 and (o.count > 16).sum() > 10
         _compare_step(cfg, g.get_state(), o, precision)
-    assert o.count.max() > 8 and (o.count > 8).mean() > 0.1
-    assert g.bucket_cap() == 8
+    assert g.bucket_cap() == 16
 
 
 def test_bucket_overflow_is_reported():

@@ -1,4 +1,5 @@
-"""Pins of the oracle's grid shift, cell keys and stable counting sort (§1.4)."""
+"""Pins of the oracle's grid shift, cell keys and counting sort (§1.4): cells
+in key order, particles of a cell in id order."""
 import numpy as np
 
 from paper_1608_04904_gb300 import synth
@@ -51,15 +52,21 @@ def test_cell_keys_with_walls(orc):
         assert np.array_equal(orc.cell_keys(cfg, x, s), _brute_cell(x, s, cfg["L"], True))
 
 
-def test_counting_sort_is_stable_sort(orc):
+def test_counting_sort_orders_by_cell_then_id(orc):
+    """The order is lexicographic in (cell key, particle id), whatever order
+    the particles come in (ids unique, not necessarily 0..n-1)."""
     rng = np.random.Generator(np.random.PCG64(5))
     for ncells, n in [(1, 50), (7, 0), (64, 1000), (1000, 300)]:
         key = rng.integers(0, ncells, size=n).astype(np.int32)
-        perm, count, start = orc.counting_sort(key, ncells)
-        assert np.array_equal(perm, np.argsort(key, kind="stable"))
+        ids = rng.permutation(5 * n)[:n].astype(np.uint32)
+        perm, count, start = orc.counting_sort(key, ncells, ids)
+        assert np.array_equal(perm, np.lexsort((ids, key)))
         assert np.array_equal(count, np.bincount(key, minlength=ncells))
         assert np.array_equal(start, np.concatenate([[0], np.cumsum(count)[:-1]]) if ncells else start)
         assert count.sum() == n
+        # without ids the index is the id: a stable sort by key
+        perm0, _, _ = orc.counting_sort(key, ncells)
+        assert np.array_equal(perm0, np.argsort(key, kind="stable"))
 
 
 def test_shift_and_sort_reorders_state(orc):
@@ -68,7 +75,7 @@ def test_shift_and_sort_reorders_state(orc):
     s = orc.OracleSystem(cfg, x, v, fl)
     s.shift_and_sort()
     key = orc.cell_keys(cfg, x, orc.grid_shift(cfg["seed"], 0))
-    order = np.argsort(key, kind="stable")
+    order = np.argsort(key, kind="stable")   # ids are 0..n-1 in input order
     assert np.array_equal(s.id, order)
     assert np.array_equal(s.x, x[order])
     assert np.array_equal(s.flags, fl[order])
