@@ -143,15 +143,18 @@ def _dimer_replica(**kw):
 
 def test_workspace_size_counts_the_buffers_without_a_gpu(api):
     """rmpcd_workspace_size makes no CUDA call.  Its answer grows with the
-    bucket width by exactly the two bucket arrays (cells x width x 4 bytes
-    each, rounded to 256), with the particle count by at least the two record
-    buffers, and the FP64 records (64 B) need more than the mixed ones (32 B)."""
+    bucket width by exactly the two arrays of cell rows (cells x width x one
+    record each -- 32 bytes mixed, 64 FP64 --, rounded to 256), with the
+    particle count by at least the two record buffers, and the FP64 records
+    (64 B) need more than the mixed ones (32 B)."""
     rep = _dimer_replica()
     cells = 32 ** 3
     r256 = lambda b: (b + 255) // 256 * 256
     a = api.workspace_size([rep], "mixed", 48)
     b = api.workspace_size([rep], "mixed", 64)
-    assert b - a == 2 * (r256(cells * 64 * 4) - r256(cells * 48 * 4))
+    assert b - a == 2 * (r256(cells * 64 * 32) - r256(cells * 48 * 32))
+    a64 = api.workspace_size([rep], "fp64", 48)
+    assert api.workspace_size([rep], "fp64", 64) - a64 == 2 * (r256(cells * 64 * 64) - r256(cells * 48 * 64))
     big = dict(rep, n=rep["n"] + 8192)
     assert api.workspace_size([big], "mixed", 48) - a >= 2 * 32 * 8192
     assert api.workspace_size([rep], "fp64", 48) - a >= 2 * 32 * rep["n"]
