@@ -450,6 +450,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--bucket-cap", type=int, default=None,
+                    help="cell row width (default: the automatic width)")
     ap.add_argument("--replicas", type=int, default=None,
                     help="batch256 only: keep the first N replicas (a smaller case for profiling)")
     args = ap.parse_args()
@@ -475,6 +477,9 @@ def main():
     api.load()
 
     reps, desc = workload(args.workload, args.precision, seed_offset=rank, n_replicas=args.replicas)
+    if args.bucket_cap is not None:
+        for rep in reps:
+            rep[0]["bucket_cap"] = args.bucket_cap
     states = [initial_state(r) for r in reps]
     cfg = reps[0][0]
     n = sum(len(st[0]) for st in states)

@@ -319,8 +319,10 @@ rmpcd_status rmpcd_get_tuning(const rmpcd_system *sys, int32_t *md_cluster, int3
  * directly.  Results are identical either way.  Errors: EINVAL. */
 rmpcd_status rmpcd_set_graphs(rmpcd_system *sys, int32_t on);
 
-/* Test hook of the bounded waits (the paper has no counterpart).  The cell
- * pass finds each tile's first output slot by waiting for its predecessors'
+/* Test hook of the bounded waits (the paper has no counterpart).  A sorting
+ * pass of the flat layout (the granular calls, and the flattening of a fused
+ * run's state that rmpcd_get_state, rmpcd_observables and rmpcd_profile do)
+ * finds each tile's first output slot by waiting for its predecessors'
  * published prefixes; that wait gives up after max_polls polls (0 = the
  * default, 4,194,304: well over a second), latches RMPCD_ETIMEOUT (reported by
  * the next call that checks errors, e.g. rmpcd_sync) and leaves the tile's

@@ -152,6 +152,14 @@ __device__ __forceinline__ void cp_async_rec(Rec *dst, const Rec *src)
         cp_async16(reinterpret_cast<char *>(dst) + 16 * q, reinterpret_cast<const char *>(src) + 16 * q);
 }
 
+// Staging place of the i-th particle of a cell of n in canonical order
+// (clamped to the cell: a state with colliding ids leaves gaps in perm).
+__device__ __forceinline__ int canon(const unsigned short *pm, int i, int n)
+{
+    const int q = pm[i];
+    return q < n ? q : n - 1;
+}
+
 // Per-tile state shared by the threads of one CTA.
 template <bool MIXED>
 struct TileShared {
@@ -182,7 +190,7 @@ __device__ __forceinline__ void mpcat_cell(const ReplicaDev &rp, uint32_t step, 
 {
     double sum[3] = {0.0, 0.0, 0.0};
     for (int i = 0; i < n; ++i)
-        for (int k = 0; k < 3; ++k) sum[k] = sum[k] + (double)v[pm[i]].v[k];
+        for (int k = 0; k < 3; ++k) sum[k] = sum[k] + (double)v[canon(pm, i, n)].v[k];
     double vcm[3];
     if (virt) {
         const int nv = rp.rho_wall - n;
@@ -206,13 +214,13 @@ __device__ __forceinline__ void mpcat_cell(const ReplicaDev &rp, uint32_t step, 
         const R gg[3] = {g0, g1, g2};
         for (int k = 0; k < 3; ++k) {
             const R xi = sd * gg[k];
-            v[pm[i]].v[k] = xi;
+            v[canon(pm, i, n)].v[k] = xi;
             xs[k] = xs[k] + (double)xi;
         }
     }
     for (int k = 0; k < 3; ++k) xs[k] = xs[k] / (double)n;
     for (int i = 0; i < n; ++i)
-        for (int k = 0; k < 3; ++k) v[pm[i]].v[k] = (R)(vcm[k] + ((double)v[pm[i]].v[k] - xs[k]));
+        for (int k = 0; k < 3; ++k) v[canon(pm, i, n)].v[k] = (R)(vcm[k] + ((double)v[canon(pm, i, n)].v[k] - xs[k]));
 }
 
 // Stage D, one thread per cell, particles summed in canonical order (the
@@ -254,7 +262,7 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
         R sum[3] = {R(0), R(0), R(0)};
         if (slab < 0 && (coll || nearq))
             for (int i = 0; i < n; ++i) {
-                const int q = pm[i];
+                const int q = canon(pm, i, n);
                 for (int k = 0; k < 3; ++k) sum[k] = sum[k] + cr[q].v[k];
             }
         int nbB = -1;   // B count, when the near bound's loop has taken it
@@ -333,7 +341,7 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
                     // the pick-th B particle of the cell in canonical order
                     const int pick = (int)(((unsigned long long)w.y * (unsigned long long)nbB) >> 32);
                     for (int i = 0, seen = 0; i < n; ++i) {
-                        const int q = pm[i];
+                        const int q = canon(pm, i, n);
                         if (cr[q].fid & F_B) {
                             if (seen == pick) { T.react[c] = lo + q; break; }
                             ++seen;
@@ -470,7 +478,7 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
             if (j < nb) {
                 const int c = cb + cellof[j];
                 const int r = j + pofs - T.ls[c];
-                if (r < d.cap) cp_async_rec(srec + j, rows + (long long)(gc0 + c) * d.cap + r);
+                if (r < d.cap) cp_async_rec(srec + j, rows + row_index(d, gc0 + c, r));
             }
         }
         if (ovf) {
@@ -501,7 +509,7 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
             if (j < nb) {
                 const int c = cb + cellof[j];
                 const int r = j + pofs - T.ls[c];
-                e[u] = r < d.cap ? d.bucket[a.cur][(long long)(gc0 + c) * d.cap + r] : -1;
+                e[u] = r < d.cap ? d.bucket[a.cur][row_index(d, gc0 + c, r)] : -1;
             }
         }
 #pragma unroll
@@ -548,9 +556,10 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
         if (j < nb) ent[j] = (int)(srec[j].fid & ID_MASK);
     }
     __syncthreads();
-    // the canonical place of every particle in its cell: rank by id (ties,
-    // which valid states do not have, by staging place, so that the ranks
-    // always form a permutation)
+    // the canonical place of every particle in its cell: its rank by id (ids
+    // are unique in a valid state; should two collide, two ranks coincide
+    // and the reads of perm below clamp to the cell, so every access stays
+    // in the staging area and the latched error reports the state)
     int rk[K];
 #pragma unroll
     for (int u = 0; u < K; ++u) {
@@ -558,14 +567,11 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
         if (j < nb) {
             const int c = cb + cellof[j];
             const int lo = T.ls[c] - pofs, n = T.cnt[c];
-            const int id = ent[j], me = j - lo;
+            const int id = ent[j];
             int rank = 0;
-            for (int k = 0; k < n; ++k) {
-                const int o = ent[lo + k];
-                rank += (o < id || (o == id && k < me)) ? 1 : 0;
-            }
+            for (int k = 0; k < n; ++k) rank += ent[lo + k] < id ? 1 : 0;
             rk[u] = rank;
-            perm[lo + rank] = (unsigned short)me;
+            perm[lo + rank] = (unsigned short)(j - lo);
         }
     }
     if constexpr (!FUSED) {
@@ -716,7 +722,7 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
             double ke2 = 0.0;
             int nbB = 0;
             for (int i = 0; i < n; ++i) {
-                const Rec &ri = cr[pm[i]];
+                const Rec &ri = cr[canon(pm, i, n)];
                 for (int k = 0; k < 3; ++k) {
                     const double vk = (double)ri.v[k];
                     sum[k] = sum[k] + vk;
@@ -729,7 +735,7 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
                 double ke = 0.0;
                 for (int i = 0; i < n; ++i)
                     for (int k = 0; k < 3; ++k) {
-                        const double u = (double)cr[pm[i]].v[k] - vcm[k];
+                        const double u = (double)cr[canon(pm, i, n)].v[k] - vcm[k];
                         ke = ke + u * u;
                     }
                 acc[0] += ke / (double)(n - 1);

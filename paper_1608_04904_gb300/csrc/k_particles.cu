@@ -212,8 +212,8 @@ __global__ void k_flatten_rows(Dev d, int b, int fbuf, int *fill)
         const int n = min(d.count[b][g], d.cap);
         if (n <= 0) continue;
         const int r = d.tile_rep[g / CPT];
-        const Rec *row = reinterpret_cast<const Rec *>(d.brec[b]) + g * d.cap;
-        for (int i = 0; i < n; ++i) flat_put(d, r, fbuf, fill, load_rec(row + i));
+        const Rec *rows = reinterpret_cast<const Rec *>(d.brec[b]);
+        for (int i = 0; i < n; ++i) flat_put(d, r, fbuf, fill, load_rec(rows + row_index(d, g, i)));
     }
 }
 

@@ -564,6 +564,18 @@ __device__ __forceinline__ void wrapped_colloid(const ReplicaDev &rp, const doub
 }
 
 // ---------------------------------------------------------------------------
+// Cell rows: place r of global cell g is element g * cap + r.  A cell's
+// records are contiguous, so the consecutive particles a warp stages (a few
+// cells' worth) are a few contiguous runs: each load instruction touches few
+// lines.  (Measured: a plane-major order within a tile, place r of a tile's
+// cells contiguous, was 5 % slower for the uncoalesced loads it makes.)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long row_index(const Dev &d, long long g, int r)
+{
+    return g * d.cap + r;
+}
+
+// ---------------------------------------------------------------------------
 // Bins: one particle into its cell.  The first bucket_cap entries of a cell go
 // to its bucket row; the rest are appended to the buffer's overflow list,
 // which the cell pass reads for the cells that need it.  A full overflow list
@@ -572,7 +584,7 @@ __device__ __forceinline__ void wrapped_colloid(const ReplicaDev &rp, const doub
 __device__ __forceinline__ void bin_store(const Dev &d, int buf, int gcell, int r, int slot)
 {
     if (r < d.cap) {
-        d.bucket[buf][(long long)gcell * d.cap + r] = slot;
+        d.bucket[buf][row_index(d, gcell, r)] = slot;
     } else {
         const unsigned k = atomicAdd(&d.ovf_n[buf], 1u);
         if (k < (unsigned)d.ovf_cap) d.ovf[buf][k] = make_int2(gcell, slot);
@@ -591,7 +603,7 @@ template <class Rec>
 __device__ __forceinline__ void bin_record_at(const Dev &d, int buf, int gcell, int r, const Rec &rec)
 {
     if (r < d.cap) {
-        store_rec(reinterpret_cast<Rec *>(d.brec[buf]) + (long long)gcell * d.cap + r, rec);
+        store_rec(reinterpret_cast<Rec *>(d.brec[buf]) + row_index(d, gcell, r), rec);
     } else {
         const unsigned k = atomicAdd(&d.ovf_n[buf], 1u);
         if (k < (unsigned)d.ovf_cap) {

@@ -1,7 +1,9 @@
 """The error path of the bounded waits, exercised without any GPU fault.
 
-The cell pass finds each tile's output base by waiting for its predecessors'
-published prefixes (decoupled look-back); that wait is bounded.  The test
+A sorting pass of the flat layout (the granular calls, and the flattening of
+a fused run's state for state transfer and observables) finds each tile's
+output base by waiting for its predecessors' published prefixes (decoupled
+look-back); that wait is bounded.  The test
 hook rmpcd_set_wait_test(stall) makes every predecessor read as not ready --
 a flag that nothing sets -- so each wait runs out after a few polls: the
 kernel must return, latch RMPCD_ETIMEOUT for the host, write nothing out of
@@ -37,7 +39,8 @@ def test_lookback_wait_runs_out_and_reports_etimeout(precision):
     s.step(1)
     s.sync()                                   # a normal interval: no error
     s.set_wait_test(max_polls=1000, stall=True)
-    s.step(2)                                  # every tile but the first gives up
+    s.step(1)
+    s.shift_and_sort()                         # flat sorting passes: every tile but the first gives up
     with pytest.raises(api.RmpcdError) as e:
         s.sync()
     assert e.value.code == "ETIMEOUT", str(e.value)
@@ -62,5 +65,6 @@ def test_wait_limit_rejects_negative():
     assert e.value.code == "EINVAL"
     s.set_wait_test(max_polls=0, stall=False)    # back to the default: runs normally
     s.step(2)
+    s.shift_and_sort()
     s.sync()
     s.close()
