@@ -73,6 +73,11 @@ typedef struct {
     double slab_x0[4], slab_x1[4], slab_kT[4];  /* MPC-AT slabs: cells with x0 <= cx < x1 */
     double cc_eps, cc_sigma, cc_rc;             /* colloid-colloid LJ; cc_rc = 0 disables  */
     uint64_t seed;         /* key of the counter-based RNG                               */
+    int32_t res_y[4];      /* species reservoirs of the chemotactic set-up (§1.5
+                            * chemotactic_cell): after every collision the particles of
+                            * a cell whose y column on the collision grid lies in
+                            * [res_y[0], res_y[1]) become A, in [res_y[2], res_y[3]) B
+                            * (tags cleared); empty ranges (all 0) disable it          */
 } rmpcd_params;
 
 /* One colloid (§1.1: mass, position, velocity; §1.4: WCA sigma and per-species
@@ -223,8 +228,8 @@ rmpcd_status rmpcd_get_step(const rmpcd_system *sys, uint32_t *step);
  * Does not advance the step counter. */
 rmpcd_status rmpcd_stream(rmpcd_system *sys);
 
-/* Random grid shift of the current step, cell keys and stable counting sort:
- * storage becomes sorted by cell, ties kept in previous storage order. */
+/* Random grid shift of the current step, cell keys and counting sort: storage
+ * becomes sorted by cell, the particles of a cell in increasing id order. */
 rmpcd_status rmpcd_shift_and_sort(rmpcd_system *sys);
 
 /* Collision on the grid of the current step: SRD rotation by alpha about a
@@ -232,8 +237,9 @@ rmpcd_status rmpcd_shift_and_sort(rmpcd_system *sys);
  * Requires the state sorted on that grid (rmpcd_shift_and_sort). */
 rmpcd_status rmpcd_collide(rmpcd_system *sys);
 
-/* Bulk B -> A reaction per cell (one B with probability 1 - exp(-k N_B tau)).
- * Requires the state sorted on the current grid. */
+/* Bulk B -> A reaction per cell (one B with probability 1 - exp(-k N_B tau)),
+ * then the species reservoirs (res_y) if any.  Requires the state sorted on
+ * the current grid. */
 rmpcd_status rmpcd_react(rmpcd_system *sys);
 
 /* n_intervals full collision intervals (motion, shift, sort, collision,

@@ -35,6 +35,7 @@ class Params(C.Structure):
         ("bulk_rate", C.c_double), ("cat_prob", C.c_double), ("skin", C.c_double),
         ("slab_x0", C.c_double * 4), ("slab_x1", C.c_double * 4), ("slab_kT", C.c_double * 4),
         ("cc_eps", C.c_double), ("cc_sigma", C.c_double), ("cc_rc", C.c_double), ("seed", C.c_uint64),
+        ("res_y", C.c_int32 * 4),
     ]
 
 
@@ -165,6 +166,10 @@ def make_params(cfg: dict, n_solvent: int, n_colloids: int = 0, n_bonds: int = 0
     if cc:
         p.cc_eps, p.cc_sigma, p.cc_rc = cc
     p.seed = int(cfg["seed"]) & 0xFFFFFFFFFFFFFFFF
+    res = cfg.get("reservoirs")
+    if res:
+        (ya0, ya1), (yb0, yb1) = res
+        p.res_y[:] = [int(ya0), int(ya1), int(yb0), int(yb1)]
     return p
 
 

@@ -269,6 +269,7 @@ static void fill_rep(ReplicaDev &rp, const rmpcd_params &p)
     rp.cc_eps = p.cc_eps;
     rp.cc_sigma = p.cc_sigma;
     rp.cc_rc = p.cc_rc;
+    for (int k = 0; k < 4; ++k) rp.res_y[k] = p.res_y[k];
     rp.tau_f = (float)rp.tau;
     rp.dt_f = (float)rp.dt;
     rp.hdt_f = (float)rp.hdt;
@@ -311,6 +312,10 @@ static rmpcd_status validate(const rmpcd_params &p, int r, const rmpcd_colloid *
         if (b.a < 0 || b.b < 0 || b.a >= p.n_colloids || b.b >= p.n_colloids || b.a == b.b || !(b.d > 0.0))
             return fail(nullptr, RMPCD_EINVAL, "replica %d bond %d invalid", r, k);
     }
+    for (int k = 0; k < 4; k += 2)
+        if (p.res_y[k] < 0 || p.res_y[k] > p.res_y[k + 1] || p.res_y[k + 1] > p.L[1])
+            return fail(nullptr, RMPCD_EINVAL, "replica %d: reservoir columns [%d, %d) not within [0, L[1]]", r,
+                        p.res_y[k], p.res_y[k + 1]);
     return RMPCD_OK;
 }
 

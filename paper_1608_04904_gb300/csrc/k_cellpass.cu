@@ -160,6 +160,20 @@ __device__ __forceinline__ int canon(const unsigned short *pm, int i, int n)
     return q < n ? q : n - 1;
 }
 
+// Canonical order of one cell of n staged particles built by its own thread
+// (pm[rank by id] = staging place), for the cells that need it when the pass
+// does not rank every particle.
+template <class Rec>
+__device__ __forceinline__ void cell_order(const Rec *cr, int n, unsigned short *pm)
+{
+    for (int q = 0; q < n; ++q) {
+        const uint32_t id = cr[q].fid & ID_MASK;
+        int rank = 0;
+        for (int k = 0; k < n; ++k) rank += (cr[k].fid & ID_MASK) < id ? 1 : 0;
+        pm[rank < n ? rank : n - 1] = (unsigned short)q;
+    }
+}
+
 // Per-tile state shared by the threads of one CTA.
 template <bool MIXED>
 struct TileShared {
@@ -223,13 +237,18 @@ __device__ __forceinline__ void mpcat_cell(const ReplicaDev &rp, uint32_t step, 
         for (int k = 0; k < 3; ++k) v[canon(pm, i, n)].v[k] = (R)(vcm[k] + ((double)v[canon(pm, i, n)].v[k] - xs[k]));
 }
 
-// Stage D, one thread per cell, particles summed in canonical order (the
-// order of the FP64 definition): the i-th particle of the cell at staging
-// index lo + perm[lo + i].
-template <bool MIXED, bool MANY, bool FUSED>
+// Stage D, one thread per cell.  With CANON every particle's canonical place
+// is known (perm: the i-th particle of the cell at staging index lo +
+// perm[lo + i]) and the cell's velocity sum follows the canonical order (the
+// order of the FP64 definition).  Without it (the mixed path's fused run,
+// held to a tolerance, not to the oracle's summation order) the SRD sum
+// follows the staging order, and the canonical order is built only where a
+// result depends on it: the MPC-AT draws of a slab cell and the choice of
+// the reacting B particle.
+template <bool MIXED, bool MANY, bool FUSED, bool CANON>
 __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, TileShared<MIXED> &T, int gt,
                                         int cb, int ce, int pofs, typename Traits<MIXED>::Rec *srec,
-                                        const unsigned short *perm)
+                                        unsigned short *perm)
 {
     using R = typename Traits<MIXED>::R;
     const ReplicaDev &rp = T.rp;
@@ -239,7 +258,7 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
     for (int c = cb + gt; c < ce; c += CP_THREADS) {
         const int n = T.cnt[c];
         const int lo = T.ls[c] - pofs;
-        const unsigned short *pm = perm + lo;
+        unsigned short *pm = perm + lo;
         typename Traits<MIXED>::Rec *cr = srec + lo;
         const int lc = lc0 + c;
         T.mode[c] = 0;
@@ -262,12 +281,13 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
         R sum[3] = {R(0), R(0), R(0)};
         if (slab < 0 && (coll || nearq))
             for (int i = 0; i < n; ++i) {
-                const int q = canon(pm, i, n);
+                const int q = CANON ? canon(pm, i, n) : i;
                 for (int k = 0; k < 3; ++k) sum[k] = sum[k] + cr[q].v[k];
             }
         int nbB = -1;   // B count, when the near bound's loop has taken it
         if (coll) {
             if (slab >= 0) {
+                if (!CANON) cell_order(cr, n, pm);
                 mpcat_cell<R>(rp, a.step, (uint32_t)lc, slab, n, virt, cr, pm);
                 T.mode[c] = 2;
             } else {
@@ -340,11 +360,23 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
                 if ((unsigned long long)w.x < d.bulk_thr[rp.thr_off + nbB]) {
                     // the pick-th B particle of the cell in canonical order
                     const int pick = (int)(((unsigned long long)w.y * (unsigned long long)nbB) >> 32);
-                    for (int i = 0, seen = 0; i < n; ++i) {
-                        const int q = canon(pm, i, n);
-                        if (cr[q].fid & F_B) {
-                            if (seen == pick) { T.react[c] = lo + q; break; }
-                            ++seen;
+                    if (CANON) {
+                        for (int i = 0, seen = 0; i < n; ++i) {
+                            const int q = canon(pm, i, n);
+                            if (cr[q].fid & F_B) {
+                                if (seen == pick) { T.react[c] = lo + q; break; }
+                                ++seen;
+                            }
+                        }
+                    } else {
+                        // the B particle with exactly pick B particles of smaller id
+                        for (int q = 0; q < n; ++q) {
+                            if (!(cr[q].fid & F_B)) continue;
+                            const uint32_t id = cr[q].fid & ID_MASK;
+                            int below = 0;
+                            for (int k = 0; k < n; ++k)
+                                below += ((cr[k].fid & F_B) && (cr[k].fid & ID_MASK) < id) ? 1 : 0;
+                            if (below == pick) { T.react[c] = lo + q; break; }
                         }
                     }
                 }
@@ -548,6 +580,10 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
     }
     cp_async_wait_all();
     __syncthreads();
+    // the canonical order within each cell, for every particle except on the
+    // mixed path's fused run (see cells_D)
+    constexpr bool CANON = !(MIXED && FUSED);
+    if constexpr (CANON) {
     // the id of every staged particle (a record missing after an overflow
     // keeps stale contents; the run has latched the overflow)
 #pragma unroll
@@ -580,6 +616,7 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
         for (int u = 0; u < K; ++u)
             if (gt + u * G < nb) ent[gt + u * G] = rk[u];   // the canonical place within the cell
     }
+    }   // CANON
     // C: fly the records the MD kernel did not move
 #pragma unroll 1
     for (int p = gt; p < nb; p += G) {
@@ -590,7 +627,7 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
     }
     __syncthreads();
     // D: per-cell work
-    cells_D<MIXED, MANY, FUSED>(d, a, T, gt, cb, ce, pofs, srec, perm);
+    cells_D<MIXED, MANY, FUSED, CANON>(d, a, T, gt, cb, ce, pofs, srec, perm);
     __syncthreads();
     if constexpr (MANY) {
         if (opts & CP_NEXT) {
@@ -630,6 +667,13 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
             rec.v[2] = vc[2] + (ca * u2 + sa * x2 + od * nh[2]);
         }
         if (T.react[c] == p) rec.fid &= ~(F_B | F_TAG);
+        if (opts & CP_REACT) {
+            // species reservoirs (§1.5 chemotactic_cell): after the bulk
+            // reaction, the cells of the reservoir y columns are made pure
+            const int cy = ((T.tile * CPT - rp.cell_off + c) / rp.L[0]) % rp.L[1];
+            if (cy >= rp.res_y[0] && cy < rp.res_y[1]) rec.fid &= ~(F_B | F_TAG);
+            else if (cy >= rp.res_y[2] && cy < rp.res_y[3]) rec.fid = (rec.fid & ~F_TAG) | F_B;
+        }
         if constexpr (FUSED) {
             srec[p] = rec;
             int nkey = -1;

@@ -63,6 +63,7 @@ struct ReplicaDev {
     double gnorm, cat_thr, skin;
     double slab_x0[4], slab_x1[4], slab_sd[4];
     int slab_lo[4], slab_hi[4];      // cx in slab k iff slab_lo <= cx < slab_hi
+    int res_y[4];                    // species reservoirs: cy in [res_y[0], res_y[1]) -> A, [res_y[2], res_y[3]) -> B
     double cc_eps, cc_sigma, cc_rc;
     float tau_f, dt_f, hdt_f, ca_f, sa_f, omc_f;
     float g_f[3];

@@ -177,3 +177,14 @@ def test_workspace_size_rejects_what_create_rejects(api):
     lib = api.load()
     p = api.make_params(synth.base_config(), 100)
     assert lib.rmpcd_workspace_size(1, 1, p, None, None, 64, None) == 1
+
+
+def test_reservoir_columns_outside_the_box_are_rejected(api):
+    """rmpcd_workspace_size validates like rmpcd_create, without a GPU."""
+    from paper_1608_04904_gb300 import synth
+    cfg = synth.base_config(L=(8, 16, 6), reservoirs=((0, 2), (14, 17)))
+    with pytest.raises(api.RmpcdError) as e:
+        api.workspace_size([dict(cfg=cfg, n=100)], "fp64", 64)
+    assert e.value.code == "EINVAL"
+    ok = synth.base_config(L=(8, 16, 6), reservoirs=((0, 2), (14, 16)))
+    assert api.workspace_size([dict(cfg=ok, n=100)], "fp64", 64) > 0

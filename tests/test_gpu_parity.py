@@ -523,3 +523,31 @@ def test_automatic_bucket_width():
     assert runs[0][1] > cap0   # the shifted grid splits the crowd over up to 8 cells
     for key in runs[0][0]:
         assert np.array_equal(runs[0][0][key], runs[1][0][key]), key
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_chemotactic_reservoirs_in_the_cell_pass(precision):
+    """The chemotactic set-up (§1.5 chemotactic_cell): a Poiseuille channel
+    whose y columns [0, 2) and [14, 16) of the collision grid are species
+    reservoirs (A and B).  Fused steps equal the oracle's (fp64 bit for bit,
+    species flags bit-exact on both paths), and after each step the
+    reservoir cells are pure."""
+    cfg = synth.base_config(L=(8, 16, 6), walls=1, rho_wall=10, g=(0.005, 0.0, 0.0), alpha=math.radians(130.0),
+                            tau=0.5, kT=1.0, seed=21, bulk_rate=0.02, reservoirs=((0, 2), (14, 16)),
+                            precision=precision)
+    x, v, fl = synth.solvent(cfg, seed=22, frac_b=0.5)
+    g = gpu(cfg, x, v, fl, precision=precision, step=3)
+    o = oracle(cfg, x, v, fl, step=3)
+    for _ in range(3):
+        g.step(1)
+        o.step(1)
+        st = g.get_state()
+        _compare_step(cfg, st, o, precision)
+        gid, gf = by_id(st["id"], st["id"], st["flags"])
+        oid, of = by_id(o.id, o.id, o.flags)
+        assert np.array_equal(gf, of)
+        cy = (st["cell"] // cfg["L"][0]) % cfg["L"][1]
+        assert np.all(st["flags"][(cy >= 0) & (cy < 2)] == 0)
+        assert np.all(st["flags"][(cy >= 14) & (cy < 16)] == 1)
+    assert ((st["flags"] & 1) == 1).sum() > 0.2 * len(x)
+
