@@ -228,6 +228,20 @@ rmpcd_status rmpcd_get_step(const rmpcd_system *sys, uint32_t *step);
  * Does not advance the step counter. */
 rmpcd_status rmpcd_stream(rmpcd_system *sys);
 
+/* One velocity-Verlet sub-step of the current interval (the interval of
+ * rmpcd_stream, run one sub-step at a time; the paper's MD sub-step, §1.1,
+ * dt = tau / n_md).  Sub-step 0 also flies the far particles over tau and
+ * collects the particles near a colloid; sub-steps must run in order
+ * 0, 1, ..., n_md - 1, and after the last one the state equals that of
+ * rmpcd_stream bit for bit (same arithmetic; the colloid forces are exact
+ * fixed-point sums).  Between sub-steps rmpcd_get_colloids reads the colloids
+ * after sub-step k; the solvent is written back after the last sub-step, and
+ * every call other than rmpcd_md_substep, rmpcd_get_colloids, rmpcd_sync and
+ * the queries fails with ESTATE until then.  Replicas with fewer sub-steps
+ * finish early.  Errors: EINVAL (k outside 0..n_md - 1, rigid bodies), ESTATE
+ * (out of order), ECUDA. */
+rmpcd_status rmpcd_md_substep(rmpcd_system *sys, int32_t k);
+
 /* Random grid shift of the current step, cell keys and counting sort: storage
  * becomes sorted by cell, the particles of a cell in increasing id order. */
 rmpcd_status rmpcd_shift_and_sort(rmpcd_system *sys);

@@ -86,7 +86,7 @@ EXPORTS = [
     "rmpcd_collide", "rmpcd_react", "rmpcd_step", "rmpcd_observables", "rmpcd_sync", "rmpcd_launch_count",
     "rmpcd_last_error", "rmpcd_enable_timers", "rmpcd_read_timers", "rmpcd_set_tuning", "rmpcd_get_tuning",
     "rmpcd_observables_noalloc", "rmpcd_set_graphs", "rmpcd_get_bucket_cap", "rmpcd_set_body", "rmpcd_get_body",
-    "rmpcd_profile", "rmpcd_workspace_size", "rmpcd_set_wait_test",
+    "rmpcd_profile", "rmpcd_workspace_size", "rmpcd_set_wait_test", "rmpcd_md_substep",
 ]
 
 _LIB = None
@@ -109,6 +109,7 @@ def load():
     vp, i32, i64, u32, d = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_double
     L.rmpcd_create.argtypes = [P(vp), i32, i32, P(Params), P(Colloid), P(Bond), i32, vp]
     L.rmpcd_set_wait_test.argtypes = [vp, i32, i32]
+    L.rmpcd_md_substep.argtypes = [vp, i32]
     L.rmpcd_destroy.argtypes = [vp]
     L.rmpcd_destroy.restype = None
     L.rmpcd_set_state.argtypes = [vp, i32, vp, vp, vp, i64, i32]
@@ -382,6 +383,10 @@ class System:
     # -- the steps -----------------------------------------------------------
     def stream_interval(self):
         self._check(self._lib.rmpcd_stream(self._h))
+
+    def md_substep(self, k):
+        """rmpcd_md_substep: sub-step k of the current interval (in order from 0)."""
+        self._check(self._lib.rmpcd_md_substep(self._h, int(k)))
 
     def shift_and_sort(self):
         self._check(self._lib.rmpcd_shift_and_sort(self._h))

@@ -45,6 +45,7 @@ struct rmpcd_system {
     int bcur = 0;       // count/bucket buffer of the next collision (fused)
     bool primed = false;       // bins for the collision of `step` exist
     bool in_rows = false;      // the state lives in record rows + near area (fused run), not in rec[cur]
+    int md_sub_next = 0;       // next sub-step of an interval run by rmpcd_md_substep (0: none open)
     bool has_sort = false;
     uint32_t sort_step = 0;
     bool obs_valid = false;
@@ -607,6 +608,8 @@ static rmpcd_status create_system(rmpcd_system **out, int32_t precision, int32_t
     AL(&d.body, n_replicas);
     sys->work_bytes = (sys->mixed ? 64 : 80) * (size_t)(sys->any_colloids ? n_total : 1);
     AL(&work, sys->work_bytes);
+    unsigned char *colsave = nullptr;
+    AL(&colsave, md_col_state_bytes(sys->mixed) * (size_t)n_replicas);
     AL(&sys->prof_acc, (size_t)PROF_MAX_BINS * PROF_FIELDS);
     AL(&sys->stage_x, 3 * (size_t)sys->max_part);
     AL(&sys->stage_v, 3 * (size_t)sys->max_part);
@@ -694,6 +697,7 @@ static rmpcd_status create_system(rmpcd_system **out, int32_t precision, int32_t
     d.colInvM_f = dIM;
     d.bonds = dB;
     d.md_work = work;
+    d.md_col_save = colsave;
     d.cap = bucket_cap;
     d.ovf_cap = (int)ovf_cap;
     d.lb_limit = LB_SPIN_LIMIT;
@@ -733,6 +737,8 @@ static void drop_graphs(rmpcd_system *sys)
 // grid of its last collision); pending bins of a primed run are dropped.
 static rmpcd_status unprime(rmpcd_system *sys)
 {
+    if (sys->md_sub_next != 0)
+        return fail(sys, RMPCD_ESTATE, "an interval is being sub-stepped (rmpcd_md_substep): run its last sub-step first");
     if (sys->in_rows) return flatten(sys);
     if (!sys->primed) return RMPCD_OK;
     const size_t ncells = (size_t)sys->n_tiles * CPT;
@@ -1004,6 +1010,32 @@ rmpcd_status rmpcd_stream(rmpcd_system *sys)
     return RMPCD_OK;
 }
 
+rmpcd_status rmpcd_md_substep(rmpcd_system *sys, int32_t k)
+{
+    if (!sys) return RMPCD_EINVAL;
+    if (sys->any_body) return fail(sys, RMPCD_EINVAL, "rmpcd_md_substep: not for replicas with a rigid body");
+    int n_md = 0;
+    for (const auto &rp : sys->rep) n_md = std::max(n_md, rp.n_md);
+    if (k < 0 || k >= n_md) return fail(sys, RMPCD_EINVAL, "sub-step %d outside 0..%d", k, n_md - 1);
+    if (k != sys->md_sub_next)
+        return fail(sys, RMPCD_ESTATE, "sub-step %d out of order: the next sub-step is %d", k, sys->md_sub_next);
+    rmpcd_status st;
+    if (k == 0) {
+        // the interval starts: far particles fly, near particles join the near area
+        if ((st = unprime(sys)) != RMPCD_OK) return st;
+        launch_particles(sys->mixed, sys->d, PM_STREAM, sys->step, sys->cur, 0, sys->stream);
+        if ((st = after_launch(sys, sys->n_total > 0 ? 1 : 0)) != RMPCD_OK) return st;
+    }
+    if (sys->any_colloids) {
+        launch_md_range(sys->mixed, sys->d, sys->step, sys->cur, 0, 0, 1, k, k + 1, sys->stream);
+        if ((st = after_launch(sys, 1)) != RMPCD_OK) return st;
+    }
+    sys->md_sub_next = (k + 1 < n_md) ? k + 1 : 0;
+    sys->has_sort = false;
+    sys->obs_valid = false;
+    return RMPCD_OK;
+}
+
 rmpcd_status rmpcd_shift_and_sort(rmpcd_system *sys)
 {
     if (!sys) return RMPCD_EINVAL;
@@ -1138,6 +1170,8 @@ rmpcd_status rmpcd_step(rmpcd_system *sys, int32_t n_intervals)
 {
     if (!sys) return RMPCD_EINVAL;
     if (n_intervals < 0) return fail(sys, RMPCD_EINVAL, "n_intervals < 0");
+    if (sys->md_sub_next != 0)
+        return fail(sys, RMPCD_ESTATE, "an interval is being sub-stepped (rmpcd_md_substep): run its last sub-step first");
     if (n_intervals == 0) return RMPCD_OK;
     rmpcd_status st;
     cudaEvent_t ev;

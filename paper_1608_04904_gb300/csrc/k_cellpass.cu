@@ -160,20 +160,6 @@ __device__ __forceinline__ int canon(const unsigned short *pm, int i, int n)
     return q < n ? q : n - 1;
 }
 
-// Canonical order of one cell of n staged particles built by its own thread
-// (pm[rank by id] = staging place), for the cells that need it when the pass
-// does not rank every particle.
-template <class Rec>
-__device__ __forceinline__ void cell_order(const Rec *cr, int n, unsigned short *pm)
-{
-    for (int q = 0; q < n; ++q) {
-        const uint32_t id = cr[q].fid & ID_MASK;
-        int rank = 0;
-        for (int k = 0; k < n; ++k) rank += (cr[k].fid & ID_MASK) < id ? 1 : 0;
-        pm[rank < n ? rank : n - 1] = (unsigned short)q;
-    }
-}
-
 // Per-tile state shared by the threads of one CTA.
 template <bool MIXED>
 struct TileShared {
@@ -187,7 +173,7 @@ struct TileShared {
     float shf[3], shnf[3];
     R vcm[CPT][3], ax[CPT][3];
     int react[CPT];
-    unsigned char mode[CPT];    // 0: untouched, 1: SRD rotation, 2: MPC-AT
+    unsigned char mode[CPT];    // bits 0-1: 0 untouched, 1 SRD rotation, 2 MPC-AT; 4: reservoir A, 8: reservoir B
     unsigned char mnear[CPT];   // 0: no particle of the cell can come near a colloid
     float vbc[CPT];   // bound on the cell's post-collision speeds (< 0: none, MPC-AT)
     unsigned long long cand;   // colloids that can reach the batch (many-colloid replicas)
@@ -237,18 +223,14 @@ __device__ __forceinline__ void mpcat_cell(const ReplicaDev &rp, uint32_t step, 
         for (int k = 0; k < 3; ++k) v[canon(pm, i, n)].v[k] = (R)(vcm[k] + ((double)v[canon(pm, i, n)].v[k] - xs[k]));
 }
 
-// Stage D, one thread per cell.  With CANON every particle's canonical place
-// is known (perm: the i-th particle of the cell at staging index lo +
-// perm[lo + i]) and the cell's velocity sum follows the canonical order (the
-// order of the FP64 definition).  Without it (the mixed path's fused run,
-// held to a tolerance, not to the oracle's summation order) the SRD sum
-// follows the staging order, and the canonical order is built only where a
-// result depends on it: the MPC-AT draws of a slab cell and the choice of
-// the reacting B particle.
-template <bool MIXED, bool MANY, bool FUSED, bool CANON>
+// Stage D, one thread per cell, particles summed in canonical order (the
+// order of the FP64 definition, and on the mixed path what makes reruns
+// bit-identical whatever order the atomics delivered the particles in): the
+// i-th particle of the cell at staging index lo + perm[lo + i].
+template <bool MIXED, bool MANY, bool FUSED>
 __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, TileShared<MIXED> &T, int gt,
                                         int cb, int ce, int pofs, typename Traits<MIXED>::Rec *srec,
-                                        unsigned short *perm)
+                                        const unsigned short *perm)
 {
     using R = typename Traits<MIXED>::R;
     const ReplicaDev &rp = T.rp;
@@ -258,7 +240,7 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
     for (int c = cb + gt; c < ce; c += CP_THREADS) {
         const int n = T.cnt[c];
         const int lo = T.ls[c] - pofs;
-        unsigned short *pm = perm + lo;
+        const unsigned short *pm = perm + lo;
         typename Traits<MIXED>::Rec *cr = srec + lo;
         const int lc = lc0 + c;
         T.mode[c] = 0;
@@ -281,15 +263,21 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
         R sum[3] = {R(0), R(0), R(0)};
         if (slab < 0 && (coll || nearq))
             for (int i = 0; i < n; ++i) {
-                const int q = CANON ? canon(pm, i, n) : i;
+                const int q = canon(pm, i, n);
                 for (int k = 0; k < 3; ++k) sum[k] = sum[k] + cr[q].v[k];
             }
         int nbB = -1;   // B count, when the near bound's loop has taken it
+        unsigned char res = 0;   // species reservoir of the cell's y column (chemotactic set-up)
+        if ((opts & CP_REACT) && (rp.res_y[0] < rp.res_y[1] || rp.res_y[2] < rp.res_y[3])) {
+            const int cy = (lc / rp.L[0]) % rp.L[1];
+            if (cy >= rp.res_y[0] && cy < rp.res_y[1]) res = 4;
+            else if (cy >= rp.res_y[2] && cy < rp.res_y[3]) res = 8;
+            T.mode[c] = res;
+        }
         if (coll) {
             if (slab >= 0) {
-                if (!CANON) cell_order(cr, n, pm);
                 mpcat_cell<R>(rp, a.step, (uint32_t)lc, slab, n, virt, cr, pm);
-                T.mode[c] = 2;
+                T.mode[c] = 2 | res;
             } else {
                 R vcm[3];
                 if (virt) {
@@ -308,7 +296,7 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
                 R ax[3];
                 rotation_axis<R>(rp.seed, a.step, (uint32_t)lc, ax);
                 for (int k = 0; k < 3; ++k) { T.vcm[c][k] = vcm[k]; T.ax[c][k] = ax[k]; }
-                T.mode[c] = 1;
+                T.mode[c] = 1 | res;
             }
         }
         if (nearq) {
@@ -360,23 +348,11 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
                 if ((unsigned long long)w.x < d.bulk_thr[rp.thr_off + nbB]) {
                     // the pick-th B particle of the cell in canonical order
                     const int pick = (int)(((unsigned long long)w.y * (unsigned long long)nbB) >> 32);
-                    if (CANON) {
-                        for (int i = 0, seen = 0; i < n; ++i) {
-                            const int q = canon(pm, i, n);
-                            if (cr[q].fid & F_B) {
-                                if (seen == pick) { T.react[c] = lo + q; break; }
-                                ++seen;
-                            }
-                        }
-                    } else {
-                        // the B particle with exactly pick B particles of smaller id
-                        for (int q = 0; q < n; ++q) {
-                            if (!(cr[q].fid & F_B)) continue;
-                            const uint32_t id = cr[q].fid & ID_MASK;
-                            int below = 0;
-                            for (int k = 0; k < n; ++k)
-                                below += ((cr[k].fid & F_B) && (cr[k].fid & ID_MASK) < id) ? 1 : 0;
-                            if (below == pick) { T.react[c] = lo + q; break; }
+                    for (int i = 0, seen = 0; i < n; ++i) {
+                        const int q = canon(pm, i, n);
+                        if (cr[q].fid & F_B) {
+                            if (seen == pick) { T.react[c] = lo + q; break; }
+                            ++seen;
                         }
                     }
                 }
@@ -502,7 +478,9 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
     }
     // B: every particle's record into the staging area, in arrival order
     if constexpr (FUSED) {
-        // the first cap of a cell from its row, contiguous in memory
+        // the first cap of a cell from its row, contiguous in memory (16-byte
+        // asynchronous copies issued by every thread: measured faster than
+        // one bulk copy per cell issued by one warp)
         const Rec *rows = reinterpret_cast<const Rec *>(d.brec[a.cur]);
 #pragma unroll
         for (int u = 0; u < K; ++u) {
@@ -580,22 +558,12 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
     }
     cp_async_wait_all();
     __syncthreads();
-    // the canonical order within each cell, for every particle except on the
-    // mixed path's fused run (see cells_D)
-    constexpr bool CANON = !(MIXED && FUSED);
-    if constexpr (CANON) {
-    // the id of every staged particle (a record missing after an overflow
-    // keeps stale contents; the run has latched the overflow)
-#pragma unroll
-    for (int u = 0; u < K; ++u) {
-        const int j = gt + u * G;
-        if (j < nb) ent[j] = (int)(srec[j].fid & ID_MASK);
-    }
-    __syncthreads();
-    // the canonical place of every particle in its cell: its rank by id (ids
-    // are unique in a valid state; should two collide, two ranks coincide
-    // and the reads of perm below clamp to the cell, so every access stays
-    // in the staging area and the latched error reports the state)
+    // the canonical place of every particle in its cell: its rank by id, read
+    // from the staged records (ids are unique in a valid state; should two
+    // collide -- a record left stale after an overflow, which the run has
+    // latched --, two ranks coincide and the reads of perm below clamp to the
+    // cell, so every access stays in the staging area).  Stage C may rewrite
+    // a record meanwhile: only its flag bits change, not the id read here.
     int rk[K];
 #pragma unroll
     for (int u = 0; u < K; ++u) {
@@ -603,9 +571,9 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
         if (j < nb) {
             const int c = cb + cellof[j];
             const int lo = T.ls[c] - pofs, n = T.cnt[c];
-            const int id = ent[j];
+            const uint32_t id = srec[j].fid & ID_MASK;
             int rank = 0;
-            for (int k = 0; k < n; ++k) rank += ent[lo + k] < id ? 1 : 0;
+            for (int k = 0; k < n; ++k) rank += (srec[lo + k].fid & ID_MASK) < id ? 1 : 0;
             rk[u] = rank;
             perm[lo + rank] = (unsigned short)(j - lo);
         }
@@ -616,18 +584,25 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
         for (int u = 0; u < K; ++u)
             if (gt + u * G < nb) ent[gt + u * G] = rk[u];   // the canonical place within the cell
     }
-    }   // CANON
-    // C: fly the records the MD kernel did not move
+    // C: fly the records the MD kernel did not move, with the velocities of
+    // the interval.  Stage E may fly them instead (before it rotates the
+    // velocities) unless the flight changes velocities that stage D sums
+    // (walls, body force) or stage D replaces velocities before E runs
+    // (MPC-AT slabs).
+    const bool c_stage = (opts & CP_FLIGHT) && (rp.walls || rp.has_g || rp.n_slabs > 0);
+    const bool fly_in_E = (opts & CP_FLIGHT) && !c_stage;
+    if (c_stage) {
 #pragma unroll 1
-    for (int p = gt; p < nb; p += G) {
-        Rec rec = srec[p];
-        if ((opts & CP_FLIGHT) && !(rec.fid & F_PROP)) rec_flight(hp, rec);
-        rec.fid &= ~F_PROP;
-        srec[p] = rec;
+        for (int p = gt; p < nb; p += G) {
+            Rec rec = srec[p];
+            if (!(rec.fid & F_PROP)) rec_flight(hp, rec);
+            rec.fid &= ~F_PROP;
+            srec[p] = rec;
+        }
     }
     __syncthreads();
     // D: per-cell work
-    cells_D<MIXED, MANY, FUSED, CANON>(d, a, T, gt, cb, ce, pofs, srec, perm);
+    cells_D<MIXED, MANY, FUSED>(d, a, T, gt, cb, ce, pofs, srec, perm);
     __syncthreads();
     if constexpr (MANY) {
         if (opts & CP_NEXT) {
@@ -652,7 +627,10 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
     for (int p = gt; p < nb; p += G) {
         const int c = cb + cellof[p];
         Rec rec = srec[p];
-        if (T.mode[c] == 1) {
+        if (fly_in_E && !(rec.fid & F_PROP)) rec_flight(hp, rec);
+        rec.fid &= ~F_PROP;
+        const unsigned mode = T.mode[c];
+        if ((mode & 3) == 1) {
             const R *vc = T.vcm[c];
             const R *nh = T.ax[c];
             const R u0 = rec.v[0] - vc[0], u1 = rec.v[1] - vc[1], u2 = rec.v[2] - vc[2];
@@ -667,13 +645,10 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
             rec.v[2] = vc[2] + (ca * u2 + sa * x2 + od * nh[2]);
         }
         if (T.react[c] == p) rec.fid &= ~(F_B | F_TAG);
-        if (opts & CP_REACT) {
-            // species reservoirs (§1.5 chemotactic_cell): after the bulk
-            // reaction, the cells of the reservoir y columns are made pure
-            const int cy = ((T.tile * CPT - rp.cell_off + c) / rp.L[0]) % rp.L[1];
-            if (cy >= rp.res_y[0] && cy < rp.res_y[1]) rec.fid &= ~(F_B | F_TAG);
-            else if (cy >= rp.res_y[2] && cy < rp.res_y[3]) rec.fid = (rec.fid & ~F_TAG) | F_B;
-        }
+        // species reservoirs (§1.5 chemotactic_cell): after the bulk
+        // reaction, the cells of the reservoir y columns are made pure
+        if (mode & 4) rec.fid &= ~(F_B | F_TAG);
+        if (mode & 8) rec.fid = (rec.fid & ~F_TAG) | F_B;
         if constexpr (FUSED) {
             srec[p] = rec;
             int nkey = -1;

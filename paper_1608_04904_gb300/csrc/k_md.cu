@@ -589,10 +589,31 @@ __device__ __forceinline__ void publish_cluster(cg::cluster_group &cl, MDShared<
     }
 }
 
+// Copy the colloid state of replica r between shared memory and its save
+// slot (the sub-stepped interval of rmpcd_md_substep), by all threads.
+template <bool MIXED>
+__device__ void col_state_copy(const Dev &d, MDShared<MIXED> &S, int r, bool save)
+{
+    using CT = typename std::conditional<MIXED, ColM, ColD>::type;
+    static_assert(sizeof(CT) % 4 == 0, "word copy");
+    unsigned *g = reinterpret_cast<unsigned *>(reinterpret_cast<unsigned char *>(d.md_col_save) + (size_t)r * sizeof(CT));
+    unsigned *s = reinterpret_cast<unsigned *>(&S.C);
+    for (int i = threadIdx.x; i < (int)(sizeof(CT) / 4); i += blockDim.x) {
+        if (save) g[i] = s[i];
+        else s[i] = g[i];
+    }
+}
+
+// Sub-steps [s0, s1) of the interval (s1 < 0: to the end).  s0 = 0 starts
+// the interval from the near area; s0 > 0 continues from the near working set
+// in md_work and the colloid state saved by the previous call.  An interval
+// that ends before its last sub-step saves the colloid state (and stores its
+// positions and velocities for inspection) and keeps the near particles.
 template <bool MIXED, bool REG, int CS>
 __device__ void md_body(const Dev &d, MDShared<MIXED> &S, const ReplicaDev &rp, cg::cluster_group &cl,
-                        uint32_t step, int rbuf, int bbuf, int do_bin, int r)
+                        uint32_t step, int rbuf, int bbuf, int do_bin, int r, int s0, int s1)
 {
+    const int s_end = s1 < 0 ? rp.n_md : min(s1, rp.n_md);
     using W = typename std::conditional<MIXED, WorkM, WorkD>::type;
     constexpr int NT = MDGeom<CS>::NT;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -636,6 +657,7 @@ __device__ void md_body(const Dev &d, MDShared<MIXED> &S, const ReplicaDev &rp, 
     };
 
     // forces at the start of the interval
+    if (s0 == 0) {
     zero_acc();
     zero_fq();
     __syncthreads();
@@ -661,9 +683,10 @@ __device__ void md_body(const Dev &d, MDShared<MIXED> &S, const ReplicaDev &rp, 
     } else {
         if (tid == 0) col_gather<CS>(rp, S, 0);
     }
+    }   // s0 == 0
 
     const double dt = rp.dt, hdt = rp.hdt;
-    for (int s = 0; s < rp.n_md; ++s) {
+    for (int s = s0; s < s_end; ++s) {
         const int par = (s + 1) & 1;
         // colloids: first half kick, drift, RATTLE position stage
         if constexpr (MIXED) {
@@ -718,6 +741,21 @@ __device__ void md_body(const Dev &d, MDShared<MIXED> &S, const ReplicaDev &rp, 
         }
     }
 
+    if (s_end < rp.n_md) {
+        // a sub-stepped interval continues later: save the colloids, keep
+        // the near particles in md_work and the near count
+        __syncthreads();
+        if (rank == 0) {
+            if (tid == 0) {
+                if constexpr (!MIXED) col_frames(rp, S);
+                col_store(d, rp, S);
+            }
+            __syncthreads();
+            col_state_copy<MIXED>(d, S, r, true);
+        }
+        if (CS > 1) cl.sync();
+        return;
+    }
     // last half kick, wrap, write back (and bin for the collision of `step`)
     double sh[3];
     grid_shift(rp.seed, step, sh);
@@ -754,7 +792,8 @@ __device__ void md_body(const Dev &d, MDShared<MIXED> &S, const ReplicaDev &rp, 
 }
 
 template <bool MIXED, int CS>
-__global__ void __launch_bounds__(MDGeom<CS>::NT, 1) k_md(Dev d, uint32_t step, int rbuf, int bbuf, int do_bin)
+__global__ void __launch_bounds__(MDGeom<CS>::NT, 1) k_md(Dev d, uint32_t step, int rbuf, int bbuf, int do_bin,
+                                                          int s0, int s1)
 {
     step = resolve_step(d, step);   // STEP_DEVICE: the step of the control block
     __shared__ MDShared<MIXED> S;
@@ -782,14 +821,20 @@ __global__ void __launch_bounds__(MDGeom<CS>::NT, 1) k_md(Dev d, uint32_t step, 
     }
     if (tid < rp.n_bond) S.bond[tid] = d.bonds[rp.bond_off + tid];
     __syncthreads();
+    if (s0 > 0) {
+        // a continued interval: the colloid state of the previous call
+        col_state_copy<MIXED>(d, S, r, false);
+        __syncthreads();
+    }
     if constexpr (!MIXED) {
         if (tid == 0) col_frames(rp, S);
         __syncthreads();
     }
     // all CTAs of the cluster must have read near_count before rank 0 resets it
     if (CS > 1) cl.sync();
-    if (rp.n_col <= NCR) md_body<MIXED, true, CS>(d, S, rp, cl, step, rbuf, bbuf, do_bin, r);
-    else md_body<MIXED, false, CS>(d, S, rp, cl, step, rbuf, bbuf, do_bin, r);
+    if (s0 >= rp.n_md) return;   // this replica's interval has fewer sub-steps
+    if (rp.n_col <= NCR) md_body<MIXED, true, CS>(d, S, rp, cl, step, rbuf, bbuf, do_bin, r, s0, s1);
+    else md_body<MIXED, false, CS>(d, S, rp, cl, step, rbuf, bbuf, do_bin, r, s0, s1);
 }
 
 // ===========================================================================
@@ -1140,7 +1185,7 @@ void launch_md_wide(const Dev &d, const std::vector<int> &reps, int grid, uint32
 }
 
 template <bool MIXED, int CS>
-static void launch_md_cs(const Dev &d, uint32_t step, int rbuf, int bbuf, int do_bin, cudaStream_t s)
+static void launch_md_cs(const Dev &d, uint32_t step, int rbuf, int bbuf, int do_bin, int s0, int s1, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(d.n_rep * CS), 1, 1);
@@ -1154,20 +1199,28 @@ static void launch_md_cs(const Dev &d, uint32_t step, int rbuf, int bbuf, int do
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_md<MIXED, CS>, d, step, rbuf, bbuf, do_bin);
+    cudaLaunchKernelEx(&cfg, k_md<MIXED, CS>, d, step, rbuf, bbuf, do_bin, s0, s1);
 }
 
 const int MD_CLUSTER_SIZES[4] = {1, 2, 4, 8};
 
 void launch_md(bool mixed, const Dev &d, uint32_t step, int rbuf, int bbuf, int do_bin, int cs, cudaStream_t s)
 {
+    launch_md_range(mixed, d, step, rbuf, bbuf, do_bin, cs, 0, -1, s);
+}
+
+void launch_md_range(bool mixed, const Dev &d, uint32_t step, int rbuf, int bbuf, int do_bin, int cs, int s0, int s1,
+                     cudaStream_t s)
+{
     if (d.n_rep <= 0) return;
     switch (cs) {
-    case 1: mixed ? launch_md_cs<true, 1>(d, step, rbuf, bbuf, do_bin, s) : launch_md_cs<false, 1>(d, step, rbuf, bbuf, do_bin, s); break;
-    case 2: mixed ? launch_md_cs<true, 2>(d, step, rbuf, bbuf, do_bin, s) : launch_md_cs<false, 2>(d, step, rbuf, bbuf, do_bin, s); break;
-    case 4: mixed ? launch_md_cs<true, 4>(d, step, rbuf, bbuf, do_bin, s) : launch_md_cs<false, 4>(d, step, rbuf, bbuf, do_bin, s); break;
-    default: mixed ? launch_md_cs<true, 8>(d, step, rbuf, bbuf, do_bin, s) : launch_md_cs<false, 8>(d, step, rbuf, bbuf, do_bin, s); break;
+    case 1: mixed ? launch_md_cs<true, 1>(d, step, rbuf, bbuf, do_bin, s0, s1, s) : launch_md_cs<false, 1>(d, step, rbuf, bbuf, do_bin, s0, s1, s); break;
+    case 2: mixed ? launch_md_cs<true, 2>(d, step, rbuf, bbuf, do_bin, s0, s1, s) : launch_md_cs<false, 2>(d, step, rbuf, bbuf, do_bin, s0, s1, s); break;
+    case 4: mixed ? launch_md_cs<true, 4>(d, step, rbuf, bbuf, do_bin, s0, s1, s) : launch_md_cs<false, 4>(d, step, rbuf, bbuf, do_bin, s0, s1, s); break;
+    default: mixed ? launch_md_cs<true, 8>(d, step, rbuf, bbuf, do_bin, s0, s1, s) : launch_md_cs<false, 8>(d, step, rbuf, bbuf, do_bin, s0, s1, s); break;
     }
 }
+
+size_t md_col_state_bytes(bool mixed) { return mixed ? sizeof(ColM) : sizeof(ColD); }
 
 }  // namespace rmpcd

@@ -169,6 +169,7 @@ struct Dev {
     const int *colCat;
     const BondDev *bonds;
     void *md_work;               // near-particle working state
+    void *md_col_save;           // per replica: colloid state between the calls of a sub-stepped interval
     MdWideGlobal *md_wide;       // wide MD kernel scratch
     Ctl *ctl;                    // interval control (step, cell-pass launch counter)
     unsigned int *maxcnt;        // largest cell count seen (bucket-width tuner)

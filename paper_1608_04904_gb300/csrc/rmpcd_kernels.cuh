@@ -37,6 +37,12 @@ void launch_particles(bool mixed, const Dev &d, int mode, uint32_t step, int rbu
 // cs: CTAs per replica cluster, one of MD_CLUSTER_SIZES (results do not depend on it)
 extern const int MD_CLUSTER_SIZES[4];
 void launch_md(bool mixed, const Dev &d, uint32_t step, int rbuf, int bbuf, int do_bin, int cs, cudaStream_t s);
+// Sub-steps [s0, s1) of the general MD kernel's interval (s1 < 0: to its end;
+// see rmpcd_md_substep); the colloid state between calls lives in
+// d.md_col_save (md_col_state_bytes per replica).
+void launch_md_range(bool mixed, const Dev &d, uint32_t step, int rbuf, int bbuf, int do_bin, int cs, int s0, int s1,
+                     cudaStream_t s);
+size_t md_col_state_bytes(bool mixed);
 // Few-colloid variant (every replica: at most MD_FAST_NC colloids, no
 // colloid-colloid potential); bit-identical results to launch_md.
 constexpr int MD_FAST_NC = 2;

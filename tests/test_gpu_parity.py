@@ -551,3 +551,43 @@ def test_chemotactic_reservoirs_in_the_cell_pass(precision):
         assert np.all(st["flags"][(cy >= 14) & (cy < 16)] == 1)
     assert ((st["flags"] & 1) == 1).sum() > 0.2 * len(x)
 
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_md_substeps_equal_the_interval(precision):
+    """rmpcd_md_substep: the interval's n_md velocity-Verlet sub-steps run one
+    call at a time equal rmpcd_stream's whole interval bit for bit (solvent,
+    species, colloids), the RATTLE bond holds after every sub-step, and the
+    sub-steps must come in order."""
+    cfg, col, bonds, x, v, fl = _dimer(precision)
+    col[0]["v"] = (0.03, -0.01, 0.0)
+    col[1]["v"] = (0.03, -0.01, 0.0)
+    a = gpu(cfg, x, v, fl, col, bonds, precision=precision, step=3)
+    a.stream_interval()
+    sa, ca = a.get_state(), a.get_colloids(0)
+    b = gpu(cfg, x, v, fl, col, bonds, precision=precision, step=3)
+    with pytest.raises(api.RmpcdError) as e:
+        b.md_substep(1)
+    assert e.value.code == "ESTATE"
+    prev = b.get_colloids(0)["x"]
+    moved = 0
+    for k in range(cfg["n_md"]):
+        b.md_substep(k)
+        if k < cfg["n_md"] - 1:
+            X = b.get_colloids(0)["x"]
+            bond = np.linalg.norm(X[0] - X[1])
+            assert abs(bond - 4.5) < (1e-11 if precision == "fp64" else 1e-5), (k, bond)
+            moved += np.abs(X - prev).max() > 0
+            prev = X
+            if k == 5:
+                with pytest.raises(api.RmpcdError) as e:
+                    b.get_state()
+                assert e.value.code == "ESTATE"
+    assert moved >= cfg["n_md"] - 2
+    sb, cb2 = b.get_state(), b.get_colloids(0)
+    for key in ("id", "x", "v", "flags"):
+        assert np.array_equal(sa[key], sb[key]), key
+    assert np.array_equal(ca["x"], cb2["x"]) and np.array_equal(ca["v"], cb2["v"])
+    # the interval is closed: the next step runs
+    b.step(1)
+    b.sync()
