@@ -337,20 +337,26 @@ struct __align__(16) RecD {
 static_assert(sizeof(RecM) == 32, "mixed record is one 32-byte sector");
 static_assert(sizeof(RecD) == 64, "fp64 record is two 32-byte sectors");
 
+// A mixed record is one 32-byte sector, moved by one 256-bit access (every
+// record array is 32-byte aligned): one request per record instead of two
+// half-sector ones.
 __device__ __forceinline__ RecM load_rec(const RecM *p)
 {
-    const uint4 *q = reinterpret_cast<const uint4 *>(p);
-    uint4 a = __ldg(q), b = __ldg(q + 1);
+    unsigned a[8];
+    asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7])
+                 : "l"(p));
     RecM r;
-    r.cw = a.x; r.o[0] = __uint_as_float(a.y); r.o[1] = __uint_as_float(a.z); r.o[2] = __uint_as_float(a.w);
-    r.v[0] = __uint_as_float(b.x); r.v[1] = __uint_as_float(b.y); r.v[2] = __uint_as_float(b.z); r.fid = b.w;
+    r.cw = a[0]; r.o[0] = __uint_as_float(a[1]); r.o[1] = __uint_as_float(a[2]); r.o[2] = __uint_as_float(a[3]);
+    r.v[0] = __uint_as_float(a[4]); r.v[1] = __uint_as_float(a[5]); r.v[2] = __uint_as_float(a[6]); r.fid = a[7];
     return r;
 }
 __device__ __forceinline__ void store_rec(RecM *p, const RecM &r)
 {
-    uint4 *q = reinterpret_cast<uint4 *>(p);
-    q[0] = make_uint4(r.cw, __float_as_uint(r.o[0]), __float_as_uint(r.o[1]), __float_as_uint(r.o[2]));
-    q[1] = make_uint4(__float_as_uint(r.v[0]), __float_as_uint(r.v[1]), __float_as_uint(r.v[2]), r.fid);
+    asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(r.cw), "r"(__float_as_uint(r.o[0])),
+                 "r"(__float_as_uint(r.o[1])), "r"(__float_as_uint(r.o[2])), "r"(__float_as_uint(r.v[0])),
+                 "r"(__float_as_uint(r.v[1])), "r"(__float_as_uint(r.v[2])), "r"(r.fid)
+                 : "memory");
 }
 __device__ __forceinline__ RecD load_rec(const RecD *p)
 {
