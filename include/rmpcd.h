@@ -123,6 +123,18 @@ typedef struct {
 
 #define RMPCD_MAX_BEADS 1024
 
+/* One bead of a bead network held by iterative RATTLE (the paper's Janus
+ * integrator, §1.4): position (unwrapped, box frame) and velocity, mass, WCA
+ * epsilon towards A and B solvent, catalytic flag (§1.5). */
+typedef struct {
+    double x[3], v[3];
+    double mass, eps_A, eps_B;
+    int32_t catalytic;
+    int32_t pad;
+} rmpcd_net_bead;
+
+#define RMPCD_MAX_NET_BEADS 512
+
 /* Observables of one replica after the last collision (§1.4 temperature
  * estimator; totals accumulated in FP64). */
 typedef struct {
@@ -213,6 +225,31 @@ rmpcd_status rmpcd_set_body(rmpcd_system *sys, int32_t replica, const rmpcd_body
  * are not returned).  Synchronises and returns latched device errors.
  * Errors: EINVAL (no body), ECUDA, EOVERFLOW, ESKIN, ETIMEOUT. */
 rmpcd_status rmpcd_get_body(rmpcd_system *sys, int32_t replica, rmpcd_body *body);
+
+/* Give one replica a bead network held at fixed link lengths by iterative
+ * RATTLE (§1.4: the paper's integrator of the Janus particle; every bead a
+ * point mass), or replace it.  FP64 systems only; the replica must have been
+ * created with no colloids, bonds or walls and hold no rigid body.
+ * beads[n_beads], 1 <= n_beads <= RMPCD_MAX_NET_BEADS; links[n_links] join
+ * beads a != b at length d > 0; colors[n_links] >= 0 with no bead twice in one
+ * colour.  Each velocity-Verlet sub-step corrects positions (along the link
+ * vectors of the sub-step's start) and then velocities (along the current
+ * ones), sweeping the links colour by colour -- the links of a colour at once,
+ * in the order given within a colour -- until every link holds within tol
+ * (|d^2 - |x_a - x_b|^2| <= 2 tol d^2; |(v_a - v_b).(x_a - x_b)| <= tol d),
+ * at most max_sweeps sweeps (more latches ESTATE).  Solvent within the beads'
+ * reach (largest bead distance from the centre of mass plus 2^(1/6) sigma)
+ * + |v| tau + |g| tau^2/2 + skin of the centre of mass takes the MD sub-steps.
+ * Discards a primed fused pipeline; synchronises.  Errors: EINVAL, ENOMEM,
+ * ECUDA. */
+rmpcd_status rmpcd_set_network(rmpcd_system *sys, int32_t replica, const rmpcd_net_bead *beads, int32_t n_beads,
+                               const rmpcd_bond *links, const int32_t *colors, int32_t n_links, double sigma,
+                               double tol, int32_t max_sweeps);
+
+/* Bead positions and velocities (host arrays of 3 n_beads doubles) of one
+ * replica's network, as of the last completed interval.  Synchronises and
+ * returns latched device errors.  Errors: EINVAL (no network, wrong count). */
+rmpcd_status rmpcd_get_network(rmpcd_system *sys, int32_t replica, double *x, double *v, int32_t n_beads);
 
 /* Collision counter that keys every random draw of the next interval. */
 rmpcd_status rmpcd_set_step(rmpcd_system *sys, uint32_t step);

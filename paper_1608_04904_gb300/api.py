@@ -61,6 +61,14 @@ class Bead(C.Structure):
 MAX_BEADS = 1024
 
 
+class NetBead(C.Structure):
+    _fields_ = [("x", C.c_double * 3), ("v", C.c_double * 3), ("mass", C.c_double), ("eps_A", C.c_double),
+                ("eps_B", C.c_double), ("catalytic", C.c_int32), ("pad", C.c_int32)]
+
+
+MAX_NET_BEADS = 512
+
+
 class Obs(C.Structure):
     _fields_ = [("temperature", C.c_double), ("momentum", C.c_double * 3), ("kinetic", C.c_double),
                 ("n_cells_used", C.c_int64), ("n_B", C.c_int64), ("n_solvent", C.c_int64),
@@ -86,7 +94,8 @@ EXPORTS = [
     "rmpcd_collide", "rmpcd_react", "rmpcd_step", "rmpcd_observables", "rmpcd_sync", "rmpcd_launch_count",
     "rmpcd_last_error", "rmpcd_enable_timers", "rmpcd_read_timers", "rmpcd_set_tuning", "rmpcd_get_tuning",
     "rmpcd_observables_noalloc", "rmpcd_set_graphs", "rmpcd_get_bucket_cap", "rmpcd_set_body", "rmpcd_get_body",
-    "rmpcd_profile", "rmpcd_workspace_size", "rmpcd_set_wait_test", "rmpcd_md_substep",
+    "rmpcd_profile", "rmpcd_workspace_size", "rmpcd_set_wait_test", "rmpcd_md_substep", "rmpcd_set_network",
+    "rmpcd_get_network",
 ]
 
 _LIB = None
@@ -110,6 +119,8 @@ def load():
     L.rmpcd_create.argtypes = [P(vp), i32, i32, P(Params), P(Colloid), P(Bond), i32, vp]
     L.rmpcd_set_wait_test.argtypes = [vp, i32, i32]
     L.rmpcd_md_substep.argtypes = [vp, i32]
+    L.rmpcd_set_network.argtypes = [vp, i32, P(NetBead), i32, P(Bond), P(i32), i32, d, d, i32]
+    L.rmpcd_get_network.argtypes = [vp, i32, P(d), P(d), i32]
     L.rmpcd_destroy.argtypes = [vp]
     L.rmpcd_destroy.restype = None
     L.rmpcd_set_state.argtypes = [vp, i32, vp, vp, vp, i64, i32]
@@ -364,6 +375,44 @@ class System:
             beads[j].eps_B = float(eB[j])
             beads[j].catalytic = int(cat[j])
         self._check(self._lib.rmpcd_set_body(self._h, replica, C.byref(B), beads))
+
+    def set_network(self, replica, xb, vb, mb, eps_A, eps_B, catalytic, sigma, links, d, colors, tol=1e-12,
+                    max_sweeps=10000):
+        """rmpcd_set_network: a bead network held by iterative RATTLE (FP64
+        systems).  xb, vb [nb, 3] (box frame, unwrapped); mb, eps_A, eps_B,
+        catalytic per bead or scalar; links [(a, b)] of lengths d with an
+        edge colouring `colors` (no bead twice in a colour)."""
+        xb = np.ascontiguousarray(xb, dtype=np.float64).reshape(-1, 3)
+        vb = np.ascontiguousarray(vb, dtype=np.float64).reshape(-1, 3)
+        nb = len(xb)
+        mb = np.broadcast_to(np.asarray(mb, np.float64), nb)
+        eA = np.broadcast_to(np.asarray(eps_A, np.float64), nb)
+        eB = np.broadcast_to(np.asarray(eps_B, np.float64), nb)
+        cat = np.broadcast_to(np.asarray(catalytic, np.int32), nb)
+        beads = (NetBead * max(1, nb))()
+        for j in range(nb):
+            beads[j].x[:] = [float(a) for a in xb[j]]
+            beads[j].v[:] = [float(a) for a in vb[j]]
+            beads[j].mass, beads[j].eps_A, beads[j].eps_B = float(mb[j]), float(eA[j]), float(eB[j])
+            beads[j].catalytic = int(cat[j])
+        nl = len(links)
+        la = (Bond * max(1, nl))()
+        for k, (a, b) in enumerate(links):
+            la[k].a, la[k].b, la[k].d = int(a), int(b), float(d[k])
+        col = (C.c_int32 * max(1, nl))(*[int(c) for c in colors])
+        self._check(self._lib.rmpcd_set_network(self._h, int(replica), beads, nb, la, col, nl, float(sigma),
+                                                float(tol), int(max_sweeps)))
+        self._net_nb = getattr(self, "_net_nb", {})
+        self._net_nb[int(replica)] = nb
+
+    def get_network(self, replica=0):
+        """Bead positions and velocities of a replica's network: (x, v)."""
+        nb = self._net_nb[int(replica)]
+        x = np.empty((nb, 3))
+        v = np.empty((nb, 3))
+        self._check(self._lib.rmpcd_get_network(self._h, int(replica), x.ctypes.data_as(C.POINTER(C.c_double)),
+                                                v.ctypes.data_as(C.POINTER(C.c_double)), nb))
+        return x, v
 
     def get_body(self, replica=0) -> dict:
         """State of a replica's body: x, v, q, l (numpy arrays)."""

@@ -97,6 +97,18 @@ struct rmpcd_system {
     int nb_max = 0;
     int grid_room = 0;                // shared-memory room for the lookup grids (0: global)
     std::vector<void *> body_allocs;  // bead and grid arrays
+    // bead networks (iterative RATTLE): per replica host copy (beads empty:
+    // none), links grouped by colour, and the device arrays of all networks
+    struct NetHost {
+        std::vector<rmpcd_net_bead> beads;
+        std::vector<int> la, lb, cs;
+        std::vector<double> dl;
+        NetDev dev{};
+    };
+    std::vector<NetHost> nets;
+    bool any_net = false;
+    size_t net_smem = 0;
+    std::vector<void *> net_allocs;
     double *col_rc = nullptr;         // writable colloid constants (body slots)
     float *col_rb = nullptr;
     size_t work_bytes = 0;            // md_work size
@@ -245,6 +257,7 @@ static void fill_rep(ReplicaDev &rp, const rmpcd_params &p)
     rp.n_col = p.n_colloids;
     rp.n_bond = p.n_bonds;
     rp.body = -1;
+    rp.net = -1;
     rp.bulk_on = p.bulk_rate > 0.0 ? 1 : 0;
     rp.has_g = (p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0) ? 1 : 0;
     rp.kT = p.kT;
@@ -337,6 +350,7 @@ void rmpcd_destroy(rmpcd_system *sys)
     if (sys->maxcnt_ev) cudaEventDestroy(sys->maxcnt_ev);
     for (void *p : sys->allocs) cudaFree(p);
     for (void *p : sys->body_allocs) cudaFree(p);
+    for (void *p : sys->net_allocs) cudaFree(p);
     for (auto &q : sys->pending) { sys->ev_pool.push_back(q.a); sys->ev_pool.push_back(q.b); }
     for (auto &q : sys->md_trials) { sys->ev_pool.push_back(q.a); sys->ev_pool.push_back(q.b); }
     for (cudaEvent_t e : sys->ev_pool) cudaEventDestroy(e);
@@ -606,6 +620,7 @@ static rmpcd_status create_system(rmpcd_system **out, int32_t precision, int32_t
     AL(&dIM, n_slot);
     AL(&dB, n_bond);
     AL(&d.body, n_replicas);
+    AL(&d.net, n_replicas);
     sys->work_bytes = (sys->mixed ? 64 : 80) * (size_t)(sys->any_colloids ? n_total : 1);
     AL(&work, sys->work_bytes);
     unsigned char *colsave = nullptr;
@@ -694,6 +709,7 @@ static rmpcd_status create_system(rmpcd_system **out, int32_t precision, int32_t
     sys->col_rc = dR;
     sys->col_rb = dRb;
     sys->bodies.resize(n_replicas);
+    sys->nets.resize(n_replicas);
     d.colInvM_f = dIM;
     d.bonds = dB;
     d.md_work = work;
@@ -813,6 +829,8 @@ static rmpcd_status check_errors(rmpcd_system *sys)
                     "(%d entries) ran full; the state is invalid", e[ERR_OVERFLOW], CP_MAX_CELL, sys->cap,
                     sys->d.ovf_cap);
     if (e[ERR_BOUNDS]) return fail(sys, RMPCD_ESTATE, "inconsistent bins (slot out of range); the state is invalid");
+    if (e[ERR_RATTLE])
+        return fail(sys, RMPCD_ESTATE, "a bead network's RATTLE stage did not converge within max_sweeps");
     if (e[ERR_SKIN]) return fail(sys, RMPCD_ESKIN, "a colloid moved further than skin in one interval (%u times)", e[ERR_SKIN]);
     return fail(sys, RMPCD_ESTATE, "device error");
 }
@@ -1005,6 +1023,10 @@ rmpcd_status rmpcd_stream(rmpcd_system *sys)
         launch_md_body(sys->mixed, sys->d, sys->nb_max, sys->grid_room, sys->step, sys->cur, 0, 0, sys->stream);
         if ((st = after_launch(sys, 1)) != RMPCD_OK) return st;
     }
+    if (sys->any_net) {
+        launch_md_network(sys->d, sys->net_smem, sys->step, sys->cur, 0, 0, sys->stream);
+        if ((st = after_launch(sys, 1)) != RMPCD_OK) return st;
+    }
     sys->has_sort = false;
     sys->obs_valid = false;
     return RMPCD_OK;
@@ -1013,7 +1035,8 @@ rmpcd_status rmpcd_stream(rmpcd_system *sys)
 rmpcd_status rmpcd_md_substep(rmpcd_system *sys, int32_t k)
 {
     if (!sys) return RMPCD_EINVAL;
-    if (sys->any_body) return fail(sys, RMPCD_EINVAL, "rmpcd_md_substep: not for replicas with a rigid body");
+    if (sys->any_body || sys->any_net)
+        return fail(sys, RMPCD_EINVAL, "rmpcd_md_substep: not for replicas with a rigid body or a bead network");
     int n_md = 0;
     for (const auto &rp : sys->rep) n_md = std::max(n_md, rp.n_md);
     if (k < 0 || k >= n_md) return fail(sys, RMPCD_EINVAL, "sub-step %d outside 0..%d", k, n_md - 1);
@@ -1129,6 +1152,12 @@ static int launch_interval(rmpcd_system *sys, int cur, int bcur, bool instrument
     if (sys->any_body) {
         if (instrument) tstart(sys, &ev);
         launch_md_body(sys->mixed, sys->d, sys->nb_max, sys->grid_room, STEP_DEVICE, cur, bcur, 1, sys->stream);
+        if (instrument) tstop(sys, 1, ev);
+        n += 1;
+    }
+    if (sys->any_net) {
+        if (instrument) tstart(sys, &ev);
+        launch_md_network(sys->d, sys->net_smem, STEP_DEVICE, cur, bcur, 1, sys->stream);
         if (instrument) tstop(sys, 1, ev);
         n += 1;
     }
@@ -1504,7 +1533,213 @@ static rmpcd_status upload_bodies(rmpcd_system *sys)
     return st;
 }
 
+// Centre of mass (sum in bead order) and reach (largest bead distance from it
+// plus the cut-off) of a network, as the FP64 definition computes them.
+static void net_com_reach(const std::vector<rmpcd_net_bead> &bd, double rc2, double X[3], double *reach)
+{
+    double s[3] = {0.0, 0.0, 0.0}, m = 0.0;
+    for (const auto &b : bd) {
+        m = m + b.mass;
+        for (int t = 0; t < 3; ++t) s[t] = s[t] + b.mass * b.x[t];
+    }
+    for (int t = 0; t < 3; ++t) X[t] = s[t] / m;
+    double rmax = 0.0;
+    for (const auto &b : bd) {
+        double e2 = 0.0;
+        for (int t = 0; t < 3; ++t) { const double e = b.x[t] - X[t]; e2 = e2 + e * e; }
+        if (sqrt(e2) > rmax) rmax = sqrt(e2);
+    }
+    *reach = rmax + sqrt(rc2);
+}
+
+// The arrays of every network, concatenated into fresh device buffers (the
+// offsets go into each network's constants), and the constants themselves.
+static rmpcd_status upload_networks(rmpcd_system *sys)
+{
+    std::vector<double> x, v, m, eps, dl;
+    std::vector<int> cat, la, lb, cs;
+    std::vector<NetDev> all(sys->n_rep);
+    size_t smem = 0;
+    for (int r = 0; r < sys->n_rep; ++r) {
+        auto &H = sys->nets[r];
+        if (H.beads.empty()) continue;
+        H.dev.bead_off = (int)m.size();
+        H.dev.link_off = (int)dl.size();
+        H.dev.color_off = (int)cs.size();
+        for (const auto &b : H.beads) {
+            for (int t = 0; t < 3; ++t) { x.push_back(b.x[t]); v.push_back(b.v[t]); }
+            m.push_back(b.mass);
+            eps.push_back(b.eps_A);
+            eps.push_back(b.eps_B);
+            cat.push_back(b.catalytic ? 1 : 0);
+        }
+        la.insert(la.end(), H.la.begin(), H.la.end());
+        lb.insert(lb.end(), H.lb.begin(), H.lb.end());
+        dl.insert(dl.end(), H.dl.begin(), H.dl.end());
+        cs.insert(cs.end(), H.cs.begin(), H.cs.end());
+        all[r] = H.dev;
+        smem = std::max(smem, md_network_smem(H.dev.nb, H.dev.nl, H.dev.ncol));
+    }
+    CK(cudaStreamSynchronize(sys->stream));
+    for (void *p : sys->net_allocs) cudaFree(p);
+    sys->net_allocs.clear();
+    auto put = [&](void **dst, const void *src, size_t bytes) -> rmpcd_status {
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
+        if (e != cudaSuccess) return cuda_check(sys, e, "cudaMalloc (networks)");
+        sys->net_allocs.push_back(p);
+        *dst = p;
+        return cuda_check(sys, cudaMemcpyAsync(p, src, bytes, cudaMemcpyHostToDevice, sys->stream), "upload (networks)");
+    };
+    rmpcd_status st = RMPCD_OK;
+    Dev &d = sys->d;
+    void *p = nullptr;
+    if (st == RMPCD_OK && (st = put(&p, x.data(), sizeof(double) * x.size())) == RMPCD_OK) d.net_x = (double *)p;
+    if (st == RMPCD_OK && (st = put(&p, v.data(), sizeof(double) * v.size())) == RMPCD_OK) d.net_v = (double *)p;
+    if (st == RMPCD_OK && (st = put(&p, m.data(), sizeof(double) * m.size())) == RMPCD_OK) d.net_m = (const double *)p;
+    if (st == RMPCD_OK && (st = put(&p, eps.data(), sizeof(double) * eps.size())) == RMPCD_OK) d.net_eps = (const double *)p;
+    if (st == RMPCD_OK && (st = put(&p, cat.data(), sizeof(int) * cat.size())) == RMPCD_OK) d.net_cat = (const int *)p;
+    if (st == RMPCD_OK && (st = put(&p, la.data(), sizeof(int) * la.size())) == RMPCD_OK) d.net_la = (const int *)p;
+    if (st == RMPCD_OK && (st = put(&p, lb.data(), sizeof(int) * lb.size())) == RMPCD_OK) d.net_lb = (const int *)p;
+    if (st == RMPCD_OK && (st = put(&p, dl.data(), sizeof(double) * dl.size())) == RMPCD_OK) d.net_d = (const double *)p;
+    if (st == RMPCD_OK && (st = put(&p, cs.data(), sizeof(int) * cs.size())) == RMPCD_OK) d.net_cs = (const int *)p;
+    if (st != RMPCD_OK) return st;
+    CK(cudaMemcpyAsync(d.net, all.data(), sizeof(NetDev) * sys->n_rep, cudaMemcpyHostToDevice, sys->stream));
+    sys->net_smem = smem;
+    CK(prepare_md_network(smem));
+    return RMPCD_OK;
+}
+
+// The current bead states of every network, from the device into the host
+// copies (before the arrays are rebuilt).
+static rmpcd_status fetch_networks(rmpcd_system *sys)
+{
+    if (!sys->any_net) return RMPCD_OK;
+    CK(cudaStreamSynchronize(sys->stream));
+    for (auto &H : sys->nets) {
+        if (H.beads.empty()) continue;
+        const int nb = (int)H.beads.size();
+        std::vector<double> x(3 * nb), v(3 * nb);
+        CK(cudaMemcpy(x.data(), sys->d.net_x + 3 * H.dev.bead_off, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(v.data(), sys->d.net_v + 3 * H.dev.bead_off, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost));
+        for (int j = 0; j < nb; ++j)
+            for (int t = 0; t < 3; ++t) { H.beads[j].x[t] = x[3 * j + t]; H.beads[j].v[t] = v[3 * j + t]; }
+    }
+    return RMPCD_OK;
+}
+
 extern "C" {
+
+rmpcd_status rmpcd_set_network(rmpcd_system *sys, int32_t replica, const rmpcd_net_bead *beads, int32_t n_beads,
+                               const rmpcd_bond *links, const int32_t *colors, int32_t n_links, double sigma,
+                               double tol, int32_t max_sweeps)
+{
+    if (!sys) return RMPCD_EINVAL;
+    if (replica < 0 || replica >= sys->n_rep) return fail(sys, RMPCD_EINVAL, "replica %d out of range", replica);
+    if (sys->mixed) return fail(sys, RMPCD_EINVAL, "a bead network needs an FP64 system");
+    const rmpcd_params &p = sys->params[replica];
+    if (p.n_colloids != 0 || p.n_bonds != 0 || p.walls || !sys->bodies[replica].beads.empty())
+        return fail(sys, RMPCD_EINVAL, "replica %d: a network needs a replica with no colloids, bonds, walls or body",
+                    replica);
+    if (n_beads < 1 || n_beads > RMPCD_MAX_NET_BEADS || !beads)
+        return fail(sys, RMPCD_EINVAL, "n_beads %d not in [1,%d]", n_beads, RMPCD_MAX_NET_BEADS);
+    if (n_links < 0 || (n_links > 0 && (!links || !colors))) return fail(sys, RMPCD_EINVAL, "links and colors required");
+    if (!(sigma > 0.0) || !std::isfinite(sigma) || !(tol > 0.0) || !(max_sweeps >= 1))
+        return fail(sys, RMPCD_EINVAL, "need sigma > 0, tol > 0, max_sweeps >= 1");
+    for (int j = 0; j < n_beads; ++j) {
+        const rmpcd_net_bead &b = beads[j];
+        bool ok = b.mass > 0.0 && std::isfinite(b.mass) && b.eps_A >= 0.0 && b.eps_B >= 0.0 &&
+                  std::isfinite(b.eps_A) && std::isfinite(b.eps_B);
+        for (int t = 0; t < 3; ++t) ok = ok && std::isfinite(b.x[t]) && std::isfinite(b.v[t]);
+        if (!ok) return fail(sys, RMPCD_EINVAL, "bead %d: finite state, mass > 0 and epsilons >= 0 required", j);
+    }
+    int ncol = 0;
+    for (int k = 0; k < n_links; ++k) {
+        const rmpcd_bond &l = links[k];
+        if (l.a < 0 || l.b < 0 || l.a >= n_beads || l.b >= n_beads || l.a == l.b || !(l.d > 0.0) || !std::isfinite(l.d) ||
+            colors[k] < 0 || colors[k] >= 4 * n_beads)
+            return fail(sys, RMPCD_EINVAL, "link %d invalid", k);
+        ncol = std::max(ncol, colors[k] + 1);
+    }
+    // links of one colour must share no bead
+    std::vector<int> seen((size_t)ncol * n_beads, 0);
+    for (int k = 0; k < n_links; ++k)
+        for (int e : {links[k].a, links[k].b}) {
+            int &s = seen[(size_t)colors[k] * n_beads + e];
+            if (s) return fail(sys, RMPCD_EINVAL, "link %d: bead %d appears twice in colour %d", k, e, colors[k]);
+            s = 1;
+        }
+    const double rc2 = sigma * sigma * cbrt(2.0);
+    std::vector<rmpcd_net_bead> bd(beads, beads + n_beads);
+    double X[3], reach;
+    net_com_reach(bd, rc2, X, &reach);
+    if (2.0 * reach + 2.0 * p.skin >= (double)std::min(p.L[0], std::min(p.L[1], p.L[2])))
+        return fail(sys, RMPCD_EINVAL, "replica %d: box too small for the network's reach", replica);
+    if (md_network_smem(n_beads, n_links, ncol) > 200 * 1024)
+        return fail(sys, RMPCD_EINVAL, "network too large for shared memory");
+    rmpcd_status st = unprime(sys);
+    if (st != RMPCD_OK) return st;
+    CK(cudaStreamSynchronize(sys->stream));
+    drop_graphs(sys);
+    if ((st = fetch_networks(sys)) != RMPCD_OK) return st;
+    auto &H = sys->nets[replica];
+    H.beads = bd;
+    H.la.clear(); H.lb.clear(); H.dl.clear(); H.cs.assign(1, 0);
+    for (int c = 0; c < ncol; ++c) {
+        for (int k = 0; k < n_links; ++k)
+            if (colors[k] == c) { H.la.push_back(links[k].a); H.lb.push_back(links[k].b); H.dl.push_back(links[k].d); }
+        H.cs.push_back((int)H.la.size());
+    }
+    std::memset(&H.dev, 0, sizeof H.dev);
+    H.dev.nb = n_beads;
+    H.dev.nl = n_links;
+    H.dev.ncol = ncol;
+    H.dev.max_sweeps = max_sweeps;
+    H.dev.sigma = sigma;
+    H.dev.rc2 = rc2;
+    H.dev.tol = tol;
+    sys->any_net = true;
+    if ((st = upload_networks(sys)) != RMPCD_OK) return st;
+    // the network's colloid slot: centre of mass and reach for the near test
+    const int g = sys->n_col + replica;
+    cudaStream_t s = sys->stream;
+    CK(cudaMemcpyAsync(sys->d.colX + 3 * g, X, sizeof(double) * 3, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(sys->col_rc + g, &reach, sizeof(double), cudaMemcpyHostToDevice, s));
+    ReplicaDev &rp = sys->rep[replica];
+    rp.n_col = 1;
+    rp.col_off = g;
+    rp.net = replica;
+    CK(cudaMemcpyAsync(const_cast<ReplicaDev *>(sys->d.rep) + replica, &rp, sizeof rp, cudaMemcpyHostToDevice, s));
+    // working state of the near particles
+    const size_t need = 80 * (size_t)std::max(sys->n_total, 1);
+    if (sys->work_bytes < need) {
+        CK(cudaStreamSynchronize(s));
+        auto it = std::find(sys->allocs.begin(), sys->allocs.end(), sys->d.md_work);
+        if (it != sys->allocs.end()) sys->allocs.erase(it);
+        cudaFree(sys->d.md_work);
+        sys->d.md_work = nullptr;
+        unsigned char *w = nullptr;
+        if ((st = dalloc(sys, &w, need)) != RMPCD_OK) return st;
+        sys->d.md_work = w;
+        sys->work_bytes = need;
+    }
+    CK(cudaStreamSynchronize(s));
+    return RMPCD_OK;
+}
+
+rmpcd_status rmpcd_get_network(rmpcd_system *sys, int32_t replica, double *x, double *v, int32_t n_beads)
+{
+    if (!sys) return RMPCD_EINVAL;
+    if (replica < 0 || replica >= sys->n_rep) return fail(sys, RMPCD_EINVAL, "replica %d out of range", replica);
+    const auto &H = sys->nets[replica];
+    if (H.beads.empty()) return fail(sys, RMPCD_EINVAL, "replica %d has no network", replica);
+    if (n_beads != (int)H.beads.size() || !x || !v)
+        return fail(sys, RMPCD_EINVAL, "replica %d's network has %d beads", replica, (int)H.beads.size());
+    const size_t o = 3 * (size_t)H.dev.bead_off;
+    CK(cudaMemcpyAsync(x, sys->d.net_x + o, sizeof(double) * 3 * n_beads, cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaMemcpyAsync(v, sys->d.net_v + o, sizeof(double) * 3 * n_beads, cudaMemcpyDeviceToHost, sys->stream));
+    return check_errors(sys);
+}
 
 rmpcd_status rmpcd_set_body(rmpcd_system *sys, int32_t replica, const rmpcd_body *body, const rmpcd_bead *beads)
 {
@@ -1512,8 +1747,9 @@ rmpcd_status rmpcd_set_body(rmpcd_system *sys, int32_t replica, const rmpcd_body
     if (replica < 0 || replica >= sys->n_rep) return fail(sys, RMPCD_EINVAL, "replica %d out of range", replica);
     if (!body || !beads) return fail(sys, RMPCD_EINVAL, "body and beads are required");
     const rmpcd_params &p = sys->params[replica];
-    if (p.n_colloids != 0 || p.n_bonds != 0 || p.walls)
-        return fail(sys, RMPCD_EINVAL, "replica %d: a body needs a replica created with no colloids, bonds or walls", replica);
+    if (p.n_colloids != 0 || p.n_bonds != 0 || p.walls || !sys->nets[replica].beads.empty())
+        return fail(sys, RMPCD_EINVAL, "replica %d: a body needs a replica created with no colloids, bonds, walls or network",
+                    replica);
     const int nb = body->n_beads;
     if (nb < 1 || nb > RMPCD_MAX_BEADS) return fail(sys, RMPCD_EINVAL, "n_beads %d not in [1,%d]", nb, RMPCD_MAX_BEADS);
     const double mb = body->bead_mass, sig = body->sigma;

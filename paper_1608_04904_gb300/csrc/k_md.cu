@@ -804,7 +804,7 @@ __global__ void __launch_bounds__(MDGeom<CS>::NT, 1) k_md(Dev d, uint32_t step, 
     if (tid == 0) s_rp = d.rep[r];
     __syncthreads();
     const ReplicaDev &rp = s_rp;
-    if (rp.n_col == 0 || rp.body >= 0) return;   // uniform over the cluster (bodies: k_md_body)
+    if (rp.n_col == 0 || rp.body >= 0 || rp.net >= 0) return;   // uniform over the cluster (bodies, networks: own kernels)
     if (tid == 0) {
         S.nc = rp.n_col;
         S.nbond = rp.n_bond;

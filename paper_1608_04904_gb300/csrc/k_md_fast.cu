@@ -693,7 +693,7 @@ __global__ void __launch_bounds__(MDF_NT, 1) k_md_fast(Dev d, uint32_t step, int
     if (tid == 0) s_rp = d.rep[r];
     __syncthreads();
     const ReplicaDev &rp = s_rp;
-    if (rp.n_col == 0 || rp.body >= 0) return;   // uniform over the cluster (bodies: k_md_body)
+    if (rp.n_col == 0 || rp.body >= 0 || rp.net >= 0) return;   // uniform over the cluster (bodies, networks: own kernels)
     const int nc = rp.n_col, nbond = rp.n_bond, n_md = rp.n_md;
     if (tid == 0) {
         S.nn = min(d.near_count[r], rp.n_part);

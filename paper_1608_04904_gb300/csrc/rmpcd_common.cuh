@@ -44,7 +44,7 @@ constexpr uint32_t ID_MASK = (1u << 29) - 1u;
 
 enum Purpose : uint32_t { P_SHIFT = 1, P_ROT = 2, P_REACT = 3, P_THERMO = 4, P_VIRT = 5, P_CAT = 6 };
 
-enum ErrSlot { ERR_OVERFLOW = 0, ERR_SKIN = 1, ERR_TIMEOUT = 2, ERR_BOUNDS = 3, ERR_COUNT = 8 };
+enum ErrSlot { ERR_OVERFLOW = 0, ERR_SKIN = 1, ERR_TIMEOUT = 2, ERR_BOUNDS = 3, ERR_RATTLE = 4, ERR_COUNT = 8 };
 
 // Per-replica constants, computed on the host once.
 struct ReplicaDev {
@@ -58,6 +58,7 @@ struct ReplicaDev {
     int bulk_on, has_g;
     int thr_off;
     int body;               // index of the replica's rigid bead body, -1: none
+    int net;                // index of the replica's bead network (iterative RATTLE), -1: none
     double kT, tau, dt, hdt, ca, sa, omc;
     double g[3];
     double gnorm, cat_thr, skin;
@@ -73,6 +74,16 @@ struct ReplicaDev {
 };
 
 struct BondDev { int a, b; double d; };
+
+// A bead network of one replica (the Janus particle under iterative RATTLE):
+// beads [bead_off, bead_off + nb) of the network arrays, links [link_off,
+// link_off + nl) grouped by colour (colour c: links cs[c] .. cs[c + 1] of the
+// colour starts at color_off), the beads' WCA sigma and cut-off^2, and the
+// RATTLE tolerance and sweep bound.
+struct NetDev {
+    int nb, bead_off, nl, link_off, ncol, color_off, max_sweeps, pad;
+    double sigma, rc2, tol;
+};
 
 // The replica constants the mixed per-particle code reads (flight, cell key,
 // minimum image, near test), as a value the compiler keeps in registers: a
@@ -173,6 +184,13 @@ struct Dev {
     MdWideGlobal *md_wide;       // wide MD kernel scratch
     Ctl *ctl;                    // interval control (step, cell-pass launch counter)
     unsigned int *maxcnt;        // largest cell count seen (bucket-width tuner)
+    NetDev *net;                 // bead networks
+    double *net_x, *net_v;       // [3 * bead] network bead positions (unwrapped), velocities
+    const double *net_m, *net_eps;   // [bead], [2 * bead] (eps_A, eps_B)
+    const int *net_cat;          // [bead]
+    const int *net_la, *net_lb;  // [link] bead indices within the network, grouped by colour
+    const double *net_d;         // [link] lengths
+    const int *net_cs;           // colour starts per network
     BodyDev *body;               // rigid bead bodies
     const double *bead_b;        // [3 * bead] body-frame bead positions
     const double *bead_eps;      // [2 * bead] eps_A, eps_B

@@ -63,6 +63,13 @@ void launch_md_body(bool mixed, const Dev &d, int nb_max, int grid_bytes, uint32
                     int do_bin, cudaStream_t s);
 cudaError_t prepare_md_body(bool mixed, int nb_max, int grid_bytes);
 int md_body_grid_room(bool mixed, int nb_max, long long grid_entries_max);
+// Bead networks (FP64 path): one CTA per replica (replicas without a network
+// return at once) with `smem` bytes of dynamic shared memory
+// (md_network_smem of the largest network; prepare_md_network sets the
+// kernel's limit, not a stream operation).
+size_t md_network_smem(int nb, int nl, int ncol);
+cudaError_t prepare_md_network(size_t smem);
+void launch_md_network(const Dev &d, size_t smem, uint32_t step, int rbuf, int bbuf, int do_bin, cudaStream_t s);
 void launch_set_state(bool mixed, const Dev &d, int replica, int n, const double *x, const double *v,
                       const uint8_t *flags, int rbuf, cudaStream_t s);
 void launch_get_state(bool mixed, const Dev &d, int replica, int n, int rbuf, double *x, double *v, uint8_t *flags,

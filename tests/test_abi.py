@@ -41,7 +41,7 @@ def test_struct_layouts_match_header(api, tmp_path):
         pytest.skip("gcc not available")
     structs = {"rmpcd_params": api.Params, "rmpcd_colloid": api.Colloid, "rmpcd_bond": api.Bond,
                "rmpcd_obs": api.Obs, "rmpcd_timers": api.Timers, "rmpcd_body": api.Body, "rmpcd_bead": api.Bead,
-               "rmpcd_profile_bin": api.ProfileBin}
+               "rmpcd_profile_bin": api.ProfileBin, "rmpcd_net_bead": api.NetBead}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rmpcd.h"', "int main(void){"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
