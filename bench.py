@@ -83,6 +83,18 @@ def workload(name, precision, seed_offset=0, n_replicas=None):
                 "(seed 4), rho 10, one rigid Janus particle each (100-300 beads on a sphere of radius 4, "
                 "sigma_b 1, catalytic hemisphere A->B), alpha 130 deg, tau 0.5, 25 MD sub-steps dt 0.02")
         return reps, desc
+    elif name == "network64":
+        sides = synth.batch_sides(256, seed=4)[:64][:n_replicas]
+        reps = []
+        for r, L in enumerate(sides):
+            cfg, body = synth.batch_janus(L, seed=4 + r + 1000 * seed_offset, precision="fp64")
+            body = dict(body, network=synth.janus_network(body))
+            reps.append((cfg, [], [], body))
+        desc = (f"{len(sides)} independent replicas (the first of batch256: same sides, seeds and solvent), each "
+                "Janus particle a bead network held by iterative RATTLE (links to each bead's ring of neighbours, "
+                "edge-coloured; tolerance 1e-12) instead of a rigid body; FP64 (the network integrator's "
+                "precision), 25 MD sub-steps dt 0.02")
+        return reps, desc
     else:
         raise SystemExit(f"unknown workload {name}")
     return [(cfg, col, bonds, None) for cfg, col, bonds in reps], desc
@@ -96,10 +108,40 @@ def initial_state(rep):
     return synth.solvent(cfg, excl, seed=cfg["seed"] + 100)
 
 
+class _NetworkOracle:
+    """The oracle's interval of a bead-network replica followed by its
+    collision step (the same sequence a GPU interval runs)."""
+
+    def __init__(self, oracle, cfg, state, net):
+        import numpy as np
+        from paper_1608_04904_gb300 import network
+        x, v, fl = state
+        links, d = net["links"], np.asarray(net["d"])
+        order = network.order_by_color(links, network.color_links(links, len(net["xb"])))
+        self.orc = oracle
+        self.net = oracle.Network(net["xb"], net["vb"], net["mb"], net["eps_A"], net["eps_B"], net["catalytic"],
+                                  net["sigma"], [links[k] for k in order], d[order])
+        self.o = oracle.OracleSystem(cfg, x, v, fl)
+        self.cfg = cfg
+
+    def step(self, k):
+        o = self.o
+        for _ in range(k):
+            rc, _ = self.orc.interval_network(self.cfg, o.x, o.v, o.flags, o.id, self.net, step=o.step_index)
+            if rc != 0:
+                raise RuntimeError(f"oracle network interval status {rc}")
+            o.shift_and_sort()
+            o.collide()
+            o.react()
+            o.step_index += 1
+
+
 def oracle_system(oracle, rep, state):
     from paper_1608_04904_gb300 import synth
     cfg, col, bonds, body = rep
     x, v, fl = state
+    if body is not None and "network" in body:
+        return _NetworkOracle(oracle, cfg, state, body["network"])
     return oracle.OracleSystem(cfg, x, v, fl, colloids=synth.colloid_arrays(col) if col else None, bonds=bonds,
                                body=body)
 
@@ -331,11 +373,19 @@ def run_reference(args, ws, rank):
 
 
 def make_system(api, reps, states, precision, stream):
-    s = api.System([dict(cfg=cfg, n=len(st[0]), colloids=col, bonds=bonds, body=body)
+    from paper_1608_04904_gb300 import network
+    rigid = lambda b: None if b is not None and "network" in b else b
+    s = api.System([dict(cfg=cfg, n=len(st[0]), colloids=col, bonds=bonds, body=rigid(body))
                     for (cfg, col, bonds, body), st in zip(reps, states)], precision=precision,
                    bucket_cap=reps[0][0].get("bucket_cap", 0), stream=stream)
     for r, (x, v, fl) in enumerate(states):
         s.set_state(r, x, v, fl)
+    for r, (cfg, col, bonds, body) in enumerate(reps):
+        if body is not None and "network" in body:
+            net = body["network"]
+            colors = network.color_links(net["links"], len(net["xb"]))
+            s.set_network(r, net["xb"], net["vb"], net["mb"], net["eps_A"], net["eps_B"], net["catalytic"],
+                          net["sigma"], net["links"], net["d"], colors)
     return s
 
 
@@ -360,7 +410,16 @@ def _timed_run(api, torch, reps, states, precision, steps, warmup, flush, dev_in
     torch.cuda.synchronize()
     # rigid bodies: centre of mass before the timed steps (for the MSD)
     body_reps = [r for r, rep in enumerate(reps) if rep[3] is not None]
-    x0 = [s.get_body(r)["x"] for r in body_reps]
+
+    def com(r):
+        body = reps[r][3]
+        if "network" not in body:
+            return s.get_body(r)["x"]
+        xb, _ = s.get_network(r)
+        m = body["network"]["mb"]
+        return (m[:, None] * xb).sum(0) / m.sum()
+
+    x0 = [com(r) for r in body_reps]
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     launches0 = s.launch_count()
@@ -382,7 +441,7 @@ def _timed_run(api, torch, reps, states, precision, steps, warmup, flush, dev_in
     msd = None
     if body_reps:
         import numpy as np
-        d2 = np.array([float(((s.get_body(r)["x"] - a) ** 2).sum()) for r, a in zip(body_reps, x0)])
+        d2 = np.array([float(((com(r) - a) ** 2).sum()) for r, a in zip(body_reps, x0)])
         msd = {"intervals": steps, "time": steps * reps[body_reps[0]][0]["tau"], "mean": float(d2.mean()),
                "min": float(d2.min()), "max": float(d2.max()), "replicas": len(d2),
                "per_replica_first8": [round(float(v), 6) for v in d2[:8]]}
@@ -443,7 +502,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batch256",
-                    choices=["dimer32", "dimer64", "sphere16", "poiseuille128", "thermal", "batch256"])
+                    choices=["dimer32", "dimer64", "sphere16", "poiseuille128", "thermal", "batch256",
+                             "network64"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--md-cluster", type=int, default=0, help="MD CTAs per replica (0 = autotune)")
     ap.add_argument("--md-kernel", type=int, default=0, help="MD kernel: 0 auto, 1 general, 2 few-colloid")
@@ -456,6 +516,8 @@ def main():
                     help="batch256 only: keep the first N replicas (a smaller case for profiling)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.workload == "network64":
+        args.precision = "fp64"   # the network integrator is FP64 only
     ws, rank, local = dist_setup()
 
     if args.impl == "reference":
@@ -495,7 +557,9 @@ def main():
     dominant = max(phases, key=lambda k: phases[k]["ms"])
     peak, peak_src = measured_peaks()
     kernel_names = dict(KERNEL_NAMES)
-    if any(r[3] is not None for r in reps):
+    if any(r[3] is not None and "network" in r[3] for r in reps):
+        kernel_names["md"] = "k_md_network"
+    elif any(r[3] is not None for r in reps):
         kernel_names["md"] = "k_md_body"
     elif obs["md_kernel"] == 2:
         kernel_names["md"] = "k_md_fast"

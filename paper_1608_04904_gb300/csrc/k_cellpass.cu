@@ -6,12 +6,18 @@
 // The work is cut into tiles of CPT consecutive cells of one replica.  As many
 // CTAs as fit on the GPU run persistently, each taking tiles in ticket order.
 // A CTA stages a tile's particles in shared memory (in batches of whole cells
-// when they exceed the staging area) in the order they arrive, then ranks the
-// particles of each cell by id: that rank is the canonical order in which a
-// cell's velocities are summed, its reaction partner counted and (flat
-// layout) its records written.  Stages run with all threads of the CTA: one
-// thread per particle for the gather, rotation, write and binning, one thread
-// per cell for the cell sums and the per-cell draws.
+// when they exceed the staging area) in the order they arrive.  The result of
+// a cell must not depend on that order:
+//   FP64: the particles of each cell are ranked by id, the canonical order in
+//     which the cell's velocities are summed (the order of the definition),
+//     its reaction partner counted and (flat layout) its records written;
+//   mixed: the cell's velocity sum is taken in units of 2^-24 as an integer
+//     sum (exact in any order) and the reaction partner is found by comparing
+//     ids, so the fused pass needs no ranks; MPC-AT cells (per-particle
+//     draws), observable passes and the flat layout's write order still rank.
+// Stages run with all threads of the CTA: one thread per particle for the
+// gather, rotation, write and binning, one thread per cell for the cell sums
+// and the per-cell draws.
 //
 // Two layouts (see Dev):
 //   fused run (FUSED): a cell's records are read contiguously from its row;
@@ -152,6 +158,15 @@ __device__ __forceinline__ void cp_async_rec(Rec *dst, const Rec *src)
         cp_async16(reinterpret_cast<char *>(dst) + 16 * q, reinterpret_cast<const char *>(src) + 16 * q);
 }
 
+// v * 2^24 rounded to an integer, for any v: an integer part and a fraction,
+// each converted exactly (adding an integer commutes with the rounding).
+__device__ __forceinline__ long long fixed24(float v)
+{
+    if (fabsf(v) < 128.0f) return (long long)__float2int_rn(v * 0x1p24f);
+    const float t = truncf(v);
+    return ((long long)__float2int_rz(t) << 24) + (long long)__float2int_rn((v - t) * 0x1p24f);
+}
+
 // Staging place of the i-th particle of a cell of n in canonical order
 // (clamped to the cell: a state with colliding ids leaves gaps in perm).
 __device__ __forceinline__ int canon(const unsigned short *pm, int i, int n)
@@ -169,6 +184,7 @@ struct TileShared {
     int tile, next_tile, r, base;
     uint32_t epoch, step;     // this launch's counter and collision index (from the control block)
     int cnt[CPT], ls[CPT + 1], wt[CPT / 32];
+    int __align__(16) cnt_next[CPT];   // the next tile's counts (asynchronous copy during this tile)
     double sh[3], shn[3];     // fp64 path
     float shf[3], shnf[3];
     R vcm[CPT][3], ax[CPT][3];
@@ -257,15 +273,39 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
             for (int k = 0; k < rp.n_slabs; ++k)
                 if (cx >= rp.slab_lo[k] && cx < rp.slab_hi[k]) { slab = k; break; }
         const bool nearq = want_near && n > 0;
-        // the cell's velocity sum, in canonical order: for the SRD collision
-        // and for the near bound (stage D leaves the velocities unchanged
-        // outside MPC-AT slabs, where the bound is not taken)
+        // the cell's velocity sum: for the SRD collision and for the near
+        // bound (stage D leaves the velocities unchanged outside MPC-AT
+        // slabs, where the bound is not taken).  FP64: in canonical order.
+        // Mixed: each component rounded to a multiple of 2^-24 and summed as
+        // a 64-bit integer -- exact, so the same in any order -- then rounded
+        // once to FP32 (|v| < 128 takes one conversion; wider values or
+        // non-finite ones take the split conversion for the whole cell).
         R sum[3] = {R(0), R(0), R(0)};
-        if (slab < 0 && (coll || nearq))
-            for (int i = 0; i < n; ++i) {
-                const int q = canon(pm, i, n);
-                for (int k = 0; k < 3; ++k) sum[k] = sum[k] + cr[q].v[k];
+        if (slab < 0 && (coll || nearq)) {
+            if constexpr (MIXED) {
+                long long fx[3] = {0ll, 0ll, 0ll};
+                bool wide = false;
+#pragma unroll 2
+                for (int i = 0; i < n; ++i)
+                    for (int k = 0; k < 3; ++k) {
+                        const float t = cr[i].v[k] * 0x1p24f;
+                        wide |= !(fabsf(t) < 0x1p31f);
+                        fx[k] += (long long)__float2int_rn(t);
+                    }
+                if (wide) {
+                    // a speed of 128 or more (or not finite): the split conversion
+                    fx[0] = fx[1] = fx[2] = 0ll;
+                    for (int i = 0; i < n; ++i)
+                        for (int k = 0; k < 3; ++k) fx[k] += fixed24(cr[i].v[k]);
+                }
+                for (int k = 0; k < 3; ++k) sum[k] = exact_to_R(fx[k], R(0)) * (R)0x1p-24;
+            } else {
+                for (int i = 0; i < n; ++i) {
+                    const int q = canon(pm, i, n);
+                    for (int k = 0; k < 3; ++k) sum[k] = sum[k] + cr[q].v[k];
+                }
             }
+        }
         int nbB = -1;   // B count, when the near bound's loop has taken it
         unsigned char res = 0;   // species reservoir of the cell's y column (chemotactic set-up)
         if ((opts & CP_REACT) && (rp.res_y[0] < rp.res_y[1] || rp.res_y[2] < rp.res_y[3])) {
@@ -348,11 +388,23 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
                 if ((unsigned long long)w.x < d.bulk_thr[rp.thr_off + nbB]) {
                     // the pick-th B particle of the cell in canonical order
                     const int pick = (int)(((unsigned long long)w.y * (unsigned long long)nbB) >> 32);
-                    for (int i = 0, seen = 0; i < n; ++i) {
-                        const int q = canon(pm, i, n);
-                        if (cr[q].fid & F_B) {
-                            if (seen == pick) { T.react[c] = lo + q; break; }
-                            ++seen;
+                    if constexpr (MIXED) {
+                        // without ranks: the B particle with pick B particles of smaller id
+                        for (int q = 0; q < n; ++q) {
+                            if (!(cr[q].fid & F_B)) continue;
+                            const uint32_t idq = cr[q].fid & ID_MASK;
+                            int below = 0;
+                            for (int k = 0; k < n; ++k)
+                                below += ((cr[k].fid & F_B) && (cr[k].fid & ID_MASK) < idq) ? 1 : 0;
+                            if (below == pick) { T.react[c] = lo + q; break; }
+                        }
+                    } else {
+                        for (int i = 0, seen = 0; i < n; ++i) {
+                            const int q = canon(pm, i, n);
+                            if (cr[q].fid & F_B) {
+                                if (seen == pick) { T.react[c] = lo + q; break; }
+                                ++seen;
+                            }
                         }
                     }
                 }
@@ -441,7 +493,7 @@ __device__ void near_candidates(TileShared<MIXED> &T, int gt, int cb, int ce)
 template <bool MIXED, bool MANY, bool FUSED>
 __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXED> &T, int gt, int cb, int ce,
                             typename Traits<MIXED>::Rec *srec, int *ent, unsigned short *perm,
-                            unsigned char *cellof, double acc[8], bool &have_base, int &npref, bool &pref, bool ovf)
+                            unsigned char *cellof, double acc[8], bool &have_base, bool &pref, bool ovf)
 {
     using Rec = typename Traits<MIXED>::Rec;
     using R = typename Traits<MIXED>::R;
@@ -471,9 +523,10 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
     }
     __syncthreads();
     if (pref) {
-        // the next tile's counts, read now and used when this tile is done
+        // the next tile's counts, copied now (no register waits on them)
+        // and read when this tile is done; stage B's wait covers the copy
         const int nt = T.next_tile;
-        if (gt < CPT && nt < d.n_tiles) npref = d.count[a.cur][nt * CPT + gt];
+        if (gt < CPT / 4 && nt < d.n_tiles) cp_async16(&T.cnt_next[4 * gt], d.count[a.cur] + (long long)nt * CPT + 4 * gt);
         pref = false;
     }
     // B: every particle's record into the staging area, in arrival order
@@ -564,11 +617,14 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
     // latched --, two ranks coincide and the reads of perm below clamp to the
     // cell, so every access stays in the staging area).  Stage C may rewrite
     // a record meanwhile: only its flag bits change, not the id read here.
+    // The mixed fused pass ranks only for MPC-AT replicas and observable
+    // passes (the flat layout ranks for its write order).
+    const bool need_rank = !MIXED || !FUSED || rp.n_slabs > 0 || (opts & CP_OBS);
     int rk[K];
 #pragma unroll
     for (int u = 0; u < K; ++u) {
         const int j = gt + u * G;
-        if (j < nb) {
+        if (need_rank && j < nb) {
             const int c = cb + cellof[j];
             const int lo = T.ls[c] - pofs, n = T.cnt[c];
             const uint32_t id = srec[j].fid & ID_MASK;
@@ -824,8 +880,7 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
     // the chain ticket -> counts is off the critical path; the replica's
     // constants are reloaded only when the replica changes.
     int cur_r = -1;
-    int npref = 0;
-    if (tid < CPT && T.tile < d.n_tiles) npref = d.count[a.cur][T.tile * CPT + tid];
+    if (tid < CPT && T.tile < d.n_tiles) T.cnt_next[tid] = d.count[a.cur][T.tile * CPT + tid];
     for (;;) {
         const int tile = T.tile;
         if (tile >= d.n_tiles) break;
@@ -862,7 +917,7 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
         int x = 0;
         bool big = false;   // a cell of the tile holds more than cap
         if (tid < CPT) {
-            int n = npref;
+            int n = T.cnt_next[tid];
             d.count[a.cur][gc0 + tid] = 0;
             const int mraw = __reduce_max_sync(0xffffffffu, n);
             if (lane == 0 && mraw > 0) atomicMax(d.maxcnt, (unsigned int)mraw);   // for the bucket-width tuner
@@ -902,8 +957,8 @@ __global__ void __launch_bounds__(CP_THREADS, MIXED ? 3 : 2) k_cellpass(Dev d, C
         bool have_base = false, pref = true;
         for (int cb = 0; cb < CPT;) {
             const int ce = batch_end(T.ls, cb, CPT, TP);
-            cells_batch<MIXED, MANY, FUSED>(d, a, T, tid, cb, ce, srec, ent, perm, cellof, acc, have_base, npref,
-                                            pref, tile_ovf);
+            cells_batch<MIXED, MANY, FUSED>(d, a, T, tid, cb, ce, srec, ent, perm, cellof, acc, have_base, pref,
+                                            tile_ovf);
             cb = ce;
         }
 

@@ -270,6 +270,29 @@ def janus_body(nb: int, center, seed: int, radius: float = 4.0, rho: float = 10.
             "catalytic": cat, "bead_mass": m_b, "sigma": sigma}
 
 
+def janus_network(body, radius: float = 4.0, factor: float = 1.6) -> dict:
+    """The beads of a Janus body description (``janus_body`` of the same
+    radius) as a bead network for iterative RATTLE: positions on the
+    construction-frame sphere about the body's centre, every bead moving with
+    the body's centre-of-mass velocity (a rigid translation, so the links hold
+    and their velocities agree from the start), the body's masses,
+    couplings and catalytic flags, and links joining every bead pair closer
+    than `factor` times the median nearest-neighbour distance (``bead_links``).
+    At 1.6 a shell of 100-300 beads has more than 3 nb - 6 links, so the
+    network is rigid; the sparser ring-of-neighbours network (1.35) leaves
+    floppy modes, along which the iterative RATTLE can need more than 10^4
+    sweeps."""
+    nb = len(body["b"])
+    b0 = fibonacci_sphere(nb, radius)
+    b0 = b0 - b0.mean(axis=0)
+    links, d = bead_links(b0, factor=factor)
+    return {"xb": np.asarray(body["x"], np.float64) + b0,
+            "vb": np.broadcast_to(np.asarray(body["v"], np.float64), (nb, 3)).copy(),
+            "mb": np.full(nb, float(body["bead_mass"])), "eps_A": np.asarray(body["eps_A"], np.float64),
+            "eps_B": np.asarray(body["eps_B"], np.float64), "catalytic": np.asarray(body["catalytic"], np.int32),
+            "sigma": float(body["sigma"]), "links": links, "d": np.asarray(d, np.float64)}
+
+
 def body_exclusion(body) -> list:
     """A pseudo-colloid whose cut-off covers the body's bounding sphere, for
     ``solvent(..., col=...)``: no solvent starts inside the bead shell."""
