@@ -201,6 +201,24 @@ rmpcd_status rmpcd_set_state(rmpcd_system *sys, int32_t replica, const double *x
 rmpcd_status rmpcd_get_state(rmpcd_system *sys, int32_t replica, double *x, double *v, uint8_t *flags,
                              uint32_t *id, int32_t *cell, int64_t n, int32_t on_device);
 
+/* The solvent of every replica in one call: the arrays of rmpcd_set_state /
+ * rmpcd_get_state concatenated in replica order (replica r's particles start
+ * at the sum of params.n_solvent over the replicas before it; n = that sum
+ * over all replicas).  Host arrays travel in one copy each way through a
+ * staging area of n particles (allocated on the first host call, freed with
+ * the system) with one synchronisation per call, where the per-replica calls
+ * synchronise once per replica; device arrays are read or written in place.
+ * The results are those of the per-replica calls, replica by replica.
+ * rmpcd_set_state_all: flags may be NULL (all A); the host arrays may be
+ * reused when it returns.  rmpcd_get_state_all: any output pointer may be
+ * NULL; synchronises and returns latched device errors.  Errors: EINVAL (n
+ * is not the system's total), ENOMEM (staging area), ECUDA, and for
+ * rmpcd_get_state_all EOVERFLOW, ESKIN, ETIMEOUT. */
+rmpcd_status rmpcd_set_state_all(rmpcd_system *sys, const double *x, const double *v, const uint8_t *flags,
+                                 int64_t n, int32_t on_device);
+rmpcd_status rmpcd_get_state_all(rmpcd_system *sys, double *x, double *v, uint8_t *flags, uint32_t *id,
+                                 int32_t *cell, int64_t n, int32_t on_device);
+
 /* Colloids of one replica (host arrays of params.n_colloids entries). */
 rmpcd_status rmpcd_set_colloids(rmpcd_system *sys, int32_t replica, const rmpcd_colloid *c, int32_t n);
 rmpcd_status rmpcd_get_colloids(rmpcd_system *sys, int32_t replica, rmpcd_colloid *c, int32_t n);

@@ -542,8 +542,8 @@ static void colloid_colloid(const orc_params *p, const colloids_t *cs, const dou
         }
 }
 
-/* RATTLE (Andersen 1983), exact for one bond between two bodies (§1.4:
- * "exactly for the dimer motor").  Position stage: move along the old bond
+/* RATTLE (Andersen 1983), exact for one bond between two bodies (§1.4 solves
+ * the dimer motor's single bond exactly).  Position stage: move along the old bond
  * vector so that |X_a - X_b| = d; velocity stage: remove the relative
  * velocity along the bond. */
 static void rattle_pos(colloids_t *cs, const double (*Xold)[3], double dt)
@@ -1128,11 +1128,11 @@ double orc_body_forces(const orc_params *p, int64_t n, const double *x, const ui
 }
 
 /* ------------------------------------------------------------------------ */
-/* Iterative RATTLE for beads linked by fixed distances (§1.4 names RATTLE   */
-/* "in its iterative implementation" for the Janus particle; Andersen 1983). */
-/* Each link in turn is corrected, sweeping the list until every link holds  */
-/* within the tolerance.  This models the Janus particle as the paper does;  */
-/* the rigid body above is the reading the GPU path implements today.        */
+/* Iterative RATTLE for beads linked by fixed distances (§1.4 integrates the */
+/* Janus particle's bead network with the iterative form of RATTLE; Andersen */
+/* 1983).  Each link in turn is corrected, sweeping the list until every     */
+/* link holds within the tolerance.  This models the Janus particle as the   */
+/* paper does; the rigid body above is the other form the GPU path offers.   */
 /* ------------------------------------------------------------------------ */
 
 /* Position stage.  xold: bead positions at the start of the sub-step; x, v:
@@ -1156,15 +1156,19 @@ int orc_rattle_pos_iter(int nl, const int32_t *la, const int32_t *lb, const doub
             const double d2 = dl[k] * dl[k];
             const double diff = d2 - (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
             if (fabs(diff) <= 2.0 * tol * d2) continue;
-            const double inv = 1.0 / m[a] + 1.0 / m[b];
+            /* inverse-mass form: bead a moves by g w_a along the old bond,
+             * w = 1/m, and its velocity by that displacement times 1/dt */
+            const double wa = 1.0 / m[a], wb = 1.0 / m[b], idt = 1.0 / dt;
+            const double inv = wa + wb;
             const double sro = s[0] * ro[0] + s[1] * ro[1] + s[2] * ro[2];
             const double g = diff / (2.0 * sro * inv);
+            const double ga = g * wa, gb = g * wb;
             for (int t = 0; t < 3; ++t) {
-                const double ca = g * ro[t] / m[a], cb = g * ro[t] / m[b];
+                const double ca = ga * ro[t], cb = gb * ro[t];
                 x[3 * a + t] = x[3 * a + t] + ca;
                 x[3 * b + t] = x[3 * b + t] - cb;
-                v[3 * a + t] = v[3 * a + t] + ca / dt;
-                v[3 * b + t] = v[3 * b + t] - cb / dt;
+                v[3 * a + t] = v[3 * a + t] + ca * idt;
+                v[3 * b + t] = v[3 * b + t] - cb * idt;
             }
             moved = 1;
         }
@@ -1191,12 +1195,14 @@ int orc_rattle_vel_iter(int nl, const int32_t *la, const int32_t *lb, const doub
             }
             const double rv = s[0] * w[0] + s[1] * w[1] + s[2] * w[2];
             if (fabs(rv) <= tol * dl[k]) continue;
-            const double inv = 1.0 / m[a] + 1.0 / m[b];
+            const double wa = 1.0 / m[a], wb = 1.0 / m[b];   /* inverse masses */
+            const double inv = wa + wb;
             const double ss = s[0] * s[0] + s[1] * s[1] + s[2] * s[2];
             const double kk = rv / (ss * inv);
+            const double ka = kk * wa, kb = kk * wb;
             for (int t = 0; t < 3; ++t) {
-                v[3 * a + t] = v[3 * a + t] - kk * s[t] / m[a];
-                v[3 * b + t] = v[3 * b + t] + kk * s[t] / m[b];
+                v[3 * a + t] = v[3 * a + t] - ka * s[t];
+                v[3 * b + t] = v[3 * b + t] + kb * s[t];
             }
             moved = 1;
         }

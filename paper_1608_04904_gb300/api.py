@@ -95,7 +95,7 @@ EXPORTS = [
     "rmpcd_last_error", "rmpcd_enable_timers", "rmpcd_read_timers", "rmpcd_set_tuning", "rmpcd_get_tuning",
     "rmpcd_observables_noalloc", "rmpcd_set_graphs", "rmpcd_get_bucket_cap", "rmpcd_set_body", "rmpcd_get_body",
     "rmpcd_profile", "rmpcd_workspace_size", "rmpcd_set_wait_test", "rmpcd_md_substep", "rmpcd_set_network",
-    "rmpcd_get_network",
+    "rmpcd_get_network", "rmpcd_set_state_all", "rmpcd_get_state_all",
 ]
 
 _LIB = None
@@ -125,6 +125,8 @@ def load():
     L.rmpcd_destroy.restype = None
     L.rmpcd_set_state.argtypes = [vp, i32, vp, vp, vp, i64, i32]
     L.rmpcd_get_state.argtypes = [vp, i32, vp, vp, vp, vp, vp, i64, i32]
+    L.rmpcd_set_state_all.argtypes = [vp, vp, vp, vp, i64, i32]
+    L.rmpcd_get_state_all.argtypes = [vp, vp, vp, vp, vp, vp, i64, i32]
     L.rmpcd_set_colloids.argtypes = [vp, i32, P(Colloid), i32]
     L.rmpcd_get_colloids.argtypes = [vp, i32, P(Colloid), i32]
     L.rmpcd_set_body.argtypes = [vp, i32, P(Body), P(Bead)]
@@ -337,6 +339,42 @@ class System:
         ptr = lambda k: out[k].ctypes.data_as(C.c_void_p) if k in out else None
         self._check(self._lib.rmpcd_get_state(self._h, replica, ptr("x"), ptr("v"), ptr("flags"), ptr("id"),
                                               ptr("cell"), n, 0))
+        return out
+
+    def set_state_all(self, x, v, flags=None):
+        """rmpcd_set_state_all: every replica's solvent in one call, the arrays
+        concatenated in replica order (numpy host arrays or CUDA tensors)."""
+        n = int(sum(self.n))
+        if _is_torch(x) and x.is_cuda:
+            import torch
+            x = x.contiguous().to(torch.float64)
+            v = v.contiguous().to(torch.float64)
+            f = None if flags is None else flags.contiguous().to(torch.uint8)
+            self._keep = (x, v, f)
+            self._check(self._lib.rmpcd_set_state_all(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(v.data_ptr()),
+                                                      None if f is None else C.c_void_p(f.data_ptr()), n, 1))
+            return
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(n, 3)
+        v = np.ascontiguousarray(v, dtype=np.float64).reshape(n, 3)
+        f = None if flags is None else np.ascontiguousarray(flags, dtype=np.uint8).reshape(n)
+        self._check(self._lib.rmpcd_set_state_all(self._h, x.ctypes.data_as(C.c_void_p), v.ctypes.data_as(C.c_void_p),
+                                                  None if f is None else f.ctypes.data_as(C.c_void_p), n, 0))
+
+    def get_state_all(self, out=None):
+        """rmpcd_get_state_all: every replica's solvent, concatenated in replica
+        order; ``out`` as for get_state (host numpy or CUDA torch arrays)."""
+        n = int(sum(self.n))
+        if out is not None and any(_is_torch(a) and a.is_cuda for a in out.values()):
+            ptr = lambda k: C.c_void_p(out[k].data_ptr()) if k in out else None
+            self._check(self._lib.rmpcd_get_state_all(self._h, ptr("x"), ptr("v"), ptr("flags"), ptr("id"),
+                                                      ptr("cell"), n, 1))
+            return out
+        if out is None:
+            out = {"x": np.empty((n, 3)), "v": np.empty((n, 3)), "flags": np.empty(n, np.uint8),
+                   "id": np.empty(n, np.uint32), "cell": np.empty(n, np.int32)}
+        ptr = lambda k: out[k].ctypes.data_as(C.c_void_p) if k in out else None
+        self._check(self._lib.rmpcd_get_state_all(self._h, ptr("x"), ptr("v"), ptr("flags"), ptr("id"),
+                                                  ptr("cell"), n, 0))
         return out
 
     def set_colloids(self, replica, colloids):

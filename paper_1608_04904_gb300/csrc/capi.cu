@@ -35,6 +35,12 @@ struct rmpcd_system {
     uint8_t *stage_f = nullptr;
     uint32_t *stage_id = nullptr;
     int32_t *stage_cell = nullptr;
+    // staging area of every replica's particles for the batch state calls
+    // (allocated on the first host call when the system has several replicas)
+    double *sa_x = nullptr, *sa_v = nullptr;
+    uint8_t *sa_f = nullptr;
+    uint32_t *sa_id = nullptr;
+    int32_t *sa_cell = nullptr;
     unsigned long long *prof_acc = nullptr;   // [PROF_MAX_BINS * PROF_FIELDS] slab-profile sums
     int *flat_fill = nullptr;                 // [n_rep] records placed by a flatten
     bool dry = false;          // sizing only (rmpcd_workspace_size): count bytes, allocate nothing
@@ -914,6 +920,115 @@ rmpcd_status rmpcd_get_state(rmpcd_system *sys, int32_t replica, double *x, doub
             if (flags) CK(cudaMemcpyAsync(flags, sys->stage_f, n, cudaMemcpyDeviceToHost, sys->stream));
             if (id) CK(cudaMemcpyAsync(id, sys->stage_id, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, sys->stream));
             if (cell) CK(cudaMemcpyAsync(cell, sys->stage_cell, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, sys->stream));
+        }
+    }
+    return check_errors(sys);
+}
+
+// The batch calls' staging area: the per-replica one when a single replica
+// holds every particle, else n_total particles allocated once.
+static rmpcd_status ensure_stage_all(rmpcd_system *sys)
+{
+    if (sys->sa_x) return RMPCD_OK;
+    if (sys->n_total <= sys->max_part) {
+        sys->sa_x = sys->stage_x;
+        sys->sa_v = sys->stage_v;
+        sys->sa_f = sys->stage_f;
+        sys->sa_id = sys->stage_id;
+        sys->sa_cell = sys->stage_cell;
+        return RMPCD_OK;
+    }
+    const size_t n = (size_t)sys->n_total;
+    rmpcd_status st = dalloc(sys, &sys->sa_x, 3 * n);
+    if (st == RMPCD_OK) st = dalloc(sys, &sys->sa_v, 3 * n);
+    if (st == RMPCD_OK) st = dalloc(sys, &sys->sa_f, n);
+    if (st == RMPCD_OK) st = dalloc(sys, &sys->sa_id, n);
+    if (st == RMPCD_OK) st = dalloc(sys, &sys->sa_cell, n);
+    if (st != RMPCD_OK) {
+        // keep nothing half-made (the buffers stay in allocs until destroy)
+        sys->sa_x = sys->sa_v = nullptr;
+        sys->sa_f = nullptr;
+        sys->sa_id = nullptr;
+        sys->sa_cell = nullptr;
+        cudaGetLastError();
+        return fail(sys, RMPCD_ENOMEM, "staging area of %d particles for the batch state calls", sys->n_total);
+    }
+    return RMPCD_OK;
+}
+
+rmpcd_status rmpcd_set_state_all(rmpcd_system *sys, const double *x, const double *v, const uint8_t *flags,
+                                 int64_t n, int32_t on_device)
+{
+    if (!sys) return RMPCD_EINVAL;
+    if (n != sys->n_total) return fail(sys, RMPCD_EINVAL, "n = %lld but the system has %d particles", (long long)n, sys->n_total);
+    if (n > 0 && (!x || !v)) return fail(sys, RMPCD_EINVAL, "x and v are required");
+    rmpcd_status st = unprime(sys);
+    if (st != RMPCD_OK) return st;
+    const double *dx = x, *dv = v;
+    const uint8_t *df = flags;
+    if (!on_device && n > 0) {
+        if ((st = ensure_stage_all(sys)) != RMPCD_OK) return st;
+        CK(cudaMemcpyAsync(sys->sa_x, x, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, sys->stream));
+        CK(cudaMemcpyAsync(sys->sa_v, v, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, sys->stream));
+        if (flags) CK(cudaMemcpyAsync(sys->sa_f, flags, (size_t)n, cudaMemcpyHostToDevice, sys->stream));
+        dx = sys->sa_x;
+        dv = sys->sa_v;
+        df = flags ? sys->sa_f : nullptr;
+    }
+    long long off = 0;
+    for (int r = 0; r < sys->n_rep; ++r) {
+        const int nr = sys->rep[r].n_part;
+        if (nr > 0) {
+            launch_set_state(sys->mixed, sys->d, r, nr, dx + 3 * off, dv + 3 * off, df ? df + off : nullptr, sys->cur,
+                             sys->stream);
+            if ((st = after_launch(sys, 1)) != RMPCD_OK) return st;
+        }
+        off += nr;
+    }
+    if (!on_device && n > 0) CK(cudaStreamSynchronize(sys->stream));   // host arrays may be reused
+    sys->has_sort = false;
+    sys->obs_valid = false;
+    return RMPCD_OK;
+}
+
+rmpcd_status rmpcd_get_state_all(rmpcd_system *sys, double *x, double *v, uint8_t *flags, uint32_t *id,
+                                 int32_t *cell, int64_t n, int32_t on_device)
+{
+    if (!sys) return RMPCD_EINVAL;
+    if (n != sys->n_total) return fail(sys, RMPCD_EINVAL, "n = %lld but the system has %d particles", (long long)n, sys->n_total);
+    rmpcd_status st = unprime(sys);   // a fused run's state, flattened and sorted
+    if (st != RMPCD_OK) return st;
+    if (n > 0) {
+        double *ox = x, *ov = v;
+        uint8_t *of = flags;
+        uint32_t *oi = id;
+        int32_t *oc = cell;
+        if (!on_device) {
+            if ((st = ensure_stage_all(sys)) != RMPCD_OK) return st;
+            ox = x ? sys->sa_x : nullptr;
+            ov = v ? sys->sa_v : nullptr;
+            of = flags ? sys->sa_f : nullptr;
+            oi = id ? sys->sa_id : nullptr;
+            oc = cell ? sys->sa_cell : nullptr;
+        }
+        long long off = 0;
+        for (int r = 0; r < sys->n_rep; ++r) {
+            const int nr = sys->rep[r].n_part;
+            if (nr > 0) {
+                launch_get_state(sys->mixed, sys->d, r, nr, sys->cur, ox ? ox + 3 * off : nullptr,
+                                 ov ? ov + 3 * off : nullptr, of ? of + off : nullptr, oi ? oi + off : nullptr,
+                                 oc ? oc + off : nullptr, sys->has_sort ? 1 : 0, sys->sort_step, sys->stream);
+                if ((st = after_launch(sys, 1)) != RMPCD_OK) return st;
+            }
+            off += nr;
+        }
+        if (!on_device) {
+            const size_t m = (size_t)n;
+            if (x) CK(cudaMemcpyAsync(x, sys->sa_x, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, sys->stream));
+            if (v) CK(cudaMemcpyAsync(v, sys->sa_v, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, sys->stream));
+            if (flags) CK(cudaMemcpyAsync(flags, sys->sa_f, m, cudaMemcpyDeviceToHost, sys->stream));
+            if (id) CK(cudaMemcpyAsync(id, sys->sa_id, sizeof(uint32_t) * m, cudaMemcpyDeviceToHost, sys->stream));
+            if (cell) CK(cudaMemcpyAsync(cell, sys->sa_cell, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, sys->stream));
         }
     }
     return check_errors(sys);

@@ -56,20 +56,20 @@ struct NetShared {
 
 // Dynamic shared layout of one network (nb beads, nl links, ncol colours).
 struct NetSmem {
-    double *x, *v, *xo, *F, *Xw, *m, *eps;   // eps: [2 nb] (A, B)
+    double *x, *v, *xo, *F, *Xw, *m, *w, *eps;   // w = 1/m; eps: [2 nb] (A, B)
     long long *Fq;
     double *dl;
     int *la, *lb, *cs, *cat;
     unsigned *mask;                          // [MDN_CELLS * words]
 };
 
-// Bytes of the layout below: doubles x, v, xo, F, Xw (3 nb each), m (nb),
-// eps (2 nb), dl (nl); fixed-point sums (3 nb); ints la, lb (nl each), colour
+// Bytes of the layout below: doubles x, v, xo, F, Xw (3 nb each), m, w (nb
+// each), eps (2 nb), dl (nl); fixed-point sums (3 nb); ints la, lb (nl each), colour
 // starts (ncol + 1), cat (nb); the candidate masks.
 __host__ __device__ inline size_t net_smem_bytes(int nb, int nl, int ncol)
 {
     const int words = (nb + 31) / 32;
-    return sizeof(double) * (size_t)(18 * nb + nl) + sizeof(long long) * (size_t)(3 * nb) +
+    return sizeof(double) * (size_t)(19 * nb + nl) + sizeof(long long) * (size_t)(3 * nb) +
            sizeof(int) * (size_t)(2 * nl + ncol + 1 + nb) + sizeof(unsigned) * (size_t)MDN_CELLS * words;
 }
 
@@ -83,6 +83,7 @@ __device__ NetSmem net_layout(unsigned char *raw, int nb, int nl, int ncol)
     B.F = p; p += 3 * nb;
     B.Xw = p; p += 3 * nb;
     B.m = p; p += nb;
+    B.w = p; p += nb;
     B.eps = p; p += 2 * nb;
     B.dl = p; p += nl;
     long long *q = reinterpret_cast<long long *>(p);
@@ -192,6 +193,7 @@ __device__ int net_force(const ReplicaDev &rp, NetShared &S, const NetSmem &B, c
 __device__ void net_rattle_pos(NetShared &S, const NetSmem &B, double dt)
 {
     const int tid = threadIdx.x;
+    const double idt = 1.0 / dt;
     int sweep = 0;
     for (;;) {
         ++sweep;
@@ -207,15 +209,18 @@ __device__ void net_rattle_pos(NetShared &S, const NetSmem &B, double dt)
                 const double d2 = B.dl[k] * B.dl[k];
                 const double diff = d2 - (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
                 if (fabs(diff) <= 2.0 * S.tol * d2) continue;
-                const double inv = 1.0 / B.m[a] + 1.0 / B.m[b];
+                // inverse-mass form: one division per correction
+                const double wa = B.w[a], wb = B.w[b];
+                const double inv = wa + wb;
                 const double sro = s[0] * ro[0] + s[1] * ro[1] + s[2] * ro[2];
                 const double g = diff / (2.0 * sro * inv);
+                const double ga = g * wa, gb = g * wb;
                 for (int t = 0; t < 3; ++t) {
-                    const double ca = g * ro[t] / B.m[a], cb = g * ro[t] / B.m[b];
+                    const double ca = ga * ro[t], cb = gb * ro[t];
                     B.x[3 * a + t] = B.x[3 * a + t] + ca;
                     B.x[3 * b + t] = B.x[3 * b + t] - cb;
-                    B.v[3 * a + t] = B.v[3 * a + t] + ca / dt;
-                    B.v[3 * b + t] = B.v[3 * b + t] - cb / dt;
+                    B.v[3 * a + t] = B.v[3 * a + t] + ca * idt;
+                    B.v[3 * b + t] = B.v[3 * b + t] - cb * idt;
                 }
                 moved = 1;
             }
@@ -248,12 +253,14 @@ __device__ void net_rattle_vel(NetShared &S, const NetSmem &B)
                 }
                 const double rv = s[0] * w[0] + s[1] * w[1] + s[2] * w[2];
                 if (fabs(rv) <= S.tol * B.dl[k]) continue;
-                const double inv = 1.0 / B.m[a] + 1.0 / B.m[b];
+                const double wa = B.w[a], wb = B.w[b];
+                const double inv = wa + wb;
                 const double ss = s[0] * s[0] + s[1] * s[1] + s[2] * s[2];
                 const double kk = rv / (ss * inv);
+                const double ka = kk * wa, kb = kk * wb;
                 for (int t = 0; t < 3; ++t) {
-                    B.v[3 * a + t] = B.v[3 * a + t] - kk * s[t] / B.m[a];
-                    B.v[3 * b + t] = B.v[3 * b + t] + kk * s[t] / B.m[b];
+                    B.v[3 * a + t] = B.v[3 * a + t] - ka * s[t];
+                    B.v[3 * b + t] = B.v[3 * b + t] + kb * s[t];
                 }
                 moved = 1;
             }
@@ -312,6 +319,7 @@ __global__ void __launch_bounds__(MDN_NT, 1) k_md_network(Dev d, uint32_t step, 
         const int g = nd.bead_off + j;
         for (int t = 0; t < 3; ++t) { B.x[3 * j + t] = d.net_x[3 * g + t]; B.v[3 * j + t] = d.net_v[3 * g + t]; }
         B.m[j] = d.net_m[g];
+        B.w[j] = 1.0 / B.m[j];   // the inverse masses of the RATTLE corrections
         B.eps[2 * j] = d.net_eps[2 * g];
         B.eps[2 * j + 1] = d.net_eps[2 * g + 1];
         B.cat[j] = d.net_cat[g];

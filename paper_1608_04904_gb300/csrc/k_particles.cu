@@ -204,16 +204,40 @@ __device__ __forceinline__ void flat_put(const Dev &d, int r, int fbuf, int *fil
     else atomicOr(&d.err[ERR_BOUNDS], 1u);
 }
 
+// One thread per cell; the 32 cells of a warp lie in one tile, so in one
+// replica: the warp takes its slots with one atomic (a per-particle atomic on
+// the replica's single counter serialises on that address).
 template <class Rec>
 __global__ void k_flatten_rows(Dev d, int b, int fbuf, int *fill)
 {
+    static_assert(CPT % 32 == 0, "a warp's cells share a tile");
     const long long nc = (long long)d.n_tiles * CPT;
-    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < nc; g += (long long)gridDim.x * blockDim.x) {
-        const int n = min(d.count[b][g], d.cap);
-        if (n <= 0) continue;
-        const int r = d.tile_rep[g / CPT];
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long g0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); g0 < nc; g0 += stride) {
+        const long long g = g0 + lane;   // g0 is a multiple of 32 and nc of CPT: every lane is in range
+        const int n = max(0, min(d.count[b][g], d.cap));
+        int incl = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        if (tot == 0) continue;
+        const int r = d.tile_rep[g0 / CPT];
+        int base = 0;
+        if (lane == 31) base = atomicAdd(&fill[r], tot);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        const ReplicaDev &rp = d.rep[r];
         const Rec *rows = reinterpret_cast<const Rec *>(d.brec[b]);
-        for (int i = 0; i < n; ++i) flat_put(d, r, fbuf, fill, load_rec(rows + row_index(d, g, i)));
+        Rec *out = reinterpret_cast<Rec *>(d.rec[fbuf]) + rp.part_off;
+        const int k0 = base + incl - n;
+        for (int i = 0; i < n; ++i) {
+            const int k = k0 + i;
+            if (k < rp.n_part) store_rec(out + k, load_rec(rows + row_index(d, g, i)));
+            else atomicOr(&d.err[ERR_BOUNDS], 1u);
+        }
     }
 }
 

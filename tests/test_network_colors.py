@@ -45,15 +45,16 @@ def _parallel_pos_sweeps(links, d, m, xold, x, v, dt, tol, colors, max_sweeps=10
                 continue
             moved = True
             a, b, s, ro, diff = a[act], b[act], s[act], ro[act], diff[act]
-            inv = 1.0 / m[a] + 1.0 / m[b]
+            wa, wb, idt = 1.0 / m[a], 1.0 / m[b], 1.0 / dt   # inverse-mass form
+            inv = wa + wb
             sro = s[:, 0] * ro[:, 0] + s[:, 1] * ro[:, 1] + s[:, 2] * ro[:, 2]
             g = diff / (2.0 * sro * inv)
-            ca = (g[:, None] * ro) / m[a][:, None]
-            cb = (g[:, None] * ro) / m[b][:, None]
+            ca = (g * wa)[:, None] * ro
+            cb = (g * wb)[:, None] * ro
             x[a] = x[a] + ca
             x[b] = x[b] - cb
-            v[a] = v[a] + ca / dt
-            v[b] = v[b] - cb / dt
+            v[a] = v[a] + ca * idt
+            v[b] = v[b] - cb * idt
         if not moved:
             return x, v, sweep
     return x, v, -1
