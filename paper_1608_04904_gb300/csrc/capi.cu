@@ -41,6 +41,7 @@ struct rmpcd_system {
     uint8_t *sa_f = nullptr;
     uint32_t *sa_id = nullptr;
     int32_t *sa_cell = nullptr;
+    cudaStream_t xfer = nullptr;   // copies of the batch state calls, beside the system's stream
     unsigned long long *prof_acc = nullptr;   // [PROF_MAX_BINS * PROF_FIELDS] slab-profile sums
     int *flat_fill = nullptr;                 // [n_rep] records placed by a flatten
     bool dry = false;          // sizing only (rmpcd_workspace_size): count bytes, allocate nothing
@@ -360,6 +361,7 @@ void rmpcd_destroy(rmpcd_system *sys)
     for (auto &q : sys->pending) { sys->ev_pool.push_back(q.a); sys->ev_pool.push_back(q.b); }
     for (auto &q : sys->md_trials) { sys->ev_pool.push_back(q.a); sys->ev_pool.push_back(q.b); }
     for (cudaEvent_t e : sys->ev_pool) cudaEventDestroy(e);
+    if (sys->xfer) cudaStreamDestroy(sys->xfer);
     delete sys;
 }
 
@@ -956,6 +958,27 @@ static rmpcd_status ensure_stage_all(rmpcd_system *sys)
     return RMPCD_OK;
 }
 
+// Replica groups of the batch state calls: consecutive replicas of about
+// n_total / XFER_GROUPS particles.  A group's copy overlaps the kernels of
+// its neighbour group, so the state kernels hide under the host copies.
+static constexpr int XFER_GROUPS = 8;
+static void xfer_groups(const rmpcd_system *sys, std::vector<int> &bounds)
+{
+    bounds.assign(1, 0);
+    const long long target = std::max(1ll, (long long)sys->n_total / XFER_GROUPS);
+    long long acc = 0;
+    for (int r = 0; r < sys->n_rep; ++r) {
+        acc += sys->rep[r].n_part;
+        if (r + 1 == sys->n_rep || acc >= target * (long long)bounds.size()) bounds.push_back(r + 1);
+    }
+}
+
+static rmpcd_status ensure_xfer(rmpcd_system *sys)
+{
+    if (!sys->xfer) CK(cudaStreamCreateWithFlags(&sys->xfer, cudaStreamNonBlocking));
+    return RMPCD_OK;
+}
+
 rmpcd_status rmpcd_set_state_all(rmpcd_system *sys, const double *x, const double *v, const uint8_t *flags,
                                  int64_t n, int32_t on_device)
 {
@@ -964,28 +987,48 @@ rmpcd_status rmpcd_set_state_all(rmpcd_system *sys, const double *x, const doubl
     if (n > 0 && (!x || !v)) return fail(sys, RMPCD_EINVAL, "x and v are required");
     rmpcd_status st = unprime(sys);
     if (st != RMPCD_OK) return st;
-    const double *dx = x, *dv = v;
-    const uint8_t *df = flags;
-    if (!on_device && n > 0) {
+    const bool staged = !on_device && n > 0;
+    if (staged) {
         if ((st = ensure_stage_all(sys)) != RMPCD_OK) return st;
-        CK(cudaMemcpyAsync(sys->sa_x, x, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, sys->stream));
-        CK(cudaMemcpyAsync(sys->sa_v, v, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, sys->stream));
-        if (flags) CK(cudaMemcpyAsync(sys->sa_f, flags, (size_t)n, cudaMemcpyHostToDevice, sys->stream));
-        dx = sys->sa_x;
-        dv = sys->sa_v;
-        df = flags ? sys->sa_f : nullptr;
+        if ((st = ensure_xfer(sys)) != RMPCD_OK) return st;
+    }
+    const double *dx = staged ? sys->sa_x : x, *dv = staged ? sys->sa_v : v;
+    const uint8_t *df = flags ? (staged ? sys->sa_f : flags) : nullptr;
+    std::vector<int> gb;
+    xfer_groups(sys, gb);
+    std::vector<cudaEvent_t> evs;
+    if (staged) {
+        // the copies start after the work already on the system's stream
+        // (which may still read the staging area)
+        evs.push_back(pool_event(sys));
+        CK(cudaEventRecord(evs.back(), sys->stream));
+        CK(cudaStreamWaitEvent(sys->xfer, evs.back(), 0));
     }
     long long off = 0;
-    for (int r = 0; r < sys->n_rep; ++r) {
-        const int nr = sys->rep[r].n_part;
-        if (nr > 0) {
-            launch_set_state(sys->mixed, sys->d, r, nr, dx + 3 * off, dv + 3 * off, df ? df + off : nullptr, sys->cur,
-                             sys->stream);
-            if ((st = after_launch(sys, 1)) != RMPCD_OK) return st;
+    for (size_t g = 0; g + 1 < gb.size(); ++g) {
+        long long cnt = 0;
+        for (int r = gb[g]; r < gb[g + 1]; ++r) cnt += sys->rep[r].n_part;
+        if (staged && cnt > 0) {
+            const size_t o = (size_t)off, m = (size_t)cnt;
+            CK(cudaMemcpyAsync(sys->sa_x + 3 * o, x + 3 * o, sizeof(double) * 3 * m, cudaMemcpyHostToDevice, sys->xfer));
+            CK(cudaMemcpyAsync(sys->sa_v + 3 * o, v + 3 * o, sizeof(double) * 3 * m, cudaMemcpyHostToDevice, sys->xfer));
+            if (flags) CK(cudaMemcpyAsync(sys->sa_f + o, flags + o, m, cudaMemcpyHostToDevice, sys->xfer));
+            evs.push_back(pool_event(sys));
+            CK(cudaEventRecord(evs.back(), sys->xfer));
+            CK(cudaStreamWaitEvent(sys->stream, evs.back(), 0));
         }
-        off += nr;
+        for (int r = gb[g]; r < gb[g + 1]; ++r) {
+            const int nr = sys->rep[r].n_part;
+            if (nr > 0) {
+                launch_set_state(sys->mixed, sys->d, r, nr, dx + 3 * off, dv + 3 * off, df ? df + off : nullptr,
+                                 sys->cur, sys->stream);
+                if ((st = after_launch(sys, 1)) != RMPCD_OK) return st;
+            }
+            off += nr;
+        }
     }
-    if (!on_device && n > 0) CK(cudaStreamSynchronize(sys->stream));   // host arrays may be reused
+    if (staged) CK(cudaStreamSynchronize(sys->stream));   // the host arrays may be reused
+    for (cudaEvent_t e : evs) sys->ev_pool.push_back(e);
     sys->has_sort = false;
     sys->obs_valid = false;
     return RMPCD_OK;
@@ -998,40 +1041,56 @@ rmpcd_status rmpcd_get_state_all(rmpcd_system *sys, double *x, double *v, uint8_
     if (n != sys->n_total) return fail(sys, RMPCD_EINVAL, "n = %lld but the system has %d particles", (long long)n, sys->n_total);
     rmpcd_status st = unprime(sys);   // a fused run's state, flattened and sorted
     if (st != RMPCD_OK) return st;
+    std::vector<cudaEvent_t> evs;
     if (n > 0) {
-        double *ox = x, *ov = v;
-        uint8_t *of = flags;
-        uint32_t *oi = id;
-        int32_t *oc = cell;
-        if (!on_device) {
+        const bool staged = !on_device;
+        if (staged) {
             if ((st = ensure_stage_all(sys)) != RMPCD_OK) return st;
-            ox = x ? sys->sa_x : nullptr;
-            ov = v ? sys->sa_v : nullptr;
-            of = flags ? sys->sa_f : nullptr;
-            oi = id ? sys->sa_id : nullptr;
-            oc = cell ? sys->sa_cell : nullptr;
+            if ((st = ensure_xfer(sys)) != RMPCD_OK) return st;
         }
+        double *ox = x ? (staged ? sys->sa_x : x) : nullptr;
+        double *ov = v ? (staged ? sys->sa_v : v) : nullptr;
+        uint8_t *of = flags ? (staged ? sys->sa_f : flags) : nullptr;
+        uint32_t *oi = id ? (staged ? sys->sa_id : id) : nullptr;
+        int32_t *oc = cell ? (staged ? sys->sa_cell : cell) : nullptr;
+        std::vector<int> gb;
+        xfer_groups(sys, gb);
         long long off = 0;
-        for (int r = 0; r < sys->n_rep; ++r) {
-            const int nr = sys->rep[r].n_part;
-            if (nr > 0) {
-                launch_get_state(sys->mixed, sys->d, r, nr, sys->cur, ox ? ox + 3 * off : nullptr,
-                                 ov ? ov + 3 * off : nullptr, of ? of + off : nullptr, oi ? oi + off : nullptr,
-                                 oc ? oc + off : nullptr, sys->has_sort ? 1 : 0, sys->sort_step, sys->stream);
-                if ((st = after_launch(sys, 1)) != RMPCD_OK) return st;
+        for (size_t g = 0; g + 1 < gb.size(); ++g) {
+            const long long g0 = off;
+            for (int r = gb[g]; r < gb[g + 1]; ++r) {
+                const int nr = sys->rep[r].n_part;
+                if (nr > 0) {
+                    launch_get_state(sys->mixed, sys->d, r, nr, sys->cur, ox ? ox + 3 * off : nullptr,
+                                     ov ? ov + 3 * off : nullptr, of ? of + off : nullptr, oi ? oi + off : nullptr,
+                                     oc ? oc + off : nullptr, sys->has_sort ? 1 : 0, sys->sort_step, sys->stream);
+                    if ((st = after_launch(sys, 1)) != RMPCD_OK) return st;
+                }
+                off += nr;
             }
-            off += nr;
+            if (staged && off > g0) {
+                // this group's copies run beside the next group's kernels
+                evs.push_back(pool_event(sys));
+                CK(cudaEventRecord(evs.back(), sys->stream));
+                CK(cudaStreamWaitEvent(sys->xfer, evs.back(), 0));
+                const size_t o = (size_t)g0, m = (size_t)(off - g0);
+                if (x) CK(cudaMemcpyAsync(x + 3 * o, sys->sa_x + 3 * o, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, sys->xfer));
+                if (v) CK(cudaMemcpyAsync(v + 3 * o, sys->sa_v + 3 * o, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, sys->xfer));
+                if (flags) CK(cudaMemcpyAsync(flags + o, sys->sa_f + o, m, cudaMemcpyDeviceToHost, sys->xfer));
+                if (id) CK(cudaMemcpyAsync(id + o, sys->sa_id + o, sizeof(uint32_t) * m, cudaMemcpyDeviceToHost, sys->xfer));
+                if (cell) CK(cudaMemcpyAsync(cell + o, sys->sa_cell + o, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, sys->xfer));
+            }
         }
-        if (!on_device) {
-            const size_t m = (size_t)n;
-            if (x) CK(cudaMemcpyAsync(x, sys->sa_x, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, sys->stream));
-            if (v) CK(cudaMemcpyAsync(v, sys->sa_v, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, sys->stream));
-            if (flags) CK(cudaMemcpyAsync(flags, sys->sa_f, m, cudaMemcpyDeviceToHost, sys->stream));
-            if (id) CK(cudaMemcpyAsync(id, sys->sa_id, sizeof(uint32_t) * m, cudaMemcpyDeviceToHost, sys->stream));
-            if (cell) CK(cudaMemcpyAsync(cell, sys->sa_cell, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, sys->stream));
+        if (staged) {
+            // the system's stream (and so the error check below) waits for the copies
+            evs.push_back(pool_event(sys));
+            CK(cudaEventRecord(evs.back(), sys->xfer));
+            CK(cudaStreamWaitEvent(sys->stream, evs.back(), 0));
         }
     }
-    return check_errors(sys);
+    const rmpcd_status rc = check_errors(sys);
+    for (cudaEvent_t e : evs) sys->ev_pool.push_back(e);
+    return rc;
 }
 
 rmpcd_status rmpcd_set_colloids(rmpcd_system *sys, int32_t replica, const rmpcd_colloid *c, int32_t n)
