@@ -345,9 +345,15 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
             // |v - v_cm| (the rotation keeps |v - v_cm|) and it lies within
             // sqrt(3)/2 of the cell centre on this step's grid.  With many
             // colloids the test runs after the batch's candidates are known.
-            int mn = 1;
-            if (MANY) T.vbc[c] = -1.0f;
-            if (slab < 0) {
+            // MPC-AT cells have their new velocities already: the largest
+            // of their speeds is the bound.
+            float vb;
+            if (slab >= 0) {
+                R w2 = R(0);
+                for (int i = 0; i < n; ++i)
+                    w2 = max(w2, cr[i].v[0] * cr[i].v[0] + cr[i].v[1] * cr[i].v[1] + cr[i].v[2] * cr[i].v[2]);
+                vb = (float)sqrt(w2);
+            } else {
                 // the centre the rotation turns about: with virtual wall
                 // partners the collision's v_cm, else the cell's own mean
                 const R inv = R(1) / (R)n;
@@ -362,19 +368,19 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
                     nb_ += (cr[i].fid & F_B) ? 1 : 0;
                 }
                 nbB = nb_;
-                const float vb = (float)(sqrt(vc[0] * vc[0] + vc[1] * vc[1] + vc[2] * vc[2]) + sqrt(u2));
-                if (MANY) T.vbc[c] = vb;
-                const int t = lc / rp.L[0];
-                const int kc[3] = {lc % rp.L[0], t % rp.L[1], rp.walls ? t / rp.L[1] - 1 : t / rp.L[1]};
-                mn = 0;
-                for (int j = 0; j < (MANY ? 0 : rp.n_col) && !mn; ++j) {
-                    float dd[3];
-                    for (int k = 0; k < 3; ++k)
-                        dd[k] = (float)(kc[k] - T.nf.Ci[3 * j + k]) + ((0.5f + T.shf[k]) - T.nf.Cf[3 * j + k]);
-                    min_image(rp, dd);
-                    const float dist = sqrtf(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
-                    if (dist - 0.8661f < T.nf.Rb[j] + vb * rp.tau_f + 1e-3f) mn = 1;
-                }
+                vb = (float)(sqrt(vc[0] * vc[0] + vc[1] * vc[1] + vc[2] * vc[2]) + sqrt(u2));
+            }
+            if (MANY) T.vbc[c] = vb;
+            const int t = lc / rp.L[0];
+            const int kc[3] = {lc % rp.L[0], t % rp.L[1], rp.walls ? t / rp.L[1] - 1 : t / rp.L[1]};
+            int mn = 0;
+            for (int j = 0; j < (MANY ? 0 : rp.n_col) && !mn; ++j) {
+                float dd[3];
+                for (int k = 0; k < 3; ++k)
+                    dd[k] = (float)(kc[k] - T.nf.Ci[3 * j + k]) + ((0.5f + T.shf[k]) - T.nf.Cf[3 * j + k]);
+                min_image(rp, dd);
+                const float dist = sqrtf(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+                if (dist - 0.8661f < T.nf.Rb[j] + vb * rp.tau_f + 1e-3f) mn = 1;
             }
             T.mnear[c] = mn;
         }
@@ -469,7 +475,7 @@ __device__ void near_candidates(TileShared<MIXED> &T, int gt, int cb, int ce)
     }
     __syncthreads();
     for (int c = cb + gt; c < ce; c += CP_THREADS) {
-        if (T.cnt[c] == 0 || T.vbc[c] < 0.0f) continue;   // empty cell: no test; MPC-AT: mnear already 1
+        if (T.cnt[c] == 0 || T.vbc[c] < 0.0f) continue;   // empty cell: no test
         const int lc = lc0 + c;
         const int t = lc / rp.L[0];
         const int kc[3] = {lc % rp.L[0], t % rp.L[1], t / rp.L[1]};
