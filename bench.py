@@ -161,7 +161,7 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def ncu_traffic(kernel, workload_name, precision, n_particles):
+def ncu_traffic(kernel, workload_name, precision, n_particles, cell_order="linear"):
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or None
     when absent or taken on a different kernel build.  An entry captured on a
     smaller case of the same workload (bytes_per_particle) is scaled to the
@@ -173,7 +173,8 @@ def ncu_traffic(kernel, workload_name, precision, n_particles):
     d = json.load(open(p))
     if kernel not in KERNEL_SOURCES or d.get("kernel_hash") != kernel_hash(kernel):
         return None
-    e = d.get("kernels", {}).get(f"{kernel}/{workload_name}/{precision}")
+    key = f"{kernel}/{workload_name}/{precision}" + ("" if cell_order == "linear" else f"/{cell_order}")
+    e = d.get("kernels", {}).get(key)
     if e is None:
         return None
     if "bytes_per_particle" in e:
@@ -372,12 +373,16 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+CELL_ORDER = "linear"
+
+
 def make_system(api, reps, states, precision, stream):
     from paper_1608_04904_gb300 import network
     rigid = lambda b: None if b is not None and "network" in b else b
     s = api.System([dict(cfg=cfg, n=len(st[0]), colloids=col, bonds=bonds, body=rigid(body))
                     for (cfg, col, bonds, body), st in zip(reps, states)], precision=precision,
                    bucket_cap=reps[0][0].get("bucket_cap", 0), stream=stream)
+    s.set_cell_order(CELL_ORDER)
     for r, (x, v, fl) in enumerate(states):
         s.set_state(r, x, v, fl)
     for r, (cfg, col, bonds, body) in enumerate(reps):
@@ -517,12 +522,16 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--bucket-cap", type=int, default=None,
                     help="cell row width (default: the automatic width)")
+    ap.add_argument("--cell-order", default="linear", choices=["linear", "hilbert"],
+                    help="storage order of the cells (rmpcd_set_cell_order)")
     ap.add_argument("--replicas", type=int, default=None,
                     help="batch256 only: keep the first N replicas (a smaller case for profiling)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.workload == "network64":
         args.precision = "fp64"   # the network integrator is FP64 only
+    global CELL_ORDER
+    CELL_ORDER = args.cell_order
     ws, rank, local = dist_setup()
 
     if args.impl == "reference":
@@ -583,7 +592,7 @@ def main():
     alg = n * ALG_BYTES[args.precision]
     achieved = alg / cp_avg_s / 1e9
     roofline = {"kernel": "k_cellpass", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": ncu_traffic("k_cellpass", args.workload, args.precision, n),
+                "frac": achieved / peak, "traffic": ncu_traffic("k_cellpass", args.workload, args.precision, n, args.cell_order),
                 "peak_source": f"{peak_src} hbm_gbs", "dominant_kernel": kernel_names[dominant],
                 "alg_bytes_per_particle": ALG_BYTES[args.precision]}
     if dominant == "md":
@@ -605,7 +614,7 @@ def main():
                    "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
                    "timing": "CUDA events around each rmpcd_step(1) on the library's stream (intervals replayed "
                              "as CUDA graphs); per-kernel times from a further run with the library's timers",
-                   "md_cluster": obs["md_cluster"], "md_kernel": obs["md_kernel"],
+                   "md_cluster": obs["md_cluster"], "md_kernel": obs["md_kernel"], "cell_order": args.cell_order,
                    "bucket_cap": obs["bucket_cap"]},
         "roofline": roofline, "kernels": kernels, "gpu_launches": launches, "clocks": clocks,
         "observables": {"temperature": obs["temperature"], "n_B": obs["n_B"], "kT": cfg["kT"]},

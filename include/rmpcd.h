@@ -219,6 +219,28 @@ rmpcd_status rmpcd_set_state_all(rmpcd_system *sys, const double *x, const doubl
 rmpcd_status rmpcd_get_state_all(rmpcd_system *sys, double *x, double *v, uint8_t *flags, uint32_t *id,
                                  int32_t *cell, int64_t n, int32_t on_device);
 
+/* Order of the cells in storage (§1.2 sorts the particles by cell; §1.4 puts
+ * the cells in compact Hilbert order).  RMPCD_ORDER_LINEAR (the default):
+ * cell key k = x + L0 (y + L1 z) on the collision grid (z over L[2] + 1
+ * layers with walls) is also the cell's place.  RMPCD_ORDER_HILBERT: the
+ * cells of each replica are placed by their index on the 3-D Hilbert curve
+ * through the smallest enclosing cube of side 2^m (Skilling's transpose
+ * method, x the most significant axis), ranked over the box's cells.  The
+ * place decides the storage order of a sorted state (rmpcd_get_state), the
+ * record rows and the tiles of the cell pass; a cell's draws, its geometry
+ * and the cell keys reported keep the key, so every result is the same up to
+ * the storage order.  rmpcd_set_cell_order moves a fused run's state back to
+ * the flat layout first and drops captured graphs; the Hilbert tables (two
+ * ints per cell) are allocated on first use.  rmpcd_cell_places: the place
+ * of every key of a grid dims[3] (each in [1, 1023]) in the given order
+ * (host memory, dims[0] dims[1] dims[2] entries; no CUDA call).  Errors:
+ * EINVAL, ENOMEM, ECUDA. */
+#define RMPCD_ORDER_LINEAR 0
+#define RMPCD_ORDER_HILBERT 1
+rmpcd_status rmpcd_set_cell_order(rmpcd_system *sys, int32_t order);
+rmpcd_status rmpcd_get_cell_order(rmpcd_system *sys, int32_t *order);
+rmpcd_status rmpcd_cell_places(const int32_t dims[3], int32_t order, int64_t *place);
+
 /* Colloids of one replica (host arrays of params.n_colloids entries). */
 rmpcd_status rmpcd_set_colloids(rmpcd_system *sys, int32_t replica, const rmpcd_colloid *c, int32_t n);
 rmpcd_status rmpcd_get_colloids(rmpcd_system *sys, int32_t replica, rmpcd_colloid *c, int32_t n);

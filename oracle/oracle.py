@@ -363,7 +363,11 @@ class OracleSystem:
     """
 
     def __init__(self, cfg: dict, x, v, flags=None, ids=None, colloids=None, bonds=None, step: int = 0,
-                 body=None):
+                 body=None, cell_order: str = "linear"):
+        """cell_order: the order of the cells in storage -- "linear" (cell key
+        order, x fastest) or "hilbert" (the compact Hilbert order of the
+        collision grid, §1.2 / §1.4): only the storage order changes, every
+        cell keeps its key (its linear index) for its draws and geometry."""
         self.cfg = dict(cfg)
         self.p = make_params(cfg)
         n = len(x)
@@ -389,6 +393,16 @@ class OracleSystem:
             raise ValueError("a replica holds either colloids or one rigid body")
         self.step_index = int(step)
         self.ncells = int(lib().orc_n_cells(C.byref(self.p)))
+        if cell_order not in ("linear", "hilbert"):
+            raise ValueError(f"cell_order {cell_order!r}")
+        self.cell_order = cell_order
+        self.rank = None
+        if cell_order == "hilbert":
+            L = self.cfg["L"]
+            nz = int(L[2]) + (1 if self.cfg.get("walls") else 0)
+            self.rank = hilbert_rank((int(L[0]), int(L[1]), nz))
+            if len(self.rank) != self.ncells:
+                raise ValueError("Hilbert rank table does not cover the cells")
         self.key = None
         self.count = None
         self.start = None
@@ -430,7 +444,12 @@ class OracleSystem:
         key = np.zeros(self.n, dtype=np.int32)
         L.orc_cell_keys(C.byref(self.p), self.n, _ptr(self.x, C.c_double), _ptr(s, C.c_double),
                         _ptr(key, C.c_int32))
-        perm, count, start = counting_sort(key, self.ncells, self.id)
+        if self.rank is None:
+            perm, count, start = counting_sort(key, self.ncells, self.id)
+        else:
+            # storage by (Hilbert rank, id); count and start stay indexed by key
+            perm, count_r, start_r = counting_sort(self.rank[key].astype(np.int32), self.ncells, self.id)
+            count, start = count_r[self.rank], start_r[self.rank]
         self.x = gather(perm, self.x)
         self.v = gather(perm, self.v)
         self.flags = gather(perm, self.flags)

@@ -20,6 +20,18 @@ RMPCD_MIXED = 1
 STATUS = {0: "OK", 1: "EINVAL", 2: "ECUDA", 3: "ENOMEM", 4: "EOVERFLOW", 5: "ESKIN", 6: "ETIMEOUT", 7: "ESTATE"}
 
 
+def cell_places(dims, order="hilbert"):
+    """rmpcd_cell_places: the place of every cell key of a grid (host call)."""
+    L = load()
+    d = (C.c_int32 * 3)(*[int(a) for a in dims])
+    n = int(dims[0]) * int(dims[1]) * int(dims[2])
+    out = np.zeros(n, dtype=np.int64)
+    st = L.rmpcd_cell_places(d, CELL_ORDERS[order], out.ctypes.data_as(C.POINTER(C.c_int64)))
+    if st != 0:
+        raise RmpcdError(st, "rmpcd_cell_places")
+    return out
+
+
 class RmpcdError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"rmpcd {STATUS.get(status, status)}: {message}")
@@ -95,8 +107,10 @@ EXPORTS = [
     "rmpcd_last_error", "rmpcd_enable_timers", "rmpcd_read_timers", "rmpcd_set_tuning", "rmpcd_get_tuning",
     "rmpcd_observables_noalloc", "rmpcd_set_graphs", "rmpcd_get_bucket_cap", "rmpcd_set_body", "rmpcd_get_body",
     "rmpcd_profile", "rmpcd_workspace_size", "rmpcd_set_wait_test", "rmpcd_md_substep", "rmpcd_set_network",
-    "rmpcd_get_network", "rmpcd_set_state_all", "rmpcd_get_state_all",
+    "rmpcd_get_network", "rmpcd_set_state_all", "rmpcd_get_state_all", "rmpcd_set_cell_order",
+    "rmpcd_get_cell_order", "rmpcd_cell_places",
 ]
+CELL_ORDERS = {"linear": 0, "hilbert": 1}
 
 _LIB = None
 
@@ -126,6 +140,9 @@ def load():
     L.rmpcd_set_state.argtypes = [vp, i32, vp, vp, vp, i64, i32]
     L.rmpcd_get_state.argtypes = [vp, i32, vp, vp, vp, vp, vp, i64, i32]
     L.rmpcd_set_state_all.argtypes = [vp, vp, vp, vp, i64, i32]
+    L.rmpcd_set_cell_order.argtypes = [vp, i32]
+    L.rmpcd_get_cell_order.argtypes = [vp, P(i32)]
+    L.rmpcd_cell_places.argtypes = [P(i32), i32, P(i64)]
     L.rmpcd_get_state_all.argtypes = [vp, vp, vp, vp, vp, vp, i64, i32]
     L.rmpcd_set_colloids.argtypes = [vp, i32, P(Colloid), i32]
     L.rmpcd_get_colloids.argtypes = [vp, i32, P(Colloid), i32]
@@ -376,6 +393,15 @@ class System:
         self._check(self._lib.rmpcd_get_state_all(self._h, ptr("x"), ptr("v"), ptr("flags"), ptr("id"),
                                                   ptr("cell"), n, 0))
         return out
+
+    def set_cell_order(self, order):
+        """rmpcd_set_cell_order: "linear" (cell key order) or "hilbert"."""
+        self._check(self._lib.rmpcd_set_cell_order(self._h, CELL_ORDERS[order]))
+
+    def get_cell_order(self):
+        o = C.c_int32(-1)
+        self._check(self._lib.rmpcd_get_cell_order(self._h, C.byref(o)))
+        return {v: k for k, v in CELL_ORDERS.items()}[o.value]
 
     def set_colloids(self, replica, colloids):
         arr = (Colloid * max(1, len(colloids)))(*[_colloid(c) for c in colloids])

@@ -42,6 +42,8 @@ struct rmpcd_system {
     uint32_t *sa_id = nullptr;
     int32_t *sa_cell = nullptr;
     cudaStream_t xfer = nullptr;   // copies of the batch state calls, beside the system's stream
+    int cell_order = RMPCD_ORDER_LINEAR;
+    int *cell_rank_dev = nullptr, *cell_key_dev = nullptr;   // Hilbert tables (built on first use)
     unsigned long long *prof_acc = nullptr;   // [PROF_MAX_BINS * PROF_FIELDS] slab-profile sums
     int *flat_fill = nullptr;                 // [n_rep] records placed by a flatten
     bool dry = false;          // sizing only (rmpcd_workspace_size): count bytes, allocate nothing
@@ -1159,6 +1161,117 @@ rmpcd_status rmpcd_get_colloids(rmpcd_system *sys, int32_t replica, rmpcd_colloi
         }
     }
     return st;
+}
+
+// Index of cell (x, y, z) on the 3-D Hilbert curve through the 2^m cube, by
+// Skilling's transpose method ("Programming the Hilbert curve", AIP Conf.
+// Proc. 707, 2004): undo the excess rotations and reflections from the
+// coarsest level down, Gray-code across the axes, then read the bits level
+// by level, x before y before z.
+static uint64_t hilbert3(int m, uint32_t x, uint32_t y, uint32_t z)
+{
+    if (m <= 0) return 0;
+    uint32_t a[3] = {x, y, z};
+    for (int lev = m - 1; lev >= 1; --lev) {
+        const uint32_t bit = 1u << lev, low = bit - 1u;
+        for (int k = 0; k < 3; ++k) {
+            if (a[k] & bit) {
+                a[0] ^= low;
+            } else {
+                const uint32_t sw = (a[0] ^ a[k]) & low;
+                a[0] ^= sw;
+                a[k] ^= sw;
+            }
+        }
+    }
+    a[1] ^= a[0];
+    a[2] ^= a[1];
+    uint32_t flip = 0;
+    for (int lev = m - 1; lev >= 1; --lev)
+        if (a[2] & (1u << lev)) flip ^= (1u << lev) - 1u;
+    uint64_t h = 0;
+    for (int lev = m - 1; lev >= 0; --lev)
+        for (int k = 0; k < 3; ++k) h = (h << 1) | (((a[k] ^ flip) >> lev) & 1u);
+    return h;
+}
+
+// Place of every cell key k = x + L0 (y + L1 z) of a grid in the given order.
+static void cell_places(const int32_t dims[3], int order, std::vector<int64_t> &place)
+{
+    const int64_t n = (int64_t)dims[0] * dims[1] * dims[2];
+    place.resize((size_t)n);
+    if (order == RMPCD_ORDER_LINEAR) {
+        for (int64_t k = 0; k < n; ++k) place[(size_t)k] = k;
+        return;
+    }
+    int m = 0;
+    while ((1 << m) < std::max(dims[0], std::max(dims[1], dims[2]))) ++m;
+    std::vector<std::pair<uint64_t, int64_t>> hk((size_t)n);
+    for (int64_t k = 0; k < n; ++k) {
+        const uint32_t x = (uint32_t)(k % dims[0]), y = (uint32_t)((k / dims[0]) % dims[1]);
+        const uint32_t z = (uint32_t)(k / ((int64_t)dims[0] * dims[1]));
+        hk[(size_t)k] = {hilbert3(m, x, y, z), k};
+    }
+    std::sort(hk.begin(), hk.end());
+    for (int64_t r = 0; r < n; ++r) place[(size_t)hk[(size_t)r].second] = r;
+}
+
+rmpcd_status rmpcd_cell_places(const int32_t dims[3], int32_t order, int64_t *place)
+{
+    if (!dims || !place) return RMPCD_EINVAL;
+    if (order != RMPCD_ORDER_LINEAR && order != RMPCD_ORDER_HILBERT) return RMPCD_EINVAL;
+    if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1 || dims[0] > 1023 || dims[1] > 1023 || dims[2] > 1023)
+        return RMPCD_EINVAL;
+    std::vector<int64_t> p;
+    cell_places(dims, order, p);
+    std::copy(p.begin(), p.end(), place);
+    return RMPCD_OK;
+}
+
+rmpcd_status rmpcd_set_cell_order(rmpcd_system *sys, int32_t order)
+{
+    if (!sys) return RMPCD_EINVAL;
+    if (order != RMPCD_ORDER_LINEAR && order != RMPCD_ORDER_HILBERT)
+        return fail(sys, RMPCD_EINVAL, "cell order %d is neither linear nor Hilbert", order);
+    if (order == sys->cell_order) return RMPCD_OK;
+    // a fused run's rows are binned in the old order: back to the flat layout first
+    rmpcd_status st = unprime(sys);
+    if (st != RMPCD_OK) return st;
+    if (order == RMPCD_ORDER_HILBERT && !sys->cell_rank_dev) {
+        const size_t nc = (size_t)sys->n_tiles * CPT;
+        std::vector<int> rank(nc), key(nc);
+        for (int r = 0; r < sys->n_rep; ++r) {
+            const ReplicaDev &rp = sys->rep[r];
+            const int32_t dims[3] = {rp.L[0], rp.L[1], rp.nz};
+            std::vector<int64_t> place;
+            cell_places(dims, order, place);
+            const size_t off = (size_t)rp.cell_off, padded = (size_t)rp.n_tiles * CPT;
+            for (size_t k = 0; k < padded; ++k) rank[off + k] = key[off + k] = (int)k;   // padding: itself
+            for (size_t k = 0; k < place.size(); ++k) {
+                rank[off + k] = (int)place[k];
+                key[off + (size_t)place[k]] = (int)k;
+            }
+        }
+        if ((st = dalloc(sys, &sys->cell_rank_dev, nc)) != RMPCD_OK) return st;
+        if ((st = dalloc(sys, &sys->cell_key_dev, nc)) != RMPCD_OK) return st;
+        CK(cudaMemcpyAsync(sys->cell_rank_dev, rank.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, sys->stream));
+        CK(cudaMemcpyAsync(sys->cell_key_dev, key.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, sys->stream));
+        CK(cudaStreamSynchronize(sys->stream));
+    }
+    sys->cell_order = order;
+    sys->d.cell_rank = order == RMPCD_ORDER_HILBERT ? sys->cell_rank_dev : nullptr;
+    sys->d.cell_key = order == RMPCD_ORDER_HILBERT ? sys->cell_key_dev : nullptr;
+    drop_graphs(sys);   // the captured intervals hold the old tables
+    sys->has_sort = false;
+    sys->obs_valid = false;
+    return RMPCD_OK;
+}
+
+rmpcd_status rmpcd_get_cell_order(rmpcd_system *sys, int32_t *order)
+{
+    if (!sys || !order) return RMPCD_EINVAL;
+    *order = sys->cell_order;
+    return RMPCD_OK;
 }
 
 rmpcd_status rmpcd_set_step(rmpcd_system *sys, uint32_t step)

@@ -258,7 +258,7 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
         const int lo = T.ls[c] - pofs;
         const unsigned short *pm = perm + lo;
         typename Traits<MIXED>::Rec *cr = srec + lo;
-        const int lc = lc0 + c;
+        const int lc = cell_key_at(d, rp.cell_off, lc0 + c);   // the cell's key (its place in Hilbert order)
         T.mode[c] = 0;
         T.react[c] = -1;
         T.mnear[c] = MIXED ? 0 : 1;
@@ -426,7 +426,7 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
 // post-collision speed times tau -- and then every cell tests only those
 // (cells without a speed bound, MPC-AT, keep every colloid).
 template <bool MIXED>
-__device__ void near_candidates(TileShared<MIXED> &T, int gt, int cb, int ce)
+__device__ void near_candidates(const Dev &d, TileShared<MIXED> &T, int gt, int cb, int ce)
 {
     const ReplicaDev &rp = T.rp;
     const int lc0 = T.tile * CPT - rp.cell_off;
@@ -434,7 +434,7 @@ __device__ void near_candidates(TileShared<MIXED> &T, int gt, int cb, int ce)
         int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-1, -1, -1};
         float vmax = 0.0f;
         for (int c = cb + gt; c < ce; c += 32) {
-            const int lc = lc0 + c;
+            const int lc = cell_key_at(d, rp.cell_off, lc0 + c);
             const int t = lc / rp.L[0];
             const int kc[3] = {lc % rp.L[0], t % rp.L[1], t / rp.L[1]};
             for (int k = 0; k < 3; ++k) { lo[k] = min(lo[k], kc[k]); hi[k] = max(hi[k], kc[k]); }
@@ -476,7 +476,7 @@ __device__ void near_candidates(TileShared<MIXED> &T, int gt, int cb, int ce)
     __syncthreads();
     for (int c = cb + gt; c < ce; c += CP_THREADS) {
         if (T.cnt[c] == 0 || T.vbc[c] < 0.0f) continue;   // empty cell: no test
-        const int lc = lc0 + c;
+        const int lc = cell_key_at(d, rp.cell_off, lc0 + c);
         const int t = lc / rp.L[0];
         const int kc[3] = {lc % rp.L[0], t % rp.L[1], t / rp.L[1]};
         int mn = 0;
@@ -668,7 +668,7 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
     __syncthreads();
     if constexpr (MANY) {
         if (opts & CP_NEXT) {
-            near_candidates(T, gt, cb, ce);
+            near_candidates(d, T, gt, cb, ce);
             __syncthreads();
         }
     }
@@ -723,7 +723,7 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
                 } else {
                     Rec fl = rec;
                     rec_flight(hp, fl);
-                    nkey = rp.cell_off + rec_key(hp, fl, T.shn, shnf);
+                    nkey = bin_cell(d, rp.cell_off, rec_key(hp, fl, T.shn, shnf));
                 }
             }
             ent[p] = nkey;

@@ -769,7 +769,7 @@ __device__ void md_body(const Dev &d, MDShared<MIXED> &S, const ReplicaDev &rp, 
             for (int t = 0; t < 3; ++t) { rec.o[t] = w.o[t]; rec.v[t] = w.v[t]; }
             rec.fid = do_bin ? (w.fid | F_PROP) : (w.fid & ~F_PROP);
             const float sf[3] = {(float)sh[0], (float)sh[1], (float)sh[2]};
-            put_near(d, rbuf, bbuf, do_bin, do_bin ? rp.cell_off + cell_key_m(rp, w.c, w.o, sf) : 0, w.slot, rec);
+            put_near(d, rbuf, bbuf, do_bin, do_bin ? bin_cell(d, rp.cell_off, cell_key_m(rp, w.c, w.o, sf)) : 0, w.slot, rec);
         } else {
             for (int t = 0; t < 3; ++t) w.v[t] = fma(hdt, w.f[t], w.v[t]);
             wrap_periodic_d(rp, w.x);
@@ -778,7 +778,7 @@ __device__ void md_body(const Dev &d, MDShared<MIXED> &S, const ReplicaDev &rp, 
             rec.fid = do_bin ? (w.fid | F_PROP) : (w.fid & ~F_PROP);
             rec.u0 = 0u;
             rec.u1 = 0.0;
-            put_near(d, rbuf, bbuf, do_bin, do_bin ? rp.cell_off + cell_key_d(rp, w.x, sh) : 0, w.slot, rec);
+            put_near(d, rbuf, bbuf, do_bin, do_bin ? bin_cell(d, rp.cell_off, cell_key_d(rp, w.x, sh)) : 0, w.slot, rec);
         }
     }
     __syncwarp();
@@ -1139,7 +1139,7 @@ __global__ void __launch_bounds__(MDW_NT) k_md_wide(Dev d, int r, uint32_t step,
         rec.cw = cw_make(w.c[0], w.c[1], w.c[2]);
         for (int t = 0; t < 3; ++t) { rec.o[t] = w.o[t]; rec.v[t] = w.v[t]; }
         rec.fid = do_bin ? (w.fid | F_PROP) : (w.fid & ~F_PROP);
-        put_near(d, rbuf, bbuf, do_bin, do_bin ? rp.cell_off + cell_key_m(rp, w.c, w.o, sf) : 0, w.slot, rec);
+        put_near(d, rbuf, bbuf, do_bin, do_bin ? bin_cell(d, rp.cell_off, cell_key_m(rp, w.c, w.o, sf)) : 0, w.slot, rec);
     };
 #pragma unroll
     for (int p = 0; p < MDW_PPT; ++p)

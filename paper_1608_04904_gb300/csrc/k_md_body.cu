@@ -475,7 +475,7 @@ __device__ __forceinline__ void finish_m(const Dev &d, const ReplicaDev &rp, int
     rec.cw = cw_make(c[0], c[1], c[2]);
     for (int t = 0; t < 3; ++t) { rec.o[t] = w.o[t]; rec.v[t] = w.v[t]; }
     rec.fid = do_bin ? (w.fid | F_PROP) : (w.fid & ~F_PROP);
-    put_near(d, rbuf, bbuf, do_bin, do_bin ? rp.cell_off + cell_key_m(rp, c, w.o, sf) : 0, slot, rec);
+    put_near(d, rbuf, bbuf, do_bin, do_bin ? bin_cell(d, rp.cell_off, cell_key_m(rp, c, w.o, sf)) : 0, slot, rec);
 }
 
 // gsm_bytes: room for the lookup grid at the start of the dynamic shared
@@ -655,7 +655,7 @@ __global__ void __launch_bounds__(MDB_NT, 2) k_md_body(Dev d, uint32_t step, int
             rec.fid = do_bin ? (w.fid | F_PROP) : (w.fid & ~F_PROP);
             rec.u0 = 0u;
             rec.u1 = 0.0;
-            put_near(d, rbuf, bbuf, do_bin, do_bin ? rp.cell_off + cell_key_d(rp, w.x, sh) : 0, w.slot, rec);
+            put_near(d, rbuf, bbuf, do_bin, do_bin ? bin_cell(d, rp.cell_off, cell_key_d(rp, w.x, sh)) : 0, w.slot, rec);
         }
     }
     if (tid == 0) {

@@ -539,7 +539,7 @@ __device__ __forceinline__ void finish_particle(const Dev &d, const ReplicaDev &
     for (int q = 0; q < 3; ++q) { rec.o[q] = w.o[q]; rec.v[q] = w.v[q]; }
     rec.fid = do_bin ? (w.fid | F_PROP) : (w.fid & ~F_PROP);
     const float sf[3] = {(float)sh[0], (float)sh[1], (float)sh[2]};
-    put_near(d, rbuf, bbuf, do_bin, do_bin ? rp.cell_off + cell_key_m(rp, w.c, w.o, sf) : 0, w.slot, rec);
+    put_near(d, rbuf, bbuf, do_bin, do_bin ? bin_cell(d, rp.cell_off, cell_key_m(rp, w.c, w.o, sf)) : 0, w.slot, rec);
 }
 
 __device__ __forceinline__ void finish_particle(const Dev &d, const ReplicaDev &rp, FWorkD &w, const double sh[3],
@@ -552,7 +552,7 @@ __device__ __forceinline__ void finish_particle(const Dev &d, const ReplicaDev &
     rec.fid = do_bin ? (w.fid | F_PROP) : (w.fid & ~F_PROP);
     rec.u0 = 0u;
     rec.u1 = 0.0;
-    put_near(d, rbuf, bbuf, do_bin, do_bin ? rp.cell_off + cell_key_d(rp, w.x, sh) : 0, w.slot, rec);
+    put_near(d, rbuf, bbuf, do_bin, do_bin ? bin_cell(d, rp.cell_off, cell_key_d(rp, w.x, sh)) : 0, w.slot, rec);
 }
 
 // --- the cluster exchange of the force partials -------------------------------

@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(MDN_NT, 1) k_md_network(Dev d, uint32_t step, 
         rec.fid = do_bin ? (w.fid | F_PROP) : (w.fid & ~F_PROP);
         rec.u0 = 0u;
         rec.u1 = 0.0;
-        put_near(d, rbuf, bbuf, do_bin, do_bin ? rp.cell_off + cell_key_d(rp, w.x, sh) : 0, w.slot, rec);
+        put_near(d, rbuf, bbuf, do_bin, do_bin ? bin_cell(d, rp.cell_off, cell_key_d(rp, w.x, sh)) : 0, w.slot, rec);
     }
     // beads back to memory; centre and reach of the next interval's near test
     for (int j = tid; j < nb; j += MDN_NT) {

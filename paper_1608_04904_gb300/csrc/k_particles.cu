@@ -147,7 +147,7 @@ __global__ void k_particles(Dev d, int mode, uint32_t step, int rbuf, int bbuf)
         int c[3] = {cw_get(rec.cw, 0), cw_get(rec.cw, 1), cw_get(rec.cw, 2)};
         if (mode == PM_BIN) {
             float sf[3] = {(float)s[0], (float)s[1], (float)s[2]};
-            bin_particle(d, bbuf, rp.cell_off + cell_key_m(rp, c, rec.o, sf), i);
+            bin_particle(d, bbuf, bin_cell(d, rp.cell_off, cell_key_m(rp, c, rec.o, sf)), i);
             return;
         }
         if (rp.n_col > 0 && near_test_m(rp, rp.n_col, d.colCi + 3 * rp.col_off, d.colXf + 3 * rp.col_off,
@@ -164,13 +164,13 @@ __global__ void k_particles(Dev d, int mode, uint32_t step, int rbuf, int bbuf)
             store_rec(recs + i, rec);
         } else {
             float sf[3] = {(float)s[0], (float)s[1], (float)s[2]};
-            bin_record(d, bbuf, rp.cell_off + cell_key_m(rp, c, o, sf), rec);
+            bin_record(d, bbuf, bin_cell(d, rp.cell_off, cell_key_m(rp, c, o, sf)), rec);
         }
     } else {
         RecD *recs = reinterpret_cast<RecD *>(d.rec[rbuf]);
         RecD rec = load_rec(recs + i);
         if (mode == PM_BIN) {
-            bin_particle(d, bbuf, rp.cell_off + cell_key_d(rp, rec.x, s), i);
+            bin_particle(d, bbuf, bin_cell(d, rp.cell_off, cell_key_d(rp, rec.x, s)), i);
             return;
         }
         if (rp.n_col > 0 && near_test_d(d, rp, rec.x, rec.v)) {
@@ -184,7 +184,7 @@ __global__ void k_particles(Dev d, int mode, uint32_t step, int rbuf, int bbuf)
             for (int k = 0; k < 3; ++k) { rec.x[k] = x[k]; rec.v[k] = v[k]; }
             store_rec(recs + i, rec);
         } else {
-            bin_record(d, bbuf, rp.cell_off + cell_key_d(rp, x, s), rec);
+            bin_record(d, bbuf, bin_cell(d, rp.cell_off, cell_key_d(rp, x, s)), rec);
         }
     }
 }

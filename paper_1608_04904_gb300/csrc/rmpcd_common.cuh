@@ -202,11 +202,26 @@ struct Dev {
     int ovf_cap;                 // entries each overflow list holds
     int lb_limit;                // polls before a look-back wait gives up (ERR_TIMEOUT)
     int lb_stall;                // test hook: the look-back treats every predecessor as not ready
+    const int *cell_rank;        // Hilbert order: place of cell key k of a replica at cell_off + k (NULL: linear)
+    const int *cell_key;         //   and the key of the cell at place cell_off + p
     int many_col;                // 1: some replica has >= CP_NEAR_CAND_MIN colloids
     int n_rep;
     int n_tiles;
     int n_total;
 };
+
+// Where the cells live: the row (and tile place) of the cell with key k of
+// a replica whose cells start at cell_off -- k itself in linear order, its
+// compact Hilbert rank in Hilbert order -- and the key of the cell at a
+// place.  A cell's draws and geometry always use its key.
+__device__ __forceinline__ int bin_cell(const Dev &d, int cell_off, int key)
+{
+    return cell_off + (d.cell_rank ? __ldg(d.cell_rank + cell_off + key) : key);
+}
+__device__ __forceinline__ int cell_key_at(const Dev &d, int cell_off, int place)
+{
+    return d.cell_key ? __ldg(d.cell_key + cell_off + place) : place;
+}
 
 __device__ __forceinline__ uint32_t resolve_step(const Dev &d, uint32_t step)
 {

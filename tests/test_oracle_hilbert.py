@@ -60,3 +60,41 @@ def test_ranks_of_a_box_follow_the_curve(orc, L):
     path = xyz[np.argsort(rank)]
     steps = np.abs(np.diff(path, axis=0)).sum(1)
     assert np.mean(steps == 1) > 0.8
+
+
+def _by_id(o):
+    k = np.argsort(o.id)
+    return o.x[k], o.v[k], o.flags[k]
+
+
+@pytest.mark.parametrize("setup", ["dimer_bulk_slabs", "channel"])
+def test_hilbert_storage_order_changes_no_physics(orc, setup):
+    """The storage order of the cells is memory layout only: with the cells
+    in Hilbert order the same steps give the same state, bit for bit, once
+    matched by particle id; and storage runs by (Hilbert rank of the cell
+    key, id).  (Keying a cell's draws by its rank instead of its key would
+    change the velocities; the GPU path's parity tests in Hilbert order rest
+    on this equality.)"""
+    from paper_1608_04904_gb300 import synth
+    if setup == "dimer_bulk_slabs":
+        cfg, col, bonds = synth.dimer32(precision="fp64", seed=7, L=16)
+        cfg = dict(cfg, slabs=[(0.0, 3.0, 1.3), (8.0, 11.0, 0.7)], bulk_rate=0.05)
+        x, v, f = synth.solvent(cfg, col, seed=8, frac_b=0.3)
+        kw = dict(colloids=synth.colloid_arrays(col), bonds=bonds)
+    else:
+        cfg = synth.base_config(L=(10, 6, 7), walls=1, rho_wall=10, g=(0.002, 0.0, 0.0), tau=1.0, seed=9,
+                                precision="fp64", bulk_rate=0.02)
+        x, v, f = synth.solvent(cfg, seed=10, frac_b=0.4)
+        kw = {}
+    a = orc.OracleSystem(cfg, x, v, f, **kw)
+    b = orc.OracleSystem(cfg, x, v, f, cell_order="hilbert", **kw)
+    a.step(3)
+    b.step(3)
+    for p, q in zip(_by_id(a), _by_id(b)):
+        assert np.array_equal(p, q)
+    assert np.array_equal(a.X, b.X) and np.array_equal(a.V, b.V)
+    r = b.rank[b.key]
+    assert np.all(np.diff(r) >= 0)
+    same = np.diff(r) == 0
+    assert np.all(np.diff(b.id.astype(np.int64))[same] > 0)
+    assert not np.array_equal(a.key, b.key)   # the orders do differ
