@@ -1,8 +1,9 @@
 """GPU parity in compact Hilbert cell order (rmpcd_set_cell_order): fused
-steps against the oracle run in the same order, bit for bit on the FP64 path
-(storage order by (Hilbert rank, id), keys, flags, positions, velocities);
-the mixed path in Hilbert order equal by id to the mixed path in linear
-order; and a switch of order in the middle of a run."""
+steps against the oracle run in the same order on the FP64 path (storage
+order by (Hilbert rank, id), keys and flags identical; positions and
+velocities within the FP64 tolerance); the mixed path in Hilbert order
+equal by id, bit for bit, to the mixed path in linear order; and a switch
+of order in the middle of a run."""
 import numpy as np
 import pytest
 
