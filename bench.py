@@ -121,7 +121,7 @@ class _NetworkOracle:
         self.orc = oracle
         self.net = oracle.Network(net["xb"], net["vb"], net["mb"], net["eps_A"], net["eps_B"], net["catalytic"],
                                   net["sigma"], [links[k] for k in order], d[order])
-        self.o = oracle.OracleSystem(cfg, x, v, fl)
+        self.o = oracle.OracleSystem(cfg, x, v, fl, cell_order=CELL_ORDER)
         self.cfg = cfg
 
     def step(self, k):
@@ -143,7 +143,7 @@ def oracle_system(oracle, rep, state):
     if body is not None and "network" in body:
         return _NetworkOracle(oracle, cfg, state, body["network"])
     return oracle.OracleSystem(cfg, x, v, fl, colloids=synth.colloid_arrays(col) if col else None, bonds=bonds,
-                               body=body)
+                               body=body, cell_order=CELL_ORDER)
 
 
 def kernel_hash(kernel="k_cellpass"):
@@ -373,7 +373,7 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-CELL_ORDER = "linear"
+CELL_ORDER = "hilbert"
 
 
 def make_system(api, reps, states, precision, stream):
@@ -522,8 +522,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--bucket-cap", type=int, default=None,
                     help="cell row width (default: the automatic width)")
-    ap.add_argument("--cell-order", default="linear", choices=["linear", "hilbert"],
-                    help="storage order of the cells (rmpcd_set_cell_order)")
+    ap.add_argument("--cell-order", default="hilbert", choices=["linear", "hilbert"],
+                    help="storage order of the cells (rmpcd_set_cell_order; the paper sorts by compact "
+                         "Hilbert index)")
     ap.add_argument("--replicas", type=int, default=None,
                     help="batch256 only: keep the first N replicas (a smaller case for profiling)")
     args = ap.parse_args()
