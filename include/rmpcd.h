@@ -232,7 +232,7 @@ rmpcd_status rmpcd_get_state_all(rmpcd_system *sys, double *x, double *v, uint8_
  * the storage order.  rmpcd_set_cell_order moves a fused run's state back to
  * the flat layout first and drops captured graphs; the Hilbert tables (two
  * ints per cell) are allocated on first use.  rmpcd_cell_places: the place
- * of every key of a grid dims[3] (each in [1, 1023]) in the given order
+ * of every key of a grid dims[3] (each in [1, 1023], at most 2^28 cells) in the given order
  * (host memory, dims[0] dims[1] dims[2] entries; no CUDA call).  Errors:
  * EINVAL, ENOMEM, ECUDA. */
 #define RMPCD_ORDER_LINEAR 0

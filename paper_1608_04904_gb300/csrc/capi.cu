@@ -1222,6 +1222,7 @@ rmpcd_status rmpcd_cell_places(const int32_t dims[3], int32_t order, int64_t *pl
     if (order != RMPCD_ORDER_LINEAR && order != RMPCD_ORDER_HILBERT) return RMPCD_EINVAL;
     if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1 || dims[0] > 1023 || dims[1] > 1023 || dims[2] > 1023)
         return RMPCD_EINVAL;
+    if ((int64_t)dims[0] * dims[1] * dims[2] > (1ll << 28)) return RMPCD_EINVAL;   // host work bound
     std::vector<int64_t> p;
     cell_places(dims, order, p);
     std::copy(p.begin(), p.end(), place);
