@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librmpcd.so")
 SOURCES = ["capi.cu", "k_cellpass.cu", "k_md.cu", "k_md_fast.cu", "k_md_body.cu", "k_md_network.cu", "k_particles.cu",
            "k_noalloc.cu"]
-HEADERS = ["rmpcd_common.cuh", "rmpcd_kernels.cuh"]
+HEADERS = ["rmpcd_common.cuh", "rmpcd_kernels.cuh", "rmpcd_fixed.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "--fmad=false", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-Xcompiler", "-ffp-contract=off"]

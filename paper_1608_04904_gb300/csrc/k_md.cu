@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "rmpcd_kernels.cuh"
+#include "rmpcd_fixed.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -142,7 +143,7 @@ __device__ __forceinline__ void force_m(const ReplicaDev &rp, MDShared<true> &S,
             for (int k = 0; k < 3; ++k) {
                 const float fk = fr * d[k];
                 f[k] = f[k] + fk;
-                const long long q = __float2ll_rn(fk * 0x1p40f);   // exact scaling, one rounding
+                const long long q = fx40_any(fk);   // exact scaling, one rounding
                 if (REG) {
 #pragma unroll
                     for (int jj = 0; jj < NCR; ++jj)
@@ -438,7 +439,7 @@ __device__ __forceinline__ bool cc_pair_m(const ReplicaDev &rp, const SH &S, int
     const float s2 = sg * sg * ir2;
     const float s6 = s2 * s2 * s2;
     const float fr = 24.0f * ep * s6 * (2.0f * s6 - 1.0f) * ir2;
-    for (int k = 0; k < 3; ++k) q[k] = __float2ll_rn(fr * d[k] * 0x1p40f);
+    for (int k = 0; k < 3; ++k) q[k] = fx40_any(fr * d[k]);
     return true;
 }
 
@@ -957,7 +958,7 @@ __device__ __forceinline__ void force_wide(const ReplicaDev &rp, WideShared &S, 
             for (int k = 0; k < 3; ++k) {
                 const float fk = fr * d[k];
                 w.f[k] = w.f[k] + fk;
-                const long long q64 = __float2ll_rn(fk * 0x1p40f);
+                const long long q64 = fx40_any(fk);
                 atomicAdd(&S.Fq[3 * j + k], (unsigned long long)(-q64));
             }
         }

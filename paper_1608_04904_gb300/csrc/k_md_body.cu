@@ -38,6 +38,7 @@
 #include <type_traits>
 
 #include "rmpcd_kernels.cuh"
+#include "rmpcd_fixed.cuh"
 
 namespace rmpcd {
 
@@ -350,8 +351,8 @@ __device__ __forceinline__ void add_fixed(long long acc[6], const float fk[3], c
     const float c[3] = {rb[1] * fk[2] - rb[2] * fk[1], rb[2] * fk[0] - rb[0] * fk[2], rb[0] * fk[1] - rb[1] * fk[0]};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        acc[k] -= __float2ll_rn(fk[k] * 0x1p40f);
-        acc[3 + k] -= __float2ll_rn(c[k] * 0x1p40f);
+        acc[k] -= fx40_any(fk[k]);
+        acc[3 + k] -= fx40_any(c[k]);
     }
 }
 

@@ -30,6 +30,7 @@
 #include <type_traits>
 
 #include "rmpcd_kernels.cuh"
+#include "rmpcd_fixed.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -329,17 +330,6 @@ __device__ __forceinline__ void write_positions_d(FShared &S, const LaneD &C, in
 }
 
 // --- particle side ----------------------------------------------------------
-// round(f 2^40) to the nearest even integer, exactly as one float -> int64
-// conversion would give it, by two 32-bit conversions: with h = f 2^9
-// rounded to an integer, f - h 2^-9 is exact (Sterbenz) and at most 2^-10 in
-// magnitude, and h 2^31 is even, so the ties round the same way.  Valid for
-// |f| < 2^22.
-__device__ __forceinline__ long long fx40(float f)
-{
-    const float h = rintf(f * 0x1p9f);
-    const float r = f - h * 0x1p-9f;
-    return ((long long)__float2int_rn(h) << 31) + (long long)__float2int_rn(r * 0x1p40f);
-}
 
 // WCA force on one solvent particle (§1.4); the reaction on colloid j goes to
 // acc in fixed point.  inside: the particle is within the cut-off of a
