@@ -958,8 +958,7 @@ __device__ __forceinline__ void force_wide(const ReplicaDev &rp, WideShared &S, 
             for (int k = 0; k < 3; ++k) {
                 const float fk = fr * d[k];
                 w.f[k] = w.f[k] + fk;
-                const long long q64 = fx40_any(fk);
-                atomicAdd(&S.Fq[3 * j + k], (unsigned long long)(-q64));
+                sub_fixed_agg(S.Fq, 3 * j + k, fx40_any(fk));
             }
         }
     }
