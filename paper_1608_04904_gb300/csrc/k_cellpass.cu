@@ -761,12 +761,27 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
             const int wtot = appends ? __shfl_sync(0xffffffffu, incl, 31) : 0;
             int nbase = 0;
             if ((gt & 31) == 31 && wtot > 0) nbase = atomicAdd(&d.near_count[T.r], wtot);
+            // the lanes that bin into one cell take their places with one
+            // atomic (the group's size), issued for every u before any result
+            // is used; then each lane's place is the leader's base plus its
+            // rank in the group
             int pos[K];
+            unsigned grp[K];
 #pragma unroll
             for (int u = 0; u < K; ++u) {
                 const int p = gt + u * G;
                 const int key = p < nb ? ent[p] : -1;
-                pos[u] = key >= 0 ? atomicAdd(&d.count[a.nxt][key], 1) : -1;
+                grp[u] = __match_any_sync(0xffffffffu, key);
+                const int leader = __ffs(grp[u]) - 1;
+                pos[u] = (key >= 0 && (gt & 31) == leader) ? atomicAdd(&d.count[a.nxt][key], __popc(grp[u])) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < K; ++u) {
+                const int p = gt + u * G;
+                const int key = p < nb ? ent[p] : -1;
+                const int leader = __ffs(grp[u]) - 1;
+                const int base = __shfl_sync(0xffffffffu, pos[u], leader);
+                pos[u] = key >= 0 ? base + __popc(grp[u] & ((1u << (gt & 31)) - 1u)) : -1;
             }
             if (wtot > 0) {
                 int k = __shfl_sync(0xffffffffu, nbase, 31) + incl - mine;
