@@ -131,21 +131,6 @@ __device__ __forceinline__ void add_near(const Dev &d, int r, const ReplicaDev &
     }
 }
 
-// bin_record with one count atomic per group of converged lanes that bin
-// into the same cell (a sorted state bins consecutive particles into one
-// cell): the leader takes the group's places, each lane its rank among them.
-template <class Rec>
-__device__ __forceinline__ void bin_record_agg(const Dev &d, int buf, int gcell, const Rec &rec)
-{
-    const unsigned act = __activemask();
-    const unsigned grp = __match_any_sync(act, gcell);
-    const int lane = (int)(threadIdx.x & 31u), leader = __ffs(grp) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(&d.count[buf][gcell], __popc(grp));
-    base = __shfl_sync(grp, base, leader);
-    bin_record_at(d, buf, gcell, base + __popc(grp & ((1u << lane) - 1u)), rec);
-}
-
 template <bool MIXED>
 __global__ void k_particles(Dev d, int mode, uint32_t step, int rbuf, int bbuf)
 {
@@ -179,7 +164,7 @@ __global__ void k_particles(Dev d, int mode, uint32_t step, int rbuf, int bbuf)
             store_rec(recs + i, rec);
         } else {
             float sf[3] = {(float)s[0], (float)s[1], (float)s[2]};
-            bin_record_agg(d, bbuf, bin_cell(d, rp.cell_off, cell_key_m(rp, c, o, sf)), rec);
+            bin_record(d, bbuf, bin_cell(d, rp.cell_off, cell_key_m(rp, c, o, sf)), rec);
         }
     } else {
         RecD *recs = reinterpret_cast<RecD *>(d.rec[rbuf]);
@@ -199,7 +184,7 @@ __global__ void k_particles(Dev d, int mode, uint32_t step, int rbuf, int bbuf)
             for (int k = 0; k < 3; ++k) { rec.x[k] = x[k]; rec.v[k] = v[k]; }
             store_rec(recs + i, rec);
         } else {
-            bin_record_agg(d, bbuf, bin_cell(d, rp.cell_off, cell_key_d(rp, x, s)), rec);
+            bin_record(d, bbuf, bin_cell(d, rp.cell_off, cell_key_d(rp, x, s)), rec);
         }
     }
 }
