@@ -2132,7 +2132,8 @@ rmpcd_status rmpcd_set_body(rmpcd_system *sys, int32_t replica, const rmpcd_body
     rp.col_off = g;
     rp.body = replica;
     CK(cudaMemcpyAsync(const_cast<ReplicaDev *>(sys->d.rep) + replica, &rp, sizeof rp, cudaMemcpyHostToDevice, s));
-    // working state of the near particles
+    // working state of the near particles (the mixed body kernel keeps its
+    // per-sub-step list of particles in reach of a bead past its 32-byte records)
     const size_t need = (sys->mixed ? 64 : 80) * (size_t)std::max(sys->n_total, 1);
     if (sys->work_bytes < need) {
         CK(cudaStreamSynchronize(s));

@@ -187,7 +187,8 @@ struct TileShared {
     int __align__(16) cnt_next[CPT];   // the next tile's counts (asynchronous copy during this tile)
     double sh[3], shn[3];     // fp64 path
     float shf[3], shnf[3];
-    R vcm[CPT][3], ax[CPT][3];
+    __align__(16) R vcm[CPT][4];   // [3]: padding (a cell's row is one 16-byte load on the mixed path)
+    __align__(16) R ax[CPT][4];
     int react[CPT];
     unsigned char mode[CPT];    // bits 0-1: 0 untouched, 1 SRD rotation, 2 MPC-AT; 4: reservoir A, 8: reservoir B
     unsigned char mnear[CPT];   // 0: no particle of the cell can come near a colloid
@@ -286,12 +287,15 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
                 long long fx[3] = {0ll, 0ll, 0ll};
                 bool wide = false;
 #pragma unroll 2
-                for (int i = 0; i < n; ++i)
+                for (int i = 0; i < n; ++i) {
+                    const float4 q = *reinterpret_cast<const float4 *>(cr[i].v);   // v and fid: one load
+                    const float vi[3] = {q.x, q.y, q.z};
                     for (int k = 0; k < 3; ++k) {
-                        const float t = cr[i].v[k] * 0x1p24f;
+                        const float t = vi[k] * 0x1p24f;
                         wide |= !(fabsf(t) < 0x1p31f);
                         fx[k] += (long long)__float2int_rn(t);
                     }
+                }
                 if (wide) {
                     // a speed of 128 or more (or not finite): the split conversion
                     fx[0] = fx[1] = fx[2] = 0ll;
@@ -363,9 +367,19 @@ __device__ __forceinline__ void cells_D(const Dev &d, const CellPassArgs &a, Til
                 R u2 = R(0);
                 int nb_ = 0;
                 for (int i = 0; i < n; ++i) {   // order-free: a maximum and a count
-                    const R a0 = cr[i].v[0] - vc[0], a1 = cr[i].v[1] - vc[1], a2 = cr[i].v[2] - vc[2];
+                    R vi[3];
+                    uint32_t fi;
+                    if constexpr (MIXED) {
+                        const float4 q = *reinterpret_cast<const float4 *>(cr[i].v);   // v and fid: one load
+                        vi[0] = q.x; vi[1] = q.y; vi[2] = q.z;
+                        fi = __float_as_uint(q.w);
+                    } else {
+                        vi[0] = cr[i].v[0]; vi[1] = cr[i].v[1]; vi[2] = cr[i].v[2];
+                        fi = cr[i].fid;
+                    }
+                    const R a0 = vi[0] - vc[0], a1 = vi[1] - vc[1], a2 = vi[2] - vc[2];
                     u2 = max(u2, a0 * a0 + a1 * a1 + a2 * a2);
-                    nb_ += (cr[i].fid & F_B) ? 1 : 0;
+                    nb_ += (fi & F_B) ? 1 : 0;
                 }
                 nbB = nb_;
                 vb = (float)(sqrt(vc[0] * vc[0] + vc[1] * vc[1] + vc[2] * vc[2]) + sqrt(u2));
@@ -685,6 +699,61 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
     // E: apply and write (flat layout: at the canonical slot; fused run:
     // classify for the next collision -- the next cell of a far particle goes
     // to ent[p], -2 marks a near particle)
+    if constexpr (MIXED && FUSED) {
+        // the mixed fused pass: the cell word unpacked once per particle (the
+        // flight, the near test and the next key take the coordinates) and
+        // packed again only when the flight moved it; a cell's centre and
+        // axis are one 16-byte load each
+#pragma unroll 1
+        for (int p = gt; p < nb; p += G) {
+            const int c = cb + cellof[p];
+            RecM rec = srec[p];
+            int cc[3] = {cw_get(rec.cw, 0), cw_get(rec.cw, 1), cw_get(rec.cw, 2)};
+            if (fly_in_E && !(rec.fid & F_PROP)) {
+                flight_m(hp, cc, rec.o, rec.v);
+                rec.cw = cw_make(cc[0], cc[1], cc[2]);
+            }
+            rec.fid &= ~F_PROP;
+            const unsigned mode = T.mode[c];
+            if ((mode & 3) == 1) {
+                const float4 vq = *reinterpret_cast<const float4 *>(T.vcm[c]);
+                const float4 nq = *reinterpret_cast<const float4 *>(T.ax[c]);
+                const float vc[3] = {vq.x, vq.y, vq.z}, nh[3] = {nq.x, nq.y, nq.z};
+                const float u0 = rec.v[0] - vc[0], u1 = rec.v[1] - vc[1], u2 = rec.v[2] - vc[2];
+                const float dot = nh[0] * u0 + nh[1] * u1 + nh[2] * u2;
+                const float x0 = nh[1] * u2 - nh[2] * u1;
+                const float x1 = nh[2] * u0 - nh[0] * u2;
+                const float x2 = nh[0] * u1 - nh[1] * u0;
+                const float od = omc * dot;
+                rec.v[0] = vc[0] + (ca * u0 + sa * x0 + od * nh[0]);
+                rec.v[1] = vc[1] + (ca * u1 + sa * x1 + od * nh[1]);
+                rec.v[2] = vc[2] + (ca * u2 + sa * x2 + od * nh[2]);
+            }
+            if (T.react[c] == p) rec.fid &= ~(F_B | F_TAG);
+            if (mode & 4) rec.fid &= ~(F_B | F_TAG);
+            if (mode & 8) rec.fid = (rec.fid & ~F_TAG) | F_B;
+            srec[p] = rec;
+            int nkey = -1;
+            if (opts & CP_NEXT) {
+                bool near;
+                if constexpr (MANY)
+                    near = T.mnear[c] && (T.vbc[c] < 0.0f
+                                              ? near_test_m(hp, n_col, T.nf.Ci, T.nf.Cf, T.nf.Rb, cc, rec.o, rec.v)
+                                              : near_test_mask(hp, T.cand, T.nf, cc, rec.o, rec.v));
+                else
+                    near = n_col > 0 && T.mnear[c] && near_test_m(hp, n_col, T.nf.Ci, T.nf.Cf, T.nf.Rb, cc, rec.o, rec.v);
+                if (near) {
+                    nkey = -2;
+                } else {
+                    int fc[3] = {cc[0], cc[1], cc[2]};
+                    float fo[3] = {rec.o[0], rec.o[1], rec.o[2]}, fv[3] = {rec.v[0], rec.v[1], rec.v[2]};
+                    flight_m(hp, fc, fo, fv);
+                    nkey = bin_cell(d, rp.cell_off, cell_key_m(hp, fc, fo, shnf));
+                }
+            }
+            ent[p] = nkey;
+        }
+    } else {
 #pragma unroll 1
     for (int p = gt; p < nb; p += G) {
         const int c = cb + cellof[p];
@@ -737,6 +806,7 @@ __device__ void cells_batch(const Dev &d, const CellPassArgs &a, TileShared<MIXE
             }
             if (opts & CP_OBS) srec[p] = rec;
         }
+    }
     }
     if constexpr (FUSED) {
         // bin for the next collision: all count atomics, then the record

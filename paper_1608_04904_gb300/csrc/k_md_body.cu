@@ -33,8 +33,9 @@
 // lists, in ascending order, every bead whose cut-off plus a margin reaches
 // the cell, so the FP64 path adds the same pair forces in the same order as
 // a scan over all beads.  Body force and torque are summed as 64-bit fixed
-// point (2^-40): per thread, per warp by shuffles, then over the warps, so
-// the totals do not depend on the order of the near list.
+// point (2^-40) -- per pair on the FP64 path, per particle (its FP32 sums over
+// its beads) on the mixed path --: per thread, per warp by shuffles, then over
+// the warps, so the totals do not depend on the order of the near list.
 #include <type_traits>
 
 #include "rmpcd_kernels.cuh"
@@ -86,6 +87,7 @@ struct BodyShared {
     const unsigned short *glist;
     const unsigned short *gs16, *gl16;   // the lookup grid copied to shared memory (gsm: in use)
     int gsm;
+    int nreach;                      // mixed sub-step: near particles listed in reach of a bead
     unsigned long long wpart[MDB_NW][6];
 };
 
@@ -346,17 +348,22 @@ __device__ __forceinline__ void grid_range(const BodyShared &S, const float dc[3
     }
 }
 
-__device__ __forceinline__ void add_fixed(long long acc[6], const float fk[3], const float rb[3])
+// A particle's pair-force sum f and torque sum tq (about the body centre)
+// into the body's fixed-point totals, with the opposite sign.
+__device__ __forceinline__ void sub_fixed6(long long acc[6], const float f[3], const float tq[3])
 {
-    const float c[3] = {rb[1] * fk[2] - rb[2] * fk[1], rb[2] * fk[0] - rb[0] * fk[2], rb[0] * fk[1] - rb[1] * fk[0]};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        acc[k] -= fx40_any(fk[k]);
-        acc[3 + k] -= fx40_any(c[k]);
+        acc[k] -= fx40_any(f[k]);
+        acc[3 + k] -= fx40_any(tq[k]);
     }
 }
 
 // Mixed: force on one particle (cell c, offset o) from the beads it reaches.
+// The particle's pair forces and their torques (R b_j) x f are summed in
+// FP32 in bead order and enter the body's fixed-point totals once per
+// particle: order-free over particles, like the per-pair sums of the FP64
+// path, with six conversions per particle instead of six per pair.
 __device__ __forceinline__ bool body_force_m(const ReplicaDev &rp, const BodyShared &S, const BeadSmem &B,
                                              const int c[3], const float o[3], uint32_t fid, float f[3],
                                              long long acc[6])
@@ -368,7 +375,8 @@ __device__ __forceinline__ bool body_force_m(const ReplicaDev &rp, const BodySha
     int beg, end;
     grid_range(S, dc, beg, end);
     f[0] = f[1] = f[2] = 0.0f;
-    bool inside = false;
+    float tq[3] = {0.0f, 0.0f, 0.0f};
+    bool inside = false, touch = false;
     const int isb = (fid & F_B) ? 1 : 0;
     const unsigned short *gl = S.gsm ? S.gl16 : S.glist;
     int jn = beg < end ? gl[beg] : 0;
@@ -383,10 +391,14 @@ __device__ __forceinline__ bool body_force_m(const ReplicaDev &rp, const BodySha
             const float fk[3] = {fr * d[0], fr * d[1], fr * d[2]};
 #pragma unroll
             for (int k = 0; k < 3; ++k) f[k] = f[k] + fk[k];
-            add_fixed(acc, fk, rb);
+            tq[0] = tq[0] + (rb[1] * fk[2] - rb[2] * fk[1]);
+            tq[1] = tq[1] + (rb[2] * fk[0] - rb[0] * fk[2]);
+            tq[2] = tq[2] + (rb[0] * fk[1] - rb[1] * fk[0]);
+            touch = true;
             inside = inside || B.cat[j] != 0;
         }
     }
+    if (touch) sub_fixed6(acc, f, tq);
 #pragma unroll
     for (int k = 0; k < 3; ++k) f[k] = f[k] + rp.g_f[k];
     return inside;
@@ -463,6 +475,35 @@ __device__ __forceinline__ void substep_m(const ReplicaDev &rp, const BodyShared
     const float h = last ? rp.hdt_f : rp.dt_f;
 #pragma unroll
     for (int t = 0; t < 3; ++t) w.v[t] = fmaf(h, f[t], w.v[t]);
+}
+
+// Mixed path, first phase of one near particle's sub-step: true when the
+// drifted particle may be in reach of a bead (the first test of grid_range),
+// w unchanged; else the sub-step of substep_m completed here, with no bead in
+// reach: body force g only, no catalytic range.
+__device__ __forceinline__ bool substep_far_m(const ReplicaDev &rp, const BodyShared &S, BWorkM &w, uint32_t step,
+                                              int s, bool last)
+{
+    float o[3];
+#pragma unroll
+    for (int t = 0; t < 3; ++t) o[t] = fmaf(rp.dt_f, w.v[t], w.o[t]);
+    const int c[3] = {cw_get(w.cw, 0), cw_get(w.cw, 1), cw_get(w.cw, 2)};
+    float dc[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dc[k] = (float)(c[k] - S.Ci[k]) + (o[k] - S.Cf[k]);
+    min_image(rp, dc);
+    if (dc[0] * dc[0] + dc[1] * dc[1] + dc[2] * dc[2] < S.reach2_f) return true;
+    float f[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        w.o[t] = o[t];
+        f[t] = f[t] + rp.g_f[t];
+    }
+    w.fid = catalysis(rp, w.fid, false, step, s);
+    const float h = last ? rp.hdt_f : rp.dt_f;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) w.v[t] = fmaf(h, f[t], w.v[t]);
+    return false;
 }
 
 // Mixed path: write one particle back after the interval (and bin it for the
@@ -590,6 +631,7 @@ __global__ void __launch_bounds__(MDB_NT, 2) k_md_body(Dev d, uint32_t step, int
     const float sf[3] = {(float)sh[0], (float)sh[1], (float)sh[2]};
     for (int s = 0; s < rp.n_md; ++s) {
         if (tid == 0) {
+            S.nreach = 0;
             if (MIXED) {
                 body_kick_drift_rotate_fast(S, dt, hdt);
                 body_frames_fast(rp, S);
@@ -604,22 +646,41 @@ __global__ void __launch_bounds__(MDB_NT, 2) k_md_body(Dev d, uint32_t step, int
 #pragma unroll
         for (int i = 0; i < 6; ++i) acc[i] = 0;
         if constexpr (MIXED) {
-            // two particles per iteration: both records are loaded before either is used
+            // Two phases.  1: whole warps over the near particles; a particle
+            // that no bead can reach takes its whole sub-step here, one that
+            // may be in reach is listed (one shared-memory atomic per warp).
+            // 2: the threads take the listed particles densely, so the bead
+            // loops run without the lanes of the particles out of reach.  The
+            // list lives past the work records in md_work (64 bytes per
+            // solvent slot for the mixed body path, the records take 32).
             const bool last = s + 1 == rp.n_md;
-            for (int k = tid; k < nn; k += 2 * MDB_NT) {
-                const int k1 = k + MDB_NT;
-                const bool two = k1 < nn;
-                BWorkM w0 = work[k];
-                BWorkM w1 = two ? work[k1] : w0;
-                substep_m(rp, S, B, w0, acc, step, s, last);
-                if (two) substep_m(rp, S, B, w1, acc, step, s, last);
-                if (!last) {
-                    work[k] = w0;
-                    if (two) work[k1] = w1;
-                } else {
-                    finish_m(d, rp, rbuf, bbuf, do_bin, sf, w0, do_bin ? -1 : list[k]);
-                    if (two) finish_m(d, rp, rbuf, bbuf, do_bin, sf, w1, do_bin ? -1 : list[k1]);
+            const int lane = tid & 31;
+            int *reach_list = reinterpret_cast<int *>(reinterpret_cast<BWorkM *>(d.md_work) + d.n_total) + rp.part_off;
+            for (int kb = tid - lane; kb < nn; kb += MDB_NT) {
+                const int k = kb + lane;
+                bool reach = false;
+                if (k < nn) {
+                    BWorkM w = work[k];
+                    reach = substep_far_m(rp, S, w, step, s, last);
+                    if (!reach) {
+                        if (!last) work[k] = w;
+                        else finish_m(d, rp, rbuf, bbuf, do_bin, sf, w, do_bin ? -1 : list[k]);
+                    }
                 }
+                const unsigned m = __ballot_sync(0xffffffffu, reach);
+                int base = 0;
+                if (lane == 0 && m != 0u) base = atomicAdd(&S.nreach, __popc(m));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (reach) reach_list[base + __popc(m & ((1u << lane) - 1u))] = k;
+            }
+            __syncthreads();
+            const int nr = S.nreach;
+            for (int i = tid; i < nr; i += MDB_NT) {
+                const int k = reach_list[i];
+                BWorkM w = work[k];
+                substep_m(rp, S, B, w, acc, step, s, last);
+                if (!last) work[k] = w;
+                else finish_m(d, rp, rbuf, bbuf, do_bin, sf, w, do_bin ? -1 : list[k]);
             }
         } else {
             for (int k = tid; k < nn; k += MDB_NT) {
