@@ -675,8 +675,10 @@ __global__ void __launch_bounds__(MDB_NT, 2) k_md_body(Dev d, uint32_t step, int
             }
             __syncthreads();
             const int nr = S.nreach;
+            int k_next = tid < nr ? reach_list[tid] : 0;   // each list entry is read one iteration ahead
             for (int i = tid; i < nr; i += MDB_NT) {
-                const int k = reach_list[i];
+                const int k = k_next;
+                if (i + MDB_NT < nr) k_next = reach_list[i + MDB_NT];
                 BWorkM w = work[k];
                 substep_m(rp, S, B, w, acc, step, s, last);
                 if (!last) work[k] = w;
