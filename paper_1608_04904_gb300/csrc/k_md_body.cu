@@ -227,13 +227,20 @@ __device__ void body_kick_fast(BodyShared &S, double hdt)
     }
 }
 
-__device__ void body_kick_drift_rotate_fast(BodyShared &S, double dt, double hdt)
+// The sub-step's first half kick and drift of the centre, and the half kick
+// of l; then (body_rotate_fast) the free rotation.  The particles' reach test
+// needs the centre only, so the rotation runs beside it.
+__device__ void body_kick_drift_fast(BodyShared &S, double dt, double hdt)
 {
     for (int t = 0; t < 3; ++t) {
         S.V[t] = fma(hdt, S.F[t] * S.invM, S.V[t]);
         S.l[t] = fma(hdt, S.tb[t], S.l[t]);
         S.X[t] = fma(dt, S.V[t], S.X[t]);
     }
+}
+
+__device__ void body_rotate_fast(BodyShared &S, double dt)
+{
     double q[4] = {S.q[0], S.q[1], S.q[2], S.q[3]};
     double l[3] = {S.l[0], S.l[1], S.l[2]};
 #pragma unroll
@@ -260,8 +267,9 @@ __device__ void body_kick_drift_rotate_fast(BodyShared &S, double dt, double hdt
     for (int i = 0; i < 3; ++i) S.l[i] = l[i];
 }
 
-// Frame of the mixed path: R, the wrapped centre's cell and FP32 offset.
-__device__ void body_frames_fast(const ReplicaDev &rp, BodyShared &S)
+// Frame of the mixed path: R (body_rotation_frame_fast), the wrapped
+// centre's cell and FP32 offset (body_centre_frame_fast).
+__device__ void body_rotation_frame_fast(BodyShared &S)
 {
     const double w = S.q[0], x = S.q[1], y = S.q[2], z = S.q[3];
     S.R[0][0] = 1.0 - 2.0 * (y * y + z * z);
@@ -273,8 +281,12 @@ __device__ void body_frames_fast(const ReplicaDev &rp, BodyShared &S)
     S.R[2][0] = 2.0 * (x * z - w * y);
     S.R[2][1] = 2.0 * (y * z + w * x);
     S.R[2][2] = 1.0 - 2.0 * (x * x + y * y);
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 3; ++k)
         for (int t = 0; t < 3; ++t) S.Rf[k][t] = (float)S.R[k][t];
+}
+__device__ void body_centre_frame_fast(const ReplicaDev &rp, BodyShared &S)
+{
+    for (int k = 0; k < 3; ++k) {
         const double fl = floor(S.X[k]);
         int c = (int)fl;
         float o = (float)(S.X[k] - fl);
@@ -282,6 +294,11 @@ __device__ void body_frames_fast(const ReplicaDev &rp, BodyShared &S)
         S.Ci[k] = imod(c, rp.L[k]);
         S.Cf[k] = o;
     }
+}
+__device__ void body_frames_fast(const ReplicaDev &rp, BodyShared &S)
+{
+    body_rotation_frame_fast(S);
+    body_centre_frame_fast(rp, S);
 }
 
 // Fixed-point totals of the warps -> F and the body-frame torque R^T T.
@@ -633,30 +650,39 @@ __global__ void __launch_bounds__(MDB_NT, 2) k_md_body(Dev d, uint32_t step, int
         if (tid == 0) {
             S.nreach = 0;
             if (MIXED) {
-                body_kick_drift_rotate_fast(S, dt, hdt);
-                body_frames_fast(rp, S);
+                // the centre now; the rotation beside the particles' first phase
+                body_kick_drift_fast(S, dt, hdt);
+                body_centre_frame_fast(rp, S);
             } else {
                 body_kick_drift_rotate(S, dt, hdt);
                 body_frames(rp, S);
             }
         }
         __syncthreads();
-        bead_frames<MIXED>(S, B);
-        __syncthreads();
+        if constexpr (!MIXED) {
+            bead_frames<MIXED>(S, B);
+            __syncthreads();
+        }
 #pragma unroll
         for (int i = 0; i < 6; ++i) acc[i] = 0;
         if constexpr (MIXED) {
-            // Two phases.  1: whole warps over the near particles; a particle
-            // that no bead can reach takes its whole sub-step here, one that
-            // may be in reach is listed (one shared-memory atomic per warp).
-            // 2: the threads take the listed particles densely, so the bead
-            // loops run without the lanes of the particles out of reach.  The
-            // list lives past the work records in md_work (64 bytes per
-            // solvent slot for the mixed body path, the records take 32).
+            // Two phases.  1: warps 1.. over the near particles; a particle
+            // that no bead can reach (the test needs the body's centre only)
+            // takes its whole sub-step here, one that may be in reach is
+            // listed (one shared-memory atomic per warp); meanwhile thread 0
+            // turns the body and the bead offsets follow.  2: the threads take
+            // the listed particles densely, so the bead loops run without the
+            // lanes of the particles out of reach.  The list lives past the
+            // work records in md_work (64 bytes per solvent slot for the mixed
+            // body path, the records take 32).
             const bool last = s + 1 == rp.n_md;
-            const int lane = tid & 31;
+            const int lane = tid & 31, wid = tid >> 5;
             int *reach_list = reinterpret_cast<int *>(reinterpret_cast<BWorkM *>(d.md_work) + d.n_total) + rp.part_off;
-            for (int kb = tid - lane; kb < nn; kb += MDB_NT) {
+            if (tid == 0) {
+                body_rotate_fast(S, dt);
+                body_rotation_frame_fast(S);
+            }
+            for (int kb = (wid - 1) * 32; wid > 0 && kb < nn; kb += (MDB_NW - 1) * 32) {
                 const int k = kb + lane;
                 bool reach = false;
                 if (k < nn) {
@@ -673,6 +699,8 @@ __global__ void __launch_bounds__(MDB_NT, 2) k_md_body(Dev d, uint32_t step, int
                 base = __shfl_sync(0xffffffffu, base, 0);
                 if (reach) reach_list[base + __popc(m & ((1u << lane) - 1u))] = k;
             }
+            __syncthreads();
+            bead_frames<MIXED>(S, B);
             __syncthreads();
             const int nr = S.nreach;
             int k_next = tid < nr ? reach_list[tid] : 0;   // each list entry is read one iteration ahead
