@@ -317,9 +317,9 @@ __device__ void body_totals(BodyShared &S)
 
 // Bead offsets R b_j (and FP64 positions Xw + R b_j) for the current frame.
 template <bool MIXED>
-__device__ void bead_frames(BodyShared &S, const BeadSmem &B)
+__device__ void bead_frames(BodyShared &S, const BeadSmem &B, int first = threadIdx.x, int stride = MDB_NT)
 {
-    for (int j = threadIdx.x; j < S.nb; j += MDB_NT) {
+    for (int j = first; j < S.nb; j += stride) {
         if (MIXED) {
             const double b0 = B.b[3 * j], b1 = B.b[3 * j + 1], b2 = B.b[3 * j + 2];
 #pragma unroll
@@ -669,18 +669,23 @@ __global__ void __launch_bounds__(MDB_NT, 2) k_md_body(Dev d, uint32_t step, int
             // Two phases.  1: warps 1.. over the near particles; a particle
             // that no bead can reach (the test needs the body's centre only)
             // takes its whole sub-step here, one that may be in reach is
-            // listed (one shared-memory atomic per warp); meanwhile thread 0
-            // turns the body and the bead offsets follow.  2: the threads take
-            // the listed particles densely, so the bead loops run without the
-            // lanes of the particles out of reach.  The list lives past the
-            // work records in md_work (64 bytes per solvent slot for the mixed
-            // body path, the records take 32).
+            // listed (one shared-memory atomic per warp); meanwhile warp 0
+            // turns the body (thread 0) and recomputes the bead offsets.  2:
+            // the threads take the listed particles densely, so the bead loops
+            // run without the lanes of the particles out of reach.  The list
+            // lives past the work records in md_work (64 bytes per solvent
+            // slot for the mixed body path, the records take 32).
             const bool last = s + 1 == rp.n_md;
             const int lane = tid & 31, wid = tid >> 5;
             int *reach_list = reinterpret_cast<int *>(reinterpret_cast<BWorkM *>(d.md_work) + d.n_total) + rp.part_off;
-            if (tid == 0) {
-                body_rotate_fast(S, dt);
-                body_rotation_frame_fast(S);
+            if (wid == 0) {
+                // warp 0: the turn (thread 0), then the bead offsets of the new frame
+                if (lane == 0) {
+                    body_rotate_fast(S, dt);
+                    body_rotation_frame_fast(S);
+                }
+                __syncwarp();
+                bead_frames<MIXED>(S, B, lane, 32);
             }
             for (int kb = (wid - 1) * 32; wid > 0 && kb < nn; kb += (MDB_NW - 1) * 32) {
                 const int k = kb + lane;
@@ -699,8 +704,6 @@ __global__ void __launch_bounds__(MDB_NT, 2) k_md_body(Dev d, uint32_t step, int
                 base = __shfl_sync(0xffffffffu, base, 0);
                 if (reach) reach_list[base + __popc(m & ((1u << lane) - 1u))] = k;
             }
-            __syncthreads();
-            bead_frames<MIXED>(S, B);
             __syncthreads();
             const int nr = S.nreach;
             int k_next = tid < nr ? reach_list[tid] : 0;   // each list entry is read one iteration ahead
