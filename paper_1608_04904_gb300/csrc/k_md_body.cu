@@ -26,8 +26,11 @@
 // mixed path's integrator has none on its sub-step chain (reciprocals of M
 // and I_k precomputed, Newton reciprocal and inverse square root from an
 // FP32 seed); the FP64 path keeps the FP64 definition's divisions.  After
-// every turn the CTA recomputes the bead offsets R b_j (FP64, rounded to FP32
-// on the mixed path) in shared memory.  A particle finds the
+// every turn the bead offsets R b_j are recomputed (FP64, rounded to FP32 on
+// the mixed path) in shared memory.  On the mixed path the centre moves
+// first, and the turn and the bead offsets (warp 0) run beside the first
+// phase of the particles' sub-step, whose reach test needs the centre only.
+// A particle finds the
 // beads it can reach through a lookup grid in the body frame, built on the
 // host once per body: the grid cell of the particle's body-frame position
 // lists, in ascending order, every bead whose cut-off plus a margin reaches
